@@ -1,0 +1,262 @@
+"""CPU oracle for interleaved streaming rANS -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` leg of
+``bench.py`` may import this package.  The product package
+(``paper_1402_3392_b300``) never imports it, and the two share no code.
+
+The arithmetic lives in ``rans_oracle.c`` (plain scalar C, Algorithm 1 of
+Giesen, "Interleaved entropy coders", run by N round-robin coders, Section 3).
+This module compiles it with gcc on first use and wraps it with ctypes.
+
+``load(mutant=k)`` builds a copy with one planted mistake (k >= 1); the pin
+tests use those copies to show that each plausible mistake is caught.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rans_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict[int, C.CDLL] = {}
+
+# Oracle status codes (its own, independent of the library's).
+OK, ERR_ARG, ERR_SYMBOL, ERR_SPACE, ERR_CORRUPT, ERR_INVARIANT = range(6)
+
+# Production parameters of the container (readings of the paper, Section 5).
+L_PROD = 1 << 16
+B_PROD = 1 << 16
+LOG2_M_PROD = 12
+M_PROD = 1 << LOG2_M_PROD
+
+_u64p = C.POINTER(C.c_uint64)
+_u32p = C.POINTER(C.c_uint32)
+_u16p = C.POINTER(C.c_uint16)
+_u8p = C.POINTER(C.c_uint8)
+
+
+def lib_path(mutant: int = 0) -> str:
+    name = "librans_oracle.so" if mutant == 0 else f"librans_oracle_mutant{mutant}.so"
+    return os.path.join(_BUILD, name)
+
+
+def build(mutant: int = 0, force: bool = False) -> str:
+    """Compile the oracle (gcc -O2) into oracle/_build/ and return the path."""
+    out = lib_path(mutant)
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = f"{out}.{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-Wall", "-Wextra", "-shared", "-fPIC",
+           f"-DORACLE_MUTANT={mutant}", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def load(mutant: int = 0) -> C.CDLL:
+    with _LOCK:
+        if mutant in _LIBS:
+            return _LIBS[mutant]
+        lib = C.CDLL(build(mutant))
+        lib.orc_encode.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                   _u32p, C.c_uint64, _u64p, C.c_uint64, _u64p, _u64p,
+                                   _u64p, _u32p, C.c_uint64, _u64p, _u32p]
+        lib.orc_encode.restype = C.c_int
+        lib.orc_decode.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                   _u64p, C.c_uint64, _u64p, C.c_uint64, _u32p, _u64p, _u64p,
+                                   _u64p, _u32p, C.c_uint64, _u64p, _u32p]
+        lib.orc_decode.restype = C.c_int
+        lib.orc_C.argtypes = [_u64p, C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_int)]
+        lib.orc_C.restype = C.c_uint64
+        lib.orc_D.argtypes = [_u64p, C.c_uint32, C.c_uint64, _u32p, C.POINTER(C.c_int)]
+        lib.orc_D.restype = C.c_uint64
+        lib.orc_max_message_size.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        lib.orc_max_message_size.restype = C.c_uint64
+        lib.orc_encode_chunk.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                         _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_chunk.restype = C.c_int
+        lib.orc_decode_chunk.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                         _u8p, C.c_uint64]
+        lib.orc_decode_chunk.restype = C.c_int
+        lib.orc_encode_message.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                           C.c_uint32, _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_message.restype = C.c_int
+        lib.orc_decode_message.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                           C.c_uint32, _u8p, C.c_uint64]
+        lib.orc_decode_message.restype = C.c_int
+        lib.orc_quantize.argtypes = [_u64p, C.c_uint32, C.c_uint32, _u16p]
+        lib.orc_quantize.restype = C.c_int
+        _LIBS[mutant] = lib
+        return lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+class Oracle:
+    """ctypes front end of one build of the oracle (mutant 0 = the real one)."""
+
+    def __init__(self, mutant: int = 0):
+        self.mutant = mutant
+        self.lib = load(mutant)
+
+    # -- generic coder (any L, b, M; words are base-b digits) ----------------
+    def encode(self, freq, symbols, N=1, L=L_PROD, b=B_PROD, trace=False):
+        """Algorithm 1 encoder, N interleaved coders.
+
+        Returns dict(words, states, max_iters[, trace_state, trace_lane]).
+        ``words`` is in decoder read order."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        n = s.size
+        cap = max(1, 64 * n + 64)
+        words = np.zeros(cap, dtype=np.uint64)
+        states = np.zeros(N, dtype=np.uint64)
+        nw = C.c_uint64(0)
+        it = C.c_uint32(0)
+        tcap = (64 * n + N + 64) if trace else 0
+        ts = np.zeros(max(tcap, 1), dtype=np.uint64)
+        tl = np.zeros(max(tcap, 1), dtype=np.uint32)
+        nt = C.c_uint64(0)
+        rc = self.lib.orc_encode(_p(f, _u64p), f.size, L, b, N, _p(s, _u32p), n,
+                                 _p(words, _u64p), cap, C.byref(nw), _p(states, _u64p),
+                                 _p(ts, _u64p) if trace else None,
+                                 _p(tl, _u32p) if trace else None, tcap,
+                                 C.byref(nt), C.byref(it))
+        if rc != OK:
+            raise OracleError(rc, "encode")
+        out = dict(words=words[: nw.value].copy(), states=states, max_iters=it.value)
+        if trace:
+            assert nt.value <= tcap
+            out["trace_state"] = ts[: nt.value].copy()
+            out["trace_lane"] = tl[: nt.value].copy()
+        return out
+
+    def decode(self, freq, words, states, n_sym, N=1, L=L_PROD, b=B_PROD, trace=False):
+        """Algorithm 1 decoder, N interleaved coders reading one buffer.
+
+        Returns dict(symbols, consumed, states_end, max_iters[, trace...])."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        st = np.ascontiguousarray(states, dtype=np.uint64)
+        assert st.size == N
+        sym = np.zeros(max(1, n_sym), dtype=np.uint32)
+        st_end = np.zeros(N, dtype=np.uint64)
+        used = C.c_uint64(0)
+        it = C.c_uint32(0)
+        tcap = (64 * n_sym + N + 64) if trace else 0
+        ts = np.zeros(max(tcap, 1), dtype=np.uint64)
+        tl = np.zeros(max(tcap, 1), dtype=np.uint32)
+        nt = C.c_uint64(0)
+        rc = self.lib.orc_decode(_p(f, _u64p), f.size, L, b, N, _p(w, _u64p), w.size,
+                                 _p(st, _u64p), n_sym, _p(sym, _u32p), C.byref(used),
+                                 _p(st_end, _u64p),
+                                 _p(ts, _u64p) if trace else None,
+                                 _p(tl, _u32p) if trace else None, tcap,
+                                 C.byref(nt), C.byref(it))
+        if rc != OK:
+            raise OracleError(rc, "decode")
+        out = dict(symbols=sym[:n_sym].copy(), consumed=used.value, states_end=st_end,
+                   max_iters=it.value)
+        if trace:
+            out["trace_state"] = ts[: nt.value].copy()
+            out["trace_lane"] = tl[: nt.value].copy()
+        return out
+
+    def C(self, freq, s, x):
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        ok = C.c_int(0)
+        r = self.lib.orc_C(_p(f, _u64p), f.size, s, x, C.byref(ok))
+        if not ok.value:
+            raise OracleError(ERR_ARG, "C")
+        return int(r)
+
+    def D(self, freq, x):
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        ok = C.c_int(0)
+        s = C.c_uint32(0)
+        r = self.lib.orc_D(_p(f, _u64p), f.size, x, C.byref(s), C.byref(ok))
+        if not ok.value:
+            raise OracleError(ERR_ARG, "D")
+        return int(s.value), int(r)
+
+    # -- production container (L = b = 2^16, M = 2^12, u16 words) -----------
+    def max_message_size(self, n_sym, N, chunk_symbols):
+        return int(self.lib.orc_max_message_size(n_sym, N, chunk_symbols))
+
+    def encode_message(self, symbols, freq, N=32, chunk_symbols=65536):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        cap = self.max_message_size(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message(_p(s, _u8p), s.size, _p(fr, _u16p), fr.size, N,
+                                         chunk_symbols, _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message")
+        return out[: size.value].copy()
+
+    def decode_message(self, msg, n_sym, freq, N=32, chunk_symbols=65536):
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_message(_p(m, _u8p), m.size, _p(fr, _u16p), fr.size, N,
+                                         chunk_symbols, _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message")
+        return out[:n_sym].copy()
+
+    def encode_chunk(self, symbols, freq, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        cap = 4 * N + 2 * s.size
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk(_p(s, _u8p), s.size, _p(fr, _u16p), fr.size, N,
+                                       _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk")
+        return out[: size.value].copy()
+
+    def decode_chunk(self, chunk, n_sym, freq, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_chunk(_p(c, _u8p), c.size, _p(fr, _u16p), fr.size, N,
+                                       _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk")
+        return out[:n_sym].copy()
+
+    def quantize(self, weights, log2_M=LOG2_M_PROD):
+        w = np.ascontiguousarray(weights, dtype=np.uint64)
+        f = np.zeros(w.size, dtype=np.uint16)
+        rc = self.lib.orc_quantize(_p(w, _u64p), w.size, log2_M, _p(f, _u16p))
+        if rc != OK:
+            raise OracleError(rc, "quantize")
+        return f
+
+
+_DEFAULT: Oracle | None = None
+
+
+def default() -> Oracle:
+    global _DEFAULT
+    if _DEFAULT is None:
+        _DEFAULT = Oracle(0)
+    return _DEFAULT

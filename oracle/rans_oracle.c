@@ -1,0 +1,560 @@
+/*
+ * rans_oracle.c -- CPU ORACLE for interleaved streaming rANS.
+ *
+ * TEST INFRASTRUCTURE.  This file is the independent, plain, slow reference
+ * that the CUDA library is checked against.  Only tests/, the smoke check in
+ * __graft_entry__.py and the cpu_baseline leg of bench.py may load it.  The
+ * product package never includes, links or calls it, and it includes nothing
+ * from the product (no shared header, table, constant or helper).
+ *
+ * What it computes, following F. Giesen, "Interleaved entropy coders"
+ * (arXiv:1402.3392):
+ *
+ *   - Section 2: the coding function C(s,x) and its inverse D(x) with
+ *     C(D(x)) = x.  The paper leaves the concrete C open ("rANS/rABS"); its
+ *     worked example in Section 2.1 is the range variant with M = 4.  The
+ *     general range form used here is
+ *         C(s,x) = floor(x / f_s) * M + B_s + (x mod f_s),  B_s = sum_{t<s} f_t
+ *         D(x)   = (s, f_s * floor(x / M) + (x mod M) - B_s)
+ *     where s is the unique symbol with B_s <= x mod M < B_s + f_s.
+ *     The symbol search in D is a linear scan on purpose (no slot table).
+ *   - Section 2, Algorithm 1: streaming encode / decode with the normalized
+ *     interval I = [L, bL).  Both loops are literal `while` loops:
+ *         Encode: while C(s,x) not in I: emit(x mod b); x = floor(x / b)
+ *                 x = C(s,x)
+ *         Decode: (s,x) = D(x); while x not in I: x = b*x + read()
+ *     The encoder walks the message backwards and the emitted words are
+ *     reversed at the end, so the decoder reads them forwards (Section 2,
+ *     the stack property and the backwards-encoding convention).  The final
+ *     encoder states are transmitted (Section 2).
+ *   - Section 3: N coders interleaved into one buffer with no metadata.
+ *     Symbol i of a message is handled by coder (i mod N); encoder and
+ *     decoder use the same coder sequence.
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - initial encoder state x0 = L for every coder;
+ *   - symbol i -> coder i mod N;
+ *   - production parameters L = 2^16, b = 2^16, M = 2^12 (so b >= M and at
+ *     most one renormalization per symbol, Section 5);
+ *   - the chunked container (header, offset table, chunk layout) and the
+ *     weight -> frequency quantizer are not in the paper at all.
+ *
+ * Generic entry points take (f[], n, L, b) so the paper's own example
+ * (L=16, b=2, M=4) runs through the same code as the production parameters.
+ * State arithmetic is done in unsigned __int128 so that C(s,x) inside the
+ * encoder's loop test never wraps.
+ *
+ * Compile-time ORACLE_MUTANT=k plants one deliberate mistake (tests only use
+ * this to show that the pins catch it); the default build has none.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
+typedef unsigned __int128 u128;
+
+enum {
+    ORC_OK = 0,
+    ORC_ERR_ARG = 1,       /* bad parameters */
+    ORC_ERR_SYMBOL = 2,    /* symbol outside the alphabet or with f_s = 0 */
+    ORC_ERR_SPACE = 3,     /* output buffer too small */
+    ORC_ERR_CORRUPT = 4,   /* decoder: bad start state, ran out of words,
+                              did not end in x0 = L, or left words unread */
+    ORC_ERR_INVARIANT = 5  /* x left I after a step (never expected) */
+};
+
+#define ORC_MAX_ALPHA 4096u
+
+typedef struct {
+    u128 L, b, M;
+    uint32_t n;
+    u128 f[ORC_MAX_ALPHA];
+    u128 B[ORC_MAX_ALPHA];
+} orc_model;
+
+/* Build the model: M = sum f_s, B_s = sum_{t<s} f_t (Section 2: the C/D pair
+ * of the range variant).  Requires b >= 2 and L >= 1 (Section 2). */
+static int model_init(orc_model *m, const uint64_t *f, uint32_t n, uint64_t L, uint64_t b)
+{
+    if (n == 0 || n > ORC_MAX_ALPHA || L == 0 || b < 2) return ORC_ERR_ARG;
+    m->L = L;
+    m->b = b;
+    m->n = n;
+    u128 acc = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+        m->B[s] = acc;
+        m->f[s] = f[s];
+        acc += f[s];
+    }
+    m->M = acc;
+    if (acc == 0) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+static int in_I(const orc_model *m, u128 x)
+{
+    return x >= m->L && x < m->b * m->L;
+}
+
+/* C(s,x) = floor(x/f_s)*M + B_s + (x mod f_s). */
+static u128 C(const orc_model *m, uint32_t s, u128 x)
+{
+    u128 f = m->f[s];
+#if ORACLE_MUTANT == 1
+    return (x / f) * m->M + (x % f);                 /* drops B_s */
+#elif ORACLE_MUTANT == 2
+    return (x / m->M) * f + m->B[s] + (x % f);       /* M and f swapped */
+#else
+    return (x / f) * m->M + m->B[s] + (x % f);
+#endif
+}
+
+/* D(x) = (s, f_s*floor(x/M) + (x mod M) - B_s), s found by a linear scan
+ * over the cumulative frequencies. */
+static u128 D(const orc_model *m, u128 x, uint32_t *s_out)
+{
+    u128 r = x % m->M;
+    uint32_t s = 0;
+    for (s = 0; s < m->n; ++s) {
+#if ORACLE_MUTANT == 7
+        if (m->B[s] < r && r <= m->B[s] + m->f[s]) break;  /* off by one */
+#else
+        if (m->B[s] <= r && r < m->B[s] + m->f[s]) break;
+#endif
+    }
+    if (s == m->n) s = m->n - 1;  /* only reachable under a mutant */
+    *s_out = s;
+    return m->f[s] * (x / m->M) + r - m->B[s];
+}
+
+static uint32_t coder_of(uint64_t i, uint32_t N)
+{
+#if ORACLE_MUTANT == 4
+    return (uint32_t)((i + 1) % N);
+#else
+    return (uint32_t)(i % N);
+#endif
+}
+
+static u128 initial_state(const orc_model *m)
+{
+#if ORACLE_MUTANT == 6
+    return m->L + 1;
+#else
+    return m->L;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Generic coder: Algorithm 1 run by N interleaved coders (Sections 2, 3). */
+/* ---------------------------------------------------------------------- */
+
+static void trace_push(uint64_t *ts, uint32_t *tl, uint64_t cap, uint64_t *nt,
+                       uint32_t lane, u128 x)
+{
+    if (ts && *nt < cap) {
+        ts[*nt] = (uint64_t)x;
+        if (tl) tl[*nt] = lane;
+    }
+    if (ts) ++*nt;
+}
+
+/*
+ * Encode sym[0..n) with N interleaved coders sharing one output buffer.
+ * The message is processed backwards (i = n-1 .. 0); coder (i mod N) runs
+ * Encode(s_i) of Algorithm 1.  Words go into one shared buffer in emission
+ * order; at the end the buffer is reversed so that words[0] is the first
+ * word the decoder reads.  states[j] receives coder j's final state.
+ *
+ * trace (optional): every state a coder passes through, in encoder order,
+ * starting with the N initial states.
+ * max_iters (optional): the largest number of renormalization iterations
+ * any single symbol needed.
+ */
+int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+               const uint32_t *sym, uint64_t n_sym,
+               uint64_t *words, uint64_t word_cap, uint64_t *n_words,
+               uint64_t *states,
+               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+               uint64_t *n_trace, uint32_t *max_iters)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    if (!mp) return ORC_ERR_ARG;
+    int rc = model_init(mp, f, n_alpha, L, b);
+    if (rc || N == 0) { free(mp); return rc ? rc : ORC_ERR_ARG; }
+
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    if (!x) { free(mp); return ORC_ERR_ARG; }
+    uint64_t nt = 0, W = 0;
+    uint32_t worst = 0;
+    for (uint32_t j = 0; j < N; ++j) {
+        x[j] = initial_state(mp);
+        trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+    }
+
+    rc = ORC_OK;
+    for (uint64_t i = n_sym; i-- > 0;) {
+        uint32_t j = coder_of(i, N);
+        uint32_t s = sym[i];
+        if (s >= mp->n || mp->f[s] == 0) { rc = ORC_ERR_SYMBOL; break; }
+        uint32_t iters = 0;
+        /* Algorithm 1, Encode: renormalize while C(s,x) would leave I. */
+        while (!in_I(mp, C(mp, s, x[j]))) {
+            if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+#if ORACLE_MUTANT == 3
+            words[W++] = (uint64_t)(x[j] / mp->b);      /* wrong digit */
+#else
+            words[W++] = (uint64_t)(x[j] % mp->b);
+#endif
+            x[j] = x[j] / mp->b;
+            ++iters;
+            trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+            if (x[j] == 0) { rc = ORC_ERR_INVARIANT; goto done; }
+        }
+        x[j] = C(mp, s, x[j]);
+        trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+        if (!in_I(mp, x[j])) { rc = ORC_ERR_INVARIANT; goto done; }
+        if (iters > worst) worst = iters;
+    }
+done:
+    if (rc == ORC_OK) {
+#if ORACLE_MUTANT != 5
+        /* Reverse: the encoder wrote backwards, the decoder reads forwards. */
+        for (uint64_t a = 0, z = W; a + 1 < z; ++a, --z) {
+            uint64_t t = words[a];
+            words[a] = words[z - 1];
+            words[z - 1] = t;
+        }
+#endif
+        for (uint32_t j = 0; j < N; ++j) states[j] = (uint64_t)x[j];
+        *n_words = W;
+        if (n_trace) *n_trace = nt;
+        if (max_iters) *max_iters = worst;
+    }
+    free(x);
+    free(mp);
+    return rc;
+}
+
+/*
+ * Decode n_sym symbols.  Coder (i mod N) runs Decode of Algorithm 1 for
+ * symbol i, all coders reading the one shared word buffer in order
+ * (Section 3).  states_in are the transmitted final encoder states.
+ * consumed: words read.  states_out: coder states at the end (equal to the
+ * encoder's initial states for a well-formed stream).
+ */
+int orc_decode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+               const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+               uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed, uint64_t *states_out,
+               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+               uint64_t *n_trace, uint32_t *max_iters)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    if (!mp) return ORC_ERR_ARG;
+    int rc = model_init(mp, f, n_alpha, L, b);
+    if (rc || N == 0) { free(mp); return rc ? rc : ORC_ERR_ARG; }
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    if (!x) { free(mp); return ORC_ERR_ARG; }
+
+    uint64_t nt = 0, rp = 0;
+    uint32_t worst = 0;
+    for (uint32_t j = 0; j < N; ++j) {
+        x[j] = states_in[j];
+        if (!in_I(mp, x[j])) rc = ORC_ERR_CORRUPT;   /* Algorithm 1 requires x in I */
+        trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+    }
+    if (rc) goto out;
+
+    for (uint64_t i = 0; i < n_sym; ++i) {
+        uint32_t j = coder_of(i, N);
+        uint32_t s;
+        x[j] = D(mp, x[j], &s);
+        sym_out[i] = s;
+        trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+        uint32_t iters = 0;
+        while (!in_I(mp, x[j])) {
+            if (rp >= n_words || x[j] >= mp->L * mp->b) { rc = ORC_ERR_CORRUPT; goto out; }
+            x[j] = mp->b * x[j] + words[rp++];
+            ++iters;
+            trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
+        }
+        if (iters > worst) worst = iters;
+    }
+    for (uint32_t j = 0; j < N; ++j) states_out[j] = (uint64_t)x[j];
+    *consumed = rp;
+    if (n_trace) *n_trace = nt;
+    if (max_iters) *max_iters = worst;
+out:
+    free(x);
+    free(mp);
+    return rc;
+}
+
+/* Single coding-function evaluations, for checking the oracle against the
+ * paper's printed example (Section 2.1).  *ok = 0 on bad input. */
+uint64_t orc_C(const uint64_t *f, uint32_t n_alpha, uint32_t s, uint64_t x, int *ok)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    *ok = 0;
+    if (!mp) return 0;
+    if (model_init(mp, f, n_alpha, 1, 2) || s >= n_alpha || f[s] == 0) { free(mp); return 0; }
+    u128 r = C(mp, s, x);
+    free(mp);
+    if (r >> 64) return 0;
+    *ok = 1;
+    return (uint64_t)r;
+}
+
+uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out, int *ok)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    *ok = 0;
+    if (!mp) return 0;
+    if (model_init(mp, f, n_alpha, 1, 2)) { free(mp); return 0; }
+    u128 r = D(mp, x, s_out);
+    free(mp);
+    *ok = 1;
+    return (uint64_t)r;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Container with the production parameters (not in the paper).          */
+/*                                                                        */
+/*   L = 2^16, b = 2^16, M = 2^12, 32-bit states, 16-bit words.           */
+/*   header (32 bytes, little endian):                                    */
+/*     u32 magic 0x534E4152, u32 version 1, u32 N, u32 log2_M (12),       */
+/*     u64 n_symbols, u32 chunk_symbols, u32 n_chunks                     */
+/*   u32 offsets[n_chunks+1], chunk start byte offsets within the data    */
+/*     region, offsets[0] = 0, offsets[n_chunks] = data bytes             */
+/*   zero padding to 16 bytes; data region; zero padding to 16 bytes.    */
+/*   chunk c = symbols [c*chunk_symbols, min(n, (c+1)*chunk_symbols)):    */
+/*     u32 state[N] (coder order) then u16 word[W_c] in decoder order.    */
+/* ---------------------------------------------------------------------- */
+
+#define ORC_MAGIC 0x534E4152u
+#define ORC_VERSION 1u
+#define ORC_L (1ull << 16)
+#define ORC_B (1ull << 16)
+#define ORC_LOG2_M 12u
+
+static void put_u32(uint8_t *p, uint32_t v)
+{
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+static void put_u16(uint8_t *p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+static uint32_t get_u32(const uint8_t *p)
+{
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static uint32_t get_u16(const uint8_t *p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static uint64_t round16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
+
+static int prod_table(const uint16_t *freq, uint32_t n_alpha, uint64_t *f64)
+{
+    if (n_alpha == 0 || n_alpha > 256) return ORC_ERR_ARG;
+    uint64_t sum = 0;
+    for (uint32_t s = 0; s < n_alpha; ++s) { f64[s] = freq[s]; sum += freq[s]; }
+    return sum == (1ull << ORC_LOG2_M) ? ORC_OK : ORC_ERR_ARG;
+}
+
+/* Worst case: one word per symbol, since b >= M allows at most one
+ * renormalization per symbol (Section 5). */
+uint64_t orc_max_message_size(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols)
+{
+    if (chunk_symbols == 0 || N == 0) return 0;
+    uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
+    return round16(32 + 4 * (n_chunks + 1)) + round16(4ull * N * n_chunks + 2ull * n_sym);
+}
+
+/* One chunk: [u32 state[N]][u16 words in decoder order]. */
+int orc_encode_chunk(const uint8_t *sym, uint64_t n_c, const uint16_t *freq, uint32_t n_alpha,
+                     uint32_t N, uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    uint64_t f64[256];
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    int rc = prod_table(freq, n_alpha, f64);
+    if (rc) return rc;
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1) * 2);
+    if (!s32 || !w) { free(s32); free(w); return ORC_ERR_ARG; }
+    for (uint64_t i = 0; i < n_c; ++i) s32[i] = sym[i];
+    uint64_t st[32], W = 0;
+    rc = orc_encode(f64, n_alpha, ORC_L, ORC_B, N, s32, n_c, w, 2 * (n_c ? n_c : 1), &W, st,
+                    NULL, NULL, 0, NULL, NULL);
+    if (rc == ORC_OK) {
+        uint64_t need = 4ull * N + 2ull * W;
+        if (need > cap) rc = ORC_ERR_SPACE;
+        else {
+            for (uint32_t j = 0; j < N; ++j) put_u32(out + 4 * j, (uint32_t)st[j]);
+            for (uint64_t k = 0; k < W; ++k) put_u16(out + 4ull * N + 2 * k, (uint32_t)w[k]);
+            *size = need;
+        }
+    }
+    free(s32);
+    free(w);
+    return rc;
+}
+
+int orc_decode_chunk(const uint8_t *chunk, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
+                     uint32_t N, uint8_t *sym_out, uint64_t n_c)
+{
+    uint64_t f64[256];
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    int rc = prod_table(freq, n_alpha, f64);
+    if (rc) return rc;
+    if (size < 4ull * N || ((size - 4ull * N) & 1)) return ORC_ERR_CORRUPT;
+    uint64_t W = (size - 4ull * N) / 2;
+    uint64_t st[32], st_end[32], used = 0;
+    for (uint32_t j = 0; j < N; ++j) st[j] = get_u32(chunk + 4 * j);
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (W ? W : 1));
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    if (!w || !s32) { free(w); free(s32); return ORC_ERR_ARG; }
+    for (uint64_t k = 0; k < W; ++k) w[k] = get_u16(chunk + 4ull * N + 2 * k);
+    rc = orc_decode(f64, n_alpha, ORC_L, ORC_B, N, w, W, st, n_c, s32, &used, st_end,
+                    NULL, NULL, 0, NULL, NULL);
+    if (rc == ORC_OK) {
+        /* A well-formed chunk ends with every coder back at x0 = L and every
+         * word consumed (the decoder unwinds the encoder exactly, Section 3). */
+        for (uint32_t j = 0; j < N; ++j)
+            if (st_end[j] != ORC_L) rc = ORC_ERR_CORRUPT;
+        if (used != W) rc = ORC_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_c; ++i) sym_out[i] = (uint8_t)s32[i];
+    }
+    free(w);
+    free(s32);
+    return rc;
+}
+
+int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq, uint32_t n_alpha,
+                       uint32_t N, uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
+                       uint64_t *size)
+{
+    if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
+    uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
+    if (n_chunks > 0xFFFFFFFEull) return ORC_ERR_ARG;
+    uint64_t data0 = round16(32 + 4 * (n_chunks + 1));
+    if (cap < data0) return ORC_ERR_SPACE;
+    memset(out, 0, data0);
+    put_u32(out + 0, ORC_MAGIC);
+    put_u32(out + 4, ORC_VERSION);
+    put_u32(out + 8, N);
+    put_u32(out + 12, ORC_LOG2_M);
+    put_u32(out + 16, (uint32_t)n_sym);
+    put_u32(out + 20, (uint32_t)(n_sym >> 32));
+    put_u32(out + 24, chunk_symbols);
+    put_u32(out + 28, (uint32_t)n_chunks);
+    uint64_t pos = 0;
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+        uint64_t first = c * chunk_symbols;
+        uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
+        if (pos > 0xFFFFFFFFull) return ORC_ERR_ARG;
+        put_u32(out + 32 + 4 * c, (uint32_t)pos);
+        uint64_t sz = 0;
+        if (data0 + pos > cap) return ORC_ERR_SPACE;
+        int rc = orc_encode_chunk(sym + first, n_c, freq, n_alpha, N, out + data0 + pos,
+                                  cap - data0 - pos, &sz);
+        if (rc) return rc;
+        pos += sz;
+    }
+    if (pos > 0xFFFFFFFFull) return ORC_ERR_ARG;
+    put_u32(out + 32 + 4 * n_chunks, (uint32_t)pos);
+    uint64_t total = data0 + round16(pos);
+    if (total > cap) return ORC_ERR_SPACE;
+    memset(out + data0 + pos, 0, round16(pos) - pos);
+    *size = total;
+    return ORC_OK;
+}
+
+int orc_decode_message(const uint8_t *msg, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
+                       uint32_t N, uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
+{
+    if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
+    if (size < 48 || (size & 15)) return ORC_ERR_CORRUPT;
+    uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
+    uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
+    if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != ORC_VERSION || get_u32(msg + 8) != N ||
+        get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym || get_u32(msg + 24) != chunk_symbols ||
+        get_u32(msg + 28) != n_chunks)
+        return ORC_ERR_CORRUPT;
+    uint64_t data0 = round16(32 + 4 * (n_chunks + 1));
+    if (data0 > size) return ORC_ERR_CORRUPT;
+    uint64_t data_bytes = size - data0;
+    if (get_u32(msg + 32) != 0) return ORC_ERR_CORRUPT;
+    uint64_t end_all = get_u32(msg + 32 + 4 * n_chunks);
+    if (round16(end_all) != data_bytes) return ORC_ERR_CORRUPT;
+    int rc_all = ORC_OK;
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+        uint64_t a = get_u32(msg + 32 + 4 * c), z = get_u32(msg + 32 + 4 * (c + 1));
+        uint64_t first = c * chunk_symbols;
+        uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
+        if (z < a || z > end_all) return ORC_ERR_CORRUPT;
+        int rc = orc_decode_chunk(msg + data0 + a, z - a, freq, n_alpha, N, sym_out + first, n_c);
+        if (rc && !rc_all) rc_all = rc;
+    }
+    return rc_all;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Quantizer: weights w_s -> integer f_s with sum f_s = M (not in the      */
+/* paper; the paper only assumes a static model, Section 7).              */
+/*   1. f_s = floor(w_s * M / W), W = sum w; raised to 1 where w_s > 0.    */
+/*   2. While sum f < M: +1 to symbols with w_s > 0 in order of decreasing */
+/*      remainder (w_s * M mod W), ties to the lower index, cycling.       */
+/*   3. While sum f > M: -1 from the symbol with the largest f_s > 1,      */
+/*      ties to the lower index.                                          */
+/* ---------------------------------------------------------------------- */
+int orc_quantize(const uint64_t *w, uint32_t n, uint32_t log2_M, uint16_t *f_out)
+{
+    if (n == 0 || n > 4096 || log2_M == 0 || log2_M > 15) return ORC_ERR_ARG;
+    const u128 M = (u128)1 << log2_M;
+    u128 W = 0;
+    uint32_t nz = 0;
+    for (uint32_t s = 0; s < n; ++s) { W += w[s]; nz += w[s] != 0; }
+    if (W == 0 || W >> 64 || nz > (uint32_t)M) return ORC_ERR_ARG;
+    u128 *rem = (u128 *)malloc(sizeof(u128) * n);
+    uint32_t *fv = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    unsigned char *used = (unsigned char *)malloc(n);
+    if (!rem || !fv || !used) { free(rem); free(fv); free(used); return ORC_ERR_ARG; }
+    u128 sum = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+        u128 num = (u128)w[s] * M;
+        fv[s] = (uint32_t)(num / W);
+        rem[s] = num % W;
+        if (w[s] > 0 && fv[s] == 0) fv[s] = 1;
+        sum += fv[s];
+    }
+    while (sum < M) {
+        /* one pass in decreasing-remainder order, ties to the lower index */
+        memset(used, 0, n);
+        for (uint32_t k = 0; k < nz && sum < M; ++k) {
+            int best = -1;
+            for (uint32_t s = 0; s < n; ++s) {
+                if (w[s] == 0 || used[s]) continue;
+#if ORACLE_MUTANT == 8
+                if (best < 0 || rem[s] >= rem[best]) best = (int)s;   /* ties to higher index */
+#else
+                if (best < 0 || rem[s] > rem[best]) best = (int)s;
+#endif
+            }
+            used[best] = 1;
+            fv[best] += 1;
+            sum += 1;
+        }
+    }
+    while (sum > M) {
+        int best = -1;
+        for (uint32_t s = 0; s < n; ++s)
+            if (fv[s] > 1 && (best < 0 || fv[s] > fv[best])) best = (int)s;
+        fv[best] -= 1;
+        sum -= 1;
+    }
+    for (uint32_t s = 0; s < n; ++s) f_out[s] = (uint16_t)fv[s];
+    free(rem);
+    free(fv);
+    free(used);
+    return ORC_OK;
+}

@@ -1,0 +1,515 @@
+"""Pins that tie the CPU oracle to what the paper and the mathematics fix.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` and raises AssertionError
+if the oracle disagrees with:
+
+  * values the paper prints for its worked example (Section 2.1, and the
+    bypass-coding paragraph of Section 3), read from tests/golden/;
+  * properties the paper states: C(D(x)) = x (Section 2), encoder and decoder
+    pass through the same states in opposite order (Section 2.1, Section 3),
+    b-uniqueness of the precursor sets (Section 2), at most one
+    renormalization per symbol when b >= M (Section 5), and identical
+    bitstreams for the serial interleaved coder and the vectorised
+    packed-load / packed-store coder (Sections 5 and 6);
+  * closed forms derived here: the power-of-two uniform table, where C is a
+    bit-field insertion; infinite-precision ANS (no renormalization); the
+    coded-size bound around the model's information content;
+  * brute force on tiny inputs (unique decodability).
+
+tests/test_oracle_pins.py runs every pin on the real oracle;
+tests/test_oracle_mutants.py runs them on copies with planted mistakes and
+requires each copy to fail at least one pin.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+
+import numpy as np
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+L16 = 1 << 16
+B16 = 1 << 16
+M12 = 1 << 12
+
+
+def read_golden(name: str) -> dict:
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            k, v = (t.strip() for t in line.split("=", 1))
+            vals[k] = v.split()
+    return vals
+
+
+PAPER = read_golden("paper_example_babba.txt")
+PAPER_FREQ = [1, 3]          # a -> f=1, B=0 ; b -> f=3, B=1 ; M = 4
+PAPER_SYM = {"a": 0, "b": 1}
+
+
+def paper_C(s: int, x: int) -> int:
+    """The paper's printed coding function (Section 2.1)."""
+    return 4 * x if s == 0 else 4 * (x // 3) + (x % 3) + 1
+
+
+def paper_D(x: int):
+    """The paper's printed decoding function (Section 2.1)."""
+    return (0, x // 4) if x % 4 == 0 else (1, 3 * (x // 4) + (x % 4) - 1)
+
+
+def cum_of(freq):
+    f = np.asarray(freq, dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(f)[:-1]])
+
+
+# ----------------------------------------------------------------------------
+# Worked example of Section 2.1
+# ----------------------------------------------------------------------------
+
+def pin_paper_C_D(o):
+    for x in range(0, 600):
+        assert o.C(PAPER_FREQ, 0, x) == paper_C(0, x), ("C(a,x)", x)
+        assert o.C(PAPER_FREQ, 1, x) == paper_C(1, x), ("C(b,x)", x)
+    for x in range(1, 600):
+        assert o.D(PAPER_FREQ, x) == paper_D(x), ("D", x)
+
+
+def pin_paper_precursor_sets(o):
+    L, b = int(PAPER["L"][0]), int(PAPER["b"][0])
+    lo, hi = (int(v) for v in PAPER["I"])
+    assert (lo, hi) == (L, b * L - 1)
+    for s, key in ((0, "precursor_a"), (1, "precursor_b")):
+        got = [x for x in range(0, 200) if L <= o.C(PAPER_FREQ, s, x) < b * L]
+        assert got == [int(v) for v in PAPER[key]], key
+
+
+def _paper_message():
+    return [PAPER_SYM[c] for c in PAPER["message"]]
+
+
+def pin_paper_state_30(o):
+    L, b = int(PAPER["L"][0]), int(PAPER["b"][0])
+    msg = _paper_message()
+    enc = o.encode(PAPER_FREQ, msg, N=1, L=L, b=b)
+    # Decoding the first two symbols ("b", then the first "a") leaves the
+    # decoder in the state the paper names.
+    dec2 = o.decode(PAPER_FREQ, enc["words"], enc["states"], 2, N=1, L=L, b=b)
+    assert list(dec2["symbols"]) == msg[:2]
+    assert int(dec2["states_end"][0]) == int(PAPER["state_after_first_a"][0])
+    full = o.decode(PAPER_FREQ, enc["words"], enc["states"], len(msg), N=1, L=L, b=b)
+    assert list(full["symbols"]) == msg
+    assert full["consumed"] == len(enc["words"])
+    assert int(full["states_end"][0]) == L
+
+
+def pin_paper_lockstep(o):
+    L, b = int(PAPER["L"][0]), int(PAPER["b"][0])
+    msg = _paper_message()
+    enc = o.encode(PAPER_FREQ, msg, N=1, L=L, b=b, trace=True)
+    dec = o.decode(PAPER_FREQ, enc["words"], enc["states"], len(msg), N=1, L=L, b=b,
+                   trace=True)
+    assert list(dec["trace_state"]) == list(enc["trace_state"][::-1])
+    assert 30 in list(dec["trace_state"])
+    assert enc["max_iters"] == 2        # b = 2 < M = 4: two bits at once happen
+
+
+# ----------------------------------------------------------------------------
+# Properties stated in Sections 2, 3, 5
+# ----------------------------------------------------------------------------
+
+def pin_lockstep_interleaved(o):
+    """Encoder and decoder pass through the same (coder, state) sequence in
+    opposite order, for several interleaved coders (Sections 2.1 and 3)."""
+    rng = np.random.default_rng(7)
+    for N, (L, b, freq) in itertools.product(
+            (1, 2, 3, 5), ((16, 2, PAPER_FREQ), (L16, B16, [1000, 3000, 96]))):
+        msg = rng.integers(0, len(freq), size=int(rng.integers(1, 40)))
+        enc = o.encode(freq, msg, N=N, L=L, b=b, trace=True)
+        dec = o.decode(freq, enc["words"], enc["states"], msg.size, N=N, L=L, b=b,
+                       trace=True)
+        assert list(dec["symbols"]) == list(msg)
+        # Each trace starts with the N states a coder holds at the start, then
+        # records (coder, state) after every step.  Per coder, the decoder's
+        # states are the encoder's in reverse order ...
+        for j in range(N):
+            e_j = [int(v) for v, c in zip(enc["trace_state"], enc["trace_lane"]) if c == j]
+            d_j = [int(v) for v, c in zip(dec["trace_state"], dec["trace_lane"]) if c == j]
+            assert d_j == e_j[::-1], (N, j)
+        # ... and the coders take their steps in exactly the reverse order.
+        assert list(dec["trace_lane"][N:]) == list(enc["trace_lane"][N:][::-1])
+
+
+def pin_inverse_exhaustive(o):
+    """D is C's inverse: C(D(x)) = x and D(C(s,x)) = (s,x) (Section 2)."""
+    rng = np.random.default_rng(11)
+    for freq in ([16], [1, 15], [3, 5, 8], list(rng.integers(1, 9, size=6))):
+        n = len(freq)
+        for x in range(1, 1500):
+            s, y = o.D(freq, x)
+            assert o.C(freq, s, y) == x
+            for t in range(n):
+                assert o.D(freq, o.C(freq, t, x)) == (t, x)
+
+
+def pin_precursor_rans_b_unique(o):
+    """For the range coder with M | L the precursor set of every symbol is
+    {k, ..., b*k - 1} with k = f_s * L / M, i.e. b-unique (Section 2)."""
+    for freq, L, b in (([1, 3], 16, 2), ([2, 5, 9], 32, 4), ([1, 1, 6], 64, 3),
+                       ([5, 11], 16, 5)):
+        M = sum(freq)
+        assert L % M == 0
+        for s, f in enumerate(freq):
+            got = [x for x in range(0, b * L + 1) if L <= o.C(freq, s, x) < b * L]
+            k = f * L // M
+            assert got == list(range(k, b * k)), (freq, s)
+
+
+def pin_one_renorm_production(o):
+    """With b = 2^16 >= M = 2^12 no symbol needs more than one
+    renormalization step (Section 5)."""
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        n = int(rng.integers(1, 256))
+        freq = o.quantize(rng.integers(1, 1 << 20, size=n).astype(np.uint64))
+        if trial == 0:
+            freq = np.zeros(n, dtype=np.uint16)
+            freq[0] = M12 - (n - 1)
+            freq[1:] = 1
+        p = freq / freq.sum()
+        msg = rng.choice(n, size=3000, p=p)
+        msg[:50] = n - 1                      # rarest symbol, largest state jumps
+        enc = o.encode(freq, msg, N=int(rng.integers(1, 33)))
+        assert enc["max_iters"] <= 1
+
+
+# ----------------------------------------------------------------------------
+# Closed forms
+# ----------------------------------------------------------------------------
+
+def bit_insertion_stream(symbols, k, N):
+    """Stream for the uniform table over 2^k symbols (f_s = 2^(12-k),
+    B_s = s * 2^(12-k)).  With power-of-two frequencies the coding function
+    inserts the symbol's k bits at bit (12-k) of the state and moves the bits
+    above up by k; renormalization moves the low 16 bits out once the state
+    reaches 2^(32-k) = f_s * 2^20.  Only shifts and masks are used here."""
+    lo_bits = 12 - k
+    x = [L16] * N
+    emitted = []
+    n = len(symbols)
+    for i in range(n - 1, -1, -1):
+        j = i % N
+        s = int(symbols[i])
+        if x[j] >= 1 << (32 - k):
+            emitted.append(x[j] & 0xFFFF)
+            x[j] >>= 16
+        x[j] = ((x[j] >> lo_bits) << 12) | (s << lo_bits) | (x[j] & ((1 << lo_bits) - 1))
+    return emitted[::-1], x
+
+
+def bitlength_word_count(counts, k):
+    """Words emitted by a coder that codes c symbols of k bits each: the
+    state's bit length starts at 16 (x0 = 2^16), grows by exactly k per
+    symbol and drops by exactly 16 per emitted word, emitting whenever it
+    has reached 32 - k before a symbol."""
+    total = 0
+    for c in counts:
+        e = 16
+        for _ in range(c):
+            if e >= 32 - k:
+                e -= 16
+                total += 1
+            e += k
+    return total
+
+
+def pin_uniform_closed_form(o):
+    rng = np.random.default_rng(5)
+    for k, N in itertools.product((1, 2, 4, 8), (1, 7, 32)):
+        freq = [1 << (12 - k)] * (1 << k)
+        n = int(rng.integers(1, 700))
+        msg = rng.integers(0, 1 << k, size=n)
+        enc = o.encode(freq, msg, N=N)
+        words, states = bit_insertion_stream(msg, k, N)
+        assert list(enc["words"]) == words, (k, N)
+        assert list(enc["states"]) == states, (k, N)
+        counts = [len(range(j, n, N)) for j in range(N)]
+        assert len(words) == bitlength_word_count(counts, k)
+        if k == 8:
+            assert len(words) == sum(c // 2 for c in counts)
+
+
+def pin_single_symbol(o):
+    """f_s = M makes C the identity: nothing is emitted and every coder
+    keeps x0 = L."""
+    for freq, s in (([M12], 0), ([0, M12, 0], 1)):
+        msg = [s] * 77
+        enc = o.encode(freq, msg, N=5)
+        assert len(enc["words"]) == 0
+        assert list(enc["states"]) == [L16] * 5
+        dec = o.decode(freq, [], enc["states"], 77, N=5)
+        assert list(dec["symbols"]) == msg
+
+
+def pin_infinite_precision_paper(o):
+    """With an interval so wide that no renormalization happens, streaming
+    ANS is infinite-precision ANS: the final state is the nested coding
+    function of the whole message (Section 1), here with the paper's
+    printed C (Section 2.1)."""
+    L, b = 1 << 20, 1 << 40
+    for n in range(0, 13):
+        for msg in itertools.islice(itertools.product((0, 1), repeat=n), 40):
+            X = L
+            for s in reversed(msg):
+                X = paper_C(s, X)
+            enc = o.encode(PAPER_FREQ, list(msg), N=1, L=L, b=b)
+            assert len(enc["words"]) == 0
+            assert int(enc["states"][0]) == X
+            # Decoding the big state with the paper's D recovers the message.
+            got = []
+            for _ in msg:
+                s, X = paper_D(X)
+                got.append(s)
+            assert tuple(got) == msg and X == L
+
+
+def pin_infinite_precision_general(o):
+    rng = np.random.default_rng(9)
+    L, b = 1 << 16, 1 << 44
+    for _ in range(40):
+        n = int(rng.integers(2, 4))
+        freq = [int(v) for v in rng.integers(1, 6, size=n)]
+        M = sum(freq)
+        B = [sum(freq[:s]) for s in range(n)]
+        msg = [int(v) for v in rng.integers(0, n, size=int(rng.integers(1, 10)))]
+        X = L
+        for s in reversed(msg):
+            X = (X // freq[s]) * M + B[s] + X % freq[s]
+        if not (L <= X < b * L):
+            continue
+        enc = o.encode(freq, msg, N=1, L=L, b=b)
+        assert len(enc["words"]) == 0 and int(enc["states"][0]) == X
+
+
+def pin_size_bound(o):
+    """Coded size against the model's information content.
+
+    For one coding step write x = q f + r (0 <= r < f); then
+    x' = q M + B + r lies in [qM, (q+1)M), so
+        (M/f) (x - f) < x' < (M/f) (x + f).
+    After renormalization x is in the precursor set [16 f, 2^20 f), hence
+        log2(M/f) + log2(15/16) < log2(x'/x) < log2(M/f) + log2(17/16).
+    An emitted word divides x by 2^16 and drops a remainder < 2^16, and the
+    state left behind is >= 16, so each word removes between 16 and
+    16 + log2(17/16) bits.  Telescoping each coder from x0 = L:
+        bits := 16 W + sum_j log2(x_j / L)
+        bits <  sum_i log2(M / f_{s_i}) + n log2(17/16)
+        bits >  sum_i log2(M / f_{s_i}) + n log2(15/16) - W log2(17/16)
+    """
+    rng = np.random.default_rng(13)
+    up, dn = math.log2(17 / 16), math.log2(15 / 16)
+    for trial in range(10):
+        n_alpha = int(rng.integers(2, 257))
+        p = rng.dirichlet(np.full(n_alpha, 0.3 if trial % 2 else 1.0))
+        freq = o.quantize(np.maximum(np.rint(p * 2.0 ** 32), 1).astype(np.uint64))
+        q = freq / freq.sum()
+        n = int(rng.integers(1, 5000))
+        msg = rng.choice(n_alpha, size=n, p=q)
+        N = int(rng.integers(1, 33))
+        enc = o.encode(freq, msg, N=N)
+        W = len(enc["words"])
+        bits = 16 * W + sum(math.log2(int(x) / L16) for x in enc["states"])
+        info = float(np.sum(np.log2(M12 / freq[msg].astype(np.float64))))
+        assert bits < info + n * up + 1e-9
+        assert bits > info + n * dn - W * up - 1e-9
+
+
+# ----------------------------------------------------------------------------
+# Brute force
+# ----------------------------------------------------------------------------
+
+def pin_brute_force_unique(o):
+    """Every message up to length 8 over the paper's alphabet maps to a
+    different (states, words) pair and decodes back (paper parameters)."""
+    L, b = int(PAPER["L"][0]), int(PAPER["b"][0])
+    for N in (1, 2):
+        seen = {}
+        for n in range(0, 9):
+            for msg in itertools.product((0, 1), repeat=n):
+                enc = o.encode(PAPER_FREQ, list(msg), N=N, L=L, b=b)
+                key = (tuple(int(v) for v in enc["states"]), tuple(int(v) for v in enc["words"]))
+                assert key not in seen, (msg, seen.get(key))
+                seen[key] = msg
+                dec = o.decode(PAPER_FREQ, enc["words"], enc["states"], n, N=N, L=L, b=b)
+                assert tuple(int(v) for v in dec["symbols"]) == msg
+                assert dec["consumed"] == len(enc["words"])
+                assert all(int(v) == L for v in dec["states_end"])
+
+
+# ----------------------------------------------------------------------------
+# Serial interleaved == vectorised packed I/O (Sections 5, 6)
+# ----------------------------------------------------------------------------
+
+def packed_store_encode(freq, msg, N, L=L16, b=B16):
+    """All N coders advance together one step at a time (from the last step
+    to the first).  Per step each coder renormalizes at most once -- the
+    `if` form of Section 5 -- using the precursor-set bound x >= b f L / M,
+    and the words of one step are stored packed, in descending coder order
+    (the mirror image of the decoder's packed load)."""
+    freq = np.asarray(freq, dtype=np.uint64)
+    M = int(freq.sum())
+    cum = cum_of(freq).astype(np.uint64)
+    n = len(msg)
+    msg = np.asarray(msg, dtype=np.int64)
+    x = np.full(N, L, dtype=np.uint64)
+    out = []
+    T = -(-n // N)
+    lanes = np.arange(N)
+    for t in range(T - 1, -1, -1):
+        idx = t * N + lanes
+        act = idx < n
+        s = np.where(act, msg[np.minimum(idx, n - 1)], 0)
+        f = np.where(act, freq[s], np.uint64(1))
+        B = cum[s]
+        xmax = np.uint64(L // M * b) * f
+        emit = act & (x >= xmax)
+        for j in np.nonzero(emit)[0][::-1]:
+            out.append(int(x[j] % np.uint64(b)))
+        x = np.where(emit, x // np.uint64(b), x)
+        xc = (x // f) * np.uint64(M) + B + x % f
+        x = np.where(act, xc, x)
+    return out[::-1], [int(v) for v in x]
+
+
+def packed_load_decode(freq, words, states, n, N, L=L16, b=B16):
+    """Vectorised decoder in the GPU form of Section 6: D from a slot table,
+    renorm_mask = (x < L), each renormalizing coder reads the word at
+    read_pos + (number of renormalizing coders before it), then read_pos
+    advances by the mask's population count."""
+    freq = np.asarray(freq, dtype=np.int64)
+    M = int(freq.sum())
+    cum = cum_of(freq)
+    slot_sym = np.repeat(np.arange(len(freq)), freq)
+    x = np.asarray(states, dtype=np.int64).copy()
+    w = np.asarray(words, dtype=np.int64)
+    out = np.zeros(n, dtype=np.int64)
+    rp = 0
+    lanes = np.arange(N)
+    for t in range(-(-n // N)):
+        idx = t * N + lanes
+        act = idx < n
+        slot = x % M
+        s = slot_sym[slot]
+        xn = freq[s] * (x // M) + slot - cum[s]
+        x = np.where(act, xn, x)
+        out[idx[act]] = s[act]
+        mask = act & (x < L)
+        offs = np.cumsum(mask) - mask
+        pos = rp + offs
+        assert pos[mask].size == 0 or pos[mask].max() < w.size
+        x = np.where(mask, x * b + w[np.where(mask, pos, 0)] if w.size else x, x)
+        rp += int(mask.sum())
+    return out, rp, [int(v) for v in x]
+
+
+def pin_packed_io_equivalence(o):
+    rng = np.random.default_rng(17)
+    for trial in range(8):
+        n_alpha = int(rng.integers(1, 257))
+        p = rng.dirichlet(np.full(n_alpha, 0.5))
+        freq = o.quantize(np.maximum(np.rint(p * 2.0 ** 32), 1).astype(np.uint64))
+        q = freq / freq.sum()
+        n = int(rng.integers(0, 3000))
+        N = (1, 4, 13, 32, 32, 31, 2, 32)[trial]
+        msg = rng.choice(n_alpha, size=n, p=q)
+        enc = o.encode(freq, msg, N=N)
+        w2, st2 = packed_store_encode(freq, msg, N)
+        assert [int(v) for v in enc["words"]] == w2
+        assert [int(v) for v in enc["states"]] == st2
+        sym, rp, st_end = packed_load_decode(freq, enc["words"], enc["states"], n, N)
+        assert list(sym) == list(msg)
+        assert rp == len(w2) and st_end == [L16] * N
+
+
+# ----------------------------------------------------------------------------
+# Container (production format) and quantizer
+# ----------------------------------------------------------------------------
+
+def pin_round_trip_edges(o):
+    rng = np.random.default_rng(19)
+    freqs = {
+        1: np.array([M12], dtype=np.uint16),
+        2: np.array([1, M12 - 1], dtype=np.uint16),
+        256: o.quantize(rng.integers(1, 1 << 30, size=256).astype(np.uint64)),
+    }
+    for n_alpha, N, cs in itertools.product((1, 2, 256), (1, 5, 32), (1, 7, 64, 4096)):
+        fr = freqs[n_alpha]
+        for n in sorted({0, 1, N - 1, N, N + 1, cs, cs + 1, 3 * cs - 1, 2 * N * 7 + 3}):
+            if n < 0 or n > 20000:
+                continue
+            msg = rng.choice(n_alpha, size=n, p=fr / fr.sum()).astype(np.uint8)
+            blob = o.encode_message(msg, fr, N=N, chunk_symbols=cs)
+            assert blob.size % 16 == 0
+            back = o.decode_message(blob, n, fr, N=N, chunk_symbols=cs)
+            assert np.array_equal(back, msg)
+
+
+def pin_container_layout(o):
+    rng = np.random.default_rng(23)
+    fr = o.quantize(rng.integers(1, 1 << 30, size=200).astype(np.uint64))
+    for n, N, cs in ((0, 32, 64), (1000, 32, 64), (999, 7, 100), (5, 3, 1)):
+        msg = rng.choice(200, size=n, p=fr / fr.sum()).astype(np.uint8)
+        blob = o.encode_message(msg, fr, N=N, chunk_symbols=cs)
+        h = blob[:32].view(np.uint32)
+        n_chunks = -(-n // cs)
+        assert list(h[:4]) == [0x534E4152, 1, N, 12]
+        assert int(h[4]) | (int(h[5]) << 32) == n
+        assert list(h[6:8]) == [cs, n_chunks]
+        offs = blob[32:32 + 4 * (n_chunks + 1)].view(np.uint32).astype(np.int64)
+        data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+        assert offs[0] == 0 and np.all(np.diff(offs) >= 4 * N)
+        assert blob.size == data0 + (int(offs[-1]) + 15) // 16 * 16
+        assert not blob[32 + 4 * (n_chunks + 1):data0].any()
+        assert not blob[data0 + int(offs[-1]):].any()
+        for c in range(n_chunks):
+            a, z = data0 + offs[c], data0 + offs[c + 1]
+            one = o.encode_chunk(msg[c * cs:(c + 1) * cs], fr, N=N)
+            assert np.array_equal(blob[a:z], one)
+            assert (z - a - 4 * N) % 2 == 0
+
+
+def pin_quantize(o):
+    rng = np.random.default_rng(29)
+    # Hand-worked cases of the stated rule.
+    assert list(o.quantize([1, 1, 1], log2_M=2)) == [2, 1, 1]          # tie -> lower index
+    assert list(o.quantize([5, 3], log2_M=2)) == [3, 1]                # remainders tie (4, 4)
+    assert list(o.quantize([1_000_000, 1, 1, 1], log2_M=2)) == [1, 1, 1, 1]  # excess removed
+    assert list(o.quantize([0, 7, 0, 1], log2_M=3)) == [0, 7, 0, 1]     # exact
+    assert list(o.quantize([3, 0, 1], log2_M=4)) == [12, 0, 4]
+    for _ in range(200):
+        n = int(rng.integers(1, 257))
+        w = rng.integers(0, 1 << int(rng.integers(1, 55)), size=n).astype(np.uint64)
+        w[rng.random(n) < 0.2] = 0
+        if not w.any():
+            w[0] = 1
+        f = o.quantize(w)
+        assert int(f.sum()) == M12
+        assert np.array_equal(f > 0, w > 0)
+        # exact proportional weights are reproduced
+        g = o.quantize(f.astype(np.uint64) * np.uint64(rng.integers(1, 1000)))
+        assert np.array_equal(g, f)
+
+
+ALL_PINS = [
+    pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
+    pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
+    pin_one_renorm_production, pin_uniform_closed_form, pin_single_symbol,
+    pin_infinite_precision_paper, pin_infinite_precision_general, pin_size_bound,
+    pin_brute_force_unique, pin_packed_io_equivalence, pin_round_trip_edges,
+    pin_container_layout, pin_quantize,
+]

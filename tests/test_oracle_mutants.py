@@ -1,0 +1,26 @@
+"""Each planted mistake in the oracle must be caught by at least one pin.
+
+The mutants are compiled from the same source with -DORACLE_MUTANT=k:
+  1 drops B_s from C            2 swaps M and f in C
+  3 emits floor(x/b), not x mod b   4 assigns symbol i to coder (i+1) mod N
+  5 leaves the words in emission order   6 starts the coders at L+1
+  7 off-by-one symbol search in D        8 quantizer ties go to the higher index
+"""
+import pytest
+
+import oracle
+import oracle_pins
+
+MUTANTS = range(1, 9)
+
+
+@pytest.mark.parametrize("k", MUTANTS)
+def test_mutant_is_caught(k):
+    o = oracle.Oracle(mutant=k)
+    caught = []
+    for pin in oracle_pins.ALL_PINS:
+        try:
+            pin(o)
+        except (AssertionError, oracle.OracleError, IndexError, ValueError, ZeroDivisionError):
+            caught.append(pin.__name__)
+    assert caught, f"mutant {k} passed every pin"
