@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 interleaved rANS coder.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chunked]
+                    [--impl ours|reference]
+
+Workload "chunked": 1 GiB of i.i.d. bytes, Zipf(s=1.1) over 256 symbols, a
+static model quantized to M = 2^12, 16384 chunks of 64 KiB, 32 interleaved
+coders per chunk.  One step is the whole hot path over that batch: encode
+(coder kernel, offset-table scan, chunk packing) and then decode.  The
+headline value is decoded GB/s (raw bytes out of the decode phase per
+second); encode GB/s is reported beside it.  Inputs are resident in HBM when
+the timed region starts and are larger than L2, so no flush is needed.
+
+Under torchrun every rank codes its own batch (the chunks are independent,
+so the path shards with no data exchange: weak scaling); rank 0 prints one
+JSON line with the whole-job value and the max-over-ranks time.
+
+--impl reference times the CPU oracle (the plain scalar C implementation the
+tests compare against) on the host cores, on bounded samples of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1402_3392_b300 import workloads as wl  # noqa: E402
+
+DECODE_SOURCE = os.path.join(ROOT, "paper_1402_3392_b300", "csrc", "rans_decode.cu")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "decode_kernel_chunked_1GiB.md")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="chunked", choices=["chunked", "single"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--symbols", type=int, default=0,
+                    help="override the workload's symbol count (small profiling cases)")
+    return ap.parse_args(argv)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(DECODE_SOURCE, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per decode launch from the committed ncu summary, or None
+    if there is none or the kernel source changed since it was captured."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"decode_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML (read only)
+    while the timed region runs."""
+
+    REASONS = {
+        0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+        0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+        0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+        0x100: "display_clock_setting",
+    }
+
+    def __init__(self, device_index: int):
+        self.samples, self.reasons, self.ok = [], 0, False
+        self._stop = threading.Event()
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            import torch
+
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
+            try:
+                self.h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
+            except Exception:
+                self.h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.nv = pynvml
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:  # no NVML: report that instead of clocks
+            self.err = str(e)
+
+    def _run(self):
+        nv = self.nv
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
+                self.reasons |= int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+            except Exception:
+                pass
+            time.sleep(0.005)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self.ok:
+            self.t.join()
+
+    def summary(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
+        names = [n for b, n in self.REASONS.items() if self.reasons & b and n != "gpu_idle"]
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": names, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (the only places bench.py runs oracle/)
+# ---------------------------------------------------------------------------
+
+def oracle_decode_rate(chunks, freq, N, CS, threads, repeats=1):
+    """Decode the given chunks with the CPU oracle on `threads` host threads;
+    returns (decoded bytes per second, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    orc = oracle.default()
+
+    def work(ch):
+        orc.decode_chunk(ch, CS, freq, N=N)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        for _ in range(repeats):
+            list(ex.map(work, chunks))
+    dt = time.perf_counter() - t0
+    return len(chunks) * CS * repeats / dt, dt
+
+
+def split_chunks(msg: np.ndarray, n_chunks: int):
+    data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+    offs = msg[32:32 + 4 * (n_chunks + 1)].view(np.uint32).astype(np.int64)
+    return [msg[data0 + offs[c]:data0 + offs[c + 1]] for c in range(n_chunks)]
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    cfg = wl.WORKLOADS[args.workload]
+    N, CS = cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    orc = oracle.default()
+    freq = orc.quantize(wl.weights_from_probs(p))
+    cores = host_cores()
+    per_step = max(1, min(cores * 2, 256))  # chunks decoded per step
+    n = per_step * CS
+    sym = wl.iid_symbols(wl.rng_for(args.workload), p, n)
+    msg = orc.encode_message(sym, freq, N=N, chunk_symbols=CS)
+    chunks = split_chunks(msg, per_step)
+    for _ in range(args.warmup):
+        oracle_decode_rate(chunks[:cores], freq, N, CS, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_decode_rate(chunks, freq, N, CS, cores)
+        times.append(dt)
+    gbs = n * len(times) / sum(times) / 1e9
+    sample = (f"{per_step} chunks x {CS} symbols of the {args.workload} workload per step, "
+              f"oracle decode, {cores} threads")
+    line = {
+        "impl": "reference", "metric": "decoded GB/s", "value": gbs, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(args.workload, 1),
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(name, world, n_symbols=None):
+    cfg = wl.WORKLOADS[name]
+    d = {"workload": name, "n_symbols": n_symbols or cfg["n_symbols"], "alphabet": cfg["alphabet"],
+         "zipf_s": cfg["zipf_s"], "n_lanes": cfg["n_lanes"],
+         "chunk_symbols": cfg["chunk_symbols"], "log2_M": 12, "L": 65536, "b": 65536,
+         "parallelism": f"independent batch per rank x{world}",
+         "l2": "inputs larger than L2 (no flush needed)",
+         "step": "encode + decode of the batch; value counts the decode phase"}
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1402_3392_b300 import rans
+
+    cfg = wl.WORKLOADS[args.workload]
+    n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    freq = rans.rans_quantize_table(wl.weights_from_probs(p))
+    sym = wl.iid_symbols_device(p, n, wl.seed_for(args.workload, rank), dev)
+
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    scap = rans.rans_encode_scratch_size(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    out_size = torch.zeros(1, dtype=torch.int64, device=dev)
+    enc_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = torch.empty(n, dtype=torch.uint8, device=dev)
+    dec_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    # Encode once to learn the message size the decode phase reads.
+    rans.rans_encode(sym, n, freq, N, CS, msg, cap, out_size, enc_status, scratch, scap, stream)
+    torch.cuda.synchronize(dev)
+    msg_size = int(out_size.item())
+    assert int(enc_status.item()) == 0 and msg_size > 0
+
+    def step(evs):
+        evs[0].record(stream)
+        rans.rans_encode(sym, n, freq, N, CS, msg, cap, out_size, enc_status, scratch, scap,
+                         stream)
+        evs[1].record(stream)
+        rans.rans_decode(msg, msg_size, freq, N, CS, dec, n, dec_status, stream)
+        evs[2].record(stream)
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]  # noqa: E731
+    for _ in range(args.warmup):
+        step(mk())
+    torch.cuda.synchronize(dev)
+    ok = (int(enc_status.item()) == 0 and int(dec_status.item()) == 0
+          and int(out_size.item()) == msg_size and torch.equal(dec, sym))
+    if not ok:
+        raise SystemExit("round trip failed in warm-up")
+
+    evs = [mk() for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    with sampler:
+        t0 = time.perf_counter()
+        for e in evs:
+            step(e)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+    enc_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    dec_ms = [b.elapsed_time(c) for _, b, c in evs]
+    step_ms = evs[0][0].elapsed_time(evs[-1][2]) / args.steps
+    ok = int(dec_status.item()) == 0 and torch.equal(dec, sym)
+
+    t = torch.tensor([statistics.mean(dec_ms), statistics.mean(enc_ms), step_ms, wall],
+                     dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dec_mean, enc_mean, step_mean, wall_max = t.tolist()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(rans, msg[:msg_size], n, freq, N, CS, dev, max(3, min(args.steps, 10)))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(msg[:msg_size].cpu().numpy(), freq, N, CS, n // CS)
+
+    if rank == 0:
+        hbm, peak_kind = peaks()
+        alg_bytes = msg_size + n
+        achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
+        line = {
+            "metric": "decoded GB/s", "value": world * n / (dec_mean * 1e-3) / 1e9,
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(args.workload, world, n),
+            "decode_ms": dec_mean, "encode_ms": enc_mean,
+            "encode_gbs": world * n / (enc_mean * 1e-3) / 1e9,
+            "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "decode_kernel", "bound": "hbm", "achieved": achieved,
+                         "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": profiled_traffic(),
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "clocks": sampler.summary(),
+            "gpu_launches": 4 * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def end_to_end(rans, msg_dev, n, freq, N, CS, dev, steps):
+    """Decoded GB/s through the C ABI with host buffers: each step copies the
+    message from pinned host memory, decodes, and copies the symbols and the
+    status word back to pinned host memory."""
+    import torch
+
+    h_msg = torch.empty(msg_dev.numel(), dtype=torch.uint8, pin_memory=True)
+    h_msg.copy_(msg_dev)
+    h_out = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_st = torch.empty(1, dtype=torch.int32, pin_memory=True)
+    d_msg = torch.empty_like(msg_dev)
+    d_out = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_st = torch.zeros(1, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+
+    def one():
+        with torch.cuda.stream(s):
+            d_msg.copy_(h_msg, non_blocking=True)
+            rans.rans_decode(d_msg, d_msg.numel(), freq, N, CS, d_out, n, d_st, s)
+            h_out.copy_(d_out, non_blocking=True)
+            h_st.copy_(d_st, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(steps):
+        one()
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    assert int(h_st.item()) == 0
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(msg_dev.numel()), "d2h_bytes_per_step": n + 4}
+
+
+def cpu_baseline(msg, freq, N, CS, n_chunks):
+    cores = host_cores()
+    chunks = split_chunks(msg, n_chunks)
+    count = min(len(chunks), 24 * cores)
+    rate, dt = oracle_decode_rate(chunks[:count], freq, N, CS, cores)
+    return {"value": rate / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle decode of {count} chunks x {CS} symbols of this workload's "
+                      f"message ({count * CS / 2**20:.0f} MiB) on {cores} threads, "
+                      f"{dt:.1f} s"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

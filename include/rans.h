@@ -1,0 +1,170 @@
+/*
+ * rans.h -- C ABI of the B300 interleaved streaming rANS library
+ *           (libinterleaved_rans_b300.so).
+ *
+ * The library encodes and decodes byte streams with static-model streaming
+ * rANS, N coders interleaved into one bitstream without metadata, following
+ * F. Giesen, "Interleaved entropy coders" (arXiv:1402.3392):
+ *
+ *   - coding function C(s,x) = floor(x/f_s)*M + B_s + (x mod f_s) and its
+ *     inverse D (Section 2; the paper's worked example in Section 2.1 is this
+ *     function with M = 4), B_s = f_0 + ... + f_{s-1};
+ *   - streaming with the normalized interval I = [L, bL) (Section 2,
+ *     Algorithm 1); the encoder runs over the message backwards and writes
+ *     backwards, the decoder runs forwards; the final encoder states are
+ *     transmitted (Section 2);
+ *   - N coders share one word buffer, symbol i is coded by coder i mod N
+ *     (Section 3);
+ *   - L = 2^16, b = 2^16 (16-bit words), M = 2^12, 32-bit states: b >= M, so
+ *     every symbol needs at most one renormalization step and the bitstream
+ *     does not depend on how many coders run in parallel (Section 5).  On the
+ *     GPU one coder is one warp lane; the renormalization reads and writes of
+ *     a step are placed by a warp ballot and prefix population counts
+ *     (Section 6).
+ *
+ * Message format (little endian; the paper defines no container):
+ *   bytes 0..31  header: u32 magic 0x534E4152 ("RANS"), u32 version 1,
+ *                u32 n_lanes N, u32 log2_M (12), u64 n_symbols,
+ *                u32 chunk_symbols, u32 n_chunks = ceil(n_symbols/chunk_symbols)
+ *   u32 offsets[n_chunks + 1]: start of chunk c in bytes, relative to the
+ *                data region; offsets[0] = 0, offsets[n_chunks] = data bytes
+ *   zero padding up to data0 = round_up(32 + 4*(n_chunks+1), 16)
+ *   data region: the chunks back to back; chunk c codes symbols
+ *                [c*chunk_symbols, min(n_symbols, (c+1)*chunk_symbols)) as
+ *                u32 state[N] (final encoder state of coder 0..N-1) followed
+ *                by the u16 words in decoder read order
+ *   zero padding up to a multiple of 16 bytes (the message size).
+ * Chunks are independent streams, so a message of many chunks keeps every SM
+ * busy.  The frequency table is not stored: like the model of Section 3 it
+ * is agreed out of band.
+ *
+ * Conventions for every call:
+ *   - Ownership: the caller allocates and frees every buffer.  Pointers named
+ *     d_* are device pointers; h_* are host pointers.  The library keeps no
+ *     pointer after a call returns.
+ *   - Streams: work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and the call returns without synchronizing.
+ *   - Errors: argument errors are returned synchronously and enqueue
+ *     nothing.  Errors found in the data (a corrupt or truncated message, a
+ *     symbol without probability) are written to a device status word and
+ *     never trap.  RANS_ERR_CUDA means a CUDA call failed (launch error).
+ *   - Device code runs on the current CUDA device, which must be sm_103.
+ */
+#ifndef INTERLEAVED_RANS_B300_H_
+#define INTERLEAVED_RANS_B300_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
+
+/* Status codes (return values and device status words). */
+#define RANS_OK                   0
+#define RANS_ERR_INVALID_ARG      1  /* bad argument, alignment or size */
+#define RANS_ERR_ZERO_FREQ        2  /* input holds a symbol with f_s = 0 or s >= n_alpha */
+#define RANS_ERR_BUFFER_TOO_SMALL 3  /* output or scratch capacity too small */
+#define RANS_ERR_CORRUPT          4  /* message header, offsets or chunk contents inconsistent */
+#define RANS_ERR_TIMEOUT          5  /* a bounded device-side wait gave up */
+#define RANS_ERR_CUDA             6  /* a CUDA runtime call or launch failed */
+#define RANS_ERR_OOM              7  /* an admission or allocation budget was exceeded */
+
+/* Fixed coding parameters (Section 5 of the paper: b >= M). */
+#define RANS_LOG2_M        12
+#define RANS_M             4096u
+#define RANS_L             65536u      /* I = [2^16, 2^32) */
+#define RANS_LOG2_B        16
+#define RANS_MAX_ALPHABET  256
+#define RANS_MAX_LANES     32
+#define RANS_MAGIC         0x534E4152u
+#define RANS_VERSION       1u
+
+typedef struct {
+    uint32_t n_lanes;        /* N interleaved coders per chunk, 1..32 */
+    uint32_t chunk_symbols;  /* symbols per chunk, >= 1 */
+} rans_params;
+
+/* Library version (RANS_VERSION of the format it writes). */
+uint32_t rans_version(void);
+
+/* Short English text for a status code (static storage). */
+const char *rans_status_string(int status);
+
+/*
+ * rans_quantize_table -- static order-0 model: integer weights -> integer
+ * frequencies f_s with sum f_s = 2^log2_M.  The paper assumes a static
+ * probability model per file (Section 7) but does not say how it is
+ * quantized; this is the rule the library uses:
+ *   1. f_s = floor(w_s * M / W), W = sum w; raised to 1 where w_s > 0;
+ *   2. while sum f < M: +1 to the symbols with w_s > 0 in decreasing order
+ *      of the remainder w_s*M mod W (ties: lower index), repeating the
+ *      order if needed;
+ *   3. while sum f > M: -1 from the symbol with the largest f_s > 1
+ *      (ties: lower index).
+ * Hence f_s >= 1 exactly when w_s > 0.
+ * weights: host, n entries.  freq_out: host, n entries.
+ * n in [1, 4096], log2_M in [1, 15], sum w < 2^64, at most M nonzero weights;
+ * the coder itself needs log2_M = 12 and n <= 256.
+ * Returns RANS_OK or RANS_ERR_INVALID_ARG (freq_out untouched).  Host only.
+ */
+int rans_quantize_table(const uint64_t *weights, uint32_t n, uint32_t log2_M,
+                        uint16_t *freq_out);
+
+/* Worst-case message size in bytes for n_symbols symbols (one 16-bit word
+ * per symbol, Section 5, plus header, offsets, states and padding).
+ * 0 if the parameters are invalid. */
+uint64_t rans_max_encoded_size(uint64_t n_symbols, const rans_params *params);
+
+/* Scratch bytes rans_encode needs for n_symbols symbols.  0 if invalid. */
+uint64_t rans_encode_scratch_size(uint64_t n_symbols, const rans_params *params);
+
+/*
+ * rans_encode -- encode n_symbols bytes into one message (format above).
+ *
+ * d_symbols : device, n_symbols bytes, symbol values < n_alpha.
+ * h_freq    : host, n_alpha frequencies with sum = RANS_M (rans_quantize_table).
+ * n_alpha   : 1..256.
+ * params    : host; n_lanes 1..32, chunk_symbols >= 1.
+ * d_out     : device, 16-byte aligned, out_cap bytes; out_cap must be at
+ *             least rans_max_encoded_size(n_symbols, params).
+ * d_out_size: device, one u64: the message size in bytes (a multiple of 16),
+ *             or 0 if the data was rejected.
+ * d_status  : device, one u32: RANS_OK, or RANS_ERR_ZERO_FREQ if some symbol
+ *             has f_s = 0 (the message is then not valid), or RANS_ERR_TIMEOUT.
+ * d_scratch : device, 16-byte aligned, scratch_cap bytes,
+ *             >= rans_encode_scratch_size(n_symbols, params).
+ * The worst-case message (every chunk's offsets must fit in u32) must stay
+ * below 4 GiB.  Returns RANS_OK, RANS_ERR_INVALID_ARG,
+ * RANS_ERR_BUFFER_TOO_SMALL or RANS_ERR_CUDA.
+ */
+int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_freq,
+                uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
+                uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                uint64_t scratch_cap, rans_stream_t stream);
+
+/*
+ * rans_decode -- decode a message produced by rans_encode (or the same
+ * format from any encoder that follows the paper's interleaving).
+ *
+ * d_msg     : device, 16-byte aligned, msg_size bytes (a multiple of 16).
+ * h_freq, n_alpha, params : the model and layout the message was encoded
+ *             with (the header is checked against them).
+ * d_symbols : device, n_symbols bytes of output.
+ * d_status  : device, one u32, set to RANS_OK, or RANS_ERR_CORRUPT if the
+ *             header, the offsets or any chunk is inconsistent (a chunk must
+ *             end with every coder back at its initial state L and with its
+ *             words consumed exactly), or RANS_ERR_TIMEOUT.  On RANS_ERR_CORRUPT
+ *             the output of the bad chunks is unspecified.
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG or RANS_ERR_CUDA.
+ */
+int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INTERLEAVED_RANS_B300_H_ */

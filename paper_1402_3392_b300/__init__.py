@@ -5,15 +5,16 @@ in include/rans.h; ``paper_1402_3392_b300.rans`` is the thin ctypes binding.
 The binding is loaded on first use of one of its names so that the synthetic
 workload generators (``paper_1402_3392_b300.workloads``) import without it.
 """
-_BINDING_NAMES = None
+_BINDING = frozenset({
+    "RansError", "rans_version", "rans_status_string", "rans_quantize_table",
+    "rans_max_encoded_size", "rans_encode_scratch_size", "rans_encode", "rans_decode",
+    "encode", "decode",
+})
 
 
 def __getattr__(name):
-    global _BINDING_NAMES
-    from . import rans
+    if name in _BINDING:
+        from . import rans
 
-    if _BINDING_NAMES is None:
-        _BINDING_NAMES = set(rans.__all__)
-    if name in _BINDING_NAMES:
         return getattr(rans, name)
     raise AttributeError(name)

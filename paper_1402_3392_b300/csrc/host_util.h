@@ -1,0 +1,56 @@
+// host_util.h -- host-side helpers shared by the entry points of the library:
+// argument checks, message geometry and per-device launch facts.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "rans.h"
+
+namespace rans {
+
+constexpr uint64_t round16(uint64_t v) { return (v + 15u) & ~uint64_t(15); }
+constexpr uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Geometry of a message of n symbols: chunk count and the byte offset of the
+// data region (header + offset table, padded to 16 bytes).
+struct MessageGeometry {
+    uint64_t n_chunks;
+    uint64_t data0;
+};
+
+inline bool params_ok(const rans_params *p) {
+    return p && p->n_lanes >= 1 && p->n_lanes <= RANS_MAX_LANES && p->chunk_symbols >= 1;
+}
+
+inline MessageGeometry geometry(uint64_t n, const rans_params *p) {
+    MessageGeometry g;
+    g.n_chunks = ceil_div(n, p->chunk_symbols);
+    g.data0 = round16(32 + 4 * (g.n_chunks + 1));
+    return g;
+}
+
+// The model must be a valid static table: 1..256 symbols, frequencies that
+// sum to M.  Sets *const_sym to the symbol with f = M, or 0xFFFFFFFF.
+inline bool table_ok(const uint16_t *freq, uint32_t n_alpha, uint32_t *const_sym) {
+    if (!freq || n_alpha == 0 || n_alpha > RANS_MAX_ALPHABET) return false;
+    uint32_t sum = 0, cs = 0xFFFFFFFFu;
+    for (uint32_t s = 0; s < n_alpha; ++s) {
+        sum += freq[s];
+        if (freq[s] == RANS_M) cs = s;
+    }
+    if (const_sym) *const_sym = cs;
+    return sum == RANS_M;
+}
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+inline int check_launch() {
+    return cudaGetLastError() == cudaSuccess ? RANS_OK : RANS_ERR_CUDA;
+}
+
+}  // namespace rans

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI declared in include/rans.h.
+
+Every function here only marshals arguments: device buffers are torch CUDA
+tensors (or raw device addresses), host tables are numpy arrays, and the work
+runs in the CUDA kernels of libinterleaved_rans_b300.so.  There is no CPU
+fallback: if the shared library is missing the import fails with an error
+that says how to build it.
+
+Names follow the C ABI (``rans_encode`` ...).  ``encode``/``decode`` are
+small conveniences that allocate the output and scratch tensors with torch
+and call the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "RansError", "RANS_OK", "RANS_ERR_INVALID_ARG", "RANS_ERR_ZERO_FREQ",
+    "RANS_ERR_BUFFER_TOO_SMALL", "RANS_ERR_CORRUPT", "RANS_ERR_TIMEOUT", "RANS_ERR_CUDA",
+    "RANS_ERR_OOM", "RANS_M", "RANS_L", "RANS_LOG2_M", "library_path", "lib",
+    "rans_version", "rans_status_string", "rans_quantize_table", "rans_max_encoded_size",
+    "rans_encode_scratch_size", "rans_encode", "rans_decode", "encode", "decode",
+]
+
+RANS_OK = 0
+RANS_ERR_INVALID_ARG = 1
+RANS_ERR_ZERO_FREQ = 2
+RANS_ERR_BUFFER_TOO_SMALL = 3
+RANS_ERR_CORRUPT = 4
+RANS_ERR_TIMEOUT = 5
+RANS_ERR_CUDA = 6
+RANS_ERR_OOM = 7
+RANS_LOG2_M = 12
+RANS_M = 1 << RANS_LOG2_M
+RANS_L = 1 << 16
+
+
+class RansParams(C.Structure):
+    _fields_ = [("n_lanes", C.c_uint32), ("chunk_symbols", C.c_uint32)]
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def _load() -> C.CDLL:
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -m paper_1402_3392_b300.build); there is no CPU fallback")
+    lib = C.CDLL(path)
+    vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+    pp = C.POINTER(RansParams)
+    sig = {
+        "rans_version": (u32, []),
+        "rans_status_string": (C.c_char_p, [i32]),
+        "rans_quantize_table": (i32, [vp, u32, u32, vp]),
+        "rans_max_encoded_size": (u64, [u64, pp]),
+        "rans_encode_scratch_size": (u64, [u64, pp]),
+        "rans_encode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class RansError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {rans_status_string(code)} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code != RANS_OK:
+        raise RansError(code, what)
+    return code
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _params(n_lanes: int, chunk_symbols: int) -> RansParams:
+    return RansParams(int(n_lanes), int(chunk_symbols))
+
+
+def _freq(freq) -> np.ndarray:
+    return np.ascontiguousarray(freq, dtype=np.uint16)
+
+
+def rans_version() -> int:
+    return int(lib.rans_version())
+
+
+def rans_status_string(code: int) -> str:
+    return lib.rans_status_string(int(code)).decode()
+
+
+def rans_quantize_table(weights, log2_M: int = RANS_LOG2_M) -> np.ndarray:
+    w = np.ascontiguousarray(weights, dtype=np.uint64)
+    out = np.zeros(w.size, dtype=np.uint16)
+    _check(lib.rans_quantize_table(w.ctypes.data, w.size, log2_M, out.ctypes.data),
+           "rans_quantize_table")
+    return out
+
+
+def rans_max_encoded_size(n_symbols: int, n_lanes: int = 32, chunk_symbols: int = 65536) -> int:
+    p = _params(n_lanes, chunk_symbols)
+    return int(lib.rans_max_encoded_size(int(n_symbols), C.byref(p)))
+
+
+def rans_encode_scratch_size(n_symbols: int, n_lanes: int = 32,
+                             chunk_symbols: int = 65536) -> int:
+    p = _params(n_lanes, chunk_symbols)
+    return int(lib.rans_encode_scratch_size(int(n_symbols), C.byref(p)))
+
+
+def rans_encode(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_cap, d_out_size,
+                d_status, d_scratch, scratch_cap, stream=None, check=True) -> int:
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode(_ptr(d_symbols), int(n_symbols), f.ctypes.data, f.size, C.byref(p),
+                         _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
+                         _ptr(d_scratch), int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode") if check else rc
+
+
+def rans_decode(d_msg, msg_size, freq, n_lanes, chunk_symbols, d_symbols, n_symbols, d_status,
+                stream=None, check=True) -> int:
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode(_ptr(d_msg), int(msg_size), f.ctypes.data, f.size, C.byref(p),
+                         _ptr(d_symbols), int(n_symbols), _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_decode") if check else rc
+
+
+# ---- conveniences: allocate with torch, call the entry points -----------------
+
+def encode(symbols, freq, n_lanes: int = 32, chunk_symbols: int = 65536, stream=None,
+           out=None, scratch=None, sync: bool = True):
+    """Encode a CUDA uint8 tensor.  Returns (message, size, status) where
+    ``message`` is the output buffer (trimmed to the size when sync=True),
+    and ``size``/``status`` are the device words the library wrote."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size(n, n_lanes, chunk_symbols)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    if scratch is None:
+        scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode(symbols, n, freq, n_lanes, chunk_symbols, out, out.numel(), size, status,
+                scratch, scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode(msg, n_symbols: int, freq, n_lanes: int = 32, chunk_symbols: int = 65536,
+           stream=None, out=None, sync: bool = True):
+    """Decode a CUDA uint8 message tensor into n_symbols bytes.  Returns
+    (symbols, status)."""
+    import torch
+
+    dev = msg.device
+    if out is None:
+        out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode(msg, msg.numel(), freq, n_lanes, chunk_symbols, out, n_symbols, status, stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode (device status)")
+    return out[:n_symbols], status
