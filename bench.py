@@ -39,15 +39,16 @@ sys.path.insert(0, ROOT)
 
 from paper_1402_3392_b300 import workloads as wl  # noqa: E402
 
-DECODE_SOURCE = os.path.join(ROOT, "paper_1402_3392_b300", "csrc", "rans_decode.cu")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "decode_kernel_chunked_1GiB.md")
+DECODE_SOURCES = [os.path.join(ROOT, "paper_1402_3392_b300", "csrc", f)
+                  for f in ("rans_decode.cu", "device_util.cuh")]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "decode_kernel_chunked.md")
 
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="chunked", choices=["chunked", "single"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,8 +75,11 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    with open(DECODE_SOURCE, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in DECODE_SOURCES:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
@@ -92,8 +96,9 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    """Samples SM clock and clock-event reasons through NVML (read only)
-    while the timed region runs."""
+    """Samples the SM clock and the clock-event reasons while the timed region
+    runs (read only): NVML when the Python module is present, else
+    `nvidia-smi -lms` in a child process."""
 
     REASONS = {
         0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
@@ -101,54 +106,82 @@ class ClockSampler:
         0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
         0x100: "display_clock_setting",
     }
+    SMI_FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+                  "clocks_event_reasons.hw_thermal_slowdown",
+                  "clocks_event_reasons.sw_thermal_slowdown",
+                  "clocks_event_reasons.sw_power_cap"]
 
     def __init__(self, device_index: int):
-        self.samples, self.reasons, self.ok = [], 0, False
+        import torch
+
+        self.samples, self.reasons, self.max_mhz, self.mode = [], set(), None, None
+        self.uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
         self._stop = threading.Event()
         try:
             import pynvml
 
             pynvml.nvmlInit()
-            import torch
-
-            uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
-            try:
-                self.h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
-            except Exception:
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.h = pynvml.nvmlDeviceGetHandleByUUID(self.uuid)
             self.nv = pynvml
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.ok = True
-        except Exception as e:  # no NVML: report that instead of clocks
-            self.err = str(e)
+            self.mode = "nvml"
+        except Exception:
+            self.mode = "nvidia-smi"
 
-    def _run(self):
+    def _run_nvml(self):
         nv = self.nv
         while not self._stop.is_set():
             try:
                 self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                self.reasons |= int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+                bits = int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+                self.reasons |= {n for b, n in self.REASONS.items() if bits & b}
             except Exception:
                 pass
             time.sleep(0.005)
 
     def __enter__(self):
-        if self.ok:
-            self.t = threading.Thread(target=self._run, daemon=True)
+        import subprocess
+
+        if self.mode == "nvml":
+            self.t = threading.Thread(target=self._run_nvml, daemon=True)
             self.t.start()
+        else:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.uuid}",
+                     "--query-gpu=" + ",".join(self.SMI_FIELDS),
+                     "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.proc = None
         return self
 
     def __exit__(self, *a):
         self._stop.set()
-        if self.ok:
+        if self.mode == "nvml":
             self.t.join()
+        elif self.proc is not None:
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            for line in out.splitlines():
+                f = [v.strip() for v in line.split(",")]
+                if len(f) != len(self.SMI_FIELDS):
+                    continue
+                try:
+                    self.samples.append(float(f[0]))
+                    self.max_mhz = float(f[1])
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                    "sw_power_cap"), f[2:]):
+                    if v.lower() == "active":
+                        self.reasons.add(name)
 
     def summary(self):
-        if not self.ok:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
-        names = [n for b, n in self.REASONS.items() if self.reasons & b and n != "gpu_idle"]
+        names = sorted(r for r in self.reasons if r != "gpu_idle")
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
-                "sm_max_mhz": self.max_mhz, "reasons": names, "samples": len(self.samples)}
+                "sm_max_mhz": self.max_mhz, "reasons": names, "samples": len(self.samples),
+                "source": self.mode}
 
 
 # ---------------------------------------------------------------------------
@@ -392,7 +425,7 @@ def end_to_end(rans, msg_dev, n, freq, N, CS, dev, steps):
 def cpu_baseline(msg, freq, N, CS, n_chunks):
     cores = host_cores()
     chunks = split_chunks(msg, n_chunks)
-    count = min(len(chunks), 24 * cores)
+    count = min(len(chunks), 64 * cores)
     rate, dt = oracle_decode_rate(chunks[:count], freq, N, CS, cores)
     return {"value": rate / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle decode of {count} chunks x {CS} symbols of this workload's "

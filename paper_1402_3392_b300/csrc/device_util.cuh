@@ -14,10 +14,9 @@ constexpr uint32_t kM = RANS_M;
 constexpr uint32_t kL = RANS_L;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-// Upper bound on polls of one mbarrier phase before a kernel reports
-// RANS_ERR_TIMEOUT instead of waiting forever.  mbarrier.try_wait itself
-// suspends for a bounded, hardware-chosen time per poll, so this is seconds.
-constexpr uint32_t kWaitPolls = 1u << 22;
+// Longest time a kernel waits for one mbarrier phase before it reports
+// RANS_ERR_TIMEOUT instead of waiting forever (nanoseconds of %globaltimer).
+constexpr uint64_t kWaitNs = 200ull * 1000 * 1000;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -68,11 +67,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Bounded wait for phase `parity` of barrier `bar`; false if it gave up.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of barrier `bar` for at most kWaitNs; false if it
+// gave up.  The slow path polls without blocking so the bound is wall time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitPolls; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        __nanosleep(256);
+    }
 }
 
 // ---- bulk copies (TMA, non-tensor) -------------------------------------------

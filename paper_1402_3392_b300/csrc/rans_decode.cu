@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kWarps * 32)
             const uint32_t need = min(nseg, (rp + kSeg + kSeg - 1) / kSeg);
             for (; ready < need; ++ready) {
                 const uint32_t slot = ready % kNSeg;
-                if (timeouts == 0 && !mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u))
-                    ++timeouts;
+                const bool ok = timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
+                if (__any_sync(kFull, !ok)) timeouts = 1;   // warp-uniform
                 phase ^= 1u << slot;
             }
         };
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         // phases are clean for the next chunk.
         for (; ready < issued; ++ready) {
             const uint32_t slot = ready % kNSeg;
-            if (timeouts == 0 && !mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u))
-                    ++timeouts;
+            const bool ok = timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
+            if (__any_sync(kFull, !ok)) timeouts = 1;
             phase ^= 1u << slot;
         }
         // A well-formed chunk ends with every coder back at x0 = L and every

@@ -165,21 +165,23 @@ __global__ void __launch_bounds__(kWarps * 32)
         // Store every segment that lies entirely at or above wp.  The next
         // group writes into the segments of wp-1 and wp-513, whose ring slots
         // last held segments that are at least three newer stores back.
+        // wp and flushed are warp-uniform; only lane 0 issues and waits.
         auto service = [&]() {
             const uint32_t done = (wp + kSeg - 1) / kSeg;
             if (flushed > done) {
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    while (flushed > done) {
-                        --flushed;
-                        bulk_s2g(slot_base + uint64_t(flushed) * kSeg,
-                                 ring_s + (flushed % kNSeg) * kSeg, kSeg);
+                    for (uint32_t sg = flushed; sg > done;) {
+                        --sg;
+                        bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg,
+                                 kSeg);
                         bulk_commit();
                     }
                     bulk_wait_read<2>();
                 }
                 __syncwarp();
+                flushed = done;
             }
         };
 
@@ -222,12 +224,11 @@ __global__ void __launch_bounds__(kWarps * 32)
         __syncwarp();
         if (lane == 0) {
             const uint32_t done = (wp + kSeg - 1) / kSeg;
-            while (flushed > done) {
-                --flushed;
-                bulk_s2g(slot_base + uint64_t(flushed) * kSeg, ring_s + (flushed % kNSeg) * kSeg,
-                         kSeg);
+            for (uint32_t sg = flushed; sg > done;) {
+                --sg;
+                bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
             }
-            const uint32_t lo = wp & ~15u, hi = flushed * kSeg;
+            const uint32_t lo = wp & ~15u, hi = done * kSeg;
             if (lo < hi) bulk_s2g(slot_base + lo, ring_s + (lo & (kRing - 1)), hi - lo);
             bulk_commit();
             bulk_wait_read<0>();

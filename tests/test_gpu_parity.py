@@ -139,7 +139,9 @@ def test_zero_frequency_symbol_is_reported(rlib, cuda):
     with pytest.raises(rlib.RansError) as e:
         rlib.encode(sym, freq, 32, 4096)
     assert e.value.code == rlib.RANS_ERR_ZERO_FREQ
-    _, size, status = rlib.encode(sym, freq[:100], 32, 4096, sync=False)  # s >= n_alpha
+    f100 = np.full(100, 41, dtype=np.uint16)
+    f100[96:] = 40                       # 100 symbols, sum 4096: symbol 200 >= n_alpha
+    _, size, status = rlib.encode(sym, f100, 32, 4096, sync=False)
     torch.cuda.synchronize()
     assert int(status.item()) == rlib.RANS_ERR_ZERO_FREQ and int(size.item()) == 0
 
@@ -200,7 +202,7 @@ def test_wrong_size_or_model_is_an_argument_error(rlib, cuda):
     msg = torch.zeros(4096, dtype=torch.uint8, device=cuda)
     out = torch.empty(100, dtype=torch.uint8, device=cuda)
     st = torch.zeros(1, dtype=torch.int32, device=cuda)
-    assert rlib.rans_decode(msg, 4000, freq, 32, 64, out, 100, st, check=False) == \
+    assert rlib.rans_decode(msg, 4008, freq, 32, 64, out, 100, st, check=False) == \
         rlib.RANS_ERR_INVALID_ARG
     bad = freq.copy(); bad[3] = 0
     assert rlib.rans_decode(msg, 4096, bad, 32, 64, out, 100, st, check=False) == \
