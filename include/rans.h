@@ -163,6 +163,43 @@ int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
                 uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
                 uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
 
+/*
+ * rans_encode_static_scratch -- rans_encode for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a service of the
+ * library, not a step of the method.
+ *
+ * Who needs it: code that runs where cudaMalloc is not allowed or not wanted
+ * -- for example a host that has reserved the whole device up front and hands
+ * out only fixed buffers, a real-time pipeline that forbids allocation once
+ * it is running, or a plugin that is given input and output buffers by its
+ * host and nothing else.  Such a caller still passes its own input and
+ * output; only the encoder's scratch is taken from a fixed array inside the
+ * library.
+ *
+ * Arguments, output format and status codes are those of rans_encode,
+ * without d_scratch/scratch_cap.  The scratch is a file-scope device array of
+ * RANS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  An input whose scratch need,
+ * rans_encode_scratch_size(n_symbols, params), exceeds that returns
+ * RANS_ERR_BUFFER_TOO_SMALL and enqueues nothing (at 64 KiB chunks: about
+ * 32 Mi symbols).
+ *
+ * - The first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.  No call allocates device memory.
+ * - Every call on a device shares the one array and leaves its contents
+ *   behind; nothing in it needs to start at zero.  Calls whose work overlaps
+ *   on the GPU (different streams, or different host threads without
+ *   ordering) race on the array and corrupt each other's output: order them
+ *   on one stream or otherwise serialize them.
+ */
+#define RANS_STATIC_SCRATCH_BYTES (64u << 20)
+int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_symbols,
+                               const uint16_t *h_freq, uint32_t n_alpha,
+                               const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                               uint64_t *d_out_size, uint32_t *d_status,
+                               rans_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@
 // then scans the chunk sizes into the offset table and writes the header, and
 // a copy kernel packs every chunk behind it.
 #include <algorithm>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -401,6 +402,111 @@ extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const u
     ep.slot_bytes = sl.slot_bytes;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
+    if (g.n_chunks > 0) {
+        const int rc = ep.N == 32 ? launch_encode<32>(ep, st) : launch_encode<0>(ep, st);
+        if (rc != RANS_OK) return rc;
+    }
+    FinalizeParams fp{};
+    fp.out = d_out;
+    fp.out_size = d_out_size;
+    fp.sizes = ep.sizes;
+    fp.status = d_status;
+    fp.n_sym = n_symbols;
+    fp.N = ep.N;
+    fp.CS = ep.CS;
+    fp.n_chunks = ep.n_chunks;
+    fp.data0 = uint32_t(g.data0);
+    finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    if (g.n_chunks > 0) {
+        PackParams pp{};
+        pp.out = d_out;
+        pp.words = ep.words;
+        pp.states = ep.states;
+        pp.wstart = ep.wstart;
+        pp.status = d_status;
+        pp.N = ep.N;
+        pp.n_chunks = ep.n_chunks;
+        pp.data0 = fp.data0;
+        pp.slot_bytes = ep.slot_bytes;
+        const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
+        pack_kernel<<<grid, kPackThreads, 0, st>>>(pp);
+        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    }
+    return RANS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rans_encode_static_scratch: the same encoder with its scratch in a
+// file-scope device array, for callers that must not allocate device memory.
+// ---------------------------------------------------------------------------
+namespace rans {
+namespace {
+
+// Held by every GPU that loads this library, for the life of the process.
+static __device__ __align__(256) uint8_t g_static_scratch[RANS_STATIC_SCRATCH_BYTES];
+
+// Device address of g_static_scratch per device, looked up on the first call
+// made with that device current.  The host-side name of the array is only a
+// stand-in for the symbol, never a device address, so it is never passed to a
+// kernel.
+std::mutex g_static_mu;
+uint8_t *g_static_ptr[64] = {nullptr};
+
+int static_scratch_address(uint8_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RANS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (g_static_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr)
+            return RANS_ERR_CUDA;
+        g_static_ptr[dev] = static_cast<uint8_t *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return RANS_OK;
+}
+
+}  // namespace
+}  // namespace rans
+
+extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_symbols,
+                                          const uint16_t *h_freq, uint32_t n_alpha,
+                                          const rans_params *params, uint8_t *d_out,
+                                          uint64_t out_cap, uint64_t *d_out_size,
+                                          uint32_t *d_status, rans_stream_t stream) {
+    if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
+        !d_status || !aligned16(d_out))
+        return RANS_ERR_INVALID_ARG;
+    if (n_symbols && !d_symbols) return RANS_ERR_INVALID_ARG;
+    const MessageGeometry g = geometry(n_symbols, params);
+    if (g.n_chunks > 0xFFFFFFFEull ||
+        4ull * params->n_lanes * g.n_chunks + 2ull * n_symbols > 0xFFFFFFF0ull)
+        return RANS_ERR_INVALID_ARG;
+    const ScratchLayout sl = scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols);
+    if (sl.total > RANS_STATIC_SCRATCH_BYTES) return RANS_ERR_BUFFER_TOO_SMALL;
+    if (out_cap < rans_max_encoded_size(n_symbols, params)) return RANS_ERR_BUFFER_TOO_SMALL;
+    uint8_t *scr = nullptr;
+    if (static_scratch_address(&scr) != RANS_OK) return RANS_ERR_CUDA;
+
+    // Nothing in the scratch has to start at zero: the coder writes every
+    // word, state, size and offset before the later kernels read them.
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+
+    EncodeParams ep{};
+    ep.sym = d_symbols;
+    ep.words = scr + sl.words;
+    ep.states = reinterpret_cast<uint32_t *>(scr + sl.states);
+    ep.wstart = reinterpret_cast<uint32_t *>(scr + sl.wstart);
+    ep.sizes = reinterpret_cast<uint32_t *>(scr + sl.sizes);
+    ep.status = d_status;
+    ep.n_sym = n_symbols;
+    ep.N = params->n_lanes;
+    ep.CS = params->chunk_symbols;
+    ep.n_chunks = uint32_t(g.n_chunks);
+    ep.slot_bytes = sl.slot_bytes;
+    for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
     if (g.n_chunks > 0) {
         const int rc = ep.N == 32 ? launch_encode<32>(ep, st) : launch_encode<0>(ep, st);
         if (rc != RANS_OK) return rc;

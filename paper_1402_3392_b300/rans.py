@@ -24,7 +24,8 @@ __all__ = [
     "RANS_ERR_BUFFER_TOO_SMALL", "RANS_ERR_CORRUPT", "RANS_ERR_TIMEOUT", "RANS_ERR_CUDA",
     "RANS_ERR_OOM", "RANS_M", "RANS_L", "RANS_LOG2_M", "library_path", "lib",
     "rans_version", "rans_status_string", "rans_quantize_table", "rans_max_encoded_size",
-    "rans_encode_scratch_size", "rans_encode", "rans_decode", "encode", "decode",
+    "rans_encode_scratch_size", "rans_encode", "rans_decode", "rans_encode_static_scratch",
+    "RANS_STATIC_SCRATCH_BYTES", "encode", "decode",
 ]
 
 RANS_OK = 0
@@ -38,6 +39,7 @@ RANS_ERR_OOM = 7
 RANS_LOG2_M = 12
 RANS_M = 1 << RANS_LOG2_M
 RANS_L = 1 << 16
+RANS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class RansParams(C.Structure):
@@ -65,6 +67,7 @@ def _load() -> C.CDLL:
         "rans_encode_scratch_size": (u64, [u64, pp]),
         "rans_encode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
+        "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -149,6 +152,20 @@ def rans_encode(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_c
                          _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
                          _ptr(d_scratch), int(scratch_cap), _stream(stream))
     return _check(rc, "rans_encode") if check else rc
+
+
+def rans_encode_static_scratch(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out,
+                               out_cap, d_out_size, d_status, stream=None, check=True) -> int:
+    """rans_encode without a scratch argument: for callers that cannot
+    allocate device memory, the library's fixed scratch array is used (see
+    include/rans.h for the size limit and the rule that calls on one device
+    must not overlap)."""
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_static_scratch(_ptr(d_symbols), int(n_symbols), f.ctypes.data, f.size,
+                                        C.byref(p), _ptr(d_out), int(out_cap), _ptr(d_out_size),
+                                        _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_encode_static_scratch") if check else rc
 
 
 def rans_decode(d_msg, msg_size, freq, n_lanes, chunk_symbols, d_symbols, n_symbols, d_status,
