@@ -24,14 +24,15 @@ namespace {
 
 constexpr int kWarps = 8;               // warps (chunks in flight) per CTA
 constexpr uint32_t kSeg = 512;          // bytes per bulk copy
-constexpr uint32_t kNSeg = 4;           // ring segments per warp
-constexpr uint32_t kRing = kSeg * kNSeg;
-constexpr uint32_t kGroup = 8;          // steps between ring services
-// A step reads at most 32 words = 64 bytes, so a group reads < kSeg bytes.
-static_assert(kGroup * 64 <= kSeg, "a group must fit in one segment");
+constexpr uint32_t kNSeg = 8;           // ring segments per warp
+constexpr uint32_t kRing = kSeg * kNSeg;  // 4 KiB per warp, aligned to 4 KiB in shared space
+constexpr uint32_t kGroup = 16;         // steps between ring checks
+// A step reads at most 32 words = 64 bytes, so a group reads at most 1 KiB:
+// two segments, while the ring holds eight.
+static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
 constexpr uint32_t kTableBytes = kM * 4;
-constexpr uint32_t kSmemBytes = kTableBytes + kWarps * kRing + kWarps * kNSeg * 8 + 16;
-// layout: [slot table 16 KiB][ring per warp][mbarriers per warp][flags]
+// layout: [slot table 16 KiB][alignment slack][ring per warp][mbarriers][flag]
+constexpr uint32_t kSmemBytes = kTableBytes + kRing + kWarps * kRing + kWarps * kNSeg * 8 + 16;
 
 struct DecodeParams {
     const uint8_t *msg;
@@ -51,7 +52,21 @@ struct DecodeParams {
 // With E = entry >> 8 = f_s * 2^12 + (slot - B_s) the decode update is
 //     f_s * floor(x/M) + slot - B_s = f_s * (floor(x/M) - 2^12) + E  (mod 2^32).
 __device__ __forceinline__ uint32_t decode_update(uint32_t x, uint32_t e) {
-    return (e >> 20) * ((x >> kLog2M) - (1u << kLog2M)) + (e >> 8);
+    return (e >> 20) * ((x >> kLog2M) + (0u - (1u << kLog2M))) + (e >> 8);
+}
+
+// Shared-memory loads by 32-bit shared address.  The slot table does not
+// change after it is built; the ring is rewritten by TMA, so its loads stay
+// ordered after the mbarrier waits (volatile).
+__device__ __forceinline__ uint32_t ld_table(uint32_t a) {
+    uint32_t v;
+    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_ring_u16(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
 }
 
 __device__ void build_slot_table(const DecodeParams &p, uint32_t *tab, uint32_t *cum) {
@@ -101,23 +116,24 @@ __device__ bool header_ok(const DecodeParams &p) {
     return first == 0 && round16(last) == p.msg_size - p.data0;
 }
 
-// Decode one full or partial step.  FULL: every lane of the warp is a coder
-// with a symbol in this step.
+// Decode one step of a chunk: every active lane decodes one symbol and reads
+// at most one word.  FULL: every lane of the warp is a coder with a symbol in
+// this step.  rp is the byte position in the word stream (warp-uniform);
+// ring_s is the warp's 4 KiB-aligned ring, so (offset & 4095) | ring_s
+// addresses it.
 template <bool FULL>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
-                                            const uint32_t *tab, const uint8_t *ring,
-                                            uint8_t *outp, uint32_t lt) {
-    const uint32_t e = tab[x & (kM - 1)];
+                                            uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
+                                            uint32_t lt) {
+    const uint32_t e = ld_table(tab_s + ((x & (kM - 1)) << 2));
     if (FULL || active) {
         x = decode_update(x, e);
         *outp = uint8_t(e);
     }
     const bool need = (FULL || active) && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    if (need) {
-        const uint32_t at = (rp + 2u * __popc(m & lt)) & (kRing - 1);
-        x = (x << 16) | *reinterpret_cast<const uint16_t *>(ring + at);
-    }
+    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (kRing - 1)) | ring_s);
+    if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp += 2u * __popc(m);
 }
 
@@ -126,8 +142,10 @@ __global__ void __launch_bounds__(kWarps * 32)
     decode_kernel(const __grid_constant__ DecodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
-    uint8_t *rings = smem + kTableBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(rings + kWarps * kRing);
+    const uint32_t raw = smem_addr(smem + kTableBytes);
+    const uint32_t rings_s = (raw + kRing - 1) & ~(kRing - 1);
+    uint8_t *rings = smem + kTableBytes + (rings_s - raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTableBytes + kRing + kWarps * kRing);
     uint32_t &hdr_ok = *reinterpret_cast<uint32_t *>(bars + kWarps * kNSeg);
 
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -143,8 +161,8 @@ __global__ void __launch_bounds__(kWarps * 32)
         return;
     }
 
-    uint8_t *ring = rings + warp * kRing;
-    const uint32_t ring_s = smem_addr(ring);
+    const uint32_t ring_s = rings_s + warp * kRing;
+    const uint32_t tab_s = smem_addr(tab);
     const uint32_t bar0 = smem_addr(bars + warp * kNSeg);
     if (lane == 0) {
         for (uint32_t i = 0; i < kNSeg; ++i) mbar_init(bar0 + 8 * i, 1);
@@ -187,15 +205,20 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
 
         // Word stream: bytes [P0, P1) of the message, loaded in 512-byte
-        // segments starting at the 16-byte aligned A <= P0.
+        // segments starting at the 16-byte aligned A <= P0; byte P of the
+        // stream lives at ring offset (P - A) mod 4096.
         const uint64_t P0 = uint64_t(p.data0) + o + 4 * N, P1 = uint64_t(p.data0) + e;
         const uint64_t A = P0 & ~uint64_t(15);
         const uint64_t end16 = round16(P1);
         const uint32_t nseg = uint32_t((end16 - A + kSeg - 1) / kSeg);
         const uint32_t endrel = uint32_t(P1 - A);
         uint32_t rp = uint32_t(P0 - A);
-        uint32_t issued = 0, ready = 0;
+        uint32_t issued = 0, ready = 0, recheck = 0;
 
+        // Issue every segment whose ring slot is free (its previous segment
+        // lies wholly below rp), wait until the next group's bytes
+        // [rp, rp + 1 KiB) are in, and compute the read position at which
+        // either can change again.
         auto service = [&]() {
             const uint32_t limit = min(nseg, kNSeg + rp / kSeg);
             for (; issued < limit; ++issued) {
@@ -207,39 +230,48 @@ __global__ void __launch_bounds__(kWarps * 32)
                     bulk_g2s(ring_s + slot * kSeg, p.msg + src, bytes, bar0 + 8 * slot);
                 }
             }
-            const uint32_t need = min(nseg, (rp + kSeg + kSeg - 1) / kSeg);
+            const uint32_t need = min(nseg, (rp + kGroup * 64 + kSeg - 1) / kSeg);
             for (; ready < need; ++ready) {
                 const uint32_t slot = ready % kNSeg;
-                const bool ok = timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
-                if (__any_sync(kFull, !ok)) timeouts = 1;   // warp-uniform
+                const bool ok =
+                    timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
+                if (__any_sync(kFull, !ok)) timeouts = 1;  // warp-uniform
                 phase ^= 1u << slot;
             }
+            const uint32_t r_ready =
+                ready >= nseg ? 0xFFFFFFFFu
+                              : (ready * kSeg >= kGroup * 64 ? ready * kSeg - kGroup * 64 + 1 : 0u);
+            const uint32_t r_issue =
+                issued >= nseg ? 0xFFFFFFFFu
+                               : (issued + 1 >= kNSeg ? (issued + 1 - kNSeg) * kSeg : 0u);
+            recheck = min(r_ready, r_issue);
         };
 
         const uint32_t T_full = n_c / N, rem = n_c % N;
         const bool lane_on = lane < N;
         uint32_t t = 0;
         for (; t + kGroup <= T_full; t += kGroup) {
-            service();
+            if (rp >= recheck) service();
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u)
-                decode_step<NT == 32>(x, rp, lane_on, tab, ring, outp + u * N, lt);
+                decode_step<NT == 32>(x, rp, lane_on, tab_s, ring_s, outp + u * N, lt);
             outp += kGroup * N;
         }
         for (; t < T_full; ++t) {
             service();
-            decode_step<NT == 32>(x, rp, lane_on, tab, ring, outp, lt);
+            decode_step<NT == 32>(x, rp, lane_on, tab_s, ring_s, outp, lt);
             outp += N;
         }
         if (rem) {
             service();
-            decode_step<false>(x, rp, lane < rem, tab, ring, outp, lt);
+            decode_step<false>(x, rp, lane < rem, tab_s, ring_s, outp, lt);
         }
         // Drain the copies still in flight so that the ring and the barrier
         // phases are clean for the next chunk.
         for (; ready < issued; ++ready) {
             const uint32_t slot = ready % kNSeg;
-            const bool ok = timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
+            const bool ok =
+                timeouts != 0 || mbar_wait_bounded(bar0 + 8 * slot, (phase >> slot) & 1u);
             if (__any_sync(kFull, !ok)) timeouts = 1;
             phase ^= 1u << slot;
         }
