@@ -32,11 +32,14 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr uint32_t kSeg = 512;
-constexpr uint32_t kNSeg = 4;
-constexpr uint32_t kRing = kSeg * kNSeg;
-constexpr uint32_t kGroup = 8;
-static_assert(kGroup * 64 <= kSeg, "a group must fit in one segment");
-constexpr uint32_t kSmemBytes = 256 * 8 + kWarps * kRing;
+constexpr uint32_t kNSeg = 8;
+constexpr uint32_t kRing = kSeg * kNSeg;  // 4 KiB per warp, aligned to 4 KiB in shared space
+constexpr uint32_t kGroup = 16;
+// A step writes at most 32 words = 64 bytes, so a group writes at most 1 KiB
+// and touches at most three segments.
+static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
+// layout: [encode table 2 KiB][alignment slack][ring per warp]
+constexpr uint32_t kSmemBytes = 256 * 8 + kRing + kWarps * kRing;
 constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
 
 struct EncodeParams {
@@ -114,26 +117,36 @@ __device__ void build_encode_table(const EncodeParams &p, uint2 *tab, uint32_t *
     __syncthreads();
 }
 
+__device__ __forceinline__ uint2 ld_enc_table(uint32_t a) {
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void st_ring_u16(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(uint16_t(v)) : "memory");
+}
+
+// Encode one step: renormalize (emit the low 16 bits if x >= f_s * 2^20), then
+// x = C(s, x).  wp is the warp-uniform write position (bytes, counting down);
+// ring_s is the warp's 4 KiB-aligned ring.
 template <bool FULL>
 __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
-                                            uint32_t s, const uint2 *tab, uint8_t *ring,
+                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
                                             uint32_t ge) {
-    const uint2 t = tab[s];
+    const uint2 t = ld_enc_table(tab_s + (s << 3));
     const bool on = FULL || active;
     if (on) acc |= t.y;
     const bool emit = on && (x > ~(t.y & 0xFFF00000u));
     const uint32_t m = __ballot_sync(kFull, emit);
     if (emit) {
-        const uint32_t at = (wp - 2u * __popc(m & ge)) & (kRing - 1);
-        *reinterpret_cast<uint16_t *>(ring + at) = uint16_t(x);
+        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
         x >>= 16;
     }
     wp -= 2u * __popc(m);
     if (on) {
-        const uint32_t hi = __umulhi(x, t.x);
-        const uint32_t lo = x + hi;
-        const uint32_t carry = lo < x ? 1u : 0u;
-        const uint32_t q = __funnelshift_r(lo, carry, t.y >> 12);  // shift taken mod 32
+        // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
+        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
+        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
     }
 }
@@ -143,14 +156,16 @@ __global__ void __launch_bounds__(kWarps * 32)
     encode_kernel(const __grid_constant__ EncodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint2 *tab = reinterpret_cast<uint2 *>(smem);
-    uint8_t *rings = smem + 256 * 8;
+    const uint32_t raw = smem_addr(smem + 256 * 8);
+    const uint32_t rings_s = (raw + kRing - 1) & ~(kRing - 1);
+    uint8_t *rings = smem + 256 * 8 + (rings_s - raw);
 
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t N = NT ? NT : p.N;
     build_encode_table(p, tab, reinterpret_cast<uint32_t *>(rings));
 
-    uint8_t *ring = rings + warp * kRing;
-    const uint32_t ring_s = smem_addr(ring);
+    const uint32_t ring_s = rings_s + warp * kRing;
+    const uint32_t tab_s = smem_addr(tab);
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
 
@@ -164,9 +179,9 @@ __global__ void __launch_bounds__(kWarps * 32)
         uint32_t flushed = p.slot_bytes / kSeg;     // segments >= flushed are stored
 
         // Store every segment that lies entirely at or above wp.  The next
-        // group writes into the segments of wp-1 and wp-513, whose ring slots
-        // last held segments that are at least three newer stores back.
-        // wp and flushed are warp-uniform; only lane 0 issues and waits.
+        // group writes into the segments holding wp-1 .. wp-1024, whose ring
+        // slots last held segments at least five newer stores back.  wp and
+        // flushed are warp-uniform; only lane 0 issues and waits.
         auto service = [&]() {
             const uint32_t done = (wp + kSeg - 1) / kSeg;
             if (flushed > done) {
@@ -179,7 +194,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                                  kSeg);
                         bulk_commit();
                     }
-                    bulk_wait_read<2>();
+                    bulk_wait_read<5>();
                 }
                 __syncwarp();
                 flushed = done;
@@ -191,13 +206,13 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (rem) {
             const bool act = lane < rem;
             const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
-            encode_step<false>(x, wp, acc, act, s, tab, ring, ge);
+            encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge);
         }
         int64_t t = int64_t(T_full) - 1;
         for (uint32_t r = T_full % kGroup; r > 0; --r, --t) {
             service();
             const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
-            encode_step<NT == 32>(x, wp, acc, lane_on, s, tab, ring, ge);
+            encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
         }
         // Groups of kGroup steps, symbols of the next group loaded ahead.
         uint32_t cur[kGroup], nxt[kGroup];
@@ -214,7 +229,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             service();
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u)
-                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab, ring, ge);
+                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
         }
@@ -323,22 +338,65 @@ struct PackParams {
     uint32_t N, n_chunks, data0, slot_bytes;
 };
 
-// Copy chunk c (states, then words) to its place in the message.  Both ends
-// are 2-byte aligned, so the copy moves 16-bit units.
+// Copy chunk c (states, then words) to its place in the message.  The
+// destination is only 2-byte aligned, so whole 16-byte destination blocks are
+// assembled from two aligned 16-byte source loads and a funnel shift (the
+// source-to-destination shift is the same for every block of a chunk); the
+// partial blocks at both ends are written in 16-bit units.
 constexpr int kPackThreads = 256;
+
+template <int K>  // K = (source shift in bytes) / 4; rs = 8 * (shift mod 4)
+__device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, uint64_t B0,
+                                            uint64_t B1, uint64_t s_minus_d, uint32_t rs) {
+    const bool need_hi = K > 0 || rs != 0;
+    for (uint64_t B = B0 + 16ull * threadIdx.x; B < B1; B += 16ull * blockDim.x) {
+        const uint64_t sa = (B + s_minus_d) & ~uint64_t(15);
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(src + sa);
+        const uint4 v1 = need_hi ? *reinterpret_cast<const uint4 *>(src + sa + 16)
+                                 : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint4 r;
+        r.x = __funnelshift_r(w[K + 0], w[K + 1], rs);
+        r.y = __funnelshift_r(w[K + 1], w[K + 2], rs);
+        r.z = __funnelshift_r(w[K + 2], w[K + 3], rs);
+        r.w = __funnelshift_r(w[K + 3], w[K + 4], rs);
+        *reinterpret_cast<uint4 *>(out + B) = r;
+    }
+}
+
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackParams p) {
     if (*p.status != RANS_OK) return;
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(p.out + 32);
     for (uint32_t c = blockIdx.x; c < p.n_chunks; c += gridDim.x) {
-        uint16_t *dst = reinterpret_cast<uint16_t *>(p.out + p.data0 + offs[c]);
-        const uint32_t ws = p.wstart[c];
-        const uint32_t n_words = (p.slot_bytes - ws) / 2;
-        const uint16_t *src =
-            reinterpret_cast<const uint16_t *>(p.words + uint64_t(c) * p.slot_bytes + ws);
+        const uint64_t D = uint64_t(p.data0) + offs[c];
+        uint16_t *dst16 = reinterpret_cast<uint16_t *>(p.out + D);
         const uint32_t *st = p.states + uint64_t(c) * p.N;
         for (uint32_t i = threadIdx.x; i < 2 * p.N; i += blockDim.x)
-            dst[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
-        for (uint32_t i = threadIdx.x; i < n_words; i += blockDim.x) dst[2 * p.N + i] = src[i];
+            dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
+        // words: destination bytes [d0, d1), source bytes from s0 in p.words
+        const uint64_t d0 = D + 4ull * p.N;
+        const uint64_t s0 = uint64_t(c) * p.slot_bytes + p.wstart[c];
+        const uint64_t d1 = d0 + (p.slot_bytes - p.wstart[c]);
+        const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
+        const uint64_t head_end = B0 < d1 ? B0 : d1;
+        for (uint64_t b = d0 + 2ull * threadIdx.x; b < head_end; b += 2ull * blockDim.x)
+            *reinterpret_cast<uint16_t *>(p.out + b) =
+                *reinterpret_cast<const uint16_t *>(p.words + s0 + (b - d0));
+        if (B0 < B1) {
+            const uint64_t s_minus_d = s0 - d0;  // modulo 2^64
+            const uint32_t sh = uint32_t(s_minus_d & 15u);
+            const uint32_t rs = 8u * (sh & 3u);
+            switch (sh >> 2) {
+                case 0: pack_blocks<0>(p.out, p.words, B0, B1, s_minus_d, rs); break;
+                case 1: pack_blocks<1>(p.out, p.words, B0, B1, s_minus_d, rs); break;
+                case 2: pack_blocks<2>(p.out, p.words, B0, B1, s_minus_d, rs); break;
+                default: pack_blocks<3>(p.out, p.words, B0, B1, s_minus_d, rs); break;
+            }
+        }
+        const uint64_t tail_start = B1 > head_end ? B1 : head_end;
+        for (uint64_t b = tail_start + 2ull * threadIdx.x; b < d1; b += 2ull * blockDim.x)
+            *reinterpret_cast<uint16_t *>(p.out + b) =
+                *reinterpret_cast<const uint16_t *>(p.words + s0 + (b - d0));
     }
 }
 
