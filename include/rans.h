@@ -164,6 +164,88 @@ int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
                 uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
 
 /*
+ * Batched decoding: many independent messages ("streams"), each with its own
+ * model, layout and size, decoded by one persistent launch.  A CTA takes one
+ * work item at a time -- up to 8 chunks of one stream -- from a device-side
+ * counter, builds that stream's slot table in shared memory (only when the
+ * model changes) and decodes one chunk per warp.  Uneven stream sizes balance
+ * themselves because items are handed out dynamically.  The call enqueues
+ * kernels only (no allocation, no host synchronization), so it can be
+ * captured in a CUDA graph and replayed.
+ */
+typedef struct {
+    const uint8_t *msg;       /* device, 16-byte aligned: the stream's message */
+    uint64_t msg_size;        /* its size in bytes (a multiple of 16) */
+    uint8_t *symbols;         /* device: n_symbols bytes of output */
+    uint64_t n_symbols;       /* symbols in the stream */
+    uint32_t table;           /* index of the stream's model in d_freqs */
+    uint32_t n_lanes;         /* N the stream was encoded with, 1..32 */
+    uint32_t chunk_symbols;   /* chunk size it was encoded with, >= 1 */
+    uint32_t reserved;        /* set to 0 */
+} rans_stream;                /* 48 bytes */
+
+/* Scratch bytes rans_decode_batch needs for n_streams streams. */
+uint64_t rans_decode_batch_scratch_size(uint32_t n_streams);
+
+/*
+ * rans_decode_batch -- decode n_streams messages.
+ *
+ * d_streams : device, n_streams descriptors (read only).
+ * d_freqs   : device, n_tables models of 256 u16 frequencies each (zero for
+ *             symbols outside the alphabet); each must sum to RANS_M.
+ * d_status  : device, n_streams u32: per stream RANS_OK, RANS_ERR_INVALID_ARG
+ *             (bad descriptor or model; the stream is skipped),
+ *             RANS_ERR_CORRUPT or RANS_ERR_TIMEOUT (as in rans_decode).
+ * d_scratch : device, 16-byte aligned, >= rans_decode_batch_scratch_size().
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG, RANS_ERR_BUFFER_TOO_SMALL or
+ * RANS_ERR_CUDA; per-stream problems go to d_status only.
+ */
+int rans_decode_batch(const rans_stream *d_streams, uint32_t n_streams, const uint16_t *d_freqs,
+                      uint32_t n_tables, uint32_t *d_status, void *d_scratch,
+                      uint64_t scratch_cap, rans_stream_t stream);
+
+/*
+ * Batched encoding: the mirror image of rans_decode_batch.  Every stream is
+ * encoded into its own message (format above) with its own model and layout.
+ */
+typedef struct {
+    const uint8_t *symbols;   /* device: n_symbols bytes, values < the model's alphabet */
+    uint64_t n_symbols;
+    uint8_t *out;             /* device, 16-byte aligned: the stream's message */
+    uint64_t out_cap;         /* >= rans_max_encoded_size(n_symbols, {n_lanes, chunk_symbols}) */
+    uint64_t scratch_offset;  /* byte offset of the stream's scratch in d_scratch
+                                 (filled in by rans_encode_batch_plan) */
+    uint32_t table;           /* index of the stream's model in d_freqs */
+    uint32_t n_lanes;         /* N, 1..32 */
+    uint32_t chunk_symbols;   /* >= 1 */
+    uint32_t reserved;        /* set to 0 */
+} rans_encode_stream;         /* 56 bytes */
+
+/*
+ * rans_encode_batch_plan -- host: give every stream its scratch region
+ * (h_streams[i].scratch_offset, 16-byte aligned, after a work area of the
+ * batch) and return the scratch size rans_encode_batch needs, or 0 if a
+ * stream's n_lanes or chunk_symbols is out of range.
+ */
+uint64_t rans_encode_batch_plan(rans_encode_stream *h_streams, uint32_t n_streams);
+
+/*
+ * rans_encode_batch -- encode n_streams streams.
+ *
+ * d_streams  : device, n_streams descriptors planned by rans_encode_batch_plan.
+ * d_freqs    : device, n_tables models of 256 u16 frequencies each.
+ * d_out_sizes: device, n_streams u64: message sizes (0 when a stream failed).
+ * d_status   : device, n_streams u32: RANS_OK, RANS_ERR_INVALID_ARG (bad
+ *              descriptor, model or scratch range; skipped) or RANS_ERR_ZERO_FREQ.
+ * d_scratch  : device, 16-byte aligned, >= the planned size.
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG or RANS_ERR_CUDA.
+ */
+int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n_streams,
+                      const uint16_t *d_freqs, uint32_t n_tables, uint64_t *d_out_sizes,
+                      uint32_t *d_status, void *d_scratch, uint64_t scratch_cap,
+                      rans_stream_t stream);
+
+/*
  * rans_encode_static_scratch -- rans_encode for callers that cannot allocate
  * device memory.  The paper has no counterpart: this is a service of the
  * library, not a step of the method.

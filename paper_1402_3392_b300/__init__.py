@@ -8,7 +8,8 @@ workload generators (``paper_1402_3392_b300.workloads``) import without it.
 _BINDING = frozenset({
     "RansError", "rans_version", "rans_status_string", "rans_quantize_table",
     "rans_max_encoded_size", "rans_encode_scratch_size", "rans_encode", "rans_decode",
-    "rans_encode_static_scratch", "encode", "decode",
+    "rans_encode_static_scratch", "encode", "decode", "rans_decode_batch",
+    "rans_decode_batch_scratch_size", "rans_encode_batch", "rans_encode_batch_plan",
 })
 
 

@@ -1,0 +1,373 @@
+// encode_core.cuh -- the encoder's building blocks, shared by the
+// single-message entry points (rans_encode.cu) and the batched persistent
+// kernel (rans_batch.cu).
+//
+// One warp encodes one chunk; lane j is coder j of the chunk's N interleaved
+// rANS coders.  The encoder runs over the chunk backwards, step T-1 down to 0
+// (Section 2: the encoder processes the message from last to first and writes
+// backwards).  Per step every lane with a symbol renormalizes at most once
+// (b = 2^16 >= M, Section 5) and then applies C (Algorithm 1 Encode):
+//     if x >= f_s * 2^20:  emit x mod 2^16;  x = floor(x / 2^16)
+//     x = floor(x / f_s) * M + B_s + (x mod f_s)
+// In the serial interleaved order of Section 3 the emissions of one step come
+// from coder N-1 down to coder 0, and the buffer is written backwards, so the
+// lanes place their words with a reverse-lane prefix count:
+//     lane j stores at write_pos - 2 * popc(emit_mask & lanes_at_or_above_j)
+// (the packed store of Sections 5 and 6).  floor(x / f_s) is an exact
+// multiply-high by ceil(2^(32+k) / f_s), k = ceil(log2 f_s).
+//
+// Words are staged in a per-warp shared-memory ring and leave as 512-byte bulk
+// stores (TMA) into a worst-case scratch slot per chunk.  A scan of the chunk
+// sizes then gives the offset table and the header, and a copy packs every
+// chunk behind it.
+#pragma once
+
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "host_util.h"
+
+namespace rans {
+namespace enc {
+
+constexpr int kWarps = 8;
+constexpr uint32_t kThreads = kWarps * 32;
+constexpr uint32_t kSeg = 512;
+constexpr uint32_t kNSeg = 8;
+constexpr uint32_t kRing = kSeg * kNSeg;  // 4 KiB per warp, aligned to 4 KiB in shared space
+constexpr uint32_t kGroup = 16;
+// A step writes at most 32 words = 64 bytes, so a group writes at most 1 KiB
+// and touches at most three segments.
+static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
+// Shared memory: [encode table 2 KiB][alignment slack][one ring per warp][a
+// few words of CTA state].
+constexpr uint32_t kMiscOffset = 256 * 8 + kRing + kWarps * kRing;
+constexpr uint32_t kSmemBytes = kMiscOffset + 64;
+constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
+
+// Scratch of one message, all sections 16-byte aligned: one worst-case slot
+// of words per chunk (written backwards from its end), then the chunks'
+// final states, first-word offsets and byte sizes.
+struct ScratchLayout {
+    uint64_t words, states, wstart, sizes, total;
+    uint32_t slot_bytes;
+};
+
+__host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint32_t N, uint32_t CS) {
+    ScratchLayout s{};
+    s.slot_bytes = uint32_t((2ull * CS + kSeg - 1) / kSeg * kSeg);
+    s.words = 0;
+    s.states = (n_chunks * s.slot_bytes + 16 + 15) & ~uint64_t(15);
+    s.wstart = s.states + ((n_chunks * N * 4 + 15) & ~uint64_t(15));
+    s.sizes = s.wstart + ((n_chunks * 4 + 15) & ~uint64_t(15));
+    s.total = s.sizes + ((n_chunks * 4 + 15) & ~uint64_t(15));
+    return s;
+}
+
+struct Smem {
+    uint2 *tab;
+    uint32_t tab_s;
+    uint32_t rings_s;  // 4 KiB aligned
+    uint8_t *rings;
+    uint32_t *misc;
+};
+
+__device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
+    Smem s;
+    s.tab = reinterpret_cast<uint2 *>(smem);
+    s.tab_s = smem_addr(smem);
+    const uint32_t raw = smem_addr(smem + 256 * 8);
+    s.rings_s = (raw + kRing - 1) & ~(kRing - 1);
+    s.rings = smem + 256 * 8 + (s.rings_s - raw);
+    s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
+    return s;
+}
+
+// Encode-table entry for symbol s with frequency f (1 <= f <= M):
+//   .x = m_lo = ceil(2^(32+k) / f) - 2^32,  k = ceil(log2 f)   (0 <= m_lo < 2^32)
+//   .y = (M - f) << 20 | k << 12 | B_s
+// floor(x/f) = (x + umulhi(x, m_lo)) >> k for every x < 2^32: with
+// m = 2^(32+k)/f + e, 0 <= e < 1, the error x*e/2^(32+k) < 2^-k <= 1/f never
+// carries x/f past the next integer.
+// Emit test: x >= f * 2^20  <=>  x > f * 2^20 - 1 = ~((M - f) << 20)  (u32).
+// Built by the whole CTA; cum: 257 words of free shared memory.  Returns the
+// sum of the frequencies to every thread.
+__device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq, uint2 *tab,
+                                                           uint32_t *cum) {
+    const uint32_t tid = threadIdx.x;
+    if (tid < 32) {
+        uint32_t v[8], run = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = run;
+            run += freq[tid * 8 + k];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (tid >= uint32_t(d)) incl += y;
+        }
+        const uint32_t excl = incl - run;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cum[tid * 8 + k] = excl + v[k];
+        if (tid == 31) cum[256] = incl;
+    }
+    __syncthreads();
+    for (uint32_t s = tid; s < 256; s += blockDim.x) {
+        const uint32_t f = freq[s];
+        uint2 t;
+        if (f == 0) {
+            t = make_uint2(0u, kZeroFlag);  // never emits, leaves x unchanged
+        } else {
+            const uint32_t k = 32u - __clz(f - 1u);
+            const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
+            t.x = uint32_t(m - (1ull << 32));
+            t.y = ((kM - (f & (2 * kM - 1))) << 20) | (k << 12) | (cum[s] & (kM - 1));
+        }
+        tab[s] = t;
+    }
+    const uint32_t total = cum[256];
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ uint2 ld_enc_table(uint32_t a) {
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void st_ring_u16(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(uint16_t(v)) : "memory");
+}
+
+// Encode one step: renormalize (emit the low 16 bits if x >= f_s * 2^20), then
+// x = C(s, x).  wp is the warp-uniform write position (bytes, counting down);
+// ring_s is the warp's 4 KiB-aligned ring.
+template <bool FULL>
+__device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
+                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
+                                            uint32_t ge) {
+    const uint2 t = ld_enc_table(tab_s + (s << 3));
+    const bool on = FULL || active;
+    if (on) acc |= t.y;
+    const bool emit = on && (x > ~(t.y & 0xFFF00000u));
+    const uint32_t m = __ballot_sync(kFull, emit);
+    if (emit) {
+        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        x >>= 16;
+    }
+    wp -= 2u * __popc(m);
+    if (on) {
+        // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
+        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
+        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
+    }
+}
+
+// Encode n_c symbols starting at sym with N coders into the worst-case slot
+// slot_base[0, slot_bytes).  Writes the chunk's first-word offset *wstart,
+// byte size *size and final states states[0..N).  acc collects the table
+// words of every symbol coded (kZeroFlag marks a symbol without probability).
+template <int NT>
+__device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
+                                             uint8_t *slot_base, uint32_t slot_bytes,
+                                             uint32_t *wstart, uint32_t *size, uint32_t *states,
+                                             uint32_t tab_s, uint32_t ring_s, uint32_t ge,
+                                             uint32_t lane, uint32_t &acc) {
+    const uint32_t N = NT ? NT : N_rt;
+    const uint8_t *symp = sym + lane;
+    uint32_t x = kL;
+    uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
+    uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
+
+    // Store every segment that lies entirely at or above wp.  The next group
+    // writes into the segments holding wp-1 .. wp-1024, whose ring slots last
+    // held segments at least five newer stores back.  wp and flushed are
+    // warp-uniform; only lane 0 issues and waits.
+    auto service = [&]() {
+        const uint32_t done = (wp + kSeg - 1) / kSeg;
+        if (flushed > done) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                for (uint32_t sg = flushed; sg > done;) {
+                    --sg;
+                    bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
+                    bulk_commit();
+                }
+                bulk_wait_read<5>();
+            }
+            __syncwarp();
+            flushed = done;
+        }
+    };
+
+    const uint32_t T_full = n_c / N, rem = n_c % N;
+    const bool lane_on = lane < N;
+    if (rem) {
+        const bool act = lane < rem;
+        const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
+        encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge);
+    }
+    int64_t t = int64_t(T_full) - 1;
+    for (uint32_t r = T_full % kGroup; r > 0; --r, --t) {
+        service();
+        const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
+        encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
+    }
+    // Groups of kGroup steps; a group's symbols are loaded together up front.
+    for (; t >= 0; t -= kGroup) {
+        uint32_t cur[kGroup];
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+        service();
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u)
+            encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+    }
+
+    // Store what is left: complete segments, then the partial one rounded
+    // down to 16 bytes (bytes below wp are scratch garbage nobody reads).
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t done = (wp + kSeg - 1) / kSeg;
+        for (uint32_t sg = flushed; sg > done;) {
+            --sg;
+            bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
+        }
+        const uint32_t lo = wp & ~15u, hi = done * kSeg;
+        if (lo < hi) bulk_s2g(slot_base + lo, ring_s + (lo & (kRing - 1)), hi - lo);
+        bulk_commit();
+        bulk_wait_read<0>();
+        *wstart = wp;
+        *size = 4 * N + (slot_bytes - wp);
+    }
+    __syncwarp();
+    if (lane < N) states[lane] = x;
+}
+
+// With a whole CTA: exclusive scan of the chunk sizes into the offset table,
+// the header, zero padding, and the message size.  blockDim.x is a multiple
+// of 32; warp_sums: 32 words of shared memory, carry: one word.
+__device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_size,
+                                                 const uint32_t *sizes, uint64_t n_sym, uint32_t N,
+                                                 uint32_t CS, uint32_t n_chunks, uint32_t data0,
+                                                 uint32_t *warp_sums, uint32_t *carry_s) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    uint32_t *offs = reinterpret_cast<uint32_t *>(out + 32);
+    if (tid == 0) *carry_s = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < n_chunks; base += nt) {
+        const uint64_t i = base + tid;
+        const uint32_t v = i < n_chunks ? sizes[i] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= uint32_t(d)) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = lane < nt / 32 ? warp_sums[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, wi, d);
+                if (lane >= uint32_t(d)) wi += y;
+            }
+            if (lane < nt / 32) warp_sums[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const uint32_t carry = *carry_s;
+        if (i < n_chunks) offs[i] = carry + warp_sums[warp] + incl - v;
+        __syncthreads();
+        if (tid == nt - 1) *carry_s = carry + warp_sums[warp] + incl;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const uint32_t total = *carry_s;
+        uint32_t *h = reinterpret_cast<uint32_t *>(out);
+        h[0] = RANS_MAGIC;
+        h[1] = RANS_VERSION;
+        h[2] = N;
+        h[3] = kLog2M;
+        h[4] = uint32_t(n_sym);
+        h[5] = uint32_t(n_sym >> 32);
+        h[6] = CS;
+        h[7] = n_chunks;
+        offs[n_chunks] = total;
+        for (uint32_t b = 32 + 4 * (n_chunks + 1); b < data0; ++b) out[b] = 0;
+        const uint64_t end = uint64_t(data0) + total;
+        for (uint64_t b = end; b < round16(end); ++b) out[b] = 0;
+        *out_size = round16(end);
+    }
+}
+
+// Copy chunk c (states, then words) to its place in the message.  The
+// destination is only 2-byte aligned, so whole 16-byte destination blocks are
+// assembled from two aligned 16-byte source loads and a funnel shift (the
+// source-to-destination shift is the same for every block of a chunk); the
+// partial blocks at both ends are written in 16-bit units.
+template <int K>  // K = (source shift in bytes) / 4; rs = 8 * (shift mod 4)
+__device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, uint64_t B0,
+                                            uint64_t B1, uint64_t s_minus_d, uint32_t rs) {
+    const bool need_hi = K > 0 || rs != 0;
+    for (uint64_t B = B0 + 16ull * threadIdx.x; B < B1; B += 16ull * blockDim.x) {
+        const uint64_t sa = (B + s_minus_d) & ~uint64_t(15);
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(src + sa);
+        const uint4 v1 = need_hi ? *reinterpret_cast<const uint4 *>(src + sa + 16)
+                                 : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint4 r;
+        r.x = __funnelshift_r(w[K + 0], w[K + 1], rs);
+        r.y = __funnelshift_r(w[K + 1], w[K + 2], rs);
+        r.z = __funnelshift_r(w[K + 2], w[K + 3], rs);
+        r.w = __funnelshift_r(w[K + 3], w[K + 4], rs);
+        *reinterpret_cast<uint4 *>(out + B) = r;
+    }
+}
+
+// With a whole CTA: chunk c of a message (offset table already written in
+// out) from scratch (words base, states, wstart) into out.  The words buffer
+// must have 16 readable bytes past its last slot.
+__device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const uint8_t *words,
+                                           const uint32_t *states, const uint32_t *wstart,
+                                           uint32_t N, uint32_t slot_bytes, uint32_t c) {
+    const uint32_t *offs = reinterpret_cast<const uint32_t *>(out + 32);
+    const uint64_t D = uint64_t(data0) + offs[c];
+    uint16_t *dst16 = reinterpret_cast<uint16_t *>(out + D);
+    const uint32_t *st = states + uint64_t(c) * N;
+    for (uint32_t i = threadIdx.x; i < 2 * N; i += blockDim.x)
+        dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
+    // words: destination bytes [d0, d1), source bytes from s0 in words
+    const uint64_t d0 = D + 4ull * N;
+    const uint64_t s0 = uint64_t(c) * slot_bytes + wstart[c];
+    const uint64_t d1 = d0 + (slot_bytes - wstart[c]);
+    const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
+    const uint64_t head_end = B0 < d1 ? B0 : d1;
+    for (uint64_t b = d0 + 2ull * threadIdx.x; b < head_end; b += 2ull * blockDim.x)
+        *reinterpret_cast<uint16_t *>(out + b) =
+            *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+    if (B0 < B1) {
+        const uint64_t s_minus_d = s0 - d0;  // modulo 2^64
+        const uint32_t sh = uint32_t(s_minus_d & 15u);
+        const uint32_t rs = 8u * (sh & 3u);
+        switch (sh >> 2) {
+            case 0: pack_blocks<0>(out, words, B0, B1, s_minus_d, rs); break;
+            case 1: pack_blocks<1>(out, words, B0, B1, s_minus_d, rs); break;
+            case 2: pack_blocks<2>(out, words, B0, B1, s_minus_d, rs); break;
+            default: pack_blocks<3>(out, words, B0, B1, s_minus_d, rs); break;
+        }
+    }
+    const uint64_t tail_start = B1 > head_end ? B1 : head_end;
+    for (uint64_t b = tail_start + 2ull * threadIdx.x; b < d1; b += 2ull * blockDim.x)
+        *reinterpret_cast<uint16_t *>(out + b) =
+            *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+}
+
+}  // namespace enc
+}  // namespace rans

@@ -1,0 +1,533 @@
+// rans_batch.cu -- batched decoding and encoding of many independent
+// streams, each in one persistent launch.
+//
+// The work list is built on the device: a setup kernel validates every
+// descriptor and writes the exclusive prefix of work items per stream (one
+// item = up to dec::kWarps chunks of one stream).  The persistent decode
+// kernel's CTAs take items from an atomic counter; an item's stream is found
+// by binary search in the prefix; its model's slot table is rebuilt in shared
+// memory only when the model changes; each warp decodes one chunk with the
+// same per-chunk code as the single-message decoder.
+#include <algorithm>
+
+#include <cuda_runtime.h>
+
+#include "decode_core.cuh"
+#include "encode_core.cuh"
+#include "host_util.h"
+
+namespace rans {
+namespace {
+
+constexpr int kSetupThreads = 1024;
+
+struct BatchLayout {
+    uint64_t prefix, counter, total;
+};
+BatchLayout batch_layout(uint32_t n) {
+    BatchLayout l{};
+    l.prefix = 0;
+    l.counter = round16(4ull * (uint64_t(n) + 1));
+    l.total = l.counter + 16;
+    return l;
+}
+
+struct BatchDecodeParams {
+    const rans_stream *streams;
+    const uint16_t *freqs;
+    uint32_t *status;
+    uint32_t *prefix;   // n_streams + 1 work-item offsets
+    uint32_t *counter;  // next work item
+    uint32_t n_streams;
+    uint32_t n_tables;
+};
+
+struct StreamGeom {
+    uint64_t n_chunks;
+    uint32_t data0;
+    bool ok;
+};
+
+__device__ __forceinline__ StreamGeom check_stream(const rans_stream &d, uint32_t n_tables) {
+    StreamGeom g{0, 0, false};
+    if (d.n_lanes < 1 || d.n_lanes > 32 || d.chunk_symbols < 1 || d.table >= n_tables) return g;
+    if ((reinterpret_cast<uintptr_t>(d.msg) & 15u) || (d.msg_size & 15u) || d.msg == nullptr)
+        return g;
+    if (d.n_symbols && d.symbols == nullptr) return g;
+    g.n_chunks = (d.n_symbols + d.chunk_symbols - 1) / d.chunk_symbols;
+    if (g.n_chunks > 0xFFFFFFFEull) return g;
+    const uint64_t data0 = round16(32 + 4 * (g.n_chunks + 1));
+    if (d.msg_size < data0 || d.msg_size < 48 || d.msg_size - data0 > 0xFFFFFFFFull + 15)
+        return g;
+    g.data0 = uint32_t(data0);
+    g.ok = true;
+    return g;
+}
+
+// One CTA: statuses, work-item prefix, counter.
+__global__ void __launch_bounds__(kSetupThreads)
+    batch_setup_kernel(const __grid_constant__ BatchDecodeParams p) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry_s;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < p.n_streams; base += kSetupThreads) {
+        const uint32_t i = base + tid;
+        uint32_t items = 0;
+        if (i < p.n_streams) {
+            const StreamGeom g = check_stream(p.streams[i], p.n_tables);
+            p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
+            if (g.ok) {
+                const uint64_t k = (g.n_chunks + dec::kWarps - 1) / dec::kWarps;
+                items = k > 0 ? uint32_t(k) : 1u;  // an empty stream still has its header checked
+            }
+        }
+        uint32_t incl = items;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= uint32_t(d)) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = warp_sums[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, wi, d);
+                if (lane >= uint32_t(d)) wi += y;
+            }
+            warp_sums[lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t carry = carry_s;
+        if (i < p.n_streams) p.prefix[i] = carry + warp_sums[warp] + incl - items;
+        __syncthreads();
+        if (tid == kSetupThreads - 1) carry_s = carry + warp_sums[warp] + incl;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        p.prefix[p.n_streams] = carry_s;
+        *p.counter = 0;
+    }
+}
+
+__global__ void __launch_bounds__(dec::kThreads)
+    batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const dec::Smem sm = dec::smem_layout(smem);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t &item_s = sm.misc[0];
+    uint32_t &stream_s = sm.misc[1];
+    uint32_t &loaded = sm.misc[2];      // model whose slot table is in shared memory
+    uint32_t &const_sym = sm.misc[3];
+    uint32_t &model_ok = sm.misc[4];
+    uint32_t &hdr_ok = sm.misc[5];
+    if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
+    dec::WarpRing wr = dec::ring_init(sm, warp, lane);
+    const uint32_t lt = lanemask_lt();
+    const uint32_t total = p.prefix[p.n_streams];
+
+    for (;;) {
+        __syncthreads();  // every warp is done with the previous item
+        if (threadIdx.x == 0) {
+            const uint32_t it = atomicAdd(p.counter, 1u);
+            item_s = it;
+            if (it < total) {
+                uint32_t lo = 0, hi = p.n_streams;  // largest s with prefix[s] <= it
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (p.prefix[mid] <= it) lo = mid;
+                    else hi = mid;
+                }
+                stream_s = lo;
+                const rans_stream d = p.streams[lo];
+                const StreamGeom g = check_stream(d, p.n_tables);
+                hdr_ok = dec::header_ok(d.msg, d.msg_size, g.data0, d.n_symbols, d.n_lanes,
+                                        d.chunk_symbols, uint32_t(g.n_chunks));
+            }
+        }
+        __syncthreads();
+        const uint32_t it = item_s;
+        if (it >= total) break;
+        const uint32_t s = stream_s;
+        const rans_stream d = p.streams[s];
+        if (d.table != loaded) {
+            if (threadIdx.x == 0) const_sym = dec::kNoConst;
+            const uint32_t sum =
+                dec::build_slot_table(p.freqs + uint64_t(d.table) * 256, sm.tab, sm.rings, &const_sym);
+            if (threadIdx.x == 0) {
+                loaded = d.table;
+                model_ok = sum == kM;
+            }
+            __syncthreads();
+        }
+        if (!model_ok) {
+            if (threadIdx.x == 0) report(p.status + s, RANS_ERR_INVALID_ARG);
+            continue;
+        }
+        if (!hdr_ok) {
+            if (threadIdx.x == 0) report(p.status + s, RANS_ERR_CORRUPT);
+            continue;
+        }
+        const StreamGeom g = check_stream(d, p.n_tables);
+        const uint32_t c = (it - p.prefix[s]) * dec::kWarps + warp;
+        if (c < g.n_chunks && !wr.timeouts) {
+            const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
+            const uint64_t first = uint64_t(c) * d.chunk_symbols;
+            const uint32_t n_c = uint32_t(umin64(d.chunk_symbols, d.n_symbols - first));
+            const uint32_t data_end = offs[g.n_chunks];
+            const uint32_t cs = const_sym;
+            const uint32_t st =
+                d.n_lanes == 32
+                    ? dec::decode_chunk<32>(wr, sm.tab_s, d.msg, g.data0, offs[c], offs[c + 1],
+                                            data_end, n_c, 32, d.symbols + first, cs, lane, lt)
+                    : dec::decode_chunk<0>(wr, sm.tab_s, d.msg, g.data0, offs[c], offs[c + 1],
+                                           data_end, n_c, d.n_lanes, d.symbols + first, cs, lane,
+                                           lt);
+            if (st != RANS_OK && lane == 0) report(p.status + s, st);
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched encoding
+// ---------------------------------------------------------------------------
+
+struct EncBatchLayout {
+    uint64_t items, chunks, counter, total;
+};
+__host__ __device__ inline EncBatchLayout enc_batch_layout(uint32_t n) {
+    EncBatchLayout l{};
+    const uint64_t arr = (4ull * (uint64_t(n) + 1) + 15) & ~uint64_t(15);
+    l.items = 0;
+    l.chunks = arr;
+    l.counter = 2 * arr;
+    l.total = l.counter + 16;
+    return l;
+}
+
+struct BatchEncodeParams {
+    const rans_encode_stream *streams;
+    const uint16_t *freqs;
+    uint64_t *out_sizes;
+    uint32_t *status;
+    uint8_t *scratch;
+    uint64_t scratch_cap;
+    uint32_t *items;    // n_streams + 1 work-item offsets
+    uint32_t *chunks;   // n_streams + 1 chunk offsets (for packing)
+    uint32_t *counter;
+    uint32_t n_streams;
+    uint32_t n_tables;
+};
+
+struct EncGeom {
+    uint64_t n_chunks;
+    uint32_t data0;
+    enc::ScratchLayout sl;
+    bool ok;
+};
+
+__device__ __forceinline__ EncGeom check_enc_stream(const rans_encode_stream &d, uint32_t n_tables,
+                                                    uint64_t scratch_cap) {
+    EncGeom g{};
+    g.ok = false;
+    if (d.n_lanes < 1 || d.n_lanes > 32 || d.chunk_symbols < 1 || d.table >= n_tables) return g;
+    if (d.out == nullptr || (reinterpret_cast<uintptr_t>(d.out) & 15u)) return g;
+    if (d.n_symbols && d.symbols == nullptr) return g;
+    g.n_chunks = (d.n_symbols + d.chunk_symbols - 1) / d.chunk_symbols;
+    if (g.n_chunks > 0xFFFFFFFEull ||
+        4ull * d.n_lanes * g.n_chunks + 2ull * d.n_symbols > 0xFFFFFFF0ull)
+        return g;
+    const uint64_t data0 = round16(32 + 4 * (g.n_chunks + 1));
+    const uint64_t worst = data0 + round16(4ull * d.n_lanes * g.n_chunks + 2ull * d.n_symbols);
+    if (d.out_cap < worst) return g;
+    g.sl = enc::scratch_layout(g.n_chunks, d.n_lanes, d.chunk_symbols);
+    if ((d.scratch_offset & 15u) || d.scratch_offset < enc_batch_layout(0).total ||
+        d.scratch_offset > scratch_cap || scratch_cap - d.scratch_offset < g.sl.total)
+        return g;
+    g.data0 = uint32_t(data0);
+    g.ok = true;
+    return g;
+}
+
+// One CTA: statuses, work-item and chunk prefixes, counter.
+__global__ void __launch_bounds__(kSetupThreads)
+    enc_setup_kernel(const __grid_constant__ BatchEncodeParams p) {
+    __shared__ uint32_t sums[2][32];
+    __shared__ uint32_t carry_s[2];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 2) carry_s[tid] = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < p.n_streams; base += kSetupThreads) {
+        const uint32_t i = base + tid;
+        uint32_t v[2] = {0u, 0u};
+        if (i < p.n_streams) {
+            const EncGeom g = check_enc_stream(p.streams[i], p.n_tables, p.scratch_cap);
+            p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
+            p.out_sizes[i] = 0;
+            if (g.ok) {
+                v[0] = uint32_t((g.n_chunks + enc::kWarps - 1) / enc::kWarps);
+                v[1] = uint32_t(g.n_chunks);
+            }
+        }
+        uint32_t incl[2] = {v[0], v[1]};
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t y = __shfl_up_sync(kFull, incl[k], d);
+                if (lane >= uint32_t(d)) incl[k] += y;
+            }
+        }
+        if (lane == 31) {
+            sums[0][warp] = incl[0];
+            sums[1][warp] = incl[1];
+        }
+        __syncthreads();
+        if (warp < 2) {
+            const uint32_t w = sums[warp][lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, wi, d);
+                if (lane >= uint32_t(d)) wi += y;
+            }
+            sums[warp][lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t c0 = carry_s[0], c1 = carry_s[1];
+        if (i < p.n_streams) {
+            p.items[i] = c0 + sums[0][warp] + incl[0] - v[0];
+            p.chunks[i] = c1 + sums[1][warp] + incl[1] - v[1];
+        }
+        __syncthreads();
+        if (tid == kSetupThreads - 1) {
+            carry_s[0] = c0 + sums[0][warp] + incl[0];
+            carry_s[1] = c1 + sums[1][warp] + incl[1];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        p.items[p.n_streams] = carry_s[0];
+        p.chunks[p.n_streams] = carry_s[1];
+        *p.counter = 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t find_stream(const uint32_t *prefix, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;  // largest s with prefix[s] <= v
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(enc::kThreads, 4)
+    batch_encode_kernel(const __grid_constant__ BatchEncodeParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const enc::Smem sm = enc::smem_layout(smem);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t &item_s = sm.misc[0];
+    uint32_t &stream_s = sm.misc[1];
+    uint32_t &loaded = sm.misc[2];
+    uint32_t &model_ok = sm.misc[3];
+    if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
+    const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
+    const uint32_t ge = lanemask_ge();
+    const uint32_t total = p.items[p.n_streams];
+    for (;;) {
+        __syncthreads();  // every warp is done with the previous item
+        if (threadIdx.x == 0) {
+            const uint32_t it = atomicAdd(p.counter, 1u);
+            item_s = it;
+            if (it < total) stream_s = find_stream(p.items, p.n_streams, it);
+        }
+        __syncthreads();
+        const uint32_t it = item_s;
+        if (it >= total) break;
+        const uint32_t s = stream_s;
+        const rans_encode_stream d = p.streams[s];
+        if (d.table != loaded) {
+            const uint32_t sum = enc::build_encode_table(p.freqs + uint64_t(d.table) * 256, sm.tab,
+                                                         reinterpret_cast<uint32_t *>(sm.rings));
+            if (threadIdx.x == 0) {
+                loaded = d.table;
+                model_ok = sum == kM;
+            }
+            __syncthreads();
+        }
+        if (!model_ok) {
+            if (threadIdx.x == 0) report(p.status + s, RANS_ERR_INVALID_ARG);
+            continue;
+        }
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        const uint32_t c = (it - p.items[s]) * enc::kWarps + warp;
+        if (c < g.n_chunks) {
+            uint8_t *scr = p.scratch + d.scratch_offset;
+            const uint64_t first = uint64_t(c) * d.chunk_symbols;
+            const uint32_t n_c = uint32_t(umin64(d.chunk_symbols, d.n_symbols - first));
+            uint32_t acc = 0;
+            uint8_t *slot = scr + g.sl.words + uint64_t(c) * g.sl.slot_bytes;
+            uint32_t *wstart = reinterpret_cast<uint32_t *>(scr + g.sl.wstart) + c;
+            uint32_t *sizes = reinterpret_cast<uint32_t *>(scr + g.sl.sizes) + c;
+            uint32_t *states = reinterpret_cast<uint32_t *>(scr + g.sl.states) + uint64_t(c) * d.n_lanes;
+            if (d.n_lanes == 32)
+                enc::encode_chunk<32>(d.symbols + first, n_c, 32, slot, g.sl.slot_bytes, wstart, sizes,
+                                      states, sm.tab_s, ring_s, ge, lane, acc);
+            else
+                enc::encode_chunk<0>(d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart,
+                                     sizes, states, sm.tab_s, ring_s, ge, lane, acc);
+            if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0)
+                report(p.status + s, RANS_ERR_ZERO_FREQ);
+        }
+    }
+    if (lane == 0) bulk_wait<0>();
+}
+
+constexpr int kFinThreads = 256;
+__global__ void __launch_bounds__(kFinThreads)
+    enc_finalize_kernel(const __grid_constant__ BatchEncodeParams p) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry_s;
+    for (uint32_t s = blockIdx.x; s < p.n_streams; s += gridDim.x) {
+        const uint32_t st = p.status[s];
+        if (st != RANS_OK) {
+            if (threadIdx.x == 0) p.out_sizes[s] = 0;
+            continue;
+        }
+        const rans_encode_stream d = p.streams[s];
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        const uint8_t *scr = p.scratch + d.scratch_offset;
+        enc::finalize_message(d.out, p.out_sizes + s, reinterpret_cast<const uint32_t *>(scr + g.sl.sizes),
+                              d.n_symbols, d.n_lanes, d.chunk_symbols, uint32_t(g.n_chunks), g.data0,
+                              warp_sums, &carry_s);
+        __syncthreads();
+    }
+}
+
+constexpr int kEncPackThreads = 256;
+__global__ void __launch_bounds__(kEncPackThreads)
+    enc_pack_kernel(const __grid_constant__ BatchEncodeParams p) {
+    const uint32_t total = p.chunks[p.n_streams];
+    for (uint32_t gc = blockIdx.x; gc < total; gc += gridDim.x) {
+        const uint32_t s = find_stream(p.chunks, p.n_streams, gc);
+        if (p.status[s] != RANS_OK) continue;
+        const rans_encode_stream d = p.streams[s];
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        const uint8_t *scr = p.scratch + d.scratch_offset;
+        enc::pack_chunk(d.out, g.data0, scr + g.sl.words,
+                        reinterpret_cast<const uint32_t *>(scr + g.sl.states),
+                        reinterpret_cast<const uint32_t *>(scr + g.sl.wstart), d.n_lanes,
+                        g.sl.slot_bytes, gc - p.chunks[s]);
+    }
+}
+
+}  // namespace
+}  // namespace rans
+
+using namespace rans;
+
+extern "C" uint64_t rans_decode_batch_scratch_size(uint32_t n_streams) {
+    return batch_layout(n_streams).total;
+}
+
+extern "C" int rans_decode_batch(const rans_stream *d_streams, uint32_t n_streams,
+                                 const uint16_t *d_freqs, uint32_t n_tables, uint32_t *d_status,
+                                 void *d_scratch, uint64_t scratch_cap, rans_stream_t stream) {
+    if (n_streams == 0) return RANS_OK;
+    if (!d_streams || !d_freqs || n_tables == 0 || !d_status || !d_scratch ||
+        !aligned16(d_scratch) || (reinterpret_cast<uintptr_t>(d_streams) & 7u))
+        return RANS_ERR_INVALID_ARG;
+    const BatchLayout l = batch_layout(n_streams);
+    if (scratch_cap < l.total) return RANS_ERR_BUFFER_TOO_SMALL;
+    uint8_t *scr = static_cast<uint8_t *>(d_scratch);
+    BatchDecodeParams p{};
+    p.streams = d_streams;
+    p.freqs = d_freqs;
+    p.status = d_status;
+    p.prefix = reinterpret_cast<uint32_t *>(scr + l.prefix);
+    p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
+    p.n_streams = n_streams;
+    p.n_tables = n_tables;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+        if (cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(dec::kSmemBytes)) != cudaSuccess)
+            return RANS_ERR_CUDA;
+        configured[dev] = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_decode_kernel, dec::kThreads,
+                                                      dec::kSmemBytes) != cudaSuccess ||
+        per_sm <= 0)
+        return RANS_ERR_CUDA;
+    batch_setup_kernel<<<1, kSetupThreads, 0, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    batch_decode_kernel<<<unsigned(per_sm * sm_count()), dec::kThreads, dec::kSmemBytes, st>>>(p);
+    return check_launch();
+}
+
+extern "C" uint64_t rans_encode_batch_plan(rans_encode_stream *h_streams, uint32_t n_streams) {
+    if (n_streams && !h_streams) return 0;
+    uint64_t off = enc_batch_layout(n_streams).total;
+    for (uint32_t i = 0; i < n_streams; ++i) {
+        rans_encode_stream &d = h_streams[i];
+        rans_params prm{d.n_lanes, d.chunk_symbols};
+        if (!params_ok(&prm)) return 0;
+        const MessageGeometry g = geometry(d.n_symbols, &prm);
+        d.scratch_offset = off;
+        off += round16(enc::scratch_layout(g.n_chunks, d.n_lanes, d.chunk_symbols).total);
+    }
+    return off;
+}
+
+extern "C" int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n_streams,
+                                 const uint16_t *d_freqs, uint32_t n_tables, uint64_t *d_out_sizes,
+                                 uint32_t *d_status, void *d_scratch, uint64_t scratch_cap,
+                                 rans_stream_t stream) {
+    if (n_streams == 0) return RANS_OK;
+    if (!d_streams || !d_freqs || n_tables == 0 || !d_status || !d_out_sizes || !d_scratch ||
+        !aligned16(d_scratch) || (reinterpret_cast<uintptr_t>(d_streams) & 7u) ||
+        (reinterpret_cast<uintptr_t>(d_out_sizes) & 7u))
+        return RANS_ERR_INVALID_ARG;
+    const EncBatchLayout l = enc_batch_layout(n_streams);
+    if (scratch_cap < l.total) return RANS_ERR_BUFFER_TOO_SMALL;
+    uint8_t *scr = static_cast<uint8_t *>(d_scratch);
+    BatchEncodeParams p{};
+    p.streams = d_streams;
+    p.freqs = d_freqs;
+    p.out_sizes = d_out_sizes;
+    p.status = d_status;
+    p.scratch = scr;
+    p.scratch_cap = scratch_cap;
+    p.items = reinterpret_cast<uint32_t *>(scr + l.items);
+    p.chunks = reinterpret_cast<uint32_t *>(scr + l.chunks);
+    p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
+    p.n_streams = n_streams;
+    p.n_tables = n_tables;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_encode_kernel, enc::kThreads,
+                                                      enc::kSmemBytes) != cudaSuccess ||
+        per_sm <= 0)
+        return RANS_ERR_CUDA;
+    const unsigned sms = unsigned(sm_count());
+    enc_setup_kernel<<<1, kSetupThreads, 0, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    batch_encode_kernel<<<unsigned(per_sm) * sms, enc::kThreads, enc::kSmemBytes, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    enc_finalize_kernel<<<std::min<unsigned>(n_streams, 8 * sms), kFinThreads, 0, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    enc_pack_kernel<<<16 * sms, kEncPackThreads, 0, st>>>(p);
+    return check_launch();
+}

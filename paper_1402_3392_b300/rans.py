@@ -25,7 +25,9 @@ __all__ = [
     "RANS_ERR_OOM", "RANS_M", "RANS_L", "RANS_LOG2_M", "library_path", "lib",
     "rans_version", "rans_status_string", "rans_quantize_table", "rans_max_encoded_size",
     "rans_encode_scratch_size", "rans_encode", "rans_decode", "rans_encode_static_scratch",
-    "RANS_STATIC_SCRATCH_BYTES", "encode", "decode",
+    "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
+    "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
+    "rans_encode_batch",
 ]
 
 RANS_OK = 0
@@ -40,6 +42,17 @@ RANS_LOG2_M = 12
 RANS_M = 1 << RANS_LOG2_M
 RANS_L = 1 << 16
 RANS_STATIC_SCRATCH_BYTES = 64 << 20
+
+
+# Layouts of rans_stream and rans_encode_stream (include/rans.h).
+STREAM_DTYPE = np.dtype([("msg", "<u8"), ("msg_size", "<u8"), ("symbols", "<u8"),
+                         ("n_symbols", "<u8"), ("table", "<u4"), ("n_lanes", "<u4"),
+                         ("chunk_symbols", "<u4"), ("reserved", "<u4")])
+ENCODE_STREAM_DTYPE = np.dtype([("symbols", "<u8"), ("n_symbols", "<u8"), ("out", "<u8"),
+                                ("out_cap", "<u8"), ("scratch_offset", "<u8"), ("table", "<u4"),
+                                ("n_lanes", "<u4"), ("chunk_symbols", "<u4"),
+                                ("reserved", "<u4")])
+assert STREAM_DTYPE.itemsize == 48 and ENCODE_STREAM_DTYPE.itemsize == 56
 
 
 class RansParams(C.Structure):
@@ -68,6 +81,10 @@ def _load() -> C.CDLL:
         "rans_encode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
+        "rans_decode_batch_scratch_size": (u64, [u32]),
+        "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
+        "rans_encode_batch_plan": (u64, [vp, u32]),
+        "rans_encode_batch": (i32, [vp, u32, vp, u32, vp, vp, vp, u64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +192,35 @@ def rans_decode(d_msg, msg_size, freq, n_lanes, chunk_symbols, d_symbols, n_symb
     rc = lib.rans_decode(_ptr(d_msg), int(msg_size), f.ctypes.data, f.size, C.byref(p),
                          _ptr(d_symbols), int(n_symbols), _ptr(d_status), _stream(stream))
     return _check(rc, "rans_decode") if check else rc
+
+
+def rans_decode_batch_scratch_size(n_streams: int) -> int:
+    return int(lib.rans_decode_batch_scratch_size(int(n_streams)))
+
+
+def rans_decode_batch(d_streams, n_streams, d_freqs, n_tables, d_status, d_scratch, scratch_cap,
+                      stream=None, check=True) -> int:
+    rc = lib.rans_decode_batch(_ptr(d_streams), int(n_streams), _ptr(d_freqs), int(n_tables),
+                               _ptr(d_status), _ptr(d_scratch), int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_decode_batch") if check else rc
+
+
+def rans_encode_batch_plan(h_streams: np.ndarray) -> int:
+    """Fill h_streams["scratch_offset"] in place (ENCODE_STREAM_DTYPE array)
+    and return the scratch bytes rans_encode_batch needs."""
+    assert h_streams.dtype == ENCODE_STREAM_DTYPE and h_streams.flags.c_contiguous
+    total = int(lib.rans_encode_batch_plan(h_streams.ctypes.data, h_streams.size))
+    if h_streams.size and total == 0:
+        raise RansError(RANS_ERR_INVALID_ARG, "rans_encode_batch_plan")
+    return total
+
+
+def rans_encode_batch(d_streams, n_streams, d_freqs, n_tables, d_out_sizes, d_status, d_scratch,
+                      scratch_cap, stream=None, check=True) -> int:
+    rc = lib.rans_encode_batch(_ptr(d_streams), int(n_streams), _ptr(d_freqs), int(n_tables),
+                               _ptr(d_out_sizes), _ptr(d_status), _ptr(d_scratch),
+                               int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_batch") if check else rc
 
 
 # ---- conveniences: allocate with torch, call the entry points -----------------

@@ -1,0 +1,229 @@
+"""Batched encode/decode (rans_encode_batch, rans_decode_batch) against the
+CPU oracle, stream by stream and byte for byte, plus per-stream error
+statuses, CUDA-graph replay and equality with one call per stream."""
+import numpy as np
+import pytest
+
+from paper_1402_3392_b300 import batch as B
+from paper_1402_3392_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def random_model(rlib, rng):
+    kind = rng.integers(0, 5)
+    if kind == 0:
+        p = wl.zipf_probs(int(rng.integers(2, 257)), float(rng.uniform(0.8, 1.4)))
+    elif kind == 1:
+        p = wl.dirichlet_probs(rng, int(rng.integers(16, 257)), 0.3)
+    elif kind == 2:
+        p0 = float(rng.uniform(0.5, 0.999))
+        p = np.array([p0, 1 - p0])
+    elif kind == 3:
+        p = np.array([1.0])
+    else:
+        p = np.full(256, 1 / 256)
+    return rlib.rans_quantize_table(wl.weights_from_probs(p))
+
+
+def random_streams(rlib, rng, count, max_n=100_000):
+    tables = [random_model(rlib, rng) for _ in range(max(2, count // 4))]
+    streams = []
+    for i in range(count):
+        t = int(rng.integers(0, len(tables)))
+        f = tables[t]
+        n = int(rng.choice([0, 1, 31, 33, int(rng.integers(1, 5000)), int(rng.integers(1, max_n))]))
+        sym = rng.choice(len(f), size=n, p=f / f.sum()).astype(np.uint8)
+        N = int(rng.choice([32, 32, 32, 16, 7, 1]))
+        CS = int(rng.choice([4096, 1000, 65536, 333, 32]))
+        streams.append(dict(sym=sym, table=t, N=N, CS=CS))
+    return tables, streams
+
+
+def upload_symbols(torch, cuda, streams):
+    offs, total = B.aligned_offsets([s["sym"].size for s in streams])
+    host = np.zeros(max(total, B.ALIGN), dtype=np.uint8)
+    for s, o in zip(streams, offs):
+        host[o:o + s["sym"].size] = s["sym"]
+    return torch.from_numpy(host).to(cuda), offs
+
+
+def test_batch_decode_of_oracle_messages(rlib, orc, cuda):
+    import torch
+
+    rng = np.random.default_rng(101)
+    tables, streams = random_streams(rlib, rng, 60)
+    msgs = [orc.encode_message(s["sym"], tables[s["table"]], N=s["N"], chunk_symbols=s["CS"])
+            for s in streams]
+    offs, total = B.aligned_offsets([m.size for m in msgs])
+    host = np.zeros(total, dtype=np.uint8)
+    for m, o in zip(msgs, offs):
+        host[o:o + m.size] = m
+    arena = torch.from_numpy(host).to(cuda)
+    dec = B.BatchDecoder(arena, offs, [m.size for m in msgs], [s["sym"].size for s in streams],
+                         B.upload_tables(tables, cuda), [s["table"] for s in streams],
+                         [s["N"] for s in streams], [s["CS"] for s in streams])
+    status = dec()
+    torch.cuda.synchronize()
+    assert not status.any(), status.cpu().numpy()
+    for i, s in enumerate(streams):
+        assert np.array_equal(dec.output(i).cpu().numpy(), s["sym"]), i
+
+
+def test_batch_encode_matches_oracle(rlib, orc, cuda):
+    import torch
+
+    rng = np.random.default_rng(103)
+    tables, streams = random_streams(rlib, rng, 60)
+    arena, offs = upload_symbols(torch, cuda, streams)
+    eb = B.encode_batch(arena, offs, [s["sym"].size for s in streams], B.upload_tables(tables, cuda),
+                        [s["table"] for s in streams], [s["N"] for s in streams],
+                        [s["CS"] for s in streams])
+    torch.cuda.synchronize()
+    assert not eb.status.any(), eb.status.cpu().numpy()
+    sizes = eb.host_sizes()
+    for i, s in enumerate(streams):
+        ref = orc.encode_message(s["sym"], tables[s["table"]], N=s["N"], chunk_symbols=s["CS"])
+        assert sizes[i] == ref.size, i
+        assert np.array_equal(eb.message(i).cpu().numpy(), ref), i
+
+
+def test_batch_round_trip_log_uniform_streams(rlib, orc, cuda):
+    """500 streams, sizes log-uniform in [1 KiB, 1 MiB], per-stream
+    Dirichlet(0.3) models over 16..256 symbols; all round-trip on the device,
+    ten sampled streams are re-encoded by the oracle."""
+    import torch
+
+    rng = np.random.default_rng(107)
+    sizes = wl.log_uniform_sizes(rng, 500, 1 << 10, 1 << 20)
+    tables = [rlib.rans_quantize_table(wl.weights_from_probs(
+        wl.dirichlet_probs(rng, int(rng.integers(16, 257)), 0.3))) for _ in range(500)]
+    streams = [dict(sym=rng.choice(len(tables[i]), size=int(sizes[i]),
+                                   p=tables[i] / tables[i].sum()).astype(np.uint8),
+                    table=i, N=32, CS=16384) for i in range(500)]
+    arena, offs = upload_symbols(torch, cuda, streams)
+    tdev = B.upload_tables(tables, cuda)
+    n_sym = [s["sym"].size for s in streams]
+    eb = B.encode_batch(arena, offs, n_sym, tdev, list(range(500)), 32, 16384)
+    torch.cuda.synchronize()
+    assert not eb.status.any()
+    dec = B.BatchDecoder(eb.arena, eb.offsets, eb.host_sizes(), n_sym, tdev, list(range(500)),
+                         32, 16384)
+    st = dec()
+    torch.cuda.synchronize()
+    assert not st.any()
+    for i, o in enumerate(offs):
+        assert torch.equal(dec.output(i), arena[o:o + n_sym[i]]), i
+    for i in rng.choice(500, size=10, replace=False):
+        ref = orc.encode_message(streams[i]["sym"], tables[i], N=32, chunk_symbols=16384)
+        assert np.array_equal(eb.message(int(i)).cpu().numpy(), ref), i
+
+
+def test_batch_statuses_are_per_stream(rlib, orc, cuda):
+    import torch
+
+    rng = np.random.default_rng(109)
+    tables, streams = random_streams(rlib, rng, 12, max_n=20000)
+    for s in streams:
+        s["N"], s["CS"] = 32, 4096
+    zipf = rlib.rans_quantize_table(wl.weights_from_probs(wl.zipf_probs(256, 1.1)))
+    bad_table = np.zeros(256, dtype=np.uint16)
+    bad_table[:3] = 1000                       # sums to 3000: not a valid model
+    tables = list(tables) + [zipf, bad_table]
+    streams[0] = dict(sym=rng.choice(256, size=20000, p=zipf / zipf.sum()).astype(np.uint8),
+                      table=len(tables) - 2, N=32, CS=4096)
+    msgs = [orc.encode_message(s["sym"], tables[s["table"]], N=32, chunk_symbols=4096)
+            for s in streams]
+    # stream 0: one corrupt word; then a table index out of range, an invalid
+    # model and N = 0 on three other streams
+    corrupt = 0
+    m = msgs[corrupt].copy()
+    m[-20] ^= 0x10
+    msgs[corrupt] = m
+    offs, total = B.aligned_offsets([m.size for m in msgs])
+    host = np.zeros(total, dtype=np.uint8)
+    for mm, o in zip(msgs, offs):
+        host[o:o + mm.size] = mm
+    arena = torch.from_numpy(host).to(cuda)
+    table_idx = [s["table"] for s in streams]
+    n_lanes = [32] * len(streams)
+    others = [i for i in range(len(streams)) if i != corrupt]
+    t_oob, t_badmodel, t_n0 = others[0], others[1], others[2]
+    table_idx[t_oob] = len(tables) + 5
+    table_idx[t_badmodel] = len(tables) - 1
+    n_lanes[t_n0] = 0
+    dec = B.BatchDecoder(arena, offs, [m.size for m in msgs], [s["sym"].size for s in streams],
+                         B.upload_tables(tables, cuda), table_idx, n_lanes, 4096)
+    st = dec().cpu().numpy()
+    expect = {corrupt: rlib.RANS_ERR_CORRUPT, t_oob: rlib.RANS_ERR_INVALID_ARG,
+              t_badmodel: rlib.RANS_ERR_INVALID_ARG, t_n0: rlib.RANS_ERR_INVALID_ARG}
+    for i in range(len(streams)):
+        assert st[i] == expect.get(i, 0), (i, st)
+        if i not in expect:
+            assert np.array_equal(dec.output(i).cpu().numpy(), streams[i]["sym"])
+    # encoding: a symbol without probability only fails its own stream
+    tables.append(np.array([3000, 1096], dtype=np.uint16))      # binary model
+    syms = [s["sym"].copy() for s in streams]
+    z = len(streams) - 1
+    streams[z]["table"] = len(tables) - 1
+    syms[z] = rng.integers(0, 2, size=1000).astype(np.uint8)
+    syms[z][5] = 255                                             # outside the alphabet
+    enc_streams = [dict(sym=s) for s in syms]
+    sarena, soffs = upload_symbols(torch, cuda, enc_streams)
+    eb = B.encode_batch(sarena, soffs, [s.size for s in syms], B.upload_tables(tables, cuda),
+                        [s["table"] for s in streams], 32, 4096)
+    torch.cuda.synchronize()
+    est = eb.status.cpu().numpy()
+    sizes = eb.host_sizes()
+    for i in range(len(streams)):
+        if i == z:
+            assert est[i] == rlib.RANS_ERR_ZERO_FREQ and sizes[i] == 0
+        else:
+            assert est[i] == 0 and sizes[i] > 0, (i, est)
+
+
+def test_batch_decode_replays_in_a_cuda_graph(rlib, orc, cuda):
+    import torch
+
+    rng = np.random.default_rng(113)
+    tables, streams = random_streams(rlib, rng, 40)
+    msgs = [orc.encode_message(s["sym"], tables[s["table"]], N=s["N"], chunk_symbols=s["CS"])
+            for s in streams]
+    offs, total = B.aligned_offsets([m.size for m in msgs])
+    host = np.zeros(total, dtype=np.uint8)
+    for m, o in zip(msgs, offs):
+        host[o:o + m.size] = m
+    arena = torch.from_numpy(host).to(cuda)
+    dec = B.BatchDecoder(arena, offs, [m.size for m in msgs], [s["sym"].size for s in streams],
+                         B.upload_tables(tables, cuda), [s["table"] for s in streams],
+                         [s["N"] for s in streams], [s["CS"] for s in streams])
+    dec()  # first call outside capture (function attributes, occupancy query)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            dec(stream=s)
+    for _ in range(2):
+        dec.out_arena.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert not dec.status.any()
+        for i, st in enumerate(streams):
+            assert np.array_equal(dec.output(i).cpu().numpy(), st["sym"]), i
+
+
+def test_batch_equals_one_call_per_stream(rlib, orc, cuda):
+    import torch
+
+    rng = np.random.default_rng(127)
+    tables, streams = random_streams(rlib, rng, 20)
+    arena, offs = upload_symbols(torch, cuda, streams)
+    eb = B.encode_batch(arena, offs, [s["sym"].size for s in streams], B.upload_tables(tables, cuda),
+                        [s["table"] for s in streams], [s["N"] for s in streams],
+                        [s["CS"] for s in streams])
+    torch.cuda.synchronize()
+    for i, s in enumerate(streams):
+        o = int(offs[i])
+        single, _, _ = rlib.encode(arena[o:o + s["sym"].size], tables[s["table"]], s["N"], s["CS"])
+        assert torch.equal(single, eb.message(i)), i
