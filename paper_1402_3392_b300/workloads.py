@@ -115,3 +115,52 @@ def binary_chunk_probs(rng: np.random.Generator, n_chunks: int, lo: float = 0.5,
 def poisson_arrivals(rng: np.random.Generator, rate_per_s: float, count: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process with the given rate."""
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+
+
+def batched_models(rng: np.random.Generator, count: int, alpha_lo: int = 16,
+                   alpha_hi: int = 256, dirichlet: float = 0.3):
+    """Per-stream probability vectors: alphabet size uniform in
+    [alpha_lo, alpha_hi], Dirichlet(dirichlet) probabilities."""
+    sizes = rng.integers(alpha_lo, alpha_hi + 1, size=count)
+    return [dirichlet_probs(rng, int(a), dirichlet) for a in sizes]
+
+
+def streams_on_device(probs, n_symbols, offsets, arena_bytes: int, seed: int, device,
+                      piece: int = 1 << 27):
+    """i.i.d. symbols for many streams at once, on the device.  Stream k has
+    n_symbols[k] symbols drawn from probs[k], stored at arena[offsets[k]:].
+    One search over the concatenated, shifted CDFs (stream k's CDF + k) maps a
+    uniform draw u of stream k (value k + u) to its symbol.  Bytes between
+    streams (alignment filler) are zero."""
+    import torch
+
+    n = len(probs)
+    starts = np.zeros(n, dtype=np.int64)
+    cdfs = []
+    pos = 0
+    for k, p in enumerate(probs):
+        c = np.cumsum(np.asarray(p, dtype=np.float64))
+        c[-1] = 1.0
+        cdfs.append(k + c)
+        starts[k] = pos
+        pos += c.size
+    g = torch.tensor(np.concatenate(cdfs), dtype=torch.float64, device=device)
+    start_d = torch.tensor(starts, dtype=torch.int64, device=device)
+    alpha_d = torch.tensor([len(p) for p in probs], dtype=torch.int64, device=device)
+    begins = torch.tensor(np.asarray(offsets, dtype=np.int64), dtype=torch.int64, device=device)
+    ends = begins + torch.tensor(np.asarray(n_symbols, dtype=np.int64), dtype=torch.int64,
+                                 device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed & 0x7FFFFFFFFFFFFFFF)
+    arena = torch.empty(max(arena_bytes, 1), dtype=torch.uint8, device=device)
+    for a in range(0, arena_bytes, piece):
+        z = min(arena_bytes, a + piece)
+        posn = torch.arange(a, z, dtype=torch.int64, device=device)
+        k = torch.searchsorted(ends, posn, right=True).clamp_(max=n - 1)
+        u = torch.rand(z - a, generator=gen, device=device, dtype=torch.float64)
+        idx = torch.searchsorted(g, k.to(torch.float64) + u, right=True)
+        sym = torch.minimum(idx - start_d[k], alpha_d[k] - 1).clamp_(min=0)
+        sym = torch.where((posn >= begins[k]) & (posn < ends[k]), sym, 0)
+        arena[a:z] = sym.to(torch.uint8)
+        del posn, k, u, idx, sym
+    return arena
