@@ -246,6 +246,69 @@ int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n_streams,
                       rans_stream_t stream);
 
 /*
+ * Serving: a continuous-batching request loop.  The server owns a device
+ * arena (the caller's HBM budget) and a few CUDA streams ("slots").  It
+ * replays a trace of encode and decode requests in real time: a request is
+ * pending from its arrival time; pending requests are admitted in arrival
+ * order while their device input and output fit in the arena; admitted
+ * requests form the next batch in an idle slot -- copies of the inputs to the
+ * device, one rans_encode_batch and/or rans_decode_batch launch, copies of the
+ * outputs back -- while later arrivals are admitted into the other slots as
+ * memory frees up, so the batches overlap on the device.  The models stay
+ * resident on the device for the server's lifetime.
+ */
+#define RANS_REQ_ENCODE 0u
+#define RANS_REQ_DECODE 1u
+
+typedef struct {
+    uint32_t kind;            /* RANS_REQ_ENCODE or RANS_REQ_DECODE */
+    uint32_t table;           /* model index in the server's d_freqs */
+    uint32_t n_lanes;         /* N of the message (made or read) */
+    uint32_t chunk_symbols;   /* chunk size of the message */
+    const uint8_t *input;     /* host (page-locked for overlap): symbols (encode)
+                                 or a message (decode) */
+    uint64_t input_size;      /* bytes: = n_symbols (encode), message size (decode) */
+    uint64_t n_symbols;       /* symbols in the request */
+    uint8_t *output;          /* host: receives the message (encode) or symbols (decode) */
+    uint64_t output_cap;      /* >= rans_max_encoded_size (encode), >= n_symbols (decode) */
+    double arrival_s;         /* arrival, seconds after rans_server_run starts;
+                                 non-decreasing along the trace */
+} rans_request;
+
+typedef struct {
+    uint64_t output_size;     /* bytes written to output */
+    uint32_t status;          /* RANS_OK, the coder's error, or RANS_ERR_OOM when the
+                                 request can never fit the budget */
+    uint32_t batch;           /* index of the batch that served it */
+    double admit_s;           /* admission time, seconds after the start */
+    double done_s;            /* completion (output in host memory) */
+} rans_result;
+
+typedef struct rans_server rans_server;
+
+/*
+ * rans_server_create -- d_freqs: device models (n_tables x 256 u16, kept
+ * resident); d_arena: device memory of arena_bytes (16-byte aligned) that
+ * bounds everything the server places on the device; max_batch: requests per
+ * batch; n_slots: batches in flight at once (1..16).  Creates CUDA streams,
+ * events and page-locked staging; allocates no device memory.
+ */
+int rans_server_create(const uint16_t *d_freqs, uint32_t n_tables, void *d_arena,
+                       uint64_t arena_bytes, uint32_t max_batch, uint32_t n_slots,
+                       rans_server **out);
+
+/*
+ * rans_server_run -- serve n requests (host array, sorted by arrival) in real
+ * time; blocks until every request is done and fills results[0..n).
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG (a malformed request; nothing runs)
+ * or RANS_ERR_CUDA.
+ */
+int rans_server_run(rans_server *server, const rans_request *reqs, uint32_t n,
+                    rans_result *results);
+
+void rans_server_destroy(rans_server *server);
+
+/*
  * rans_encode_static_scratch -- rans_encode for callers that cannot allocate
  * device memory.  The paper has no counterpart: this is a service of the
  * library, not a step of the method.

@@ -27,7 +27,8 @@ __all__ = [
     "rans_encode_scratch_size", "rans_encode", "rans_decode", "rans_encode_static_scratch",
     "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
-    "rans_encode_batch",
+    "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
+    "Server",
 ]
 
 RANS_OK = 0
@@ -52,7 +53,16 @@ ENCODE_STREAM_DTYPE = np.dtype([("symbols", "<u8"), ("n_symbols", "<u8"), ("out"
                                 ("out_cap", "<u8"), ("scratch_offset", "<u8"), ("table", "<u4"),
                                 ("n_lanes", "<u4"), ("chunk_symbols", "<u4"),
                                 ("reserved", "<u4")])
+REQUEST_DTYPE = np.dtype([("kind", "<u4"), ("table", "<u4"), ("n_lanes", "<u4"),
+                          ("chunk_symbols", "<u4"), ("input", "<u8"), ("input_size", "<u8"),
+                          ("n_symbols", "<u8"), ("output", "<u8"), ("output_cap", "<u8"),
+                          ("arrival_s", "<f8")])
+RESULT_DTYPE = np.dtype([("output_size", "<u8"), ("status", "<u4"), ("batch", "<u4"),
+                         ("admit_s", "<f8"), ("done_s", "<f8")])
+RANS_REQ_ENCODE = 0
+RANS_REQ_DECODE = 1
 assert STREAM_DTYPE.itemsize == 48 and ENCODE_STREAM_DTYPE.itemsize == 56
+assert REQUEST_DTYPE.itemsize == 64 and RESULT_DTYPE.itemsize == 32
 
 
 class RansParams(C.Structure):
@@ -85,6 +95,9 @@ def _load() -> C.CDLL:
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
         "rans_encode_batch_plan": (u64, [vp, u32]),
         "rans_encode_batch": (i32, [vp, u32, vp, u32, vp, vp, vp, u64, vp]),
+        "rans_server_create": (i32, [vp, u32, vp, u64, u32, u32, C.POINTER(vp)]),
+        "rans_server_run": (i32, [vp, vp, u32, vp]),
+        "rans_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +234,39 @@ def rans_encode_batch(d_streams, n_streams, d_freqs, n_tables, d_out_sizes, d_st
                                _ptr(d_out_sizes), _ptr(d_status), _ptr(d_scratch),
                                int(scratch_cap), _stream(stream))
     return _check(rc, "rans_encode_batch") if check else rc
+
+
+class Server:
+    """rans_server_create / rans_server_run / rans_server_destroy.
+
+    tables_dev: device [n_tables, 256] u16 models (kept resident);
+    arena: torch uint8 device tensor = the server's HBM budget."""
+
+    def __init__(self, tables_dev, arena, max_batch: int = 64, n_slots: int = 3):
+        self._tables, self._arena = tables_dev, arena
+        h = C.c_void_p()
+        _check(lib.rans_server_create(_ptr(tables_dev), tables_dev.shape[0], _ptr(arena),
+                                      arena.numel(), max_batch, n_slots, C.byref(h)),
+               "rans_server_create")
+        self._h = h
+
+    def run(self, reqs: np.ndarray) -> np.ndarray:
+        assert reqs.dtype == REQUEST_DTYPE and reqs.flags.c_contiguous
+        res = np.zeros(reqs.size, dtype=RESULT_DTYPE)
+        _check(lib.rans_server_run(self._h, reqs.ctypes.data, reqs.size, res.ctypes.data),
+               "rans_server_run")
+        return res
+
+    def close(self):
+        if self._h:
+            lib.rans_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- conveniences: allocate with torch, call the entry points -----------------
