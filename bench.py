@@ -55,8 +55,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched",
-                    help="extra legs after the headline one: comma list of batched, none")
+    ap.add_argument("--legs", default="batched,serving",
+                    help="extra legs after the headline one: comma list of batched, serving, none")
+    ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
     return ap.parse_args(argv)
@@ -378,6 +379,92 @@ def batched_leg(rans, dev, args, hbm):
 
 
 # ---------------------------------------------------------------------------
+# Serving leg: Poisson arrivals through the continuous-batching server
+# ---------------------------------------------------------------------------
+
+def serving_leg(rans, dev, args):
+    """Encode and decode requests (50/50) of log-uniform size 4 KiB..64 MiB,
+    one Dirichlet(0.5) model over 64..256 symbols each, arriving as a Poisson
+    process at several rates, served from a 40 GiB device budget with host
+    inputs and outputs (page-locked).  Latency = completion - arrival."""
+    import torch
+
+    from paper_1402_3392_b300 import batch as B
+
+    cfg = wl.WORKLOADS["serving"]
+    count = args.serving_requests
+    rng = wl.rng_for("serving")
+    sizes = wl.log_uniform_sizes(rng, count, cfg["size_lo"], cfg["size_hi"])
+    probs = wl.batched_models(rng, count, cfg["alpha_lo"], cfg["alpha_hi"], cfg["dirichlet"])
+    tables = [rans.rans_quantize_table(wl.weights_from_probs(p)) for p in probs]
+    kinds = rng.integers(0, 2, size=count)
+    N, CS = 32, 1 << 16
+    offs, arena_bytes = B.aligned_offsets(sizes)
+    sym = wl.streams_on_device(probs, sizes, offs, arena_bytes, wl.seed_for("serving"), dev)
+    tdev = B.upload_tables(tables, dev)
+    eb = B.encode_batch(sym, offs, sizes, tdev, np.arange(count), N, CS)
+    torch.cuda.synchronize()
+    assert not eb.status.any()
+    msg_sizes = eb.host_sizes()
+    # host payloads: symbols for encode requests, messages for decode requests
+    in_sizes = np.where(kinds == rans.RANS_REQ_ENCODE, sizes, msg_sizes)
+    caps = np.where(kinds == rans.RANS_REQ_ENCODE,
+                    [rans.rans_max_encoded_size(int(n), N, CS) for n in sizes], sizes)
+    in_offs, in_total = B.aligned_offsets(in_sizes)
+    out_offs, out_total = B.aligned_offsets(caps)
+    h_in = torch.empty(in_total, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(out_total, dtype=torch.uint8, pin_memory=True)
+    for i in range(count):
+        if kinds[i] == rans.RANS_REQ_ENCODE:
+            src = sym[int(offs[i]):int(offs[i]) + int(sizes[i])]
+        else:
+            src = eb.arena[int(eb.offsets[i]):int(eb.offsets[i]) + int(msg_sizes[i])]
+        h_in[int(in_offs[i]):int(in_offs[i]) + int(in_sizes[i])].copy_(src)
+    budget = torch.empty(cfg["budget_bytes"], dtype=torch.uint8, device=dev)
+    srv = rans.Server(tdev, budget, max_batch=64, n_slots=3)
+    reqs = np.zeros(count, dtype=rans.REQUEST_DTYPE)
+    reqs["kind"] = kinds
+    reqs["table"] = np.arange(count)
+    reqs["n_lanes"] = N
+    reqs["chunk_symbols"] = CS
+    reqs["input"] = h_in.data_ptr() + in_offs
+    reqs["input_size"] = in_sizes
+    reqs["n_symbols"] = sizes
+    reqs["output"] = h_out.data_ptr() + out_offs
+    reqs["output_cap"] = caps
+    raw_total = int(sizes.sum())
+    rows = []
+    exact = None
+    for rate in (1000.0, 5000.0, 20000.0, 50000.0):
+        reqs["arrival_s"] = wl.poisson_arrivals(np.random.default_rng(int(rate)), rate, count)
+        res = srv.run(reqs)
+        lat = (res["done_s"] - reqs["arrival_s"]) * 1e3
+        span = float(res["done_s"].max() - reqs["arrival_s"].min())
+        ok = bool((res["status"] == 0).all())
+        if exact is None:  # served bytes equal the direct batched path, every request
+            exact = ok
+            for i in range(count):
+                n_out = int(res["output_size"][i])
+                got = h_out[int(out_offs[i]):int(out_offs[i]) + n_out]
+                if kinds[i] == rans.RANS_REQ_ENCODE:
+                    want = eb.arena[int(eb.offsets[i]):int(eb.offsets[i]) + int(msg_sizes[i])]
+                else:
+                    want = sym[int(offs[i]):int(offs[i]) + int(sizes[i])]
+                exact = exact and n_out == want.numel() and torch.equal(got, want.cpu())
+        rows.append({"rate_req_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)),
+                     "gbs": raw_total / span / 1e9, "achieved_req_s": count / span,
+                     "batches": int(res["batch"].max()) + 1, "all_ok": ok})
+    srv.close()
+    return {"workload": f"{count} requests, sizes log-uniform {cfg['size_lo']}..{cfg['size_hi']} B "
+                        f"({raw_total / 2**30:.2f} GiB raw), encode/decode 50/50, "
+                        f"Dirichlet({cfg['dirichlet']}) over {cfg['alpha_lo']}..{cfg['alpha_hi']} "
+                        f"symbols, {cfg['budget_bytes'] >> 30} GiB device budget, host payloads",
+            "server": "max_batch 64, 3 slots", "bit_exact_vs_batched_path": bool(exact),
+            "rates": rows}
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 
@@ -472,10 +559,15 @@ def main(argv=None):
 
     legs = [x for x in args.legs.split(",") if x and x != "none"]
     extra = {}
-    if "batched" in legs:
+    if legs:
         del msg, scratch, dec, sym
         torch.cuda.empty_cache()
+    if "batched" in legs:
         extra["batched"] = batched_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
+    if "serving" in legs:
+        extra["serving"] = serving_leg(rans, dev, args)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         hbm, peak_kind = peaks()
