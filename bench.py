@@ -55,8 +55,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched,serving",
-                    help="extra legs after the headline one: comma list of batched, serving, none")
+    ap.add_argument("--legs", default="batched,binary,single,serving",
+                    help="extra legs after the headline one: comma list of batched, binary, "
+                         "single, serving, none")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -379,6 +380,95 @@ def batched_leg(rans, dev, args, hbm):
 
 
 # ---------------------------------------------------------------------------
+# Binary and single-stream legs
+# ---------------------------------------------------------------------------
+
+def binary_leg(rans, dev, args, hbm):
+    """4096 streams of 64 KiB {0,1} symbols, stream k with its own model
+    p0 ~ U[0.5, 0.999] (one binary model per 64 KiB, as in the rABS-style
+    workload), batched encode and decode with the autotuned layout."""
+    import torch
+
+    from paper_1402_3392_b300 import autotune
+    from paper_1402_3392_b300 import batch as B
+
+    cfg = wl.WORKLOADS["binary"]
+    count = cfg["n_chunks"]
+    per = cfg["n_symbols"] // count
+    rng = wl.rng_for("binary")
+    p0 = wl.binary_chunk_probs(rng, count, cfg["p0_lo"], cfg["p0_hi"])
+    probs = [np.array([p, 1.0 - p]) for p in p0]
+    tables = [rans.rans_quantize_table(wl.weights_from_probs(p)) for p in probs]
+    sizes = np.full(count, per, dtype=np.int64)
+    offs, arena_bytes = B.aligned_offsets(sizes)
+    sym = wl.streams_on_device(probs, sizes, offs, arena_bytes, wl.seed_for("binary"), dev)
+    tdev = B.upload_tables(tables, dev)
+    idx = np.arange(count)
+    sample = np.arange(0, count, 16)
+    best, tried = autotune.autotune(sym, offs[sample], sizes[sample], tdev, sample, widths=(32,),
+                                    reps=3)
+    cs = autotune.chunk_sizes(sizes, best["chunk"], best["policy"])
+    eb = B.encode_batch(sym, offs, sizes, tdev, idx, 32, cs)
+    torch.cuda.synchronize()
+    assert not eb.status.any()
+    d_desc, scratch = eb._keep
+    enc_ms = _events(torch, lambda: rans.rans_encode_batch(
+        d_desc, count, tdev, count, eb.sizes, eb.status, scratch, scratch.numel()), 3)
+    msg_sizes = eb.host_sizes()
+    dec = B.BatchDecoder(eb.arena, eb.offsets, msg_sizes, sizes, tdev, idx, 32, cs,
+                         out_offsets=offs,
+                         out_arena=torch.zeros(arena_bytes, dtype=torch.uint8, device=dev))
+    dec()
+    torch.cuda.synchronize()
+    dec_ms = _events(torch, dec, 10)
+    ok = (not dec.status.any()) and torch.equal(dec.out_arena, sym)
+    total, msg_total = int(sizes.sum()), int(msg_sizes.sum())
+    dm = statistics.median(dec_ms)
+    achieved = (msg_total + total) / (dm * 1e-3) / 1e9
+    return {"workload": f"{count} streams x {per} binary symbols (u8 in {{0,1}}), per-stream "
+                        f"p0 ~ U[{cfg['p0_lo']}, {cfg['p0_hi']}]",
+            "decode_gbs": total / (dm * 1e-3) / 1e9, "decode_ms": dm,
+            "encode_gbs": total / (statistics.median(enc_ms) * 1e-3) / 1e9,
+            "compression_ratio": msg_total / total, "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "batch_decode_kernel", "bound": "hbm", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
+            "layout": {"n_lanes": 32, "chunk": best["chunk"], "policy": best["policy"]}}
+
+
+def single_leg(rans, dev, args):
+    """One 1 MiB stream, Zipf(1.2) over 256 symbols, 32 coders in one chunk:
+    a single warp's chain of 32768 dependent steps, so a latency figure."""
+    import torch
+
+    cfg = wl.WORKLOADS["single"]
+    n, N, CS = cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    freq = rans.rans_quantize_table(wl.weights_from_probs(p))
+    sym = torch.from_numpy(wl.iid_symbols(wl.rng_for("single"), p, n)).to(dev)
+    msg, _, _ = rans.encode(sym, freq, N, CS)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    scap = rans.rans_encode_scratch_size(n, N, CS)
+    ebuf = torch.empty(cap, dtype=torch.uint8, device=dev)
+    escr = torch.empty(scap, dtype=torch.uint8, device=dev)
+    esz = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode(msg, msg.numel(), freq, N, CS, out, n, st)  # noqa: E731
+    enc = lambda: rans.rans_encode(sym, n, freq, N, CS, ebuf, cap, esz, est, escr, scap)  # noqa: E731
+    dec()
+    enc()
+    torch.cuda.synchronize()
+    d_ms = statistics.median(_events(torch, dec, 20))
+    e_ms = statistics.median(_events(torch, enc, 20))
+    ok = int(st.item()) == 0 and torch.equal(out, sym)
+    return {"workload": "1 MiB, Zipf(1.2) over 256, one stream of 32 interleaved coders",
+            "decode_us": d_ms * 1e3, "encode_us": e_ms * 1e3,
+            "decode_gbs": n / (d_ms * 1e-3) / 1e9, "encode_gbs": n / (e_ms * 1e-3) / 1e9,
+            "bit_exact_roundtrip": bool(ok)}
+
+
+# ---------------------------------------------------------------------------
 # Serving leg: Poisson arrivals through the continuous-batching server
 # ---------------------------------------------------------------------------
 
@@ -565,6 +655,11 @@ def main(argv=None):
     if "batched" in legs:
         extra["batched"] = batched_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
+    if "binary" in legs:
+        extra["binary"] = binary_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
+    if "single" in legs:
+        extra["single"] = single_leg(rans, dev, args)
     if "serving" in legs:
         extra["serving"] = serving_leg(rans, dev, args)
         torch.cuda.empty_cache()

@@ -52,7 +52,7 @@ def _time(fn, reps):
 
 
 def autotune(sym_arena, sym_offsets, n_symbols, tables_dev, table, widths=WIDTHS,
-             chunks=CHUNKS, policies=POLICIES, reps=3):
+             chunks=CHUNKS, policies=POLICIES, reps=3):  # noqa: D401
     """Return (best, results): best = dict(n_lanes, chunk, policy); results =
     list of dicts with the measured decode GB/s of every candidate."""
     import torch
