@@ -170,7 +170,7 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
 // slot_base[0, slot_bytes).  Writes the chunk's first-word offset *wstart,
 // byte size *size and final states states[0..N).  acc collects the table
 // words of every symbol coded (kZeroFlag marks a symbol without probability).
-template <int NT>
+template <int NT, bool PREFETCH>  // PREFETCH: load the next group's symbols while coding this one
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
@@ -217,15 +217,36 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
         encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
     }
-    // Groups of kGroup steps; a group's symbols are loaded together up front.
-    for (; t >= 0; t -= kGroup) {
-        uint32_t cur[kGroup];
+    if (PREFETCH) {
+        // Groups of kGroup steps, symbols of the next group loaded ahead.
+        uint32_t cur[kGroup], nxt[kGroup];
+        if (t >= 0) {
 #pragma unroll
-        for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
-        service();
+            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+        }
+        for (; t >= 0; t -= kGroup) {
+            const int64_t tn = t - int64_t(kGroup);
 #pragma unroll
-        for (uint32_t u = 0; u < kGroup; ++u)
-            encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+            for (uint32_t u = 0; u < kGroup; ++u)
+                nxt[u] = (tn >= 0 && lane_on) ? symp[uint64_t(tn - u) * N] : 0u;
+            service();
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u)
+                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
+        }
+    } else {
+        // Groups of kGroup steps; a group's symbols are loaded together up front.
+        for (; t >= 0; t -= kGroup) {
+            uint32_t cur[kGroup];
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+            service();
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u)
+                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+        }
     }
 
     // Store what is left: complete segments, then the partial one rounded

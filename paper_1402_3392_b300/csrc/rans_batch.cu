@@ -378,10 +378,10 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             uint32_t *sizes = reinterpret_cast<uint32_t *>(scr + g.sl.sizes) + c;
             uint32_t *states = reinterpret_cast<uint32_t *>(scr + g.sl.states) + uint64_t(c) * d.n_lanes;
             if (d.n_lanes == 32)
-                enc::encode_chunk<32>(d.symbols + first, n_c, 32, slot, g.sl.slot_bytes, wstart, sizes,
+                enc::encode_chunk<32, false>(d.symbols + first, n_c, 32, slot, g.sl.slot_bytes, wstart, sizes,
                                       states, sm.tab_s, ring_s, ge, lane, acc);
             else
-                enc::encode_chunk<0>(d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart,
+                enc::encode_chunk<0, false>(d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart,
                                      sizes, states, sm.tab_s, ring_s, ge, lane, acc);
             if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0)
                 report(p.status + s, RANS_ERR_ZERO_FREQ);

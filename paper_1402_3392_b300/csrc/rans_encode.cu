@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(enc::kThreads)
     for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        enc::encode_chunk<NT>(p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes,
+        enc::encode_chunk<NT, true>(p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes,
                               p.slot_bytes, p.wstart + c, p.sizes + c,
                               p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane, acc);
     }
