@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 from paper_1402_3392_b300 import workloads as wl  # noqa: E402
 
 DECODE_SOURCES = [os.path.join(ROOT, "paper_1402_3392_b300", "csrc", f)
-                  for f in ("rans_decode.cu", "device_util.cuh")]
+                  for f in ("rans_decode.cu", "decode_core.cuh", "device_util.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "decode_kernel_chunked.md")
 
 

@@ -1,19 +1,20 @@
 // decode_core.cuh -- the decoder's building blocks, shared by the single-message
 // kernel (rans_decode.cu) and the batched persistent kernel (rans_batch.cu).
 //
-// One warp decodes one chunk; lane j is coder j of the chunk's N interleaved
-// rANS coders.  Per step every lane decodes one symbol (Algorithm 1 Decode,
-// Section 2):
+// One warp decodes two chunks side by side; lane j is coder j of each
+// chunk's N interleaved rANS coders.  Per step every lane decodes one symbol
+// of each chunk (Algorithm 1 Decode, Section 2):
 //     slot = x mod M;  (s, f_s, slot - B_s) from a slot table in shared memory
 //     x    = f_s * floor(x / M) + slot - B_s
 // and then renormalizes at most once (b = 2^16 >= M, Section 5): the lanes
 // with x < L form renorm_mask = ballot(x < L); a lane reads the word at
 // read_pos + popc(renorm_mask & lanes_below_me) and read_pos advances by
-// popc(renorm_mask) -- the packed load of Section 6.
+// popc(renorm_mask) -- the packed load of Section 6.  The two chunks' state
+// chains are independent, so their steps overlap in one instruction stream.
 //
-// Compressed words stream into a per-warp shared-memory ring through 512-byte
-// bulk copies (TMA, cp.async.bulk) completed on mbarriers; decoded bytes go
-// out as one coalesced 32-byte store per warp and step.
+// Each chunk's compressed words stream into its own shared-memory ring
+// through 512-byte bulk copies (TMA, cp.async.bulk) completed on mbarriers;
+// decoded bytes go out as one coalesced 32-byte store per chunk and step.
 #pragma once
 
 #include <cstdint>
@@ -24,27 +25,31 @@
 namespace rans {
 namespace dec {
 
-constexpr int kWarps = 8;                 // warps (chunks in flight) per CTA
+constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint32_t kThreads = kWarps * 32;
+constexpr uint32_t kChains = 2;           // chunks a warp decodes side by side
+constexpr uint32_t kChunksPerCta = kWarps * kChains;
 constexpr uint32_t kSeg = 512;            // bytes per bulk copy
-constexpr uint32_t kNSeg = 8;             // ring segments per warp
-constexpr uint32_t kRing = kSeg * kNSeg;  // 4 KiB per warp, aligned to 4 KiB in shared space
-constexpr uint32_t kGroup = 16;           // steps between ring checks
-// A step reads at most 32 words = 64 bytes, so a group reads at most 1 KiB:
-// two segments, while the ring holds eight.
-static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
+constexpr uint32_t kNSeg = 4;             // ring segments per chunk
+constexpr uint32_t kRing = kSeg * kNSeg;  // 2 KiB per chunk, aligned to 2 KiB in shared space
+constexpr uint32_t kGroup = 8;            // steps between ring checks
+// A step reads at most 32 words = 64 bytes.  A group's bytes [rp, rp + 512)
+// touch at most two segments, so with four in the ring at least two more
+// are in flight ahead of the group.
+constexpr uint32_t kGroupBytes = kGroup * 64;
+static_assert(kGroupBytes <= (kNSeg - 3) * kSeg, "a group must leave two segments of look-ahead");
 constexpr uint32_t kTableBytes = kM * 4;
-// Shared memory: [slot table 16 KiB][alignment slack 4 KiB][one ring per
-// warp][mbarriers][a few words of CTA state].
-constexpr uint32_t kBarOffset = kTableBytes + kRing + kWarps * kRing;
-constexpr uint32_t kMiscOffset = kBarOffset + kWarps * kNSeg * 8;
+// Shared memory: [slot table 16 KiB][alignment slack 2 KiB][one ring per
+// chunk in flight][mbarriers][a few words of CTA state].
+constexpr uint32_t kBarOffset = kTableBytes + kRing + kChunksPerCta * kRing;
+constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
 constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 
 struct Smem {
     uint32_t *tab;
     uint32_t tab_s;
-    uint32_t rings_s;   // 4 KiB aligned
+    uint32_t rings_s;   // kRing aligned
     uint8_t *rings;     // generic pointer of rings_s
     uint64_t *bars;
     uint32_t *misc;     // CTA-shared words
@@ -166,32 +171,139 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
     return total;
 }
 
-// Per-warp ring state, carried across the chunks a warp decodes.
-struct WarpRing {
-    uint32_t ring_s;    // this warp's ring (4 KiB aligned shared address)
+// Ring of one chain (one of the warp's two chunks in flight), carried across
+// the chunks the warp decodes.
+struct ChainRing {
+    uint32_t ring_s;    // kRing-aligned shared address
     uint32_t bar0;      // its kNSeg mbarriers
     uint32_t phase;     // bit i: parity of the next wait on barrier i
+};
+
+struct WarpRings {
+    ChainRing r[kChains];
     uint32_t timeouts;  // warp-uniform: a bounded wait gave up
 };
 
-__device__ __forceinline__ WarpRing ring_init(const Smem &sm, uint32_t warp, uint32_t lane) {
-    WarpRing r;
-    r.ring_s = sm.rings_s + warp * kRing;
-    r.bar0 = smem_addr(sm.bars + warp * kNSeg);
-    r.phase = 0;
-    r.timeouts = 0;
+__device__ __forceinline__ WarpRings rings_init(const Smem &sm, uint32_t warp, uint32_t lane) {
+    WarpRings w;
+#pragma unroll
+    for (uint32_t k = 0; k < kChains; ++k) {
+        const uint32_t i = warp * kChains + k;
+        w.r[k].ring_s = sm.rings_s + i * kRing;
+        w.r[k].bar0 = smem_addr(sm.bars + i * kNSeg);
+        w.r[k].phase = 0;
+    }
+    w.timeouts = 0;
     if (lane == 0) {
-        for (uint32_t i = 0; i < kNSeg; ++i) mbar_init(r.bar0 + 8 * i, 1);
+        for (uint32_t i = 0; i < kChains * kNSeg; ++i)
+            mbar_init(smem_addr(sm.bars + warp * kChains * kNSeg + i), 1);
         fence_mbar_init();
     }
     __syncwarp();
-    return r;
+    return w;
+}
+
+// Decoding state of one chunk.  Byte positions in its word stream are taken
+// relative to A, the 16-byte aligned message offset at or below the first
+// word; stream byte P then lives at ring offset P mod kRing.
+struct Chain {
+    const uint8_t *src;  // message + A: source of segment 0
+    uint8_t *outp;       // where this lane's next symbol goes
+    uint32_t x;          // this lane's coder state
+    uint32_t rp;         // read position (warp-uniform)
+    uint32_t issued;     // segments whose copy has been issued
+    uint32_t ready;      // segments known to be in the ring
+    uint32_t recheck;    // rp at which service() has work again
+    uint32_t nseg;       // segments of the chunk
+    uint32_t span;       // bytes copied in all (a multiple of 16)
+    uint32_t endrel;     // end of the chunk's words
+    uint32_t steps;      // full steps (all N coders) left
+    uint32_t rem;        // coders with a symbol in the final partial step
+    uint32_t st;         // RANS_OK, or the error found when opening
+};
+
+__device__ __forceinline__ void chain_empty(Chain &c) {
+    c.src = nullptr;
+    c.outp = nullptr;
+    c.x = kL;
+    c.rp = c.issued = c.ready = c.nseg = c.span = c.endrel = c.steps = c.rem = 0;
+    c.recheck = 0xFFFFFFFFu;
+    c.st = RANS_OK;
+}
+
+// Open chunk [o, e) (byte offsets in the data region that starts at msg +
+// data0; data_end = end of all chunks) of n_c symbols with N coders, output
+// at out.  Reads the N initial states; a malformed chunk gets c.st set and no
+// steps.
+__device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
+                                           uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,
+                                           uint8_t *out, uint32_t lane) {
+    chain_empty(c);
+    // Offsets must be even (states and words are 2-byte aligned) and in range.
+    if (((o | e) & 1u) || e < o || e > data_end || e - o < 4 * N || e - o > 0xFFFFFF00u) {
+        c.st = RANS_ERR_CORRUPT;
+        return;
+    }
+    const uint8_t *chunk = msg + data0 + o;
+    uint32_t x = kL;
+    if (lane < N) x = ld_u16_global(chunk + 4 * lane) | (ld_u16_global(chunk + 4 * lane + 2) << 16);
+    if (!__all_sync(kFull, x >= kL)) {  // Algorithm 1 requires x in I
+        c.st = RANS_ERR_CORRUPT;
+        return;
+    }
+    const uint64_t P0 = uint64_t(data0) + o + 4 * N, P1 = uint64_t(data0) + e;
+    const uint64_t A = P0 & ~uint64_t(15);
+    c.x = x;
+    c.src = msg + A;
+    c.span = uint32_t(round16(P1) - A);
+    c.nseg = (c.span + kSeg - 1) / kSeg;
+    c.endrel = uint32_t(P1 - A);
+    c.rp = uint32_t(P0 - A);
+    c.recheck = 0;
+    c.outp = out + lane;
+    c.steps = n_c / N;
+    c.rem = n_c % N;
+}
+
+// Bounded wait for segment c.ready, then mark it ready.
+__device__ __forceinline__ void chain_wait_next(Chain &c, ChainRing &r, uint32_t &timeouts) {
+    const uint32_t slot = c.ready % kNSeg;
+    const bool ok = timeouts != 0 || mbar_wait_bounded(r.bar0 + 8 * slot, (r.phase >> slot) & 1u);
+    if (__any_sync(kFull, !ok)) timeouts = 1;  // warp-uniform
+    r.phase ^= 1u << slot;
+    ++c.ready;
+}
+
+// Issue every segment whose ring slot is free (its previous segment lies
+// wholly below rp), wait until the next group's bytes [rp, rp + kGroupBytes)
+// are in, and compute the read position at which either can change again.
+__device__ __forceinline__ void chain_service(Chain &c, ChainRing &r, uint32_t &timeouts,
+                                              uint32_t lane) {
+    const uint32_t limit = min(c.nseg, kNSeg + c.rp / kSeg);
+    for (; c.issued < limit; ++c.issued) {
+        if (lane == 0) {
+            const uint32_t slot = c.issued % kNSeg;
+            const uint32_t off = c.issued * kSeg;
+            const uint32_t bytes = min(kSeg, c.span - off);
+            mbar_arrive_expect_tx(r.bar0 + 8 * slot, bytes);
+            bulk_g2s(r.ring_s + slot * kSeg, c.src + off, bytes, r.bar0 + 8 * slot);
+        }
+    }
+    const uint32_t need = min(c.nseg, (c.rp + kGroupBytes + kSeg - 1) / kSeg);
+    while (c.ready < need) chain_wait_next(c, r, timeouts);
+    const uint32_t r_ready =
+        c.ready >= c.nseg ? 0xFFFFFFFFu
+                          : (c.ready * kSeg >= kGroupBytes ? c.ready * kSeg - kGroupBytes + 1 : 0u);
+    const uint32_t r_issue = c.issued >= c.nseg
+                                 ? 0xFFFFFFFFu
+                                 : (c.issued + 1 >= kNSeg ? (c.issued + 1 - kNSeg) * kSeg : 0u);
+    c.recheck = min(r_ready, r_issue);
 }
 
 // Decode one step of a chunk: every active lane decodes one symbol and reads
 // at most one word.  FULL: every lane of the warp is a coder with a symbol in
 // this step.  rp is the byte position in the word stream (warp-uniform);
-// ring_s is the warp's 4 KiB-aligned ring, so (offset & 4095) | ring_s
+// ring_s is the chunk's kRing-aligned ring, so (offset & (kRing - 1)) | ring_s
 // addresses it.
 template <bool FULL>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
@@ -209,105 +321,136 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
     rp += 2u * __popc(m);
 }
 
-// Decode chunk [o, e) (byte offsets in the data region that starts at msg +
-// data0; data_end = end of all chunks) of n_c symbols with N coders into out.
-// const_sym != kNoConst: the model has one symbol with f = M.  Returns the
-// warp-uniform status (RANS_OK, RANS_ERR_CORRUPT or RANS_ERR_TIMEOUT).
-template <int NT>  // NT = 32: all 32 lanes are coders; NT = 0: runtime N
-__device__ __forceinline__ uint32_t decode_chunk(WarpRing &wr, uint32_t tab_s, const uint8_t *msg,
-                                                 uint32_t data0, uint32_t o, uint32_t e,
-                                                 uint32_t data_end, uint32_t n_c, uint32_t N_rt,
-                                                 uint8_t *out, uint32_t const_sym,
-                                                 uint32_t lane, uint32_t lt) {
-    const uint32_t N = NT ? NT : N_rt;
-    // Offsets must be even (states and words are 2-byte aligned) and in range.
-    if (((o | e) & 1u) || e < o || e > data_end || e - o < 4 * N) return RANS_ERR_CORRUPT;
+// One step of two chunks a and b, their instructions interleaved.
+template <bool FULL>
+__device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32_t ra_s, uint8_t *oa,
+                                             uint32_t &xb, uint32_t &rpb, uint32_t rb_s, uint8_t *ob,
+                                             bool active, uint32_t tab_s, uint32_t lt) {
+    const uint32_t ea = ld_table(tab_s + ((xa & (kM - 1)) << 2));
+    const uint32_t eb = ld_table(tab_s + ((xb & (kM - 1)) << 2));
+    if (FULL || active) {
+        xa = decode_update(xa, ea);
+        xb = decode_update(xb, eb);
+        *oa = uint8_t(ea);
+        *ob = uint8_t(eb);
+    }
+    const bool na = (FULL || active) && xa < kL;
+    const bool nb = (FULL || active) && xb < kL;
+    const uint32_t ma = __ballot_sync(kFull, na);
+    const uint32_t mb = __ballot_sync(kFull, nb);
+    const uint32_t wa = ld_ring_u16(((rpa + 2u * __popc(ma & lt)) & (kRing - 1)) | ra_s);
+    const uint32_t wb = ld_ring_u16(((rpb + 2u * __popc(mb & lt)) & (kRing - 1)) | rb_s);
+    if (na) xa = __byte_perm(xa, wa, 0x1054u);
+    if (nb) xb = __byte_perm(xb, wb, 0x1054u);
+    rpa += 2u * __popc(ma);
+    rpb += 2u * __popc(mb);
+}
+
+// Decode what is left of one chunk on its own.
+template <bool FULL>
+__device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &timeouts, uint32_t N,
+                                          bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt) {
+    for (; c.steps >= kGroup; c.steps -= kGroup) {
+        if (c.rp >= c.recheck) chain_service(c, r, timeouts, lane);
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u)
+            decode_step<FULL>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N, lt);
+        c.outp += kGroup * N;
+    }
+    for (; c.steps > 0; --c.steps) {
+        chain_service(c, r, timeouts, lane);
+        decode_step<FULL>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
+        c.outp += N;
+    }
+    if (c.rem) {
+        chain_service(c, r, timeouts, lane);
+        decode_step<false>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
+        c.rem = 0;
+    }
+}
+
+// Drain the copies still in flight, so that the ring and the barrier phases
+// are clean for the next chunk, and check the chunk's end: a well-formed
+// chunk ends with every coder back at x0 = L and every word read exactly once
+// (decoder and encoder in lockstep, Section 3).
+__device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t &timeouts,
+                                                bool lane_on) {
+    while (c.ready < c.issued) chain_wait_next(c, r, timeouts);
+    if (c.st != RANS_OK) return c.st;
+    if (timeouts) return RANS_ERR_TIMEOUT;
+    const bool ok = __all_sync(kFull, !lane_on || c.x == kL) && c.rp == c.endrel;
+    return ok ? RANS_OK : RANS_ERR_CORRUPT;
+}
+
+// A model with one symbol s of frequency M: C is the identity, so a
+// well-formed chunk is N states equal to L and no words.
+__device__ __forceinline__ uint32_t const_chunk(const uint8_t *msg, uint32_t data0, uint32_t o,
+                                                uint32_t e, uint32_t data_end, uint32_t n_c,
+                                                uint32_t N, uint8_t *out, uint32_t const_sym,
+                                                uint32_t lane) {
+    if (((o | e) & 1u) || e < o || e > data_end || e - o != 4 * N) return RANS_ERR_CORRUPT;
     const uint8_t *chunk = msg + data0 + o;
     uint32_t x = kL;
     if (lane < N) x = ld_u16_global(chunk + 4 * lane) | (ld_u16_global(chunk + 4 * lane + 2) << 16);
-    if (!__all_sync(kFull, x >= kL)) return RANS_ERR_CORRUPT;  // Algorithm 1 requires x in I
-    uint8_t *outp = out + lane;
+    for (uint32_t i = lane; i < n_c; i += 32) out[i] = uint8_t(const_sym);
+    return __all_sync(kFull, x == kL) ? RANS_OK : RANS_ERR_CORRUPT;
+}
+
+// Decode chunks c and, when count == 2, c + 1 of a message (offsets table
+// offs, data region at msg + data0, data_end = offs[n_chunks]) of n_sym
+// symbols in chunks of CS with N coders; chunk k's symbols go to out + k*CS.
+// const_sym != kNoConst: the model has one symbol with f = M.  Returns the
+// warp-uniform status (RANS_OK, or the first of RANS_ERR_CORRUPT /
+// RANS_ERR_TIMEOUT found in the two chunks).
+template <int NT>  // NT = 32: all 32 lanes are coders; NT = 0: runtime N
+__device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
+                                                  uint32_t data0, const uint32_t *offs,
+                                                  uint32_t data_end, uint32_t c, uint32_t count,
+                                                  uint64_t n_sym, uint32_t CS, uint32_t N_rt,
+                                                  uint8_t *out, uint32_t const_sym, uint32_t lane,
+                                                  uint32_t lt) {
+    constexpr bool kFullWarp = NT == 32;
+    const uint32_t N = NT ? NT : N_rt;
+    const bool lane_on = lane < N;
+    const uint64_t first = uint64_t(c) * CS;
+    const uint32_t n_a = uint32_t(umin64(CS, n_sym - first));
+    const uint32_t n_b = count > 1 ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
+    const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = count > 1 ? offs[c + 2] : 0u;
 
     if (const_sym != kNoConst) {
-        // f = M: C is the identity; the chunk is N states equal to L.
-        for (uint32_t i = lane; i < n_c; i += 32) out[i] = uint8_t(const_sym);
-        return (e - o == 4 * N && __all_sync(kFull, x == kL)) ? RANS_OK : RANS_ERR_CORRUPT;
+        uint32_t st = const_chunk(msg, data0, o0, o1, data_end, n_a, N, out + first, const_sym, lane);
+        if (count > 1) {
+            const uint32_t sb =
+                const_chunk(msg, data0, o1, o2, data_end, n_b, N, out + first + CS, const_sym, lane);
+            if (st == RANS_OK) st = sb;
+        }
+        return st;
     }
 
-    // Word stream: bytes [P0, P1) of the message, loaded in 512-byte segments
-    // starting at the 16-byte aligned A <= P0; stream byte P lives at ring
-    // offset (P - A) mod 4096.
-    const uint64_t P0 = uint64_t(data0) + o + 4 * N, P1 = uint64_t(data0) + e;
-    const uint64_t A = P0 & ~uint64_t(15);
-    const uint64_t end16 = round16(P1);
-    const uint32_t nseg = uint32_t((end16 - A + kSeg - 1) / kSeg);
-    const uint32_t endrel = uint32_t(P1 - A);
-    uint32_t rp = uint32_t(P0 - A);
-    uint32_t issued = 0, ready = 0, recheck = 0;
+    Chain a, b;
+    chain_open(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
+    if (count > 1) chain_open(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, lane);
+    else chain_empty(b);
 
-    // Issue every segment whose ring slot is free (its previous segment lies
-    // wholly below rp), wait until the next group's bytes [rp, rp + 1 KiB)
-    // are in, and compute the read position at which either can change again.
-    auto service = [&]() {
-        const uint32_t limit = min(nseg, kNSeg + rp / kSeg);
-        for (; issued < limit; ++issued) {
-            if (lane == 0) {
-                const uint32_t slot = issued % kNSeg;
-                const uint64_t src = A + uint64_t(issued) * kSeg;
-                const uint32_t bytes = uint32_t(umin64(kSeg, end16 - src));
-                mbar_arrive_expect_tx(wr.bar0 + 8 * slot, bytes);
-                bulk_g2s(wr.ring_s + slot * kSeg, msg + src, bytes, wr.bar0 + 8 * slot);
-            }
-        }
-        const uint32_t need = min(nseg, (rp + kGroup * 64 + kSeg - 1) / kSeg);
-        for (; ready < need; ++ready) {
-            const uint32_t slot = ready % kNSeg;
-            const bool ok =
-                wr.timeouts != 0 || mbar_wait_bounded(wr.bar0 + 8 * slot, (wr.phase >> slot) & 1u);
-            if (__any_sync(kFull, !ok)) wr.timeouts = 1;  // warp-uniform
-            wr.phase ^= 1u << slot;
-        }
-        const uint32_t r_ready =
-            ready >= nseg ? 0xFFFFFFFFu
-                          : (ready * kSeg >= kGroup * 64 ? ready * kSeg - kGroup * 64 + 1 : 0u);
-        const uint32_t r_issue =
-            issued >= nseg ? 0xFFFFFFFFu : (issued + 1 >= kNSeg ? (issued + 1 - kNSeg) * kSeg : 0u);
-        recheck = min(r_ready, r_issue);
-    };
-
-    const uint32_t T_full = n_c / N, rem = n_c % N;
-    const bool lane_on = lane < N;
-    uint32_t t = 0;
-    for (; t + kGroup <= T_full; t += kGroup) {
-        if (rp >= recheck) service();
+    // Both chunks step together while each has a full group left.
+    uint32_t groups = min(a.steps, b.steps) / kGroup;
+    a.steps -= groups * kGroup;
+    b.steps -= groups * kGroup;
+    for (; groups > 0; --groups) {
+        if (a.rp >= a.recheck) chain_service(a, w.r[0], w.timeouts, lane);
+        if (b.rp >= b.recheck) chain_service(b, w.r[1], w.timeouts, lane);
 #pragma unroll
         for (uint32_t u = 0; u < kGroup; ++u)
-            decode_step<NT == 32>(x, rp, lane_on, tab_s, wr.ring_s, outp + u * N, lt);
-        outp += kGroup * N;
+            decode_step2<kFullWarp>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x, b.rp,
+                                    w.r[1].ring_s, b.outp + u * N, lane_on, tab_s, lt);
+        a.outp += kGroup * N;
+        b.outp += kGroup * N;
     }
-    for (; t < T_full; ++t) {
-        service();
-        decode_step<NT == 32>(x, rp, lane_on, tab_s, wr.ring_s, outp, lt);
-        outp += N;
-    }
-    if (rem) {
-        service();
-        decode_step<false>(x, rp, lane < rem, tab_s, wr.ring_s, outp, lt);
-    }
-    // Drain the copies still in flight so that the ring and the barrier
-    // phases are clean for the next chunk.
-    for (; ready < issued; ++ready) {
-        const uint32_t slot = ready % kNSeg;
-        const bool ok =
-            wr.timeouts != 0 || mbar_wait_bounded(wr.bar0 + 8 * slot, (wr.phase >> slot) & 1u);
-        if (__any_sync(kFull, !ok)) wr.timeouts = 1;
-        wr.phase ^= 1u << slot;
-    }
-    if (wr.timeouts) return RANS_ERR_TIMEOUT;
-    // A well-formed chunk ends with every coder back at x0 = L and every word
-    // read exactly once (decoder and encoder in lockstep, Section 3).
-    const bool ok = __all_sync(kFull, !lane_on || x == kL) && rp == endrel;
-    return ok ? RANS_OK : RANS_ERR_CORRUPT;
+    chain_run<kFullWarp>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt);
+    chain_run<kFullWarp>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
+    const uint32_t sa = chain_close(a, w.r[0], w.timeouts, lane_on);
+    const uint32_t sb = count > 1 ? chain_close(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
+    return sa != RANS_OK ? sa : sb;
 }
 
 // Header check of a message of n_sym symbols in chunks of CS with N coders;

@@ -3,11 +3,11 @@
 //
 // The work list is built on the device: a setup kernel validates every
 // descriptor and writes the exclusive prefix of work items per stream (one
-// item = up to dec::kWarps chunks of one stream).  The persistent decode
+// item = up to dec::kChunksPerCta chunks of one stream).  The persistent decode
 // kernel's CTAs take items from an atomic counter; an item's stream is found
 // by binary search in the prefix; its model's slot table is rebuilt in shared
 // memory only when the model changes; each warp decodes one chunk with the
-// same per-chunk code as the single-message decoder.
+// same code as the single-message decoder (two chunks per warp).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kSetupThreads)
             const StreamGeom g = check_stream(p.streams[i], p.n_tables);
             p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
             if (g.ok) {
-                const uint64_t k = (g.n_chunks + dec::kWarps - 1) / dec::kWarps;
+                const uint64_t k = (g.n_chunks + dec::kChunksPerCta - 1) / dec::kChunksPerCta;
                 items = k > 0 ? uint32_t(k) : 1u;  // an empty stream still has its header checked
             }
         }
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     uint32_t &model_ok = sm.misc[4];
     uint32_t &hdr_ok = sm.misc[5];
     if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
-    dec::WarpRing wr = dec::ring_init(sm, warp, lane);
+    dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t lt = lanemask_lt();
     const uint32_t total = p.prefix[p.n_streams];
 
@@ -173,20 +173,20 @@ __global__ void __launch_bounds__(dec::kThreads)
             continue;
         }
         const StreamGeom g = check_stream(d, p.n_tables);
-        const uint32_t c = (it - p.prefix[s]) * dec::kWarps + warp;
+        const uint32_t c = (it - p.prefix[s]) * dec::kChunksPerCta + dec::kChains * warp;
         if (c < g.n_chunks && !wr.timeouts) {
             const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
-            const uint64_t first = uint64_t(c) * d.chunk_symbols;
-            const uint32_t n_c = uint32_t(umin64(d.chunk_symbols, d.n_symbols - first));
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
+            const uint32_t count = uint32_t(umin64(dec::kChains, g.n_chunks - c));
             const uint32_t st =
                 d.n_lanes == 32
-                    ? dec::decode_chunk<32>(wr, sm.tab_s, d.msg, g.data0, offs[c], offs[c + 1],
-                                            data_end, n_c, 32, d.symbols + first, cs, lane, lt)
-                    : dec::decode_chunk<0>(wr, sm.tab_s, d.msg, g.data0, offs[c], offs[c + 1],
-                                           data_end, n_c, d.n_lanes, d.symbols + first, cs, lane,
-                                           lt);
+                    ? dec::decode_chunks<32>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                                             d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane,
+                                             lt)
+                    : dec::decode_chunks<0>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                                            d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs,
+                                            lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);
         }
     }

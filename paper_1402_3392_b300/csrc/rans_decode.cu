@@ -1,4 +1,5 @@
-// rans_decode.cu -- single-message GPU decoder: one warp per chunk, the
+// rans_decode.cu -- single-message GPU decoder: one warp per chunk or per
+// pair of consecutive chunks (chosen per launch from the chunk count), each
 // chunk's N interleaved coders on the warp's lanes (decode_core.cuh), one
 // slot table per CTA built from the message's model.
 #include <algorithm>
@@ -24,6 +25,7 @@ struct DecodeParams {
     uint32_t CS;
     uint32_t n_chunks;
     uint32_t data0;
+    uint32_t per_warp;  // chunks a warp decodes side by side: 1 or dec::kChains
     uint16_t freq[RANS_MAX_ALPHABET];
 };
 
@@ -45,24 +47,39 @@ __global__ void __launch_bounds__(dec::kThreads)
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
         return;
     }
-    dec::WarpRing wr = dec::ring_init(sm, warp, lane);
+    dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t cs = const_sym;
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(p.msg + 32);
     const uint32_t data_end = offs[p.n_chunks];
     const uint32_t lt = lanemask_lt();
+    const uint32_t per = p.per_warp;
+    const uint32_t n_units = (p.n_chunks + per - 1) / per;
 
-    for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
-        const uint64_t first = uint64_t(c) * p.CS;
-        const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        const uint32_t st = dec::decode_chunk<NT>(wr, sm.tab_s, p.msg, p.data0, offs[c], offs[c + 1],
-                                                  data_end, n_c, p.N, p.out + first, cs, lane, lt);
+    for (uint32_t q = blockIdx.x * kWarps + warp; q < n_units; q += gridDim.x * kWarps) {
+        const uint32_t c = q * per;
+        const uint32_t st = dec::decode_chunks<NT>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
+                                                   min(per, p.n_chunks - c), p.n_sym, p.CS, p.N,
+                                                   p.out, cs, lane, lt);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
 }
 
+// Chunks per warp for a message of n_chunks chunks when `warps` warps are
+// resident.  A chunk is one chain of dependent steps, so a launch lasts at
+// least one chunk's latency and its last wave leaves warps idle.  Two chains
+// per warp raise the step rate of a fully occupied SM by 7-12%, but halve
+// the chains in flight, which makes a partly filled last wave costlier.
+// Measured on a B300 (64 KiB chunks, N = 32; W = resident warps):
+//   n_chunks / W      0.4-1.0  1.3  1.7  2.0  2.6  3.0  3.5  4.3  5.2
+//   faster mode       one      two  two  two  two  one  one  two  two
+uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
+    const double w = double(n_chunks) / double(warps);
+    return (w > 1.0 && w <= 2.8) || w >= 4.0 ? dec::kChains : 1u;
+}
+
 template <int NT>
-int launch_decode(const DecodeParams &p, cudaStream_t stream) {
+int launch_decode(DecodeParams &p, cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -77,8 +94,9 @@ int launch_decode(const DecodeParams &p, cudaStream_t stream) {
                                                       kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
-    const uint64_t want = ceil_div(p.n_chunks, kWarps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
+    p.per_warp = chunks_per_warp(p.n_chunks, cap * kWarps);
+    const uint64_t want = ceil_div(p.n_chunks, uint64_t(kWarps) * p.per_warp);
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     decode_kernel<NT><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();

@@ -9,6 +9,7 @@ import zlib
 import numpy as np
 import pytest
 
+import oracle
 from paper_1402_3392_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -100,6 +101,36 @@ def test_long_chunk_many_segments(rlib, orc, cuda):
         msg, back = gpu_roundtrip(rlib, cuda, sym, freq, 32, 1 << 20)
         assert np.array_equal(msg, orc.encode_message(sym, freq, N=32, chunk_symbols=1 << 20))
         assert np.array_equal(back, sym)
+
+
+@pytest.mark.parametrize("n_chunks,N,CS", [(9473, 32, 64), (30001, 32, 48), (12001, 7, 61)])
+def test_more_chunks_than_resident_warps(rlib, orc, cuda, n_chunks, N, CS):
+    """Messages with thousands of short chunks, so that warps decode two
+    chunks side by side; odd chunk counts leave one warp a single chunk and
+    the last chunk is ragged.  A corrupt word in the first or the second
+    chunk of a pair is reported."""
+    import torch
+
+    rng = np.random.default_rng(n_chunks + N)
+    freq = model(rlib, "zipf256", rng)
+    n = (n_chunks - 1) * CS + CS // 2 + 1
+    sym = draw(rng, freq, n, "zipf256")
+    msg, back = gpu_roundtrip(rlib, cuda, sym, freq, N, CS)
+    ref = orc.encode_message(sym, freq, N=N, chunk_symbols=CS)
+    assert np.array_equal(msg, ref)
+    assert np.array_equal(back, sym)
+    offs = ref[32:32 + 4 * (n_chunks + 1)].view(np.uint32)
+    data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+    for c in (n_chunks // 2, n_chunks // 2 + 1):
+        bad = ref.copy()
+        last_word = data0 + int(offs[c + 1]) - 2
+        assert last_word >= data0 + int(offs[c]) + 4 * N   # the chunk has words
+        bad[last_word] ^= 0x01
+        with pytest.raises(oracle.OracleError):
+            orc.decode_message(bad, n, freq, N=N, chunk_symbols=CS)
+        _, status = rlib.decode(torch.from_numpy(bad).to(cuda), n, freq, N, CS, sync=False)
+        torch.cuda.synchronize()
+        assert int(status.item()) == rlib.RANS_ERR_CORRUPT, c
 
 
 def test_decodes_oracle_messages(rlib, orc, cuda):
