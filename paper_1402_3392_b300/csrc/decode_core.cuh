@@ -13,7 +13,7 @@
 // chains are independent, so their steps overlap in one instruction stream.
 //
 // Each chunk's compressed words stream into its own shared-memory ring
-// through 512-byte bulk copies (TMA, cp.async.bulk) completed on mbarriers;
+// through 1 KiB bulk copies (TMA, cp.async.bulk) completed on mbarriers;
 // decoded bytes go out as one coalesced 32-byte store per chunk and step.
 #pragma once
 
@@ -29,15 +29,19 @@ constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint32_t kThreads = kWarps * 32;
 constexpr uint32_t kChains = 2;           // chunks a warp decodes side by side
 constexpr uint32_t kChunksPerCta = kWarps * kChains;
-constexpr uint32_t kSeg = 512;            // bytes per bulk copy
-constexpr uint32_t kNSeg = 4;             // ring segments per chunk
+constexpr uint32_t kSeg = 1024;           // bytes per bulk copy
+constexpr uint32_t kNSeg = 2;             // ring segments per chunk
 constexpr uint32_t kRing = kSeg * kNSeg;  // 2 KiB per chunk, aligned to 2 KiB in shared space
 constexpr uint32_t kGroup = 8;            // steps between ring checks
-// A step reads at most 32 words = 64 bytes.  A group's bytes [rp, rp + 512)
-// touch at most two segments, so with four in the ring at least two more
-// are in flight ahead of the group.
+// A step reads at most 32 words = 64 bytes, a group at most kGroupBytes.
+// Before a group the segments holding [rp, rp + kGroupBytes) must be in;
+// segment i + kNSeg is issued once rp has left segment i.  So the copy of a
+// segment starts kRing - kSeg - kGroupBytes = 512 bytes of words (about 20
+// steps) before the first group that can read it.  Segments are large
+// because each one costs the warp a wait, a copy issue and bookkeeping.
 constexpr uint32_t kGroupBytes = kGroup * 64;
-static_assert(kGroupBytes <= (kNSeg - 3) * kSeg, "a group must leave two segments of look-ahead");
+static_assert(kGroupBytes <= (kNSeg - 1) * kSeg, "a group's segments must fit in the ring");
+static_assert(kRing - kSeg - kGroupBytes >= 512, "copies must start well ahead of use");
 constexpr uint32_t kTableBytes = kM * 4;
 // Shared memory: [slot table 16 KiB][alignment slack 2 KiB][one ring per
 // chunk in flight][mbarriers][a few words of CTA state].

@@ -68,14 +68,14 @@ __global__ void __launch_bounds__(dec::kThreads)
 // Chunks per warp for a message of n_chunks chunks when `warps` warps are
 // resident.  A chunk is one chain of dependent steps, so a launch lasts at
 // least one chunk's latency and its last wave leaves warps idle.  Two chains
-// per warp raise the step rate of a fully occupied SM by 7-12%, but halve
+// per warp raise the step rate of a fully occupied SM by 8-13%, but halve
 // the chains in flight, which makes a partly filled last wave costlier.
-// Measured on a B300 (64 KiB chunks, N = 32; W = resident warps):
-//   n_chunks / W      0.4-1.0  1.3  1.7  2.0  2.6  3.0  3.5  4.3  5.2
-//   faster mode       one      two  two  two  two  one  one  two  two
+// Measured on a B300 (64 KiB chunks, N = 32; w = n_chunks / resident warps):
+//   w            0.4-1.0  1.3  1.7  2.0  2.3  2.6  3.0  3.5  3.8  4.3  5.2
+//   faster mode  one      two  two  two  two  two  one  one  two  two  two
 uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
     const double w = double(n_chunks) / double(warps);
-    return (w > 1.0 && w <= 2.8) || w >= 4.0 ? dec::kChains : 1u;
+    return (w > 1.0 && w <= 2.8) || w >= 3.6 ? dec::kChains : 1u;
 }
 
 template <int NT>

@@ -92,7 +92,7 @@ def test_edge_sizes(rlib, orc, cuda, n, N, CS):
 
 
 def test_long_chunk_many_segments(rlib, orc, cuda):
-    """One chunk whose word stream spans hundreds of 512-byte ring segments,
+    """One chunk whose word stream spans hundreds of ring segments,
     for the least compressible (uniform) and a skewed model."""
     rng = np.random.default_rng(41)
     for kind in ("uniform256", "zipf256", "binary_extreme"):
