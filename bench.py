@@ -558,6 +558,31 @@ def serving_leg(rans, dev, args):
 # Our arm
 # ---------------------------------------------------------------------------
 
+def rank_seed(workload: str, rank: int) -> int:
+    """Seed of rank `rank`'s batch: every rank codes its own independent
+    batch of the workload (weak scaling, no data exchange)."""
+    return wl.seed_for(workload, rank)
+
+
+def max_over_ranks(values, device, world: int):
+    """Element-wise maximum of per-rank timings over all ranks (the job takes
+    as long as its slowest rank); the identity on one rank."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(world: int, n_symbols: int, decode_ms: float) -> float:
+    """Whole-job decoded GB/s: the symbols all ranks decoded over the
+    slowest rank's decode time."""
+    return world * n_symbols / (decode_ms * 1e-3) / 1e9
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -580,7 +605,7 @@ def main(argv=None):
     n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
     p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
     freq = rans.rans_quantize_table(wl.weights_from_probs(p))
-    sym = wl.iid_symbols_device(p, n, wl.seed_for(args.workload, rank), dev)
+    sym = wl.iid_symbols_device(p, n, rank_seed(args.workload, rank), dev)
 
     cap = rans.rans_max_encoded_size(n, N, CS)
     scap = rans.rans_encode_scratch_size(n, N, CS)
@@ -633,11 +658,8 @@ def main(argv=None):
     step_ms = evs[0][0].elapsed_time(evs[-1][2]) / args.steps
     ok = int(dec_status.item()) == 0 and torch.equal(dec, sym)
 
-    t = torch.tensor([statistics.mean(dec_ms), statistics.mean(enc_ms), step_ms, wall],
-                     dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dec_mean, enc_mean, step_mean, wall_max = t.tolist()
+    dec_mean, enc_mean, step_mean, wall_max = max_over_ranks(
+        [statistics.mean(dec_ms), statistics.mean(enc_ms), step_ms, wall], dev, world)
 
     e2e = None
     if not args.no_e2e:
@@ -669,7 +691,7 @@ def main(argv=None):
         alg_bytes = msg_size + n
         achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
         line = {
-            "metric": "decoded GB/s", "value": world * n / (dec_mean * 1e-3) / 1e9,
+            "metric": "decoded GB/s", "value": job_value(world, n, dec_mean),
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_mean, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
