@@ -345,6 +345,22 @@ int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_symbols,
                                uint64_t *d_out_size, uint32_t *d_status,
                                rans_stream_t stream);
 
+/*
+ * rans_check_bounded_wait -- diagnostic of the failure path; no step of the
+ * paper's method.  Launches one warp that waits, with the same bounded wait
+ * the coder kernels use for their bulk copies (at most 200 ms of
+ * %globaltimer), on a shared-memory mbarrier that nothing ever completes.
+ * The wait gives up, the kernel writes RANS_ERR_TIMEOUT to *d_status and
+ * returns, and the context stays usable: this is how a copy that never
+ * lands ends a coder kernel with a status instead of a hang.
+ *
+ * d_status : device u32, overwritten (RANS_ERR_TIMEOUT once the kernel ends).
+ * Returns RANS_OK when the kernel was enqueued, RANS_ERR_INVALID_ARG for a
+ * null d_status, RANS_ERR_CUDA on a launch error.  The kernel takes about
+ * 200 ms of GPU time.
+ */
+int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,8 +8,9 @@ size), so the choice is made before encoding.  Candidates:
                one warp lane, so N < 32 leaves lanes idle)
   chunk      : 16, 32, 64, 128, 256 KiB
   per-stream : "fixed" (every stream uses the chunk size) or "fill" (a stream
-               shorter than 8 chunks is cut into up to 8 smaller chunks, at
-               least 4 KiB each, so its one work item keeps all warps busy)
+               shorter than 16 chunks is cut into up to 16 smaller chunks, at
+               least 4 KiB each, so its one work item keeps all 16 chunk
+               slots of a CTA -- 8 warps x 2 chunks -- busy)
 The score is decoded bytes per second of the batched decoder (median of a few
 runs); ties go to the larger chunk.
 """
@@ -24,7 +25,7 @@ from . import batch as B
 WIDTHS = (4, 8, 16, 32)
 CHUNKS = (16 << 10, 32 << 10, 64 << 10, 128 << 10, 256 << 10)
 POLICIES = ("fixed", "fill")
-ITEM_CHUNKS = 8        # chunks in one work item of the batched kernels
+ITEM_CHUNKS = 16       # chunks in one work item of the batched decoder
 MIN_FILL_CHUNK = 4096
 
 

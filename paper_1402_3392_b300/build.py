@@ -20,7 +20,8 @@ LIB_DIR = os.path.join(PKG, "_lib")
 LIB_NAME = "libinterleaved_rans_b300.so"
 LIB_PATH = os.path.join(LIB_DIR, LIB_NAME)
 
-SOURCES = ["rans_host.cpp", "rans_decode.cu", "rans_encode.cu", "rans_batch.cu", "rans_server.cu"]
+SOURCES = ["rans_host.cpp", "rans_decode.cu", "rans_encode.cu", "rans_batch.cu", "rans_server.cu",
+           "rans_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,35 @@
+// rans_check.cu -- diagnostic of the coder kernels' failure path: a bounded
+// device-side wait that runs out ends the kernel with a status, not a hang.
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "host_util.h"
+
+namespace rans {
+namespace {
+
+// One warp waits on an mbarrier that no thread or copy ever completes, with
+// the coder kernels' bounded wait; the status records that it gave up.
+__global__ void __launch_bounds__(32) bounded_wait_kernel(uint32_t *status) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(b, 0);
+    const uint32_t st = __any_sync(kFull, !ok) ? RANS_ERR_TIMEOUT : RANS_OK;
+    if (threadIdx.x == 0) *status = st;
+}
+
+}  // namespace
+}  // namespace rans
+
+using namespace rans;
+
+extern "C" int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream) {
+    if (!d_status) return RANS_ERR_INVALID_ARG;
+    bounded_wait_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_status);
+    return check_launch();
+}

@@ -28,7 +28,7 @@ __all__ = [
     "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
     "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
-    "Server",
+    "Server", "rans_check_bounded_wait",
 ]
 
 RANS_OK = 0
@@ -91,6 +91,7 @@ def _load() -> C.CDLL:
         "rans_encode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
+        "rans_check_bounded_wait": (i32, [vp, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
         "rans_encode_batch_plan": (u64, [vp, u32]),
@@ -182,6 +183,13 @@ def rans_encode(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_c
                          _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
                          _ptr(d_scratch), int(scratch_cap), _stream(stream))
     return _check(rc, "rans_encode") if check else rc
+
+
+def rans_check_bounded_wait(d_status, stream=None, check=True) -> int:
+    """Diagnostic: a kernel whose bounded wait on a barrier that nothing
+    completes gives up after about 200 ms and writes RANS_ERR_TIMEOUT."""
+    rc = lib.rans_check_bounded_wait(_ptr(d_status), _stream(stream))
+    return _check(rc, "rans_check_bounded_wait") if check else rc
 
 
 def rans_encode_static_scratch(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out,
