@@ -1,23 +1,24 @@
 // decode_core.cuh -- the decoder's building blocks, shared by the single-message
 // kernel (rans_decode.cu) and the batched persistent kernel (rans_batch.cu).
 //
-// One warp decodes two chunks side by side; lane j is coder j of each
-// chunk's N interleaved rANS coders.  Per step every lane decodes one symbol
-// of each chunk (Algorithm 1 Decode, Section 2):
+// A warp decodes one chunk, or two chunks side by side; lane j is coder j of
+// each chunk's N interleaved rANS coders.  Per step every lane decodes one
+// symbol of each chunk (Algorithm 1 Decode, Section 2):
 //     slot = x mod M;  (s, f_s, slot - B_s) from a slot table in shared memory
 //     x    = f_s * floor(x / M) + slot - B_s
 // and then renormalizes at most once (b = 2^16 >= M, Section 5): the lanes
 // with x < L form renorm_mask = ballot(x < L); a lane reads the word at
 // read_pos + popc(renorm_mask & lanes_below_me) and read_pos advances by
-// popc(renorm_mask) -- the packed load of Section 6.  The two chunks' state
+// popc(renorm_mask) -- the packed load of Section 6.  Two chunks' state
 // chains are independent, so their steps overlap in one instruction stream.
 //
-// Each chunk's compressed words stream into its own shared-memory ring
-// through 1 KiB bulk copies (TMA, cp.async.bulk) completed on mbarriers;
-// decoded bytes go out as one coalesced 32-byte store per chunk and step.
+// Each chunk's compressed words stream into a shared-memory ring through
+// bulk copies (TMA, cp.async.bulk) completed on mbarriers; decoded bytes go
+// out as one coalesced 32-byte store per chunk and step.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "host_util.h"
@@ -29,23 +30,41 @@ constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint32_t kThreads = kWarps * 32;
 constexpr uint32_t kChains = 2;           // chunks a warp decodes side by side
 constexpr uint32_t kChunksPerCta = kWarps * kChains;
-constexpr uint32_t kSeg = 1024;           // bytes per bulk copy
-constexpr uint32_t kNSeg = 2;             // ring segments per chunk
-constexpr uint32_t kRing = kSeg * kNSeg;  // 2 KiB per chunk, aligned to 2 KiB in shared space
-constexpr uint32_t kGroup = 8;            // steps between ring checks
-// A step reads at most 32 words = 64 bytes, a group at most kGroupBytes.
-// Before a group the segments holding [rp, rp + kGroupBytes) must be in;
-// segment i + kNSeg is issued once rp has left segment i.  So the copy of a
-// segment starts kRing - kSeg - kGroupBytes = 512 bytes of words (about 20
-// steps) before the first group that can read it.  Segments are large
-// because each one costs the warp a wait, a copy issue and bookkeeping.
-constexpr uint32_t kGroupBytes = kGroup * 64;
-static_assert(kGroupBytes <= (kNSeg - 1) * kSeg, "a group's segments must fit in the ring");
-static_assert(kRing - kSeg - kGroupBytes >= 512, "copies must start well ahead of use");
+constexpr uint32_t kWarpRing = 4096;      // ring bytes per warp (4 KiB aligned)
+constexpr uint32_t kNSeg = 4;             // ring segments (and mbarriers) per chunk
+
+// Ring geometry of one chunk in flight: a ring of NSEG segments of SEG bytes,
+// checked every GROUP steps.  A step reads at most 32 words = 64 bytes, so a
+// group reads at most GROUP * 64 bytes.  Ring event k (due once the read
+// position rp reaches (k - NSEG + 1) * SEG) issues the copy of segment k into
+// the slot that segment k - NSEG has left, and waits for segment k - LAG.
+// After the events due at rp, the segments up to floor(rp / SEG) + NSEG - 1 -
+// LAG are in: enough for the next group when LAG <= NSEG - 1 - ceil(GROUP *
+// 64 / SEG).  A copy is waited for LAG segments (LAG * SEG bytes of words)
+// after it is issued.
+template <uint32_t SEG, uint32_t NSEG, uint32_t GROUP>
+struct Geometry {
+    static constexpr uint32_t kSeg = SEG;
+    static constexpr uint32_t kNSeg = NSEG;
+    static constexpr uint32_t kRing = SEG * NSEG;
+    static constexpr uint32_t kGroup = GROUP;
+    static constexpr uint32_t kLag = NSEG - 1 - (GROUP * 64 + SEG - 1) / SEG;
+    static_assert((kRing & (kRing - 1)) == 0, "the ring is indexed by masking");
+    static_assert(NSEG - 1 >= (GROUP * 64 + SEG - 1) / SEG + 1, "a copy must be issued ahead of use");
+    static_assert(NSEG <= 32, "one phase bit per segment");
+};
+// One chunk per warp: the warp's whole 4 KiB as one ring, 1 KiB copies,
+// waited 2 KiB after issue.  Two chunks per warp: 2 KiB each, 512-byte
+// copies, waited 512 bytes after issue.  Copies are large because each one
+// costs the warp an issue, a wait and bookkeeping.
+using GeoOne = Geometry<1024, kNSeg, 16>;
+using GeoPair = Geometry<512, kNSeg, 16>;
+static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing, "ring sizes");
+
 constexpr uint32_t kTableBytes = kM * 4;
-// Shared memory: [slot table 16 KiB][alignment slack 2 KiB][one ring per
-// chunk in flight][mbarriers][a few words of CTA state].
-constexpr uint32_t kBarOffset = kTableBytes + kRing + kChunksPerCta * kRing;
+// Shared memory: [slot table 16 KiB][alignment slack 4 KiB][4 KiB ring per
+// warp][kNSeg mbarriers per chunk slot][a few words of CTA state].
+constexpr uint32_t kBarOffset = kTableBytes + kWarpRing + kWarps * kWarpRing;
 constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
 constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
@@ -53,7 +72,7 @@ constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 struct Smem {
     uint32_t *tab;
     uint32_t tab_s;
-    uint32_t rings_s;   // kRing aligned
+    uint32_t rings_s;   // kWarpRing aligned
     uint8_t *rings;     // generic pointer of rings_s
     uint64_t *bars;
     uint32_t *misc;     // CTA-shared words
@@ -64,7 +83,7 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     s.tab = reinterpret_cast<uint32_t *>(smem);
     s.tab_s = smem_addr(smem);
     const uint32_t raw = smem_addr(smem + kTableBytes);
-    s.rings_s = (raw + kRing - 1) & ~(kRing - 1);
+    s.rings_s = (raw + kWarpRing - 1) & ~(kWarpRing - 1);
     s.rings = smem + kTableBytes + (s.rings_s - raw);
     s.bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
     s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
@@ -175,10 +194,11 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
     return total;
 }
 
-// Ring of one chain (one of the warp's two chunks in flight), carried across
-// the chunks the warp decodes.
+// The ring and barriers of one chunk slot of a warp, carried across the
+// chunks the warp decodes.  With one chunk per warp, slot 0's ring is the
+// warp's whole 4 KiB.
 struct ChainRing {
-    uint32_t ring_s;    // kRing-aligned shared address
+    uint32_t ring_s;    // shared address, aligned to the ring's size
     uint32_t bar0;      // its kNSeg mbarriers
     uint32_t phase;     // bit i: parity of the next wait on barrier i
 };
@@ -193,7 +213,7 @@ __device__ __forceinline__ WarpRings rings_init(const Smem &sm, uint32_t warp, u
 #pragma unroll
     for (uint32_t k = 0; k < kChains; ++k) {
         const uint32_t i = warp * kChains + k;
-        w.r[k].ring_s = sm.rings_s + i * kRing;
+        w.r[k].ring_s = sm.rings_s + warp * kWarpRing + k * GeoPair::kRing;
         w.r[k].bar0 = smem_addr(sm.bars + i * kNSeg);
         w.r[k].phase = 0;
     }
@@ -209,15 +229,14 @@ __device__ __forceinline__ WarpRings rings_init(const Smem &sm, uint32_t warp, u
 
 // Decoding state of one chunk.  Byte positions in its word stream are taken
 // relative to A, the 16-byte aligned message offset at or below the first
-// word; stream byte P then lives at ring offset P mod kRing.
+// word; stream byte P then lives at ring offset P mod (ring size).
 struct Chain {
     const uint8_t *src;  // message + A: source of segment 0
     uint8_t *outp;       // where this lane's next symbol goes
     uint32_t x;          // this lane's coder state
     uint32_t rp;         // read position (warp-uniform)
-    uint32_t issued;     // segments whose copy has been issued
-    uint32_t ready;      // segments known to be in the ring
-    uint32_t recheck;    // rp at which service() has work again
+    uint32_t evt;        // ring events done
+    uint32_t next_evt;   // rp at which event evt is due (~0: none left)
     uint32_t nseg;       // segments of the chunk
     uint32_t span;       // bytes copied in all (a multiple of 16)
     uint32_t endrel;     // end of the chunk's words
@@ -230,8 +249,8 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.src = nullptr;
     c.outp = nullptr;
     c.x = kL;
-    c.rp = c.issued = c.ready = c.nseg = c.span = c.endrel = c.steps = c.rem = 0;
-    c.recheck = 0xFFFFFFFFu;
+    c.rp = c.evt = c.nseg = c.span = c.endrel = c.steps = c.rem = 0;
+    c.next_evt = 0xFFFFFFFFu;
     c.st = RANS_OK;
 }
 
@@ -239,6 +258,7 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
 // data0; data_end = end of all chunks) of n_c symbols with N coders, output
 // at out.  Reads the N initial states; a malformed chunk gets c.st set and no
 // steps.
+template <class G>
 __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
                                            uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,
                                            uint8_t *out, uint32_t lane) {
@@ -260,56 +280,53 @@ __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_
     c.x = x;
     c.src = msg + A;
     c.span = uint32_t(round16(P1) - A);
-    c.nseg = (c.span + kSeg - 1) / kSeg;
+    c.nseg = (c.span + G::kSeg - 1) / G::kSeg;
     c.endrel = uint32_t(P1 - A);
     c.rp = uint32_t(P0 - A);
-    c.recheck = 0;
+    c.next_evt = 0;
     c.outp = out + lane;
     c.steps = n_c / N;
     c.rem = n_c % N;
 }
 
-// Bounded wait for segment c.ready, then mark it ready.
-__device__ __forceinline__ void chain_wait_next(Chain &c, ChainRing &r, uint32_t &timeouts) {
-    const uint32_t slot = c.ready % kNSeg;
+// Bounded wait for the copy into barrier slot `slot`, then flip its parity.
+__device__ __forceinline__ void ring_wait(ChainRing &r, uint32_t slot, uint32_t &timeouts) {
     const bool ok = timeouts != 0 || mbar_wait_bounded(r.bar0 + 8 * slot, (r.phase >> slot) & 1u);
     if (__any_sync(kFull, !ok)) timeouts = 1;  // warp-uniform
     r.phase ^= 1u << slot;
-    ++c.ready;
 }
 
-// Issue every segment whose ring slot is free (its previous segment lies
-// wholly below rp), wait until the next group's bytes [rp, rp + kGroupBytes)
-// are in, and compute the read position at which either can change again.
+// Ring event c.evt: issue the copy of segment evt (its slot's previous
+// segment lies wholly below rp and was waited for), wait for segment
+// evt - LAG, and work out when the next event is due.
+template <class G>
+__device__ __forceinline__ void chain_event(Chain &c, ChainRing &r, uint32_t &timeouts,
+                                            uint32_t lane) {
+    const uint32_t k = c.evt;
+    const uint32_t slot = k % G::kNSeg;
+    const bool issue = k < c.nseg;
+    const uint32_t off = k * G::kSeg;
+    bulk_g2s_armed_if(issue && lane == 0, r.ring_s + slot * G::kSeg, c.src + off,
+                      issue ? min(G::kSeg, c.span - off) : 0u, r.bar0 + 8 * slot);
+    if (k >= G::kLag && k - G::kLag < c.nseg) ring_wait(r, (k - G::kLag) % G::kNSeg, timeouts);
+    c.evt = k + 1;
+    c.next_evt = k + 1 >= c.nseg + G::kLag
+                     ? 0xFFFFFFFFu
+                     : (k + 2 > G::kNSeg ? (k + 2 - G::kNSeg) * G::kSeg : 0u);
+}
+
+template <class G>
 __device__ __forceinline__ void chain_service(Chain &c, ChainRing &r, uint32_t &timeouts,
                                               uint32_t lane) {
-    const uint32_t limit = min(c.nseg, kNSeg + c.rp / kSeg);
-    for (; c.issued < limit; ++c.issued) {
-        if (lane == 0) {
-            const uint32_t slot = c.issued % kNSeg;
-            const uint32_t off = c.issued * kSeg;
-            const uint32_t bytes = min(kSeg, c.span - off);
-            mbar_arrive_expect_tx(r.bar0 + 8 * slot, bytes);
-            bulk_g2s(r.ring_s + slot * kSeg, c.src + off, bytes, r.bar0 + 8 * slot);
-        }
-    }
-    const uint32_t need = min(c.nseg, (c.rp + kGroupBytes + kSeg - 1) / kSeg);
-    while (c.ready < need) chain_wait_next(c, r, timeouts);
-    const uint32_t r_ready =
-        c.ready >= c.nseg ? 0xFFFFFFFFu
-                          : (c.ready * kSeg >= kGroupBytes ? c.ready * kSeg - kGroupBytes + 1 : 0u);
-    const uint32_t r_issue = c.issued >= c.nseg
-                                 ? 0xFFFFFFFFu
-                                 : (c.issued + 1 >= kNSeg ? (c.issued + 1 - kNSeg) * kSeg : 0u);
-    c.recheck = min(r_ready, r_issue);
+    while (c.rp >= c.next_evt) chain_event<G>(c, r, timeouts, lane);
 }
 
 // Decode one step of a chunk: every active lane decodes one symbol and reads
 // at most one word.  FULL: every lane of the warp is a coder with a symbol in
 // this step.  rp is the byte position in the word stream (warp-uniform);
-// ring_s is the chunk's kRing-aligned ring, so (offset & (kRing - 1)) | ring_s
-// addresses it.
-template <bool FULL>
+// ring_s is the chunk's ring of RING bytes, aligned to RING, so
+// (offset & (RING - 1)) | ring_s addresses it.
+template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
                                             uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
                                             uint32_t lt) {
@@ -320,13 +337,13 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
     }
     const bool need = (FULL || active) && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (kRing - 1)) | ring_s);
+    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp += 2u * __popc(m);
 }
 
 // One step of two chunks a and b, their instructions interleaved.
-template <bool FULL>
+template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32_t ra_s, uint8_t *oa,
                                              uint32_t &xb, uint32_t &rpb, uint32_t rb_s, uint8_t *ob,
                                              bool active, uint32_t tab_s, uint32_t lt) {
@@ -342,8 +359,8 @@ __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32
     const bool nb = (FULL || active) && xb < kL;
     const uint32_t ma = __ballot_sync(kFull, na);
     const uint32_t mb = __ballot_sync(kFull, nb);
-    const uint32_t wa = ld_ring_u16(((rpa + 2u * __popc(ma & lt)) & (kRing - 1)) | ra_s);
-    const uint32_t wb = ld_ring_u16(((rpb + 2u * __popc(mb & lt)) & (kRing - 1)) | rb_s);
+    const uint32_t wa = ld_ring_u16(((rpa + 2u * __popc(ma & lt)) & (RING - 1)) | ra_s);
+    const uint32_t wb = ld_ring_u16(((rpb + 2u * __popc(mb & lt)) & (RING - 1)) | rb_s);
     if (na) xa = __byte_perm(xa, wa, 0x1054u);
     if (nb) xb = __byte_perm(xb, wb, 0x1054u);
     rpa += 2u * __popc(ma);
@@ -351,35 +368,39 @@ __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32
 }
 
 // Decode what is left of one chunk on its own.
-template <bool FULL>
+template <bool FULL, class G>
 __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &timeouts, uint32_t N,
                                           bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt) {
-    for (; c.steps >= kGroup; c.steps -= kGroup) {
-        if (c.rp >= c.recheck) chain_service(c, r, timeouts, lane);
+    for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
+        chain_service<G>(c, r, timeouts, lane);
 #pragma unroll
-        for (uint32_t u = 0; u < kGroup; ++u)
-            decode_step<FULL>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N, lt);
-        c.outp += kGroup * N;
+        for (uint32_t u = 0; u < G::kGroup; ++u)
+            decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N, lt);
+        c.outp += G::kGroup * N;
     }
-    for (; c.steps > 0; --c.steps) {
-        chain_service(c, r, timeouts, lane);
-        decode_step<FULL>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
+    for (uint32_t t = c.steps % G::kGroup; t > 0; --t) {
+        chain_service<G>(c, r, timeouts, lane);
+        decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
         c.outp += N;
     }
+    c.steps = 0;
     if (c.rem) {
-        chain_service(c, r, timeouts, lane);
-        decode_step<false>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
+        chain_service<G>(c, r, timeouts, lane);
+        decode_step<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
         c.rem = 0;
     }
 }
 
-// Drain the copies still in flight, so that the ring and the barrier phases
-// are clean for the next chunk, and check the chunk's end: a well-formed
-// chunk ends with every coder back at x0 = L and every word read exactly once
-// (decoder and encoder in lockstep, Section 3).
+// Wait for the copies still in flight, so that the ring and the barrier
+// phases are clean for the next chunk, and check the chunk's end: a
+// well-formed chunk ends with every coder back at x0 = L and every word read
+// exactly once (decoder and encoder in lockstep, Section 3).
+template <class G>
 __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t &timeouts,
                                                 bool lane_on) {
-    while (c.ready < c.issued) chain_wait_next(c, r, timeouts);
+    const uint32_t issued = min(c.evt, c.nseg);
+    for (uint32_t j = c.evt > G::kLag ? c.evt - G::kLag : 0u; j < issued; ++j)
+        ring_wait(r, j % G::kNSeg, timeouts);
     if (c.st != RANS_OK) return c.st;
     if (timeouts) return RANS_ERR_TIMEOUT;
     const bool ok = __all_sync(kFull, !lane_on || c.x == kL) && c.rp == c.endrel;
@@ -400,30 +421,33 @@ __device__ __forceinline__ uint32_t const_chunk(const uint8_t *msg, uint32_t dat
     return __all_sync(kFull, x == kL) ? RANS_OK : RANS_ERR_CORRUPT;
 }
 
-// Decode chunks c and, when count == 2, c + 1 of a message (offsets table
-// offs, data region at msg + data0, data_end = offs[n_chunks]) of n_sym
-// symbols in chunks of CS with N coders; chunk k's symbols go to out + k*CS.
-// const_sym != kNoConst: the model has one symbol with f = M.  Returns the
-// warp-uniform status (RANS_OK, or the first of RANS_ERR_CORRUPT /
-// RANS_ERR_TIMEOUT found in the two chunks).
-template <int NT>  // NT = 32: all 32 lanes are coders; NT = 0: runtime N
+// Decode chunks c .. c + count - 1 (count = 1, or 2 when PAIR) of a message
+// (offsets table offs, data region at msg + data0, data_end = offs[n_chunks])
+// of n_sym symbols in chunks of CS with N coders; chunk k's symbols go to
+// out + k*CS.  PAIR: the warp's two 2 KiB rings, the two chunks' steps
+// interleaved; otherwise one chunk in the warp's 4 KiB ring.  const_sym !=
+// kNoConst: the model has one symbol with f = M.  Returns the warp-uniform
+// status (RANS_OK, or the first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
+template <int NT, bool PAIR>  // NT = 32: all 32 lanes are coders; NT = 0: runtime N
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
                                                   uint64_t n_sym, uint32_t CS, uint32_t N_rt,
                                                   uint8_t *out, uint32_t const_sym, uint32_t lane,
                                                   uint32_t lt) {
+    using G = typename std::conditional<PAIR, GeoPair, GeoOne>::type;
     constexpr bool kFullWarp = NT == 32;
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;
+    const bool two = PAIR && count > 1;
     const uint64_t first = uint64_t(c) * CS;
     const uint32_t n_a = uint32_t(umin64(CS, n_sym - first));
-    const uint32_t n_b = count > 1 ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
-    const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = count > 1 ? offs[c + 2] : 0u;
+    const uint32_t n_b = two ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
+    const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = two ? offs[c + 2] : 0u;
 
     if (const_sym != kNoConst) {
         uint32_t st = const_chunk(msg, data0, o0, o1, data_end, n_a, N, out + first, const_sym, lane);
-        if (count > 1) {
+        if (two) {
             const uint32_t sb =
                 const_chunk(msg, data0, o1, o2, data_end, n_b, N, out + first + CS, const_sym, lane);
             if (st == RANS_OK) st = sb;
@@ -432,28 +456,31 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     }
 
     Chain a, b;
-    chain_open(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
-    if (count > 1) chain_open(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, lane);
+    chain_open<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
+    if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, lane);
     else chain_empty(b);
 
-    // Both chunks step together while each has a full group left.
-    uint32_t groups = min(a.steps, b.steps) / kGroup;
-    a.steps -= groups * kGroup;
-    b.steps -= groups * kGroup;
-    for (; groups > 0; --groups) {
-        if (a.rp >= a.recheck) chain_service(a, w.r[0], w.timeouts, lane);
-        if (b.rp >= b.recheck) chain_service(b, w.r[1], w.timeouts, lane);
+    if (PAIR) {
+        // Both chunks step together while each has a full group left.
+        const uint32_t groups = min(a.steps, b.steps) / G::kGroup;
+        a.steps -= groups * G::kGroup;
+        b.steps -= groups * G::kGroup;
+        for (uint32_t g = groups; g > 0; --g) {
+            chain_service<G>(a, w.r[0], w.timeouts, lane);
+            chain_service<G>(b, w.r[1], w.timeouts, lane);
 #pragma unroll
-        for (uint32_t u = 0; u < kGroup; ++u)
-            decode_step2<kFullWarp>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x, b.rp,
-                                    w.r[1].ring_s, b.outp + u * N, lane_on, tab_s, lt);
-        a.outp += kGroup * N;
-        b.outp += kGroup * N;
+            for (uint32_t u = 0; u < G::kGroup; ++u)
+                decode_step2<kFullWarp, G::kRing>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x,
+                                                  b.rp, w.r[1].ring_s, b.outp + u * N, lane_on,
+                                                  tab_s, lt);
+            a.outp += G::kGroup * N;
+            b.outp += G::kGroup * N;
+        }
     }
-    chain_run<kFullWarp>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt);
-    chain_run<kFullWarp>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
-    const uint32_t sa = chain_close(a, w.r[0], w.timeouts, lane_on);
-    const uint32_t sb = count > 1 ? chain_close(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
+    chain_run<kFullWarp, G>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt);
+    if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
+    const uint32_t sa = chain_close<G>(a, w.r[0], w.timeouts, lane_on);
+    const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
     return sa != RANS_OK ? sa : sb;
 }
 

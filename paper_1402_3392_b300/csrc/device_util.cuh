@@ -106,6 +106,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// As bulk_g2s, preceded by arming `bar` for `bytes`, both only where `pred`
+// holds (predicated instructions: the calling warp does not branch).
+__device__ __forceinline__ void bulk_g2s_armed_if(bool pred, uint32_t dst, const void *src,
+                                                  uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%3], %2;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t"
+        "}" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "r"(uint32_t(pred))
+        : "memory");
+}
 // shared -> global, tracked by bulk async-groups of the issuing thread.
 __device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),

@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(dec::kThreads)
             const uint32_t count = uint32_t(umin64(dec::kChains, g.n_chunks - c));
             const uint32_t st =
                 d.n_lanes == 32
-                    ? dec::decode_chunks<32>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                    ? dec::decode_chunks<32, true>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
                                              d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane,
                                              lt)
-                    : dec::decode_chunks<0>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                    : dec::decode_chunks<0, true>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
                                             d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs,
                                             lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);

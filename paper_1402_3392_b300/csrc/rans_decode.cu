@@ -57,9 +57,12 @@ __global__ void __launch_bounds__(dec::kThreads)
 
     for (uint32_t q = blockIdx.x * kWarps + warp; q < n_units; q += gridDim.x * kWarps) {
         const uint32_t c = q * per;
-        const uint32_t st = dec::decode_chunks<NT>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
-                                                   min(per, p.n_chunks - c), p.n_sym, p.CS, p.N,
-                                                   p.out, cs, lane, lt);
+        const uint32_t count = min(per, p.n_chunks - c);
+        const uint32_t st =
+            per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
+                                                   count, p.n_sym, p.CS, p.N, p.out, cs, lane, lt)
+                    : dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
+                                                    c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
