@@ -70,15 +70,16 @@ __global__ void __launch_bounds__(dec::kThreads)
 
 // Chunks per warp for a message of n_chunks chunks when `warps` warps are
 // resident.  A chunk is one chain of dependent steps, so a launch lasts at
-// least one chunk's latency and its last wave leaves warps idle.  Two chains
-// per warp raise the step rate of a fully occupied SM by 8-13%, but halve
-// the chains in flight, which makes a partly filled last wave costlier.
-// Measured on a B300 (64 KiB chunks, N = 32; w = n_chunks / resident warps):
-//   w            0.4-1.0  1.3  1.7  2.0  2.3  2.6  3.0  3.5  3.8  4.3  5.2
-//   faster mode  one      two  two  two  two  two  one  one  two  two  two
+// least one chunk's latency and its last wave leaves warps idle.  One chunk
+// per warp streams through the warp's whole 4 KiB ring in 1 KiB copies; two
+// chunks per warp overlap two chains but have 2 KiB rings (512-byte copies)
+// and half the chains in flight.  Measured on a B300 (64 KiB chunks, N = 32;
+// w = n_chunks / resident warps; times in us):
+//   w      0.4  1.0  1.3  1.7  2.0  2.3  2.6  3.0  3.5  3.8   4.3   5.2
+//   one    202  292  430  562  561  654  722  833  958  1102  1175  1448
+//   two    271  331  431  561  560  658  758  905  1098 1100  1203  1384
 uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
-    const double w = double(n_chunks) / double(warps);
-    return (w > 1.0 && w <= 2.8) || w >= 3.6 ? dec::kChains : 1u;
+    return double(n_chunks) >= 5.0 * double(warps) ? dec::kChains : 1u;
 }
 
 template <int NT>

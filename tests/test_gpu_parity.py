@@ -103,12 +103,13 @@ def test_long_chunk_many_segments(rlib, orc, cuda):
         assert np.array_equal(back, sym)
 
 
-@pytest.mark.parametrize("n_chunks,N,CS", [(9473, 32, 64), (30001, 32, 48), (12001, 7, 61)])
+@pytest.mark.parametrize("n_chunks,N,CS", [(9473, 32, 64), (30001, 32, 48), (25001, 7, 61)])
 def test_more_chunks_than_resident_warps(rlib, orc, cuda, n_chunks, N, CS):
-    """Messages with thousands of short chunks, so that warps decode two
-    chunks side by side; odd chunk counts leave one warp a single chunk and
-    the last chunk is ragged.  A corrupt word in the first or the second
-    chunk of a pair is reported."""
+    """Messages with thousands of short chunks: several waves of one chunk
+    per warp, and (at more than five waves of the 4736 warps a B300 holds)
+    warps decoding two chunks side by side, where an odd chunk count leaves
+    one warp a single chunk.  The last chunk is ragged.  A corrupt word in
+    the first or the second chunk of a pair is reported."""
     import torch
 
     rng = np.random.default_rng(n_chunks + N)
