@@ -61,6 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
+    ap.add_argument("--batched-layout", default="",
+                    help="N,chunk_symbols,policy for the batched leg instead of the "
+                         "autotuner's choice (e.g. 32,16384,fill)")
     return ap.parse_args(argv)
 
 
@@ -308,9 +311,13 @@ def batched_leg(rans, dev, args, hbm):
     table_idx = np.arange(count)
     total = int(sizes.sum())
 
-    sample = np.arange(0, count, 25)
     t0 = time.perf_counter()
-    best, tried = autotune.autotune(arena, offs[sample], sizes[sample], tdev, sample, reps=3)
+    if args.batched_layout:
+        n_l, ch, pol = args.batched_layout.split(",")
+        best, tried = dict(n_lanes=int(n_l), chunk=int(ch), policy=pol), []
+    else:
+        sample = np.arange(0, count, 25)
+        best, tried = autotune.autotune(arena, offs[sample], sizes[sample], tdev, sample, reps=3)
     tune_s = time.perf_counter() - t0
     N = best["n_lanes"]
     cs = autotune.chunk_sizes(sizes, best["chunk"], best["policy"])
