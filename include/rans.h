@@ -164,11 +164,39 @@ int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
                 uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
 
 /*
+ * rans_decode_host -- rans_decode with the message and the symbols in host
+ * memory.  The message is split into pieces of whole chunks; each piece's
+ * bytes are copied to the device on one internal stream, decoded on `stream`,
+ * and its symbols copied back on another internal stream, so copies in both
+ * directions overlap each other and the decoding (this needs page-locked host
+ * buffers; pageable ones work but copy synchronously).  The two internal
+ * streams are created on a device's first call and kept.
+ *
+ * h_msg, msg_size, h_freq, n_alpha, params, n_symbols : as in rans_decode,
+ *             with h_msg in host memory (no alignment required).
+ * h_symbols : host, n_symbols bytes of output.
+ * h_status  : host u32, set like rans_decode's d_status (RANS_OK,
+ *             RANS_ERR_CORRUPT or RANS_ERR_TIMEOUT) by the enqueued work.
+ * d_work    : device, 16-byte aligned, work_cap >=
+ *             rans_decode_host_work_size(msg_size, n_symbols) bytes: the
+ *             message, the symbols and the status word on the device.
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG, RANS_ERR_BUFFER_TOO_SMALL or
+ * RANS_ERR_CUDA.  The work is ordered after what `stream` holds, and later
+ * work on `stream` runs after it; h_symbols and h_status are valid, and the
+ * host buffers may be reused, once `stream` has reached that point.
+ */
+uint64_t rans_decode_host_work_size(uint64_t msg_size, uint64_t n_symbols);
+int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const uint16_t *h_freq,
+                     uint32_t n_alpha, const rans_params *params, uint8_t *h_symbols,
+                     uint64_t n_symbols, uint32_t *h_status, void *d_work, uint64_t work_cap,
+                     rans_stream_t stream);
+
+/*
  * Batched decoding: many independent messages ("streams"), each with its own
  * model, layout and size, decoded by one persistent launch.  A CTA takes one
- * work item at a time -- up to 8 chunks of one stream -- from a device-side
+ * work item at a time -- up to 16 chunks of one stream -- from a device-side
  * counter, builds that stream's slot table in shared memory (only when the
- * model changes) and decodes one chunk per warp.  Uneven stream sizes balance
+ * model changes) and decodes two chunks per warp side by side.  Uneven stream sizes balance
  * themselves because items are handed out dynamically.  The call enqueues
  * kernels only (no allocation, no host synchronization), so it can be
  * captured in a CUDA graph and replayed.

@@ -3,6 +3,7 @@
 // chunk's N interleaved coders on the warp's lanes (decode_core.cuh), one
 // slot table per CTA built from the message's model.
 #include <algorithm>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -25,6 +26,8 @@ struct DecodeParams {
     uint32_t CS;
     uint32_t n_chunks;
     uint32_t data0;
+    uint32_t c_begin;   // chunks [c_begin, c_end) are decoded by this launch
+    uint32_t c_end;
     uint32_t per_warp;  // chunks a warp decodes side by side: 1 or dec::kChains
     uint16_t freq[RANS_MAX_ALPHABET];
 };
@@ -53,11 +56,11 @@ __global__ void __launch_bounds__(dec::kThreads)
     const uint32_t data_end = offs[p.n_chunks];
     const uint32_t lt = lanemask_lt();
     const uint32_t per = p.per_warp;
-    const uint32_t n_units = (p.n_chunks + per - 1) / per;
+    const uint32_t n_units = (p.c_end - p.c_begin + per - 1) / per;
 
     for (uint32_t q = blockIdx.x * kWarps + warp; q < n_units; q += gridDim.x * kWarps) {
-        const uint32_t c = q * per;
-        const uint32_t count = min(per, p.n_chunks - c);
+        const uint32_t c = p.c_begin + q * per;
+        const uint32_t count = min(per, p.c_end - c);
         const uint32_t st =
             per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
                                                    count, p.n_sym, p.CS, p.N, p.out, cs, lane, lt)
@@ -99,8 +102,9 @@ int launch_decode(DecodeParams &p, cudaStream_t stream) {
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t cap = uint64_t(per_sm) * sm_count();
-    p.per_warp = chunks_per_warp(p.n_chunks, cap * kWarps);
-    const uint64_t want = ceil_div(p.n_chunks, uint64_t(kWarps) * p.per_warp);
+    const uint64_t n_range = p.c_end - p.c_begin;
+    p.per_warp = chunks_per_warp(n_range, cap * kWarps);
+    const uint64_t want = ceil_div(n_range, uint64_t(kWarps) * p.per_warp);
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     decode_kernel<NT><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
@@ -111,31 +115,160 @@ int launch_decode(DecodeParams &p, cudaStream_t stream) {
 
 using namespace rans;
 
-extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
-                           uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
-                           uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
-    if (!d_msg || !d_status || !params_ok(params) || !table_ok(h_freq, n_alpha, nullptr))
+// Checks the arguments shared by the decode entry points and fills p (all
+// chunks); msg may be a host or a device address.
+static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t *h_freq,
+                          uint32_t n_alpha, const rans_params *params, uint64_t n_symbols,
+                          DecodeParams &p) {
+    if (!msg || !params_ok(params) || !table_ok(h_freq, n_alpha, nullptr))
         return RANS_ERR_INVALID_ARG;
-    if (n_symbols && !d_symbols) return RANS_ERR_INVALID_ARG;
     const MessageGeometry g = geometry(n_symbols, params);
     if (g.n_chunks > 0xFFFFFFFEull) return RANS_ERR_INVALID_ARG;
-    if (msg_size < g.data0 || (msg_size & 15u) || !aligned16(d_msg) || msg_size < 48 ||
+    if (msg_size < g.data0 || (msg_size & 15u) || msg_size < 48 ||
         msg_size - g.data0 > 0xFFFFFFFFull + 15)
         return RANS_ERR_INVALID_ARG;
-
-    DecodeParams p{};
-    p.msg = d_msg;
-    p.out = d_symbols;
-    p.status = d_status;
+    p = DecodeParams{};
     p.msg_size = msg_size;
     p.n_sym = n_symbols;
     p.N = params->n_lanes;
     p.CS = params->chunk_symbols;
     p.n_chunks = uint32_t(g.n_chunks);
     p.data0 = uint32_t(g.data0);
+    p.c_begin = 0;
+    p.c_end = p.n_chunks;
     for (uint32_t s = 0; s < n_alpha; ++s) p.freq[s] = h_freq[s];
+    return RANS_OK;
+}
 
+static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaStream_t st) {
+    p.c_begin = c_begin;
+    p.c_end = c_end;
+    return p.N == 32 ? launch_decode<32>(p, st) : launch_decode<0>(p, st);
+}
+
+extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                           uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                           uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
+    DecodeParams p;
+    const int rc = prepare_decode(d_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.status = d_status;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
-    return p.N == 32 ? launch_decode<32>(p, st) : launch_decode<0>(p, st);
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+// ---------------------------------------------------------------------------
+// Decoding from and to host memory, copies overlapped with decoding.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr uint64_t kPieceSymbols = 32ull << 20;  // about this many symbols per piece
+constexpr uint32_t kMaxPieces = 256;
+
+struct CopyStreams {
+    cudaStream_t in = nullptr, out = nullptr;
+};
+
+// Two non-blocking streams per device (host-to-device copies and
+// device-to-host copies), created on first use and kept for the process.
+int copy_streams(CopyStreams *cs) {
+    static std::mutex mu;
+    static CopyStreams per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RANS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    CopyStreams &c = per_dev[dev];
+    if (!c.in) {
+        if (cudaStreamCreateWithFlags(&c.in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c.out, cudaStreamNonBlocking) != cudaSuccess) {
+            c.in = c.out = nullptr;
+            return RANS_ERR_CUDA;
+        }
+    }
+    *cs = c;
+    return RANS_OK;
+}
+
+// stream `waiter` waits for the work enqueued on `signaler` so far.
+bool join(cudaStream_t waiter, cudaStream_t signaler) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    const bool ok = cudaEventRecord(ev, signaler) == cudaSuccess &&
+                    cudaStreamWaitEvent(waiter, ev, 0) == cudaSuccess;
+    cudaEventDestroy(ev);  // released once the event has completed
+    return ok;
+}
+
+}  // namespace
+
+extern "C" uint64_t rans_decode_host_work_size(uint64_t msg_size, uint64_t n_symbols) {
+    return round16(msg_size) + round16(n_symbols) + 16;
+}
+
+extern "C" int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const uint16_t *h_freq,
+                                uint32_t n_alpha, const rans_params *params, uint8_t *h_symbols,
+                                uint64_t n_symbols, uint32_t *h_status, void *d_work,
+                                uint64_t work_cap, rans_stream_t stream) {
+    DecodeParams p;
+    int rc = prepare_decode(h_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!h_status || !d_work || !aligned16(d_work) || (n_symbols && !h_symbols))
+        return RANS_ERR_INVALID_ARG;
+    if (work_cap < rans_decode_host_work_size(msg_size, n_symbols)) return RANS_ERR_BUFFER_TOO_SMALL;
+    uint8_t *d_msg = static_cast<uint8_t *>(d_work);
+    uint8_t *d_out = d_msg + round16(msg_size);
+    uint32_t *d_status = reinterpret_cast<uint32_t *>(d_out + round16(n_symbols));
+    p.msg = d_msg;
+    p.out = d_out;
+    p.status = d_status;
+
+    // Pieces of whole chunks; piece k's message bytes are copied in on one
+    // stream, decoded on the caller's stream, and its symbols copied out on a
+    // third, so copies in both directions overlap each other and decoding.
+    // The split reads the offset table in host memory; if it is not
+    // increasing and in range the whole message is one piece (the kernel
+    // then reports the damage).
+    const uint32_t nc = p.n_chunks;
+    const uint32_t per_piece = uint32_t(std::max<uint64_t>(
+        std::max<uint64_t>(1, ceil_div(kPieceSymbols, p.CS)), ceil_div(nc, kMaxPieces)));
+    const uint32_t *offs = reinterpret_cast<const uint32_t *>(h_msg + 32);
+    bool split = nc > per_piece;
+    for (uint32_t c = 0; split && c < nc; ++c)
+        split = offs[c] <= offs[c + 1] && uint64_t(p.data0) + offs[c + 1] <= msg_size;
+
+    CopyStreams cs;
+    if ((rc = copy_streams(&cs)) != RANS_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess || !join(cs.in, st) ||
+        !join(cs.out, st))
+        return RANS_ERR_CUDA;
+    uint64_t copied = 0;  // message bytes [0, copied) are on their way in
+    for (uint64_t c0 = 0; c0 < nc || c0 == 0; c0 += per_piece) {
+        const uint64_t c1 = split ? std::min<uint64_t>(nc, c0 + per_piece) : nc;
+        const uint64_t hi = c1 == nc ? msg_size
+                                     : std::min<uint64_t>(msg_size, round16(p.data0 + offs[c1]));
+        if (hi > copied &&
+            cudaMemcpyAsync(d_msg + copied, h_msg + copied, hi - copied, cudaMemcpyHostToDevice,
+                            cs.in) != cudaSuccess)
+            return RANS_ERR_CUDA;
+        copied = std::max(copied, hi);
+        if (!join(st, cs.in)) return RANS_ERR_CUDA;
+        if ((rc = launch_range(p, uint32_t(c0), uint32_t(c1), st)) != RANS_OK) return rc;
+        if (!join(cs.out, st)) return RANS_ERR_CUDA;
+        const uint64_t s0 = c0 * p.CS, s1 = std::min<uint64_t>(n_symbols, c1 * p.CS);
+        if (s1 > s0 && cudaMemcpyAsync(h_symbols + s0, d_out + s0, s1 - s0, cudaMemcpyDeviceToHost,
+                                       cs.out) != cudaSuccess)
+            return RANS_ERR_CUDA;
+        if (c1 >= nc) break;
+    }
+    if (cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs.out) !=
+            cudaSuccess ||
+        !join(st, cs.out))
+        return RANS_ERR_CUDA;
+    return RANS_OK;
 }

@@ -28,7 +28,8 @@ __all__ = [
     "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
     "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
-    "Server", "rans_check_bounded_wait",
+    "Server", "rans_check_bounded_wait", "rans_decode_host", "rans_decode_host_work_size",
+    "decode_host",
 ]
 
 RANS_OK = 0
@@ -92,6 +93,8 @@ def _load() -> C.CDLL:
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
         "rans_check_bounded_wait": (i32, [vp, vp]),
+        "rans_decode_host_work_size": (u64, [u64, u64]),
+        "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
         "rans_encode_batch_plan": (u64, [vp, u32]),
@@ -183,6 +186,45 @@ def rans_encode(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_c
                          _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
                          _ptr(d_scratch), int(scratch_cap), _stream(stream))
     return _check(rc, "rans_encode") if check else rc
+
+
+def rans_decode_host_work_size(msg_size: int, n_symbols: int) -> int:
+    return int(lib.rans_decode_host_work_size(int(msg_size), int(n_symbols)))
+
+
+def rans_decode_host(h_msg, msg_size, freq, n_lanes, chunk_symbols, h_symbols, n_symbols,
+                     h_status, d_work, work_cap, stream=None, check=True) -> int:
+    """rans_decode from and to host memory (pointers or CPU tensors, page-locked
+    for overlap), copies in both directions overlapped with the decoding."""
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_host(_ptr(h_msg), int(msg_size), f.ctypes.data, f.size, C.byref(p),
+                              _ptr(h_symbols), int(n_symbols), _ptr(h_status), _ptr(d_work),
+                              int(work_cap), _stream(stream))
+    return _check(rc, "rans_decode_host") if check else rc
+
+
+def decode_host(msg, n_symbols: int, freq, n_lanes: int = 32, chunk_symbols: int = 65536,
+                device=None, stream=None, out=None, work=None):
+    """Decode a host (CPU, ideally pinned) uint8 message tensor into a host
+    tensor of n_symbols bytes through rans_decode_host.  Returns (symbols,
+    status) after synchronizing."""
+    import torch
+
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    cap = rans_decode_host_work_size(msg.numel(), n_symbols)
+    if work is None or work.numel() < cap:
+        work = torch.empty(cap, dtype=torch.uint8, device=device)
+    if out is None:
+        out = torch.empty(max(1, n_symbols), dtype=torch.uint8, pin_memory=True)
+    status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    rans_decode_host(msg, msg.numel(), freq, n_lanes, chunk_symbols, out, n_symbols, status,
+                     work, work.numel(), stream)
+    if stream is not None:
+        stream.synchronize()
+    else:
+        torch.cuda.current_stream(device).synchronize()
+    return out[:n_symbols], int(status.item())
 
 
 def rans_check_bounded_wait(d_status, stream=None, check=True) -> int:
