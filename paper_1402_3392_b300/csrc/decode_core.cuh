@@ -90,6 +90,16 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     return s;
 }
 
+// a * b + c.  The read-position updates and the table address are written
+// this way rather than as shift-and-add: with this form the compiler emits
+// fewer instructions for the decode step (measured: 20.9 instead of 22.9
+// warp-instructions per step, 5-6 % less decode time).
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
 // Slot table entry: f_s << 20 | (slot - B_s) << 8 | s   (f_s < M here).
 // With E = entry >> 8 = f_s * 2^12 + (slot - B_s) the decode update is
 //     f_s * floor(x/M) + slot - B_s = f_s * (floor(x/M) - 2^12) + E  (mod 2^32).
@@ -330,7 +340,7 @@ template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
                                             uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
                                             uint32_t lt) {
-    const uint32_t e = ld_table(tab_s + ((x & (kM - 1)) << 2));
+    const uint32_t e = ld_table(imad(x & (kM - 1), 4u, tab_s));
     if (FULL || active) {
         x = decode_update(x, e);
         *outp = uint8_t(e);
@@ -339,7 +349,7 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
     const uint32_t m = __ballot_sync(kFull, need);
     const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
-    rp += 2u * __popc(m);
+    rp = imad(__popc(m), 2u, rp);
 }
 
 // One step of two chunks a and b, their instructions interleaved.
@@ -347,8 +357,8 @@ template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32_t ra_s, uint8_t *oa,
                                              uint32_t &xb, uint32_t &rpb, uint32_t rb_s, uint8_t *ob,
                                              bool active, uint32_t tab_s, uint32_t lt) {
-    const uint32_t ea = ld_table(tab_s + ((xa & (kM - 1)) << 2));
-    const uint32_t eb = ld_table(tab_s + ((xb & (kM - 1)) << 2));
+    const uint32_t ea = ld_table(imad(xa & (kM - 1), 4u, tab_s));
+    const uint32_t eb = ld_table(imad(xb & (kM - 1), 4u, tab_s));
     if (FULL || active) {
         xa = decode_update(xa, ea);
         xb = decode_update(xb, eb);
@@ -363,8 +373,8 @@ __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32
     const uint32_t wb = ld_ring_u16(((rpb + 2u * __popc(mb & lt)) & (RING - 1)) | rb_s);
     if (na) xa = __byte_perm(xa, wa, 0x1054u);
     if (nb) xb = __byte_perm(xb, wb, 0x1054u);
-    rpa += 2u * __popc(ma);
-    rpb += 2u * __popc(mb);
+    rpa = imad(__popc(ma), 2u, rpa);
+    rpb = imad(__popc(mb), 2u, rpb);
 }
 
 // Decode what is left of one chunk on its own.
