@@ -94,6 +94,32 @@ def load(mutant: int = 0) -> C.CDLL:
         lib.orc_decode_message.restype = C.c_int
         lib.orc_quantize.argtypes = [_u64p, C.c_uint32, C.c_uint32, _u16p]
         lib.orc_quantize.restype = C.c_int
+        lib.orc_encode_bypass.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                          _u32p, C.c_uint64, _u32p, _u64p, C.c_uint64, _u64p,
+                                          C.c_uint64, _u64p, _u64p, _u64p, _u32p, C.c_uint64,
+                                          _u64p]
+        lib.orc_encode_bypass.restype = C.c_int
+        lib.orc_decode_bypass.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                          _u64p, C.c_uint64, _u64p, C.c_uint64, _u32p, _u32p,
+                                          _u64p, C.c_uint64, _u64p, _u64p, _u64p, _u64p, _u32p,
+                                          C.c_uint64, _u64p]
+        lib.orc_decode_bypass.restype = C.c_int
+        lib.orc_max_message_size_bypass.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        lib.orc_max_message_size_bypass.restype = C.c_uint64
+        lib.orc_encode_chunk_bypass.argtypes = [_u8p, _u16p, C.c_uint64, _u16p, _u8p, C.c_uint32,
+                                                C.c_uint32, _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_chunk_bypass.restype = C.c_int
+        lib.orc_decode_chunk_bypass.argtypes = [_u8p, C.c_uint64, _u16p, _u8p, C.c_uint32,
+                                                C.c_uint32, _u8p, _u16p, C.c_uint64]
+        lib.orc_decode_chunk_bypass.restype = C.c_int
+        lib.orc_encode_message_bypass.argtypes = [_u8p, _u16p, C.c_uint64, _u16p, _u8p,
+                                                  C.c_uint32, C.c_uint32, C.c_uint32, _u8p,
+                                                  C.c_uint64, _u64p]
+        lib.orc_encode_message_bypass.restype = C.c_int
+        lib.orc_decode_message_bypass.argtypes = [_u8p, C.c_uint64, _u16p, _u8p, C.c_uint32,
+                                                  C.c_uint32, C.c_uint32, _u8p, _u16p,
+                                                  C.c_uint64]
+        lib.orc_decode_message_bypass.restype = C.c_int
         _LIBS[mutant] = lib
         return lib
 
@@ -242,6 +268,133 @@ class Oracle:
         if rc != OK:
             raise OracleError(rc, "decode_chunk")
         return out[:n_sym].copy()
+
+    # -- bypass: raw digits interleaved with the coded symbols (Section 3) ----
+    def encode_bypass(self, freq, symbols, raw_counts, raw, N=1, L=L_PROD, b=B_PROD,
+                      trace=False):
+        """Algorithm 1 encoder where symbol s carries raw_counts[s] raw base-b
+        digits; raw holds them in message order.  Returns dict(words, states
+        [, trace_state, trace_lane])."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        r = np.ascontiguousarray(raw_counts, dtype=np.uint32)
+        rw = np.ascontiguousarray(raw, dtype=np.uint64)
+        n = s.size
+        cap = max(1, 64 * n + rw.size + 64)
+        words = np.zeros(cap, dtype=np.uint64)
+        states = np.zeros(N, dtype=np.uint64)
+        nw = C.c_uint64(0)
+        tcap = (64 * n + N + 64) if trace else 0
+        ts = np.zeros(max(tcap, 1), dtype=np.uint64)
+        tl = np.zeros(max(tcap, 1), dtype=np.uint32)
+        nt = C.c_uint64(0)
+        rc = self.lib.orc_encode_bypass(_p(f, _u64p), f.size, L, b, N, _p(s, _u32p), n,
+                                        _p(r, _u32p), _p(rw, _u64p) if rw.size else None, rw.size,
+                                        _p(words, _u64p), cap, C.byref(nw), _p(states, _u64p),
+                                        _p(ts, _u64p) if trace else None,
+                                        _p(tl, _u32p) if trace else None, tcap, C.byref(nt))
+        if rc != OK:
+            raise OracleError(rc, "encode_bypass")
+        out = dict(words=words[: nw.value].copy(), states=states)
+        if trace:
+            out["trace_state"] = ts[: nt.value].copy()
+            out["trace_lane"] = tl[: nt.value].copy()
+        return out
+
+    def decode_bypass(self, freq, words, states, n_sym, raw_counts, N=1, L=L_PROD, b=B_PROD,
+                      trace=False):
+        """Decoder reading raw_counts[s] raw digits after each symbol s.
+        Returns dict(symbols, raw, consumed, states_end[, trace...])."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        st = np.ascontiguousarray(states, dtype=np.uint64)
+        r = np.ascontiguousarray(raw_counts, dtype=np.uint32)
+        sym = np.zeros(max(1, n_sym), dtype=np.uint32)
+        rcap = max(1, w.size)
+        raw = np.zeros(rcap, dtype=np.uint64)
+        nraw = C.c_uint64(0)
+        st_end = np.zeros(N, dtype=np.uint64)
+        used = C.c_uint64(0)
+        tcap = (64 * n_sym + N + 64) if trace else 0
+        ts = np.zeros(max(tcap, 1), dtype=np.uint64)
+        tl = np.zeros(max(tcap, 1), dtype=np.uint32)
+        nt = C.c_uint64(0)
+        rc = self.lib.orc_decode_bypass(_p(f, _u64p), f.size, L, b, N, _p(w, _u64p), w.size,
+                                        _p(st, _u64p), n_sym, _p(r, _u32p), _p(sym, _u32p),
+                                        _p(raw, _u64p), rcap, C.byref(nraw), C.byref(used),
+                                        _p(st_end, _u64p),
+                                        _p(ts, _u64p) if trace else None,
+                                        _p(tl, _u32p) if trace else None, tcap, C.byref(nt))
+        if rc != OK:
+            raise OracleError(rc, "decode_bypass")
+        out = dict(symbols=sym[:n_sym].copy(), raw=raw[: nraw.value].copy(),
+                   consumed=used.value, states_end=st_end)
+        if trace:
+            out["trace_state"] = ts[: nt.value].copy()
+            out["trace_lane"] = tl[: nt.value].copy()
+        return out
+
+    def max_message_size_bypass(self, n_sym, N, chunk_symbols):
+        return int(self.lib.orc_max_message_size_bypass(n_sym, N, chunk_symbols))
+
+    def encode_message_bypass(self, symbols, raw16, freq, raw_words, N=32, chunk_symbols=65536):
+        """Bypass message: symbol i is followed by raw16[i] when
+        raw_words[symbols[i]] == 1."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        rw = np.ascontiguousarray(raw16, dtype=np.uint16)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        rf = np.ascontiguousarray(raw_words, dtype=np.uint8)
+        assert rw.size == s.size and rf.size == fr.size
+        cap = self.max_message_size_bypass(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message_bypass(_p(s, _u8p), _p(rw, _u16p), s.size,
+                                                _p(fr, _u16p), _p(rf, _u8p), fr.size, N,
+                                                chunk_symbols, _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message_bypass")
+        return out[: size.value].copy()
+
+    def decode_message_bypass(self, msg, n_sym, freq, raw_words, N=32, chunk_symbols=65536):
+        """Returns (symbols, raw16) with raw16[i] = 0 where symbol i has none."""
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        rf = np.ascontiguousarray(raw_words, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        raw = np.zeros(max(1, n_sym), dtype=np.uint16)
+        rc = self.lib.orc_decode_message_bypass(_p(m, _u8p), m.size, _p(fr, _u16p),
+                                                _p(rf, _u8p), fr.size, N, chunk_symbols,
+                                                _p(out, _u8p), _p(raw, _u16p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message_bypass")
+        return out[:n_sym].copy(), raw[:n_sym].copy()
+
+    def encode_chunk_bypass(self, symbols, raw16, freq, raw_words, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        rw = np.ascontiguousarray(raw16, dtype=np.uint16)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        rf = np.ascontiguousarray(raw_words, dtype=np.uint8)
+        cap = 4 * N + 4 * s.size
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk_bypass(_p(s, _u8p), _p(rw, _u16p), s.size, _p(fr, _u16p),
+                                              _p(rf, _u8p), fr.size, N, _p(out, _u8p), cap,
+                                              C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk_bypass")
+        return out[: size.value].copy()
+
+    def decode_chunk_bypass(self, chunk, n_sym, freq, raw_words, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        rf = np.ascontiguousarray(raw_words, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        raw = np.zeros(max(1, n_sym), dtype=np.uint16)
+        rc = self.lib.orc_decode_chunk_bypass(_p(c, _u8p), c.size, _p(fr, _u16p), _p(rf, _u8p),
+                                              fr.size, N, _p(out, _u8p), _p(raw, _u16p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk_bypass")
+        return out[:n_sym].copy(), raw[:n_sym].copy()
 
     def quantize(self, weights, log2_M=LOG2_M_PROD):
         w = np.ascontiguousarray(weights, dtype=np.uint64)

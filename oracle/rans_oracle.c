@@ -30,6 +30,10 @@
  *   - Section 3: N coders interleaved into one buffer with no metadata.
  *     Symbol i of a message is handled by coder (i mod N); encoder and
  *     decoder use the same coder sequence.
+ *   - Section 3, bypass: raw digits interleaved with the coded data.  A
+ *     symbol may carry raw base-b digits that no coder touches; the encoder
+ *     sends them right before encoding the symbol, the decoder reads them
+ *     right after decoding it, and the two stay in lockstep.
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   - initial encoder state x0 = L for every coder;
@@ -170,17 +174,26 @@ static void trace_push(uint64_t *ts, uint32_t *tl, uint64_t cap, uint64_t *nt,
  * order; at the end the buffer is reversed so that words[0] is the first
  * word the decoder reads.  states[j] receives coder j's final state.
  *
+ * Raw (bypass) digits, Section 3: when r is given, symbol s carries r[s]
+ * raw base-b digits that no coder touches.  raw[0..n_raw) holds them in
+ * message order (symbol i's digits, first digit first).  The encoder sends a
+ * symbol's raw digits right before it encodes the symbol -- in its backwards
+ * emission order, last digit first -- so that after the final reversal the
+ * decoder finds them right after the words it reads when decoding that
+ * symbol.  r = NULL: no raw digits.
+ *
  * trace (optional): every state a coder passes through, in encoder order,
  * starting with the N initial states.
  * max_iters (optional): the largest number of renormalization iterations
  * any single symbol needed.
  */
-int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
-               const uint32_t *sym, uint64_t n_sym,
-               uint64_t *words, uint64_t word_cap, uint64_t *n_words,
-               uint64_t *states,
-               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
-               uint64_t *n_trace, uint32_t *max_iters)
+static int encode_impl(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                       const uint32_t *sym, uint64_t n_sym, const uint32_t *r,
+                       const uint64_t *raw, uint64_t n_raw,
+                       uint64_t *words, uint64_t word_cap, uint64_t *n_words,
+                       uint64_t *states,
+                       uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+                       uint64_t *n_trace, uint32_t *max_iters)
 {
     orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
     if (!mp) return ORC_ERR_ARG;
@@ -189,7 +202,7 @@ int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint
 
     u128 *x = (u128 *)malloc(sizeof(u128) * N);
     if (!x) { free(mp); return ORC_ERR_ARG; }
-    uint64_t nt = 0, W = 0;
+    uint64_t nt = 0, W = 0, raw_end = n_raw;
     uint32_t worst = 0;
     for (uint32_t j = 0; j < N; ++j) {
         x[j] = initial_state(mp);
@@ -201,6 +214,17 @@ int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint
         uint32_t j = coder_of(i, N);
         uint32_t s = sym[i];
         if (s >= mp->n || mp->f[s] == 0) { rc = ORC_ERR_SYMBOL; break; }
+        uint32_t nr = r ? r[s] : 0;
+        if (nr > raw_end) { rc = ORC_ERR_ARG; break; }
+        raw_end -= nr;
+#if ORACLE_MUTANT != 9
+        /* Raw digits first: the decoder reads them after decoding s_i. */
+        for (uint32_t k = nr; k-- > 0;) {
+            if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+            if (raw[raw_end + k] >= (uint64_t)mp->b) { rc = ORC_ERR_ARG; goto done; }
+            words[W++] = raw[raw_end + k];
+        }
+#endif
         uint32_t iters = 0;
         /* Algorithm 1, Encode: renormalize while C(s,x) would leave I. */
         while (!in_I(mp, C(mp, s, x[j]))) {
@@ -219,7 +243,15 @@ int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint
         trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
         if (!in_I(mp, x[j])) { rc = ORC_ERR_INVARIANT; goto done; }
         if (iters > worst) worst = iters;
+#if ORACLE_MUTANT == 9
+        /* planted mistake: raw digits sent after the symbol is encoded */
+        for (uint32_t k = nr; k-- > 0;) {
+            if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+            words[W++] = raw[raw_end + k];
+        }
+#endif
     }
+    if (rc == ORC_OK && raw_end != 0) rc = ORC_ERR_ARG;   /* raw digits left over */
 done:
     if (rc == ORC_OK) {
 #if ORACLE_MUTANT != 5
@@ -240,18 +272,45 @@ done:
     return rc;
 }
 
+int orc_encode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+               const uint32_t *sym, uint64_t n_sym,
+               uint64_t *words, uint64_t word_cap, uint64_t *n_words,
+               uint64_t *states,
+               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+               uint64_t *n_trace, uint32_t *max_iters)
+{
+    return encode_impl(f, n_alpha, L, b, N, sym, n_sym, NULL, NULL, 0, words, word_cap, n_words,
+                       states, trace_state, trace_lane, trace_cap, n_trace, max_iters);
+}
+
+int orc_encode_bypass(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                      const uint32_t *sym, uint64_t n_sym, const uint32_t *r,
+                      const uint64_t *raw, uint64_t n_raw,
+                      uint64_t *words, uint64_t word_cap, uint64_t *n_words, uint64_t *states,
+                      uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+                      uint64_t *n_trace)
+{
+    if (!r) return ORC_ERR_ARG;
+    return encode_impl(f, n_alpha, L, b, N, sym, n_sym, r, raw, n_raw, words, word_cap, n_words,
+                       states, trace_state, trace_lane, trace_cap, n_trace, NULL);
+}
+
 /*
  * Decode n_sym symbols.  Coder (i mod N) runs Decode of Algorithm 1 for
  * symbol i, all coders reading the one shared word buffer in order
- * (Section 3).  states_in are the transmitted final encoder states.
- * consumed: words read.  states_out: coder states at the end (equal to the
- * encoder's initial states for a well-formed stream).
+ * (Section 3); with r given, the r[s_i] raw digits of symbol i are read
+ * right after it (Section 3, bypass) into raw_out (message order).
+ * states_in are the transmitted final encoder states.  consumed: words
+ * read.  states_out: coder states at the end (equal to the encoder's initial
+ * states for a well-formed stream).
  */
-int orc_decode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
-               const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
-               uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed, uint64_t *states_out,
-               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
-               uint64_t *n_trace, uint32_t *max_iters)
+static int decode_impl(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                       const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+                       uint64_t n_sym, const uint32_t *r, uint32_t *sym_out,
+                       uint64_t *raw_out, uint64_t raw_cap, uint64_t *n_raw_out,
+                       uint64_t *consumed, uint64_t *states_out,
+                       uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+                       uint64_t *n_trace, uint32_t *max_iters)
 {
     orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
     if (!mp) return ORC_ERR_ARG;
@@ -260,7 +319,7 @@ int orc_decode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint
     u128 *x = (u128 *)malloc(sizeof(u128) * N);
     if (!x) { free(mp); return ORC_ERR_ARG; }
 
-    uint64_t nt = 0, rp = 0;
+    uint64_t nt = 0, rp = 0, nr_out = 0;
     uint32_t worst = 0;
     for (uint32_t j = 0; j < N; ++j) {
         x[j] = states_in[j];
@@ -283,15 +342,46 @@ int orc_decode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint
             trace_push(trace_state, trace_lane, trace_cap, &nt, j, x[j]);
         }
         if (iters > worst) worst = iters;
+        for (uint32_t k = 0; r && k < r[s]; ++k) {
+            if (rp >= n_words) { rc = ORC_ERR_CORRUPT; goto out; }
+            if (nr_out >= raw_cap) { rc = ORC_ERR_SPACE; goto out; }
+            raw_out[nr_out++] = words[rp++];
+        }
     }
     for (uint32_t j = 0; j < N; ++j) states_out[j] = (uint64_t)x[j];
     *consumed = rp;
+    if (n_raw_out) *n_raw_out = nr_out;
     if (n_trace) *n_trace = nt;
     if (max_iters) *max_iters = worst;
 out:
     free(x);
     free(mp);
     return rc;
+}
+
+int orc_decode(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+               const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+               uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed, uint64_t *states_out,
+               uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+               uint64_t *n_trace, uint32_t *max_iters)
+{
+    return decode_impl(f, n_alpha, L, b, N, words, n_words, states_in, n_sym, NULL, sym_out,
+                       NULL, 0, NULL, consumed, states_out, trace_state, trace_lane, trace_cap,
+                       n_trace, max_iters);
+}
+
+int orc_decode_bypass(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                      const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+                      uint64_t n_sym, const uint32_t *r, uint32_t *sym_out,
+                      uint64_t *raw_out, uint64_t raw_cap, uint64_t *n_raw_out,
+                      uint64_t *consumed, uint64_t *states_out,
+                      uint64_t *trace_state, uint32_t *trace_lane, uint64_t trace_cap,
+                      uint64_t *n_trace)
+{
+    if (!r) return ORC_ERR_ARG;
+    return decode_impl(f, n_alpha, L, b, N, words, n_words, states_in, n_sym, r, sym_out,
+                       raw_out, raw_cap, n_raw_out, consumed, states_out, trace_state,
+                       trace_lane, trace_cap, n_trace, NULL);
 }
 
 /* Single coding-function evaluations, for checking the oracle against the
@@ -337,6 +427,7 @@ uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out,
 
 #define ORC_MAGIC 0x534E4152u
 #define ORC_VERSION 1u
+#define ORC_VERSION_BYPASS 2u  /* messages with raw words (Section 3, bypass) */
 #define ORC_L (1ull << 16)
 #define ORC_B (1ull << 16)
 #define ORC_LOG2_M 12u
@@ -362,29 +453,59 @@ static int prod_table(const uint16_t *freq, uint32_t n_alpha, uint64_t *f64)
 }
 
 /* Worst case: one word per symbol, since b >= M allows at most one
- * renormalization per symbol (Section 5). */
-uint64_t orc_max_message_size(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols)
+ * renormalization per symbol (Section 5); with raw words, one more word per
+ * symbol at most. */
+static uint64_t max_size(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols, uint64_t per_sym)
 {
     if (chunk_symbols == 0 || N == 0) return 0;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
-    return round16(32 + 4 * (n_chunks + 1)) + round16(4ull * N * n_chunks + 2ull * n_sym);
+    return round16(32 + 4 * (n_chunks + 1)) + round16(4ull * N * n_chunks + per_sym * n_sym);
+}
+uint64_t orc_max_message_size(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols)
+{
+    return max_size(n_sym, N, chunk_symbols, 2);
+}
+uint64_t orc_max_message_size_bypass(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols)
+{
+    return max_size(n_sym, N, chunk_symbols, 4);
 }
 
-/* One chunk: [u32 state[N]][u16 words in decoder order]. */
-int orc_encode_chunk(const uint8_t *sym, uint64_t n_c, const uint16_t *freq, uint32_t n_alpha,
-                     uint32_t N, uint8_t *out, uint64_t cap, uint64_t *size)
+/* Raw-word flags of a bypass model: rawf[s] in {0, 1} is the number of raw
+ * 16-bit words symbol s carries (one base-2^16 digit at most). */
+static int raw_counts(const uint8_t *rawf, uint32_t n_alpha, uint32_t *r)
+{
+    for (uint32_t s = 0; s < n_alpha; ++s) {
+        if (rawf[s] > 1) return ORC_ERR_ARG;
+        r[s] = rawf[s];
+    }
+    return ORC_OK;
+}
+
+/* One chunk: [u32 state[N]][u16 words in decoder order].  rawf != NULL: a
+ * bypass chunk, symbol i followed by raw16[i] when rawf[sym[i]] = 1. */
+static int chunk_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_c,
+                        const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
+                        uint8_t *out, uint64_t cap, uint64_t *size)
 {
     uint64_t f64[256];
+    uint32_t r[256];
     if (N == 0 || N > 32) return ORC_ERR_ARG;
     int rc = prod_table(freq, n_alpha, f64);
+    if (!rc && rawf) rc = raw_counts(rawf, n_alpha, r);
     if (rc) return rc;
+    uint64_t cap_w = 3 * (n_c ? n_c : 1);
     uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
-    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1) * 2);
-    if (!s32 || !w) { free(s32); free(w); return ORC_ERR_ARG; }
-    for (uint64_t i = 0; i < n_c; ++i) s32[i] = sym[i];
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * cap_w);
+    uint64_t *raw = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1));
+    if (!s32 || !w || !raw) { free(s32); free(w); free(raw); return ORC_ERR_ARG; }
+    uint64_t n_raw = 0;
+    for (uint64_t i = 0; i < n_c; ++i) {
+        s32[i] = sym[i];
+        if (rawf && sym[i] < n_alpha && r[sym[i]]) raw[n_raw++] = raw16[i];
+    }
     uint64_t st[32], W = 0;
-    rc = orc_encode(f64, n_alpha, ORC_L, ORC_B, N, s32, n_c, w, 2 * (n_c ? n_c : 1), &W, st,
-                    NULL, NULL, 0, NULL, NULL);
+    rc = encode_impl(f64, n_alpha, ORC_L, ORC_B, N, s32, n_c, rawf ? r : NULL, raw, n_raw, w,
+                     cap_w, &W, st, NULL, NULL, 0, NULL, NULL);
     if (rc == ORC_OK) {
         uint64_t need = 4ull * N + 2ull * W;
         if (need > cap) rc = ORC_ERR_SPACE;
@@ -396,42 +517,79 @@ int orc_encode_chunk(const uint8_t *sym, uint64_t n_c, const uint16_t *freq, uin
     }
     free(s32);
     free(w);
+    free(raw);
     return rc;
 }
 
-int orc_decode_chunk(const uint8_t *chunk, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
-                     uint32_t N, uint8_t *sym_out, uint64_t n_c)
+/* raw_out[i] = the raw word of symbol i, or 0 for a symbol without one. */
+static int chunk_decode(const uint8_t *chunk, uint64_t size, const uint16_t *freq,
+                        const uint8_t *rawf, uint32_t n_alpha, uint32_t N, uint8_t *sym_out,
+                        uint16_t *raw_out, uint64_t n_c)
 {
     uint64_t f64[256];
+    uint32_t r[256];
     if (N == 0 || N > 32) return ORC_ERR_ARG;
     int rc = prod_table(freq, n_alpha, f64);
+    if (!rc && rawf) rc = raw_counts(rawf, n_alpha, r);
     if (rc) return rc;
     if (size < 4ull * N || ((size - 4ull * N) & 1)) return ORC_ERR_CORRUPT;
     uint64_t W = (size - 4ull * N) / 2;
-    uint64_t st[32], st_end[32], used = 0;
+    uint64_t st[32], st_end[32], used = 0, n_raw = 0;
     for (uint32_t j = 0; j < N; ++j) st[j] = get_u32(chunk + 4 * j);
     uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (W ? W : 1));
     uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
-    if (!w || !s32) { free(w); free(s32); return ORC_ERR_ARG; }
+    uint64_t *raw = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1));
+    if (!w || !s32 || !raw) { free(w); free(s32); free(raw); return ORC_ERR_ARG; }
     for (uint64_t k = 0; k < W; ++k) w[k] = get_u16(chunk + 4ull * N + 2 * k);
-    rc = orc_decode(f64, n_alpha, ORC_L, ORC_B, N, w, W, st, n_c, s32, &used, st_end,
-                    NULL, NULL, 0, NULL, NULL);
+    rc = decode_impl(f64, n_alpha, ORC_L, ORC_B, N, w, W, st, n_c, rawf ? r : NULL, s32, raw,
+                     n_c ? n_c : 1, &n_raw, &used, st_end, NULL, NULL, 0, NULL, NULL);
     if (rc == ORC_OK) {
         /* A well-formed chunk ends with every coder back at x0 = L and every
          * word consumed (the decoder unwinds the encoder exactly, Section 3). */
         for (uint32_t j = 0; j < N; ++j)
             if (st_end[j] != ORC_L) rc = ORC_ERR_CORRUPT;
         if (used != W) rc = ORC_ERR_CORRUPT;
-        for (uint64_t i = 0; i < n_c; ++i) sym_out[i] = (uint8_t)s32[i];
+        uint64_t k = 0;
+        for (uint64_t i = 0; i < n_c; ++i) {
+            sym_out[i] = (uint8_t)s32[i];
+            if (raw_out) raw_out[i] = (rawf && r[s32[i]]) ? (uint16_t)raw[k++] : 0;
+        }
     }
     free(w);
     free(s32);
+    free(raw);
     return rc;
 }
 
-int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq, uint32_t n_alpha,
-                       uint32_t N, uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
-                       uint64_t *size)
+int orc_encode_chunk(const uint8_t *sym, uint64_t n_c, const uint16_t *freq, uint32_t n_alpha,
+                     uint32_t N, uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    return chunk_encode(sym, NULL, n_c, freq, NULL, n_alpha, N, out, cap, size);
+}
+int orc_decode_chunk(const uint8_t *chunk, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
+                     uint32_t N, uint8_t *sym_out, uint64_t n_c)
+{
+    return chunk_decode(chunk, size, freq, NULL, n_alpha, N, sym_out, NULL, n_c);
+}
+int orc_encode_chunk_bypass(const uint8_t *sym, const uint16_t *raw16, uint64_t n_c,
+                            const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha,
+                            uint32_t N, uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    if (!rawf || !raw16) return ORC_ERR_ARG;
+    return chunk_encode(sym, raw16, n_c, freq, rawf, n_alpha, N, out, cap, size);
+}
+int orc_decode_chunk_bypass(const uint8_t *chunk, uint64_t size, const uint16_t *freq,
+                            const uint8_t *rawf, uint32_t n_alpha, uint32_t N, uint8_t *sym_out,
+                            uint16_t *raw_out, uint64_t n_c)
+{
+    if (!rawf || !raw_out) return ORC_ERR_ARG;
+    return chunk_decode(chunk, size, freq, rawf, n_alpha, N, sym_out, raw_out, n_c);
+}
+
+/* Message = header + offsets + chunks; version 2 marks a bypass message. */
+static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
+                          const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
+                          uint32_t chunk_symbols, uint8_t *out, uint64_t cap, uint64_t *size)
 {
     if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
@@ -440,7 +598,7 @@ int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
     if (cap < data0) return ORC_ERR_SPACE;
     memset(out, 0, data0);
     put_u32(out + 0, ORC_MAGIC);
-    put_u32(out + 4, ORC_VERSION);
+    put_u32(out + 4, rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
     put_u32(out + 8, N);
     put_u32(out + 12, ORC_LOG2_M);
     put_u32(out + 16, (uint32_t)n_sym);
@@ -455,8 +613,8 @@ int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
         put_u32(out + 32 + 4 * c, (uint32_t)pos);
         uint64_t sz = 0;
         if (data0 + pos > cap) return ORC_ERR_SPACE;
-        int rc = orc_encode_chunk(sym + first, n_c, freq, n_alpha, N, out + data0 + pos,
-                                  cap - data0 - pos, &sz);
+        int rc = chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq, rawf, n_alpha,
+                              N, out + data0 + pos, cap - data0 - pos, &sz);
         if (rc) return rc;
         pos += sz;
     }
@@ -469,16 +627,18 @@ int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
     return ORC_OK;
 }
 
-int orc_decode_message(const uint8_t *msg, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
-                       uint32_t N, uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
+static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *freq,
+                          const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
+                          uint32_t chunk_symbols, uint8_t *sym_out, uint16_t *raw_out,
+                          uint64_t n_sym)
 {
     if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
     if (size < 48 || (size & 15)) return ORC_ERR_CORRUPT;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
     uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
-    if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != ORC_VERSION || get_u32(msg + 8) != N ||
-        get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym || get_u32(msg + 24) != chunk_symbols ||
-        get_u32(msg + 28) != n_chunks)
+    if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != (rawf ? ORC_VERSION_BYPASS : ORC_VERSION) ||
+        get_u32(msg + 8) != N || get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym ||
+        get_u32(msg + 24) != chunk_symbols || get_u32(msg + 28) != n_chunks)
         return ORC_ERR_CORRUPT;
     uint64_t data0 = round16(32 + 4 * (n_chunks + 1));
     if (data0 > size) return ORC_ERR_CORRUPT;
@@ -492,10 +652,40 @@ int orc_decode_message(const uint8_t *msg, uint64_t size, const uint16_t *freq, 
         uint64_t first = c * chunk_symbols;
         uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
         if (z < a || z > end_all) return ORC_ERR_CORRUPT;
-        int rc = orc_decode_chunk(msg + data0 + a, z - a, freq, n_alpha, N, sym_out + first, n_c);
+        int rc = chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N, sym_out + first,
+                              raw_out ? raw_out + first : NULL, n_c);
         if (rc && !rc_all) rc_all = rc;
     }
     return rc_all;
+}
+
+int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq, uint32_t n_alpha,
+                       uint32_t N, uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
+                       uint64_t *size)
+{
+    return message_encode(sym, NULL, n_sym, freq, NULL, n_alpha, N, chunk_symbols, out, cap, size);
+}
+int orc_decode_message(const uint8_t *msg, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
+                       uint32_t N, uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
+{
+    return message_decode(msg, size, freq, NULL, n_alpha, N, chunk_symbols, sym_out, NULL, n_sym);
+}
+int orc_encode_message_bypass(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
+                              const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha,
+                              uint32_t N, uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
+                              uint64_t *size)
+{
+    if (!rawf || !raw16) return ORC_ERR_ARG;
+    return message_encode(sym, raw16, n_sym, freq, rawf, n_alpha, N, chunk_symbols, out, cap, size);
+}
+int orc_decode_message_bypass(const uint8_t *msg, uint64_t size, const uint16_t *freq,
+                              const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
+                              uint32_t chunk_symbols, uint8_t *sym_out, uint16_t *raw_out,
+                              uint64_t n_sym)
+{
+    if (!rawf || !raw_out) return ORC_ERR_ARG;
+    return message_decode(msg, size, freq, rawf, n_alpha, N, chunk_symbols, sym_out, raw_out,
+                          n_sym);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -505,11 +505,100 @@ def pin_quantize(o):
         assert np.array_equal(g, f)
 
 
+# ----------------------------------------------------------------------------
+# Bypass: raw digits interleaved with the coded symbols (Section 3)
+# ----------------------------------------------------------------------------
+
+def pin_bypass_paper_example(o):
+    """The paper's bypass example: each a of "babba" carries two raw bits
+    (its subtype), sent before the a is encoded and read right after it is
+    decoded.  The bits sit in the stream exactly where the plain decoder has
+    just finished the a (state 30 for the first one), and no coder state
+    changes: the state traces with and without the raw bits are equal."""
+    L, b = int(PAPER["L"][0]), int(PAPER["b"][0])
+    nbits = int(PAPER["bypass_bits_per_a"][0])
+    msg = _paper_message()
+    counts = [nbits, 0]
+    subtypes = [[1, 0], [1, 1]]                       # a_2 and a_3, first bit first
+    raw = [bit for st in subtypes for bit in st]
+    plain = o.encode(PAPER_FREQ, msg, N=1, L=L, b=b, trace=True)
+    byp = o.encode_bypass(PAPER_FREQ, msg, counts, raw, N=1, L=L, b=b, trace=True)
+    assert list(byp["trace_state"]) == list(plain["trace_state"])
+    assert list(byp["states"]) == list(plain["states"])
+    # where the plain decoder stands after each a
+    a_at = [i for i, c in enumerate(msg) if c == PAPER_SYM["a"]]
+    cut = [o.decode(PAPER_FREQ, plain["words"], plain["states"], i + 1, N=1, L=L, b=b)["consumed"]
+           for i in a_at]
+    first = o.decode(PAPER_FREQ, plain["words"], plain["states"], a_at[0] + 1, N=1, L=L, b=b)
+    assert int(first["states_end"][0]) == int(PAPER["state_after_first_a"][0])
+    w, expect, prev = list(plain["words"]), [], 0
+    for c, st in zip(cut, subtypes):
+        expect += w[prev:c] + st
+        prev = c
+    expect += w[prev:]
+    assert list(byp["words"]) == expect
+    dec = o.decode_bypass(PAPER_FREQ, byp["words"], byp["states"], len(msg), counts, N=1, L=L,
+                          b=b, trace=True)
+    assert list(dec["symbols"]) == msg and list(dec["raw"]) == raw
+    assert dec["consumed"] == len(expect) and int(dec["states_end"][0]) == L
+    assert list(dec["trace_state"]) == list(plain["trace_state"][::-1])
+
+
+def pin_bypass_without_raw_is_plain(o):
+    """No symbol carries raw digits: the bypass coder is the plain coder, and
+    a bypass message differs from the plain one only in its version field."""
+    rng = np.random.default_rng(11)
+    for N in (1, 5, 32):
+        freq = o.quantize(np.maximum(1, rng.integers(0, 1000, size=40)).astype(np.uint64))
+        msg = rng.choice(40, size=777, p=freq / freq.sum())
+        plain = o.encode(freq, msg, N=N)
+        byp = o.encode_bypass(freq, msg, np.zeros(40, np.uint32), [], N=N)
+        assert np.array_equal(plain["words"], byp["words"])
+        assert np.array_equal(plain["states"], byp["states"])
+        m_plain = o.encode_message(msg.astype(np.uint8), freq, N=N, chunk_symbols=300)
+        m_byp = o.encode_message_bypass(msg.astype(np.uint8), np.zeros(777, np.uint16), freq,
+                                        np.zeros(40, np.uint8), N=N, chunk_symbols=300)
+        assert m_plain.size == m_byp.size
+        diff = np.nonzero(m_plain != m_byp)[0]
+        assert list(diff) == [4], diff                 # version 1 -> 2
+        assert m_byp[4] == 2 and m_plain[4] == 1
+
+
+def pin_bypass_interleaved(o):
+    """Production parameters, N interleaved coders, random raw-word flags:
+    the raw words change no coder state (same encoder trace as without
+    them), add exactly one word each, and decode back, words and symbols."""
+    rng = np.random.default_rng(13)
+    for N, n in ((1, 50), (3, 401), (32, 3000), (32, 31)):
+        k = int(rng.integers(2, 60))
+        freq = o.quantize(np.maximum(1, rng.integers(0, 1000, size=k)).astype(np.uint64))
+        flags = (rng.random(k) < 0.5).astype(np.uint32)
+        msg = rng.choice(k, size=n, p=freq / freq.sum())
+        raw = rng.integers(0, 1 << 16, size=int(flags[msg].sum()))
+        plain = o.encode(freq, msg, N=N, trace=True)
+        byp = o.encode_bypass(freq, msg, flags, raw, N=N, trace=True)
+        assert np.array_equal(plain["trace_state"], byp["trace_state"])
+        assert byp["words"].size == plain["words"].size + raw.size
+        dec = o.decode_bypass(freq, byp["words"], byp["states"], n, flags, N=N)
+        assert np.array_equal(dec["symbols"], msg) and np.array_equal(dec["raw"], raw)
+        assert dec["consumed"] == byp["words"].size
+        assert all(int(v) == L16 for v in dec["states_end"])
+        # container: per-position raw words, zero where a symbol has none
+        r16 = np.zeros(n, np.uint16)
+        r16[flags[msg] == 1] = raw
+        m = o.encode_message_bypass(msg.astype(np.uint8), r16, freq, flags.astype(np.uint8), N=N,
+                                    chunk_symbols=200)
+        sym2, raw2 = o.decode_message_bypass(m, n, freq, flags.astype(np.uint8), N=N,
+                                             chunk_symbols=200)
+        assert np.array_equal(sym2, msg) and np.array_equal(raw2, r16)
+
+
 ALL_PINS = [
     pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
     pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
     pin_one_renorm_production, pin_uniform_closed_form, pin_single_symbol,
     pin_infinite_precision_paper, pin_infinite_precision_general, pin_size_bound,
     pin_brute_force_unique, pin_packed_io_equivalence, pin_round_trip_edges,
-    pin_container_layout, pin_quantize,
+    pin_container_layout, pin_quantize, pin_bypass_paper_example,
+    pin_bypass_without_raw_is_plain, pin_bypass_interleaved,
 ]

@@ -5,13 +5,14 @@ The mutants are compiled from the same source with -DORACLE_MUTANT=k:
   3 emits floor(x/b), not x mod b   4 assigns symbol i to coder (i+1) mod N
   5 leaves the words in emission order   6 starts the coders at L+1
   7 off-by-one symbol search in D        8 quantizer ties go to the higher index
+  9 sends a symbol's raw (bypass) digits after encoding it, not before
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTANTS = range(1, 9)
+MUTANTS = range(1, 10)
 
 
 @pytest.mark.parametrize("k", MUTANTS)
