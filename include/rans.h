@@ -80,6 +80,7 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_MAX_LANES     32
 #define RANS_MAGIC         0x534E4152u
 #define RANS_VERSION       1u
+#define RANS_VERSION_BYPASS 2u         /* messages with raw words (rans_encode_bypass) */
 
 typedef struct {
     uint32_t n_lanes;        /* N interleaved coders per chunk, 1..32 */
@@ -190,6 +191,45 @@ int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const uint16_t *h_
                      uint32_t n_alpha, const rans_params *params, uint8_t *h_symbols,
                      uint64_t n_symbols, uint32_t *h_status, void *d_work, uint64_t work_cap,
                      rans_stream_t stream);
+
+/*
+ * Bypass (raw) words interleaved with the coded symbols -- Section 3 of the
+ * paper (bypass coding): because encoder and decoder run in lockstep, raw
+ * data can be written into the same stream at agreed points with no
+ * metadata and no coder state change.  Here the agreed point is a per-symbol
+ * flag of the model: raw_words[s] in {0, 1} is the number of raw 16-bit
+ * words symbol s carries.  The encoder sends a symbol's raw word right before
+ * it encodes the symbol; the decoder reads it right after it has decoded the
+ * symbol and renormalized.  Within a step of N coders, each coder's
+ * renormalization word is followed by its raw word, coders in order.
+ * A bypass message is a version-2 container (RANS_VERSION_BYPASS); the model
+ * (frequencies and raw_words) is not stored in it.
+ *
+ * rans_encode_bypass -- as rans_encode, plus:
+ *   d_raw       : device, n_symbols u16 (2-byte aligned): d_raw[i] is sent
+ *                 after symbol i when h_raw_words[symbol i] == 1, ignored
+ *                 otherwise.
+ *   h_raw_words : host, n_alpha bytes, each 0 or 1.
+ *   out_cap     : >= rans_max_encoded_size_bypass(n_symbols, params).
+ *   scratch_cap : >= rans_encode_scratch_size_bypass(n_symbols, params).
+ * rans_decode_bypass -- as rans_decode, plus:
+ *   h_raw_words : as above (must equal the encoder's).
+ *   d_raw       : device, n_symbols u16 (2-byte aligned): d_raw[i] = the raw
+ *                 word after symbol i, or 0 when its symbol carries none.
+ * A bypass message is decoded with one chunk per warp.  Messages of one kind
+ * given to the other kind's decoder are reported RANS_ERR_CORRUPT (version).
+ */
+uint64_t rans_max_encoded_size_bypass(uint64_t n_symbols, const rans_params *params);
+uint64_t rans_encode_scratch_size_bypass(uint64_t n_symbols, const rans_params *params);
+int rans_encode_bypass(const uint8_t *d_symbols, const uint16_t *d_raw, uint64_t n_symbols,
+                       const uint16_t *h_freq, const uint8_t *h_raw_words, uint32_t n_alpha,
+                       const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                       uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                       uint64_t scratch_cap, rans_stream_t stream);
+int rans_decode_bypass(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                       const uint8_t *h_raw_words, uint32_t n_alpha, const rans_params *params,
+                       uint8_t *d_symbols, uint16_t *d_raw, uint64_t n_symbols,
+                       uint32_t *d_status, rans_stream_t stream);
 
 /*
  * Batched decoding: many independent messages ("streams"), each with its own

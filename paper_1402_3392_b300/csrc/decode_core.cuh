@@ -34,39 +34,46 @@ constexpr uint32_t kWarpRing = 4096;      // ring bytes per warp (4 KiB aligned)
 constexpr uint32_t kNSeg = 4;             // ring segments (and mbarriers) per chunk
 
 // Ring geometry of one chunk in flight: a ring of NSEG segments of SEG bytes,
-// checked every GROUP steps.  A step reads at most 32 words = 64 bytes, so a
-// group reads at most GROUP * 64 bytes.  Ring event k (due once the read
-// position rp reaches (k - NSEG + 1) * SEG) issues the copy of segment k into
-// the slot that segment k - NSEG has left, and waits for segment k - LAG.
-// After the events due at rp, the segments up to floor(rp / SEG) + NSEG - 1 -
-// LAG are in: enough for the next group when LAG <= NSEG - 1 - ceil(GROUP *
-// 64 / SEG).  A copy is waited for LAG segments (LAG * SEG bytes of words)
-// after it is issued.
-template <uint32_t SEG, uint32_t NSEG, uint32_t GROUP>
+// checked every GROUP steps.  A step reads at most STEP bytes (32 words = 64
+// bytes; 128 with raw words, two words per lane), so a group reads at most
+// GROUP * STEP bytes.  Ring event k (due once the read position rp reaches
+// (k - NSEG + 1) * SEG) issues the copy of segment k into the slot that
+// segment k - NSEG has left, and waits for segment k - LAG.  After the events
+// due at rp, the segments up to floor(rp / SEG) + NSEG - 1 - LAG are in:
+// enough for the next group when LAG <= NSEG - 1 - ceil(GROUP * STEP / SEG).
+// A copy is waited for LAG segments (LAG * SEG bytes of words) after it is
+// issued.
+template <uint32_t SEG, uint32_t NSEG, uint32_t GROUP, uint32_t STEP = 64>
 struct Geometry {
     static constexpr uint32_t kSeg = SEG;
     static constexpr uint32_t kNSeg = NSEG;
     static constexpr uint32_t kRing = SEG * NSEG;
     static constexpr uint32_t kGroup = GROUP;
-    static constexpr uint32_t kLag = NSEG - 1 - (GROUP * 64 + SEG - 1) / SEG;
+    static constexpr uint32_t kLag = NSEG - 1 - (GROUP * STEP + SEG - 1) / SEG;
     static_assert((kRing & (kRing - 1)) == 0, "the ring is indexed by masking");
-    static_assert(NSEG - 1 >= (GROUP * 64 + SEG - 1) / SEG + 1, "a copy must be issued ahead of use");
+    static_assert(NSEG - 1 >= (GROUP * STEP + SEG - 1) / SEG + 1, "a copy must be issued ahead of use");
     static_assert(NSEG <= 32, "one phase bit per segment");
 };
 // One chunk per warp: the warp's whole 4 KiB as one ring, 1 KiB copies,
 // waited 2 KiB after issue.  Two chunks per warp: 2 KiB each, 512-byte
 // copies, waited 512 bytes after issue.  Copies are large because each one
-// costs the warp an issue, a wait and bookkeeping.
+// costs the warp an issue, a wait and bookkeeping.  With raw words (bypass
+// messages, one chunk per warp): 1 KiB copies waited 1 KiB after issue.
 using GeoOne = Geometry<1024, kNSeg, 16>;
 using GeoPair = Geometry<512, kNSeg, 16>;
-static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing, "ring sizes");
+using GeoRaw = Geometry<1024, kNSeg, 16, 128>;
+static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing &&
+                  GeoRaw::kRing == kWarpRing,
+              "ring sizes");
 
 constexpr uint32_t kTableBytes = kM * 4;
 // Shared memory: [slot table 16 KiB][alignment slack 4 KiB][4 KiB ring per
-// warp][kNSeg mbarriers per chunk slot][a few words of CTA state].
+// warp][kNSeg mbarriers per chunk slot][a few words of CTA state][256 raw-word
+// flags].
 constexpr uint32_t kBarOffset = kTableBytes + kWarpRing + kWarps * kWarpRing;
 constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
-constexpr uint32_t kSmemBytes = kMiscOffset + 64;
+constexpr uint32_t kFlagsOffset = kMiscOffset + 64;   // 256 raw-word flags (bypass)
+constexpr uint32_t kSmemBytes = kFlagsOffset + 256;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 
 struct Smem {
@@ -76,6 +83,8 @@ struct Smem {
     uint8_t *rings;     // generic pointer of rings_s
     uint64_t *bars;
     uint32_t *misc;     // CTA-shared words
+    uint8_t *flags;     // raw words per symbol (0 or 1), bypass messages
+    uint32_t flags_s;
 };
 
 __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
@@ -87,6 +96,8 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     s.rings = smem + kTableBytes + (s.rings_s - raw);
     s.bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
     s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
+    s.flags = smem + kFlagsOffset;
+    s.flags_s = smem_addr(smem + kFlagsOffset);
     return s;
 }
 
@@ -113,6 +124,11 @@ __device__ __forceinline__ uint32_t decode_update(uint32_t x, uint32_t e) {
 __device__ __forceinline__ uint32_t ld_table(uint32_t a) {
     uint32_t v;
     asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_flag(uint32_t a) {
+    uint32_t v;
+    asm("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ uint32_t ld_ring_u16(uint32_t a) {
@@ -243,6 +259,7 @@ __device__ __forceinline__ WarpRings rings_init(const Smem &sm, uint32_t warp, u
 struct Chain {
     const uint8_t *src;  // message + A: source of segment 0
     uint8_t *outp;       // where this lane's next symbol goes
+    uint16_t *rawp;      // where its next raw word goes (bypass messages)
     uint32_t x;          // this lane's coder state
     uint32_t rp;         // read position (warp-uniform)
     uint32_t evt;        // ring events done
@@ -258,6 +275,7 @@ struct Chain {
 __device__ __forceinline__ void chain_empty(Chain &c) {
     c.src = nullptr;
     c.outp = nullptr;
+    c.rawp = nullptr;
     c.x = kL;
     c.rp = c.evt = c.nseg = c.span = c.endrel = c.steps = c.rem = 0;
     c.next_evt = 0xFFFFFFFFu;
@@ -271,7 +289,7 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
 template <class G>
 __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
                                            uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,
-                                           uint8_t *out, uint32_t lane) {
+                                           uint8_t *out, uint16_t *raw_out, uint32_t lane) {
     chain_empty(c);
     // Offsets must be even (states and words are 2-byte aligned) and in range.
     if (((o | e) & 1u) || e < o || e > data_end || e - o < 4 * N || e - o > 0xFFFFFF00u) {
@@ -295,6 +313,7 @@ __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_
     c.rp = uint32_t(P0 - A);
     c.next_evt = 0;
     c.outp = out + lane;
+    c.rawp = raw_out ? raw_out + lane : nullptr;
     c.steps = n_c / N;
     c.rem = n_c % N;
 }
@@ -377,26 +396,70 @@ __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32
     rpb = imad(__popc(mb), 2u, rpb);
 }
 
-// Decode what is left of one chunk on its own.
-template <bool FULL, class G>
+// One step of a bypass chunk (Section 3): as decode_step, and then every
+// lane whose symbol carries a raw word reads it right after its own
+// renormalization word; one prefix over the lanes places both kinds of word
+// in lane order.  The raw word, or 0 for a symbol without one, goes to *rawp.
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step_raw(uint32_t &x, uint32_t &rp, bool active,
+                                                uint32_t tab_s, uint32_t ring_s, uint32_t flags_s,
+                                                uint8_t *outp, uint16_t *rawp, uint32_t lt) {
+    const uint32_t e = ld_table(imad(x & (kM - 1), 4u, tab_s));
+    const bool on = FULL || active;
+    const uint32_t fl = ld_flag(flags_s + (e & 0xFFu));
+    if (on) {
+        x = decode_update(x, e);
+        *outp = uint8_t(e);
+    }
+    const bool need = on && x < kL;
+    const bool has = on && fl != 0u;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t mr = __ballot_sync(kFull, has);
+    const uint32_t pos = imad(__popc(m & lt) + __popc(mr & lt), 2u, rp);
+    const uint32_t w = ld_ring_u16((pos & (RING - 1)) | ring_s);
+    const uint32_t rw = ld_ring_u16((imad(uint32_t(need), 2u, pos) & (RING - 1)) | ring_s);
+    if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
+    if (on) *rawp = uint16_t(has ? rw : 0u);
+    rp = imad(__popc(m) + __popc(mr), 2u, rp);
+}
+
+// Decode what is left of one chunk on its own.  RAW: a bypass chunk.
+template <bool FULL, class G, bool RAW = false>
 __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &timeouts, uint32_t N,
-                                          bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt) {
+                                          bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt,
+                                          uint32_t flags_s = 0) {
     for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
         chain_service<G>(c, r, timeouts, lane);
 #pragma unroll
-        for (uint32_t u = 0; u < G::kGroup; ++u)
-            decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N, lt);
+        for (uint32_t u = 0; u < G::kGroup; ++u) {
+            if (RAW)
+                decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s,
+                                                c.outp + u * N, c.rawp + u * N, lt);
+            else
+                decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N,
+                                            lt);
+        }
         c.outp += G::kGroup * N;
+        if (RAW) c.rawp += G::kGroup * N;
     }
     for (uint32_t t = c.steps % G::kGroup; t > 0; --t) {
         chain_service<G>(c, r, timeouts, lane);
-        decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
+        if (RAW)
+            decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s, c.outp,
+                                            c.rawp, lt);
+        else
+            decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
         c.outp += N;
+        if (RAW) c.rawp += N;
     }
     c.steps = 0;
     if (c.rem) {
         chain_service<G>(c, r, timeouts, lane);
-        decode_step<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
+        if (RAW)
+            decode_step_raw<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, flags_s,
+                                             c.outp, c.rawp, lt);
+        else
+            decode_step<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
         c.rem = 0;
     }
 }
@@ -431,21 +494,46 @@ __device__ __forceinline__ uint32_t const_chunk(const uint8_t *msg, uint32_t dat
     return __all_sync(kFull, x == kL) ? RANS_OK : RANS_ERR_CORRUPT;
 }
 
+// const_chunk for a bypass message: when the one symbol carries a raw word,
+// the chunk is the N states followed by one raw word per symbol, in order.
+__device__ __forceinline__ uint32_t const_chunk_raw(const uint8_t *msg, uint32_t data0, uint32_t o,
+                                                    uint32_t e, uint32_t data_end, uint32_t n_c,
+                                                    uint32_t N, uint8_t *out, uint16_t *raw_out,
+                                                    uint32_t const_sym, bool has_raw,
+                                                    uint32_t lane) {
+    const uint64_t words = has_raw ? n_c : 0u;
+    if (((o | e) & 1u) || e < o || e > data_end || uint64_t(e - o) != 4ull * N + 2 * words)
+        return RANS_ERR_CORRUPT;
+    const uint8_t *chunk = msg + data0 + o;
+    uint32_t x = kL;
+    if (lane < N) x = ld_u16_global(chunk + 4 * lane) | (ld_u16_global(chunk + 4 * lane + 2) << 16);
+    for (uint32_t i = lane; i < n_c; i += 32) {
+        out[i] = uint8_t(const_sym);
+        raw_out[i] = has_raw ? uint16_t(ld_u16_global(chunk + 4 * N + 2 * i)) : uint16_t(0);
+    }
+    return __all_sync(kFull, x == kL) ? RANS_OK : RANS_ERR_CORRUPT;
+}
+
 // Decode chunks c .. c + count - 1 (count = 1, or 2 when PAIR) of a message
 // (offsets table offs, data region at msg + data0, data_end = offs[n_chunks])
 // of n_sym symbols in chunks of CS with N coders; chunk k's symbols go to
 // out + k*CS.  PAIR: the warp's two 2 KiB rings, the two chunks' steps
-// interleaved; otherwise one chunk in the warp's 4 KiB ring.  const_sym !=
+// interleaved; otherwise one chunk in the warp's 4 KiB ring.  RAW: a bypass
+// message (one chunk per warp); symbol i's raw word, or 0, goes to
+// raw_out[i] and flags_s addresses the 256 raw-word flags.  const_sym !=
 // kNoConst: the model has one symbol with f = M.  Returns the warp-uniform
 // status (RANS_OK, or the first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
-template <int NT, bool PAIR>  // NT = 32: all 32 lanes are coders; NT = 0: runtime N
+template <int NT, bool PAIR, bool RAW = false>  // NT = 32: all lanes are coders; 0: runtime N
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
                                                   uint64_t n_sym, uint32_t CS, uint32_t N_rt,
                                                   uint8_t *out, uint32_t const_sym, uint32_t lane,
-                                                  uint32_t lt) {
-    using G = typename std::conditional<PAIR, GeoPair, GeoOne>::type;
+                                                  uint32_t lt, uint16_t *raw_out = nullptr,
+                                                  uint32_t flags_s = 0, bool const_raw = false) {
+    static_assert(!(PAIR && RAW), "bypass messages are decoded one chunk per warp");
+    using G = typename std::conditional<RAW, GeoRaw,
+                                        typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type;
     constexpr bool kFullWarp = NT == 32;
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;
@@ -456,6 +544,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = two ? offs[c + 2] : 0u;
 
     if (const_sym != kNoConst) {
+        if (RAW)
+            return const_chunk_raw(msg, data0, o0, o1, data_end, n_a, N, out + first,
+                                   raw_out + first, const_sym, const_raw, lane);
         uint32_t st = const_chunk(msg, data0, o0, o1, data_end, n_a, N, out + first, const_sym, lane);
         if (two) {
             const uint32_t sb =
@@ -466,8 +557,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     }
 
     Chain a, b;
-    chain_open<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
-    if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, lane);
+    chain_open<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
+                  RAW ? raw_out + first : nullptr, lane);
+    if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, nullptr, lane);
     else chain_empty(b);
 
     if (PAIR) {
@@ -487,7 +579,7 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
             b.outp += G::kGroup * N;
         }
     }
-    chain_run<kFullWarp, G>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt);
+    chain_run<kFullWarp, G, RAW>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
     if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
     const uint32_t sa = chain_close<G>(a, w.r[0], w.timeouts, lane_on);
     const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
@@ -498,10 +590,10 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
 // msg_size is the message size and data0 its data-region offset.
 __device__ __forceinline__ bool header_ok(const uint8_t *msg, uint64_t msg_size, uint32_t data0,
                                           uint64_t n_sym, uint32_t N, uint32_t CS,
-                                          uint32_t n_chunks) {
+                                          uint32_t n_chunks, uint32_t version = RANS_VERSION) {
     const uint32_t *h32 = reinterpret_cast<const uint32_t *>(msg);
     const uint64_t hn = uint64_t(h32[4]) | (uint64_t(h32[5]) << 32);
-    if (h32[0] != RANS_MAGIC || h32[1] != RANS_VERSION || h32[2] != N || h32[3] != kLog2M ||
+    if (h32[0] != RANS_MAGIC || h32[1] != version || h32[2] != N || h32[3] != kLog2M ||
         hn != n_sym || h32[6] != CS || h32[7] != n_chunks)
         return false;
     const uint32_t first = h32[8], last = h32[8 + n_chunks];

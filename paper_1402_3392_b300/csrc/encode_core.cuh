@@ -44,6 +44,7 @@ static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
 constexpr uint32_t kMiscOffset = 256 * 8 + kRing + kWarps * kRing;
 constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
+constexpr uint32_t kRawFlag = 1u << 18;   // encode-table bit: the symbol carries a raw word
 
 // Scratch of one message, all sections 16-byte aligned: one worst-case slot
 // of words per chunk (written backwards from its end), then the chunks'
@@ -53,9 +54,11 @@ struct ScratchLayout {
     uint32_t slot_bytes;
 };
 
-__host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint32_t N, uint32_t CS) {
+// words_per_symbol: 1, or 2 for bypass messages (a raw word after a symbol).
+__host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint32_t N, uint32_t CS,
+                                                        uint32_t words_per_symbol = 1) {
     ScratchLayout s{};
-    s.slot_bytes = uint32_t((2ull * CS + kSeg - 1) / kSeg * kSeg);
+    s.slot_bytes = uint32_t((2ull * words_per_symbol * CS + kSeg - 1) / kSeg * kSeg);
     s.words = 0;
     s.states = (n_chunks * s.slot_bytes + 16 + 15) & ~uint64_t(15);
     s.wstart = s.states + ((n_chunks * N * 4 + 15) & ~uint64_t(15));
@@ -92,8 +95,11 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
 // Emit test: x >= f * 2^20  <=>  x > f * 2^20 - 1 = ~((M - f) << 20)  (u32).
 // Built by the whole CTA; cum: 257 words of free shared memory.  Returns the
 // sum of the frequencies to every thread.
+// raw_words (bypass messages, may be null): symbol s carries raw_words[s]
+// (0 or 1) raw words; marked by kRawFlag in .y.
 __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq, uint2 *tab,
-                                                           uint32_t *cum) {
+                                                           uint32_t *cum,
+                                                           const uint8_t *raw_words = nullptr) {
     const uint32_t tid = threadIdx.x;
     if (tid < 32) {
         uint32_t v[8], run = 0;
@@ -124,6 +130,7 @@ __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq,
             const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
             t.x = uint32_t(m - (1ull << 32));
             t.y = ((kM - (f & (2 * kM - 1))) << 20) | (k << 12) | (cum[s] & (kM - 1));
+            if (raw_words && raw_words[s]) t.y |= kRawFlag;  // the shift uses k's 5 bits only
         }
         tab[s] = t;
     }
@@ -166,18 +173,55 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
     }
 }
 
+// One step of a bypass chunk (Section 3): a lane whose symbol carries a raw
+// word rw sends it before encoding the symbol, so in the stream (decoder
+// order) it follows that lane's renormalization word.  One reverse-lane
+// prefix over both kinds of word places them: the words of lanes >= j fill
+// [wp - 2A, wp), lane j's own at the bottom (renormalization word first).
+template <bool FULL>
+__device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint32_t &acc,
+                                                bool active, uint32_t s, uint32_t rw,
+                                                uint32_t tab_s, uint32_t ring_s, uint32_t ge) {
+    const uint2 t = ld_enc_table(tab_s + (s << 3));
+    const bool on = FULL || active;
+    if (on) acc |= t.y;
+    const bool emit = on && (x > ~(t.y & 0xFFF00000u));
+    const bool has = on && (t.y & kRawFlag) != 0u;
+    const uint32_t m = __ballot_sync(kFull, emit);
+    const uint32_t mr = __ballot_sync(kFull, has);
+    const uint32_t pos = wp - 2u * (__popc(m & ge) + __popc(mr & ge));
+    if (has) st_ring_u16(((pos + 2u * uint32_t(emit)) & (kRing - 1)) | ring_s, rw);
+    if (emit) {
+        st_ring_u16((pos & (kRing - 1)) | ring_s, x);
+        x >>= 16;
+    }
+    wp -= 2u * (__popc(m) + __popc(mr));
+    if (on) {
+        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
+        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
+    }
+}
+
 // Encode n_c symbols starting at sym with N coders into the worst-case slot
 // slot_base[0, slot_bytes).  Writes the chunk's first-word offset *wstart,
 // byte size *size and final states states[0..N).  acc collects the table
 // words of every symbol coded (kZeroFlag marks a symbol without probability).
-template <int NT, bool PREFETCH>  // PREFETCH: load the next group's symbols while coding this one
+// PREFETCH: load the next group's symbols while coding this one.  RAW: a
+// bypass chunk, raw[i] is the raw word of symbol i (used where the symbol
+// carries one); groups are halved so that a group still writes at most 1 KiB.
+template <int NT, bool PREFETCH, bool RAW = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
                                              uint32_t tab_s, uint32_t ring_s, uint32_t ge,
-                                             uint32_t lane, uint32_t &acc) {
+                                             uint32_t lane, uint32_t &acc,
+                                             const uint16_t *raw = nullptr) {
+    static_assert(!(RAW && PREFETCH), "bypass chunks load each group's symbols up front");
+    constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
+    const uint16_t *rawp = RAW ? raw + lane : nullptr;
     uint32_t x = kL;
     uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
     uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
@@ -209,13 +253,23 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     if (rem) {
         const bool act = lane < rem;
         const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
-        encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge);
+        if (RAW) {
+            const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
+            encode_step_raw<false>(x, wp, acc, act, s, rw, tab_s, ring_s, ge);
+        } else {
+            encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge);
+        }
     }
     int64_t t = int64_t(T_full) - 1;
-    for (uint32_t r = T_full % kGroup; r > 0; --r, --t) {
+    for (uint32_t r = T_full % kG; r > 0; --r, --t) {
         service();
         const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
-        encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
+        if (RAW) {
+            const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
+            encode_step_raw<NT == 32>(x, wp, acc, lane_on, s, rw, tab_s, ring_s, ge);
+        } else {
+            encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
+        }
     }
     if (PREFETCH) {
         // Groups of kGroup steps, symbols of the next group loaded ahead.
@@ -237,15 +291,23 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
         }
     } else {
-        // Groups of kGroup steps; a group's symbols are loaded together up front.
-        for (; t >= 0; t -= kGroup) {
-            uint32_t cur[kGroup];
+        // Groups of kG steps; a group's symbols are loaded together up front.
+        for (; t >= 0; t -= kG) {
+            uint32_t cur[kG], curw[kG];
 #pragma unroll
-            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+            for (uint32_t u = 0; u < kG; ++u) {
+                cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+                if (RAW) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : 0u;
+            }
             service();
 #pragma unroll
-            for (uint32_t u = 0; u < kGroup; ++u)
-                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+            for (uint32_t u = 0; u < kG; ++u) {
+                if (RAW)
+                    encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
+                                              ge);
+                else
+                    encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+            }
         }
     }
 
@@ -276,7 +338,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
 __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_size,
                                                  const uint32_t *sizes, uint64_t n_sym, uint32_t N,
                                                  uint32_t CS, uint32_t n_chunks, uint32_t data0,
-                                                 uint32_t *warp_sums, uint32_t *carry_s) {
+                                                 uint32_t *warp_sums, uint32_t *carry_s,
+                                                 uint32_t version = RANS_VERSION) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     uint32_t *offs = reinterpret_cast<uint32_t *>(out + 32);
     if (tid == 0) *carry_s = 0;
@@ -313,7 +376,7 @@ __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_siz
         const uint32_t total = *carry_s;
         uint32_t *h = reinterpret_cast<uint32_t *>(out);
         h[0] = RANS_MAGIC;
-        h[1] = RANS_VERSION;
+        h[1] = version;
         h[2] = N;
         h[3] = kLog2M;
         h[4] = uint32_t(n_sym);

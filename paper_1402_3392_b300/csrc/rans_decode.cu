@@ -29,10 +29,15 @@ struct DecodeParams {
     uint32_t c_begin;   // chunks [c_begin, c_end) are decoded by this launch
     uint32_t c_end;
     uint32_t per_warp;  // chunks a warp decodes side by side: 1 or dec::kChains
+    uint32_t bypass;    // 1: a bypass message (raw words after their symbols)
+    uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
+    uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
 
-template <int NT>  // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N
+// NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  RAW: a bypass
+// message (version 2, raw words after their symbols), one chunk per warp.
+template <int NT, bool RAW>
 __global__ void __launch_bounds__(dec::kThreads)
     decode_kernel(const __grid_constant__ DecodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -42,9 +47,11 @@ __global__ void __launch_bounds__(dec::kThreads)
     uint32_t &const_sym = sm.misc[1];
 
     if (threadIdx.x == 0) {
-        hdr_ok = dec::header_ok(p.msg, p.msg_size, p.data0, p.n_sym, p.N, p.CS, p.n_chunks);
+        hdr_ok = dec::header_ok(p.msg, p.msg_size, p.data0, p.n_sym, p.N, p.CS, p.n_chunks,
+                                RAW ? RANS_VERSION_BYPASS : RANS_VERSION);
         const_sym = dec::kNoConst;
     }
+    if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
     dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
     if (!hdr_ok) {
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
@@ -61,11 +68,19 @@ __global__ void __launch_bounds__(dec::kThreads)
     for (uint32_t q = blockIdx.x * kWarps + warp; q < n_units; q += gridDim.x * kWarps) {
         const uint32_t c = p.c_begin + q * per;
         const uint32_t count = min(per, p.c_end - c);
-        const uint32_t st =
-            per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
-                                                   count, p.n_sym, p.CS, p.N, p.out, cs, lane, lt)
-                    : dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
-                                                    c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
+        uint32_t st;
+        if (RAW)
+            st = dec::decode_chunks<NT, false, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
+                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
+                                                     p.raw_out, sm.flags_s,
+                                                     cs != dec::kNoConst && sm.flags[cs & 0xFFu]);
+        else
+            st = per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs,
+                                                        data_end, c, count, p.n_sym, p.CS, p.N,
+                                                        p.out, cs, lane, lt)
+                         : dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs,
+                                                         data_end, c, 1, p.n_sym, p.CS, p.N,
+                                                         p.out, cs, lane, lt);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
@@ -85,28 +100,29 @@ uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
     return double(n_chunks) >= 5.0 * double(warps) ? dec::kChains : 1u;
 }
 
-template <int NT>
+template <int NT, bool RAW>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-        if (cudaFuncSetAttribute(decode_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(decode_kernel<NT, RAW>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(kSmemBytes)) != cudaSuccess)
             return RANS_ERR_CUDA;
         configured[dev] = true;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT>, kWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT, RAW>, kWarps * 32,
                                                       kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const uint64_t n_range = p.c_end - p.c_begin;
-    p.per_warp = chunks_per_warp(n_range, cap * kWarps);
+    p.per_warp = RAW ? 1u : chunks_per_warp(n_range, cap * kWarps);
     const uint64_t want = ceil_div(n_range, uint64_t(kWarps) * p.per_warp);
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    decode_kernel<NT><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    decode_kernel<NT, RAW><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
@@ -143,7 +159,8 @@ static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t 
 static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaStream_t st) {
     p.c_begin = c_begin;
     p.c_end = c_end;
-    return p.N == 32 ? launch_decode<32>(p, st) : launch_decode<0>(p, st);
+    if (p.bypass) return p.N == 32 ? launch_decode<32, true>(p, st) : launch_decode<0, true>(p, st);
+    return p.N == 32 ? launch_decode<32, false>(p, st) : launch_decode<0, false>(p, st);
 }
 
 extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
@@ -155,6 +172,30 @@ extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16
     if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
     p.msg = d_msg;
     p.out = d_symbols;
+    p.status = d_status;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+extern "C" int rans_decode_bypass(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                                  const uint8_t *h_raw_words, uint32_t n_alpha,
+                                  const rans_params *params, uint8_t *d_symbols, uint16_t *d_raw,
+                                  uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
+    DecodeParams p;
+    const int rc = prepare_decode(d_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || !h_raw_words || (n_symbols && (!d_symbols || !d_raw)) ||
+        (reinterpret_cast<uintptr_t>(d_raw) & 1u))
+        return RANS_ERR_INVALID_ARG;
+    for (uint32_t s = 0; s < n_alpha; ++s) {
+        if (h_raw_words[s] > 1) return RANS_ERR_INVALID_ARG;
+        p.raw_words[s] = h_raw_words[s];
+    }
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.raw_out = d_raw;
+    p.bypass = 1;
     p.status = d_status;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;

@@ -29,25 +29,31 @@ struct EncodeParams {
     uint32_t CS;
     uint32_t n_chunks;
     uint32_t slot_bytes;
+    const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint16_t freq[RANS_MAX_ALPHABET];
+    uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
 
-template <int NT>
+// RAW: a bypass message (a raw word after every symbol that carries one).
+template <int NT, bool RAW>
 __global__ void __launch_bounds__(enc::kThreads)
     encode_kernel(const __grid_constant__ EncodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const enc::Smem sm = enc::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings));
+    enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings),
+                            RAW ? p.raw_words : nullptr);
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
     for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        enc::encode_chunk<NT, true>(p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes,
-                              p.slot_bytes, p.wstart + c, p.sizes + c,
-                              p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane, acc);
+        enc::encode_chunk<NT, !RAW, RAW>(p.sym + first, n_c, p.N,
+                                         p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
+                                         p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N,
+                                         sm.tab_s, ring_s, ge, lane, acc,
+                                         RAW ? p.raw + first : nullptr);
     }
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
@@ -60,7 +66,7 @@ struct FinalizeParams {
     const uint32_t *sizes;
     const uint32_t *status;
     uint64_t n_sym;
-    uint32_t N, CS, n_chunks, data0;
+    uint32_t N, CS, n_chunks, data0, version;
 };
 
 constexpr int kScanThreads = 1024;
@@ -73,7 +79,7 @@ __global__ void __launch_bounds__(kScanThreads)
         return;
     }
     enc::finalize_message(p.out, p.out_size, p.sizes, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
-                          warp_sums, &carry_s);
+                          warp_sums, &carry_s, p.version);
 }
 
 struct PackParams {
@@ -92,17 +98,17 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
         enc::pack_chunk(p.out, p.data0, p.words, p.states, p.wstart, p.N, p.slot_bytes, c);
 }
 
-template <int NT>
+template <int NT, bool RAW>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel<NT>, kWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel<NT, RAW>, kWarps * 32,
                                                       kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t want = ceil_div(p.n_chunks, kWarps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    encode_kernel<NT><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    encode_kernel<NT, RAW><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
@@ -117,29 +123,52 @@ extern "C" uint64_t rans_encode_scratch_size(uint64_t n_symbols, const rans_para
     return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).total;
 }
 
-extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_freq,
-                           uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
-                           uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status,
-                           void *d_scratch, uint64_t scratch_cap, rans_stream_t stream) {
+extern "C" uint64_t rans_encode_scratch_size_bypass(uint64_t n_symbols, const rans_params *params) {
+    if (!params_ok(params)) return 0;
+    const MessageGeometry g = geometry(n_symbols, params);
+    return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols, 2).total;
+}
+
+// rans_encode and rans_encode_bypass: raw_words == nullptr for a plain
+// message, else a bypass message with d_raw[i] after symbol i where
+// raw_words[symbol] = 1.
+static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint64_t n_symbols,
+                          const uint16_t *h_freq, const uint8_t *raw_words, uint32_t n_alpha,
+                          const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                          uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                          uint64_t scratch_cap, rans_stream_t stream) {
     if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
         !d_status || !d_scratch || !aligned16(d_out) || !aligned16(d_scratch))
         return RANS_ERR_INVALID_ARG;
     if (n_symbols && !d_symbols) return RANS_ERR_INVALID_ARG;
+    const bool bypass = raw_words != nullptr;
+    if (bypass && n_symbols && (!d_raw || (reinterpret_cast<uintptr_t>(d_raw) & 1u)))
+        return RANS_ERR_INVALID_ARG;
+    const uint32_t wps = bypass ? 2u : 1u;
     const MessageGeometry g = geometry(n_symbols, params);
     // Offsets are u32: the worst-case data region must fit.
     if (g.n_chunks > 0xFFFFFFFEull ||
-        4ull * params->n_lanes * g.n_chunks + 2ull * n_symbols > 0xFFFFFFF0ull)
+        4ull * params->n_lanes * g.n_chunks + 2ull * wps * n_symbols > 0xFFFFFFF0ull)
         return RANS_ERR_INVALID_ARG;
-    const ScratchLayout sl = scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols);
-    if (out_cap < rans_max_encoded_size(n_symbols, params) || scratch_cap < sl.total)
-        return RANS_ERR_BUFFER_TOO_SMALL;
+    const ScratchLayout sl =
+        scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols, wps);
+    const uint64_t max_out = bypass ? rans_max_encoded_size_bypass(n_symbols, params)
+                                    : rans_max_encoded_size(n_symbols, params);
+    if (out_cap < max_out || scratch_cap < sl.total) return RANS_ERR_BUFFER_TOO_SMALL;
 
+    EncodeParams ep{};
+    if (bypass) {
+        for (uint32_t s = 0; s < n_alpha; ++s) {
+            if (raw_words[s] > 1) return RANS_ERR_INVALID_ARG;
+            ep.raw_words[s] = raw_words[s];
+        }
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     uint8_t *scr = static_cast<uint8_t *>(d_scratch);
 
-    EncodeParams ep{};
     ep.sym = d_symbols;
+    ep.raw = d_raw;
     ep.words = scr + sl.words;
     ep.states = reinterpret_cast<uint32_t *>(scr + sl.states);
     ep.wstart = reinterpret_cast<uint32_t *>(scr + sl.wstart);
@@ -153,7 +182,9 @@ extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const u
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
     if (g.n_chunks > 0) {
-        const int rc = ep.N == 32 ? launch_encode<32>(ep, st) : launch_encode<0>(ep, st);
+        int rc;
+        if (bypass) rc = ep.N == 32 ? launch_encode<32, true>(ep, st) : launch_encode<0, true>(ep, st);
+        else rc = ep.N == 32 ? launch_encode<32, false>(ep, st) : launch_encode<0, false>(ep, st);
         if (rc != RANS_OK) return rc;
     }
     FinalizeParams fp{};
@@ -166,6 +197,7 @@ extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const u
     fp.CS = ep.CS;
     fp.n_chunks = ep.n_chunks;
     fp.data0 = uint32_t(g.data0);
+    fp.version = bypass ? RANS_VERSION_BYPASS : RANS_VERSION;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {
@@ -184,6 +216,25 @@ extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const u
         if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     }
     return RANS_OK;
+}
+
+extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_freq,
+                           uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
+                           uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status,
+                           void *d_scratch, uint64_t scratch_cap, rans_stream_t stream) {
+    return encode_message(d_symbols, nullptr, n_symbols, h_freq, nullptr, n_alpha, params, d_out,
+                          out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream);
+}
+
+extern "C" int rans_encode_bypass(const uint8_t *d_symbols, const uint16_t *d_raw,
+                                  uint64_t n_symbols, const uint16_t *h_freq,
+                                  const uint8_t *h_raw_words, uint32_t n_alpha,
+                                  const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                                  uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                                  uint64_t scratch_cap, rans_stream_t stream) {
+    if (!h_raw_words) return RANS_ERR_INVALID_ARG;
+    return encode_message(d_symbols, d_raw, n_symbols, h_freq, h_raw_words, n_alpha, params,
+                          d_out, out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,7 +309,7 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     ep.slot_bytes = sl.slot_bytes;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
     if (g.n_chunks > 0) {
-        const int rc = ep.N == 32 ? launch_encode<32>(ep, st) : launch_encode<0>(ep, st);
+        const int rc = ep.N == 32 ? launch_encode<32, false>(ep, st) : launch_encode<0, false>(ep, st);
         if (rc != RANS_OK) return rc;
     }
     FinalizeParams fp{};
@@ -271,6 +322,7 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     fp.CS = ep.CS;
     fp.n_chunks = ep.n_chunks;
     fp.data0 = uint32_t(g.data0);
+    fp.version = RANS_VERSION;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {

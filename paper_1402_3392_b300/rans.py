@@ -29,7 +29,8 @@ __all__ = [
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
     "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
     "Server", "rans_check_bounded_wait", "rans_decode_host", "rans_decode_host_work_size",
-    "decode_host",
+    "decode_host", "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass",
+    "rans_encode_bypass", "rans_decode_bypass", "encode_bypass", "decode_bypass",
 ]
 
 RANS_OK = 0
@@ -94,6 +95,10 @@ def _load() -> C.CDLL:
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
         "rans_check_bounded_wait": (i32, [vp, vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
+        "rans_max_encoded_size_bypass": (u64, [u64, pp]),
+        "rans_encode_scratch_size_bypass": (u64, [u64, pp]),
+        "rans_encode_bypass": (i32, [vp, vp, u64, vp, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode_bypass": (i32, [vp, u64, vp, vp, u32, pp, vp, vp, u64, vp, vp]),
         "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
@@ -186,6 +191,93 @@ def rans_encode(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_c
                          _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
                          _ptr(d_scratch), int(scratch_cap), _stream(stream))
     return _check(rc, "rans_encode") if check else rc
+
+
+def _raw_words(raw_words, n_alpha: int) -> np.ndarray:
+    r = np.ascontiguousarray(raw_words, dtype=np.uint8)
+    if r.size != n_alpha:
+        raise ValueError("raw_words needs one entry per alphabet symbol")
+    return r
+
+
+def rans_max_encoded_size_bypass(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_max_encoded_size_bypass(int(n_symbols), C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_scratch_size_bypass(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_encode_scratch_size_bypass(int(n_symbols),
+                                                   C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_bypass(d_symbols, d_raw, n_symbols, freq, raw_words, n_lanes, chunk_symbols, d_out,
+                       out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream=None,
+                       check=True) -> int:
+    """rans_encode with raw 16-bit words after the symbols whose raw_words
+    entry is 1 (bypass, Section 3)."""
+    f = _freq(freq)
+    r = _raw_words(raw_words, f.size)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_bypass(_ptr(d_symbols), _ptr(d_raw), int(n_symbols), f.ctypes.data,
+                                r.ctypes.data, f.size, C.byref(p), _ptr(d_out), int(out_cap),
+                                _ptr(d_out_size), _ptr(d_status), _ptr(d_scratch),
+                                int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_bypass") if check else rc
+
+
+def rans_decode_bypass(d_msg, msg_size, freq, raw_words, n_lanes, chunk_symbols, d_symbols, d_raw,
+                       n_symbols, d_status, stream=None, check=True) -> int:
+    f = _freq(freq)
+    r = _raw_words(raw_words, f.size)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_bypass(_ptr(d_msg), int(msg_size), f.ctypes.data, r.ctypes.data, f.size,
+                                C.byref(p), _ptr(d_symbols), _ptr(d_raw), int(n_symbols),
+                                _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_decode_bypass") if check else rc
+
+
+def encode_bypass(symbols, raw, freq, raw_words, n_lanes: int = 32, chunk_symbols: int = 65536,
+                  stream=None, sync: bool = True):
+    """Encode CUDA tensors symbols (uint8) and raw (int16/uint16 view, one
+    per symbol).  Returns (message, size, status) like encode()."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size_bypass(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size_bypass(n, n_lanes, chunk_symbols)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(scap, 16), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode_bypass(symbols, raw, n, freq, raw_words, n_lanes, chunk_symbols, out, cap, size,
+                       status, scratch, scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode_bypass (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode_bypass(msg, n_symbols: int, freq, raw_words, n_lanes: int = 32,
+                  chunk_symbols: int = 65536, stream=None, sync: bool = True):
+    """Decode a bypass message.  Returns (symbols, raw, status), raw as an
+    int16 tensor holding the u16 raw words (0 where a symbol has none)."""
+    import torch
+
+    dev = msg.device
+    out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    raw = torch.empty(max(1, n_symbols), dtype=torch.int16, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode_bypass(msg, msg.numel(), freq, raw_words, n_lanes, chunk_symbols, out, raw,
+                       n_symbols, status, stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode_bypass (device status)")
+    return out[:n_symbols], raw[:n_symbols], status
 
 
 def rans_decode_host_work_size(msg_size: int, n_symbols: int) -> int:
