@@ -55,9 +55,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched,binary,single,serving",
+    ap.add_argument("--legs", default="batched,binary,single,serving,bypass",
                     help="extra legs after the headline one: comma list of batched, binary, "
-                         "single, serving, none")
+                         "single, serving, bypass, none")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -446,6 +446,62 @@ def binary_leg(rans, dev, args, hbm):
             "layout": {"n_lanes": 32, "chunk": best["chunk"], "policy": best["policy"]}}
 
 
+def bypass_leg(rans, dev, args, hbm):
+    """Raw words with the coded symbols (bypass coding, Section 3): 512 Mi
+    Zipf(1.1) symbols (a bypass message holds up to about 2^30 symbols, its
+    worst case being 4 bytes per symbol), every symbol >= 16 followed by one
+    raw 16-bit word; encode and decode timed with CUDA events, the round trip
+    checked."""
+    import torch
+
+    cfg = wl.WORKLOADS["bypass"]
+    n, N, CS = cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    freq = rans.rans_quantize_table(wl.weights_from_probs(p))
+    flags = (np.arange(cfg["alphabet"]) >= cfg["raw_from"]).astype(np.uint8)
+    sym = wl.iid_symbols_device(p, n, wl.seed_for("bypass"), dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(wl.seed_for("bypass", 1) & 0x7FFFFFFFFFFFFFFF)
+    raw = torch.randint(-(1 << 15), 1 << 15, (n,), generator=gen, device=dev, dtype=torch.int16)
+    cap = rans.rans_max_encoded_size_bypass(n, N, CS)
+    scap = rans.rans_encode_scratch_size_bypass(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    enc = lambda: rans.rans_encode_bypass(sym, raw, n, freq, flags, N, CS, msg, cap, size, est,  # noqa: E731
+                                          scratch, scap)
+    enc()
+    torch.cuda.synchronize()
+    assert int(est.item()) == 0
+    msg_size = int(size.item())
+    enc_ms = statistics.median(_events(torch, enc, 5))
+    del scratch
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    rout = torch.empty(n, dtype=torch.int16, device=dev)
+    dst = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode_bypass(msg, msg_size, freq, flags, N, CS, out, rout, n, dst)  # noqa: E731
+    dec()
+    torch.cuda.synchronize()
+    has = sym >= cfg["raw_from"]                  # the symbols whose flag is set
+    ok = (int(dst.item()) == 0 and torch.equal(out, sym)
+          and torch.equal(rout, torch.where(has, raw, torch.zeros_like(raw))))
+    n_raw = int(has.sum().item())
+    dec_ms = statistics.median(_events(torch, dec, 10))
+    alg = msg_size + n + 2 * n   # message read, symbols and one raw word slot per symbol written
+    return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, symbols >= "
+                        f"{cfg['raw_from']} followed by a raw 16-bit word ({n_raw} raw words), "
+                        f"{n // CS} chunks x {CS}, N = {N}",
+            "decode_gsym_s": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
+            "decoded_gbs": (n + 2 * n_raw) / (dec_ms * 1e-3) / 1e9,
+            "encode_gsym_s": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
+            "message_bytes": msg_size, "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "decode_kernel (bypass)", "bound": "hbm",
+                         "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def single_leg(rans, dev, args):
     """One 1 MiB stream, Zipf(1.2) over 256 symbols, 32 coders in one chunk:
     a single warp's chain of 32768 dependent steps, so a latency figure."""
@@ -696,6 +752,9 @@ def main(argv=None):
         extra["single"] = single_leg(rans, dev, args)
     if "serving" in legs:
         extra["serving"] = serving_leg(rans, dev, args)
+        torch.cuda.empty_cache()
+    if "bypass" in legs:
+        extra["bypass"] = bypass_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
 
     if rank == 0:

@@ -20,6 +20,9 @@ Workloads (sizes and distributions):
              size uniform in [16, 256], Dirichlet(0.3) probabilities
   serving  : Poisson arrivals, sizes log-uniform in [4 KiB, 64 MiB], alphabet
              size uniform in [64, 256], Dirichlet(0.5) probabilities
+  bypass   : 512 Mi i.i.d. bytes of the chunked distribution with raw words
+             (bypass coding, 8192 chunks of 64 KiB, 32-way interleaving): symbols
+             >= 16 carry one raw 16-bit word, uniform in [0, 2^16)
 """
 from __future__ import annotations
 
@@ -40,6 +43,8 @@ WORKLOADS = {
                     alpha_lo=16, alpha_hi=256, dirichlet=0.3),
     "serving": dict(index=4, size_lo=4 << 10, size_hi=64 << 20, alpha_lo=64,
                     alpha_hi=256, dirichlet=0.5, budget_bytes=40 << 30),
+    "bypass": dict(index=5, n_symbols=1 << 29, zipf_s=1.1, alphabet=256, raw_from=16,
+                   n_lanes=32, chunk_symbols=1 << 16),
 }
 
 
