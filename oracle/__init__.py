@@ -120,6 +120,26 @@ def load(mutant: int = 0) -> C.CDLL:
                                                   C.c_uint32, C.c_uint32, _u8p, _u16p,
                                                   C.c_uint64]
         lib.orc_decode_message_bypass.restype = C.c_int
+        lib.orc_encode_wide.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                        _u32p, C.c_uint64, _u64p, C.c_uint64, _u64p, _u64p]
+        lib.orc_encode_wide.restype = C.c_int
+        lib.orc_decode_wide.argtypes = [_u64p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                        _u64p, C.c_uint64, _u64p, C.c_uint64, _u32p, _u64p, _u64p]
+        lib.orc_decode_wide.restype = C.c_int
+        lib.orc_max_message_size_bytes.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        lib.orc_max_message_size_bytes.restype = C.c_uint64
+        lib.orc_encode_chunk_bytes.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                               _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_chunk_bytes.restype = C.c_int
+        lib.orc_decode_chunk_bytes.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                               _u8p, C.c_uint64]
+        lib.orc_decode_chunk_bytes.restype = C.c_int
+        lib.orc_encode_message_bytes.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                                 C.c_uint32, _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_message_bytes.restype = C.c_int
+        lib.orc_decode_message_bytes.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
+                                                 C.c_uint32, _u8p, C.c_uint64]
+        lib.orc_decode_message_bytes.restype = C.c_int
         _LIBS[mutant] = lib
         return lib
 
@@ -395,6 +415,84 @@ class Oracle:
         if rc != OK:
             raise OracleError(rc, "decode_chunk_bypass")
         return out[:n_sym].copy(), raw[:n_sym].copy()
+
+    # -- width-baked interleaving: digits read breadth-first per step (Section 5)
+    def encode_wide(self, freq, symbols, N=1, L=L_PROD, b=B_PROD):
+        """Returns dict(words, states); words in decoder read order."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        cap = max(1, 64 * s.size + 64)
+        words = np.zeros(cap, dtype=np.uint64)
+        states = np.zeros(N, dtype=np.uint64)
+        nw = C.c_uint64(0)
+        rc = self.lib.orc_encode_wide(_p(f, _u64p), f.size, L, b, N, _p(s, _u32p), s.size,
+                                      _p(words, _u64p), cap, C.byref(nw), _p(states, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "encode_wide")
+        return dict(words=words[: nw.value].copy(), states=states)
+
+    def decode_wide(self, freq, words, states, n_sym, N=1, L=L_PROD, b=B_PROD):
+        """Returns dict(symbols, consumed, states_end)."""
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        st = np.ascontiguousarray(states, dtype=np.uint64)
+        sym = np.zeros(max(1, n_sym), dtype=np.uint32)
+        st_end = np.zeros(N, dtype=np.uint64)
+        used = C.c_uint64(0)
+        rc = self.lib.orc_decode_wide(_p(f, _u64p), f.size, L, b, N, _p(w, _u64p), w.size,
+                                      _p(st, _u64p), n_sym, _p(sym, _u32p), C.byref(used),
+                                      _p(st_end, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "decode_wide")
+        return dict(symbols=sym[:n_sym].copy(), consumed=used.value, states_end=st_end)
+
+    def max_message_size_bytes(self, n_sym, N, chunk_symbols):
+        return int(self.lib.orc_max_message_size_bytes(n_sym, N, chunk_symbols))
+
+    def encode_message_bytes(self, symbols, freq, N=32, chunk_symbols=65536):
+        """Byte-wise (version 3) message: L = 2^23, b = 2^8, digits breadth-first."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        cap = self.max_message_size_bytes(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message_bytes(_p(s, _u8p), s.size, _p(fr, _u16p), fr.size, N,
+                                               chunk_symbols, _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message_bytes")
+        return out[: size.value].copy()
+
+    def decode_message_bytes(self, msg, n_sym, freq, N=32, chunk_symbols=65536):
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_message_bytes(_p(m, _u8p), m.size, _p(fr, _u16p), fr.size, N,
+                                               chunk_symbols, _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message_bytes")
+        return out[:n_sym].copy()
+
+    def encode_chunk_bytes(self, symbols, freq, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        cap = 4 * N + 2 * s.size + 8
+        out = np.zeros(cap, dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk_bytes(_p(s, _u8p), s.size, _p(fr, _u16p), fr.size, N,
+                                             _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk_bytes")
+        return out[: size.value].copy()
+
+    def decode_chunk_bytes(self, chunk, n_sym, freq, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        fr = np.ascontiguousarray(freq, dtype=np.uint16)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_chunk_bytes(_p(c, _u8p), c.size, _p(fr, _u16p), fr.size, N,
+                                             _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk_bytes")
+        return out[:n_sym].copy()
 
     def quantize(self, weights, log2_M=LOG2_M_PROD):
         w = np.ascontiguousarray(weights, dtype=np.uint64)

@@ -30,6 +30,10 @@
  *   - Section 3: N coders interleaved into one buffer with no metadata.
  *     Symbol i of a message is handled by coder (i mod N); encoder and
  *     decoder use the same coder sequence.
+ *   - Section 5, more than one renormalization digit per symbol (b < M):
+ *     a SIMD decoder reads the digits of a step breadth-first across its N
+ *     lanes, which bakes N into the stream; orc_*_wide and the byte-wise
+ *     container (b = 2^8) follow that order.
  *   - Section 3, bypass: raw digits interleaved with the coded data.  A
  *     symbol may carry raw base-b digits that no coder touches; the encoder
  *     sends them right before encoding the symbol, the decoder reads them
@@ -384,6 +388,130 @@ int orc_decode_bypass(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t 
                        trace_lane, trace_cap, n_trace, NULL);
 }
 
+/* ---------------------------------------------------------------------- */
+/* Width-baked interleaving (Section 5): several renormalization digits    */
+/* per symbol, read breadth-first across the N lanes of a step.            */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Symbols go in steps of N (step t holds symbols tN .. tN+N-1, symbol tN+j
+ * on lane j = coder j; the last step may be partial).  Decoder, per step:
+ * every lane decodes its symbol (D); then in rounds r = 1, 2, ... every lane
+ * still below L reads one digit, lanes in order, until all lanes are in I.
+ * That is the order of a SIMD decoder with one lane per coder; it differs
+ * from Algorithm 1's depth-first order as soon as a lane needs two digits,
+ * so N is part of the stream.  The encoder gives the same order: per step it
+ * renormalizes and codes every lane (lanes are independent coders), then
+ * lays the step's digits out round by round -- lane j's digits in the order
+ * its decoder reads them, high digit first.  With N = 1 this is Algorithm 1.
+ */
+#define ORC_WIDE_MAX_DIGITS 128u
+int orc_encode_wide(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                    const uint32_t *sym, uint64_t n_sym, uint64_t *words, uint64_t word_cap,
+                    uint64_t *n_words, uint64_t *states)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    if (!mp) return ORC_ERR_ARG;
+    int rc = model_init(mp, f, n_alpha, L, b);
+    if (rc || N == 0) { free(mp); return rc ? rc : ORC_ERR_ARG; }
+    uint64_t T = (n_sym + N - 1) / N;
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    uint64_t *dig = (uint64_t *)malloc(sizeof(uint64_t) * N * ORC_WIDE_MAX_DIGITS);
+    uint32_t *k = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    uint64_t *tmp = (uint64_t *)malloc(sizeof(uint64_t) * (word_cap ? word_cap : 1));
+    uint64_t *bstart = (uint64_t *)malloc(sizeof(uint64_t) * (T ? T : 1));
+    uint64_t *blen = (uint64_t *)malloc(sizeof(uint64_t) * (T ? T : 1));
+    if (!x || !dig || !k || !tmp || !bstart || !blen) { rc = ORC_ERR_ARG; goto done; }
+    for (uint32_t j = 0; j < N; ++j) x[j] = initial_state(mp);
+    uint64_t W = 0;
+    for (uint64_t t = T; t-- > 0;) {
+        uint32_t lanes = (t == T - 1 && n_sym % N) ? (uint32_t)(n_sym % N) : N;
+        uint32_t kmax = 0;
+        for (uint32_t j = 0; j < lanes; ++j) {
+            uint32_t s = sym[t * N + j];
+            if (s >= mp->n || mp->f[s] == 0) { rc = ORC_ERR_SYMBOL; goto done; }
+            k[j] = 0;
+            while (!in_I(mp, C(mp, s, x[j]))) {            /* Algorithm 1, Encode */
+                if (k[j] >= ORC_WIDE_MAX_DIGITS) { rc = ORC_ERR_ARG; goto done; }
+                dig[(uint64_t)j * ORC_WIDE_MAX_DIGITS + k[j]++] = (uint64_t)(x[j] % mp->b);
+                x[j] = x[j] / mp->b;
+            }
+            x[j] = C(mp, s, x[j]);
+            if (!in_I(mp, x[j])) { rc = ORC_ERR_INVARIANT; goto done; }
+            if (k[j] > kmax) kmax = k[j];
+        }
+        bstart[t] = W;
+#if ORACLE_MUTANT == 10
+        /* planted mistake: depth-first (lane by lane) instead of round by round */
+        for (uint32_t j = 0; j < lanes; ++j)
+            for (uint32_t r = 1; r <= k[j]; ++r) {
+                if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+                tmp[W++] = dig[(uint64_t)j * ORC_WIDE_MAX_DIGITS + k[j] - r];
+            }
+#else
+        for (uint32_t r = 1; r <= kmax; ++r)               /* round r: lanes in order */
+            for (uint32_t j = 0; j < lanes; ++j)
+                if (k[j] >= r) {
+                    if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+                    tmp[W++] = dig[(uint64_t)j * ORC_WIDE_MAX_DIGITS + k[j] - r];
+                }
+#endif
+        blen[t] = W - bstart[t];
+    }
+    {
+        uint64_t o = 0;                                     /* steps in decoder order */
+        for (uint64_t t = 0; t < T; ++t)
+            for (uint64_t q = 0; q < blen[t]; ++q) words[o++] = tmp[bstart[t] + q];
+    }
+    for (uint32_t j = 0; j < N; ++j) states[j] = (uint64_t)x[j];
+    *n_words = W;
+    rc = ORC_OK;
+done:
+    free(x); free(dig); free(k); free(tmp); free(bstart); free(blen); free(mp);
+    return rc;
+}
+
+int orc_decode_wide(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b, uint32_t N,
+                    const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+                    uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed, uint64_t *states_out)
+{
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    if (!mp) return ORC_ERR_ARG;
+    int rc = model_init(mp, f, n_alpha, L, b);
+    if (rc || N == 0) { free(mp); return rc ? rc : ORC_ERR_ARG; }
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    if (!x) { free(mp); return ORC_ERR_ARG; }
+    uint64_t rp = 0, T = (n_sym + N - 1) / N;
+    for (uint32_t j = 0; j < N; ++j) {
+        x[j] = states_in[j];
+        if (!in_I(mp, x[j])) rc = ORC_ERR_CORRUPT;
+    }
+    for (uint64_t t = 0; !rc && t < T; ++t) {
+        uint32_t lanes = (t == T - 1 && n_sym % N) ? (uint32_t)(n_sym % N) : N;
+        for (uint32_t j = 0; j < lanes; ++j) {
+            uint32_t s;
+            x[j] = D(mp, x[j], &s);
+            sym_out[t * N + j] = s;
+        }
+        for (int any = 1; any && !rc;) {                    /* rounds */
+            any = 0;
+            for (uint32_t j = 0; j < lanes; ++j)
+                if (!in_I(mp, x[j])) {
+                    if (rp >= n_words || x[j] >= mp->L * mp->b) { rc = ORC_ERR_CORRUPT; break; }
+                    x[j] = mp->b * x[j] + words[rp++];
+                    any = 1;
+                }
+        }
+    }
+    if (!rc) {
+        for (uint32_t j = 0; j < N; ++j) states_out[j] = (uint64_t)x[j];
+        *consumed = rp;
+    }
+    free(x);
+    free(mp);
+    return rc;
+}
+
 /* Single coding-function evaluations, for checking the oracle against the
  * paper's printed example (Section 2.1).  *ok = 0 on bad input. */
 uint64_t orc_C(const uint64_t *f, uint32_t n_alpha, uint32_t s, uint64_t x, int *ok)
@@ -428,6 +556,9 @@ uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out,
 #define ORC_MAGIC 0x534E4152u
 #define ORC_VERSION 1u
 #define ORC_VERSION_BYPASS 2u  /* messages with raw words (Section 3, bypass) */
+#define ORC_VERSION_BYTES 3u   /* byte-wise, width-baked messages (Section 5) */
+#define ORC_L8 (1ull << 23)    /* byte-wise: L = 2^23, b = 2^8, I = [2^23, 2^31) */
+#define ORC_B8 (1ull << 8)
 #define ORC_L (1ull << 16)
 #define ORC_B (1ull << 16)
 #define ORC_LOG2_M 12u
@@ -586,10 +717,94 @@ int orc_decode_chunk_bypass(const uint8_t *chunk, uint64_t size, const uint16_t 
     return chunk_decode(chunk, size, freq, rawf, n_alpha, N, sym_out, raw_out, n_c);
 }
 
-/* Message = header + offsets + chunks; version 2 marks a bypass message. */
+/* Byte-wise chunk (version 3): [u32 state[N]][u8 digits, breadth-first per
+ * step][zero bytes up to a multiple of 4].  b = 2^8 < M = 2^12, so a lane
+ * can read two digits for one symbol (Section 5); N is part of the stream. */
+static uint64_t round4(uint64_t v) { return (v + 3u) & ~(uint64_t)3u; }
+
+static int chunk_encode_bytes(const uint8_t *sym, uint64_t n_c, const uint16_t *freq,
+                              uint32_t n_alpha, uint32_t N, uint8_t *out, uint64_t cap,
+                              uint64_t *size)
+{
+    uint64_t f64[256];
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    int rc = prod_table(freq, n_alpha, f64);
+    if (rc) return rc;
+    uint64_t cap_w = 2 * (n_c ? n_c : 1) + 8;
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * cap_w);
+    if (!s32 || !w) { free(s32); free(w); return ORC_ERR_ARG; }
+    for (uint64_t i = 0; i < n_c; ++i) s32[i] = sym[i];
+    uint64_t st[32], W = 0;
+    rc = orc_encode_wide(f64, n_alpha, ORC_L8, ORC_B8, N, s32, n_c, w, cap_w, &W, st);
+    if (rc == ORC_OK) {
+        uint64_t need = round4(4ull * N + W);
+        if (need > cap) rc = ORC_ERR_SPACE;
+        else {
+            for (uint32_t j = 0; j < N; ++j) put_u32(out + 4 * j, (uint32_t)st[j]);
+            for (uint64_t q = 0; q < W; ++q) out[4ull * N + q] = (uint8_t)w[q];
+            for (uint64_t q = 4ull * N + W; q < need; ++q) out[q] = 0;
+            *size = need;
+        }
+    }
+    free(s32);
+    free(w);
+    return rc;
+}
+
+static int chunk_decode_bytes(const uint8_t *chunk, uint64_t size, const uint16_t *freq,
+                              uint32_t n_alpha, uint32_t N, uint8_t *sym_out, uint64_t n_c)
+{
+    uint64_t f64[256];
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    int rc = prod_table(freq, n_alpha, f64);
+    if (rc) return rc;
+    if (size < 4ull * N || (size & 3)) return ORC_ERR_CORRUPT;
+    uint64_t W = size - 4ull * N;
+    uint64_t st[32], st_end[32], used = 0;
+    for (uint32_t j = 0; j < N; ++j) st[j] = get_u32(chunk + 4 * j);
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (W ? W : 1));
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    if (!w || !s32) { free(w); free(s32); return ORC_ERR_ARG; }
+    for (uint64_t q = 0; q < W; ++q) w[q] = chunk[4ull * N + q];
+    rc = orc_decode_wide(f64, n_alpha, ORC_L8, ORC_B8, N, w, W, st, n_c, s32, &used, st_end);
+    if (rc == ORC_OK) {
+        /* every coder back at L, every digit read, then only zero padding */
+        for (uint32_t j = 0; j < N; ++j)
+            if (st_end[j] != ORC_L8) rc = ORC_ERR_CORRUPT;
+        if (round4(4ull * N + used) != size) rc = ORC_ERR_CORRUPT;
+        for (uint64_t q = used; q < W; ++q)
+            if (w[q] != 0) rc = ORC_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_c; ++i) sym_out[i] = (uint8_t)s32[i];
+    }
+    free(w);
+    free(s32);
+    return rc;
+}
+
+uint64_t orc_max_message_size_bytes(uint64_t n_sym, uint32_t N, uint32_t chunk_symbols)
+{
+    if (chunk_symbols == 0 || N == 0) return 0;
+    uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
+    return round16(32 + 4 * (n_chunks + 1)) + round16(n_chunks * (4ull * N + 3) + 2ull * n_sym);
+}
+int orc_encode_chunk_bytes(const uint8_t *sym, uint64_t n_c, const uint16_t *freq,
+                           uint32_t n_alpha, uint32_t N, uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    return chunk_encode_bytes(sym, n_c, freq, n_alpha, N, out, cap, size);
+}
+int orc_decode_chunk_bytes(const uint8_t *chunk, uint64_t size, const uint16_t *freq,
+                           uint32_t n_alpha, uint32_t N, uint8_t *sym_out, uint64_t n_c)
+{
+    return chunk_decode_bytes(chunk, size, freq, n_alpha, N, sym_out, n_c);
+}
+
+/* Message = header + offsets + chunks; version 2 marks a bypass message,
+ * version 3 a byte-wise one (bytes != 0). */
 static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
                           const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
-                          uint32_t chunk_symbols, uint8_t *out, uint64_t cap, uint64_t *size)
+                          uint32_t chunk_symbols, uint8_t *out, uint64_t cap, uint64_t *size,
+                          int bytes)
 {
     if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
@@ -598,7 +813,7 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
     if (cap < data0) return ORC_ERR_SPACE;
     memset(out, 0, data0);
     put_u32(out + 0, ORC_MAGIC);
-    put_u32(out + 4, rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
+    put_u32(out + 4, bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
     put_u32(out + 8, N);
     put_u32(out + 12, ORC_LOG2_M);
     put_u32(out + 16, (uint32_t)n_sym);
@@ -613,8 +828,10 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
         put_u32(out + 32 + 4 * c, (uint32_t)pos);
         uint64_t sz = 0;
         if (data0 + pos > cap) return ORC_ERR_SPACE;
-        int rc = chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq, rawf, n_alpha,
-                              N, out + data0 + pos, cap - data0 - pos, &sz);
+        int rc = bytes ? chunk_encode_bytes(sym + first, n_c, freq, n_alpha, N,
+                                            out + data0 + pos, cap - data0 - pos, &sz)
+                       : chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq, rawf,
+                                      n_alpha, N, out + data0 + pos, cap - data0 - pos, &sz);
         if (rc) return rc;
         pos += sz;
     }
@@ -630,13 +847,14 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
 static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *freq,
                           const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
                           uint32_t chunk_symbols, uint8_t *sym_out, uint16_t *raw_out,
-                          uint64_t n_sym)
+                          uint64_t n_sym, int bytes)
 {
     if (N == 0 || N > 32 || chunk_symbols == 0) return ORC_ERR_ARG;
     if (size < 48 || (size & 15)) return ORC_ERR_CORRUPT;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
     uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
-    if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != (rawf ? ORC_VERSION_BYPASS : ORC_VERSION) ||
+    uint32_t version = bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
+    if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != version ||
         get_u32(msg + 8) != N || get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym ||
         get_u32(msg + 24) != chunk_symbols || get_u32(msg + 28) != n_chunks)
         return ORC_ERR_CORRUPT;
@@ -652,8 +870,10 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
         uint64_t first = c * chunk_symbols;
         uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
         if (z < a || z > end_all) return ORC_ERR_CORRUPT;
-        int rc = chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N, sym_out + first,
-                              raw_out ? raw_out + first : NULL, n_c);
+        int rc = bytes ? chunk_decode_bytes(msg + data0 + a, z - a, freq, n_alpha, N,
+                                            sym_out + first, n_c)
+                       : chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N,
+                                      sym_out + first, raw_out ? raw_out + first : NULL, n_c);
         if (rc && !rc_all) rc_all = rc;
     }
     return rc_all;
@@ -663,12 +883,14 @@ int orc_encode_message(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
                        uint32_t N, uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
                        uint64_t *size)
 {
-    return message_encode(sym, NULL, n_sym, freq, NULL, n_alpha, N, chunk_symbols, out, cap, size);
+    return message_encode(sym, NULL, n_sym, freq, NULL, n_alpha, N, chunk_symbols, out, cap, size,
+                          0);
 }
 int orc_decode_message(const uint8_t *msg, uint64_t size, const uint16_t *freq, uint32_t n_alpha,
                        uint32_t N, uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
 {
-    return message_decode(msg, size, freq, NULL, n_alpha, N, chunk_symbols, sym_out, NULL, n_sym);
+    return message_decode(msg, size, freq, NULL, n_alpha, N, chunk_symbols, sym_out, NULL, n_sym,
+                          0);
 }
 int orc_encode_message_bypass(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
                               const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha,
@@ -676,7 +898,8 @@ int orc_encode_message_bypass(const uint8_t *sym, const uint16_t *raw16, uint64_
                               uint64_t *size)
 {
     if (!rawf || !raw16) return ORC_ERR_ARG;
-    return message_encode(sym, raw16, n_sym, freq, rawf, n_alpha, N, chunk_symbols, out, cap, size);
+    return message_encode(sym, raw16, n_sym, freq, rawf, n_alpha, N, chunk_symbols, out, cap, size,
+                          0);
 }
 int orc_decode_message_bypass(const uint8_t *msg, uint64_t size, const uint16_t *freq,
                               const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
@@ -685,7 +908,21 @@ int orc_decode_message_bypass(const uint8_t *msg, uint64_t size, const uint16_t 
 {
     if (!rawf || !raw_out) return ORC_ERR_ARG;
     return message_decode(msg, size, freq, rawf, n_alpha, N, chunk_symbols, sym_out, raw_out,
-                          n_sym);
+                          n_sym, 0);
+}
+int orc_encode_message_bytes(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
+                             uint32_t n_alpha, uint32_t N, uint32_t chunk_symbols, uint8_t *out,
+                             uint64_t cap, uint64_t *size)
+{
+    return message_encode(sym, NULL, n_sym, freq, NULL, n_alpha, N, chunk_symbols, out, cap, size,
+                          1);
+}
+int orc_decode_message_bytes(const uint8_t *msg, uint64_t size, const uint16_t *freq,
+                             uint32_t n_alpha, uint32_t N, uint32_t chunk_symbols,
+                             uint8_t *sym_out, uint64_t n_sym)
+{
+    return message_decode(msg, size, freq, NULL, n_alpha, N, chunk_symbols, sym_out, NULL, n_sym,
+                          1);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -593,6 +593,101 @@ def pin_bypass_interleaved(o):
         assert np.array_equal(sym2, msg) and np.array_equal(raw2, r16)
 
 
+# ----------------------------------------------------------------------------
+# Several renormalization digits per symbol, width-baked order (Section 5)
+# ----------------------------------------------------------------------------
+
+L23 = 1 << 23
+B8 = 1 << 8
+
+
+def digits_per_symbol(o, freq, msg, N, L, b):
+    """k_i = renormalization digits the serial decoder reads for symbol i,
+    from its state trace: per symbol one entry after D, then one per digit
+    (consecutive symbols sit on different lanes when N >= 2)."""
+    enc = o.encode(freq, msg, N=N, L=L, b=b)
+    dec = o.decode(freq, enc["words"], enc["states"], len(msg), N=N, L=L, b=b, trace=True)
+    lanes = list(dec["trace_lane"][N:])
+    k, i = [], 0
+    while i < len(lanes):
+        j = i + 1
+        while j < len(lanes) and lanes[j] == lanes[i]:
+            j += 1
+        k.append(j - i - 1)
+        i = j
+    assert len(k) == len(msg)
+    return enc, k
+
+
+def pin_wide_one_lane_is_algorithm1(o):
+    """With N = 1 the width-baked coder is Algorithm 1 itself."""
+    rng = np.random.default_rng(17)
+    for L, b in ((16, 2), (L23, B8), (1 << 14, 4)):
+        freq = [1, 3] if L == 16 else o.quantize(
+            np.maximum(1, rng.integers(0, 1000, size=30)).astype(np.uint64))
+        msg = _paper_message() if L == 16 else rng.choice(30, size=500, p=np.asarray(freq) / np.sum(freq))
+        a = o.encode(freq, msg, N=1, L=L, b=b)
+        w = o.encode_wide(freq, msg, N=1, L=L, b=b)
+        assert list(a["words"]) == list(w["words"]) and list(a["states"]) == list(w["states"])
+
+
+def pin_wide_breadth_first(o):
+    """The SIMD order of Section 5: within a step of N symbols the decoder
+    reads first one digit for every lane that needs one (lanes in order),
+    then a second digit for every lane that needs two, and so on -- the
+    paper's two-lane example: lane 0's first byte, lane 1's byte, lane 0's
+    second byte.  Built here from the serial (depth-first) stream of
+    Algorithm 1 and compared with the width-baked coder; states are equal."""
+    rng = np.random.default_rng(19)
+    saw_example = False
+    for N in (2, 5, 32):
+        freq = o.quantize(np.maximum(1, rng.integers(0, 1000, size=64)).astype(np.uint64))
+        msg = rng.choice(64, size=40 * N + 3, p=freq / freq.sum())
+        ser, k = digits_per_symbol(o, freq, msg, N, L23, B8)
+        pos, per_sym = 0, []
+        for ki in k:
+            per_sym.append(list(ser["words"][pos:pos + ki]))
+            pos += ki
+        expect = []
+        for t0 in range(0, len(msg), N):
+            syms = list(range(t0, min(len(msg), t0 + N)))
+            for r in range(max(k[i] for i in syms)):
+                expect += [per_sym[i][r] for i in syms if k[i] > r]
+            if N >= 2 and len(syms) >= 2 and k[syms[0]] == 2 and k[syms[1]] == 1:
+                saw_example = True
+        wide = o.encode_wide(freq, msg, N=N, L=L23, b=B8)
+        assert list(wide["words"]) == expect, N
+        assert list(wide["states"]) == list(ser["states"])
+        dec = o.decode_wide(freq, wide["words"], wide["states"], len(msg), N=N, L=L23, b=B8)
+        assert list(dec["symbols"]) == list(msg) and dec["consumed"] == len(expect)
+        assert all(int(v) == L23 for v in dec["states_end"])
+    assert saw_example
+
+
+def pin_bytes_container(o):
+    """Byte-wise messages: version 3, chunks of [N states][digits][zeros to
+    a multiple of 4]; round trip; a chunk equals the width-baked coder's
+    output for its symbols."""
+    rng = np.random.default_rng(23)
+    freq = o.quantize(np.maximum(1, rng.integers(0, 1000, size=100)).astype(np.uint64))
+    msg = rng.choice(100, size=5000, p=freq / freq.sum()).astype(np.uint8)
+    N, CS = 7, 1000
+    m = o.encode_message_bytes(msg, freq, N=N, chunk_symbols=CS)
+    assert int.from_bytes(m[4:8].tobytes(), "little") == 3
+    n_chunks = 5
+    data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+    offs = m[32:32 + 4 * (n_chunks + 1)].view(np.uint32)
+    for c in range(n_chunks):
+        ch = m[data0 + offs[c]:data0 + offs[c + 1]]
+        assert ch.size % 4 == 0
+        w = o.encode_wide(freq, msg[c * CS:(c + 1) * CS], N=N, L=L23, b=B8)
+        assert list(ch[:4 * N].view(np.uint32)) == list(w["states"])
+        body = ch[4 * N:]
+        assert list(body[:w["words"].size]) == list(w["words"])
+        assert not body[w["words"].size:].any()
+    assert np.array_equal(o.decode_message_bytes(m, msg.size, freq, N=N, chunk_symbols=CS), msg)
+
+
 ALL_PINS = [
     pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
     pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
@@ -600,5 +695,6 @@ ALL_PINS = [
     pin_infinite_precision_paper, pin_infinite_precision_general, pin_size_bound,
     pin_brute_force_unique, pin_packed_io_equivalence, pin_round_trip_edges,
     pin_container_layout, pin_quantize, pin_bypass_paper_example,
-    pin_bypass_without_raw_is_plain, pin_bypass_interleaved,
+    pin_bypass_without_raw_is_plain, pin_bypass_interleaved, pin_wide_one_lane_is_algorithm1,
+    pin_wide_breadth_first, pin_bytes_container,
 ]

@@ -6,13 +6,14 @@ The mutants are compiled from the same source with -DORACLE_MUTANT=k:
   5 leaves the words in emission order   6 starts the coders at L+1
   7 off-by-one symbol search in D        8 quantizer ties go to the higher index
   9 sends a symbol's raw (bypass) digits after encoding it, not before
+ 10 lays a width-baked step's digits out depth-first, not breadth-first
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTANTS = range(1, 10)
+MUTANTS = range(1, 11)
 
 
 @pytest.mark.parametrize("k", MUTANTS)
