@@ -81,6 +81,7 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_MAGIC         0x534E4152u
 #define RANS_VERSION       1u
 #define RANS_VERSION_BYPASS 2u         /* messages with raw words (rans_encode_bypass) */
+#define RANS_VERSION_BYTES 3u          /* byte-wise messages (rans_encode_bytes) */
 
 typedef struct {
     uint32_t n_lanes;        /* N interleaved coders per chunk, 1..32 */
@@ -230,6 +231,30 @@ int rans_decode_bypass(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *
                        const uint8_t *h_raw_words, uint32_t n_alpha, const rans_params *params,
                        uint8_t *d_symbols, uint16_t *d_raw, uint64_t n_symbols,
                        uint32_t *d_status, rans_stream_t stream);
+
+/*
+ * Byte-wise messages -- Section 5 of the paper: with 8-bit digits (b = 2^8 <
+ * M = 2^12) a coder can need two renormalization digits for one symbol, and
+ * a SIMD/GPU decoder with one lane per coder reads a step's digits
+ * breadth-first (one digit for every lane that needs one, lanes in order,
+ * then the second digits).  The stream therefore depends on N (N is "baked
+ * in"): a byte-wise message must be decoded with the N it was encoded with,
+ * which the header records.  L = 2^23, b = 2^8, I = [2^23, 2^31); chunks
+ * are [u32 state[N]][bytes][zeros up to a multiple of 4]; version 3
+ * (RANS_VERSION_BYTES).
+ *
+ * rans_encode_bytes / rans_decode_bytes: arguments, buffers and statuses as
+ * rans_encode / rans_decode; out_cap >= rans_max_encoded_size_bytes(...),
+ * scratch_cap >= rans_encode_scratch_size(...).  Decoded one chunk per warp.
+ */
+uint64_t rans_max_encoded_size_bytes(uint64_t n_symbols, const rans_params *params);
+int rans_encode_bytes(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_freq,
+                      uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
+                      uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status,
+                      void *d_scratch, uint64_t scratch_cap, rans_stream_t stream);
+int rans_decode_bytes(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                      uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                      uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
 
 /*
  * Batched decoding: many independent messages ("streams"), each with its own

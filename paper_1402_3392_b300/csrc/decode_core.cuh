@@ -75,6 +75,8 @@ constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
 constexpr uint32_t kFlagsOffset = kMiscOffset + 64;   // 256 raw-word flags (bypass)
 constexpr uint32_t kSmemBytes = kFlagsOffset + 256;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
+// Byte-wise messages (version 3): L = 2^23, b = 2^8, I = [2^23, 2^31).
+constexpr uint32_t kL8 = 1u << 23;
 
 struct Smem {
     uint32_t *tab;
@@ -129,6 +131,11 @@ __device__ __forceinline__ uint32_t ld_table(uint32_t a) {
 __device__ __forceinline__ uint32_t ld_flag(uint32_t a) {
     uint32_t v;
     asm("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_ring_u8(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ uint32_t ld_ring_u16(uint32_t a) {
@@ -270,6 +277,8 @@ struct Chain {
     uint32_t steps;      // full steps (all N coders) left
     uint32_t rem;        // coders with a symbol in the final partial step
     uint32_t st;         // RANS_OK, or the error found when opening
+    uint32_t rp0;        // byte-wise messages: rp at the first digit
+    uint32_t len;        // byte-wise messages: chunk bytes (states, digits, padding)
 };
 
 __device__ __forceinline__ void chain_empty(Chain &c) {
@@ -280,13 +289,14 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.rp = c.evt = c.nseg = c.span = c.endrel = c.steps = c.rem = 0;
     c.next_evt = 0xFFFFFFFFu;
     c.st = RANS_OK;
+    c.rp0 = c.len = 0;
 }
 
 // Open chunk [o, e) (byte offsets in the data region that starts at msg +
 // data0; data_end = end of all chunks) of n_c symbols with N coders, output
 // at out.  Reads the N initial states; a malformed chunk gets c.st set and no
 // steps.
-template <class G>
+template <class G, bool BYTES = false>
 __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
                                            uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,
                                            uint8_t *out, uint16_t *raw_out, uint32_t lane) {
@@ -297,9 +307,10 @@ __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_
         return;
     }
     const uint8_t *chunk = msg + data0 + o;
-    uint32_t x = kL;
+    uint32_t x = BYTES ? kL8 : kL;
     if (lane < N) x = ld_u16_global(chunk + 4 * lane) | (ld_u16_global(chunk + 4 * lane + 2) << 16);
-    if (!__all_sync(kFull, x >= kL)) {  // Algorithm 1 requires x in I
+    // Algorithm 1 requires x in I
+    if (!__all_sync(kFull, BYTES ? (x >= kL8 && x < (kL8 << 8)) : x >= kL)) {
         c.st = RANS_ERR_CORRUPT;
         return;
     }
@@ -311,6 +322,8 @@ __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_
     c.nseg = (c.span + G::kSeg - 1) / G::kSeg;
     c.endrel = uint32_t(P1 - A);
     c.rp = uint32_t(P0 - A);
+    c.rp0 = c.rp;
+    c.len = e - o;
     c.next_evt = 0;
     c.outp = out + lane;
     c.rawp = raw_out ? raw_out + lane : nullptr;
@@ -423,8 +436,37 @@ __device__ __forceinline__ void decode_step_raw(uint32_t &x, uint32_t &rp, bool 
     rp = imad(__popc(m) + __popc(mr), 2u, rp);
 }
 
+// One step of a byte-wise chunk (b = 2^8 < M, Section 5): after D a lane may
+// need two digits.  The digits are read breadth-first across the warp: round
+// 1 gives every lane below L one byte (lanes in order), round 2 -- taken
+// only when some lane is still below L -- a second one.  (x << 8) | byte is
+// a byte permute.
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step_bytes(uint32_t &x, uint32_t &rp, bool active,
+                                                  uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
+                                                  uint32_t lt) {
+    const uint32_t e = ld_table(imad(x & (kM - 1), 4u, tab_s));
+    const bool on = FULL || active;
+    if (on) {
+        x = decode_update(x, e);
+        *outp = uint8_t(e);
+    }
+    bool need = on && x < kL8;
+    uint32_t m = __ballot_sync(kFull, need);
+    uint32_t w = ld_ring_u8(((rp + __popc(m & lt)) & (RING - 1)) | ring_s);
+    if (need) x = __byte_perm(x, w, 0x2104u);  // (x << 8) | w
+    rp += __popc(m);
+    need = on && x < kL8;
+    m = __ballot_sync(kFull, need);
+    if (m) {
+        w = ld_ring_u8(((rp + __popc(m & lt)) & (RING - 1)) | ring_s);
+        if (need) x = __byte_perm(x, w, 0x2104u);
+        rp += __popc(m);
+    }
+}
+
 // Decode what is left of one chunk on its own.  RAW: a bypass chunk.
-template <bool FULL, class G, bool RAW = false>
+template <bool FULL, class G, bool RAW = false, bool BYTES = false>
 __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &timeouts, uint32_t N,
                                           bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt,
                                           uint32_t flags_s = 0) {
@@ -435,6 +477,9 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
             if (RAW)
                 decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s,
                                                 c.outp + u * N, c.rawp + u * N, lt);
+            else if (BYTES)
+                decode_step_bytes<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s,
+                                                  c.outp + u * N, lt);
             else
                 decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N,
                                             lt);
@@ -447,6 +492,8 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
         if (RAW)
             decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s, c.outp,
                                             c.rawp, lt);
+        else if (BYTES)
+            decode_step_bytes<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
         else
             decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
         c.outp += N;
@@ -458,6 +505,9 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
         if (RAW)
             decode_step_raw<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, flags_s,
                                              c.outp, c.rawp, lt);
+        else if (BYTES)
+            decode_step_bytes<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp,
+                                               lt);
         else
             decode_step<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
         c.rem = 0;
@@ -468,14 +518,28 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
 // phases are clean for the next chunk, and check the chunk's end: a
 // well-formed chunk ends with every coder back at x0 = L and every word read
 // exactly once (decoder and encoder in lockstep, Section 3).
-template <class G>
+// Byte-wise chunks end in zero padding up to a multiple of 4 bytes: the chunk
+// must be exactly round4(4N + digits read) long, with zeros after the digits
+// (src + rp .. src + endrel, at most 3 bytes).
+template <class G, bool BYTES = false>
 __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t &timeouts,
-                                                bool lane_on) {
+                                                bool lane_on, uint32_t N = 0) {
     const uint32_t issued = min(c.evt, c.nseg);
     for (uint32_t j = c.evt > G::kLag ? c.evt - G::kLag : 0u; j < issued; ++j)
         ring_wait(r, j % G::kNSeg, timeouts);
     if (c.st != RANS_OK) return c.st;
     if (timeouts) return RANS_ERR_TIMEOUT;
+    if (BYTES) {
+        const uint32_t used = c.rp - c.rp0;
+        bool ok = __all_sync(kFull, !lane_on || c.x == kL8) &&
+                  ((4 * N + used + 3) & ~3u) == c.len && c.rp <= c.endrel;
+        if (ok) {
+            const uint32_t i = c.rp + (threadIdx.x & 31);
+            const uint32_t pad = i < c.endrel ? c.src[i] : 0u;
+            ok = !__any_sync(kFull, pad != 0u);
+        }
+        return ok ? RANS_OK : RANS_ERR_CORRUPT;
+    }
     const bool ok = __all_sync(kFull, !lane_on || c.x == kL) && c.rp == c.endrel;
     return ok ? RANS_OK : RANS_ERR_CORRUPT;
 }
@@ -485,13 +549,13 @@ __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t
 __device__ __forceinline__ uint32_t const_chunk(const uint8_t *msg, uint32_t data0, uint32_t o,
                                                 uint32_t e, uint32_t data_end, uint32_t n_c,
                                                 uint32_t N, uint8_t *out, uint32_t const_sym,
-                                                uint32_t lane) {
+                                                uint32_t lane, uint32_t L = kL) {
     if (((o | e) & 1u) || e < o || e > data_end || e - o != 4 * N) return RANS_ERR_CORRUPT;
     const uint8_t *chunk = msg + data0 + o;
-    uint32_t x = kL;
+    uint32_t x = L;
     if (lane < N) x = ld_u16_global(chunk + 4 * lane) | (ld_u16_global(chunk + 4 * lane + 2) << 16);
     for (uint32_t i = lane; i < n_c; i += 32) out[i] = uint8_t(const_sym);
-    return __all_sync(kFull, x == kL) ? RANS_OK : RANS_ERR_CORRUPT;
+    return __all_sync(kFull, x == L) ? RANS_OK : RANS_ERR_CORRUPT;
 }
 
 // const_chunk for a bypass message: when the one symbol carries a raw word,
@@ -523,7 +587,7 @@ __device__ __forceinline__ uint32_t const_chunk_raw(const uint8_t *msg, uint32_t
 // raw_out[i] and flags_s addresses the 256 raw-word flags.  const_sym !=
 // kNoConst: the model has one symbol with f = M.  Returns the warp-uniform
 // status (RANS_OK, or the first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
-template <int NT, bool PAIR, bool RAW = false>  // NT = 32: all lanes are coders; 0: runtime N
+template <int NT, bool PAIR, bool RAW = false, bool BYTES = false>  // NT = 32: all lanes are coders
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
@@ -531,7 +595,8 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
                                                   uint8_t *out, uint32_t const_sym, uint32_t lane,
                                                   uint32_t lt, uint16_t *raw_out = nullptr,
                                                   uint32_t flags_s = 0, bool const_raw = false) {
-    static_assert(!(PAIR && RAW), "bypass messages are decoded one chunk per warp");
+    static_assert(!(PAIR && (RAW || BYTES)), "bypass and byte-wise messages: one chunk per warp");
+    static_assert(!(RAW && BYTES), "one message kind");
     using G = typename std::conditional<RAW, GeoRaw,
                                         typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type;
     constexpr bool kFullWarp = NT == 32;
@@ -547,6 +612,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
         if (RAW)
             return const_chunk_raw(msg, data0, o0, o1, data_end, n_a, N, out + first,
                                    raw_out + first, const_sym, const_raw, lane);
+        if (BYTES)
+            return const_chunk(msg, data0, o0, o1, data_end, n_a, N, out + first, const_sym, lane,
+                               kL8);
         uint32_t st = const_chunk(msg, data0, o0, o1, data_end, n_a, N, out + first, const_sym, lane);
         if (two) {
             const uint32_t sb =
@@ -557,8 +625,8 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     }
 
     Chain a, b;
-    chain_open<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
-                  RAW ? raw_out + first : nullptr, lane);
+    chain_open<G, BYTES>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
+                         RAW ? raw_out + first : nullptr, lane);
     if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, nullptr, lane);
     else chain_empty(b);
 
@@ -579,9 +647,10 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
             b.outp += G::kGroup * N;
         }
     }
-    chain_run<kFullWarp, G, RAW>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
+    chain_run<kFullWarp, G, RAW, BYTES>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt,
+                                        flags_s);
     if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
-    const uint32_t sa = chain_close<G>(a, w.r[0], w.timeouts, lane_on);
+    const uint32_t sa = chain_close<G, BYTES>(a, w.r[0], w.timeouts, lane_on, N);
     const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
     return sa != RANS_OK ? sa : sb;
 }

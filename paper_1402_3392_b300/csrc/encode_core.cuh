@@ -45,6 +45,7 @@ constexpr uint32_t kMiscOffset = 256 * 8 + kRing + kWarps * kRing;
 constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
 constexpr uint32_t kRawFlag = 1u << 18;   // encode-table bit: the symbol carries a raw word
+constexpr uint32_t kL8 = 1u << 23;         // byte-wise messages: L = 2^23, b = 2^8
 
 // Scratch of one message, all sections 16-byte aligned: one worst-case slot
 // of words per chunk (written backwards from its end), then the chunks'
@@ -144,6 +145,9 @@ __device__ __forceinline__ uint2 ld_enc_table(uint32_t a) {
     asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
     return v;
 }
+__device__ __forceinline__ void st_ring_u8(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_ring_u16(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(uint16_t(v)) : "memory");
 }
@@ -167,6 +171,38 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
     wp -= 2u * __popc(m);
     if (on) {
         // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
+        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
+        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
+    }
+}
+
+// One step of a byte-wise chunk (b = 2^8 < M, Section 5): a lane emits
+// k = [x >= f*2^19] + [x >= f*2^27] bytes (x must end below f*2^19 = the top
+// of I_s) before coding.  The decoder reads a step's bytes breadth-first --
+// round 1: one byte for every lane that needs one, lanes in order; round 2:
+// the second byte of the lanes that need two -- so in the backwards-filled
+// buffer the step's round-2 bytes sit above its round-1 bytes.  A lane's
+// round-1 byte is the one its decoder reads first: the higher of two.
+template <bool FULL>
+__device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uint32_t &acc,
+                                                  bool active, uint32_t s, uint32_t tab_s,
+                                                  uint32_t ring_s, uint32_t ge) {
+    const uint2 t = ld_enc_table(tab_s + (s << 3));
+    const bool on = FULL || active;
+    if (on) acc |= t.y;
+    const uint32_t thr = (kM - (t.y >> 20)) << 19;  // f * 2^19; 2^31 for f = M or f = 0
+    const bool e1 = on && x >= thr;
+    const bool e2 = e1 && (x >> 8) >= thr;
+    const uint32_t m1 = __ballot_sync(kFull, e1);
+    const uint32_t m2 = __ballot_sync(kFull, e2);
+    const uint32_t lt = ~ge;
+    const uint32_t n1 = __popc(m1), n2 = __popc(m2);
+    if (e2) st_ring_u8(((wp - n2 + __popc(m2 & lt)) & (kRing - 1)) | ring_s, x);
+    if (e1) st_ring_u8(((wp - n2 - n1 + __popc(m1 & lt)) & (kRing - 1)) | ring_s, e2 ? x >> 8 : x);
+    if (e1) x >>= e2 ? 16 : 8;
+    wp -= n1 + n2;
+    if (on) {
         const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
         const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
@@ -210,7 +246,8 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // PREFETCH: load the next group's symbols while coding this one.  RAW: a
 // bypass chunk, raw[i] is the raw word of symbol i (used where the symbol
 // carries one); groups are halved so that a group still writes at most 1 KiB.
-template <int NT, bool PREFETCH, bool RAW = false>
+// BYTES: a byte-wise chunk (at most 2 bytes per symbol, size padded to 4).
+template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
@@ -222,7 +259,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
     const uint16_t *rawp = RAW ? raw + lane : nullptr;
-    uint32_t x = kL;
+    uint32_t x = BYTES ? kL8 : kL;
     uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
     uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
 
@@ -257,7 +294,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
             encode_step_raw<false>(x, wp, acc, act, s, rw, tab_s, ring_s, ge);
         } else {
-            encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge);
+            (BYTES ? encode_step_bytes<false>(x, wp, acc, act, s, tab_s, ring_s, ge)
+                   : encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge));
         }
     }
     int64_t t = int64_t(T_full) - 1;
@@ -268,7 +306,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
             encode_step_raw<NT == 32>(x, wp, acc, lane_on, s, rw, tab_s, ring_s, ge);
         } else {
-            encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
+            (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge)
+                   : encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge));
         }
     }
     if (PREFETCH) {
@@ -286,7 +325,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             service();
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u)
-                encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+                (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge)
+                   : encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge));
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
         }
@@ -306,7 +346,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                     encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
                                               ge);
                 else
-                    encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+                    (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge)
+                   : encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge));
             }
         }
     }
@@ -326,7 +367,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         bulk_commit();
         bulk_wait_read<0>();
         *wstart = wp;
-        *size = 4 * N + (slot_bytes - wp);
+        *size = BYTES ? (4 * N + (slot_bytes - wp) + 3) & ~3u : 4 * N + (slot_bytes - wp);
     }
     __syncwarp();
     if (lane < N) states[lane] = x;
@@ -418,6 +459,9 @@ __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, ui
 // With a whole CTA: chunk c of a message (offset table already written in
 // out) from scratch (words base, states, wstart) into out.  The words buffer
 // must have 16 readable bytes past its last slot.
+// BYTES: the chunk's byte count may be odd and its start in the slot too;
+// the chunk is padded with zeros to a multiple of 4 bytes.
+template <bool BYTES = false>
 __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const uint8_t *words,
                                            const uint32_t *states, const uint32_t *wstart,
                                            uint32_t N, uint32_t slot_bytes, uint32_t c) {
@@ -433,9 +477,14 @@ __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const u
     const uint64_t d1 = d0 + (slot_bytes - wstart[c]);
     const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
     const uint64_t head_end = B0 < d1 ? B0 : d1;
-    for (uint64_t b = d0 + 2ull * threadIdx.x; b < head_end; b += 2ull * blockDim.x)
-        *reinterpret_cast<uint16_t *>(out + b) =
-            *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+    if (BYTES) {
+        for (uint64_t b = d0 + threadIdx.x; b < head_end; b += blockDim.x)
+            out[b] = words[s0 + (b - d0)];
+    } else {
+        for (uint64_t b = d0 + 2ull * threadIdx.x; b < head_end; b += 2ull * blockDim.x)
+            *reinterpret_cast<uint16_t *>(out + b) =
+                *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+    }
     if (B0 < B1) {
         const uint64_t s_minus_d = s0 - d0;  // modulo 2^64
         const uint32_t sh = uint32_t(s_minus_d & 15u);
@@ -448,9 +497,16 @@ __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const u
         }
     }
     const uint64_t tail_start = B1 > head_end ? B1 : head_end;
-    for (uint64_t b = tail_start + 2ull * threadIdx.x; b < d1; b += 2ull * blockDim.x)
-        *reinterpret_cast<uint16_t *>(out + b) =
-            *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+    if (BYTES) {
+        for (uint64_t b = tail_start + threadIdx.x; b < d1; b += blockDim.x)
+            out[b] = words[s0 + (b - d0)];
+        const uint64_t end = D + ((d1 - D + 3) & ~uint64_t(3));
+        for (uint64_t b = d1 + threadIdx.x; b < end; b += blockDim.x) out[b] = 0;
+    } else {
+        for (uint64_t b = tail_start + 2ull * threadIdx.x; b < d1; b += 2ull * blockDim.x)
+            *reinterpret_cast<uint16_t *>(out + b) =
+                *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+    }
 }
 
 }  // namespace enc

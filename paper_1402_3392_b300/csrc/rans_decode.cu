@@ -29,17 +29,23 @@ struct DecodeParams {
     uint32_t c_begin;   // chunks [c_begin, c_end) are decoded by this launch
     uint32_t c_end;
     uint32_t per_warp;  // chunks a warp decodes side by side: 1 or dec::kChains
-    uint32_t bypass;    // 1: a bypass message (raw words after their symbols)
+    uint32_t kind;      // kPlain, kBypass (raw words after their symbols) or kBytes
     uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
 
-// NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  RAW: a bypass
-// message (version 2, raw words after their symbols), one chunk per warp.
-template <int NT, bool RAW>
+// Message kinds: plain (version 1), bypass (version 2: raw words after their
+// symbols) and byte-wise (version 3: b = 2^8, digits breadth-first per step).
+constexpr int kPlain = 0, kBypass = 1, kBytes = 2;
+
+// NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  Bypass and
+// byte-wise messages are decoded one chunk per warp.
+template <int NT, int KIND>
 __global__ void __launch_bounds__(dec::kThreads)
     decode_kernel(const __grid_constant__ DecodeParams p) {
+    constexpr bool RAW = KIND == kBypass;
+    constexpr bool BYTES = KIND == kBytes;
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -48,7 +54,8 @@ __global__ void __launch_bounds__(dec::kThreads)
 
     if (threadIdx.x == 0) {
         hdr_ok = dec::header_ok(p.msg, p.msg_size, p.data0, p.n_sym, p.N, p.CS, p.n_chunks,
-                                RAW ? RANS_VERSION_BYPASS : RANS_VERSION);
+                                RAW ? RANS_VERSION_BYPASS : BYTES ? RANS_VERSION_BYTES
+                                                                  : RANS_VERSION);
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
@@ -74,6 +81,10 @@ __global__ void __launch_bounds__(dec::kThreads)
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
                                                      p.raw_out, sm.flags_s,
                                                      cs != dec::kNoConst && sm.flags[cs & 0xFFu]);
+        else if (BYTES)
+            st = dec::decode_chunks<NT, false, false, true>(wr, sm.tab_s, p.msg, p.data0, offs,
+                                                            data_end, c, 1, p.n_sym, p.CS, p.N,
+                                                            p.out, cs, lane, lt);
         else
             st = per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs,
                                                         data_end, c, count, p.n_sym, p.CS, p.N,
@@ -100,29 +111,29 @@ uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
     return double(n_chunks) >= 5.0 * double(warps) ? dec::kChains : 1u;
 }
 
-template <int NT, bool RAW>
+template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-        if (cudaFuncSetAttribute(decode_kernel<NT, RAW>,
+        if (cudaFuncSetAttribute(decode_kernel<NT, KIND>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(kSmemBytes)) != cudaSuccess)
             return RANS_ERR_CUDA;
         configured[dev] = true;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT, RAW>, kWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT, KIND>, kWarps * 32,
                                                       kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const uint64_t n_range = p.c_end - p.c_begin;
-    p.per_warp = RAW ? 1u : chunks_per_warp(n_range, cap * kWarps);
+    p.per_warp = KIND != kPlain ? 1u : chunks_per_warp(n_range, cap * kWarps);
     const uint64_t want = ceil_div(n_range, uint64_t(kWarps) * p.per_warp);
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    decode_kernel<NT, RAW><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    decode_kernel<NT, KIND><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
@@ -159,8 +170,11 @@ static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t 
 static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaStream_t st) {
     p.c_begin = c_begin;
     p.c_end = c_end;
-    if (p.bypass) return p.N == 32 ? launch_decode<32, true>(p, st) : launch_decode<0, true>(p, st);
-    return p.N == 32 ? launch_decode<32, false>(p, st) : launch_decode<0, false>(p, st);
+    if (p.kind == kBypass)
+        return p.N == 32 ? launch_decode<32, kBypass>(p, st) : launch_decode<0, kBypass>(p, st);
+    if (p.kind == kBytes)
+        return p.N == 32 ? launch_decode<32, kBytes>(p, st) : launch_decode<0, kBytes>(p, st);
+    return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 
 extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
@@ -195,8 +209,24 @@ extern "C" int rans_decode_bypass(const uint8_t *d_msg, uint64_t msg_size, const
     p.msg = d_msg;
     p.out = d_symbols;
     p.raw_out = d_raw;
-    p.bypass = 1;
+    p.kind = kBypass;
     p.status = d_status;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+extern "C" int rans_decode_bytes(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
+                                 uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                                 uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
+    DecodeParams p;
+    const int rc = prepare_decode(d_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.status = d_status;
+    p.kind = kBytes;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     return launch_range(p, 0, p.n_chunks, st);

@@ -34,10 +34,15 @@ struct EncodeParams {
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
 
-// RAW: a bypass message (a raw word after every symbol that carries one).
-template <int NT, bool RAW>
+// Message kinds: plain (version 1), bypass (version 2: a raw word after every
+// symbol that carries one) and byte-wise (version 3: b = 2^8).
+constexpr int kPlain = 0, kBypass = 1, kBytes = 2;
+
+template <int NT, int KIND>
 __global__ void __launch_bounds__(enc::kThreads)
     encode_kernel(const __grid_constant__ EncodeParams p) {
+    constexpr bool RAW = KIND == kBypass;
+    constexpr bool BYTES = KIND == kBytes;
     extern __shared__ __align__(128) uint8_t smem[];
     const enc::Smem sm = enc::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(enc::kThreads)
     for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        enc::encode_chunk<NT, !RAW, RAW>(p.sym + first, n_c, p.N,
+        enc::encode_chunk<NT, !RAW, RAW, BYTES>(p.sym + first, n_c, p.N,
                                          p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
                                          p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N,
                                          sm.tab_s, ring_s, ge, lane, acc,
@@ -92,23 +97,24 @@ struct PackParams {
 };
 
 constexpr int kPackThreads = 256;
+template <bool BYTES>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackParams p) {
     if (*p.status != RANS_OK) return;
     for (uint32_t c = blockIdx.x; c < p.n_chunks; c += gridDim.x)
-        enc::pack_chunk(p.out, p.data0, p.words, p.states, p.wstart, p.N, p.slot_bytes, c);
+        enc::pack_chunk<BYTES>(p.out, p.data0, p.words, p.states, p.wstart, p.N, p.slot_bytes, c);
 }
 
-template <int NT, bool RAW>
+template <int NT, int KIND>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel<NT, RAW>, kWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel<NT, KIND>, kWarps * 32,
                                                       kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t want = ceil_div(p.n_chunks, kWarps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    encode_kernel<NT, RAW><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    encode_kernel<NT, KIND><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
@@ -136,7 +142,7 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
                           const uint16_t *h_freq, const uint8_t *raw_words, uint32_t n_alpha,
                           const rans_params *params, uint8_t *d_out, uint64_t out_cap,
                           uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
-                          uint64_t scratch_cap, rans_stream_t stream) {
+                          uint64_t scratch_cap, rans_stream_t stream, bool bytes = false) {
     if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
         !d_status || !d_scratch || !aligned16(d_out) || !aligned16(d_scratch))
         return RANS_ERR_INVALID_ARG;
@@ -148,12 +154,14 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     const MessageGeometry g = geometry(n_symbols, params);
     // Offsets are u32: the worst-case data region must fit.
     if (g.n_chunks > 0xFFFFFFFEull ||
-        4ull * params->n_lanes * g.n_chunks + 2ull * wps * n_symbols > 0xFFFFFFF0ull)
+        (4ull * params->n_lanes + (bytes ? 3u : 0u)) * g.n_chunks + 2ull * wps * n_symbols >
+            0xFFFFFFF0ull)
         return RANS_ERR_INVALID_ARG;
     const ScratchLayout sl =
         scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols, wps);
-    const uint64_t max_out = bypass ? rans_max_encoded_size_bypass(n_symbols, params)
-                                    : rans_max_encoded_size(n_symbols, params);
+    const uint64_t max_out = bypass  ? rans_max_encoded_size_bypass(n_symbols, params)
+                             : bytes ? rans_max_encoded_size_bytes(n_symbols, params)
+                                     : rans_max_encoded_size(n_symbols, params);
     if (out_cap < max_out || scratch_cap < sl.total) return RANS_ERR_BUFFER_TOO_SMALL;
 
     EncodeParams ep{};
@@ -183,8 +191,12 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
 
     if (g.n_chunks > 0) {
         int rc;
-        if (bypass) rc = ep.N == 32 ? launch_encode<32, true>(ep, st) : launch_encode<0, true>(ep, st);
-        else rc = ep.N == 32 ? launch_encode<32, false>(ep, st) : launch_encode<0, false>(ep, st);
+        if (bypass)
+            rc = ep.N == 32 ? launch_encode<32, kBypass>(ep, st) : launch_encode<0, kBypass>(ep, st);
+        else if (bytes)
+            rc = ep.N == 32 ? launch_encode<32, kBytes>(ep, st) : launch_encode<0, kBytes>(ep, st);
+        else
+            rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
         if (rc != RANS_OK) return rc;
     }
     FinalizeParams fp{};
@@ -197,7 +209,7 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     fp.CS = ep.CS;
     fp.n_chunks = ep.n_chunks;
     fp.data0 = uint32_t(g.data0);
-    fp.version = bypass ? RANS_VERSION_BYPASS : RANS_VERSION;
+    fp.version = bypass ? RANS_VERSION_BYPASS : bytes ? RANS_VERSION_BYTES : RANS_VERSION;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {
@@ -212,10 +224,20 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
         pp.data0 = fp.data0;
         pp.slot_bytes = ep.slot_bytes;
         const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
-        pack_kernel<<<grid, kPackThreads, 0, st>>>(pp);
+        if (bytes) pack_kernel<true><<<grid, kPackThreads, 0, st>>>(pp);
+        else pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
         if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     }
     return RANS_OK;
+}
+
+extern "C" int rans_encode_bytes(const uint8_t *d_symbols, uint64_t n_symbols,
+                                 const uint16_t *h_freq, uint32_t n_alpha,
+                                 const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                                 uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                                 uint64_t scratch_cap, rans_stream_t stream) {
+    return encode_message(d_symbols, nullptr, n_symbols, h_freq, nullptr, n_alpha, params, d_out,
+                          out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream, true);
 }
 
 extern "C" int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_freq,
@@ -309,7 +331,7 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     ep.slot_bytes = sl.slot_bytes;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
     if (g.n_chunks > 0) {
-        const int rc = ep.N == 32 ? launch_encode<32, false>(ep, st) : launch_encode<0, false>(ep, st);
+        const int rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
         if (rc != RANS_OK) return rc;
     }
     FinalizeParams fp{};
@@ -337,7 +359,7 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
         pp.data0 = fp.data0;
         pp.slot_bytes = ep.slot_bytes;
         const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
-        pack_kernel<<<grid, kPackThreads, 0, st>>>(pp);
+        pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
         if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     }
     return RANS_OK;

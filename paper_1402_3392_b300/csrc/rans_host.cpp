@@ -95,6 +95,14 @@ extern "C" uint64_t rans_max_encoded_size(uint64_t n_symbols, const rans_params 
     return g.data0 + round16(4ull * params->n_lanes * g.n_chunks + 2ull * n_symbols);
 }
 
+// A byte-wise chunk holds at most two bytes per symbol and up to 3 bytes of
+// padding.
+extern "C" uint64_t rans_max_encoded_size_bytes(uint64_t n_symbols, const rans_params *params) {
+    if (!params_ok(params)) return 0;
+    const MessageGeometry g = geometry(n_symbols, params);
+    return g.data0 + round16((4ull * params->n_lanes + 3) * g.n_chunks + 2ull * n_symbols);
+}
+
 // A bypass message can hold a raw word after every symbol as well.
 extern "C" uint64_t rans_max_encoded_size_bypass(uint64_t n_symbols, const rans_params *params) {
     if (!params_ok(params)) return 0;

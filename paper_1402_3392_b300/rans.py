@@ -31,6 +31,8 @@ __all__ = [
     "Server", "rans_check_bounded_wait", "rans_decode_host", "rans_decode_host_work_size",
     "decode_host", "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass",
     "rans_encode_bypass", "rans_decode_bypass", "encode_bypass", "decode_bypass",
+    "rans_max_encoded_size_bytes", "rans_encode_bytes", "rans_decode_bytes", "encode_bytes",
+    "decode_bytes",
 ]
 
 RANS_OK = 0
@@ -99,6 +101,9 @@ def _load() -> C.CDLL:
         "rans_encode_scratch_size_bypass": (u64, [u64, pp]),
         "rans_encode_bypass": (i32, [vp, vp, u64, vp, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_bypass": (i32, [vp, u64, vp, vp, u32, pp, vp, vp, u64, vp, vp]),
+        "rans_max_encoded_size_bytes": (u64, [u64, pp]),
+        "rans_encode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
@@ -278,6 +283,72 @@ def decode_bypass(msg, n_symbols: int, freq, raw_words, n_lanes: int = 32,
         if st != RANS_OK:
             raise RansError(st, "rans_decode_bypass (device status)")
     return out[:n_symbols], raw[:n_symbols], status
+
+
+def rans_max_encoded_size_bytes(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_max_encoded_size_bytes(int(n_symbols), C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_bytes(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out, out_cap,
+                      d_out_size, d_status, d_scratch, scratch_cap, stream=None, check=True) -> int:
+    """Byte-wise (b = 2^8, digits breadth-first per step, Section 5) encode."""
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_bytes(_ptr(d_symbols), int(n_symbols), f.ctypes.data, f.size, C.byref(p),
+                               _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
+                               _ptr(d_scratch), int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_bytes") if check else rc
+
+
+def rans_decode_bytes(d_msg, msg_size, freq, n_lanes, chunk_symbols, d_symbols, n_symbols,
+                      d_status, stream=None, check=True) -> int:
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_bytes(_ptr(d_msg), int(msg_size), f.ctypes.data, f.size, C.byref(p),
+                               _ptr(d_symbols), int(n_symbols), _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_decode_bytes") if check else rc
+
+
+def encode_bytes(symbols, freq, n_lanes: int = 32, chunk_symbols: int = 65536, stream=None,
+                 sync: bool = True):
+    """Encode a CUDA uint8 tensor as a byte-wise message; (message, size, status)."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size_bytes(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size(n, n_lanes, chunk_symbols)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(scap, 16), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode_bytes(symbols, n, freq, n_lanes, chunk_symbols, out, cap, size, status, scratch,
+                      scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode_bytes (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode_bytes(msg, n_symbols: int, freq, n_lanes: int = 32, chunk_symbols: int = 65536,
+                 stream=None, sync: bool = True):
+    """Decode a byte-wise message; (symbols, status)."""
+    import torch
+
+    dev = msg.device
+    out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode_bytes(msg, msg.numel(), freq, n_lanes, chunk_symbols, out, n_symbols, status,
+                      stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode_bytes (device status)")
+    return out[:n_symbols], status
 
 
 def rans_decode_host_work_size(msg_size: int, n_symbols: int) -> int:
