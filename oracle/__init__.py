@@ -140,6 +140,25 @@ def load(mutant: int = 0) -> C.CDLL:
         lib.orc_decode_message_bytes.argtypes = [_u8p, C.c_uint64, _u16p, C.c_uint32, C.c_uint32,
                                                  C.c_uint32, _u8p, C.c_uint64]
         lib.orc_decode_message_bytes.restype = C.c_int
+        lib.orc_encode_adaptive.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
+                                            C.c_uint32, C.c_uint64, _u32p, C.c_uint64, _u64p,
+                                            C.c_uint64, _u64p, _u64p]
+        lib.orc_encode_adaptive.restype = C.c_int
+        lib.orc_decode_adaptive.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
+                                            C.c_uint32, C.c_uint64, _u64p, C.c_uint64, _u64p,
+                                            C.c_uint64, _u32p, _u64p, _u64p]
+        lib.orc_decode_adaptive.restype = C.c_int
+        lib.orc_encode_chunk_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, _u8p, C.c_uint64,
+                                                  _u64p]
+        lib.orc_encode_chunk_adaptive.restype = C.c_int
+        lib.orc_decode_chunk_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, _u8p, C.c_uint64]
+        lib.orc_decode_chunk_adaptive.restype = C.c_int
+        lib.orc_encode_message_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                    _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_message_adaptive.restype = C.c_int
+        lib.orc_decode_message_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                    _u8p, C.c_uint64]
+        lib.orc_decode_message_adaptive.restype = C.c_int
         _LIBS[mutant] = lib
         return lib
 
@@ -492,6 +511,77 @@ class Oracle:
                                              _p(out, _u8p), n_sym)
         if rc != OK:
             raise OracleError(rc, "decode_chunk_bytes")
+        return out[:n_sym].copy()
+
+    # -- adaptive binary contexts, one per coder (Section 5) ---------------------
+    ADAPT_RATE = 5
+    ADAPT_P0 = 2048
+
+    def encode_adaptive(self, symbols, N=1, M=1 << 12, L=L_PROD, b=B_PROD, R=5, p0=2048):
+        """Binary symbols, coder j with its own adaptive probability.  Returns
+        dict(words, states)."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        cap = max(1, 64 * s.size + 64)
+        words = np.zeros(cap, dtype=np.uint64)
+        states = np.zeros(N, dtype=np.uint64)
+        nw = C.c_uint64(0)
+        rc = self.lib.orc_encode_adaptive(M, L, b, N, R, p0, _p(s, _u32p), s.size,
+                                          _p(words, _u64p), cap, C.byref(nw), _p(states, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "encode_adaptive")
+        return dict(words=words[: nw.value].copy(), states=states)
+
+    def decode_adaptive(self, words, states, n_sym, N=1, M=1 << 12, L=L_PROD, b=B_PROD, R=5,
+                        p0=2048):
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        st = np.ascontiguousarray(states, dtype=np.uint64)
+        sym = np.zeros(max(1, n_sym), dtype=np.uint32)
+        st_end = np.zeros(N, dtype=np.uint64)
+        used = C.c_uint64(0)
+        rc = self.lib.orc_decode_adaptive(M, L, b, N, R, p0, _p(w, _u64p), w.size, _p(st, _u64p),
+                                          n_sym, _p(sym, _u32p), C.byref(used),
+                                          _p(st_end, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "decode_adaptive")
+        return dict(symbols=sym[:n_sym].copy(), consumed=used.value, states_end=st_end)
+
+    def encode_message_adaptive(self, symbols, N=32, chunk_symbols=65536):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        cap = self.max_message_size(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message_adaptive(_p(s, _u8p), s.size, N, chunk_symbols,
+                                                  _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message_adaptive")
+        return out[: size.value].copy()
+
+    def decode_message_adaptive(self, msg, n_sym, N=32, chunk_symbols=65536):
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_message_adaptive(_p(m, _u8p), m.size, N, chunk_symbols,
+                                                  _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message_adaptive")
+        return out[:n_sym].copy()
+
+    def encode_chunk_adaptive(self, symbols, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        cap = 4 * N + 2 * s.size
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk_adaptive(_p(s, _u8p), s.size, N, _p(out, _u8p), cap,
+                                                C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk_adaptive")
+        return out[: size.value].copy()
+
+    def decode_chunk_adaptive(self, chunk, n_sym, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_chunk_adaptive(_p(c, _u8p), c.size, N, _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk_adaptive")
         return out[:n_sym].copy()
 
     def quantize(self, weights, log2_M=LOG2_M_PROD):

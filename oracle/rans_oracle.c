@@ -34,6 +34,9 @@
  *     a SIMD decoder reads the digits of a step breadth-first across its N
  *     lanes, which bakes N into the stream; orc_*_wide and the byte-wise
  *     container (b = 2^8) follow that order.
+ *   - Section 5, adaptive models: they vectorize when every lane has its own
+ *     context; orc_*_adaptive codes binary symbols with one adaptive
+ *     probability per coder.
  *   - Section 3, bypass: raw digits interleaved with the coded data.  A
  *     symbol may carry raw base-b digits that no coder touches; the encoder
  *     sends them right before encoding the symbol, the decoder reads them
@@ -512,6 +515,122 @@ int orc_decode_wide(const uint64_t *f, uint32_t n_alpha, uint64_t L, uint64_t b,
     return rc;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Adaptive binary models, one context per coder (Section 5: adaptive      */
+/* models vectorize when no two lanes update the same model).              */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Binary alphabet {0, 1}.  Coder j keeps its own probability p_j of a 0,
+ * scaled to M (1 <= p_j <= M-1), starting at p0.  Symbol s is coded with
+ * f_0 = p, f_1 = M - p, B_0 = 0, B_1 = p (the range form of Section 2), and
+ * afterwards the coder's context moves towards s:
+ *     s = 0:  p += (M - p) >> R        s = 1:  p -= p >> R
+ * Coder j's context sees only its own symbols j, j+N, j+2N, ...  The
+ * decoder updates after decoding; the encoder, which runs backwards, first
+ * runs every context forwards to know the p each symbol was coded with.
+ */
+static void adapt(u128 *p, uint32_t s, u128 M, uint32_t R)
+{
+    if (s == 0) *p += (M - *p) >> R;
+    else *p -= *p >> R;
+}
+
+static int adaptive_model(orc_model *m, u128 p, u128 M, uint64_t L, uint64_t b)
+{
+    uint64_t f[2] = {(uint64_t)p, (uint64_t)(M - p)};
+    return model_init(m, f, 2, L, b);
+}
+
+int orc_encode_adaptive(uint64_t M, uint64_t L, uint64_t b, uint32_t N, uint32_t R, uint64_t p0,
+                        const uint32_t *sym, uint64_t n_sym, uint64_t *words, uint64_t word_cap,
+                        uint64_t *n_words, uint64_t *states)
+{
+    if (N == 0 || M < 2 || p0 < 1 || p0 >= M || R == 0 || R > 30) return ORC_ERR_ARG;
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    u128 *ctx = (u128 *)malloc(sizeof(u128) * N);
+    u128 *pi = (u128 *)malloc(sizeof(u128) * (n_sym ? n_sym : 1));
+    int rc = ORC_OK;
+    uint64_t W = 0;
+    if (!mp || !x || !ctx || !pi) { rc = ORC_ERR_ARG; goto done; }
+    /* forward: the probability every symbol is coded with */
+    for (uint32_t j = 0; j < N; ++j) ctx[j] = p0;
+    for (uint64_t i = 0; i < n_sym; ++i) {
+        uint32_t j = coder_of(i, N);
+        if (sym[i] > 1) { rc = ORC_ERR_SYMBOL; goto done; }
+#if ORACLE_MUTANT == 11
+        adapt(&ctx[j], sym[i], M, R);          /* planted mistake: update before coding */
+        pi[i] = ctx[j];
+#else
+        pi[i] = ctx[j];
+        adapt(&ctx[j], sym[i], M, R);
+#endif
+    }
+    /* backwards: Algorithm 1 with symbol i's model */
+    if ((rc = adaptive_model(mp, p0, M, L, b)) != ORC_OK) goto done;
+    for (uint32_t j = 0; j < N; ++j) x[j] = initial_state(mp);
+    for (uint64_t i = n_sym; i-- > 0;) {
+        uint32_t j = coder_of(i, N), s = sym[i];
+        if ((rc = adaptive_model(mp, pi[i], M, L, b)) != ORC_OK) goto done;
+        while (!in_I(mp, C(mp, s, x[j]))) {
+            if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+            words[W++] = (uint64_t)(x[j] % mp->b);
+            x[j] = x[j] / mp->b;
+        }
+        x[j] = C(mp, s, x[j]);
+        if (!in_I(mp, x[j])) { rc = ORC_ERR_INVARIANT; goto done; }
+    }
+    for (uint64_t a = 0, z = W; a + 1 < z; ++a, --z) {
+        uint64_t t = words[a];
+        words[a] = words[z - 1];
+        words[z - 1] = t;
+    }
+    for (uint32_t j = 0; j < N; ++j) states[j] = (uint64_t)x[j];
+    *n_words = W;
+done:
+    free(mp); free(x); free(ctx); free(pi);
+    return rc;
+}
+
+int orc_decode_adaptive(uint64_t M, uint64_t L, uint64_t b, uint32_t N, uint32_t R, uint64_t p0,
+                        const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+                        uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed,
+                        uint64_t *states_out)
+{
+    if (N == 0 || M < 2 || p0 < 1 || p0 >= M || R == 0 || R > 30) return ORC_ERR_ARG;
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    u128 *ctx = (u128 *)malloc(sizeof(u128) * N);
+    int rc = ORC_OK;
+    uint64_t rp = 0;
+    if (!mp || !x || !ctx) { rc = ORC_ERR_ARG; goto done; }
+    if ((rc = adaptive_model(mp, p0, M, L, b)) != ORC_OK) goto done;
+    for (uint32_t j = 0; j < N; ++j) {
+        x[j] = states_in[j];
+        ctx[j] = p0;
+        if (!in_I(mp, x[j])) rc = ORC_ERR_CORRUPT;
+    }
+    for (uint64_t i = 0; !rc && i < n_sym; ++i) {
+        uint32_t j = coder_of(i, N), s;
+        if ((rc = adaptive_model(mp, ctx[j], M, L, b)) != ORC_OK) break;
+        x[j] = D(mp, x[j], &s);
+        sym_out[i] = s;
+        while (!in_I(mp, x[j])) {
+            if (rp >= n_words || x[j] >= mp->L * mp->b) { rc = ORC_ERR_CORRUPT; break; }
+            x[j] = mp->b * x[j] + words[rp++];
+        }
+        adapt(&ctx[j], s, M, R);
+    }
+    if (!rc) {
+        for (uint32_t j = 0; j < N; ++j) states_out[j] = (uint64_t)x[j];
+        *consumed = rp;
+    }
+done:
+    free(mp); free(x); free(ctx);
+    return rc;
+}
+
 /* Single coding-function evaluations, for checking the oracle against the
  * paper's printed example (Section 2.1).  *ok = 0 on bad input. */
 uint64_t orc_C(const uint64_t *f, uint32_t n_alpha, uint32_t s, uint64_t x, int *ok)
@@ -557,6 +676,9 @@ uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out,
 #define ORC_VERSION 1u
 #define ORC_VERSION_BYPASS 2u  /* messages with raw words (Section 3, bypass) */
 #define ORC_VERSION_BYTES 3u   /* byte-wise, width-baked messages (Section 5) */
+#define ORC_VERSION_ADAPTIVE 4u /* adaptive binary contexts, one per coder */
+#define ORC_ADAPT_RATE 5u      /* adaptive messages: p moves by (target - p) >> 5 */
+#define ORC_ADAPT_P0 2048u     /* ... from p = M/2 at the start of every chunk */
 #define ORC_L8 (1ull << 23)    /* byte-wise: L = 2^23, b = 2^8, I = [2^23, 2^31) */
 #define ORC_B8 (1ull << 8)
 #define ORC_L (1ull << 16)
@@ -799,6 +921,69 @@ int orc_decode_chunk_bytes(const uint8_t *chunk, uint64_t size, const uint16_t *
     return chunk_decode_bytes(chunk, size, freq, n_alpha, N, sym_out, n_c);
 }
 
+/* Adaptive chunk (version 4): [u32 state[N]][u16 words], M = 2^12, L = b =
+ * 2^16, binary symbols, per-coder contexts from p = M/2, rate 5. */
+static int chunk_encode_adaptive(const uint8_t *sym, uint64_t n_c, uint32_t N, uint8_t *out,
+                                 uint64_t cap, uint64_t *size)
+{
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1) * 2);
+    if (!s32 || !w) { free(s32); free(w); return ORC_ERR_ARG; }
+    for (uint64_t i = 0; i < n_c; ++i) s32[i] = sym[i];
+    uint64_t st[32], W = 0;
+    int rc = orc_encode_adaptive(1ull << ORC_LOG2_M, ORC_L, ORC_B, N, ORC_ADAPT_RATE, ORC_ADAPT_P0,
+                                 s32, n_c, w, 2 * (n_c ? n_c : 1), &W, st);
+    if (rc == ORC_OK) {
+        uint64_t need = 4ull * N + 2ull * W;
+        if (need > cap) rc = ORC_ERR_SPACE;
+        else {
+            for (uint32_t j = 0; j < N; ++j) put_u32(out + 4 * j, (uint32_t)st[j]);
+            for (uint64_t k = 0; k < W; ++k) put_u16(out + 4ull * N + 2 * k, (uint32_t)w[k]);
+            *size = need;
+        }
+    }
+    free(s32);
+    free(w);
+    return rc;
+}
+
+static int chunk_decode_adaptive(const uint8_t *chunk, uint64_t size, uint32_t N,
+                                 uint8_t *sym_out, uint64_t n_c)
+{
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    if (size < 4ull * N || ((size - 4ull * N) & 1)) return ORC_ERR_CORRUPT;
+    uint64_t W = (size - 4ull * N) / 2;
+    uint64_t st[32], st_end[32], used = 0;
+    for (uint32_t j = 0; j < N; ++j) st[j] = get_u32(chunk + 4 * j);
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (W ? W : 1));
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    if (!w || !s32) { free(w); free(s32); return ORC_ERR_ARG; }
+    for (uint64_t k = 0; k < W; ++k) w[k] = get_u16(chunk + 4ull * N + 2 * k);
+    int rc = orc_decode_adaptive(1ull << ORC_LOG2_M, ORC_L, ORC_B, N, ORC_ADAPT_RATE,
+                                 ORC_ADAPT_P0, w, W, st, n_c, s32, &used, st_end);
+    if (rc == ORC_OK) {
+        for (uint32_t j = 0; j < N; ++j)
+            if (st_end[j] != ORC_L) rc = ORC_ERR_CORRUPT;
+        if (used != W) rc = ORC_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_c; ++i) sym_out[i] = (uint8_t)s32[i];
+    }
+    free(w);
+    free(s32);
+    return rc;
+}
+
+int orc_encode_chunk_adaptive(const uint8_t *sym, uint64_t n_c, uint32_t N, uint8_t *out,
+                              uint64_t cap, uint64_t *size)
+{
+    return chunk_encode_adaptive(sym, n_c, N, out, cap, size);
+}
+int orc_decode_chunk_adaptive(const uint8_t *chunk, uint64_t size, uint32_t N, uint8_t *sym_out,
+                              uint64_t n_c)
+{
+    return chunk_decode_adaptive(chunk, size, N, sym_out, n_c);
+}
+
 /* Message = header + offsets + chunks; version 2 marks a bypass message,
  * version 3 a byte-wise one (bytes != 0). */
 static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
@@ -813,7 +998,8 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
     if (cap < data0) return ORC_ERR_SPACE;
     memset(out, 0, data0);
     put_u32(out + 0, ORC_MAGIC);
-    put_u32(out + 4, bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
+    put_u32(out + 4, bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
+                     : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
     put_u32(out + 8, N);
     put_u32(out + 12, ORC_LOG2_M);
     put_u32(out + 16, (uint32_t)n_sym);
@@ -828,10 +1014,13 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
         put_u32(out + 32 + 4 * c, (uint32_t)pos);
         uint64_t sz = 0;
         if (data0 + pos > cap) return ORC_ERR_SPACE;
-        int rc = bytes ? chunk_encode_bytes(sym + first, n_c, freq, n_alpha, N,
-                                            out + data0 + pos, cap - data0 - pos, &sz)
-                       : chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq, rawf,
-                                      n_alpha, N, out + data0 + pos, cap - data0 - pos, &sz);
+        int rc = bytes == 2 ? chunk_encode_adaptive(sym + first, n_c, N, out + data0 + pos,
+                                                    cap - data0 - pos, &sz)
+                 : bytes ? chunk_encode_bytes(sym + first, n_c, freq, n_alpha, N,
+                                              out + data0 + pos, cap - data0 - pos, &sz)
+                         : chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq,
+                                        rawf, n_alpha, N, out + data0 + pos, cap - data0 - pos,
+                                        &sz);
         if (rc) return rc;
         pos += sz;
     }
@@ -853,7 +1042,8 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
     if (size < 48 || (size & 15)) return ORC_ERR_CORRUPT;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
     uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
-    uint32_t version = bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
+    uint32_t version = bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
+                       : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
     if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != version ||
         get_u32(msg + 8) != N || get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym ||
         get_u32(msg + 24) != chunk_symbols || get_u32(msg + 28) != n_chunks)
@@ -870,10 +1060,12 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
         uint64_t first = c * chunk_symbols;
         uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
         if (z < a || z > end_all) return ORC_ERR_CORRUPT;
-        int rc = bytes ? chunk_decode_bytes(msg + data0 + a, z - a, freq, n_alpha, N,
-                                            sym_out + first, n_c)
-                       : chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N,
-                                      sym_out + first, raw_out ? raw_out + first : NULL, n_c);
+        int rc = bytes == 2 ? chunk_decode_adaptive(msg + data0 + a, z - a, N, sym_out + first,
+                                                    n_c)
+                 : bytes ? chunk_decode_bytes(msg + data0 + a, z - a, freq, n_alpha, N,
+                                              sym_out + first, n_c)
+                         : chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N,
+                                        sym_out + first, raw_out ? raw_out + first : NULL, n_c);
         if (rc && !rc_all) rc_all = rc;
     }
     return rc_all;
@@ -909,6 +1101,16 @@ int orc_decode_message_bypass(const uint8_t *msg, uint64_t size, const uint16_t 
     if (!rawf || !raw_out) return ORC_ERR_ARG;
     return message_decode(msg, size, freq, rawf, n_alpha, N, chunk_symbols, sym_out, raw_out,
                           n_sym, 0);
+}
+int orc_encode_message_adaptive(const uint8_t *sym, uint64_t n_sym, uint32_t N,
+                                uint32_t chunk_symbols, uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    return message_encode(sym, NULL, n_sym, NULL, NULL, 0, N, chunk_symbols, out, cap, size, 2);
+}
+int orc_decode_message_adaptive(const uint8_t *msg, uint64_t size, uint32_t N,
+                                uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
+{
+    return message_decode(msg, size, NULL, NULL, 0, N, chunk_symbols, sym_out, NULL, n_sym, 2);
 }
 int orc_encode_message_bytes(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
                              uint32_t n_alpha, uint32_t N, uint32_t chunk_symbols, uint8_t *out,

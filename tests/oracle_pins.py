@@ -688,6 +688,84 @@ def pin_bytes_container(o):
     assert np.array_equal(o.decode_message_bytes(m, msg.size, freq, N=N, chunk_symbols=CS), msg)
 
 
+# ----------------------------------------------------------------------------
+# Adaptive binary contexts, one per coder (Section 5)
+# ----------------------------------------------------------------------------
+
+def pin_adaptive_lanes_independent(o):
+    """Separate contexts per lane: with N coders, coder j's final state is
+    exactly that of a single coder run on symbols j, j+N, j+2N, ... alone, and
+    the interleaved stream decodes back."""
+    rng = np.random.default_rng(29)
+    for N in (2, 3, 8):
+        msg = (rng.random(40 * N + 5) < rng.uniform(0.02, 0.5)).astype(np.uint32)
+        enc = o.encode_adaptive(msg, N=N)
+        for j in range(N):
+            solo = o.encode_adaptive(msg[j::N], N=1)
+            assert int(enc["states"][j]) == int(solo["states"][0]), (N, j)
+        dec = o.decode_adaptive(enc["words"], enc["states"], msg.size, N=N)
+        assert np.array_equal(dec["symbols"], msg) and dec["consumed"] == enc["words"].size
+        assert all(int(v) == L16 for v in dec["states_end"])
+
+
+def pin_adaptive_brute_force(o):
+    """All binary messages up to 10 symbols, N = 1..3: distinct messages get
+    distinct encodings, and every one decodes back."""
+    for N in (1, 2, 3):
+        seen = {}
+        for n in range(0, 11):
+            for bits in itertools.product((0, 1), repeat=n):
+                enc = o.encode_adaptive(list(bits), N=N)
+                key = (n, tuple(enc["words"]), tuple(int(v) for v in enc["states"]))
+                assert key not in seen
+                seen[key] = bits
+                dec = o.decode_adaptive(enc["words"], enc["states"], n, N=N)
+                assert tuple(dec["symbols"]) == bits
+
+
+def pin_adaptive_size_and_learning(o):
+    """The coded size stays within the derived bound around the information
+    content of the probabilities the contexts give (reading 13, per symbol);
+    a long run of one bit costs a small fraction of a bit per symbol once the
+    context has learned it; the context never leaves [1, M-1] (else coding
+    would fail)."""
+    rng = np.random.default_rng(31)
+    M, R = 1 << 12, 5
+    for N, msg in ((1, (rng.random(3000) < 0.1).astype(np.uint32)),
+                   (4, (rng.random(4000) < 0.3).astype(np.uint32)),
+                   (2, np.concatenate([np.zeros(6000, np.uint32), np.ones(6000, np.uint32)]))):
+        ctx = [2048] * N
+        info = 0.0
+        for i, s in enumerate(msg):
+            j = i % N
+            f = ctx[j] if s == 0 else M - ctx[j]
+            info += math.log2(M / f)
+            ctx[j] = ctx[j] + ((M - ctx[j]) >> R) if s == 0 else ctx[j] - (ctx[j] >> R)
+            assert 1 <= ctx[j] <= M - 1
+        enc = o.encode_adaptive(msg, N=N)
+        W = enc["words"].size
+        bits = 16 * W + sum(math.log2(int(x) / L16) for x in enc["states"])
+        n = msg.size
+        lo = info + n * math.log2(15 / 16) - W * math.log2(17 / 16) - 1e-6
+        hi = info + n * math.log2(17 / 16) + 1e-6
+        assert lo <= bits <= hi, (N, lo, bits, hi)
+    assert bits / msg.size < 0.2      # the runs: far below 1 bit per symbol
+
+
+def pin_adaptive_container(o):
+    rng = np.random.default_rng(37)
+    msg = (rng.random(5000) < 0.2).astype(np.uint8)
+    m = o.encode_message_adaptive(msg, N=7, chunk_symbols=999)
+    assert int.from_bytes(m[4:8].tobytes(), "little") == 4
+    assert np.array_equal(o.decode_message_adaptive(m, msg.size, N=7, chunk_symbols=999), msg)
+    data0 = (32 + 4 * 7 + 15) // 16 * 16
+    offs = m[32:32 + 4 * 7].view(np.uint32)
+    enc = o.encode_adaptive(msg[:999].astype(np.uint32), N=7)
+    ch = m[data0 + offs[0]:data0 + offs[1]]
+    assert list(ch[:28].view(np.uint32)) == list(enc["states"])
+    assert list(ch[28:].view(np.uint16)) == list(enc["words"])
+
+
 ALL_PINS = [
     pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
     pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
@@ -696,5 +774,6 @@ ALL_PINS = [
     pin_brute_force_unique, pin_packed_io_equivalence, pin_round_trip_edges,
     pin_container_layout, pin_quantize, pin_bypass_paper_example,
     pin_bypass_without_raw_is_plain, pin_bypass_interleaved, pin_wide_one_lane_is_algorithm1,
-    pin_wide_breadth_first, pin_bytes_container,
+    pin_wide_breadth_first, pin_bytes_container, pin_adaptive_lanes_independent,
+    pin_adaptive_brute_force, pin_adaptive_size_and_learning, pin_adaptive_container,
 ]

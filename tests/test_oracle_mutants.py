@@ -7,13 +7,14 @@ The mutants are compiled from the same source with -DORACLE_MUTANT=k:
   7 off-by-one symbol search in D        8 quantizer ties go to the higher index
   9 sends a symbol's raw (bypass) digits after encoding it, not before
  10 lays a width-baked step's digits out depth-first, not breadth-first
+ 11 updates an adaptive context before coding the symbol, not after
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTANTS = range(1, 11)
+MUTANTS = range(1, 12)
 
 
 @pytest.mark.parametrize("k", MUTANTS)
