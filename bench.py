@@ -55,9 +55,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched,binary,single,serving,bypass,bytes",
+    ap.add_argument("--legs", default="batched,binary,single,serving,bypass,bytes,adaptive",
                     help="extra legs after the headline one: comma list of batched, binary, "
-                         "single, serving, bypass, bytes, none")
+                         "single, serving, bypass, bytes, adaptive, none")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -545,6 +545,54 @@ def bytes_leg(rans, dev, args, hbm):
                          "algorithmic_bytes_per_launch": alg}}
 
 
+def adaptive_leg(rans, dev, args, hbm):
+    """256 Mi bits whose statistics drift (P(0) constant over runs of 4096
+    symbols, U[0.001, 0.999] per run), coded with one adaptive context per
+    coder (Section 5): encode and decode timed, the round trip checked, the
+    size set beside one static binary model for the whole message."""
+    import torch
+
+    cfg = wl.WORKLOADS["adaptive"]
+    n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    sym = wl.drifting_bits_device(n, cfg["segment"], wl.seed_for("adaptive"), dev, cfg["p0_lo"],
+                                  cfg["p0_hi"])
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    scap = rans.rans_encode_scratch_size_adaptive(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    enc = lambda: rans.rans_encode_adaptive(sym, n, N, CS, msg, cap, size, est, scratch, scap)  # noqa: E731
+    enc()
+    torch.cuda.synchronize()
+    assert int(est.item()) == 0
+    msg_size = int(size.item())
+    enc_ms = statistics.median(_events(torch, enc, 5))
+    p1 = float(sym.float().mean().item())
+    freq = rans.rans_quantize_table(wl.weights_from_probs(np.array([1.0 - p1, p1])))
+    del scratch
+    static_size = int(rans.encode(sym, freq, N, CS)[1].item())   # not timed
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    dst = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode_adaptive(msg, msg_size, N, CS, out, n, dst)  # noqa: E731
+    dec()
+    torch.cuda.synchronize()
+    ok = int(dst.item()) == 0 and torch.equal(out, sym)
+    dec_ms = statistics.median(_events(torch, dec, 10))
+    alg = msg_size + n
+    return {"workload": f"{n} bits, P(0) ~ U[{cfg['p0_lo']}, {cfg['p0_hi']}] per run of "
+                        f"{cfg['segment']}, {n // CS} chunks x {CS}, N = {N}, one adaptive "
+                        f"context per coder (rate 1/32)",
+            "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
+            "encode_gbs": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
+            "bits_per_symbol": 8 * msg_size / n, "static_bits_per_symbol": 8 * static_size / n,
+            "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "decode_kernel (adaptive)", "bound": "hbm",
+                         "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def single_leg(rans, dev, args):
     """One 1 MiB stream, Zipf(1.2) over 256 symbols, 32 coders in one chunk:
     a single warp's chain of 32768 dependent steps, so a latency figure."""
@@ -801,6 +849,9 @@ def main(argv=None):
         torch.cuda.empty_cache()
     if "bytes" in legs:
         extra["bytes"] = bytes_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
+    if "adaptive" in legs:
+        extra["adaptive"] = adaptive_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
 
     if rank == 0:

@@ -82,6 +82,7 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_VERSION       1u
 #define RANS_VERSION_BYPASS 2u         /* messages with raw words (rans_encode_bypass) */
 #define RANS_VERSION_BYTES 3u          /* byte-wise messages (rans_encode_bytes) */
+#define RANS_VERSION_ADAPTIVE 4u       /* adaptive binary messages (rans_encode_adaptive) */
 
 typedef struct {
     uint32_t n_lanes;        /* N interleaved coders per chunk, 1..32 */
@@ -255,6 +256,32 @@ int rans_encode_bytes(const uint8_t *d_symbols, uint64_t n_symbols, const uint16
 int rans_decode_bytes(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
                       uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
                       uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
+
+/*
+ * Adaptive binary messages -- Section 5 of the paper: adaptive models still
+ * vectorize when no two lanes update the same model, e.g. with one context
+ * per lane.  Symbols are bytes 0 or 1.  Coder j keeps its own context p (the
+ * probability of a 0, scaled to M = 2^12, starting at M/2 in every chunk);
+ * a symbol is coded with f_0 = p, f_1 = M - p and afterwards p moves towards
+ * it by (target - p) >> 5.  Coder j's context sees only its own symbols, so
+ * the stream depends on N like the rest of the container.  L = b = 2^16,
+ * 16-bit words, version 4 (RANS_VERSION_ADAPTIVE).  No model table is passed.
+ *
+ * rans_encode_adaptive: as rans_encode without the model; out_cap >=
+ *   rans_max_encoded_size(...), scratch_cap >=
+ *   rans_encode_scratch_size_adaptive(...) (the plain scratch plus a u16 per
+ *   symbol: the encoder runs the contexts forwards, then codes backwards).
+ *   A symbol other than 0 or 1 gives RANS_ERR_ZERO_FREQ.
+ * rans_decode_adaptive: as rans_decode without the model.
+ */
+uint64_t rans_encode_scratch_size_adaptive(uint64_t n_symbols, const rans_params *params);
+int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols, const rans_params *params,
+                         uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_size,
+                         uint32_t *d_status, void *d_scratch, uint64_t scratch_cap,
+                         rans_stream_t stream);
+int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size, const rans_params *params,
+                         uint8_t *d_symbols, uint64_t n_symbols, uint32_t *d_status,
+                         rans_stream_t stream);
 
 /*
  * Batched decoding: many independent messages ("streams"), each with its own

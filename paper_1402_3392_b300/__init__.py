@@ -14,6 +14,8 @@ _BINDING = frozenset({
     "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass", "rans_encode_bypass",
     "rans_decode_bypass", "encode_bypass", "decode_bypass", "rans_max_encoded_size_bytes",
     "rans_encode_bytes", "rans_decode_bytes", "encode_bytes", "decode_bytes",
+    "rans_encode_scratch_size_adaptive", "rans_encode_adaptive", "rans_decode_adaptive",
+    "encode_adaptive", "decode_adaptive",
 })
 
 

@@ -77,6 +77,14 @@ constexpr uint32_t kSmemBytes = kFlagsOffset + 256;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 // Byte-wise messages (version 3): L = 2^23, b = 2^8, I = [2^23, 2^31).
 constexpr uint32_t kL8 = 1u << 23;
+// Message kinds: plain (version 1), bypass (2: raw words after symbols),
+// byte-wise (3: b = 2^8, digits breadth-first), adaptive (4: binary symbols,
+// one adaptive context per coder).
+constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3;
+// Adaptive contexts: p = probability of a 0 scaled to M, from M/2, moving by
+// (target - p) >> kAdaptRate after every symbol.
+constexpr uint32_t kAdaptRate = 5;
+constexpr uint32_t kAdaptP0 = kM / 2;
 
 struct Smem {
     uint32_t *tab;
@@ -277,6 +285,7 @@ struct Chain {
     uint32_t steps;      // full steps (all N coders) left
     uint32_t rem;        // coders with a symbol in the final partial step
     uint32_t st;         // RANS_OK, or the error found when opening
+    uint32_t p;          // adaptive messages: this lane's context
     uint32_t rp0;        // byte-wise messages: rp at the first digit
     uint32_t len;        // byte-wise messages: chunk bytes (states, digits, padding)
 };
@@ -290,6 +299,7 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.next_evt = 0xFFFFFFFFu;
     c.st = RANS_OK;
     c.rp0 = c.len = 0;
+    c.p = kAdaptP0;
 }
 
 // Open chunk [o, e) (byte offsets in the data region that starts at msg +
@@ -465,59 +475,74 @@ __device__ __forceinline__ void decode_step_bytes(uint32_t &x, uint32_t &rp, boo
     }
 }
 
-// Decode what is left of one chunk on its own.  RAW: a bypass chunk.
-template <bool FULL, class G, bool RAW = false, bool BYTES = false>
+// One step of an adaptive chunk (binary symbols, Section 5): the lane's own
+// context p gives f_0 = p, f_1 = M - p, B_1 = p; no table.  D, then the
+// context moves towards the decoded bit, then the usual renormalization.
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step_adaptive(uint32_t &x, uint32_t &p, uint32_t &rp,
+                                                     bool active, uint32_t ring_s, uint8_t *outp,
+                                                     uint32_t lt) {
+    const bool on = FULL || active;
+    if (on) {
+        const uint32_t slot = x & (kM - 1);
+        const bool one = slot >= p;
+        const uint32_t f = one ? kM - p : p;
+        x = imad(f, x >> kLog2M, slot - (one ? p : 0u));
+        *outp = uint8_t(one);
+        p = one ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+    }
+    const bool need = on && x < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
+    rp = imad(__popc(m), 2u, rp);
+}
+
+// One step of chunk c of message kind KIND; outp/rawp: this step's output.
+template <bool FULL, uint32_t RING, int KIND>
+__device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s, uint32_t ring_s,
+                                          uint32_t flags_s, uint8_t *outp, uint16_t *rawp,
+                                          uint32_t lt) {
+    if (KIND == kKindRaw)
+        decode_step_raw<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, flags_s, outp, rawp, lt);
+    else if (KIND == kKindBytes)
+        decode_step_bytes<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
+    else if (KIND == kKindAdaptive)
+        decode_step_adaptive<FULL, RING>(c.x, c.p, c.rp, active, ring_s, outp, lt);
+    else
+        decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
+}
+
+// Decode what is left of one chunk on its own.
+template <bool FULL, class G, int KIND = kKindPlain>
 __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &timeouts, uint32_t N,
                                           bool lane_on, uint32_t lane, uint32_t tab_s, uint32_t lt,
                                           uint32_t flags_s = 0) {
+    constexpr bool RAW = KIND == kKindRaw;
     for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
         chain_service<G>(c, r, timeouts, lane);
 #pragma unroll
-        for (uint32_t u = 0; u < G::kGroup; ++u) {
-            if (RAW)
-                decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s,
-                                                c.outp + u * N, c.rawp + u * N, lt);
-            else if (BYTES)
-                decode_step_bytes<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s,
-                                                  c.outp + u * N, lt);
-            else
-                decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp + u * N,
-                                            lt);
-        }
+        for (uint32_t u = 0; u < G::kGroup; ++u)
+            kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp + u * N,
+                                            RAW ? c.rawp + u * N : nullptr, lt);
         c.outp += G::kGroup * N;
         if (RAW) c.rawp += G::kGroup * N;
     }
     for (uint32_t t = c.steps % G::kGroup; t > 0; --t) {
         chain_service<G>(c, r, timeouts, lane);
-        if (RAW)
-            decode_step_raw<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, flags_s, c.outp,
-                                            c.rawp, lt);
-        else if (BYTES)
-            decode_step_bytes<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
-        else
-            decode_step<FULL, G::kRing>(c.x, c.rp, lane_on, tab_s, r.ring_s, c.outp, lt);
+        kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp, c.rawp, lt);
         c.outp += N;
         if (RAW) c.rawp += N;
     }
     c.steps = 0;
     if (c.rem) {
         chain_service<G>(c, r, timeouts, lane);
-        if (RAW)
-            decode_step_raw<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, flags_s,
-                                             c.outp, c.rawp, lt);
-        else if (BYTES)
-            decode_step_bytes<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp,
-                                               lt);
-        else
-            decode_step<false, G::kRing>(c.x, c.rp, lane < c.rem, tab_s, r.ring_s, c.outp, lt);
+        kind_step<false, G::kRing, KIND>(c, lane < c.rem, tab_s, r.ring_s, flags_s, c.outp,
+                                         c.rawp, lt);
         c.rem = 0;
     }
 }
 
-// Wait for the copies still in flight, so that the ring and the barrier
-// phases are clean for the next chunk, and check the chunk's end: a
-// well-formed chunk ends with every coder back at x0 = L and every word read
-// exactly once (decoder and encoder in lockstep, Section 3).
 // Byte-wise chunks end in zero padding up to a multiple of 4 bytes: the chunk
 // must be exactly round4(4N + digits read) long, with zeros after the digits
 // (src + rp .. src + endrel, at most 3 bytes).
@@ -587,7 +612,7 @@ __device__ __forceinline__ uint32_t const_chunk_raw(const uint8_t *msg, uint32_t
 // raw_out[i] and flags_s addresses the 256 raw-word flags.  const_sym !=
 // kNoConst: the model has one symbol with f = M.  Returns the warp-uniform
 // status (RANS_OK, or the first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
-template <int NT, bool PAIR, bool RAW = false, bool BYTES = false>  // NT = 32: all lanes are coders
+template <int NT, bool PAIR, int KIND = kKindPlain>  // NT = 32: all lanes are coders
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
@@ -595,8 +620,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
                                                   uint8_t *out, uint32_t const_sym, uint32_t lane,
                                                   uint32_t lt, uint16_t *raw_out = nullptr,
                                                   uint32_t flags_s = 0, bool const_raw = false) {
-    static_assert(!(PAIR && (RAW || BYTES)), "bypass and byte-wise messages: one chunk per warp");
-    static_assert(!(RAW && BYTES), "one message kind");
+    constexpr bool RAW = KIND == kKindRaw;
+    constexpr bool BYTES = KIND == kKindBytes;
+    static_assert(!(PAIR && KIND != kKindPlain), "only plain messages pair chunks");
     using G = typename std::conditional<RAW, GeoRaw,
                                         typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type;
     constexpr bool kFullWarp = NT == 32;
@@ -608,7 +634,7 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     const uint32_t n_b = two ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
     const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = two ? offs[c + 2] : 0u;
 
-    if (const_sym != kNoConst) {
+    if (KIND != kKindAdaptive && const_sym != kNoConst) {
         if (RAW)
             return const_chunk_raw(msg, data0, o0, o1, data_end, n_a, N, out + first,
                                    raw_out + first, const_sym, const_raw, lane);
@@ -647,8 +673,7 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
             b.outp += G::kGroup * N;
         }
     }
-    chain_run<kFullWarp, G, RAW, BYTES>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt,
-                                        flags_s);
+    chain_run<kFullWarp, G, KIND>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
     if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
     const uint32_t sa = chain_close<G, BYTES>(a, w.r[0], w.timeouts, lane_on, N);
     const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;

@@ -46,12 +46,16 @@ constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
 constexpr uint32_t kRawFlag = 1u << 18;   // encode-table bit: the symbol carries a raw word
 constexpr uint32_t kL8 = 1u << 23;         // byte-wise messages: L = 2^23, b = 2^8
+// Adaptive messages: binary symbols, each coder's context p (probability of
+// a 0 scaled to M) starts at M/2 and moves by (target - p) >> kAdaptRate.
+constexpr uint32_t kAdaptRate = 5;
+constexpr uint32_t kAdaptP0 = kM / 2;
 
 // Scratch of one message, all sections 16-byte aligned: one worst-case slot
 // of words per chunk (written backwards from its end), then the chunks'
 // final states, first-word offsets and byte sizes.
 struct ScratchLayout {
-    uint64_t words, states, wstart, sizes, total;
+    uint64_t words, states, wstart, sizes, probs, total;
     uint32_t slot_bytes;
 };
 
@@ -65,6 +69,7 @@ __host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint3
     s.wstart = s.states + ((n_chunks * N * 4 + 15) & ~uint64_t(15));
     s.sizes = s.wstart + ((n_chunks * 4 + 15) & ~uint64_t(15));
     s.total = s.sizes + ((n_chunks * 4 + 15) & ~uint64_t(15));
+    s.probs = s.total;  // adaptive messages: one u16 context per symbol follows
     return s;
 }
 
@@ -209,6 +214,50 @@ __device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uin
     }
 }
 
+// Adaptive chunks, pass 1: run every coder's context forwards over its own
+// symbols and store the p each symbol will be coded with (probs[i] for
+// symbol i of the chunk).  A symbol other than 0 or 1 sets kZeroFlag in acc.
+__device__ __forceinline__ void adaptive_forward(const uint8_t *sym, uint32_t n_c, uint32_t N,
+                                                 uint16_t *probs, uint32_t lane, uint32_t &acc) {
+    uint32_t p = kAdaptP0;
+    for (uint32_t i = lane; lane < N && i < n_c; i += N) {
+        const uint32_t s = sym[i];
+        probs[i] = uint16_t(p);
+        if (s > 1u) acc |= kZeroFlag;
+        p = s ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+    }
+}
+
+// Adaptive chunks, pass 2, one step: symbol s (0 or 1) coded with the stored
+// context p: f = p or M - p, B = 0 or p.  floor(x/f) comes from a float
+// estimate rounded towards zero throughout -- never above x/f, and below it
+// by less than 1 since x < f * 2^20 here -- and one exact correction.
+template <bool FULL>
+__device__ __forceinline__ void encode_step_adaptive(uint32_t &x, uint32_t &wp, bool active,
+                                                     uint32_t s, uint32_t p, uint32_t ring_s,
+                                                     uint32_t ge) {
+    const bool on = FULL || active;
+    const bool one = s != 0u;
+    const uint32_t f = one ? kM - p : p;
+    const bool emit = on && x >= (f << 20);
+    const uint32_t m = __ballot_sync(kFull, emit);
+    if (emit) {
+        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        x >>= 16;
+    }
+    wp -= 2u * __popc(m);
+    if (on) {
+        const float rf = __frcp_rz(float(f));
+        uint32_t q = __float2uint_rz(__fmul_rz(__uint2float_rz(x), rf));
+        uint32_t r = x - q * f;
+        if (r >= f) {
+            ++q;
+            r -= f;
+        }
+        x = (q << kLog2M) + (one ? p : 0u) + r;
+    }
+}
+
 // One step of a bypass chunk (Section 3): a lane whose symbol carries a raw
 // word rw sends it before encoding the symbol, so in the stream (decoder
 // order) it follows that lane's renormalization word.  One reverse-lane
@@ -247,18 +296,20 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // bypass chunk, raw[i] is the raw word of symbol i (used where the symbol
 // carries one); groups are halved so that a group still writes at most 1 KiB.
 // BYTES: a byte-wise chunk (at most 2 bytes per symbol, size padded to 4).
-template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false>
+// ADAPT: an adaptive chunk; raw then points at the contexts pass 1 stored.
+template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
                                              uint32_t tab_s, uint32_t ring_s, uint32_t ge,
                                              uint32_t lane, uint32_t &acc,
                                              const uint16_t *raw = nullptr) {
-    static_assert(!(RAW && PREFETCH), "bypass chunks load each group's symbols up front");
+    static_assert(!((RAW || ADAPT) && PREFETCH), "these chunks load each group up front");
     constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
+    constexpr bool kWord = RAW || ADAPT;  // a u16 per symbol: raw word or context
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
-    const uint16_t *rawp = RAW ? raw + lane : nullptr;
+    const uint16_t *rawp = kWord ? raw + lane : nullptr;
     uint32_t x = BYTES ? kL8 : kL;
     uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
     uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
@@ -290,7 +341,10 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     if (rem) {
         const bool act = lane < rem;
         const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
-        if (RAW) {
+        if (ADAPT) {
+            const uint32_t pw = act ? rawp[uint64_t(T_full) * N] : kAdaptP0;
+            encode_step_adaptive<false>(x, wp, act, s, pw, ring_s, ge);
+        } else if (RAW) {
             const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
             encode_step_raw<false>(x, wp, acc, act, s, rw, tab_s, ring_s, ge);
         } else {
@@ -302,7 +356,10 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     for (uint32_t r = T_full % kG; r > 0; --r, --t) {
         service();
         const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
-        if (RAW) {
+        if (ADAPT) {
+            const uint32_t pw = lane_on ? rawp[uint64_t(t) * N] : kAdaptP0;
+            encode_step_adaptive<NT == 32>(x, wp, lane_on, s, pw, ring_s, ge);
+        } else if (RAW) {
             const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
             encode_step_raw<NT == 32>(x, wp, acc, lane_on, s, rw, tab_s, ring_s, ge);
         } else {
@@ -337,12 +394,14 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
 #pragma unroll
             for (uint32_t u = 0; u < kG; ++u) {
                 cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
-                if (RAW) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : 0u;
+                if (kWord) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : kAdaptP0;
             }
             service();
 #pragma unroll
             for (uint32_t u = 0; u < kG; ++u) {
-                if (RAW)
+                if (ADAPT)
+                    encode_step_adaptive<NT == 32>(x, wp, lane_on, cur[u], curw[u], ring_s, ge);
+                else if (RAW)
                     encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
                                               ge);
                 else

@@ -36,8 +36,10 @@ struct DecodeParams {
 };
 
 // Message kinds: plain (version 1), bypass (version 2: raw words after their
-// symbols) and byte-wise (version 3: b = 2^8, digits breadth-first per step).
-constexpr int kPlain = 0, kBypass = 1, kBytes = 2;
+// symbols), byte-wise (version 3: b = 2^8, digits breadth-first per step) and
+// adaptive (version 4: binary symbols, one adaptive context per coder).
+constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::kKindBytes,
+              kAdaptive = dec::kKindAdaptive;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  Bypass and
 // byte-wise messages are decoded one chunk per warp.
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     decode_kernel(const __grid_constant__ DecodeParams p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
+    constexpr bool ADAPTIVE = KIND == kAdaptive;
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -55,11 +58,13 @@ __global__ void __launch_bounds__(dec::kThreads)
     if (threadIdx.x == 0) {
         hdr_ok = dec::header_ok(p.msg, p.msg_size, p.data0, p.n_sym, p.N, p.CS, p.n_chunks,
                                 RAW ? RANS_VERSION_BYPASS : BYTES ? RANS_VERSION_BYTES
+                                : ADAPTIVE                        ? RANS_VERSION_ADAPTIVE
                                                                   : RANS_VERSION);
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
-    dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
+    if (ADAPTIVE) __syncthreads();  // no table: the contexts live in registers
+    else dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
     if (!hdr_ok) {
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
         return;
@@ -77,14 +82,15 @@ __global__ void __launch_bounds__(dec::kThreads)
         const uint32_t count = min(per, p.c_end - c);
         uint32_t st;
         if (RAW)
-            st = dec::decode_chunks<NT, false, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
-                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
-                                                     p.raw_out, sm.flags_s,
-                                                     cs != dec::kNoConst && sm.flags[cs & 0xFFu]);
-        else if (BYTES)
-            st = dec::decode_chunks<NT, false, false, true>(wr, sm.tab_s, p.msg, p.data0, offs,
-                                                            data_end, c, 1, p.n_sym, p.CS, p.N,
-                                                            p.out, cs, lane, lt);
+            st = dec::decode_chunks<NT, false, kBypass>(wr, sm.tab_s, p.msg, p.data0, offs,
+                                                        data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
+                                                        cs, lane, lt, p.raw_out, sm.flags_s,
+                                                        cs != dec::kNoConst &&
+                                                            sm.flags[cs & 0xFFu]);
+        else if (BYTES || ADAPTIVE)
+            st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
+                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
+                                                     lt);
         else
             st = per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs,
                                                         data_end, c, count, p.n_sym, p.CS, p.N,
@@ -174,6 +180,8 @@ static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaSt
         return p.N == 32 ? launch_decode<32, kBypass>(p, st) : launch_decode<0, kBypass>(p, st);
     if (p.kind == kBytes)
         return p.N == 32 ? launch_decode<32, kBytes>(p, st) : launch_decode<0, kBytes>(p, st);
+    if (p.kind == kAdaptive)
+        return p.N == 32 ? launch_decode<32, kAdaptive>(p, st) : launch_decode<0, kAdaptive>(p, st);
     return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 
@@ -227,6 +235,23 @@ extern "C" int rans_decode_bytes(const uint8_t *d_msg, uint64_t msg_size, const 
     p.out = d_symbols;
     p.status = d_status;
     p.kind = kBytes;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+extern "C" int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size,
+                                    const rans_params *params, uint8_t *d_symbols,
+                                    uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
+    uint16_t any_model[2] = {RANS_M / 2, RANS_M / 2};  // the contexts need no table
+    DecodeParams p;
+    const int rc = prepare_decode(d_msg, msg_size, any_model, 2, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.status = d_status;
+    p.kind = kAdaptive;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     return launch_range(p, 0, p.n_chunks, st);

@@ -30,35 +30,39 @@ struct EncodeParams {
     uint32_t n_chunks;
     uint32_t slot_bytes;
     const uint16_t *raw;  // bypass messages: raw word of each symbol
+    uint16_t *probs;      // adaptive messages: scratch, the context of each symbol
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
 
 // Message kinds: plain (version 1), bypass (version 2: a raw word after every
-// symbol that carries one) and byte-wise (version 3: b = 2^8).
-constexpr int kPlain = 0, kBypass = 1, kBytes = 2;
+// symbol that carries one), byte-wise (version 3: b = 2^8) and adaptive
+// (version 4: binary symbols, one adaptive context per coder).
+constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
 
 template <int NT, int KIND>
 __global__ void __launch_bounds__(enc::kThreads)
     encode_kernel(const __grid_constant__ EncodeParams p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
+    constexpr bool ADAPT = KIND == kAdaptive;
     extern __shared__ __align__(128) uint8_t smem[];
     const enc::Smem sm = enc::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings),
-                            RAW ? p.raw_words : nullptr);
+    if (!ADAPT)  // adaptive contexts need no table
+        enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings),
+                                RAW ? p.raw_words : nullptr);
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
     for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        enc::encode_chunk<NT, !RAW, RAW, BYTES>(p.sym + first, n_c, p.N,
-                                         p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
-                                         p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N,
-                                         sm.tab_s, ring_s, ge, lane, acc,
-                                         RAW ? p.raw + first : nullptr);
+        if (ADAPT) enc::adaptive_forward(p.sym + first, n_c, p.N, p.probs + first, lane, acc);
+        enc::encode_chunk<NT, !RAW && !ADAPT, RAW, BYTES, ADAPT>(
+            p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
+            p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
+            acc, RAW ? p.raw + first : ADAPT ? p.probs + first : nullptr);
     }
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
@@ -142,7 +146,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
                           const uint16_t *h_freq, const uint8_t *raw_words, uint32_t n_alpha,
                           const rans_params *params, uint8_t *d_out, uint64_t out_cap,
                           uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
-                          uint64_t scratch_cap, rans_stream_t stream, bool bytes = false) {
+                          uint64_t scratch_cap, rans_stream_t stream, bool bytes = false,
+                          bool adaptive = false) {
     if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
         !d_status || !d_scratch || !aligned16(d_out) || !aligned16(d_scratch))
         return RANS_ERR_INVALID_ARG;
@@ -162,7 +167,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     const uint64_t max_out = bypass  ? rans_max_encoded_size_bypass(n_symbols, params)
                              : bytes ? rans_max_encoded_size_bytes(n_symbols, params)
                                      : rans_max_encoded_size(n_symbols, params);
-    if (out_cap < max_out || scratch_cap < sl.total) return RANS_ERR_BUFFER_TOO_SMALL;
+    const uint64_t need_scratch = adaptive ? sl.probs + round16(2 * n_symbols) : sl.total;
+    if (out_cap < max_out || scratch_cap < need_scratch) return RANS_ERR_BUFFER_TOO_SMALL;
 
     EncodeParams ep{};
     if (bypass) {
@@ -181,6 +187,7 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.states = reinterpret_cast<uint32_t *>(scr + sl.states);
     ep.wstart = reinterpret_cast<uint32_t *>(scr + sl.wstart);
     ep.sizes = reinterpret_cast<uint32_t *>(scr + sl.sizes);
+    ep.probs = reinterpret_cast<uint16_t *>(scr + sl.probs);
     ep.status = d_status;
     ep.n_sym = n_symbols;
     ep.N = params->n_lanes;
@@ -191,7 +198,9 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
 
     if (g.n_chunks > 0) {
         int rc;
-        if (bypass)
+        if (adaptive)
+            rc = ep.N == 32 ? launch_encode<32, kAdaptive>(ep, st) : launch_encode<0, kAdaptive>(ep, st);
+        else if (bypass)
             rc = ep.N == 32 ? launch_encode<32, kBypass>(ep, st) : launch_encode<0, kBypass>(ep, st);
         else if (bytes)
             rc = ep.N == 32 ? launch_encode<32, kBytes>(ep, st) : launch_encode<0, kBytes>(ep, st);
@@ -209,7 +218,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     fp.CS = ep.CS;
     fp.n_chunks = ep.n_chunks;
     fp.data0 = uint32_t(g.data0);
-    fp.version = bypass ? RANS_VERSION_BYPASS : bytes ? RANS_VERSION_BYTES : RANS_VERSION;
+    fp.version = bypass ? RANS_VERSION_BYPASS : bytes ? RANS_VERSION_BYTES
+                 : adaptive ? RANS_VERSION_ADAPTIVE : RANS_VERSION;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {
@@ -229,6 +239,23 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
         if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     }
     return RANS_OK;
+}
+
+extern "C" uint64_t rans_encode_scratch_size_adaptive(uint64_t n_symbols, const rans_params *params) {
+    if (!params_ok(params)) return 0;
+    const MessageGeometry g = geometry(n_symbols, params);
+    return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).probs +
+           round16(2 * n_symbols);
+}
+
+extern "C" int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols,
+                                    const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                                    uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                                    uint64_t scratch_cap, rans_stream_t stream) {
+    const uint16_t any_model[2] = {RANS_M / 2, RANS_M / 2};  // the contexts need no table
+    return encode_message(d_symbols, nullptr, n_symbols, any_model, nullptr, 2, params, d_out,
+                          out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream, false,
+                          true);
 }
 
 extern "C" int rans_encode_bytes(const uint8_t *d_symbols, uint64_t n_symbols,

@@ -104,6 +104,9 @@ def _load() -> C.CDLL:
         "rans_max_encoded_size_bytes": (u64, [u64, pp]),
         "rans_encode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
+        "rans_encode_scratch_size_adaptive": (u64, [u64, pp]),
+        "rans_encode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp]),
         "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
@@ -348,6 +351,70 @@ def decode_bytes(msg, n_symbols: int, freq, n_lanes: int = 32, chunk_symbols: in
         st = int(status.item())
         if st != RANS_OK:
             raise RansError(st, "rans_decode_bytes (device status)")
+    return out[:n_symbols], status
+
+
+def rans_encode_scratch_size_adaptive(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_encode_scratch_size_adaptive(int(n_symbols),
+                                                     C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_adaptive(d_symbols, n_symbols, n_lanes, chunk_symbols, d_out, out_cap, d_out_size,
+                         d_status, d_scratch, scratch_cap, stream=None, check=True) -> int:
+    """Adaptive binary encode: one context per coder (Section 5)."""
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_adaptive(_ptr(d_symbols), int(n_symbols), C.byref(p), _ptr(d_out),
+                                  int(out_cap), _ptr(d_out_size), _ptr(d_status), _ptr(d_scratch),
+                                  int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_adaptive") if check else rc
+
+
+def rans_decode_adaptive(d_msg, msg_size, n_lanes, chunk_symbols, d_symbols, n_symbols, d_status,
+                         stream=None, check=True) -> int:
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_adaptive(_ptr(d_msg), int(msg_size), C.byref(p), _ptr(d_symbols),
+                                  int(n_symbols), _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_decode_adaptive") if check else rc
+
+
+def encode_adaptive(symbols, n_lanes: int = 32, chunk_symbols: int = 65536, stream=None,
+                    sync: bool = True):
+    """Encode a CUDA uint8 tensor of bits (0/1) as an adaptive message; (message, size, status)."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size_adaptive(n, n_lanes, chunk_symbols)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(scap, 16), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode_adaptive(symbols, n, n_lanes, chunk_symbols, out, cap, size, status, scratch,
+                         scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode_adaptive (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode_adaptive(msg, n_symbols: int, n_lanes: int = 32, chunk_symbols: int = 65536,
+                    stream=None, sync: bool = True):
+    """Decode an adaptive message; (bits, status)."""
+    import torch
+
+    dev = msg.device
+    out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode_adaptive(msg, msg.numel(), n_lanes, chunk_symbols, out, n_symbols, status, stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode_adaptive (device status)")
     return out[:n_symbols], status
 
 

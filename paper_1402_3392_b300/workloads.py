@@ -23,6 +23,9 @@ Workloads (sizes and distributions):
   bypass   : 512 Mi i.i.d. bytes of the chunked distribution with raw words
              (bypass coding, 8192 chunks of 64 KiB, 32-way interleaving): symbols
              >= 16 carry one raw 16-bit word, uniform in [0, 2^16)
+  adaptive : 256 Mi bits for adaptive per-coder contexts, 4096 chunks of
+             64 Ki, 32-way interleaving; P(bit = 0) is piecewise constant over
+             segments of 4096 symbols, each segment's p0 ~ U[0.001, 0.999]
 """
 from __future__ import annotations
 
@@ -45,6 +48,8 @@ WORKLOADS = {
                     alpha_hi=256, dirichlet=0.5, budget_bytes=40 << 30),
     "bypass": dict(index=5, n_symbols=1 << 29, zipf_s=1.1, alphabet=256, raw_from=16,
                    n_lanes=32, chunk_symbols=1 << 16),
+    "adaptive": dict(index=6, n_symbols=1 << 28, n_lanes=32, chunk_symbols=1 << 16,
+                     segment=4096, p0_lo=0.001, p0_hi=0.999),
 }
 
 
@@ -115,6 +120,34 @@ def binary_chunk_probs(rng: np.random.Generator, n_chunks: int, lo: float = 0.5,
                        hi: float = 0.999) -> np.ndarray:
     """Per-chunk p0 ~ U[lo, hi] for the binary workload (fp64)."""
     return rng.uniform(lo, hi, size=n_chunks)
+
+
+def drifting_bits(rng: np.random.Generator, n: int, segment: int, lo: float = 0.001,
+                  hi: float = 0.999) -> np.ndarray:
+    """n bits (uint8 0/1); P(bit = 0) is constant over each run of `segment`
+    symbols and drawn U[lo, hi] per run (host)."""
+    p0 = rng.uniform(lo, hi, size=max(1, -(-n // segment)))
+    u = rng.random(n)
+    return (u >= np.repeat(p0, segment)[:n]).astype(np.uint8)
+
+
+def drifting_bits_device(n: int, segment: int, seed: int, device, lo: float = 0.001,
+                         hi: float = 0.999, piece: int = 1 << 26):
+    """drifting_bits generated on a CUDA device (torch), in pieces; piece must
+    be a multiple of segment."""
+    import torch
+
+    assert piece % segment == 0
+    g = torch.Generator(device=device)
+    g.manual_seed(seed & 0x7FFFFFFFFFFFFFFF)
+    out = torch.empty(n, dtype=torch.uint8, device=device)
+    for a in range(0, n, piece):
+        z = min(n, a + piece)
+        n_seg = -(-(z - a) // segment)
+        p0 = lo + (hi - lo) * torch.rand(n_seg, generator=g, device=device, dtype=torch.float64)
+        u = torch.rand(z - a, generator=g, device=device, dtype=torch.float64)
+        out[a:z] = (u >= p0.repeat_interleave(segment)[: z - a]).to(torch.uint8)
+    return out
 
 
 def poisson_arrivals(rng: np.random.Generator, rate_per_s: float, count: int) -> np.ndarray:
