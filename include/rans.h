@@ -269,8 +269,10 @@ int rans_decode_bytes(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h
  *
  * rans_encode_adaptive: as rans_encode without the model; out_cap >=
  *   rans_max_encoded_size(...), scratch_cap >=
- *   rans_encode_scratch_size_adaptive(...) (the plain scratch plus a u16 per
- *   symbol: the encoder runs the contexts forwards, then codes backwards).
+ *   rans_encode_scratch_size_adaptive(...) (the plain scratch plus about 4
+ *   bytes per 16 steps of each coder: the encoder runs the contexts forwards,
+ *   storing a checkpoint and the symbols' bits for every 16 steps, then codes
+ *   backwards from those alone).
  *   A symbol other than 0 or 1 gives RANS_ERR_ZERO_FREQ.
  * rans_decode_adaptive: as rans_decode without the model.
  */

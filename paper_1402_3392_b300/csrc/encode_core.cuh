@@ -55,7 +55,7 @@ constexpr uint32_t kAdaptP0 = kM / 2;
 // of words per chunk (written backwards from its end), then the chunks'
 // final states, first-word offsets and byte sizes.
 struct ScratchLayout {
-    uint64_t words, states, wstart, sizes, probs, total;
+    uint64_t words, states, wstart, sizes, ctx, total;
     uint32_t slot_bytes;
 };
 
@@ -69,7 +69,7 @@ __host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint3
     s.wstart = s.states + ((n_chunks * N * 4 + 15) & ~uint64_t(15));
     s.sizes = s.wstart + ((n_chunks * 4 + 15) & ~uint64_t(15));
     s.total = s.sizes + ((n_chunks * 4 + 15) & ~uint64_t(15));
-    s.probs = s.total;  // adaptive messages: one u16 context per symbol follows
+    s.ctx = s.total;  // adaptive messages: the contexts' words (adaptive_ctx_stride) follow
     return s;
 }
 
@@ -214,18 +214,59 @@ __device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uin
     }
 }
 
+__device__ __forceinline__ uint32_t adapt_ctx(uint32_t p, uint32_t s) {
+    return s ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+}
+
+// Adaptive scratch of one chunk, in u32 words: for each full group g of
+// kGroup steps and each coder, word [g*N + lane] = the context at the
+// group's first step | the group's symbols as bits << 16 (bit v: step
+// g*kGroup + v); above the last full group, word [(t - top0)*N + lane] = the
+// context of step t (top0 = G*kGroup - G, G = full groups).
+__host__ __device__ constexpr uint64_t adaptive_ctx_stride(uint32_t CS, uint32_t N) {
+    return (uint64_t(CS) + kGroup - 1) / kGroup + uint64_t(kGroup) * N;
+}
+static_assert(kGroup <= 16, "a group's symbol bits share a word with the context");
+
 // Adaptive chunks, pass 1: run every coder's context forwards over its own
-// symbols and store the p each symbol will be coded with (probs[i] for
-// symbol i of the chunk).  A symbol other than 0 or 1 sets kZeroFlag in acc.
-__device__ __forceinline__ void adaptive_forward(const uint8_t *sym, uint32_t n_c, uint32_t N,
-                                                 uint16_t *probs, uint32_t lane, uint32_t &acc) {
-    uint32_t p = kAdaptP0;
-    for (uint32_t i = lane; lane < N && i < n_c; i += N) {
-        const uint32_t s = sym[i];
-        probs[i] = uint16_t(p);
-        if (s > 1u) acc |= kZeroFlag;
-        p = s ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+// symbols (a group's symbols loaded while the previous group updates) and
+// store the words above.  A symbol other than 0 or 1 sets kZeroFlag.
+template <int NT>
+__device__ __forceinline__ void adaptive_forward(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
+                                                 uint32_t *ctx, uint32_t lane, uint32_t &acc) {
+    const uint32_t N = NT ? NT : N_rt;
+    if (lane >= N) return;
+    const uint32_t T_full = n_c / N, G = T_full / kGroup, top0 = G * kGroup - G;
+    const uint8_t *sp = sym + lane;
+    uint32_t *cp = ctx + lane;
+    uint32_t p = kAdaptP0, bad = 0, nxt[kGroup];
+    if (G) {
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u) nxt[u] = sp[uint64_t(u) * N];
     }
+    for (uint32_t g = 0; g < G; ++g) {
+        uint32_t bits = 0;  // bit u: step g*kGroup + u
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u) {
+            bad |= nxt[u];
+            bits |= uint32_t(nxt[u] != 0u) << u;
+        }
+        const bool more = g + 1 < G;
+        const uint64_t base = uint64_t(g + 1) * kGroup;
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u) nxt[u] = more ? sp[(base + u) * N] : 0u;
+        cp[uint64_t(g) * N] = p | bits << 16;
+#pragma unroll
+        for (uint32_t u = 0; u < kGroup; ++u) p = adapt_ctx(p, (bits >> u) & 1u);
+    }
+    const uint32_t T_end = T_full + (lane < n_c % N ? 1u : 0u);
+    for (uint32_t t = G * kGroup; t < T_end; ++t) {
+        const uint32_t s = sp[uint64_t(t) * N];
+        cp[uint64_t(t - top0) * N] = p;
+        bad |= s;
+        p = adapt_ctx(p, s);
+    }
+    if (bad > 1u) acc |= kZeroFlag;
 }
 
 // Adaptive chunks, pass 2, one step: symbol s (0 or 1) coded with the stored
@@ -296,20 +337,21 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // bypass chunk, raw[i] is the raw word of symbol i (used where the symbol
 // carries one); groups are halved so that a group still writes at most 1 KiB.
 // BYTES: a byte-wise chunk (at most 2 bytes per symbol, size padded to 4).
-// ADAPT: an adaptive chunk; raw then points at the contexts pass 1 stored.
+// ADAPT: an adaptive chunk; ctx holds the chunk's words from adaptive_forward.
 template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
                                              uint32_t tab_s, uint32_t ring_s, uint32_t ge,
                                              uint32_t lane, uint32_t &acc,
-                                             const uint16_t *raw = nullptr) {
+                                             const uint16_t *raw = nullptr,
+                                             const uint32_t *ctx = nullptr) {
     static_assert(!((RAW || ADAPT) && PREFETCH), "these chunks load each group up front");
     constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
-    constexpr bool kWord = RAW || ADAPT;  // a u16 per symbol: raw word or context
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
-    const uint16_t *rawp = kWord ? raw + lane : nullptr;
+    const uint16_t *rawp = RAW ? raw + lane : nullptr;
+    const uint32_t *ctxp = ADAPT ? ctx + lane : nullptr;
     uint32_t x = BYTES ? kL8 : kL;
     uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
     uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
@@ -337,12 +379,13 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     };
 
     const uint32_t T_full = n_c / N, rem = n_c % N;
+    const uint32_t top0 = ADAPT ? T_full / kGroup * (kGroup - 1) : 0u;  // see adaptive_ctx_stride
     const bool lane_on = lane < N;
     if (rem) {
         const bool act = lane < rem;
         const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
         if (ADAPT) {
-            const uint32_t pw = act ? rawp[uint64_t(T_full) * N] : kAdaptP0;
+            const uint32_t pw = act ? ctxp[uint64_t(T_full - top0) * N] : kAdaptP0;
             encode_step_adaptive<false>(x, wp, act, s, pw, ring_s, ge);
         } else if (RAW) {
             const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
@@ -357,7 +400,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         service();
         const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
         if (ADAPT) {
-            const uint32_t pw = lane_on ? rawp[uint64_t(t) * N] : kAdaptP0;
+            const uint32_t pw = lane_on ? ctxp[uint64_t(t - top0) * N] : kAdaptP0;
             encode_step_adaptive<NT == 32>(x, wp, lane_on, s, pw, ring_s, ge);
         } else if (RAW) {
             const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
@@ -367,7 +410,36 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                    : encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge));
         }
     }
-    if (PREFETCH) {
+    if (ADAPT) {
+        // Groups of kGroup steps coded from pass 1's words alone (the next
+        // group's word loaded ahead): the contexts are re-run forwards from
+        // the group's first step into registers, two per word, then the group
+        // is coded backwards.
+        uint32_t wn = 0;
+        if (t >= 0 && lane_on) wn = ctxp[uint64_t((t + 1) / kGroup - 1) * N];
+        for (; t >= 0; t -= kGroup) {
+            const uint32_t w = wn;
+            const int64_t tn = t - int64_t(kGroup);
+            if (tn >= 0 && lane_on) wn = ctxp[uint64_t((tn + 1) / kGroup - 1) * N];
+            service();
+            const uint32_t bits = w >> 16;  // bit v: step t - (kGroup - 1) + v
+            uint32_t pv[kGroup / 2];
+            uint32_t pc = w & 0xFFFFu;
+#pragma unroll
+            for (uint32_t v = 0; v < kGroup; ++v) {
+                if (v & 1u) pv[v >> 1] |= pc << 16;
+                else pv[v >> 1] = pc;
+                pc = adapt_ctx(pc, (bits >> v) & 1u);
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) {  // step t - u
+                const uint32_t v = kGroup - 1 - u;
+                encode_step_adaptive<NT == 32>(x, wp, lane_on, (bits >> v) & 1u,
+                                               (v & 1u) ? pv[v >> 1] >> 16 : pv[v >> 1] & 0xFFFFu,
+                                               ring_s, ge);
+            }
+        }
+    } else if (PREFETCH) {
         // Groups of kGroup steps, symbols of the next group loaded ahead.
         uint32_t cur[kGroup], nxt[kGroup];
         if (t >= 0) {
@@ -394,14 +466,12 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
 #pragma unroll
             for (uint32_t u = 0; u < kG; ++u) {
                 cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
-                if (kWord) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : kAdaptP0;
+                if (RAW) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : 0u;
             }
             service();
 #pragma unroll
             for (uint32_t u = 0; u < kG; ++u) {
-                if (ADAPT)
-                    encode_step_adaptive<NT == 32>(x, wp, lane_on, cur[u], curw[u], ring_s, ge);
-                else if (RAW)
+                if (RAW)
                     encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
                                               ge);
                 else

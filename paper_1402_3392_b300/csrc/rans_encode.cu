@@ -16,6 +16,7 @@ using enc::kSmemBytes;
 using enc::kWarps;
 using enc::ScratchLayout;
 using enc::scratch_layout;
+using enc::adaptive_ctx_stride;
 
 struct EncodeParams {
     const uint8_t *sym;
@@ -30,7 +31,8 @@ struct EncodeParams {
     uint32_t n_chunks;
     uint32_t slot_bytes;
     const uint16_t *raw;  // bypass messages: raw word of each symbol
-    uint16_t *probs;      // adaptive messages: scratch, the context of each symbol
+    uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
+    uint64_t ctx_stride;  // u32 words per chunk in ctx
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
@@ -40,8 +42,9 @@ struct EncodeParams {
 // (version 4: binary symbols, one adaptive context per coder).
 constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
 
+// Adaptive chunks keep four CTAs resident per SM (64 registers a thread).
 template <int NT, int KIND>
-__global__ void __launch_bounds__(enc::kThreads)
+__global__ void __launch_bounds__(enc::kThreads, KIND == kAdaptive ? 4 : 1)
     encode_kernel(const __grid_constant__ EncodeParams p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
@@ -58,11 +61,12 @@ __global__ void __launch_bounds__(enc::kThreads)
     for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        if (ADAPT) enc::adaptive_forward(p.sym + first, n_c, p.N, p.probs + first, lane, acc);
+        uint32_t *ctx = ADAPT ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
+        if (ADAPT) enc::adaptive_forward<NT>(p.sym + first, n_c, p.N, ctx, lane, acc);
         enc::encode_chunk<NT, !RAW && !ADAPT, RAW, BYTES, ADAPT>(
             p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
-            acc, RAW ? p.raw + first : ADAPT ? p.probs + first : nullptr);
+            acc, RAW ? p.raw + first : nullptr, ctx);
     }
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
@@ -167,7 +171,9 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     const uint64_t max_out = bypass  ? rans_max_encoded_size_bypass(n_symbols, params)
                              : bytes ? rans_max_encoded_size_bytes(n_symbols, params)
                                      : rans_max_encoded_size(n_symbols, params);
-    const uint64_t need_scratch = adaptive ? sl.probs + round16(2 * n_symbols) : sl.total;
+    const uint64_t ctx_stride = adaptive_ctx_stride(params->chunk_symbols, params->n_lanes);
+    const uint64_t need_scratch =
+        adaptive ? sl.ctx + round16(4 * g.n_chunks * ctx_stride) : sl.total;
     if (out_cap < max_out || scratch_cap < need_scratch) return RANS_ERR_BUFFER_TOO_SMALL;
 
     EncodeParams ep{};
@@ -187,7 +193,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.states = reinterpret_cast<uint32_t *>(scr + sl.states);
     ep.wstart = reinterpret_cast<uint32_t *>(scr + sl.wstart);
     ep.sizes = reinterpret_cast<uint32_t *>(scr + sl.sizes);
-    ep.probs = reinterpret_cast<uint16_t *>(scr + sl.probs);
+    ep.ctx = reinterpret_cast<uint32_t *>(scr + sl.ctx);
+    ep.ctx_stride = ctx_stride;
     ep.status = d_status;
     ep.n_sym = n_symbols;
     ep.N = params->n_lanes;
@@ -244,8 +251,9 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
 extern "C" uint64_t rans_encode_scratch_size_adaptive(uint64_t n_symbols, const rans_params *params) {
     if (!params_ok(params)) return 0;
     const MessageGeometry g = geometry(n_symbols, params);
-    return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).probs +
-           round16(2 * n_symbols);
+    return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).ctx +
+           round16(4 * g.n_chunks *
+                   adaptive_ctx_stride(params->chunk_symbols, params->n_lanes));
 }
 
 extern "C" int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols,
