@@ -5,8 +5,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` leg of
 (``paper_1402_3392_b300``) never imports it, and the two share no code.
 
 The arithmetic lives in ``rans_oracle.c`` (plain scalar C, Algorithm 1 of
-Giesen, "Interleaved entropy coders", run by N round-robin coders, Section 3).
-This module compiles it with gcc on first use and wraps it with ctypes.
+Giesen, "Interleaved entropy coders", run by N round-robin coders, Section 3)
+and ``mux_oracle.c`` (Section 4: interleaving arbitrary coders by running an
+instrumented decoder, with rANS and a canonical prefix code as the coders).
+This module compiles both with gcc on first use and wraps them with ctypes.
 
 ``load(mutant=k)`` builds a copy with one planted mistake (k >= 1); the pin
 tests use those copies to show that each plausible mistake is caught.
@@ -21,7 +23,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rans_oracle.c")
+_SRCS = [os.path.join(_HERE, "rans_oracle.c"), os.path.join(_HERE, "mux_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict[int, C.CDLL] = {}
@@ -50,12 +52,12 @@ def build(mutant: int = 0, force: bool = False) -> str:
     """Compile the oracle (gcc -O2) into oracle/_build/ and return the path."""
     out = lib_path(mutant)
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(out) >= os.path.getmtime(src) for src in _SRCS)):
         return out
     os.makedirs(_BUILD, exist_ok=True)
     tmp = f"{out}.{os.getpid()}.tmp"
     cmd = ["gcc", "-std=gnu11", "-O2", "-Wall", "-Wextra", "-shared", "-fPIC",
-           f"-DORACLE_MUTANT={mutant}", "-o", tmp, _SRC]
+           f"-DORACLE_MUTANT={mutant}", "-o", tmp, *_SRCS]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -159,6 +161,35 @@ def load(mutant: int = 0) -> C.CDLL:
         lib.orc_decode_message_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
                                                     _u8p, C.c_uint64]
         lib.orc_decode_message_adaptive.restype = C.c_int
+        # Section 4: instrumented-decoder mux (mux_oracle.c)
+        lib.orc_mux_rans.argtypes = [_u32p, C.c_uint64, C.c_uint32, _u64p, C.c_uint32,
+                                     C.c_uint64, C.c_uint64, _u64p, C.c_uint64, _u64p]
+        lib.orc_demux_rans.argtypes = [_u64p, C.c_uint64, C.c_uint64, C.c_uint32, _u64p,
+                                       C.c_uint32, C.c_uint64, C.c_uint64, _u32p]
+        lib.orc_prefix_codes.argtypes = [_u8p, C.c_uint32, _u32p]
+        lib.orc_prefix_lengths.argtypes = [_u64p, C.c_uint32, C.c_uint32, _u8p]
+        lib.orc_mux_prefix.argtypes = [_u8p, C.c_uint64, C.c_uint32, _u32p, _u8p, C.c_uint32,
+                                       _u32p, C.c_uint64, _u64p]
+        lib.orc_demux_prefix.argtypes = [_u32p, C.c_uint64, C.c_uint64, C.c_uint32, _u32p, _u8p,
+                                         C.c_uint32, _u8p]
+        lib.orc_mux_prefix_peak.argtypes = [_u8p, C.c_uint64, C.c_uint32, _u32p, _u8p,
+                                            C.c_uint32, C.c_uint64, _u64p, _u64p]
+        lib.orc_max_message_size_prefix.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+        lib.orc_max_message_size_prefix.restype = C.c_uint64
+        lib.orc_encode_chunk_prefix.argtypes = [_u8p, C.c_uint64, _u8p, C.c_uint32, C.c_uint32,
+                                                _u8p, C.c_uint64, _u64p]
+        lib.orc_decode_chunk_prefix.argtypes = [_u8p, C.c_uint64, _u8p, C.c_uint32, C.c_uint32,
+                                                _u8p, C.c_uint64]
+        lib.orc_encode_message_prefix.argtypes = [_u8p, C.c_uint64, _u8p, C.c_uint32,
+                                                  C.c_uint32, C.c_uint32, _u8p, C.c_uint64,
+                                                  _u64p]
+        lib.orc_decode_message_prefix.argtypes = [_u8p, C.c_uint64, _u8p, C.c_uint32,
+                                                  C.c_uint32, C.c_uint32, _u8p, C.c_uint64]
+        for fn in ("orc_mux_rans", "orc_demux_rans", "orc_prefix_codes", "orc_prefix_lengths",
+                   "orc_mux_prefix", "orc_demux_prefix", "orc_mux_prefix_peak",
+                   "orc_encode_chunk_prefix", "orc_decode_chunk_prefix",
+                   "orc_encode_message_prefix", "orc_decode_message_prefix"):
+            getattr(lib, fn).restype = C.c_int
         _LIBS[mutant] = lib
         return lib
 
@@ -582,6 +613,143 @@ class Oracle:
         rc = self.lib.orc_decode_chunk_adaptive(_p(c, _u8p), c.size, N, _p(out, _u8p), n_sym)
         if rc != OK:
             raise OracleError(rc, "decode_chunk_adaptive")
+        return out[:n_sym].copy()
+
+    # -- Section 4: interleaving arbitrary coders by an instrumented decoder --
+
+    def mux_rans(self, symbols, freq, N, L=L_PROD, b=B_PROD):
+        """Coder j encodes symbols j, j+N, ... alone (Algorithm 1); the
+        instrumented decoders mux the N buffers.  Returns the words (u64)."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        cap = 64 * s.size + 8 * N + 8
+        out = np.zeros(cap, dtype=np.uint64)
+        n = C.c_uint64(0)
+        rc = self.lib.orc_mux_rans(_p(s, _u32p), s.size, N, _p(f, _u64p), f.size, L, b,
+                                   _p(out, _u64p), cap, C.byref(n))
+        if rc != OK:
+            raise OracleError(rc, "mux_rans")
+        return out[: n.value].copy()
+
+    def demux_rans(self, words, n_sym, freq, N, L=L_PROD, b=B_PROD):
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        f = np.ascontiguousarray(freq, dtype=np.uint64)
+        out = np.zeros(max(1, n_sym), dtype=np.uint32)
+        rc = self.lib.orc_demux_rans(_p(w, _u64p), w.size, n_sym, N, _p(f, _u64p), f.size, L, b,
+                                     _p(out, _u32p))
+        if rc != OK:
+            raise OracleError(rc, "demux_rans")
+        return out[:n_sym].copy()
+
+    def prefix_codes(self, lengths):
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        code = np.zeros(max(1, ln.size), dtype=np.uint32)
+        rc = self.lib.orc_prefix_codes(_p(ln, _u8p), ln.size, _p(code, _u32p))
+        if rc != OK:
+            raise OracleError(rc, "prefix_codes")
+        return code[: ln.size].copy()
+
+    def prefix_lengths(self, weights, max_len=12):
+        w = np.ascontiguousarray(weights, dtype=np.uint64)
+        ln = np.zeros(max(1, w.size), dtype=np.uint8)
+        rc = self.lib.orc_prefix_lengths(_p(w, _u64p), w.size, max_len, _p(ln, _u8p))
+        if rc != OK:
+            raise OracleError(rc, "prefix_lengths")
+        return ln[: w.size].copy()
+
+    @staticmethod
+    def _lanes(lane_of):
+        if lane_of is None:
+            return None, None
+        a = np.ascontiguousarray(lane_of, dtype=np.uint32)
+        return a, _p(a, _u32p)
+
+    def mux_prefix(self, symbols, lengths, N, lane_of=None):
+        """Prefix-code mux: coder lane_of[i] (i mod N) takes symbol i.
+        Returns the u32 words in the receiver's read order."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        keep, lp = self._lanes(lane_of)
+        cap = (12 * s.size) // 32 + 2 * N + 8
+        out = np.zeros(cap, dtype=np.uint32)
+        n = C.c_uint64(0)
+        rc = self.lib.orc_mux_prefix(_p(s, _u8p), s.size, N, lp, _p(ln, _u8p), ln.size,
+                                     _p(out, _u32p), cap, C.byref(n))
+        del keep
+        if rc != OK:
+            raise OracleError(rc, "mux_prefix")
+        return out[: n.value].copy()
+
+    def demux_prefix(self, words, n_sym, lengths, N, lane_of=None):
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        keep, lp = self._lanes(lane_of)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_demux_prefix(_p(w, _u32p), w.size, n_sym, N, lp, _p(ln, _u8p),
+                                       ln.size, _p(out, _u8p))
+        del keep
+        if rc != OK:
+            raise OracleError(rc, "demux_prefix")
+        return out[:n_sym].copy()
+
+    def mux_prefix_peak(self, symbols, lengths, N, lane_of=None, segment=0):
+        """Coroutine mux (Section 4): (peak words buffered, words output)."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        keep, lp = self._lanes(lane_of)
+        peak, total = C.c_uint64(0), C.c_uint64(0)
+        rc = self.lib.orc_mux_prefix_peak(_p(s, _u8p), s.size, N, lp, _p(ln, _u8p), ln.size,
+                                          segment, C.byref(peak), C.byref(total))
+        del keep
+        if rc != OK:
+            raise OracleError(rc, "mux_prefix_peak")
+        return peak.value, total.value
+
+    def max_message_size_prefix(self, n_sym, N, chunk_symbols):
+        return int(self.lib.orc_max_message_size_prefix(n_sym, N, chunk_symbols))
+
+    def encode_chunk_prefix(self, symbols, lengths, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        cap = 4 * ((12 * s.size + 31) // 32 + 2 * N + 1)
+        out = np.zeros(cap, dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk_prefix(_p(s, _u8p), s.size, _p(ln, _u8p), ln.size, N,
+                                              _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk_prefix")
+        return out[: size.value].copy()
+
+    def decode_chunk_prefix(self, chunk, n_sym, lengths, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_chunk_prefix(_p(c, _u8p), c.size, _p(ln, _u8p), ln.size, N,
+                                              _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk_prefix")
+        return out[:n_sym].copy()
+
+    def encode_message_prefix(self, symbols, lengths, N=32, chunk_symbols=65536):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        cap = self.max_message_size_prefix(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message_prefix(_p(s, _u8p), s.size, _p(ln, _u8p), ln.size, N,
+                                                chunk_symbols, _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message_prefix")
+        return out[: size.value].copy()
+
+    def decode_message_prefix(self, msg, n_sym, lengths, N=32, chunk_symbols=65536):
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_message_prefix(_p(m, _u8p), m.size, _p(ln, _u8p), ln.size, N,
+                                                chunk_symbols, _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message_prefix")
         return out[:n_sym].copy()
 
     def quantize(self, weights, log2_M=LOG2_M_PROD):

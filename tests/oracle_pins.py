@@ -766,6 +766,203 @@ def pin_adaptive_container(o):
     assert list(ch[28:].view(np.uint16)) == list(enc["words"])
 
 
+# ----------------------------------------------------------------------------
+# Section 4: interleaving arbitrary coders by running an instrumented decoder
+# ----------------------------------------------------------------------------
+
+RFC1951 = read_golden("rfc1951_canonical_codes.txt")
+
+
+def pin_mux_rans_is_section3_interleaving(o):
+    """Section 4 applied to rANS: N coders each encode their own symbols
+    into their own buffer; the instrumented decoders' mux of those buffers
+    is exactly the interleaved stream Section 3's encoder writes directly
+    (the production chunk, and the paper's own L = 16, b = 2 model), and it
+    decodes back."""
+    rng = np.random.default_rng(41)
+    for alpha, n, N in ((6, 700, 1), (6, 700, 2), (40, 2000, 5), (3, 901, 32)):
+        freq = o.quantize(rng.integers(1, 1000, size=alpha).astype(np.uint64))
+        sym = rng.choice(alpha, size=n, p=freq / freq.sum()).astype(np.uint8)
+        words = o.mux_rans(sym, freq.astype(np.uint64), N)
+        chunk = o.encode_chunk(sym, freq, N=N)
+        assert np.array_equal(words.astype(np.uint16).view(np.uint8), chunk), (alpha, N)
+        assert np.array_equal(o.demux_rans(words, n, freq.astype(np.uint64), N), sym)
+    # the paper's model, two coders: state digits (5 binary digits each, low
+    # first, coder 0 then coder 1), then the interleaved words
+    msg = [PAPER_SYM[c] for c in "babbaabbbabbab"]
+    enc = o.encode(PAPER_FREQ, msg, N=2, L=16, b=2)
+    digits = [(int(x) >> k) & 1 for x in enc["states"] for k in range(5)]
+    words = o.mux_rans(msg, np.array(PAPER_FREQ, dtype=np.uint64), 2, L=16, b=2)
+    assert list(words) == digits + [int(w) for w in enc["words"]]
+
+
+def pin_prefix_codes_rfc1951(o):
+    """Canonical codes: the RFC 1951 worked example (golden file), and for
+    random length vectors the prefix property and Kraft's inequality."""
+    lengths = np.array([int(v) for v in RFC1951["lengths"]], dtype=np.uint8)
+    want = [int(c, 2) for c in RFC1951["codes"]]
+    assert list(o.prefix_codes(lengths)) == want
+    rng = np.random.default_rng(43)
+    for _ in range(30):
+        n = int(rng.integers(2, 40))
+        w = rng.integers(1, 1 << 20, size=n).astype(np.uint64)
+        ln = o.prefix_lengths(w, 12)
+        codes = o.prefix_codes(ln)
+        words = [format(int(c), "b").zfill(int(l)) for c, l in zip(codes, ln)]
+        for a in range(n):
+            for b in range(n):
+                if a != b:
+                    assert not words[b].startswith(words[a])
+    bad = np.array([1, 1, 1], dtype=np.uint8)          # Kraft sum 3/2
+    try:
+        o.prefix_codes(bad)
+        raise AssertionError("over-full code accepted")
+    except oracle.OracleError:
+        pass
+
+
+def _huffman_cost(w):
+    """Textbook Huffman (repeatedly merge the two lightest): total cost."""
+    import heapq
+    h = [int(x) for x in w if x]
+    if len(h) == 1:
+        return h[0]
+    heapq.heapify(h)
+    cost = 0
+    while len(h) > 1:
+        a, b = heapq.heappop(h), heapq.heappop(h)
+        cost += a + b
+        heapq.heappush(h, a + b)
+    return cost
+
+
+def pin_prefix_lengths_optimal(o):
+    """Package-merge lengths: optimal among all codes with lengths <= the
+    limit (brute force on small alphabets), a complete code (Kraft sum 1),
+    heavier symbols never longer, and without a binding limit the cost of a
+    textbook Huffman code."""
+    rng = np.random.default_rng(47)
+    for n, lim in ((2, 1), (3, 2), (4, 2), (5, 3), (6, 3), (6, 4), (7, 3), (7, 5)):
+        for _ in range(12):
+            w = rng.integers(1, 60, size=n).astype(np.uint64)
+            if rng.random() < 0.3:
+                w = (2 ** rng.integers(0, 12, size=n)).astype(np.uint64)  # skewed
+            ln = o.prefix_lengths(w, lim)
+            assert ln.max() <= lim and ln.min() >= 1
+            assert sum(2.0 ** -int(l) for l in ln) == 1.0
+            best = min(sum(int(a) * b for a, b in zip(w, ls))
+                       for ls in itertools.product(range(1, lim + 1), repeat=n)
+                       if sum(2.0 ** -b for b in ls) <= 1.0)
+            assert sum(int(a) * int(b) for a, b in zip(w, ln)) == best, (w, lim, ln)
+            for a in range(n):
+                for b in range(n):
+                    if w[a] > w[b]:
+                        assert ln[a] <= ln[b]
+    for _ in range(20):
+        n = int(rng.integers(2, 200))
+        w = rng.integers(1, 1000, size=n).astype(np.uint64)
+        w[rng.random(n) < 0.2] = 0                      # unused symbols get length 0
+        if np.count_nonzero(w) < 2:
+            continue
+        ln = o.prefix_lengths(w, 16)
+        assert all((ln[i] == 0) == (w[i] == 0) for i in range(n))
+        assert sum(int(a) * int(b) for a, b in zip(w, ln)) == _huffman_cost(w)
+
+
+def _schedule(o, sym, lengths, N):
+    """Bit-length bookkeeping of the prefix decoder's reads (it takes a word
+    whenever it holds fewer than 12 bits before a symbol): the (step, lane)
+    of every read, in read order."""
+    held = [0] * N
+    reads = []
+    for i, s in enumerate(sym):
+        j = i % N
+        if held[j] < 12:
+            reads.append(j)
+            held[j] += 32
+        held[j] -= int(lengths[s])
+    return reads
+
+
+def pin_prefix_mux_lane_streams(o):
+    """Split the prefix-code mux by the reading coder (schedule from bit
+    counts): coder j's words, in order, are its own symbols' codes
+    concatenated MSB first, zero-padded -- every word the receiver needs and
+    nothing else -- and the mux decodes back."""
+    rng = np.random.default_rng(53)
+    for n_alpha, n, N in ((2, 300, 1), (5, 999, 3), (17, 4000, 8), (60, 3001, 32)):
+        w = rng.integers(1, 5000, size=n_alpha).astype(np.uint64)
+        ln = o.prefix_lengths(w, 12)
+        codes = o.prefix_codes(ln)
+        sym = rng.choice(n_alpha, size=n, p=w / w.sum()).astype(np.uint8)
+        mux = o.mux_prefix(sym, ln, N)
+        reads = _schedule(o, sym, ln, N)
+        assert mux.size == len(reads)
+        for j in range(N):
+            mine = [int(x) for x, r in zip(mux, reads) if r == j]
+            bits = "".join(format(int(codes[s]), "b").zfill(int(ln[s])) for s in sym[j::N])
+            bits = bits.ljust(32 * len(mine), "0")
+            assert mine == [int(bits[32 * k:32 * k + 32], 2) for k in range(len(mine))], (N, j)
+        assert np.array_equal(o.demux_prefix(mux, n, ln, N), sym)
+
+
+def pin_prefix_mux_brute_force(o):
+    """All messages of up to 6 symbols over a 3-symbol code, 1..3 coders:
+    distinct messages give distinct muxes, and each decodes back."""
+    ln = np.array([1, 2, 2], dtype=np.uint8)
+    for N in (1, 2, 3):
+        seen = {}
+        for n in range(0, 7):
+            for msg in itertools.product(range(3), repeat=n):
+                m = np.array(msg, dtype=np.uint8)
+                mux = tuple(int(x) for x in o.mux_prefix(m, ln, N))
+                assert (n, mux) not in seen
+                seen[(n, mux)] = msg
+                assert tuple(o.demux_prefix(np.array(mux, dtype=np.uint32), n, ln, N)) == msg
+
+
+def pin_mux_coroutine_and_flush(o):
+    """Section 4's catch: coder 0 takes the first symbol and coder 1 all the
+    rest; a coroutine mux then waits on coder 0 until it flushes, so nearly
+    every word is buffered.  Flushing every F symbols bounds the buffer
+    (about F symbols' words) at a small cost in size; with coders taking
+    symbols in turn the buffer stays at a few words per coder."""
+    rng = np.random.default_rng(59)
+    ln = np.array([2, 3, 3, 2, 4, 4, 3], dtype=np.uint8)      # Kraft sum 1
+    n = 30_000
+    sym = rng.integers(0, 7, size=n).astype(np.uint8)
+    lane = np.ones(n, dtype=np.uint32)
+    lane[0] = 0
+    peak, total = o.mux_prefix_peak(sym, ln, 2, lane, 0)
+    assert peak >= 0.95 * total
+    for F in (500, 3000):
+        pk, tot = o.mux_prefix_peak(sym, ln, 2, lane, F)
+        assert pk <= F * 4 // 32 + 8, (F, pk)
+        assert total <= tot <= total + 2 * 3 * (n // F + 1)
+    for N in (2, 7, 32):
+        pk, tot = o.mux_prefix_peak(sym, ln, N, None, 0)
+        assert pk <= 3 * N, (N, pk)
+        assert tot == o.mux_prefix(sym, ln, N).size
+
+
+def pin_prefix_container(o):
+    """Version-5 container: chunk c is the mux of its symbols (coder i mod N),
+    u32 little-endian words; round trip."""
+    rng = np.random.default_rng(61)
+    w = rng.integers(1, 100, size=30).astype(np.uint64)
+    ln = o.prefix_lengths(w, 12)
+    sym = rng.choice(30, size=5000, p=w / w.sum()).astype(np.uint8)
+    m = o.encode_message_prefix(sym, ln, N=7, chunk_symbols=999)
+    h = m[:32].view(np.uint32)
+    assert list(h[:4]) == [0x534E4152, 5, 7, 12] and list(h[6:8]) == [999, 6]
+    data0 = (32 + 4 * 7 + 15) // 16 * 16
+    offs = m[32:32 + 4 * 7].view(np.uint32)
+    for c in range(6):
+        ch = m[data0 + offs[c]:data0 + offs[c + 1]]
+        assert list(ch.view(np.uint32)) == list(o.mux_prefix(sym[999 * c:999 * (c + 1)], ln, 7))
+    assert np.array_equal(o.decode_message_prefix(m, sym.size, ln, N=7, chunk_symbols=999), sym)
+
+
 ALL_PINS = [
     pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
     pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
@@ -776,4 +973,7 @@ ALL_PINS = [
     pin_bypass_without_raw_is_plain, pin_bypass_interleaved, pin_wide_one_lane_is_algorithm1,
     pin_wide_breadth_first, pin_bytes_container, pin_adaptive_lanes_independent,
     pin_adaptive_brute_force, pin_adaptive_size_and_learning, pin_adaptive_container,
+    pin_mux_rans_is_section3_interleaving, pin_prefix_codes_rfc1951, pin_prefix_lengths_optimal,
+    pin_prefix_mux_lane_streams, pin_prefix_mux_brute_force, pin_mux_coroutine_and_flush,
+    pin_prefix_container,
 ]

@@ -8,13 +8,15 @@ The mutants are compiled from the same source with -DORACLE_MUTANT=k:
   9 sends a symbol's raw (bypass) digits after encoding it, not before
  10 lays a width-baked step's digits out depth-first, not breadth-first
  11 updates an adaptive context before coding the symbol, not after
+ 12 muxes the coders' buffers by concatenation, not in the decoders' read order
+ 13 hands out canonical codes of one length in decreasing symbol order
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTANTS = range(1, 12)
+MUTANTS = range(1, 14)
 
 
 @pytest.mark.parametrize("k", MUTANTS)
