@@ -55,9 +55,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched,binary,single,serving,bypass,bytes,adaptive",
+    ap.add_argument("--legs", default="batched,binary,single,serving,bypass,bytes,adaptive,prefix",
                     help="extra legs after the headline one: comma list of batched, binary, "
-                         "single, serving, bypass, bytes, adaptive, none")
+                         "single, serving, bypass, bytes, adaptive, prefix, none")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -593,6 +593,52 @@ def adaptive_leg(rans, dev, args, hbm):
                          "algorithmic_bytes_per_launch": alg}}
 
 
+def prefix_leg(rans, dev, args, hbm):
+    """Section 4: the 1 GiB chunked workload coded by 32 prefix coders per
+    chunk (package-merge lengths <= 12 from the Zipf(1.1) weights), their
+    words laid down in the decoders' read order; encode and decode timed,
+    the round trip checked, the size set beside the rANS message's."""
+    import torch
+
+    cfg = wl.WORKLOADS["chunked"]
+    n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    ln = rans.rans_prefix_lengths(wl.weights_from_probs(p), rans.RANS_PREFIX_MAX_LEN)
+    sym = wl.iid_symbols_device(p, n, wl.seed_for("chunked"), dev)
+    cap = rans.rans_max_encoded_size_prefix(n, N, CS)
+    scap = rans.rans_encode_scratch_size_prefix(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    enc = lambda: rans.rans_encode_prefix(sym, n, ln, N, CS, msg, cap, size, est, scratch, scap)  # noqa: E731
+    enc()
+    torch.cuda.synchronize()
+    assert int(est.item()) == 0
+    msg_size = int(size.item())
+    enc_ms = statistics.median(_events(torch, enc, 5))
+    del scratch
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    dst = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode_prefix(msg, msg_size, ln, N, CS, out, n, dst)  # noqa: E731
+    dec()
+    torch.cuda.synchronize()
+    ok = int(dst.item()) == 0 and torch.equal(out, sym)
+    dec_ms = statistics.median(_events(torch, dec, 10))
+    alg = msg_size + n
+    mean_len = float((p * ln[: p.size]).sum())
+    return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, {n // CS} "
+                        f"chunks x {CS}, N = {N} prefix coders (lengths <= 12, mean "
+                        f"{mean_len:.3f} bits), words in the decoders' read order",
+            "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
+            "encode_gbs": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
+            "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "decode_kernel (prefix)", "bound": "hbm",
+                         "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def single_leg(rans, dev, args):
     """One 1 MiB stream, Zipf(1.2) over 256 symbols, 32 coders in one chunk:
     a single warp's chain of 32768 dependent steps, so a latency figure."""
@@ -852,6 +898,9 @@ def main(argv=None):
         torch.cuda.empty_cache()
     if "adaptive" in legs:
         extra["adaptive"] = adaptive_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
+    if "prefix" in legs:
+        extra["prefix"] = prefix_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
 
     if rank == 0:

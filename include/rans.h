@@ -83,6 +83,8 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_VERSION_BYPASS 2u         /* messages with raw words (rans_encode_bypass) */
 #define RANS_VERSION_BYTES 3u          /* byte-wise messages (rans_encode_bytes) */
 #define RANS_VERSION_ADAPTIVE 4u       /* adaptive binary messages (rans_encode_adaptive) */
+#define RANS_VERSION_PREFIX 5u         /* prefix-code messages (rans_encode_prefix) */
+#define RANS_PREFIX_MAX_LEN 12         /* longest prefix code */
 
 typedef struct {
     uint32_t n_lanes;        /* N interleaved coders per chunk, 1..32 */
@@ -284,6 +286,52 @@ int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols, const ran
 int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size, const rans_params *params,
                          uint8_t *d_symbols, uint64_t n_symbols, uint32_t *d_status,
                          rans_stream_t stream);
+
+/*
+ * Interleaving arbitrary coders -- Section 4 of the paper: any entropy
+ * coder's streams can be interleaved without metadata if the encoder runs
+ * (an instrumented copy of) the decoder and lays the words down in the order
+ * the decoder will read them.  The coder here is a canonical prefix code.
+ *
+ * Code: lengths l_s in 0..RANS_PREFIX_MAX_LEN (0 = symbol not in the code)
+ * with sum 2^-l_s <= 1; codes assigned in order of (length, symbol), each
+ * length's codes consecutive (the canonical rule of RFC 1951, 3.2.2).
+ * Coder j of a chunk takes symbols j, j+N, ... and writes their codes MSB
+ * first into 32-bit words.  Its decoder holds up to 43 bits and, before each
+ * symbol, reads one word when it holds fewer than 12 bits; the reads of one
+ * step are taken in lane order.  The message lays every word where that
+ * read finds it.  A chunk ends with every coder's leftover bits zero and
+ * every word read.  Container as rans.h's plain one, version 5
+ * (RANS_VERSION_PREFIX), log2_M field 12; chunk c = u32 little-endian words
+ * only (no states), so offsets are multiples of 4.
+ *
+ * rans_prefix_lengths: host.  Optimal code lengths <= max_len (1..12) for
+ *   weights[0..n_alpha) (0 = unused), by package-merge; ties between equal
+ *   weights go to the lower symbol index first.  One used symbol gets
+ *   length 1.  Returns RANS_OK, or RANS_ERR_INVALID_ARG (no used symbol,
+ *   more than 2^max_len used symbols, bad pointers or sizes).
+ * rans_prefix_codes: host.  The canonical codes of lengths[0..n_alpha)
+ *   (codes_out[s], right-aligned; 0 for unused symbols).  RANS_ERR_INVALID_ARG
+ *   if a length exceeds 12, no symbol is used, or Kraft's sum exceeds 1.
+ * rans_encode_prefix: as rans_encode with code lengths (host, n_alpha <=
+ *   256) instead of a frequency table; out_cap >=
+ *   rans_max_encoded_size_prefix(...), scratch_cap >=
+ *   rans_encode_scratch_size_prefix(...).  A symbol without a code gives
+ *   RANS_ERR_ZERO_FREQ.
+ * rans_decode_prefix: as rans_decode with the same code lengths.
+ */
+int rans_prefix_lengths(const uint64_t *weights, uint32_t n_alpha, uint32_t max_len,
+                        uint8_t *lengths_out);
+int rans_prefix_codes(const uint8_t *lengths, uint32_t n_alpha, uint16_t *codes_out);
+uint64_t rans_max_encoded_size_prefix(uint64_t n_symbols, const rans_params *params);
+uint64_t rans_encode_scratch_size_prefix(uint64_t n_symbols, const rans_params *params);
+int rans_encode_prefix(const uint8_t *d_symbols, uint64_t n_symbols, const uint8_t *h_lengths,
+                       uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
+                       uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status,
+                       void *d_scratch, uint64_t scratch_cap, rans_stream_t stream);
+int rans_decode_prefix(const uint8_t *d_msg, uint64_t msg_size, const uint8_t *h_lengths,
+                       uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                       uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream);
 
 /*
  * Batched decoding: many independent messages ("streams"), each with its own

@@ -15,7 +15,9 @@ _BINDING = frozenset({
     "rans_decode_bypass", "encode_bypass", "decode_bypass", "rans_max_encoded_size_bytes",
     "rans_encode_bytes", "rans_decode_bytes", "encode_bytes", "decode_bytes",
     "rans_encode_scratch_size_adaptive", "rans_encode_adaptive", "rans_decode_adaptive",
-    "encode_adaptive", "decode_adaptive",
+    "encode_adaptive", "decode_adaptive", "rans_prefix_lengths", "rans_prefix_codes",
+    "rans_max_encoded_size_prefix", "rans_encode_scratch_size_prefix", "rans_encode_prefix",
+    "rans_decode_prefix", "encode_prefix", "decode_prefix",
 })
 
 

@@ -21,7 +21,7 @@ LIB_NAME = "libinterleaved_rans_b300.so"
 LIB_PATH = os.path.join(LIB_DIR, LIB_NAME)
 
 SOURCES = ["rans_host.cpp", "rans_decode.cu", "rans_encode.cu", "rans_batch.cu", "rans_server.cu",
-           "rans_check.cu"]
+           "rans_check.cu", "rans_prefix.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -62,6 +62,8 @@ struct Geometry {
 using GeoOne = Geometry<1024, kNSeg, 16>;
 using GeoPair = Geometry<512, kNSeg, 16>;
 using GeoRaw = Geometry<1024, kNSeg, 16, 128>;
+// Prefix messages read up to one 32-bit word per lane and step: as GeoRaw.
+using GeoPrefix = Geometry<1024, kNSeg, 16, 128>;
 static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing &&
                   GeoRaw::kRing == kWarpRing,
               "ring sizes");
@@ -79,8 +81,13 @@ constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 constexpr uint32_t kL8 = 1u << 23;
 // Message kinds: plain (version 1), bypass (2: raw words after symbols),
 // byte-wise (3: b = 2^8, digits breadth-first), adaptive (4: binary symbols,
-// one adaptive context per coder).
-constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3;
+// one adaptive context per coder), prefix (5: canonical prefix codes muxed in
+// their decoder's read order, Section 4).
+constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3, kKindPrefix = 4;
+// Prefix messages: longest code, also the bit count below which a coder's
+// decoder reads its next 32-bit word; entries of the 4096-entry code table
+// are len << 8 | symbol (0: no code starts with these 12 bits).
+constexpr uint32_t kPrefixMaxLen = 12;
 // Adaptive contexts: p = probability of a 0 scaled to M, from M/2, moving by
 // (target - p) >> kAdaptRate after every symbol.
 constexpr uint32_t kAdaptRate = 5;
@@ -149,6 +156,11 @@ __device__ __forceinline__ uint32_t ld_ring_u8(uint32_t a) {
 __device__ __forceinline__ uint32_t ld_ring_u16(uint32_t a) {
     uint32_t v;
     asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_ring_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
@@ -235,6 +247,25 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
     return total;
 }
 
+// The 4096-entry decode table of a canonical prefix code, with the whole CTA:
+// the entries whose top len bits are symbol s's code hold len << 8 | s, the
+// rest 0.  len[s] = 0: s not in the code.
+__device__ __noinline__ static void build_prefix_table(const uint8_t *len, const uint16_t *code,
+                                                       uint32_t *tab) {
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < kM / 4; i += kThreads)
+        reinterpret_cast<uint4 *>(tab)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    for (uint32_t s = tid; s < RANS_MAX_ALPHABET; s += kThreads) {
+        const uint32_t l = len[s];
+        if (l == 0 || l > kPrefixMaxLen) continue;
+        const uint32_t first = uint32_t(code[s]) << (kPrefixMaxLen - l), n = 1u << (kPrefixMaxLen - l);
+        const uint32_t e = (l << 8) | s;
+        for (uint32_t k = 0; k < n; ++k) tab[first + k] = e;
+    }
+    __syncthreads();
+}
+
 // The ring and barriers of one chunk slot of a warp, carried across the
 // chunks the warp decodes.  With one chunk per warp, slot 0's ring is the
 // warp's whole 4 KiB.
@@ -288,6 +319,9 @@ struct Chain {
     uint32_t p;          // adaptive messages: this lane's context
     uint32_t rp0;        // byte-wise messages: rp at the first digit
     uint32_t len;        // byte-wise messages: chunk bytes (states, digits, padding)
+    uint32_t bhi, blo;   // prefix messages: this lane's bits, right-aligned in bhi:blo
+    uint32_t nb;         // prefix messages: bits held (at most 43)
+    uint32_t emin;       // prefix messages: smallest table entry used (< 256: no code)
 };
 
 __device__ __forceinline__ void chain_empty(Chain &c) {
@@ -300,6 +334,33 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.st = RANS_OK;
     c.rp0 = c.len = 0;
     c.p = kAdaptP0;
+    c.bhi = c.blo = c.nb = 0;
+    c.emin = 0xFFFFFFFFu;
+}
+
+// Open a prefix-message chunk [o, e): no states, its 32-bit words start at
+// the chunk's first byte; offsets must be multiples of 4.
+template <class G>
+__device__ __forceinline__ void chain_open_prefix(Chain &c, const uint8_t *msg, uint32_t data0,
+                                                  uint32_t o, uint32_t e, uint32_t data_end,
+                                                  uint32_t n_c, uint32_t N, uint8_t *out,
+                                                  uint32_t lane) {
+    chain_empty(c);
+    if (((o | e) & 3u) || e < o || e > data_end || e - o > 0xFFFFFF00u) {
+        c.st = RANS_ERR_CORRUPT;
+        return;
+    }
+    const uint64_t P0 = uint64_t(data0) + o, P1 = uint64_t(data0) + e;
+    const uint64_t A = P0 & ~uint64_t(15);
+    c.src = msg + A;
+    c.span = uint32_t(round16(P1) - A);
+    c.nseg = (c.span + G::kSeg - 1) / G::kSeg;
+    c.endrel = uint32_t(P1 - A);
+    c.rp = uint32_t(P0 - A);
+    c.next_evt = 0;
+    c.outp = out + lane;
+    c.steps = n_c / N;
+    c.rem = n_c % N;
 }
 
 // Open chunk [o, e) (byte offsets in the data region that starts at msg +
@@ -498,6 +559,34 @@ __device__ __forceinline__ void decode_step_adaptive(uint32_t &x, uint32_t &p, u
     rp = imad(__popc(m), 2u, rp);
 }
 
+// One step of a prefix-message chunk (Section 4): a lane holding fewer than
+// 12 bits reads its next 32-bit word first (lanes in order, ballot + popc,
+// as for rANS words), then the top 12 of its bits index the code table;
+// the symbol's length is dropped from the bit count.  Bits are kept
+// right-aligned, so a read shifts bhi:blo up by one word and a symbol costs
+// no shift.
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step_prefix(Chain &c, bool active, uint32_t tab_s,
+                                                   uint32_t ring_s, uint8_t *outp, uint32_t lt) {
+    const bool on = FULL || active;
+    const bool need = on && c.nb < kPrefixMaxLen;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = ld_ring_u32(((c.rp + 4u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    if (need) {
+        c.bhi = c.blo;
+        c.blo = w;
+        c.nb += 32;
+    }
+    c.rp = imad(__popc(m), 4u, c.rp);
+    if (on) {
+        const uint32_t idx = __funnelshift_r(c.blo, c.bhi, c.nb - kPrefixMaxLen) & (kM - 1);
+        const uint32_t e = ld_table(imad(idx, 4u, tab_s));
+        *outp = uint8_t(e);
+        c.nb -= e >> 8;
+        c.emin = min(c.emin, e);
+    }
+}
+
 // One step of chunk c of message kind KIND; outp/rawp: this step's output.
 template <bool FULL, uint32_t RING, int KIND>
 __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s, uint32_t ring_s,
@@ -509,6 +598,8 @@ __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s,
         decode_step_bytes<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
     else if (KIND == kKindAdaptive)
         decode_step_adaptive<FULL, RING>(c.x, c.p, c.rp, active, ring_s, outp, lt);
+    else if (KIND == kKindPrefix)
+        decode_step_prefix<FULL, RING>(c, active, tab_s, ring_s, outp, lt);
     else
         decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
 }
@@ -546,7 +637,9 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
 // Byte-wise chunks end in zero padding up to a multiple of 4 bytes: the chunk
 // must be exactly round4(4N + digits read) long, with zeros after the digits
 // (src + rp .. src + endrel, at most 3 bytes).
-template <class G, bool BYTES = false>
+// Prefix chunks end with every word read, every coder's leftover bits zero
+// and no table miss.
+template <class G, bool BYTES = false, bool PREFIX = false>
 __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t &timeouts,
                                                 bool lane_on, uint32_t N = 0) {
     const uint32_t issued = min(c.evt, c.nseg);
@@ -554,6 +647,12 @@ __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t
         ring_wait(r, j % G::kNSeg, timeouts);
     if (c.st != RANS_OK) return c.st;
     if (timeouts) return RANS_ERR_TIMEOUT;
+    if (PREFIX) {
+        const uint64_t bits = (uint64_t(c.bhi) << 32) | c.blo;
+        const bool clean = (bits & ((uint64_t(1) << c.nb) - 1)) == 0 && c.emin >= 256u;
+        const bool ok = __all_sync(kFull, !lane_on || clean) && c.rp == c.endrel;
+        return ok ? RANS_OK : RANS_ERR_CORRUPT;
+    }
     if (BYTES) {
         const uint32_t used = c.rp - c.rp0;
         bool ok = __all_sync(kFull, !lane_on || c.x == kL8) &&
@@ -622,9 +721,12 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
                                                   uint32_t flags_s = 0, bool const_raw = false) {
     constexpr bool RAW = KIND == kKindRaw;
     constexpr bool BYTES = KIND == kKindBytes;
+    constexpr bool PREFIX = KIND == kKindPrefix;
     static_assert(!(PAIR && KIND != kKindPlain), "only plain messages pair chunks");
-    using G = typename std::conditional<RAW, GeoRaw,
-                                        typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type;
+    using G = typename std::conditional<
+        RAW, GeoRaw,
+        typename std::conditional<PREFIX, GeoPrefix,
+                                  typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type>::type;
     constexpr bool kFullWarp = NT == 32;
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;
@@ -634,7 +736,7 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     const uint32_t n_b = two ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
     const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = two ? offs[c + 2] : 0u;
 
-    if (KIND != kKindAdaptive && const_sym != kNoConst) {
+    if (KIND != kKindAdaptive && !PREFIX && const_sym != kNoConst) {
         if (RAW)
             return const_chunk_raw(msg, data0, o0, o1, data_end, n_a, N, out + first,
                                    raw_out + first, const_sym, const_raw, lane);
@@ -651,8 +753,11 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     }
 
     Chain a, b;
-    chain_open<G, BYTES>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
-                         RAW ? raw_out + first : nullptr, lane);
+    if (PREFIX)
+        chain_open_prefix<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
+    else
+        chain_open<G, BYTES>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
+                             RAW ? raw_out + first : nullptr, lane);
     if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, nullptr, lane);
     else chain_empty(b);
 
@@ -675,7 +780,7 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     }
     chain_run<kFullWarp, G, KIND>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
     if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
-    const uint32_t sa = chain_close<G, BYTES>(a, w.r[0], w.timeouts, lane_on, N);
+    const uint32_t sa = chain_close<G, BYTES, PREFIX>(a, w.r[0], w.timeouts, lane_on, N);
     const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
     return sa != RANS_OK ? sa : sb;
 }

@@ -33,13 +33,16 @@ struct DecodeParams {
     uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
+    uint8_t plen[RANS_MAX_ALPHABET];       // prefix messages: code lengths (0: no code)
+    uint16_t pcode[RANS_MAX_ALPHABET];     // prefix messages: canonical codes
 };
 
 // Message kinds: plain (version 1), bypass (version 2: raw words after their
 // symbols), byte-wise (version 3: b = 2^8, digits breadth-first per step) and
-// adaptive (version 4: binary symbols, one adaptive context per coder).
+// adaptive (version 4: binary symbols, one adaptive context per coder) and
+// prefix (version 5: canonical prefix codes in their decoder's read order).
 constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::kKindBytes,
-              kAdaptive = dec::kKindAdaptive;
+              kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  Bypass and
 // byte-wise messages are decoded one chunk per warp.
@@ -49,6 +52,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPTIVE = KIND == kAdaptive;
+    constexpr bool PREFIX = KIND == kPrefix;
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -59,11 +63,13 @@ __global__ void __launch_bounds__(dec::kThreads)
         hdr_ok = dec::header_ok(p.msg, p.msg_size, p.data0, p.n_sym, p.N, p.CS, p.n_chunks,
                                 RAW ? RANS_VERSION_BYPASS : BYTES ? RANS_VERSION_BYTES
                                 : ADAPTIVE                        ? RANS_VERSION_ADAPTIVE
+                                : PREFIX                          ? RANS_VERSION_PREFIX
                                                                   : RANS_VERSION);
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
     if (ADAPTIVE) __syncthreads();  // no table: the contexts live in registers
+    else if (PREFIX) dec::build_prefix_table(p.plen, p.pcode, sm.tab);
     else dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
     if (!hdr_ok) {
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(dec::kThreads)
                                                         cs, lane, lt, p.raw_out, sm.flags_s,
                                                         cs != dec::kNoConst &&
                                                             sm.flags[cs & 0xFFu]);
-        else if (BYTES || ADAPTIVE)
+        else if (BYTES || ADAPTIVE || PREFIX)
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt);
@@ -182,6 +188,8 @@ static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaSt
         return p.N == 32 ? launch_decode<32, kBytes>(p, st) : launch_decode<0, kBytes>(p, st);
     if (p.kind == kAdaptive)
         return p.N == 32 ? launch_decode<32, kAdaptive>(p, st) : launch_decode<0, kAdaptive>(p, st);
+    if (p.kind == kPrefix)
+        return p.N == 32 ? launch_decode<32, kPrefix>(p, st) : launch_decode<0, kPrefix>(p, st);
     return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 
@@ -252,6 +260,29 @@ extern "C" int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size,
     p.out = d_symbols;
     p.status = d_status;
     p.kind = kAdaptive;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+extern "C" int rans_decode_prefix(const uint8_t *d_msg, uint64_t msg_size, const uint8_t *h_lengths,
+                                  uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
+                                  uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
+    uint16_t any_model[2] = {RANS_M / 2, RANS_M / 2};  // the code table replaces the model
+    uint16_t codes[RANS_MAX_ALPHABET];
+    DecodeParams p;
+    int rc = prepare_decode(d_msg, msg_size, any_model, 2, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
+    if ((rc = rans_prefix_codes(h_lengths, n_alpha, codes)) != RANS_OK) return rc;
+    for (uint32_t s = 0; s < n_alpha; ++s) {
+        p.plen[s] = h_lengths[s];
+        p.pcode[s] = codes[s];
+    }
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.status = d_status;
+    p.kind = kPrefix;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     return launch_range(p, 0, p.n_chunks, st);

@@ -47,6 +47,7 @@ RANS_LOG2_M = 12
 RANS_M = 1 << RANS_LOG2_M
 RANS_L = 1 << 16
 RANS_STATIC_SCRATCH_BYTES = 64 << 20
+RANS_PREFIX_MAX_LEN = 12
 
 
 # Layouts of rans_stream and rans_encode_stream (include/rans.h).
@@ -104,6 +105,12 @@ def _load() -> C.CDLL:
         "rans_max_encoded_size_bytes": (u64, [u64, pp]),
         "rans_encode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_bytes": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
+        "rans_prefix_lengths": (i32, [vp, u32, u32, vp]),
+        "rans_prefix_codes": (i32, [vp, u32, vp]),
+        "rans_max_encoded_size_prefix": (u64, [u64, pp]),
+        "rans_encode_scratch_size_prefix": (u64, [u64, pp]),
+        "rans_encode_prefix": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode_prefix": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_scratch_size_adaptive": (u64, [u64, pp]),
         "rans_encode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp]),
@@ -415,6 +422,98 @@ def decode_adaptive(msg, n_symbols: int, n_lanes: int = 32, chunk_symbols: int =
         st = int(status.item())
         if st != RANS_OK:
             raise RansError(st, "rans_decode_adaptive (device status)")
+    return out[:n_symbols], status
+
+
+def rans_prefix_lengths(weights, max_len: int = RANS_PREFIX_MAX_LEN) -> np.ndarray:
+    """Optimal code lengths <= max_len (package-merge, host)."""
+    w = np.ascontiguousarray(weights, dtype=np.uint64)
+    out = np.zeros(max(1, w.size), dtype=np.uint8)
+    _check(lib.rans_prefix_lengths(w.ctypes.data, w.size, max_len, out.ctypes.data),
+           "rans_prefix_lengths")
+    return out[: w.size]
+
+
+def rans_prefix_codes(lengths) -> np.ndarray:
+    """Canonical codes of the given code lengths (host)."""
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    out = np.zeros(max(1, ln.size), dtype=np.uint16)
+    _check(lib.rans_prefix_codes(ln.ctypes.data, ln.size, out.ctypes.data), "rans_prefix_codes")
+    return out[: ln.size]
+
+
+def rans_max_encoded_size_prefix(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_max_encoded_size_prefix(int(n_symbols), C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_scratch_size_prefix(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_encode_scratch_size_prefix(int(n_symbols),
+                                                   C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def _lengths(lengths) -> np.ndarray:
+    return np.ascontiguousarray(lengths, dtype=np.uint8)
+
+
+def rans_encode_prefix(d_symbols, n_symbols, lengths, n_lanes, chunk_symbols, d_out, out_cap,
+                       d_out_size, d_status, d_scratch, scratch_cap, stream=None, check=True) -> int:
+    """Prefix-code coders muxed in their decoders' read order (Section 4)."""
+    ln = _lengths(lengths)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_prefix(_ptr(d_symbols), int(n_symbols), ln.ctypes.data, ln.size,
+                                C.byref(p), _ptr(d_out), int(out_cap), _ptr(d_out_size),
+                                _ptr(d_status), _ptr(d_scratch), int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_prefix") if check else rc
+
+
+def rans_decode_prefix(d_msg, msg_size, lengths, n_lanes, chunk_symbols, d_symbols, n_symbols,
+                       d_status, stream=None, check=True) -> int:
+    ln = _lengths(lengths)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_prefix(_ptr(d_msg), int(msg_size), ln.ctypes.data, ln.size, C.byref(p),
+                                _ptr(d_symbols), int(n_symbols), _ptr(d_status), _stream(stream))
+    return _check(rc, "rans_decode_prefix") if check else rc
+
+
+def encode_prefix(symbols, lengths, n_lanes: int = 32, chunk_symbols: int = 65536, stream=None,
+                  sync: bool = True):
+    """Encode a CUDA uint8 tensor as a prefix-code message; (message, size, status)."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size_prefix(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size_prefix(n, n_lanes, chunk_symbols)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(scap, 16), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode_prefix(symbols, n, lengths, n_lanes, chunk_symbols, out, cap, size, status,
+                       scratch, scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode_prefix (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode_prefix(msg, n_symbols: int, lengths, n_lanes: int = 32, chunk_symbols: int = 65536,
+                  stream=None, sync: bool = True):
+    """Decode a prefix-code message; (symbols, status)."""
+    import torch
+
+    dev = msg.device
+    out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode_prefix(msg, msg.numel(), lengths, n_lanes, chunk_symbols, out, n_symbols, status,
+                       stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode_prefix (device status)")
     return out[:n_symbols], status
 
 
