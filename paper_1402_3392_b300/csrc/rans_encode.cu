@@ -42,10 +42,8 @@ struct EncodeParams {
 // (version 4: binary symbols, one adaptive context per coder).
 constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
 
-// Adaptive chunks keep four CTAs resident per SM (64 registers a thread).
 template <int NT, int KIND>
-__global__ void __launch_bounds__(enc::kThreads, KIND == kAdaptive ? 4 : 1)
-    encode_kernel(const __grid_constant__ EncodeParams p) {
+__device__ __forceinline__ void encode_body(const EncodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPT = KIND == kAdaptive;
@@ -71,6 +69,22 @@ __global__ void __launch_bounds__(enc::kThreads, KIND == kAdaptive ? 4 : 1)
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
     if (lane == 0) bulk_wait<0>();
+}
+
+// The launch bound alone keeps the plain, bypass and byte-wise encoders at
+// 64 registers or fewer (four CTAs per SM); asking for a minimum of one CTA
+// per SM lets the compiler spend more and costs a CTA per SM.  Adaptive
+// chunks need the explicit bound of four CTAs per SM.
+template <int NT, int KIND>
+__global__ void __launch_bounds__(enc::kThreads)
+    encode_kernel(const __grid_constant__ EncodeParams p) {
+    encode_body<NT, KIND>(p);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(enc::kThreads, 4)
+    encode_kernel_adaptive(const __grid_constant__ EncodeParams p) {
+    encode_body<NT, kAdaptive>(p);
 }
 
 struct FinalizeParams {
@@ -114,15 +128,18 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 
 template <int NT, int KIND>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
+    void (*kernel)(EncodeParams);
+    if constexpr (KIND == kAdaptive) kernel = encode_kernel_adaptive<NT>;
+    else kernel = encode_kernel<NT, KIND>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel<NT, KIND>, kWarps * 32,
-                                                      kSmemBytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, kSmemBytes) !=
+            cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
     const uint64_t want = ceil_div(p.n_chunks, kWarps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    encode_kernel<NT, KIND><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    kernel<<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
