@@ -287,3 +287,42 @@ def test_full_size_chunked_sampled_parity(rlib, orc, cuda):
         gpu_chunk = msg[data0 + offs[c]: data0 + offs[c + 1]].cpu().numpy()
         assert np.array_equal(gpu_chunk, orc.encode_chunk(chunk_sym, freq, N=N)), c
         assert np.array_equal(orc.decode_chunk(gpu_chunk, CS, freq, N=N), chunk_sym), c
+
+
+def test_largest_message_the_format_holds(rlib, orc, cuda):
+    """Offsets are u32, so with N = 32 and 64 Ki-symbol chunks a message holds
+    at most 32736 chunks (its worst-case data region, 128 bytes of states a
+    chunk plus 2 bytes a symbol, must stay below 2^32 - 16): that size round
+    trips, sampled chunks equal the oracle's, and one chunk more is refused
+    before anything runs."""
+    import torch
+
+    N, CS = 32, 1 << 16
+    k_max = (0xFFFFFFF0 // (4 * N + 2 * CS))
+    assert (4 * N + 2 * CS) * (k_max + 1) > 0xFFFFFFF0
+    n = k_max * CS
+    p = wl.zipf_probs(256, 1.1)
+    freq = rlib.rans_quantize_table(wl.weights_from_probs(p))
+    d = wl.iid_symbols_device(p, n, wl.seed_for("chunked", 7), cuda)
+    msg, _, _ = rlib.encode(d, freq, N, CS)
+    out, _ = rlib.decode(msg, n, freq, N, CS)
+    assert torch.equal(out, d)
+    del out
+    head = msg[: 32 + 4 * (k_max + 1)].cpu().numpy()
+    offs = head[32:].view(np.uint32).astype(np.int64)
+    data0 = (32 + 4 * (k_max + 1) + 15) // 16 * 16
+    for c in (0, k_max // 2, k_max - 1):
+        chunk_sym = d[c * CS:(c + 1) * CS].cpu().numpy()
+        gpu_chunk = msg[data0 + offs[c]: data0 + offs[c + 1]].cpu().numpy()
+        assert np.array_equal(gpu_chunk, orc.encode_chunk(chunk_sym, freq, N=N)), c
+    del msg
+    torch.cuda.empty_cache()
+    # One chunk more: refused by the size limit, which the library checks
+    # before the buffer capacities (given as 0 here, so no launch can follow
+    # whatever the answer).
+    n2 = n + CS
+    st = torch.zeros(1, dtype=torch.int32, device=cuda)
+    size = torch.zeros(1, dtype=torch.int64, device=cuda)
+    tiny = torch.empty(16, dtype=torch.uint8, device=cuda)
+    assert rlib.rans_encode(d, n2, freq, N, CS, tiny, 0, size, st, tiny, 0,
+                            check=False) == rlib.RANS_ERR_INVALID_ARG
