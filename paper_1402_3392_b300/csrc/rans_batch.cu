@@ -9,6 +9,7 @@
 // memory only when the model changes; each warp decodes one chunk with the
 // same code as the single-message decoder (two chunks per warp).
 #include <algorithm>
+#include <atomic>
 
 #include <cuda_runtime.h>
 
@@ -457,14 +458,15 @@ extern "C" int rans_decode_batch(const rans_stream *d_streams, uint32_t n_stream
     p.n_tables = n_tables;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-    static bool configured[64] = {false};
+    // Set once per device; concurrent first calls may both set it (harmless).
+    static std::atomic<bool> configured[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
         if (cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(dec::kSmemBytes)) != cudaSuccess)
             return RANS_ERR_CUDA;
-        configured[dev] = true;
+        configured[dev].store(true);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_decode_kernel, dec::kThreads,

@@ -3,6 +3,7 @@
 // chunk's N interleaved coders on the warp's lanes (decode_core.cuh), one
 // slot table per CTA built from the message's model.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -125,15 +126,16 @@ uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
 
 template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
-    static bool configured[64] = {false};
+    // Set once per device; concurrent first calls may both set it (harmless).
+    static std::atomic<bool> configured[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
         if (cudaFuncSetAttribute(decode_kernel<NT, KIND>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(kSmemBytes)) != cudaSuccess)
             return RANS_ERR_CUDA;
-        configured[dev] = true;
+        configured[dev].store(true);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT, KIND>, kWarps * 32,
