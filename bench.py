@@ -865,10 +865,12 @@ def main(argv=None):
     dec_mean, enc_mean, step_mean, wall_max = max_over_ranks(
         [statistics.mean(dec_ms), statistics.mean(enc_ms), step_ms, wall], dev, world)
 
-    e2e = None
+    e2e = e2e_enc = None
     if not args.no_e2e:
         e2e = end_to_end(rans, msg[:msg_size], n, freq, N, CS, dev, max(3, min(args.steps, 10)),
                          sym)
+        e2e_enc = end_to_end_encode(rans, sym, freq, N, CS, dev, max(3, min(args.steps, 10)),
+                                    msg[:msg_size])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -923,6 +925,7 @@ def main(argv=None):
             "clocks": sampler.summary(),
             "gpu_launches": 4 * args.steps,
             "e2e": e2e,
+            "e2e_encode": e2e_enc,
             "cpu_baseline": cpu,
         }
         line.update(extra)
@@ -965,6 +968,44 @@ def end_to_end(rans, msg_dev, n, freq, N, CS, dev, steps, sym_dev):
     return {"value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(msg_dev.numel()), "d2h_bytes_per_step": n + 4,
             "api": "rans_decode_host"}
+
+
+def end_to_end_encode(rans, sym_dev, freq, N, CS, dev, steps, msg_dev):
+    """Encoded input GB/s through the C ABI with host buffers
+    (rans_encode_host): each step copies the symbols in from pinned host
+    memory and the device writes the message straight into pinned host
+    memory, pieces overlapped; the size and status words come back too."""
+    import torch
+
+    n = sym_dev.numel()
+    h_sym = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_sym.copy_(sym_dev)
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    h_out = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
+    h_size = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+    h_st = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    work = torch.empty(rans.rans_encode_host_work_size(n, N, CS), dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+
+    def one():
+        rans.rans_encode_host(h_sym, n, freq, N, CS, h_out, cap, h_size, h_st, work,
+                              work.numel(), s)
+
+    one()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(steps):
+        one()
+    b.record(s)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    size = int(h_size.item())
+    assert int(h_st.item()) == 0 and size == msg_dev.numel()
+    assert torch.equal(h_out[:size], msg_dev.cpu()), "end-to-end encode differs"
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": n, "d2h_bytes_per_step": size + 12,
+            "api": "rans_encode_host"}
 
 
 def cpu_baseline(msg, freq, N, CS, n_chunks):

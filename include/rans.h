@@ -190,6 +190,33 @@ int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16_t *h_freq,
  * work on `stream` runs after it; h_symbols and h_status are valid, and the
  * host buffers may be reused, once `stream` has reached that point.
  */
+/*
+ * rans_encode_host -- rans_encode with the symbols and the message in host
+ * memory.  The symbols are copied in by pieces of whole chunks on one
+ * internal stream, coded on `stream`, and each piece's chunks are given
+ * their final offsets (a running total on the device) and packed into the
+ * output on another internal stream, so the copies overlap the coding.  A
+ * page-locked, 16-byte aligned h_out is written directly by the device,
+ * piece by piece; any other h_out receives the message in one copy at the
+ * end, and then the call waits for `stream` before it returns.
+ *
+ * h_symbols, n_symbols, h_freq, n_alpha, params : as in rans_encode, with
+ *             h_symbols in host memory.
+ * h_out     : host, out_cap >= rans_max_encoded_size(n_symbols, params).
+ * h_out_size: host u64: the message size (0 if the encode failed).
+ * h_status  : host u32: RANS_OK or RANS_ERR_ZERO_FREQ (or RANS_ERR_TIMEOUT).
+ * d_work    : device, 16-byte aligned, work_cap >=
+ *             rans_encode_host_work_size(n_symbols, params): the symbols, the
+ *             encode scratch, the offsets and a worst-case message.
+ * Returns RANS_OK, RANS_ERR_INVALID_ARG, RANS_ERR_BUFFER_TOO_SMALL or
+ * RANS_ERR_CUDA.  h_out, *h_out_size and *h_status are valid, and the host
+ * buffers may be reused, once `stream` has reached the end of the work.
+ */
+uint64_t rans_encode_host_work_size(uint64_t n_symbols, const rans_params *params);
+int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols, const uint16_t *h_freq,
+                     uint32_t n_alpha, const rans_params *params, uint8_t *h_out,
+                     uint64_t out_cap, uint64_t *h_out_size, uint32_t *h_status, void *d_work,
+                     uint64_t work_cap, rans_stream_t stream);
 uint64_t rans_decode_host_work_size(uint64_t msg_size, uint64_t n_symbols);
 int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const uint16_t *h_freq,
                      uint32_t n_alpha, const rans_params *params, uint8_t *h_symbols,

@@ -502,21 +502,20 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     if (lane < N) states[lane] = x;
 }
 
-// With a whole CTA: exclusive scan of the chunk sizes into the offset table,
-// the header, zero padding, and the message size.  blockDim.x is a multiple
-// of 32; warp_sums: 32 words of shared memory, carry: one word.
-__device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_size,
-                                                 const uint32_t *sizes, uint64_t n_sym, uint32_t N,
-                                                 uint32_t CS, uint32_t n_chunks, uint32_t data0,
-                                                 uint32_t *warp_sums, uint32_t *carry_s,
-                                                 uint32_t version = RANS_VERSION) {
+// With a whole CTA (blockDim.x a multiple of 32): offsets of chunks
+// [c_begin, c_end) = carry + the exclusive prefix of their sizes, written to
+// offs_a[c] and, if not null, offs_b[c].  Returns (to every thread) carry +
+// the sizes' total.  warp_sums: 32 words of shared memory, carry_s: one.
+__device__ __forceinline__ uint64_t scan_sizes(const uint32_t *sizes, uint32_t c_begin,
+                                               uint32_t c_end, uint64_t carry, uint32_t *offs_a,
+                                               uint32_t *offs_b, uint32_t *warp_sums,
+                                               uint64_t *carry_s) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    uint32_t *offs = reinterpret_cast<uint32_t *>(out + 32);
-    if (tid == 0) *carry_s = 0;
+    if (tid == 0) *carry_s = carry;
     __syncthreads();
-    for (uint64_t base = 0; base < n_chunks; base += nt) {
+    for (uint64_t base = c_begin; base < c_end; base += nt) {
         const uint64_t i = base + tid;
-        const uint32_t v = i < n_chunks ? sizes[i] : 0u;
+        const uint32_t v = i < c_end ? sizes[i] : 0u;
         uint32_t incl = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -536,29 +535,52 @@ __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_siz
             if (lane < nt / 32) warp_sums[lane] = wi - w;  // exclusive prefix of warp totals
         }
         __syncthreads();
-        const uint32_t carry = *carry_s;
-        if (i < n_chunks) offs[i] = carry + warp_sums[warp] + incl - v;
+        const uint64_t c0 = *carry_s;
+        if (i < c_end) {
+            const uint32_t o = uint32_t(c0 + warp_sums[warp] + incl - v);
+            offs_a[i] = o;
+            if (offs_b) offs_b[i] = o;
+        }
         __syncthreads();
-        if (tid == nt - 1) *carry_s = carry + warp_sums[warp] + incl;
+        if (tid == nt - 1) *carry_s = c0 + warp_sums[warp] + incl;
         __syncthreads();
     }
-    if (tid == 0) {
-        const uint32_t total = *carry_s;
-        uint32_t *h = reinterpret_cast<uint32_t *>(out);
-        h[0] = RANS_MAGIC;
-        h[1] = version;
-        h[2] = N;
-        h[3] = kLog2M;
-        h[4] = uint32_t(n_sym);
-        h[5] = uint32_t(n_sym >> 32);
-        h[6] = CS;
-        h[7] = n_chunks;
-        offs[n_chunks] = total;
-        for (uint32_t b = 32 + 4 * (n_chunks + 1); b < data0; ++b) out[b] = 0;
-        const uint64_t end = uint64_t(data0) + total;
-        for (uint64_t b = end; b < round16(end); ++b) out[b] = 0;
-        *out_size = round16(end);
-    }
+    return *carry_s;
+}
+
+// One thread: the header, the offset table's last entry (total data bytes),
+// the zero padding before and after the data region, and the message size.
+__device__ __forceinline__ void write_header(uint8_t *out, uint64_t *out_size, uint64_t n_sym,
+                                             uint32_t N, uint32_t CS, uint32_t n_chunks,
+                                             uint32_t data0, uint32_t total, uint32_t version) {
+    uint32_t *h = reinterpret_cast<uint32_t *>(out);
+    h[0] = RANS_MAGIC;
+    h[1] = version;
+    h[2] = N;
+    h[3] = kLog2M;
+    h[4] = uint32_t(n_sym);
+    h[5] = uint32_t(n_sym >> 32);
+    h[6] = CS;
+    h[7] = n_chunks;
+    reinterpret_cast<uint32_t *>(out + 32)[n_chunks] = total;
+    for (uint32_t b = 32 + 4 * (n_chunks + 1); b < data0; ++b) out[b] = 0;
+    const uint64_t end = uint64_t(data0) + total;
+    for (uint64_t b = end; b < round16(end); ++b) out[b] = 0;
+    *out_size = round16(end);
+}
+
+// With a whole CTA: exclusive scan of the chunk sizes into the offset table,
+// the header, zero padding, and the message size.  blockDim.x is a multiple
+// of 32; warp_sums: 32 words of shared memory, carry: one.
+__device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_size,
+                                                 const uint32_t *sizes, uint64_t n_sym, uint32_t N,
+                                                 uint32_t CS, uint32_t n_chunks, uint32_t data0,
+                                                 uint32_t *warp_sums, uint64_t *carry_s,
+                                                 uint32_t version = RANS_VERSION) {
+    uint32_t *offs = reinterpret_cast<uint32_t *>(out + 32);
+    const uint64_t total = scan_sizes(sizes, 0, n_chunks, 0, offs, nullptr, warp_sums, carry_s);
+    if (threadIdx.x == 0)
+        write_header(out, out_size, n_sym, N, CS, n_chunks, data0, uint32_t(total), version);
 }
 
 // Copy chunk c (states, then words) to its place in the message.  The
@@ -590,11 +612,13 @@ __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, ui
 // must have 16 readable bytes past its last slot.
 // BYTES: the chunk's byte count may be odd and its start in the slot too;
 // the chunk is padded with zeros to a multiple of 4 bytes.
+// offs_in: the chunk offsets, if not those in out's own offset table.
 template <bool BYTES = false>
 __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const uint8_t *words,
                                            const uint32_t *states, const uint32_t *wstart,
-                                           uint32_t N, uint32_t slot_bytes, uint32_t c) {
-    const uint32_t *offs = reinterpret_cast<const uint32_t *>(out + 32);
+                                           uint32_t N, uint32_t slot_bytes, uint32_t c,
+                                           const uint32_t *offs_in = nullptr) {
+    const uint32_t *offs = offs_in ? offs_in : reinterpret_cast<const uint32_t *>(out + 32);
     const uint64_t D = uint64_t(data0) + offs[c];
     uint16_t *dst16 = reinterpret_cast<uint16_t *>(out + D);
     const uint32_t *st = states + uint64_t(c) * N;

@@ -49,6 +49,16 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Two non-blocking streams per device, one for host-to-device and one for
+// device-to-host copies, created on a device's first use and kept.
+struct CopyStreams {
+    cudaStream_t in = nullptr, out = nullptr;
+};
+int copy_streams(CopyStreams *cs);
+
+// Stream `waiter` waits for the work enqueued on `signaler` so far.
+bool join(cudaStream_t waiter, cudaStream_t signaler);
+
 inline int check_launch() {
     return cudaGetLastError() == cudaSuccess ? RANS_OK : RANS_ERR_CUDA;
 }

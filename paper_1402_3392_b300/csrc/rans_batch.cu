@@ -395,7 +395,7 @@ constexpr int kFinThreads = 256;
 __global__ void __launch_bounds__(kFinThreads)
     enc_finalize_kernel(const __grid_constant__ BatchEncodeParams p) {
     __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry_s;
+    __shared__ uint64_t carry_s;
     for (uint32_t s = blockIdx.x; s < p.n_streams; s += gridDim.x) {
         const uint32_t st = p.status[s];
         if (st != RANS_OK) {

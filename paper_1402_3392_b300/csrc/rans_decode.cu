@@ -299,40 +299,6 @@ namespace {
 constexpr uint64_t kPieceSymbols = 32ull << 20;  // about this many symbols per piece
 constexpr uint32_t kMaxPieces = 256;
 
-struct CopyStreams {
-    cudaStream_t in = nullptr, out = nullptr;
-};
-
-// Two non-blocking streams per device (host-to-device copies and
-// device-to-host copies), created on first use and kept for the process.
-int copy_streams(CopyStreams *cs) {
-    static std::mutex mu;
-    static CopyStreams per_dev[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RANS_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(mu);
-    CopyStreams &c = per_dev[dev];
-    if (!c.in) {
-        if (cudaStreamCreateWithFlags(&c.in, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c.out, cudaStreamNonBlocking) != cudaSuccess) {
-            c.in = c.out = nullptr;
-            return RANS_ERR_CUDA;
-        }
-    }
-    *cs = c;
-    return RANS_OK;
-}
-
-// stream `waiter` waits for the work enqueued on `signaler` so far.
-bool join(cudaStream_t waiter, cudaStream_t signaler) {
-    cudaEvent_t ev;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
-    const bool ok = cudaEventRecord(ev, signaler) == cudaSuccess &&
-                    cudaStreamWaitEvent(waiter, ev, 0) == cudaSuccess;
-    cudaEventDestroy(ev);  // released once the event has completed
-    return ok;
-}
-
 }  // namespace
 
 extern "C" uint64_t rans_decode_host_work_size(uint64_t msg_size, uint64_t n_symbols) {

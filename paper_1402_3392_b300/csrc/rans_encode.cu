@@ -30,6 +30,7 @@ struct EncodeParams {
     uint32_t CS;
     uint32_t n_chunks;
     uint32_t slot_bytes;
+    uint32_t c_begin, c_end;  // chunks [c_begin, c_end) are coded by this launch
     const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
     uint64_t ctx_stride;  // u32 words per chunk in ctx
@@ -56,7 +57,8 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
-    for (uint32_t c = blockIdx.x * kWarps + warp; c < p.n_chunks; c += gridDim.x * kWarps) {
+    for (uint32_t c = p.c_begin + blockIdx.x * kWarps + warp; c < p.c_end;
+         c += gridDim.x * kWarps) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
         uint32_t *ctx = ADAPT ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
@@ -100,7 +102,7 @@ constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads)
     finalize_kernel(const __grid_constant__ FinalizeParams p) {
     __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry_s;
+    __shared__ uint64_t carry_s;
     if (*p.status != RANS_OK) {
         if (threadIdx.x == 0) *p.out_size = 0;
         return;
@@ -115,15 +117,18 @@ struct PackParams {
     const uint32_t *states;
     const uint32_t *wstart;
     const uint32_t *status;
+    const uint32_t *offs;     // chunk offsets, or nullptr: out's own offset table
     uint32_t N, n_chunks, data0, slot_bytes;
+    uint32_t c_begin, c_end;  // chunks packed by this launch
 };
 
 constexpr int kPackThreads = 256;
 template <bool BYTES>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackParams p) {
     if (*p.status != RANS_OK) return;
-    for (uint32_t c = blockIdx.x; c < p.n_chunks; c += gridDim.x)
-        enc::pack_chunk<BYTES>(p.out, p.data0, p.words, p.states, p.wstart, p.N, p.slot_bytes, c);
+    for (uint32_t c = p.c_begin + blockIdx.x; c < p.c_end; c += gridDim.x)
+        enc::pack_chunk<BYTES>(p.out, p.data0, p.words, p.states, p.wstart, p.N, p.slot_bytes, c,
+                               p.offs);
 }
 
 template <int NT, int KIND>
@@ -136,7 +141,7 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
             cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
-    const uint64_t want = ceil_div(p.n_chunks, kWarps);
+    const uint64_t want = ceil_div(p.c_end - p.c_begin, kWarps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     kernel<<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
@@ -218,6 +223,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.CS = params->chunk_symbols;
     ep.n_chunks = uint32_t(g.n_chunks);
     ep.slot_bytes = sl.slot_bytes;
+    ep.c_begin = 0;
+    ep.c_end = ep.n_chunks;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
     if (g.n_chunks > 0) {
@@ -257,6 +264,8 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
         pp.n_chunks = ep.n_chunks;
         pp.data0 = fp.data0;
         pp.slot_bytes = ep.slot_bytes;
+        pp.c_begin = 0;
+        pp.c_end = ep.n_chunks;
         const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
         if (bytes) pack_kernel<true><<<grid, kPackThreads, 0, st>>>(pp);
         else pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
@@ -381,6 +390,8 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     ep.CS = params->chunk_symbols;
     ep.n_chunks = uint32_t(g.n_chunks);
     ep.slot_bytes = sl.slot_bytes;
+    ep.c_begin = 0;
+    ep.c_end = ep.n_chunks;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
     if (g.n_chunks > 0) {
         const int rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
@@ -410,9 +421,216 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
         pp.n_chunks = ep.n_chunks;
         pp.data0 = fp.data0;
         pp.slot_bytes = ep.slot_bytes;
+        pp.c_begin = 0;
+        pp.c_end = ep.n_chunks;
         const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
         pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
         if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    }
+    return RANS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rans_encode_host: encoding from and to host memory, copies overlapped with
+// coding.
+// ---------------------------------------------------------------------------
+namespace rans {
+namespace {
+
+constexpr uint64_t kHostPieceSymbols = 32ull << 20;  // about this many symbols per piece
+constexpr uint32_t kHostMaxPieces = 256;
+
+struct RangeOffsetsParams {
+    const uint32_t *sizes;
+    uint32_t *d_offs;      // device copy of the offset table
+    uint32_t *msg_offs;    // the message's offset table (device or page-locked host memory)
+    uint64_t *running;     // data bytes of the chunks before c_begin; advanced past c_end
+    uint32_t c_begin, c_end;
+};
+
+// One CTA: the offsets of chunks [c_begin, c_end), after those before them.
+__global__ void __launch_bounds__(kScanThreads)
+    range_offsets_kernel(const __grid_constant__ RangeOffsetsParams p) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint64_t carry_s;
+    const uint64_t total = enc::scan_sizes(p.sizes, p.c_begin, p.c_end, *p.running, p.d_offs,
+                                           p.msg_offs, warp_sums, &carry_s);
+    if (threadIdx.x == 0) *p.running = total;
+}
+
+struct HeaderParams {
+    uint8_t *out;
+    uint64_t *d_size;
+    const uint64_t *running;
+    const uint32_t *status;
+    uint64_t n_sym;
+    uint32_t N, CS, n_chunks, data0;
+};
+
+__global__ void host_header_kernel(const __grid_constant__ HeaderParams p) {
+    if (*p.status != RANS_OK) {
+        *p.d_size = 0;
+        return;
+    }
+    enc::write_header(p.out, p.d_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
+                      uint32_t(*p.running), RANS_VERSION);
+}
+
+// Work space: [symbols][encode scratch][device offsets][running, status,
+// size][message, for a pageable output buffer].
+struct HostWork {
+    uint64_t sym, scratch, offs, misc, msg, total;
+};
+
+HostWork host_work(uint64_t n_symbols, const rans_params *params) {
+    const MessageGeometry g = geometry(n_symbols, params);
+    HostWork w;
+    w.sym = 0;
+    w.scratch = round16(n_symbols);
+    w.offs = w.scratch + scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).total;
+    w.misc = w.offs + round16(4 * (g.n_chunks + 1));
+    w.msg = w.misc + 64;
+    w.total = w.msg + round16(rans_max_encoded_size(n_symbols, params));
+    return w;
+}
+
+}  // namespace
+}  // namespace rans
+
+extern "C" uint64_t rans_encode_host_work_size(uint64_t n_symbols, const rans_params *params) {
+    if (!params_ok(params)) return 0;
+    return host_work(n_symbols, params).total;
+}
+
+extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
+                                const uint16_t *h_freq, uint32_t n_alpha,
+                                const rans_params *params, uint8_t *h_out, uint64_t out_cap,
+                                uint64_t *h_out_size, uint32_t *h_status, void *d_work,
+                                uint64_t work_cap, rans_stream_t stream) {
+    if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !h_out || !h_out_size ||
+        !h_status || !d_work || !aligned16(d_work) || (n_symbols && !h_symbols))
+        return RANS_ERR_INVALID_ARG;
+    const MessageGeometry g = geometry(n_symbols, params);
+    if (g.n_chunks > 0xFFFFFFFEull ||
+        4ull * params->n_lanes * g.n_chunks + 2ull * n_symbols > 0xFFFFFFF0ull)
+        return RANS_ERR_INVALID_ARG;
+    const uint64_t max_out = rans_max_encoded_size(n_symbols, params);
+    const HostWork hw = host_work(n_symbols, params);
+    if (out_cap < max_out || work_cap < hw.total) return RANS_ERR_BUFFER_TOO_SMALL;
+
+    // A page-locked, 16-byte aligned output buffer is written by the kernels
+    // through its device address, piece by piece (the pack writes 16-byte
+    // blocks); any other gets the message from device memory once the coding
+    // is done.
+    uint8_t *out_dev = nullptr;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, h_out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer != nullptr && aligned16(attr.devicePointer))
+        out_dev = static_cast<uint8_t *>(attr.devicePointer);
+    else
+        cudaGetLastError();  // a pageable pointer may leave an error behind
+    uint8_t *w = static_cast<uint8_t *>(d_work);
+    const bool staged = out_dev == nullptr;
+    if (staged) out_dev = w + hw.msg;
+
+    const ScratchLayout sl = scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols);
+    uint8_t *scr = w + hw.scratch;
+    uint64_t *running = reinterpret_cast<uint64_t *>(w + hw.misc);
+    uint32_t *d_status = reinterpret_cast<uint32_t *>(w + hw.misc + 8);
+    uint64_t *d_size = reinterpret_cast<uint64_t *>(w + hw.misc + 16);
+    uint32_t *d_offs = reinterpret_cast<uint32_t *>(w + hw.offs);
+
+    EncodeParams ep{};
+    ep.sym = w + hw.sym;
+    ep.words = scr + sl.words;
+    ep.states = reinterpret_cast<uint32_t *>(scr + sl.states);
+    ep.wstart = reinterpret_cast<uint32_t *>(scr + sl.wstart);
+    ep.sizes = reinterpret_cast<uint32_t *>(scr + sl.sizes);
+    ep.status = d_status;
+    ep.n_sym = n_symbols;
+    ep.N = params->n_lanes;
+    ep.CS = params->chunk_symbols;
+    ep.n_chunks = uint32_t(g.n_chunks);
+    ep.slot_bytes = sl.slot_bytes;
+    for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
+
+    CopyStreams cs;
+    int rc = copy_streams(&cs);
+    if (rc != RANS_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(w + hw.misc, 0, 64, st) != cudaSuccess || !join(cs.in, st) ||
+        !join(cs.out, st))
+        return RANS_ERR_CUDA;
+
+    // Pieces of whole chunks: the symbols of piece k are copied in on one
+    // stream, coded and given their offsets on the caller's stream, and
+    // packed into the output on a third, so the copy-in of piece k+1 and the
+    // output of piece k-1 overlap the coding of piece k.
+    const uint32_t nc = ep.n_chunks;
+    const uint32_t per_piece = uint32_t(std::max<uint64_t>(
+        std::max<uint64_t>(1, ceil_div(kHostPieceSymbols, ep.CS)), ceil_div(nc, kHostMaxPieces)));
+    for (uint64_t c0 = 0; c0 < nc; c0 += per_piece) {
+        const uint64_t c1 = std::min<uint64_t>(nc, c0 + per_piece);
+        const uint64_t s0 = c0 * ep.CS, s1 = std::min<uint64_t>(n_symbols, c1 * ep.CS);
+        if (cudaMemcpyAsync(w + hw.sym + s0, h_symbols + s0, s1 - s0, cudaMemcpyHostToDevice,
+                            cs.in) != cudaSuccess ||
+            !join(st, cs.in))
+            return RANS_ERR_CUDA;
+        ep.c_begin = uint32_t(c0);
+        ep.c_end = uint32_t(c1);
+        rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
+        if (rc != RANS_OK) return rc;
+        RangeOffsetsParams rp{};
+        rp.sizes = ep.sizes;
+        rp.d_offs = d_offs;
+        rp.msg_offs = reinterpret_cast<uint32_t *>(out_dev + 32);
+        rp.running = running;
+        rp.c_begin = uint32_t(c0);
+        rp.c_end = uint32_t(c1);
+        range_offsets_kernel<<<1, kScanThreads, 0, st>>>(rp);
+        if (check_launch() != RANS_OK || !join(cs.out, st)) return RANS_ERR_CUDA;
+        PackParams pp{};
+        pp.out = out_dev;
+        pp.words = ep.words;
+        pp.states = ep.states;
+        pp.wstart = ep.wstart;
+        pp.status = d_status;
+        pp.offs = d_offs;
+        pp.N = ep.N;
+        pp.n_chunks = nc;
+        pp.data0 = uint32_t(g.data0);
+        pp.slot_bytes = ep.slot_bytes;
+        pp.c_begin = uint32_t(c0);
+        pp.c_end = uint32_t(c1);
+        const unsigned grid = unsigned(std::min<uint64_t>(c1 - c0, 65535ull * 8));
+        pack_kernel<false><<<grid, kPackThreads, 0, cs.out>>>(pp);
+        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    }
+    if (!join(cs.out, st)) return RANS_ERR_CUDA;
+    HeaderParams hp{};
+    hp.out = out_dev;
+    hp.d_size = d_size;
+    hp.running = running;
+    hp.status = d_status;
+    hp.n_sym = n_symbols;
+    hp.N = ep.N;
+    hp.CS = ep.CS;
+    hp.n_chunks = nc;
+    hp.data0 = uint32_t(g.data0);
+    host_header_kernel<<<1, 1, 0, cs.out>>>(hp);
+    if (check_launch() != RANS_OK ||
+        cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs.out) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(h_out_size, d_size, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs.out) !=
+            cudaSuccess ||
+        !join(st, cs.out))
+        return RANS_ERR_CUDA;
+    if (staged) {
+        // Pageable output: the size is known once the work is done.
+        if (cudaStreamSynchronize(st) != cudaSuccess) return RANS_ERR_CUDA;
+        if (*h_out_size &&
+            cudaMemcpy(h_out, out_dev, *h_out_size, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return RANS_ERR_CUDA;
     }
     return RANS_OK;
 }

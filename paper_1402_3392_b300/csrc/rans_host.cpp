@@ -25,6 +25,36 @@ int sm_count() {
     return cached[dev];
 }
 
+// Two non-blocking streams per device (host-to-device copies and
+// device-to-host copies), created on first use and kept for the process.
+int copy_streams(CopyStreams *cs) {
+    static std::mutex mu;
+    static CopyStreams per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RANS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    CopyStreams &c = per_dev[dev];
+    if (!c.in) {
+        if (cudaStreamCreateWithFlags(&c.in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c.out, cudaStreamNonBlocking) != cudaSuccess) {
+            c.in = c.out = nullptr;
+            return RANS_ERR_CUDA;
+        }
+    }
+    *cs = c;
+    return RANS_OK;
+}
+
+// stream `waiter` waits for the work enqueued on `signaler` so far.
+bool join(cudaStream_t waiter, cudaStream_t signaler) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    const bool ok = cudaEventRecord(ev, signaler) == cudaSuccess &&
+                    cudaStreamWaitEvent(waiter, ev, 0) == cudaSuccess;
+    cudaEventDestroy(ev);  // released once the event has completed
+    return ok;
+}
+
 }  // namespace rans
 
 using namespace rans;

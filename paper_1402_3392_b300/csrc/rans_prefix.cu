@@ -160,7 +160,7 @@ constexpr int kFinThreads = 1024;
 __global__ void __launch_bounds__(kFinThreads)
     prefix_finalize_kernel(const __grid_constant__ PrefixFinalizeParams p) {
     __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry_s;
+    __shared__ uint64_t carry_s;
     if (*p.status != RANS_OK) {
         if (threadIdx.x == 0) *p.out_size = 0;
         return;

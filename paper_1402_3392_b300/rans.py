@@ -115,6 +115,8 @@ def _load() -> C.CDLL:
         "rans_encode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp]),
         "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
+        "rans_encode_host_work_size": (u64, [u64, pp]),
+        "rans_encode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_batch_scratch_size": (u64, [u32]),
         "rans_decode_batch": (i32, [vp, u32, vp, u32, vp, vp, u64, vp]),
         "rans_encode_batch_plan": (u64, [vp, u32]),
@@ -554,6 +556,49 @@ def decode_host(msg, n_symbols: int, freq, n_lanes: int = 32, chunk_symbols: int
     else:
         torch.cuda.current_stream(device).synchronize()
     return out[:n_symbols], int(status.item())
+
+
+def rans_encode_host_work_size(n_symbols: int, n_lanes: int = 32, chunk_symbols: int = 65536) -> int:
+    return int(lib.rans_encode_host_work_size(int(n_symbols),
+                                              C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_host(h_symbols, n_symbols, freq, n_lanes, chunk_symbols, h_out, out_cap,
+                     h_out_size, h_status, d_work, work_cap, stream=None, check=True) -> int:
+    """rans_encode from and to host memory (pointers or CPU tensors; a
+    page-locked, 16-byte aligned output is written by the device directly)."""
+    f = _freq(freq)
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_host(_ptr(h_symbols), int(n_symbols), f.ctypes.data, f.size, C.byref(p),
+                              _ptr(h_out), int(out_cap), _ptr(h_out_size), _ptr(h_status),
+                              _ptr(d_work), int(work_cap), _stream(stream))
+    return _check(rc, "rans_encode_host") if check else rc
+
+
+def encode_host(symbols, freq, n_lanes: int = 32, chunk_symbols: int = 65536, device=None,
+                stream=None, out=None, work=None):
+    """Encode a host (CPU, ideally pinned) uint8 tensor through
+    rans_encode_host.  Returns (message, status) after synchronizing; the
+    message is a view of the output buffer."""
+    import torch
+
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    n = symbols.numel()
+    cap = rans_max_encoded_size(n, n_lanes, chunk_symbols)
+    wcap = rans_encode_host_work_size(n, n_lanes, chunk_symbols)
+    if work is None or work.numel() < wcap:
+        work = torch.empty(wcap, dtype=torch.uint8, device=device)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
+    size = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+    status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    rans_encode_host(symbols, n, freq, n_lanes, chunk_symbols, out, out.numel(), size, status,
+                     work, work.numel(), stream)
+    if stream is not None:
+        stream.synchronize()
+    else:
+        torch.cuda.current_stream(device).synchronize()
+    return out[: int(size.item())], int(status.item())
 
 
 def rans_check_bounded_wait(d_status, stream=None, check=True) -> int:

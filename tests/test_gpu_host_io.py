@@ -1,6 +1,7 @@
-"""rans_decode_host: decoding from and to host memory with the copies
-overlapped with the decoding, against the CPU oracle byte for byte.  Sizes
-span several pieces (a piece is about 32 Mi symbols of whole chunks)."""
+"""rans_decode_host and rans_encode_host: decoding and encoding from and to
+host memory with the copies overlapped with the coding, against the CPU
+oracle byte for byte.  Sizes span several pieces (a piece is about 32 Mi
+symbols of whole chunks)."""
 import numpy as np
 import pytest
 
@@ -91,3 +92,57 @@ def test_host_decode_small_and_pageable(rlib, orc, cuda):
     with pytest.raises(rlib.RansError) as e:
         rlib.rans_decode_host(h_msg, msg.size, freq, 32, 65536, out, n, status, work, 16)
     assert e.value.code == rlib.RANS_ERR_BUFFER_TOO_SMALL
+
+
+# ---------------------------------------------------------------------------
+# rans_encode_host: symbols and message in host memory
+# ---------------------------------------------------------------------------
+
+def test_host_encode_matches_oracle(rlib, cuda, big):
+    """Page-locked input and output: the device writes the message straight
+    into host memory piece by piece (four pieces here)."""
+    freq, sym, msg = big
+    out, st = rlib.encode_host(pinned(sym), freq, 32, 65536, device=cuda)
+    assert st == rlib.RANS_OK
+    assert np.array_equal(out.numpy(), msg)
+
+
+def test_host_encode_pageable_and_misaligned_outputs(rlib, cuda, big):
+    """A pageable output (and pageable input), and a page-locked output that
+    is not 16-byte aligned, take the staged path: same message."""
+    import torch
+
+    freq, sym, msg = big
+    n = 40 << 20                                      # two pieces
+    cap = rlib.rans_max_encoded_size(n, 32, 65536)
+    pageable = torch.empty(cap, dtype=torch.uint8)
+    got, st = rlib.encode_host(torch.from_numpy(sym[:n].copy()), freq, 32, 65536, device=cuda,
+                               out=pageable)
+    assert st == rlib.RANS_OK
+    ref_msg = oracle.default().encode_message(sym[:n], freq, N=32, chunk_symbols=65536)
+    assert np.array_equal(got.numpy(), ref_msg)
+    base = torch.empty(cap + 16, dtype=torch.uint8, pin_memory=True)
+    shifted = base[4:4 + cap]
+    got, st = rlib.encode_host(pinned(sym[:n]), freq, 32, 65536, device=cuda, out=shifted)
+    assert st == rlib.RANS_OK
+    assert np.array_equal(got.numpy(), ref_msg)
+
+
+@pytest.mark.parametrize("n,N,CS", [(0, 32, 65536), (1, 32, 65536), (33, 7, 4), (100_003, 5, 999)])
+def test_host_encode_small(rlib, orc, cuda, n, N, CS):
+    rng = np.random.default_rng(n + N)
+    freq = rlib.rans_quantize_table(wl.weights_from_probs(wl.zipf_probs(40, 1.0)))
+    sym = wl.iid_symbols(rng, freq / freq.sum(), n)
+    out, st = rlib.encode_host(pinned(sym), freq, N, CS, device=cuda)
+    assert st == rlib.RANS_OK
+    assert np.array_equal(out.numpy(), orc.encode_message(sym, freq, N=N, chunk_symbols=CS))
+
+
+def test_host_encode_zero_frequency_symbol(rlib, cuda):
+    freq = np.zeros(4, dtype=np.uint16)
+    freq[:3] = [2048, 1024, 1024]
+    sym = np.zeros(300_000, dtype=np.uint8)
+    sym[123_456] = 3
+    out, st = rlib.encode_host(pinned(sym), freq, 32, 4096, device=cuda)
+    assert st == rlib.RANS_ERR_ZERO_FREQ
+    assert out.numel() == 0
