@@ -1011,12 +1011,12 @@ def end_to_end_encode(rans, sym_dev, freq, N, CS, dev, steps, msg_dev):
 def cpu_baseline(msg, freq, N, CS, n_chunks):
     cores = host_cores()
     chunks = split_chunks(msg, n_chunks)
-    count = min(len(chunks), 128 * cores)
+    count = min(len(chunks), 256 * cores)       # about 20 s of CPU work
     rate, dt = oracle_decode_rate(chunks[:count], freq, N, CS, cores)
     return {"value": rate / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle decode of {count} chunks x {CS} symbols of this workload's "
                       f"message ({count * CS / 2**20:.0f} MiB) on {cores} threads, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s ({dt * cores:.0f} CPU-seconds)"}
 
 
 if __name__ == "__main__":
