@@ -546,11 +546,15 @@ __device__ __forceinline__ void decode_step_adaptive(uint32_t &x, uint32_t &p, u
     const bool on = FULL || active;
     if (on) {
         const uint32_t slot = x & (kM - 1);
-        const bool one = slot >= p;
-        const uint32_t f = one ? kM - p : p;
+        const uint32_t one = slot >= p;
+        const uint32_t q = kM - p;
+        const uint32_t f = one ? q : p;
         x = imad(f, x >> kLog2M, slot - (one ? p : 0u));
         *outp = uint8_t(one);
-        p = one ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+        // p + floor((T - p) / 2^rate) with T = M after a 0 and T = 2^rate - 1
+        // after a 1, where floor((2^rate - 1 - p) / 2^rate) = -floor(p / 2^rate):
+        // the two updates of the model in one arithmetic shift.
+        p += uint32_t(int32_t(q - one * (kM - ((1u << kAdaptRate) - 1))) >> kAdaptRate);
     }
     const bool need = on && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);

@@ -214,8 +214,12 @@ __device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uin
     }
 }
 
+// After a 0, p += (M - p) >> rate; after a 1, p -= p >> rate -- both as
+// p + floor((T - p) / 2^rate), T = M or 2^rate - 1 (s is 0 or 1 here, any
+// nonzero symbol counting as a 1).
 __device__ __forceinline__ uint32_t adapt_ctx(uint32_t p, uint32_t s) {
-    return s ? p - (p >> kAdaptRate) : p + ((kM - p) >> kAdaptRate);
+    const uint32_t one = s != 0u;
+    return p + uint32_t(int32_t((kM - p) - one * (kM - ((1u << kAdaptRate) - 1))) >> kAdaptRate);
 }
 
 // Adaptive scratch of one chunk, in u32 words: for each full group g of
