@@ -221,6 +221,38 @@ def oracle_decode_rate(chunks, freq, N, CS, threads, repeats=1):
     return len(chunks) * CS * repeats / dt, dt
 
 
+def _oracle():
+    import oracle
+
+    return oracle.default()
+
+
+def host_chunks(msg_dev, n_chunks: int, k: int):
+    """The first k chunks of a message in device memory, as host arrays."""
+    k = min(k, n_chunks)
+    data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+    offs = msg_dev[32:32 + 4 * (k + 1)].cpu().numpy().view(np.uint32).astype(np.int64)
+    data = msg_dev[data0:data0 + int(offs[k])].cpu().numpy()
+    return [data[offs[c]:offs[c + 1]] for c in range(k)]
+
+
+def oracle_leg_baseline(decode_one, chunks, symbols_per_chunk, unit_bytes=True):
+    """The CPU oracle beside a leg: decode_one(chunk) over a bounded sample of
+    the leg's own chunks on the host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    cores = host_cores()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(decode_one, chunks))
+    dt = time.perf_counter() - t0
+    rate = len(chunks) * symbols_per_chunk / dt / 1e9
+    return {"value": rate, "unit": "GB/s" if unit_bytes else "G symbols/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle decode of the leg's first {len(chunks)} chunks x "
+                      f"{symbols_per_chunk} symbols on {cores} threads, {dt:.2f} s"}
+
+
 def split_chunks(msg: np.ndarray, n_chunks: int):
     data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
     offs = msg[32:32 + 4 * (n_chunks + 1)].view(np.uint32).astype(np.int64)
@@ -488,6 +520,10 @@ def bypass_leg(rans, dev, args, hbm):
           and torch.equal(rout, torch.where(has, raw, torch.zeros_like(raw))))
     n_raw = int(has.sum().item())
     dec_ms = statistics.median(_events(torch, dec, 10))
+    orc = _oracle()
+    cpu = oracle_leg_baseline(
+        lambda ch: orc.decode_chunk_bypass(ch, CS, freq, flags, N=N),
+        host_chunks(msg, n // CS, 16 * host_cores()), CS, unit_bytes=False)
     alg = msg_size + n + 2 * n   # message read, symbols and one raw word slot per symbol written
     return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, symbols >= "
                         f"{cfg['raw_from']} followed by a raw 16-bit word ({n_raw} raw words), "
@@ -495,7 +531,7 @@ def bypass_leg(rans, dev, args, hbm):
             "decode_gsym_s": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
             "decoded_gbs": (n + 2 * n_raw) / (dec_ms * 1e-3) / 1e9,
             "encode_gsym_s": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
-            "message_bytes": msg_size, "bit_exact_roundtrip": bool(ok),
+            "message_bytes": msg_size, "bit_exact_roundtrip": bool(ok), "cpu_baseline": cpu,
             "roofline": {"kernel": "decode_kernel (bypass)", "bound": "hbm",
                          "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
@@ -534,8 +570,11 @@ def bytes_leg(rans, dev, args, hbm):
     ok = int(dst.item()) == 0 and torch.equal(out, sym)
     dec_ms = statistics.median(_events(torch, dec, 10))
     alg = msg_size + n
+    orc = _oracle()
+    cpu = oracle_leg_baseline(lambda ch: orc.decode_chunk_bytes(ch, CS, freq, N=N),
+                              host_chunks(msg, n // CS, 16 * host_cores()), CS)
     return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, {n // CS} "
-                        f"chunks x {CS}, N = {N}, byte-wise (L = 2^23, b = 2^8)",
+                        f"chunks x {CS}, N = {N}, byte-wise (L = 2^23, b = 2^8)", "cpu_baseline": cpu,
             "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
             "encode_gbs": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
             "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok),
@@ -580,7 +619,11 @@ def adaptive_leg(rans, dev, args, hbm):
     ok = int(dst.item()) == 0 and torch.equal(out, sym)
     dec_ms = statistics.median(_events(torch, dec, 10))
     alg = msg_size + n
-    return {"workload": f"{n} bits, P(0) ~ U[{cfg['p0_lo']}, {cfg['p0_hi']}] per run of "
+    orc = _oracle()
+    cpu = oracle_leg_baseline(lambda ch: orc.decode_chunk_adaptive(ch, CS, N=N),
+                              host_chunks(msg, n // CS, 16 * host_cores()), CS, unit_bytes=False)
+    return {"cpu_baseline": cpu,
+            "workload": f"{n} bits, P(0) ~ U[{cfg['p0_lo']}, {cfg['p0_hi']}] per run of "
                         f"{cfg['segment']}, {n // CS} chunks x {CS}, N = {N}, one adaptive "
                         f"context per coder (rate 1/32)",
             "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
@@ -627,12 +670,15 @@ def prefix_leg(rans, dev, args, hbm):
     dec_ms = statistics.median(_events(torch, dec, 10))
     alg = msg_size + n
     mean_len = float((p * ln[: p.size]).sum())
+    orc = _oracle()
+    cpu = oracle_leg_baseline(lambda ch: orc.decode_chunk_prefix(ch, CS, ln, N=N),
+                              host_chunks(msg, n // CS, 16 * host_cores()), CS)
     return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, {n // CS} "
                         f"chunks x {CS}, N = {N} prefix coders (lengths <= 12, mean "
                         f"{mean_len:.3f} bits), words in the decoders' read order",
             "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
             "encode_gbs": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
-            "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok),
+            "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok), "cpu_baseline": cpu,
             "roofline": {"kernel": "decode_kernel (prefix)", "bound": "hbm",
                          "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
