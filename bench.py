@@ -487,7 +487,7 @@ def bypass_leg(rans, dev, args, hbm):
     import torch
 
     cfg = wl.WORKLOADS["bypass"]
-    n, N, CS = cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
     p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
     freq = rans.rans_quantize_table(wl.weights_from_probs(p))
     flags = (np.arange(cfg["alphabet"]) >= cfg["raw_from"]).astype(np.uint8)
