@@ -558,6 +558,25 @@ int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_symbols,
  */
 int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream);
 
+/*
+ * Checked builds (a test build compiled with -DRANS_CHECKED; the library
+ * built normally answers RANS_ERR_INVALID_ARG to both calls).  The kernels
+ * then test their invariants as they run and count the ones that fail (the
+ * access a failed check guards is skipped):
+ *   - decoder: before each group of steps, every byte the group can read lies
+ *     in ring segments whose copies have completed and that no later copy has
+ *     taken over (the ring's ordering, i.e. no read of stale or in-flight data);
+ *   - encoder: the staged words fit the chunk's slot and every bulk store
+ *     lands inside it; the prefix encoder stores only to positions its
+ *     decoder's reads were given, inside the slot.
+ * rans_debug_checks: host.  Waits for the device, then stores the number of
+ *   failed checks since the last call in *failures and clears the counters.
+ * rans_debug_check_selftest: enqueues a kernel whose one check fails on
+ *   purpose (the next rans_debug_checks then reports at least one).
+ */
+int rans_debug_checks(uint64_t *failures);
+int rans_debug_check_selftest(rans_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ _BINDING = frozenset({
     "encode_adaptive", "decode_adaptive", "rans_prefix_lengths", "rans_prefix_codes",
     "rans_max_encoded_size_prefix", "rans_encode_scratch_size_prefix", "rans_encode_prefix",
     "rans_decode_prefix", "encode_prefix", "decode_prefix", "rans_encode_host_work_size",
-    "rans_encode_host", "encode_host",
+    "rans_encode_host", "encode_host", "rans_debug_checks", "rans_debug_check_selftest",
 })
 
 

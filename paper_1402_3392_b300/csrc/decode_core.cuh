@@ -49,6 +49,7 @@ struct Geometry {
     static constexpr uint32_t kNSeg = NSEG;
     static constexpr uint32_t kRing = SEG * NSEG;
     static constexpr uint32_t kGroup = GROUP;
+    static constexpr uint32_t kStep = STEP;
     static constexpr uint32_t kLag = NSEG - 1 - (GROUP * STEP + SEG - 1) / SEG;
     static_assert((kRing & (kRing - 1)) == 0, "the ring is indexed by masking");
     static_assert(NSEG - 1 >= (GROUP * STEP + SEG - 1) / SEG + 1, "a copy must be issued ahead of use");
@@ -434,6 +435,21 @@ __device__ __forceinline__ void chain_service(Chain &c, ChainRing &r, uint32_t &
     while (c.rp >= c.next_evt) chain_event<G>(c, r, timeouts, lane);
 }
 
+// The ring's invariant, checked in checked builds after each service: every
+// byte the next `bytes` of reads can touch (up to the chunk's end) lies in a
+// segment whose copy has been waited for (after events 0..evt-1: segments
+// below evt - LAG) and whose ring slot no later copy has taken (segment j's
+// slot goes to segment j + NSEG, issued once j + NSEG < min(evt, nseg)).
+template <class G>
+__device__ __forceinline__ bool ring_window_ok(const Chain &c, uint32_t bytes) {
+    const uint32_t hi = min(c.rp + bytes, c.endrel);
+    if (hi <= c.rp || c.st != RANS_OK) return true;
+    const uint32_t first = c.rp / G::kSeg, last = (hi - 1) / G::kSeg;
+    const bool not_overwritten = first + G::kNSeg >= min(c.evt, c.nseg);
+    const bool complete = c.evt >= G::kLag && last < c.evt - G::kLag;
+    return not_overwritten && complete;
+}
+
 // Decode one step of a chunk: every active lane decodes one symbol and reads
 // at most one word.  FULL: every lane of the warp is a coder with a symbol in
 // this step.  rp is the byte position in the word stream (warp-uniform);
@@ -616,6 +632,7 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
     constexpr bool RAW = KIND == kKindRaw;
     for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
         chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kGroup * G::kStep));
 #pragma unroll
         for (uint32_t u = 0; u < G::kGroup; ++u)
             kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp + u * N,
@@ -625,6 +642,7 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
     }
     for (uint32_t t = c.steps % G::kGroup; t > 0; --t) {
         chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kStep));
         kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp, c.rawp, lt);
         c.outp += N;
         if (RAW) c.rawp += N;
@@ -632,6 +650,7 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
     c.steps = 0;
     if (c.rem) {
         chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kStep));
         kind_step<false, G::kRing, KIND>(c, lane < c.rem, tab_s, r.ring_s, flags_s, c.outp,
                                          c.rawp, lt);
         c.rem = 0;
@@ -773,6 +792,8 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
         for (uint32_t g = groups; g > 0; --g) {
             chain_service<G>(a, w.r[0], w.timeouts, lane);
             chain_service<G>(b, w.r[1], w.timeouts, lane);
+            RANS_CHECK(w.timeouts || (ring_window_ok<G>(a, G::kGroup * G::kStep) &&
+                                      ring_window_ok<G>(b, G::kGroup * G::kStep)));
 #pragma unroll
             for (uint32_t u = 0; u < G::kGroup; ++u)
                 decode_step2<kFullWarp, G::kRing>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x,

@@ -45,6 +45,29 @@ __device__ __forceinline__ void report(uint32_t *status, uint32_t code) {
     atomicCAS(status, 0u, code);
 }
 
+// ---- checked builds ---------------------------------------------------------
+// Compiled with -DRANS_CHECKED (a test build), RANS_CHECK(cond) counts a failed
+// invariant in this translation unit's counter and yields cond, so that an
+// access it guards is skipped; in normal builds it is `true` and cond is not
+// evaluated.  take_check_failures() (host) reads and clears the counter.
+#ifdef RANS_CHECKED
+static __device__ unsigned long long g_check_failures;
+__device__ __forceinline__ bool check_ok(bool ok) {
+    if (!ok) atomicAdd(&g_check_failures, 1ull);
+    return ok;
+}
+#define RANS_CHECK(cond) (::rans::check_ok(cond))
+static inline uint64_t take_check_failures() {
+    unsigned long long v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_failures, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_check_failures, &zero, sizeof zero) != cudaSuccess)
+        return ~0ull;
+    return v;
+}
+#else
+#define RANS_CHECK(cond) true
+#endif
+
 // ---- mbarrier ---------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");

@@ -365,6 +365,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     // held segments at least five newer stores back.  wp and flushed are
     // warp-uniform; only lane 0 issues and waits.
     auto service = [&]() {
+        // Checked builds: the words so far fit the slot (wp has not wrapped).
+        RANS_CHECK(wp <= slot_bytes);
         const uint32_t done = (wp + kSeg - 1) / kSeg;
         if (flushed > done) {
             fence_proxy_async_smem();
@@ -372,7 +374,9 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             if (lane == 0) {
                 for (uint32_t sg = flushed; sg > done;) {
                     --sg;
-                    bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
+                    if (RANS_CHECK(uint64_t(sg + 1) * kSeg <= slot_bytes))
+                        bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg,
+                                 kSeg);
                     bulk_commit();
                 }
                 bulk_wait_read<5>();
@@ -493,10 +497,12 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         const uint32_t done = (wp + kSeg - 1) / kSeg;
         for (uint32_t sg = flushed; sg > done;) {
             --sg;
-            bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
+            if (RANS_CHECK(uint64_t(sg + 1) * kSeg <= slot_bytes))
+                bulk_s2g(slot_base + uint64_t(sg) * kSeg, ring_s + (sg % kNSeg) * kSeg, kSeg);
         }
         const uint32_t lo = wp & ~15u, hi = done * kSeg;
-        if (lo < hi) bulk_s2g(slot_base + lo, ring_s + (lo & (kRing - 1)), hi - lo);
+        if (lo < hi && RANS_CHECK(wp <= slot_bytes && hi <= slot_bytes))
+            bulk_s2g(slot_base + lo, ring_s + (lo & (kRing - 1)), hi - lo);
         bulk_commit();
         bulk_wait_read<0>();
         *wstart = wp;

@@ -533,3 +533,8 @@ extern "C" int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n
     enc_pack_kernel<<<16 * sms, kEncPackThreads, 0, st>>>(p);
     return check_launch();
 }
+
+#ifdef RANS_CHECKED
+// Checked builds: failed invariants of this file's kernels since the last call.
+uint64_t rans_check_failures_batch() { return rans::take_check_failures(); }
+#endif

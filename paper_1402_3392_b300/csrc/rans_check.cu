@@ -23,10 +23,30 @@ __global__ void __launch_bounds__(32) bounded_wait_kernel(uint32_t *status) {
     if (threadIdx.x == 0) *status = st;
 }
 
+// Checked builds: one invariant that fails on purpose, so a test can see the
+// counters work.
+__global__ void check_selftest_kernel() {
+    if (threadIdx.x == 0) RANS_CHECK(false);
+}
+
 }  // namespace
 }  // namespace rans
 
 using namespace rans;
+
+#ifdef RANS_CHECKED
+uint64_t rans_check_failures_check() { return take_check_failures(); }
+#endif
+
+extern "C" int rans_debug_check_selftest(rans_stream_t stream) {
+#ifdef RANS_CHECKED
+    check_selftest_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>();
+    return check_launch();
+#else
+    (void)stream;
+    return RANS_ERR_INVALID_ARG;
+#endif
+}
 
 extern "C" int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream) {
     if (!d_status) return RANS_ERR_INVALID_ARG;

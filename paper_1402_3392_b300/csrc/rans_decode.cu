@@ -367,3 +367,8 @@ extern "C" int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const u
         return RANS_ERR_CUDA;
     return RANS_OK;
 }
+
+#ifdef RANS_CHECKED
+// Checked builds: failed invariants of this file's kernels since the last call.
+uint64_t rans_check_failures_decode() { return rans::take_check_failures(); }
+#endif

@@ -634,3 +634,8 @@ extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
     }
     return RANS_OK;
 }
+
+#ifdef RANS_CHECKED
+// Checked builds: failed invariants of this file's kernels since the last call.
+uint64_t rans_check_failures_encode() { return rans::take_check_failures(); }
+#endif

@@ -243,3 +243,33 @@ extern "C" uint64_t rans_max_encoded_size_prefix(uint64_t n_symbols, const rans_
     return g.data0 + round16(4ull * ((n_symbols * RANS_PREFIX_MAX_LEN + 31) / 32 +
                                      g.n_chunks * (2ull * params->n_lanes + 1)));
 }
+
+// Checked builds (-DRANS_CHECKED): the failed invariants of all kernels since
+// the last call, summed over the files that define kernels.
+#ifdef RANS_CHECKED
+uint64_t rans_check_failures_decode();
+uint64_t rans_check_failures_encode();
+uint64_t rans_check_failures_batch();
+uint64_t rans_check_failures_prefix();
+uint64_t rans_check_failures_check();
+#endif
+
+extern "C" int rans_debug_checks(uint64_t *failures) {
+#ifdef RANS_CHECKED
+    if (!failures) return RANS_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return RANS_ERR_CUDA;
+    const uint64_t parts[] = {rans_check_failures_decode(), rans_check_failures_encode(),
+                              rans_check_failures_batch(), rans_check_failures_prefix(),
+                              rans_check_failures_check()};
+    uint64_t sum = 0;
+    for (uint64_t v : parts) {
+        if (v == ~0ull) return RANS_ERR_CUDA;
+        sum += v;
+    }
+    *failures = sum;
+    return RANS_OK;
+#else
+    (void)failures;
+    return RANS_ERR_INVALID_ARG;
+#endif
+}

@@ -48,10 +48,11 @@ struct PfxLane {
 
 // One step: the decoder's read (if it holds fewer than 12 bits), then the
 // symbol's code appended; a completed word goes to the oldest waiting read.
+// (slot_words: the slot's capacity, for the checks of checked builds.)
 template <bool FULL>
 __device__ __forceinline__ void prefix_enc_step(PfxLane &c, bool active, uint32_t s,
                                                 const uint32_t *tab, uint32_t *slot, uint32_t &wpos,
-                                                uint32_t &err, uint32_t lt) {
+                                                uint32_t &err, uint32_t lt, uint32_t slot_words) {
     const bool on = FULL || active;
     const bool need = on && c.held < kPfxMaxLen;
     const uint32_t m = __ballot_sync(kFull, need);
@@ -71,7 +72,7 @@ __device__ __forceinline__ void prefix_enc_step(PfxLane &c, bool active, uint32_
         c.held -= len;
         if (c.na >= 32) {
             c.na -= 32;
-            slot[c.q0] = uint32_t(c.acc >> c.na);
+            if (RANS_CHECK(c.q0 < slot_words)) slot[c.q0] = uint32_t(c.acc >> c.na);
             c.q0 = c.q1;
             c.q1 = kNoPos;
         }
@@ -82,9 +83,9 @@ __device__ __forceinline__ void prefix_enc_step(PfxLane &c, bool active, uint32_
 // the chunk's byte size to *size.
 template <int NT>
 __device__ __forceinline__ void prefix_encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
-                                                    uint32_t *slot, uint32_t *size,
-                                                    const uint32_t *tab, uint32_t lane, uint32_t lt,
-                                                    uint32_t &err) {
+                                                    uint32_t *slot, uint32_t slot_words,
+                                                    uint32_t *size, const uint32_t *tab,
+                                                    uint32_t lane, uint32_t lt, uint32_t &err) {
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;
     const uint32_t T = n_c / N, rem = n_c % N, G = T / kPfxGroup;
@@ -104,28 +105,29 @@ __device__ __forceinline__ void prefix_encode_chunk(const uint8_t *sym, uint32_t
         for (uint32_t u = 0; u < kPfxGroup; ++u) nxt[u] = more ? sp[(base + u) * N] : 0u;
 #pragma unroll
         for (uint32_t u = 0; u < kPfxGroup; ++u)
-            prefix_enc_step<NT == 32>(c, lane_on, cur[u], tab, slot, wpos, err, lt);
+            prefix_enc_step<NT == 32>(c, lane_on, cur[u], tab, slot, wpos, err, lt, slot_words);
 #pragma unroll
         for (uint32_t u = 0; u < kPfxGroup; ++u) cur[u] = nxt[u];
     }
     for (uint32_t t = G * kPfxGroup; t < T; ++t) {
         const uint32_t s = lane_on ? sp[uint64_t(t) * N] : 0u;
-        prefix_enc_step<NT == 32>(c, lane_on, s, tab, slot, wpos, err, lt);
+        prefix_enc_step<NT == 32>(c, lane_on, s, tab, slot, wpos, err, lt, slot_words);
     }
     if (rem) {
         const bool act = lane < rem;
         const uint32_t s = act ? sp[uint64_t(T) * N] : 0u;
-        prefix_enc_step<false>(c, act, s, tab, slot, wpos, err, lt);
+        prefix_enc_step<false>(c, act, s, tab, slot, wpos, err, lt, slot_words);
     }
     // Flush: the last bits padded with zeros, then zero words for the reads
     // the decoder makes beyond them (at most one).
     if (c.na) {
-        slot[c.q0] = uint32_t(c.acc << (32 - c.na));
+        if (RANS_CHECK(c.q0 < slot_words)) slot[c.q0] = uint32_t(c.acc << (32 - c.na));
         c.q0 = c.q1;
         c.q1 = kNoPos;
     }
-    if (c.q0 != kNoPos) slot[c.q0] = 0u;
-    if (c.q1 != kNoPos) slot[c.q1] = 0u;
+    if (c.q0 != kNoPos && RANS_CHECK(c.q0 < slot_words)) slot[c.q0] = 0u;
+    if (c.q1 != kNoPos && RANS_CHECK(c.q1 < slot_words)) slot[c.q1] = 0u;
+    RANS_CHECK(wpos <= slot_words);
     if (lane == 0) *size = 4u * wpos;
 }
 
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kPfxWarps * 32)
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
         prefix_encode_chunk<NT>(p.sym + first, n_c, p.N,
                                 reinterpret_cast<uint32_t *>(p.slots + uint64_t(c) * p.slot_bytes),
-                                p.sizes + c, tab, lane, lt, err);
+                                p.slot_bytes / 4, p.sizes + c, tab, lane, lt, err);
     }
     if (__any_sync(kFull, err) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
 }
@@ -280,3 +282,8 @@ extern "C" int rans_encode_prefix(const uint8_t *d_symbols, uint64_t n_symbols,
     }
     return RANS_OK;
 }
+
+#ifdef RANS_CHECKED
+// Checked builds: failed invariants of this file's kernels since the last call.
+uint64_t rans_check_failures_prefix() { return rans::take_check_failures(); }
+#endif

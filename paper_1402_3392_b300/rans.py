@@ -75,6 +75,10 @@ class RansParams(C.Structure):
 
 
 def library_path() -> str:
+    """The CUDA library to load: the normal build, or with
+    RANS_LIB_VARIANT=checked the checked test build (rans_debug_checks)."""
+    if os.environ.get("RANS_LIB_VARIANT") == "checked":
+        return _build.LIB_PATH_CHECKED
     return _build.LIB_PATH
 
 
@@ -97,6 +101,8 @@ def _load() -> C.CDLL:
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
         "rans_check_bounded_wait": (i32, [vp, vp]),
+        "rans_debug_checks": (i32, [vp]),
+        "rans_debug_check_selftest": (i32, [vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
         "rans_max_encoded_size_bypass": (u64, [u64, pp]),
         "rans_encode_scratch_size_bypass": (u64, [u64, pp]),
@@ -599,6 +605,18 @@ def encode_host(symbols, freq, n_lanes: int = 32, chunk_symbols: int = 65536, de
     else:
         torch.cuda.current_stream(device).synchronize()
     return out[: int(size.item())], int(status.item())
+
+
+def rans_debug_checks() -> int:
+    """Checked builds: failed kernel invariants since the last call (the
+    counters are cleared); RansError(RANS_ERR_INVALID_ARG) otherwise."""
+    v = C.c_uint64(0)
+    _check(lib.rans_debug_checks(C.byref(v)), "rans_debug_checks")
+    return int(v.value)
+
+
+def rans_debug_check_selftest(stream=None) -> int:
+    return _check(lib.rans_debug_check_selftest(_stream(stream)), "rans_debug_check_selftest")
 
 
 def rans_check_bounded_wait(d_status, stream=None, check=True) -> int:
