@@ -98,3 +98,43 @@ def test_damaged_messages_agree_with_oracle(rlib, orc, cuda, kind, how):
             assert st == rlib.RANS_OK, (kind, how)
             assert np.array_equal(out.cpu().numpy(), want), (kind, how)
     assert accepted < 12          # the damage was seen at least once
+
+
+def _gpu_status(torch, gpu, bad, cuda):
+    out, st = gpu(torch.from_numpy(bad).to(cuda))
+    torch.cuda.synchronize()
+    return out, int(st.item())
+
+
+@pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix"])
+def test_truncated_messages_agree_with_oracle(rlib, orc, cuda, kind):
+    """Messages cut short: by whole 16-byte blocks (the size no longer matches
+    the offset table: both reject); cut with the offset table's last entry
+    set to the shorter data region (the last chunk loses its tail: the
+    verdicts agree); cut to a size that is not a multiple of 16 bytes, or
+    into the header (an argument error before anything runs)."""
+    rng = np.random.default_rng(zlib.crc32(repr(("trunc", kind)).encode()))
+    m, ref, gpu, torch = message(rlib, orc, kind, rng)
+    n_chunks = -(-N_SYM // CS)
+    data0 = (32 + 4 * (n_chunks + 1) + 15) // 16 * 16
+    for cut in (16, 48, 160):
+        bad = m[:m.size - cut].copy()
+        with pytest.raises(oracle.OracleError):
+            ref(bad)
+        assert _gpu_status(torch, gpu, bad, cuda)[1] == rlib.RANS_ERR_CORRUPT, cut
+        fixed = bad.copy()
+        offs = fixed[32:32 + 4 * (n_chunks + 1)].view(np.uint32)
+        offs[n_chunks] = np.uint32(fixed.size - data0)
+        try:
+            want = ref(fixed)
+        except oracle.OracleError:
+            want = None
+        out, st = _gpu_status(torch, gpu, fixed, cuda)
+        if want is None:
+            assert st == rlib.RANS_ERR_CORRUPT, cut
+        else:
+            assert st == rlib.RANS_OK and np.array_equal(out.cpu().numpy(), want), cut
+    for size in (m.size - 1, m.size - 7, data0 - 16, 16):
+        with pytest.raises(rlib.RansError) as e:
+            gpu(torch.from_numpy(m[:size].copy()).to(cuda))
+        assert e.value.code == rlib.RANS_ERR_INVALID_ARG, size
