@@ -87,8 +87,13 @@ constexpr uint32_t kL8 = 1u << 23;
 constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3, kKindPrefix = 4;
 // Prefix messages: longest code, also the bit count below which a coder's
 // decoder reads its next 32-bit word; entries of the 4096-entry code table
-// are len << 8 | symbol (0: no code starts with these 12 bits).
+// are len << 8 | symbol.  Bits that start no code get length 63: a coder
+// holds at most 43 bits, so using such an entry wraps its bit count, which
+// then never comes back to 43 or below (refills stop) and the chunk's end
+// check rejects it.
 constexpr uint32_t kPrefixMaxLen = 12;
+constexpr uint32_t kPrefixMaxHeld = 43;
+constexpr uint32_t kPrefixNoCode = 63u << 8;
 // Adaptive contexts: p = probability of a 0 scaled to M, from M/2, moving by
 // (target - p) >> kAdaptRate after every symbol.
 constexpr uint32_t kAdaptRate = 5;
@@ -250,12 +255,13 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
 
 // The 4096-entry decode table of a canonical prefix code, with the whole CTA:
 // the entries whose top len bits are symbol s's code hold len << 8 | s, the
-// rest 0.  len[s] = 0: s not in the code.
+// rest kPrefixNoCode.  len[s] = 0: s not in the code.
 __device__ __noinline__ static void build_prefix_table(const uint8_t *len, const uint16_t *code,
                                                        uint32_t *tab) {
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < kM / 4; i += kThreads)
-        reinterpret_cast<uint4 *>(tab)[i] = make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<uint4 *>(tab)[i] =
+            make_uint4(kPrefixNoCode, kPrefixNoCode, kPrefixNoCode, kPrefixNoCode);
     __syncthreads();
     for (uint32_t s = tid; s < RANS_MAX_ALPHABET; s += kThreads) {
         const uint32_t l = len[s];
@@ -321,8 +327,7 @@ struct Chain {
     uint32_t rp0;        // byte-wise messages: rp at the first digit
     uint32_t len;        // byte-wise messages: chunk bytes (states, digits, padding)
     uint32_t bhi, blo;   // prefix messages: this lane's bits, right-aligned in bhi:blo
-    uint32_t nb;         // prefix messages: bits held (at most 43)
-    uint32_t emin;       // prefix messages: smallest table entry used (< 256: no code)
+    uint32_t nb;         // prefix messages: bits held (at most 43 unless a code was missing)
 };
 
 __device__ __forceinline__ void chain_empty(Chain &c) {
@@ -336,7 +341,6 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.rp0 = c.len = 0;
     c.p = kAdaptP0;
     c.bhi = c.blo = c.nb = 0;
-    c.emin = 0xFFFFFFFFu;
 }
 
 // Open a prefix-message chunk [o, e): no states, its 32-bit words start at
@@ -603,7 +607,6 @@ __device__ __forceinline__ void decode_step_prefix(Chain &c, bool active, uint32
         const uint32_t e = ld_table(imad(idx, 4u, tab_s));
         *outp = uint8_t(e);
         c.nb -= e >> 8;
-        c.emin = min(c.emin, e);
     }
 }
 
@@ -660,8 +663,8 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
 // Byte-wise chunks end in zero padding up to a multiple of 4 bytes: the chunk
 // must be exactly round4(4N + digits read) long, with zeros after the digits
 // (src + rp .. src + endrel, at most 3 bytes).
-// Prefix chunks end with every word read, every coder's leftover bits zero
-// and no table miss.
+// Prefix chunks end with every word read and every coder holding at most 43
+// bits (no missing code was met), all of them zero.
 template <class G, bool BYTES = false, bool PREFIX = false>
 __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t &timeouts,
                                                 bool lane_on, uint32_t N = 0) {
@@ -672,7 +675,8 @@ __device__ __forceinline__ uint32_t chain_close(Chain &c, ChainRing &r, uint32_t
     if (timeouts) return RANS_ERR_TIMEOUT;
     if (PREFIX) {
         const uint64_t bits = (uint64_t(c.bhi) << 32) | c.blo;
-        const bool clean = (bits & ((uint64_t(1) << c.nb) - 1)) == 0 && c.emin >= 256u;
+        const bool clean =
+            c.nb <= kPrefixMaxHeld && (bits & ((uint64_t(1) << c.nb) - 1)) == 0;
         const bool ok = __all_sync(kFull, !lane_on || clean) && c.rp == c.endrel;
         return ok ? RANS_OK : RANS_ERR_CORRUPT;
     }
