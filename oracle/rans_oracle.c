@@ -684,6 +684,7 @@ uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out,
 #define ORC_L (1ull << 16)
 #define ORC_B (1ull << 16)
 #define ORC_LOG2_M 12u
+#define ORC_LOG2_M_MAX 14u     /* plain messages: M = 2^12, 2^13 or 2^14 */
 
 static void put_u32(uint8_t *p, uint32_t v)
 {
@@ -703,6 +704,21 @@ static int prod_table(const uint16_t *freq, uint32_t n_alpha, uint64_t *f64)
     uint64_t sum = 0;
     for (uint32_t s = 0; s < n_alpha; ++s) { f64[s] = freq[s]; sum += freq[s]; }
     return sum == (1ull << ORC_LOG2_M) ? ORC_OK : ORC_ERR_ARG;
+}
+
+/* Plain messages may also use M = 2^13 or 2^14 (Section 5: with b = 2^16 a
+ * coder in 32-bit integers keeps one renormalization per symbol at 12-14
+ * bits of probability resolution, since b >= M); M is the table's sum and
+ * the header records log2(M).  Other kinds keep M = 2^12. */
+static int plain_table(const uint16_t *freq, uint32_t n_alpha, uint64_t *f64, int wide_ok,
+                       uint32_t *log2_m)
+{
+    if (n_alpha == 0 || n_alpha > 256) return ORC_ERR_ARG;
+    uint64_t sum = 0;
+    for (uint32_t s = 0; s < n_alpha; ++s) { f64[s] = freq[s]; sum += freq[s]; }
+    for (uint32_t lm = ORC_LOG2_M; lm <= (wide_ok ? ORC_LOG2_M_MAX : ORC_LOG2_M); ++lm)
+        if (sum == (1ull << lm)) { *log2_m = lm; return ORC_OK; }
+    return ORC_ERR_ARG;
 }
 
 /* Worst case: one word per symbol, since b >= M allows at most one
@@ -741,9 +757,9 @@ static int chunk_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_c,
                         uint8_t *out, uint64_t cap, uint64_t *size)
 {
     uint64_t f64[256];
-    uint32_t r[256];
+    uint32_t r[256], lm;
     if (N == 0 || N > 32) return ORC_ERR_ARG;
-    int rc = prod_table(freq, n_alpha, f64);
+    int rc = plain_table(freq, n_alpha, f64, rawf == NULL, &lm);
     if (!rc && rawf) rc = raw_counts(rawf, n_alpha, r);
     if (rc) return rc;
     uint64_t cap_w = 3 * (n_c ? n_c : 1);
@@ -780,9 +796,9 @@ static int chunk_decode(const uint8_t *chunk, uint64_t size, const uint16_t *fre
                         uint16_t *raw_out, uint64_t n_c)
 {
     uint64_t f64[256];
-    uint32_t r[256];
+    uint32_t r[256], lm;
     if (N == 0 || N > 32) return ORC_ERR_ARG;
-    int rc = prod_table(freq, n_alpha, f64);
+    int rc = plain_table(freq, n_alpha, f64, rawf == NULL, &lm);
     if (!rc && rawf) rc = raw_counts(rawf, n_alpha, r);
     if (rc) return rc;
     if (size < 4ull * N || ((size - 4ull * N) & 1)) return ORC_ERR_CORRUPT;
@@ -1001,7 +1017,13 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
     put_u32(out + 4, bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
                      : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
     put_u32(out + 8, N);
-    put_u32(out + 12, ORC_LOG2_M);
+    uint32_t lm = ORC_LOG2_M;
+    if (bytes == 0 && !rawf) {
+        uint64_t f64[256];
+        int rc0 = plain_table(freq, n_alpha, f64, 1, &lm);
+        if (rc0) return rc0;
+    }
+    put_u32(out + 12, lm);
     put_u32(out + 16, (uint32_t)n_sym);
     put_u32(out + 20, (uint32_t)(n_sym >> 32));
     put_u32(out + 24, chunk_symbols);
@@ -1044,8 +1066,14 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
     uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
     uint32_t version = bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
                        : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
+    uint32_t lm = ORC_LOG2_M;
+    if (bytes == 0 && !rawf) {
+        uint64_t f64[256];
+        int rc0 = plain_table(freq, n_alpha, f64, 1, &lm);
+        if (rc0) return rc0;
+    }
     if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != version ||
-        get_u32(msg + 8) != N || get_u32(msg + 12) != ORC_LOG2_M || hdr_n != n_sym ||
+        get_u32(msg + 8) != N || get_u32(msg + 12) != lm || hdr_n != n_sym ||
         get_u32(msg + 24) != chunk_symbols || get_u32(msg + 28) != n_chunks)
         return ORC_ERR_CORRUPT;
     uint64_t data0 = round16(32 + 4 * (n_chunks + 1));

@@ -963,6 +963,46 @@ def pin_prefix_container(o):
     assert np.array_equal(o.decode_message_prefix(m, sym.size, ln, N=7, chunk_symbols=999), sym)
 
 
+def pin_wide_resolution(o):
+    """Section 5: with b = 2^16 a coder in 32-bit integers keeps one
+    renormalization per symbol at 12-14 bits of probability resolution.  For
+    M = 2^13 and 2^14 (the table's sum): no symbol needs more than one
+    renormalization, each container chunk is the generic Algorithm-1 coder's
+    stream at the production L and b, the header records log2(M), messages
+    decode back, and a table of any other sum is refused (as is a wide table
+    by the byte-wise container, which keeps M = 2^12)."""
+    rng = np.random.default_rng(67)
+    for lm in (13, 14):
+        for alpha in (2, 40, 256):
+            w = rng.integers(1, 1 << 20, size=alpha).astype(np.uint64)
+            freq = o.quantize(w, lm)
+            assert int(freq.astype(np.int64).sum()) == 1 << lm
+            sym = rng.integers(0, alpha, size=3000).astype(np.uint8)   # rare symbols too
+            for N in (1, 7, 32):
+                enc = o.encode(freq.astype(np.uint64), sym, N=N)
+                assert enc["max_iters"] <= 1
+                ref = np.concatenate([enc["states"].astype("<u4").view(np.uint8),
+                                      enc["words"].astype("<u2").view(np.uint8)])
+                assert np.array_equal(o.encode_chunk(sym, freq, N=N), ref), (lm, alpha, N)
+            m = o.encode_message(sym, freq, N=7, chunk_symbols=999)
+            assert int.from_bytes(m[12:16].tobytes(), "little") == lm
+            assert np.array_equal(o.decode_message(m, sym.size, freq, N=7, chunk_symbols=999), sym)
+    sym = rng.integers(0, 256, size=100).astype(np.uint8)
+    for bad in (np.full(256, 128, dtype=np.uint16),                 # sum 2^15
+                np.full(256, 24, dtype=np.uint16)):                 # sum 6144
+        try:
+            o.encode_message(sym, bad, N=32, chunk_symbols=64)
+            raise AssertionError("a table of sum %d was accepted" % int(bad.sum()))
+        except oracle.OracleError:
+            pass
+    wide = o.quantize(np.ones(256, dtype=np.uint64), 14)
+    try:
+        o.encode_message_bytes(sym, wide, N=32, chunk_symbols=64)
+        raise AssertionError("the byte-wise container took M = 2^14")
+    except oracle.OracleError:
+        pass
+
+
 ALL_PINS = [
     pin_paper_C_D, pin_paper_precursor_sets, pin_paper_state_30, pin_paper_lockstep,
     pin_lockstep_interleaved, pin_inverse_exhaustive, pin_precursor_rans_b_unique,
@@ -975,5 +1015,5 @@ ALL_PINS = [
     pin_adaptive_brute_force, pin_adaptive_size_and_learning, pin_adaptive_container,
     pin_mux_rans_is_section3_interleaving, pin_prefix_codes_rfc1951, pin_prefix_lengths_optimal,
     pin_prefix_mux_lane_streams, pin_prefix_mux_brute_force, pin_mux_coroutine_and_flush,
-    pin_prefix_container,
+    pin_prefix_container, pin_wide_resolution,
 ]
