@@ -76,6 +76,7 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_M             4096u
 #define RANS_L             65536u      /* I = [2^16, 2^32) */
 #define RANS_LOG2_B        16
+#define RANS_LOG2_M_MAX    14          /* plain messages: M = 2^12, 2^13 or 2^14 */
 #define RANS_MAX_ALPHABET  256
 #define RANS_MAX_LANES     32
 #define RANS_MAGIC         0x534E4152u

@@ -76,7 +76,8 @@ constexpr uint32_t kTableBytes = kM * 4;
 constexpr uint32_t kBarOffset = kTableBytes + kWarpRing + kWarps * kWarpRing;
 constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
 constexpr uint32_t kFlagsOffset = kMiscOffset + 64;   // 256 raw-word flags (bypass)
-constexpr uint32_t kSmemBytes = kFlagsOffset + 256;
+constexpr uint32_t kFbOffset = kFlagsOffset + 256;    // 256 words B << 16 | f (wide models)
+constexpr uint32_t kSmemBytes = kFbOffset + 1024;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 // Byte-wise messages (version 3): L = 2^23, b = 2^8, I = [2^23, 2^31).
 constexpr uint32_t kL8 = 1u << 23;
@@ -85,6 +86,15 @@ constexpr uint32_t kL8 = 1u << 23;
 // one adaptive context per coder), prefix (5: canonical prefix codes muxed in
 // their decoder's read order, Section 4).
 constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3, kKindPrefix = 4;
+// Plain messages at 13 or 14 bits of probability resolution (M = 2^13 or
+// 2^14, b = 2^16 >= M: still one renormalization per symbol, Section 5).
+// Their model takes a slot -> symbol byte table (M bytes, in the table area)
+// and a symbol -> (B_s << 16 | f_s) table of 256 words.
+constexpr int kKindWide13 = 5, kKindWide14 = 6;
+template <int KIND>
+struct WideBits {
+    static constexpr uint32_t kLog2 = KIND == kKindWide13 ? 13u : 14u;
+};
 // Prefix messages: longest code, also the bit count below which a coder's
 // decoder reads its next 32-bit word; entries of the 4096-entry code table
 // are len << 8 | symbol.  Bits that start no code get length 63: a coder
@@ -108,6 +118,8 @@ struct Smem {
     uint32_t *misc;     // CTA-shared words
     uint8_t *flags;     // raw words per symbol (0 or 1), bypass messages
     uint32_t flags_s;
+    uint32_t *fb;       // wide models: B_s << 16 | f_s per symbol
+    uint32_t fb_s;
 };
 
 __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
@@ -121,6 +133,8 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
     s.flags = smem + kFlagsOffset;
     s.flags_s = smem_addr(smem + kFlagsOffset);
+    s.fb = reinterpret_cast<uint32_t *>(smem + kFbOffset);
+    s.fb_s = smem_addr(smem + kFbOffset);
     return s;
 }
 
@@ -248,6 +262,82 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
         const uint32_t slot = base + i;
         const uint32_t f = cum[s + 1] - cum[s];
         tab[slot] = (f << 20) | ((slot - cum[s]) << 8) | s;
+    }
+    __syncthreads();
+    return total;
+}
+
+// The tables of a wide model (M = 2^lm, lm 13 or 14) from 256 frequencies,
+// with the whole CTA: fb[s] = B_s << 16 | f_s, and the slot -> symbol byte
+// table sym[0..M) (sym(slot) = the s with B_s <= slot < B_s + f_s).  As for
+// the slot table: cum by a warp scan, each symbol's first slot marked with
+// its index, then a running maximum over the slots (symbols lie in
+// increasing order), each thread over M/256 consecutive slots after an
+// exclusive max-scan of the threads' maxima.  scratch: >= 1.1 KiB of free
+// shared memory.  Returns the frequencies' sum; *const_sym: the symbol with
+// f = M, or kNoConst.
+__device__ __noinline__ static uint32_t build_wide_table(const uint16_t *freq, uint32_t lm,
+                                                         uint8_t *sym, uint32_t *fb,
+                                                         uint8_t *scratch, uint32_t *const_sym) {
+    uint32_t *cum = reinterpret_cast<uint32_t *>(scratch);        // 257 words
+    uint32_t *part = reinterpret_cast<uint32_t *>(scratch + 1040);  // 8 words
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = 1u << lm;
+    uint32_t *sym32 = reinterpret_cast<uint32_t *>(sym);
+    for (uint32_t i = tid; i < M / 4; i += kThreads) sym32[i] = 0;
+    if (tid < 32) {
+        uint32_t v[8], run = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = run;
+            run += freq[tid * 8 + k];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (tid >= uint32_t(d)) incl += y;
+        }
+        const uint32_t excl = incl - run;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cum[tid * 8 + k] = excl + v[k];
+        if (tid == 31) cum[256] = incl;
+    }
+    __syncthreads();
+    const uint32_t total = cum[256];
+    if (total != M) return total;  // not a valid model: the caller reports it
+    if (tid < 256) {
+        const uint32_t a = cum[tid], f = cum[tid + 1] - a;
+        fb[tid] = (a << 16) | (f & 0xFFFFu);
+        if (f > 0) sym[a] = uint8_t(tid);
+        if (f == M) *const_sym = tid;
+    }
+    __syncthreads();
+    const uint32_t words = M / 4 / kThreads, base = tid * words;   // 8 or 16 words a thread
+    uint32_t run = 0;
+    for (uint32_t q = 0; q < words; ++q) {
+        const uint32_t w = sym32[base + q];
+        run = max(run, max(max(w & 0xFFu, (w >> 8) & 0xFFu), max((w >> 16) & 0xFFu, w >> 24)));
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= uint32_t(d)) incl = max(incl, y);
+    }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    uint32_t carry = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) carry = 0;
+    for (uint32_t w = 0; w < warp; ++w) carry = max(carry, part[w]);
+    for (uint32_t q = 0; q < words; ++q) {
+        const uint32_t w = sym32[base + q];
+        uint32_t out = 0;
+#pragma unroll
+        for (uint32_t b = 0; b < 4; ++b) {
+            carry = max(carry, (w >> (8 * b)) & 0xFFu);
+            out |= carry << (8 * b);
+        }
+        sym32[base + q] = out;
     }
     __syncthreads();
     return total;
@@ -475,6 +565,27 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
     rp = imad(__popc(m), 2u, rp);
 }
 
+// One step at 13 or 14 bits of resolution (LM): the slot's symbol from the
+// byte table, its f and B from the per-symbol table, then the plain
+// renormalization (b = 2^16 >= M: at most one word).
+template <bool FULL, uint32_t RING, uint32_t LM>
+__device__ __forceinline__ void decode_step_wide(uint32_t &x, uint32_t &rp, bool active,
+                                                 uint32_t sym_s, uint32_t fb_s, uint32_t ring_s,
+                                                 uint8_t *outp, uint32_t lt) {
+    const uint32_t slot = x & ((1u << LM) - 1);
+    const uint32_t s = ld_flag(sym_s + slot);
+    const uint32_t fb = ld_table(imad(s, 4u, fb_s));
+    if (FULL || active) {
+        x = imad(fb & 0xFFFFu, x >> LM, slot - (fb >> 16));
+        *outp = uint8_t(s);
+    }
+    const bool need = (FULL || active) && x < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
+    rp = imad(__popc(m), 2u, rp);
+}
+
 // One step of two chunks a and b, their instructions interleaved.
 template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32_t ra_s, uint8_t *oa,
@@ -623,6 +734,9 @@ __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s,
         decode_step_adaptive<FULL, RING>(c.x, c.p, c.rp, active, ring_s, outp, lt);
     else if (KIND == kKindPrefix)
         decode_step_prefix<FULL, RING>(c, active, tab_s, ring_s, outp, lt);
+    else if (KIND == kKindWide13 || KIND == kKindWide14)  // flags_s: the f/B table
+        decode_step_wide<FULL, RING, WideBits<KIND>::kLog2>(c.x, c.rp, active, tab_s, flags_s,
+                                                           ring_s, outp, lt);
     else
         decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
 }
@@ -818,10 +932,11 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
 // msg_size is the message size and data0 its data-region offset.
 __device__ __forceinline__ bool header_ok(const uint8_t *msg, uint64_t msg_size, uint32_t data0,
                                           uint64_t n_sym, uint32_t N, uint32_t CS,
-                                          uint32_t n_chunks, uint32_t version = RANS_VERSION) {
+                                          uint32_t n_chunks, uint32_t version = RANS_VERSION,
+                                          uint32_t log2m = kLog2M) {
     const uint32_t *h32 = reinterpret_cast<const uint32_t *>(msg);
     const uint64_t hn = uint64_t(h32[4]) | (uint64_t(h32[5]) << 32);
-    if (h32[0] != RANS_MAGIC || h32[1] != version || h32[2] != N || h32[3] != kLog2M ||
+    if (h32[0] != RANS_MAGIC || h32[1] != version || h32[2] != N || h32[3] != log2m ||
         hn != n_sym || h32[6] != CS || h32[7] != n_chunks)
         return false;
     const uint32_t first = h32[8], last = h32[8 + n_chunks];

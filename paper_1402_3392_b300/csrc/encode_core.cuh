@@ -39,9 +39,10 @@ constexpr uint32_t kGroup = 16;
 // A step writes at most 32 words = 64 bytes, so a group writes at most 1 KiB
 // and touches at most three segments.
 static_assert(kGroup * 64 <= 2 * kSeg, "a group must fit in two segments");
-// Shared memory: [encode table 2 KiB][alignment slack][one ring per warp][a
-// few words of CTA state].
-constexpr uint32_t kMiscOffset = 256 * 8 + kRing + kWarps * kRing;
+// Shared memory: [encode table: 256 entries of 8 bytes, or of 16 for wide
+// models][alignment slack][one ring per warp][a few words of CTA state].
+constexpr uint32_t kTabBytes = 256 * 16;
+constexpr uint32_t kMiscOffset = kTabBytes + kRing + kWarps * kRing;
 constexpr uint32_t kSmemBytes = kMiscOffset + 64;
 constexpr uint32_t kZeroFlag = 1u << 19;  // encode-table bit marking f_s = 0
 constexpr uint32_t kRawFlag = 1u << 18;   // encode-table bit: the symbol carries a raw word
@@ -85,9 +86,9 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     Smem s;
     s.tab = reinterpret_cast<uint2 *>(smem);
     s.tab_s = smem_addr(smem);
-    const uint32_t raw = smem_addr(smem + 256 * 8);
+    const uint32_t raw = smem_addr(smem + kTabBytes);
     s.rings_s = (raw + kRing - 1) & ~(kRing - 1);
-    s.rings = smem + 256 * 8 + (s.rings_s - raw);
+    s.rings = smem + kTabBytes + (s.rings_s - raw);
     s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
     return s;
 }
@@ -145,6 +146,64 @@ __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq,
     return total;
 }
 
+// Wide models (M = 2^lm, lm 13 or 14; b = 2^16 >= M, one renormalization
+// per symbol): entry s of 16 bytes, built by the whole CTA (cum: 257 words of
+// free shared memory; returns the frequencies' sum):
+//   .x = m_lo as above (exact division for every x < 2^32, f up to 2^14)
+//   .y = f * 2^(32 - lm) - 1: the emit test is x > .y   (f = M: never)
+//   .z = M - f             .w = B_s | k << 24
+// A symbol with f = 0: .y = ~0 (never emits), .x = .z = 0, .w = kZeroFlag
+// (k = 0, so q = x and x is left unchanged).
+__device__ __noinline__ static uint32_t build_wide_encode_table(const uint16_t *freq, uint32_t lm,
+                                                                uint4 *tab, uint32_t *cum) {
+    const uint32_t tid = threadIdx.x, M = 1u << lm;
+    if (tid < 32) {
+        uint32_t v[8], run = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = run;
+            run += freq[tid * 8 + k];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (tid >= uint32_t(d)) incl += y;
+        }
+        const uint32_t excl = incl - run;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cum[tid * 8 + k] = excl + v[k];
+        if (tid == 31) cum[256] = incl;
+    }
+    __syncthreads();
+    for (uint32_t s = tid; s < 256; s += blockDim.x) {
+        const uint32_t f = freq[s];
+        uint4 t;
+        if (f == 0) {
+            t = make_uint4(0u, 0xFFFFFFFFu, 0u, kZeroFlag);
+        } else {
+            const uint32_t k = 32u - __clz(f - 1u);
+            const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
+            t.x = uint32_t(m - (1ull << 32));
+            t.y = uint32_t((uint64_t(f) << (32 - lm)) - 1);
+            t.z = M - f;
+            t.w = (cum[s] & 0xFFFFu) | (k << 24);
+        }
+        tab[s] = t;
+    }
+    const uint32_t total = cum[256];
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ uint4 ld_enc_table4(uint32_t a) {
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ uint2 ld_enc_table(uint32_t a) {
     uint2 v;
     asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
@@ -179,6 +238,28 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
         const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
         const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
+    }
+}
+
+// One step with a wide model: as encode_step with the 16-byte entry.
+template <bool FULL>
+__device__ __forceinline__ void encode_step_wide(uint32_t &x, uint32_t &wp, uint32_t &acc,
+                                                 bool active, uint32_t s, uint32_t tab_s,
+                                                 uint32_t ring_s, uint32_t ge) {
+    const uint4 t = ld_enc_table4(tab_s + (s << 4));
+    const bool on = FULL || active;
+    if (on) acc |= t.w;
+    const bool emit = on && x > t.y;
+    const uint32_t m = __ballot_sync(kFull, emit);
+    if (emit) {
+        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        x >>= 16;
+    }
+    wp -= 2u * __popc(m);
+    if (on) {
+        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
+        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.w >> 24);
+        x = x + q * t.z + (t.w & 0xFFFFu);
     }
 }
 
@@ -303,6 +384,16 @@ __device__ __forceinline__ void encode_step_adaptive(uint32_t &x, uint32_t &wp, 
     }
 }
 
+// The step of a chunk of the byte-wise, wide or plain kind.
+template <bool FULL, bool BYTES, bool WIDE>
+__device__ __forceinline__ void coded_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
+                                           uint32_t s, uint32_t tab_s, uint32_t ring_s,
+                                           uint32_t ge) {
+    if (BYTES) encode_step_bytes<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
+    else if (WIDE) encode_step_wide<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
+    else encode_step<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
+}
+
 // One step of a bypass chunk (Section 3): a lane whose symbol carries a raw
 // word rw sends it before encoding the symbol, so in the stream (decoder
 // order) it follows that lane's renormalization word.  One reverse-lane
@@ -342,7 +433,9 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // carries one); groups are halved so that a group still writes at most 1 KiB.
 // BYTES: a byte-wise chunk (at most 2 bytes per symbol, size padded to 4).
 // ADAPT: an adaptive chunk; ctx holds the chunk's words from adaptive_forward.
-template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false>
+// WIDE: a wide model's 16-byte table entries (encode_step_wide).
+template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false,
+          bool WIDE = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
@@ -399,8 +492,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
             encode_step_raw<false>(x, wp, acc, act, s, rw, tab_s, ring_s, ge);
         } else {
-            (BYTES ? encode_step_bytes<false>(x, wp, acc, act, s, tab_s, ring_s, ge)
-                   : encode_step<false>(x, wp, acc, act, s, tab_s, ring_s, ge));
+            coded_step<false, BYTES, WIDE>(x, wp, acc, act, s, tab_s, ring_s, ge);
         }
     }
     int64_t t = int64_t(T_full) - 1;
@@ -414,8 +506,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
             encode_step_raw<NT == 32>(x, wp, acc, lane_on, s, rw, tab_s, ring_s, ge);
         } else {
-            (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge)
-                   : encode_step<NT == 32>(x, wp, acc, lane_on, s, tab_s, ring_s, ge));
+            coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
         }
     }
     if (ADAPT) {
@@ -462,8 +553,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             service();
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u)
-                (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge)
-                   : encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge));
+                coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
 #pragma unroll
             for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
         }
@@ -483,8 +573,7 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                     encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
                                               ge);
                 else
-                    (BYTES ? encode_step_bytes<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge)
-                   : encode_step<NT == 32>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge));
+                    coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
             }
         }
     }
@@ -562,12 +651,13 @@ __device__ __forceinline__ uint64_t scan_sizes(const uint32_t *sizes, uint32_t c
 // the zero padding before and after the data region, and the message size.
 __device__ __forceinline__ void write_header(uint8_t *out, uint64_t *out_size, uint64_t n_sym,
                                              uint32_t N, uint32_t CS, uint32_t n_chunks,
-                                             uint32_t data0, uint32_t total, uint32_t version) {
+                                             uint32_t data0, uint32_t total, uint32_t version,
+                                             uint32_t log2m = kLog2M) {
     uint32_t *h = reinterpret_cast<uint32_t *>(out);
     h[0] = RANS_MAGIC;
     h[1] = version;
     h[2] = N;
-    h[3] = kLog2M;
+    h[3] = log2m;
     h[4] = uint32_t(n_sym);
     h[5] = uint32_t(n_sym >> 32);
     h[6] = CS;
@@ -586,11 +676,13 @@ __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_siz
                                                  const uint32_t *sizes, uint64_t n_sym, uint32_t N,
                                                  uint32_t CS, uint32_t n_chunks, uint32_t data0,
                                                  uint32_t *warp_sums, uint64_t *carry_s,
-                                                 uint32_t version = RANS_VERSION) {
+                                                 uint32_t version = RANS_VERSION,
+                                                 uint32_t log2m = kLog2M) {
     uint32_t *offs = reinterpret_cast<uint32_t *>(out + 32);
     const uint64_t total = scan_sizes(sizes, 0, n_chunks, 0, offs, nullptr, warp_sums, carry_s);
     if (threadIdx.x == 0)
-        write_header(out, out_size, n_sym, N, CS, n_chunks, data0, uint32_t(total), version);
+        write_header(out, out_size, n_sym, N, CS, n_chunks, data0, uint32_t(total), version,
+                     log2m);
 }
 
 // Copy chunk c (states, then words) to its place in the message.  The

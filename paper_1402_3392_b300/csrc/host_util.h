@@ -44,6 +44,21 @@ inline bool table_ok(const uint16_t *freq, uint32_t n_alpha, uint32_t *const_sym
     return sum == RANS_M;
 }
 
+// A plain message's model may also have M = 2^13 or 2^14 (b = 2^16 >= M
+// keeps one renormalization per symbol): true if the frequencies sum to 2^12,
+// 2^13 or 2^14, with *log2m set to that exponent.
+inline bool table_log2m(const uint16_t *freq, uint32_t n_alpha, uint32_t *log2m) {
+    if (!freq || n_alpha == 0 || n_alpha > RANS_MAX_ALPHABET) return false;
+    uint32_t sum = 0;
+    for (uint32_t s = 0; s < n_alpha; ++s) sum += freq[s];
+    for (uint32_t lm = RANS_LOG2_M; lm <= RANS_LOG2_M_MAX; ++lm)
+        if (sum == (1u << lm)) {
+            *log2m = lm;
+            return true;
+        }
+    return false;
+}
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Number of SMs of the current device (cached per device).

@@ -34,6 +34,7 @@ struct DecodeParams {
     uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
+    uint32_t log2m;                        // plain messages: log2 M (12, 13 or 14)
     uint8_t plen[RANS_MAX_ALPHABET];       // prefix messages: code lengths (0: no code)
     uint16_t pcode[RANS_MAX_ALPHABET];     // prefix messages: canonical codes
 };
@@ -43,7 +44,8 @@ struct DecodeParams {
 // adaptive (version 4: binary symbols, one adaptive context per coder) and
 // prefix (version 5: canonical prefix codes in their decoder's read order).
 constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::kKindBytes,
-              kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix;
+              kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix,
+              kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  Bypass and
 // byte-wise messages are decoded one chunk per warp.
@@ -54,6 +56,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPTIVE = KIND == kAdaptive;
     constexpr bool PREFIX = KIND == kPrefix;
+    constexpr bool WIDE = KIND == kWide13 || KIND == kWide14;
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -65,12 +68,16 @@ __global__ void __launch_bounds__(dec::kThreads)
                                 RAW ? RANS_VERSION_BYPASS : BYTES ? RANS_VERSION_BYTES
                                 : ADAPTIVE                        ? RANS_VERSION_ADAPTIVE
                                 : PREFIX                          ? RANS_VERSION_PREFIX
-                                                                  : RANS_VERSION);
+                                                                  : RANS_VERSION,
+                                WIDE ? dec::WideBits<KIND>::kLog2 : uint32_t(kLog2M));
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
     if (ADAPTIVE) __syncthreads();  // no table: the contexts live in registers
     else if (PREFIX) dec::build_prefix_table(p.plen, p.pcode, sm.tab);
+    else if (WIDE)
+        dec::build_wide_table(p.freq, dec::WideBits<KIND>::kLog2, reinterpret_cast<uint8_t *>(sm.tab),
+                              sm.fb, sm.rings, &const_sym);  // rings unused yet
     else dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
     if (!hdr_ok) {
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
@@ -98,6 +105,10 @@ __global__ void __launch_bounds__(dec::kThreads)
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt);
+        else if (WIDE)  // the f/B table goes where bypass messages keep their flags
+            st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
+                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
+                                                     lt, nullptr, sm.fb_s);
         else
             st = per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs,
                                                         data_end, c, count, p.n_sym, p.CS, p.N,
@@ -158,10 +169,14 @@ using namespace rans;
 
 // Checks the arguments shared by the decode entry points and fills p (all
 // chunks); msg may be a host or a device address.
+// wide_ok: a plain message, whose model may also sum to 2^13 or 2^14 (the
+// kind is then kWide13 or kWide14).
 static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t *h_freq,
                           uint32_t n_alpha, const rans_params *params, uint64_t n_symbols,
-                          DecodeParams &p) {
-    if (!msg || !params_ok(params) || !table_ok(h_freq, n_alpha, nullptr))
+                          DecodeParams &p, bool wide_ok = false) {
+    uint32_t lm = RANS_LOG2_M;
+    if (!msg || !params_ok(params) ||
+        !(wide_ok ? table_log2m(h_freq, n_alpha, &lm) : table_ok(h_freq, n_alpha, nullptr)))
         return RANS_ERR_INVALID_ARG;
     const MessageGeometry g = geometry(n_symbols, params);
     if (g.n_chunks > 0xFFFFFFFEull) return RANS_ERR_INVALID_ARG;
@@ -177,6 +192,8 @@ static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t 
     p.data0 = uint32_t(g.data0);
     p.c_begin = 0;
     p.c_end = p.n_chunks;
+    p.log2m = lm;
+    p.kind = lm == 13 ? kWide13 : lm == 14 ? kWide14 : kPlain;
     for (uint32_t s = 0; s < n_alpha; ++s) p.freq[s] = h_freq[s];
     return RANS_OK;
 }
@@ -192,6 +209,10 @@ static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaSt
         return p.N == 32 ? launch_decode<32, kAdaptive>(p, st) : launch_decode<0, kAdaptive>(p, st);
     if (p.kind == kPrefix)
         return p.N == 32 ? launch_decode<32, kPrefix>(p, st) : launch_decode<0, kPrefix>(p, st);
+    if (p.kind == kWide13)
+        return p.N == 32 ? launch_decode<32, kWide13>(p, st) : launch_decode<0, kWide13>(p, st);
+    if (p.kind == kWide14)
+        return p.N == 32 ? launch_decode<32, kWide14>(p, st) : launch_decode<0, kWide14>(p, st);
     return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 
@@ -199,7 +220,7 @@ extern "C" int rans_decode(const uint8_t *d_msg, uint64_t msg_size, const uint16
                            uint32_t n_alpha, const rans_params *params, uint8_t *d_symbols,
                            uint64_t n_symbols, uint32_t *d_status, rans_stream_t stream) {
     DecodeParams p;
-    const int rc = prepare_decode(d_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    const int rc = prepare_decode(d_msg, msg_size, h_freq, n_alpha, params, n_symbols, p, true);
     if (rc != RANS_OK) return rc;
     if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
     p.msg = d_msg;
@@ -310,7 +331,7 @@ extern "C" int rans_decode_host(const uint8_t *h_msg, uint64_t msg_size, const u
                                 uint64_t n_symbols, uint32_t *h_status, void *d_work,
                                 uint64_t work_cap, rans_stream_t stream) {
     DecodeParams p;
-    int rc = prepare_decode(h_msg, msg_size, h_freq, n_alpha, params, n_symbols, p);
+    int rc = prepare_decode(h_msg, msg_size, h_freq, n_alpha, params, n_symbols, p, true);
     if (rc != RANS_OK) return rc;
     if (!h_status || !d_work || !aligned16(d_work) || (n_symbols && !h_symbols))
         return RANS_ERR_INVALID_ARG;

@@ -31,6 +31,7 @@ struct EncodeParams {
     uint32_t n_chunks;
     uint32_t slot_bytes;
     uint32_t c_begin, c_end;  // chunks [c_begin, c_end) are coded by this launch
+    uint32_t log2m;           // plain messages: log2 M (12, 13 or 14)
     const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
     uint64_t ctx_stride;  // u32 words per chunk in ctx
@@ -42,16 +43,22 @@ struct EncodeParams {
 // symbol that carries one), byte-wise (version 3: b = 2^8) and adaptive
 // (version 4: binary symbols, one adaptive context per coder).
 constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
+// Plain messages with M = 2^13 or 2^14 (16-byte table entries).
+constexpr int kWide = 4;
 
 template <int NT, int KIND>
 __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPT = KIND == kAdaptive;
+    constexpr bool WIDE = KIND == kWide;
     extern __shared__ __align__(128) uint8_t smem[];
     const enc::Smem sm = enc::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    if (!ADAPT)  // adaptive contexts need no table
+    if (WIDE)
+        enc::build_wide_encode_table(p.freq, p.log2m, reinterpret_cast<uint4 *>(sm.tab),
+                                     reinterpret_cast<uint32_t *>(sm.rings));
+    else if (!ADAPT)  // adaptive contexts need no table
         enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings),
                                 RAW ? p.raw_words : nullptr);
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
@@ -63,7 +70,7 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
         uint32_t *ctx = ADAPT ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
         if (ADAPT) enc::adaptive_forward<NT>(p.sym + first, n_c, p.N, ctx, lane, acc);
-        enc::encode_chunk<NT, !RAW && !ADAPT, RAW, BYTES, ADAPT>(
+        enc::encode_chunk<NT, !RAW && !ADAPT, RAW, BYTES, ADAPT, WIDE>(
             p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
             acc, RAW ? p.raw + first : nullptr, ctx);
@@ -95,7 +102,7 @@ struct FinalizeParams {
     const uint32_t *sizes;
     const uint32_t *status;
     uint64_t n_sym;
-    uint32_t N, CS, n_chunks, data0, version;
+    uint32_t N, CS, n_chunks, data0, version, log2m;
 };
 
 constexpr int kScanThreads = 1024;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kScanThreads)
         return;
     }
     enc::finalize_message(p.out, p.out_size, p.sizes, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
-                          warp_sums, &carry_s, p.version);
+                          warp_sums, &carry_s, p.version, p.log2m);
 }
 
 struct PackParams {
@@ -174,8 +181,14 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
                           uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
                           uint64_t scratch_cap, rans_stream_t stream, bool bytes = false,
                           bool adaptive = false) {
-    if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
-        !d_status || !d_scratch || !aligned16(d_out) || !aligned16(d_scratch))
+    // Plain messages may use M = 2^13 or 2^14 (the table's sum); the other
+    // kinds keep M = 2^12.
+    const bool plain = raw_words == nullptr && !bytes && !adaptive;
+    uint32_t lm = RANS_LOG2_M;
+    if (!params_ok(params) ||
+        !(plain ? table_log2m(h_freq, n_alpha, &lm) : table_ok(h_freq, n_alpha, nullptr)) ||
+        !d_out || !d_out_size || !d_status || !d_scratch || !aligned16(d_out) ||
+        !aligned16(d_scratch))
         return RANS_ERR_INVALID_ARG;
     if (n_symbols && !d_symbols) return RANS_ERR_INVALID_ARG;
     const bool bypass = raw_words != nullptr;
@@ -225,11 +238,14 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.slot_bytes = sl.slot_bytes;
     ep.c_begin = 0;
     ep.c_end = ep.n_chunks;
+    ep.log2m = lm;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
     if (g.n_chunks > 0) {
         int rc;
-        if (adaptive)
+        if (lm != RANS_LOG2_M)
+            rc = ep.N == 32 ? launch_encode<32, kWide>(ep, st) : launch_encode<0, kWide>(ep, st);
+        else if (adaptive)
             rc = ep.N == 32 ? launch_encode<32, kAdaptive>(ep, st) : launch_encode<0, kAdaptive>(ep, st);
         else if (bypass)
             rc = ep.N == 32 ? launch_encode<32, kBypass>(ep, st) : launch_encode<0, kBypass>(ep, st);
@@ -251,6 +267,7 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     fp.data0 = uint32_t(g.data0);
     fp.version = bypass ? RANS_VERSION_BYPASS : bytes ? RANS_VERSION_BYTES
                  : adaptive ? RANS_VERSION_ADAPTIVE : RANS_VERSION;
+    fp.log2m = lm;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {
@@ -408,6 +425,7 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     fp.n_chunks = ep.n_chunks;
     fp.data0 = uint32_t(g.data0);
     fp.version = RANS_VERSION;
+    fp.log2m = RANS_LOG2_M;
     finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     if (g.n_chunks > 0) {
@@ -464,7 +482,7 @@ struct HeaderParams {
     const uint64_t *running;
     const uint32_t *status;
     uint64_t n_sym;
-    uint32_t N, CS, n_chunks, data0;
+    uint32_t N, CS, n_chunks, data0, log2m;
 };
 
 __global__ void host_header_kernel(const __grid_constant__ HeaderParams p) {
@@ -473,7 +491,7 @@ __global__ void host_header_kernel(const __grid_constant__ HeaderParams p) {
         return;
     }
     enc::write_header(p.out, p.d_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
-                      uint32_t(*p.running), RANS_VERSION);
+                      uint32_t(*p.running), RANS_VERSION, p.log2m);
 }
 
 // Work space: [symbols][encode scratch][device offsets][running, status,
@@ -507,7 +525,8 @@ extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
                                 const rans_params *params, uint8_t *h_out, uint64_t out_cap,
                                 uint64_t *h_out_size, uint32_t *h_status, void *d_work,
                                 uint64_t work_cap, rans_stream_t stream) {
-    if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !h_out || !h_out_size ||
+    uint32_t lm = RANS_LOG2_M;
+    if (!params_ok(params) || !table_log2m(h_freq, n_alpha, &lm) || !h_out || !h_out_size ||
         !h_status || !d_work || !aligned16(d_work) || (n_symbols && !h_symbols))
         return RANS_ERR_INVALID_ARG;
     const MessageGeometry g = geometry(n_symbols, params);
@@ -552,6 +571,7 @@ extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
     ep.CS = params->chunk_symbols;
     ep.n_chunks = uint32_t(g.n_chunks);
     ep.slot_bytes = sl.slot_bytes;
+    ep.log2m = lm;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
     CopyStreams cs;
@@ -578,7 +598,10 @@ extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
             return RANS_ERR_CUDA;
         ep.c_begin = uint32_t(c0);
         ep.c_end = uint32_t(c1);
-        rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
+        if (lm != RANS_LOG2_M)
+            rc = ep.N == 32 ? launch_encode<32, kWide>(ep, st) : launch_encode<0, kWide>(ep, st);
+        else
+            rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
         if (rc != RANS_OK) return rc;
         RangeOffsetsParams rp{};
         rp.sizes = ep.sizes;
@@ -617,6 +640,7 @@ extern "C" int rans_encode_host(const uint8_t *h_symbols, uint64_t n_symbols,
     hp.CS = ep.CS;
     hp.n_chunks = nc;
     hp.data0 = uint32_t(g.data0);
+    hp.log2m = lm;
     host_header_kernel<<<1, 1, 0, cs.out>>>(hp);
     if (check_launch() != RANS_OK ||
         cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs.out) !=
