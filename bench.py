@@ -55,9 +55,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
-    ap.add_argument("--legs", default="batched,binary,single,serving,bypass,bytes,adaptive,prefix",
+    ap.add_argument("--legs",
+                    default="batched,binary,single,serving,bypass,bytes,adaptive,prefix,wide",
                     help="extra legs after the headline one: comma list of batched, binary, "
-                         "single, serving, bypass, bytes, adaptive, prefix, none")
+                         "single, serving, bypass, bytes, adaptive, prefix, wide, none")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -685,6 +686,56 @@ def prefix_leg(rans, dev, args, hbm):
                          "algorithmic_bytes_per_launch": alg}}
 
 
+def wide_leg(rans, dev, args, hbm):
+    """The 1 GiB chunked workload with the model at 14 bits of probability
+    resolution (M = 2^14, b = 2^16: still one renormalization per symbol,
+    Section 5): encode and decode timed, the round trip checked, the size set
+    beside the 12-bit model's."""
+    import torch
+
+    cfg = wl.WORKLOADS["chunked"]
+    n, N, CS = args.symbols or cfg["n_symbols"], cfg["n_lanes"], cfg["chunk_symbols"]
+    p = wl.zipf_probs(cfg["alphabet"], cfg["zipf_s"])
+    freq = rans.rans_quantize_table(wl.weights_from_probs(p), 14)
+    sym = wl.iid_symbols_device(p, n, wl.seed_for("chunked"), dev)
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    scap = rans.rans_encode_scratch_size(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    enc = lambda: rans.rans_encode(sym, n, freq, N, CS, msg, cap, size, est, scratch, scap)  # noqa: E731
+    enc()
+    torch.cuda.synchronize()
+    assert int(est.item()) == 0
+    msg_size = int(size.item())
+    enc_ms = statistics.median(_events(torch, enc, 5))
+    f12 = rans.rans_quantize_table(wl.weights_from_probs(p))
+    size12 = int(rans.encode(sym, f12, N, CS, scratch=scratch)[1].item())   # not timed
+    del scratch
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    dst = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode(msg, msg_size, freq, N, CS, out, n, dst)  # noqa: E731
+    dec()
+    torch.cuda.synchronize()
+    ok = int(dst.item()) == 0 and torch.equal(out, sym)
+    dec_ms = statistics.median(_events(torch, dec, 10))
+    alg = msg_size + n
+    orc = _oracle()
+    cpu = oracle_leg_baseline(lambda ch: orc.decode_chunk(ch, CS, freq, N=N),
+                              host_chunks(msg, n // CS, 16 * host_cores()), CS)
+    return {"workload": f"{n} symbols, Zipf({cfg['zipf_s']}) over {cfg['alphabet']}, {n // CS} "
+                        f"chunks x {CS}, N = {N}, model at 14 bits (M = 2^14)",
+            "decode_gbs": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
+            "encode_gbs": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
+            "compression_ratio": msg_size / n, "compression_ratio_12_bits": size12 / n,
+            "bit_exact_roundtrip": bool(ok), "cpu_baseline": cpu,
+            "roofline": {"kernel": "decode_kernel (14-bit model)", "bound": "hbm",
+                         "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def single_leg(rans, dev, args):
     """One 1 MiB stream, Zipf(1.2) over 256 symbols, 32 coders in one chunk:
     a single warp's chain of 32768 dependent steps, so a latency figure."""
@@ -949,6 +1000,9 @@ def main(argv=None):
         torch.cuda.empty_cache()
     if "prefix" in legs:
         extra["prefix"] = prefix_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
+    if "wide" in legs:
+        extra["wide"] = wide_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
 
     if rank == 0:
