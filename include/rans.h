@@ -130,7 +130,12 @@ uint64_t rans_encode_scratch_size(uint64_t n_symbols, const rans_params *params)
  * rans_encode -- encode n_symbols bytes into one message (format above).
  *
  * d_symbols : device, n_symbols bytes, symbol values < n_alpha.
- * h_freq    : host, n_alpha frequencies with sum = RANS_M (rans_quantize_table).
+ * h_freq    : host, n_alpha frequencies (rans_quantize_table) with sum M =
+ *             2^12 = RANS_M, or 2^13 or 2^14: with b = 2^16 >= M a symbol still
+ *             needs at most one renormalization (Section 5's 12-14 bits of
+ *             probability resolution).  The sum selects M; the header's log2_M
+ *             field records it (the 2^13/2^14 tables cost the decoder a
+ *             second table lookup per symbol).
  * n_alpha   : 1..256.
  * params    : host; n_lanes 1..32, chunk_symbols >= 1.
  * d_out     : device, 16-byte aligned, out_cap bytes; out_cap must be at
@@ -156,7 +161,7 @@ int rans_encode(const uint8_t *d_symbols, uint64_t n_symbols, const uint16_t *h_
  *
  * d_msg     : device, 16-byte aligned, msg_size bytes (a multiple of 16).
  * h_freq, n_alpha, params : the model and layout the message was encoded
- *             with (the header is checked against them).
+ *             with (the header is checked against them, log2_M included).
  * d_symbols : device, n_symbols bytes of output.
  * d_status  : device, one u32, set to RANS_OK, or RANS_ERR_CORRUPT if the
  *             header, the offsets or any chunk is inconsistent (a chunk must
