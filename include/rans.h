@@ -24,7 +24,8 @@
  *
  * Message format (little endian; the paper defines no container):
  *   bytes 0..31  header: u32 magic 0x534E4152 ("RANS"), u32 version 1,
- *                u32 n_lanes N, u32 log2_M (12), u64 n_symbols,
+ *                u32 n_lanes N, u32 log2_M (12; 13 or 14 for version 1),
+ *                u64 n_symbols,
  *                u32 chunk_symbols, u32 n_chunks = ceil(n_symbols/chunk_symbols)
  *   u32 offsets[n_chunks + 1]: start of chunk c in bytes, relative to the
  *                data region; offsets[0] = 0, offsets[n_chunks] = data bytes
@@ -112,7 +113,8 @@ const char *rans_status_string(int status);
  * Hence f_s >= 1 exactly when w_s > 0.
  * weights: host, n entries.  freq_out: host, n entries.
  * n in [1, 4096], log2_M in [1, 15], sum w < 2^64, at most M nonzero weights;
- * the coder itself needs log2_M = 12 and n <= 256.
+ * the coders need n <= 256 and log2_M = 12 (12, 13 or 14 for the plain
+ * rans_encode / rans_decode family).
  * Returns RANS_OK or RANS_ERR_INVALID_ARG (freq_out untouched).  Host only.
  */
 int rans_quantize_table(const uint64_t *weights, uint32_t n, uint32_t log2_M,
