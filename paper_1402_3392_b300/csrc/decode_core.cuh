@@ -544,11 +544,20 @@ __device__ __forceinline__ bool ring_window_ok(const Chain &c, uint32_t bytes) {
     return not_overwritten && complete;
 }
 
+// Shared address of the word k words of B bytes past read position rp.
+// RING > 0: rp is the byte position in the chunk's word stream and ring_s the
+// chunk's ring of RING bytes, aligned to RING, so (offset & (RING - 1)) |
+// ring_s addresses it.  RING = 0: rp is the shared address of the read
+// position itself, for groups of steps whose reads cannot reach the ring's
+// end (one multiply-add, no wrap).
+template <uint32_t RING, uint32_t B = 2>
+__device__ __forceinline__ uint32_t word_at(uint32_t rp, uint32_t k, uint32_t ring_s) {
+    return RING ? ((rp + B * k) & (RING - 1)) | ring_s : imad(k, B, rp);
+}
+
 // Decode one step of a chunk: every active lane decodes one symbol and reads
 // at most one word.  FULL: every lane of the warp is a coder with a symbol in
-// this step.  rp is the byte position in the word stream (warp-uniform);
-// ring_s is the chunk's ring of RING bytes, aligned to RING, so
-// (offset & (RING - 1)) | ring_s addresses it.
+// this step.  rp: the warp-uniform read position (word_at).
 template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
                                             uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
@@ -560,7 +569,7 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
     }
     const bool need = (FULL || active) && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    const uint32_t w = ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp = imad(__popc(m), 2u, rp);
 }
@@ -581,7 +590,7 @@ __device__ __forceinline__ void decode_step_wide(uint32_t &x, uint32_t &rp, bool
     }
     const bool need = (FULL || active) && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    const uint32_t w = ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp = imad(__popc(m), 2u, rp);
 }
@@ -630,9 +639,9 @@ __device__ __forceinline__ void decode_step_raw(uint32_t &x, uint32_t &rp, bool 
     const bool has = on && fl != 0u;
     const uint32_t m = __ballot_sync(kFull, need);
     const uint32_t mr = __ballot_sync(kFull, has);
-    const uint32_t pos = imad(__popc(m & lt) + __popc(mr & lt), 2u, rp);
-    const uint32_t w = ld_ring_u16((pos & (RING - 1)) | ring_s);
-    const uint32_t rw = ld_ring_u16((imad(uint32_t(need), 2u, pos) & (RING - 1)) | ring_s);
+    const uint32_t k = __popc(m & lt) + __popc(mr & lt);
+    const uint32_t w = ld_ring_u16(word_at<RING>(rp, k, ring_s));
+    const uint32_t rw = ld_ring_u16(word_at<RING>(rp, k + uint32_t(need), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     if (on) *rawp = uint16_t(has ? rw : 0u);
     rp = imad(__popc(m) + __popc(mr), 2u, rp);
@@ -655,13 +664,13 @@ __device__ __forceinline__ void decode_step_bytes(uint32_t &x, uint32_t &rp, boo
     }
     bool need = on && x < kL8;
     uint32_t m = __ballot_sync(kFull, need);
-    uint32_t w = ld_ring_u8(((rp + __popc(m & lt)) & (RING - 1)) | ring_s);
+    uint32_t w = ld_ring_u8(word_at<RING, 1>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x2104u);  // (x << 8) | w
     rp += __popc(m);
     need = on && x < kL8;
     m = __ballot_sync(kFull, need);
     if (m) {
-        w = ld_ring_u8(((rp + __popc(m & lt)) & (RING - 1)) | ring_s);
+        w = ld_ring_u8(word_at<RING, 1>(rp, __popc(m & lt), ring_s));
         if (need) x = __byte_perm(x, w, 0x2104u);
         rp += __popc(m);
     }
@@ -689,7 +698,7 @@ __device__ __forceinline__ void decode_step_adaptive(uint32_t &x, uint32_t &p, u
     }
     const bool need = on && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u16(((rp + 2u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    const uint32_t w = ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp = imad(__popc(m), 2u, rp);
 }
@@ -706,7 +715,7 @@ __device__ __forceinline__ void decode_step_prefix(Chain &c, bool active, uint32
     const bool on = FULL || active;
     const bool need = on && c.nb < kPrefixMaxLen;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u32(((c.rp + 4u * __popc(m & lt)) & (RING - 1)) | ring_s);
+    const uint32_t w = ld_ring_u32(word_at<RING, 4>(c.rp, __popc(m & lt), ring_s));
     if (need) {
         c.bhi = c.blo;
         c.blo = w;
@@ -750,10 +759,30 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
     for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
         chain_service<G>(c, r, timeouts, lane);
         RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kGroup * G::kStep));
+        const uint32_t off = c.rp & (G::kRing - 1);
+        // Measured on B300: 2-3.5 % faster for plain, bypass and byte-wise
+        // chunks alone in a warp's ring; no gain for adaptive, prefix and
+        // 13/14-bit chunks, and slower for chunk pairs (more code).
+        constexpr bool kLinear = (KIND == kKindPlain || KIND == kKindRaw || KIND == kKindBytes) &&
+                                 G::kRing == kWarpRing;
+        if (kLinear && off + G::kGroup * G::kStep <= G::kRing) {
+            // A group reads at most kGroup * kStep bytes from rp: here they
+            // all lie below the ring's end (3 groups in 4 with a 4 KiB ring
+            // and 1 KiB groups), so the steps address the ring by absolute
+            // position.
+            const uint32_t rp0 = c.rp, a0 = r.ring_s + off;
+            c.rp = a0;
 #pragma unroll
-        for (uint32_t u = 0; u < G::kGroup; ++u)
-            kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp + u * N,
-                                            RAW ? c.rawp + u * N : nullptr, lt);
+            for (uint32_t u = 0; u < G::kGroup; ++u)
+                kind_step<FULL, 0, KIND>(c, lane_on, tab_s, r.ring_s, flags_s, c.outp + u * N,
+                                         RAW ? c.rawp + u * N : nullptr, lt);
+            c.rp = rp0 + (c.rp - a0);
+        } else {
+#pragma unroll
+            for (uint32_t u = 0; u < G::kGroup; ++u)
+                kind_step<FULL, G::kRing, KIND>(c, lane_on, tab_s, r.ring_s, flags_s,
+                                                c.outp + u * N, RAW ? c.rawp + u * N : nullptr, lt);
+        }
         c.outp += G::kGroup * N;
         if (RAW) c.rawp += G::kGroup * N;
     }

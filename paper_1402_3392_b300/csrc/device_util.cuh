@@ -65,7 +65,8 @@ static inline uint64_t take_check_failures() {
     return v;
 }
 #else
-#define RANS_CHECK(cond) true
+__device__ __forceinline__ constexpr bool check_off() { return true; }
+#define RANS_CHECK(cond) (::rans::check_off())
 #endif
 
 // ---- mbarrier ---------------------------------------------------------------

@@ -23,11 +23,13 @@ __global__ void __launch_bounds__(32) bounded_wait_kernel(uint32_t *status) {
     if (threadIdx.x == 0) *status = st;
 }
 
+#ifdef RANS_CHECKED
 // Checked builds: one invariant that fails on purpose, so a test can see the
 // counters work.
 __global__ void check_selftest_kernel() {
     if (threadIdx.x == 0) RANS_CHECK(false);
 }
+#endif
 
 }  // namespace
 }  // namespace rans
