@@ -1023,7 +1023,9 @@ def main(argv=None):
                          "frac": achieved / hbm, "traffic": profiled_traffic(),
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": sampler.summary(),
-            "gpu_launches": 4 * args.steps,
+            # per step: encode_kernel (codes and places the chunks), settle_kernel
+            # (the size of a rejected message), decode_kernel
+            "gpu_launches": 3 * args.steps,
             "e2e": e2e,
             "e2e_encode": e2e_enc,
             "cpu_baseline": cpu,

@@ -17,9 +17,12 @@
 // multiply-high by ceil(2^(32+k) / f_s), k = ceil(log2 f_s).
 //
 // Words are staged in a per-warp shared-memory ring and leave as 512-byte bulk
-// stores (TMA) into a worst-case scratch slot per chunk.  A scan of the chunk
-// sizes then gives the offset table and the header, and a copy packs every
-// chunk behind it.
+// stores (TMA) into a worst-case scratch slot per chunk.  A whole message is
+// then placed in the same launch: each warp publishes its chunk's size, finds
+// the sizes of the chunks before it (decoupled look-back), writes its offset
+// and copies the chunk to its place.  Pieces of a message (host-memory
+// encoding) and batches of streams use a scan of the sizes and a separate
+// copy instead.
 #pragma once
 
 #include <cstdint>
@@ -54,9 +57,11 @@ constexpr uint32_t kAdaptP0 = kM / 2;
 
 // Scratch of one message, all sections 16-byte aligned: one worst-case slot
 // of words per chunk (written backwards from its end), then the chunks'
-// final states, first-word offsets and byte sizes.
+// final states, first-word offsets and byte sizes, then the look-back words
+// (one per chunk, two per group of 32 chunks) and the chunk ticket counter,
+// zeroed before each launch that places the chunks itself.
 struct ScratchLayout {
-    uint64_t words, states, wstart, sizes, ctx, total;
+    uint64_t words, states, wstart, sizes, look, glook, gacc, ticket, ctx, total;
     uint32_t slot_bytes;
 };
 
@@ -69,7 +74,12 @@ __host__ __device__ inline ScratchLayout scratch_layout(uint64_t n_chunks, uint3
     s.states = (n_chunks * s.slot_bytes + 16 + 15) & ~uint64_t(15);
     s.wstart = s.states + ((n_chunks * N * 4 + 15) & ~uint64_t(15));
     s.sizes = s.wstart + ((n_chunks * 4 + 15) & ~uint64_t(15));
-    s.total = s.sizes + ((n_chunks * 4 + 15) & ~uint64_t(15));
+    const uint64_t n_groups = (n_chunks + 31) / 32;
+    s.look = s.sizes + ((n_chunks * 4 + 15) & ~uint64_t(15));
+    s.glook = s.look + ((n_chunks * 8 + 15) & ~uint64_t(15));
+    s.gacc = s.glook + ((n_groups * 8 + 15) & ~uint64_t(15));
+    s.ticket = s.gacc + ((n_groups * 8 + 15) & ~uint64_t(15));
+    s.total = s.ticket + 16;
     s.ctx = s.total;  // adaptive messages: the contexts' words (adaptive_ctx_stride) follow
     return s;
 }
@@ -689,79 +699,205 @@ __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_siz
 // destination is only 2-byte aligned, so whole 16-byte destination blocks are
 // assembled from two aligned 16-byte source loads and a funnel shift (the
 // source-to-destination shift is the same for every block of a chunk); the
-// partial blocks at both ends are written in 16-bit units.
+// partial blocks at both ends are written in 16-bit units.  Two blocks per
+// thread are in flight.  Source loads go through L2 only (ld.global.cg): the
+// words arrived there by bulk copies in the same launch.
 template <int K>  // K = (source shift in bytes) / 4; rs = 8 * (shift mod 4)
 __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, uint64_t B0,
-                                            uint64_t B1, uint64_t s_minus_d, uint32_t rs) {
+                                            uint64_t B1, uint64_t s_minus_d, uint32_t rs,
+                                            uint32_t t, uint32_t nt) {
     const bool need_hi = K > 0 || rs != 0;
-    for (uint64_t B = B0 + 16ull * threadIdx.x; B < B1; B += 16ull * blockDim.x) {
-        const uint64_t sa = (B + s_minus_d) & ~uint64_t(15);
-        const uint4 v0 = *reinterpret_cast<const uint4 *>(src + sa);
-        const uint4 v1 = need_hi ? *reinterpret_cast<const uint4 *>(src + sa + 16)
-                                 : make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        uint4 r;
-        r.x = __funnelshift_r(w[K + 0], w[K + 1], rs);
-        r.y = __funnelshift_r(w[K + 1], w[K + 2], rs);
-        r.z = __funnelshift_r(w[K + 2], w[K + 3], rs);
-        r.w = __funnelshift_r(w[K + 3], w[K + 4], rs);
-        *reinterpret_cast<uint4 *>(out + B) = r;
+    const uint64_t stride = 16ull * nt;
+    for (uint64_t B = B0 + 16ull * t; B < B1; B += 2 * stride) {
+        uint4 v[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t Bu = B + u * stride;
+            const uint64_t sa = (Bu + s_minus_d) & ~uint64_t(15);
+            v[u][0] = v[u][1] = make_uint4(0u, 0u, 0u, 0u);
+            if (Bu < B1) {
+                v[u][0] = __ldcg(reinterpret_cast<const uint4 *>(src + sa));
+                if (need_hi) v[u][1] = __ldcg(reinterpret_cast<const uint4 *>(src + sa + 16));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t Bu = B + u * stride;
+            if (Bu >= B1) break;
+            const uint32_t w[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w,
+                                   v[u][1].x, v[u][1].y, v[u][1].z, v[u][1].w};
+            uint4 r;
+            r.x = __funnelshift_r(w[K + 0], w[K + 1], rs);
+            r.y = __funnelshift_r(w[K + 1], w[K + 2], rs);
+            r.z = __funnelshift_r(w[K + 2], w[K + 3], rs);
+            r.w = __funnelshift_r(w[K + 3], w[K + 4], rs);
+            *reinterpret_cast<uint4 *>(out + Bu) = r;
+        }
     }
 }
 
-// With a whole CTA: chunk c of a message (offset table already written in
-// out) from scratch (words base, states, wstart) into out.  The words buffer
-// must have 16 readable bytes past its last slot.
+// Threads t of nt: chunk c of a message from scratch (words base, states,
+// wstart) into out at message byte D.  The words buffer must have 16
+// readable bytes past its last slot.
 // BYTES: the chunk's byte count may be odd and its start in the slot too;
 // the chunk is padded with zeros to a multiple of 4 bytes.
-// offs_in: the chunk offsets, if not those in out's own offset table.
 template <bool BYTES = false>
-__device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const uint8_t *words,
-                                           const uint32_t *states, const uint32_t *wstart,
-                                           uint32_t N, uint32_t slot_bytes, uint32_t c,
-                                           const uint32_t *offs_in = nullptr) {
-    const uint32_t *offs = offs_in ? offs_in : reinterpret_cast<const uint32_t *>(out + 32);
-    const uint64_t D = uint64_t(data0) + offs[c];
+__device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const uint8_t *words,
+                                              const uint32_t *states, const uint32_t *wstart,
+                                              uint32_t N, uint32_t slot_bytes, uint32_t c,
+                                              uint32_t t, uint32_t nt) {
     uint16_t *dst16 = reinterpret_cast<uint16_t *>(out + D);
     const uint32_t *st = states + uint64_t(c) * N;
-    for (uint32_t i = threadIdx.x; i < 2 * N; i += blockDim.x)
-        dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
+    for (uint32_t i = t; i < 2 * N; i += nt) dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
     // words: destination bytes [d0, d1), source bytes from s0 in words
+    const uint32_t ws = wstart[c];
     const uint64_t d0 = D + 4ull * N;
-    const uint64_t s0 = uint64_t(c) * slot_bytes + wstart[c];
-    const uint64_t d1 = d0 + (slot_bytes - wstart[c]);
+    const uint64_t s0 = uint64_t(c) * slot_bytes + ws;
+    const uint64_t d1 = d0 + (slot_bytes - ws);
     const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
     const uint64_t head_end = B0 < d1 ? B0 : d1;
     if (BYTES) {
-        for (uint64_t b = d0 + threadIdx.x; b < head_end; b += blockDim.x)
-            out[b] = words[s0 + (b - d0)];
+        for (uint64_t b = d0 + t; b < head_end; b += nt) out[b] = __ldcg(words + s0 + (b - d0));
     } else {
-        for (uint64_t b = d0 + 2ull * threadIdx.x; b < head_end; b += 2ull * blockDim.x)
+        for (uint64_t b = d0 + 2ull * t; b < head_end; b += 2ull * nt)
             *reinterpret_cast<uint16_t *>(out + b) =
-                *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+                __ldcg(reinterpret_cast<const uint16_t *>(words + s0 + (b - d0)));
     }
     if (B0 < B1) {
         const uint64_t s_minus_d = s0 - d0;  // modulo 2^64
         const uint32_t sh = uint32_t(s_minus_d & 15u);
         const uint32_t rs = 8u * (sh & 3u);
         switch (sh >> 2) {
-            case 0: pack_blocks<0>(out, words, B0, B1, s_minus_d, rs); break;
-            case 1: pack_blocks<1>(out, words, B0, B1, s_minus_d, rs); break;
-            case 2: pack_blocks<2>(out, words, B0, B1, s_minus_d, rs); break;
-            default: pack_blocks<3>(out, words, B0, B1, s_minus_d, rs); break;
+            case 0: pack_blocks<0>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            case 1: pack_blocks<1>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            case 2: pack_blocks<2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            default: pack_blocks<3>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
         }
     }
     const uint64_t tail_start = B1 > head_end ? B1 : head_end;
     if (BYTES) {
-        for (uint64_t b = tail_start + threadIdx.x; b < d1; b += blockDim.x)
-            out[b] = words[s0 + (b - d0)];
+        for (uint64_t b = tail_start + t; b < d1; b += nt) out[b] = __ldcg(words + s0 + (b - d0));
         const uint64_t end = D + ((d1 - D + 3) & ~uint64_t(3));
-        for (uint64_t b = d1 + threadIdx.x; b < end; b += blockDim.x) out[b] = 0;
+        for (uint64_t b = d1 + t; b < end; b += nt) out[b] = 0;
     } else {
-        for (uint64_t b = tail_start + 2ull * threadIdx.x; b < d1; b += 2ull * blockDim.x)
+        for (uint64_t b = tail_start + 2ull * t; b < d1; b += 2ull * nt)
             *reinterpret_cast<uint16_t *>(out + b) =
-                *reinterpret_cast<const uint16_t *>(words + s0 + (b - d0));
+                __ldcg(reinterpret_cast<const uint16_t *>(words + s0 + (b - d0)));
     }
+}
+
+// With a whole CTA: chunk c of a message (offset table already written in
+// out, or offs_in) from scratch into out.
+template <bool BYTES = false>
+__device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const uint8_t *words,
+                                           const uint32_t *states, const uint32_t *wstart,
+                                           uint32_t N, uint32_t slot_bytes, uint32_t c,
+                                           const uint32_t *offs_in = nullptr) {
+    const uint32_t *offs = offs_in ? offs_in : reinterpret_cast<const uint32_t *>(out + 32);
+    pack_chunk_at<BYTES>(out, uint64_t(data0) + offs[c], words, states, wstart, N, slot_bytes, c,
+                         threadIdx.x, blockDim.x);
+}
+
+// ---- single-pass placement: decoupled look-back over the chunk sizes -------
+// look[c] holds a flag in its top two bits and a byte count below them:
+// kLookSize = chunk c's own size, kLookPrefix = the bytes of chunks 0..c
+// (inclusive prefix), kLookFailed = a wait before it gave up; zero: nothing
+// published yet.  glook[g] says the same of group g = chunks 32g .. 32g+31
+// (kLookSize = the group's total once all its chunks are published,
+// kLookPrefix = the bytes of chunks 0 .. 32g+31), and gacc[g] counts the
+// group's published chunks (<< 40) and sums their sizes.  A look-back reads
+// the chunks before c in its group, then whole groups: 32 groups (1024
+// chunks) per round.
+constexpr uint64_t kLookSize = 1ull << 62;
+constexpr uint64_t kLookPrefix = 2ull << 62;
+constexpr uint64_t kLookFailed = 3ull << 62;
+constexpr uint64_t kLookValue = (1ull << 62) - 1;
+
+struct LookBack {
+    uint64_t *look, *glook, *gacc;
+    uint32_t n_chunks;
+    uint64_t wait_ns;  // bound of the waits of one call
+};
+
+// One warp, once chunk c is in its slot: publishes its size, and its
+// group's total if it is the group's last chunk to be published (group 0's
+// total is its prefix too).  A group's total never replaces its prefix.
+__device__ __forceinline__ void publish_size(const LookBack &lb, uint32_t c, uint32_t size,
+                                             uint32_t lane) {
+    if (lane != 0) return;
+    st_release_u64(lb.look + c, (c == 0 ? kLookPrefix : kLookSize) | size);
+    const uint32_t g = c / 32, members = min(32u, lb.n_chunks - 32 * g);
+    const unsigned long long old =
+        atomicAdd(reinterpret_cast<unsigned long long *>(lb.gacc + g), (1ull << 40) | size);
+    if ((old >> 40) + 1 == members) {
+        const uint64_t total = (old & ((1ull << 40) - 1)) + size;
+        atomicCAS(reinterpret_cast<unsigned long long *>(lb.glook + g), 0ull,
+                  (g == 0 ? kLookPrefix : kLookSize) | total);
+    }
+}
+
+enum LookResult : uint32_t { kLookDone, kLookNotYet, kLookGaveUp };
+
+// One round of a look-back: lane i reads entry q - i (own = the lane has an
+// entry, else it contributes `none`), waits for it if `block`.  Adds the
+// entries up to the nearest prefix to sum; sets `found` if there was one.
+__device__ __forceinline__ LookResult look_round(const uint64_t *q, bool own, uint64_t none,
+                                                 bool block, uint64_t t0, uint64_t wait_ns,
+                                                 uint32_t lane, uint64_t &sum, bool &found) {
+    uint64_t v = none;
+    if (own) {
+        v = ld_acquire_u64(q - lane);
+        for (uint32_t ns = 64; block && (v >> 62) == 0 && globaltimer_ns() - t0 <= wait_ns;) {
+            __nanosleep(ns);
+            ns = ns < 4096 ? 2 * ns : ns;
+            v = ld_acquire_u64(q - lane);
+        }
+    }
+    const uint64_t flag = v & ~kLookValue;
+    if (__any_sync(kFull, flag == kLookFailed || (block && flag == 0))) return kLookGaveUp;
+    if (__any_sync(kFull, flag == 0)) return kLookNotYet;
+    const uint32_t pref = __ballot_sync(kFull, flag == kLookPrefix);
+    const uint32_t stop = pref ? __ffs(pref) - 1 : 31;  // the nearest prefix
+    unsigned long long add = lane <= stop ? (v & kLookValue) : 0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(kFull, add, d);
+    sum += add;
+    found = pref != 0;
+    return kLookDone;
+}
+
+// One warp: the bytes before chunk c (of `size` bytes, published), from the
+// nearest published prefix; publishes c's prefix (and its group's, if c is
+// the group's last chunk) and returns kLookDone with the bytes in `excl`.
+// An entry not yet published: without `block`, kLookNotYet at once; with
+// `block`, waits for it.  Chunks take their numbers from a counter in the
+// order the warps start them, so every chunk (or group) waited for is being
+// coded by running warps, which publish sizes before they wait for anything:
+// each wait ends.  The waits of a call share the deadline now + wait_ns;
+// kLookGaveUp if it passed or a chunk before gave up (look[c] then says so).
+__device__ __forceinline__ LookResult chunk_offset(const LookBack &lb, uint32_t c, uint32_t size,
+                                                   uint32_t lane, bool block, uint64_t &excl) {
+    excl = 0;
+    if (c == 0) return kLookDone;
+    const uint64_t t0 = globaltimer_ns();
+    const uint32_t g = c / 32, i = c % 32;
+    uint64_t sum = 0;
+    bool found = false;
+    // The chunks before c in its group (lanes at or past i add nothing).
+    LookResult r = look_round(lb.look + (c - 1), lane < i, kLookSize, block, t0, lb.wait_ns, lane,
+                              sum, found);
+    // Then whole groups, nearest first (before group 0: the message start).
+    for (uint32_t j = g; r == kLookDone && !found; j -= 32)
+        r = look_round(lb.glook + (int64_t(j) - 1), j >= 1 + lane, kLookPrefix, block, t0,
+                       lb.wait_ns, lane, sum, found);
+    if (r == kLookGaveUp && lane == 0) st_release_u64(lb.look + c, kLookFailed);
+    if (r != kLookDone) return r;
+    excl = sum;
+    if (lane == 0) {
+        st_release_u64(lb.look + c, kLookPrefix | (sum + size));
+        if (i == 31 || c + 1 == lb.n_chunks) st_release_u64(lb.glook + g, kLookPrefix | (sum + size));
+    }
+    return kLookDone;
 }
 
 }  // namespace enc

@@ -1,6 +1,8 @@
 // rans_encode.cu -- single-message GPU encoder: one warp per chunk
-// (encode_core.cuh), then a one-CTA scan of the chunk sizes into the offset
-// table and header, then a copy that packs the chunks behind it.
+// (encode_core.cuh).  A whole message is coded and placed in one launch (each
+// warp finds its chunk's offset by look-back over the sizes before it and
+// copies the chunk into the message); pieces of a message (host-memory
+// encoding) use a scan of the chunk sizes and a separate copy.
 #include <algorithm>
 #include <mutex>
 
@@ -35,6 +37,14 @@ struct EncodeParams {
     const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
     uint64_t ctx_stride;  // u32 words per chunk in ctx
+    // Whole messages placed by the coder itself: the message and its size
+    // word, the look-back words and the chunk ticket (zeroed before the
+    // launch), the data region's offset, the version, and the wait bound.
+    uint8_t *out;
+    uint64_t *out_size;
+    enc::LookBack lb;
+    uint32_t *ticket;
+    uint32_t data0, version;
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
@@ -46,7 +56,54 @@ constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
 // Plain messages with M = 2^13 or 2^14 (16-byte table entries).
 constexpr int kWide = 4;
 
-template <int NT, int KIND>
+// PLACE: the next chunk number from the ticket counter (the order the warps
+// start their chunks), else chunks strided over the grid's warps.
+template <bool PLACE>
+__device__ __forceinline__ uint32_t next_chunk(const EncodeParams &p, uint32_t c, uint32_t lane) {
+    if (!PLACE) return c + gridDim.x * kWarps;
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(p.ticket, 1u);
+    return p.c_begin + __shfl_sync(kFull, t, 0);
+}
+
+// Chunk c is coded: wait until its slot's bulk stores have completed, report
+// a symbol without probability, publish the chunk's size.
+__device__ __forceinline__ void chunk_coded(const EncodeParams &p, uint32_t c, uint32_t lane,
+                                            uint32_t acc) {
+    if (lane == 0) {
+        bulk_wait<0>();
+        fence_proxy_async_global();
+    }
+    __syncwarp();
+    if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
+    enc::publish_size(p.lb, c, p.sizes[c], lane);
+}
+
+// Place coded chunk c: its offset by look-back, the offset table entry, the
+// chunk copied to its place, and -- for the message's last chunk -- the
+// header, the last offset, the padding and the message size.  Without
+// `block`, false (nothing done) if a chunk before it is not yet published.
+template <bool BYTES>
+__device__ __forceinline__ bool place_chunk(const EncodeParams &p, uint32_t c, uint32_t lane,
+                                            bool block) {
+    const uint32_t size = p.sizes[c];
+    uint64_t excl;
+    const enc::LookResult r = enc::chunk_offset(p.lb, c, size, lane, block, excl);
+    if (r == enc::kLookNotYet) return false;
+    if (r == enc::kLookGaveUp) {
+        if (lane == 0) report(p.status, RANS_ERR_TIMEOUT);
+        return true;
+    }
+    if (lane == 0) reinterpret_cast<uint32_t *>(p.out + 32)[c] = uint32_t(excl);
+    enc::pack_chunk_at<BYTES>(p.out, uint64_t(p.data0) + excl, p.words, p.states, p.wstart, p.N,
+                              p.slot_bytes, c, lane, 32);
+    if (c + 1 == p.n_chunks && lane == 0)
+        enc::write_header(p.out, p.out_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
+                          uint32_t(excl + size), p.version, p.log2m);
+    return true;
+}
+
+template <int NT, int KIND, bool PLACE = false>
 __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
@@ -64,8 +121,13 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
-    for (uint32_t c = p.c_begin + blockIdx.x * kWarps + warp; c < p.c_end;
-         c += gridDim.x * kWarps) {
+    // PLACE: a chunk whose offset was not yet known when it was coded is
+    // placed after the warp's next chunk (never waiting on chunks started
+    // after its own).
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    uint32_t pending = kNone;
+    for (uint32_t c = PLACE ? next_chunk<true>(p, 0, lane) : p.c_begin + blockIdx.x * kWarps + warp;
+         c < p.c_end; c = next_chunk<PLACE>(p, c, lane)) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
         uint32_t *ctx = ADAPT ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
@@ -74,7 +136,13 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
             p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
             acc, RAW ? p.raw + first : nullptr, ctx);
+        if (PLACE) {
+            chunk_coded(p, c, lane, acc);
+            if (pending != kNone) place_chunk<BYTES>(p, pending, lane, true);
+            pending = place_chunk<BYTES>(p, c, lane, false) ? kNone : c;
+        }
     }
+    if (PLACE && pending != kNone) place_chunk<BYTES>(p, pending, lane, true);
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
     if (lane == 0) bulk_wait<0>();
@@ -84,16 +152,22 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
 // 64 registers or fewer (four CTAs per SM); asking for a minimum of one CTA
 // per SM lets the compiler spend more and costs a CTA per SM.  Adaptive
 // chunks need the explicit bound of four CTAs per SM.
-template <int NT, int KIND>
+template <int NT, int KIND, bool PLACE>
 __global__ void __launch_bounds__(enc::kThreads)
     encode_kernel(const __grid_constant__ EncodeParams p) {
-    encode_body<NT, KIND>(p);
+    encode_body<NT, KIND, PLACE>(p);
 }
 
-template <int NT>
+template <int NT, bool PLACE>
 __global__ void __launch_bounds__(enc::kThreads, 4)
     encode_kernel_adaptive(const __grid_constant__ EncodeParams p) {
-    encode_body<NT, kAdaptive>(p);
+    encode_body<NT, kAdaptive, PLACE>(p);
+}
+
+// After a placing launch: a rejected message has size 0 (the last chunk may
+// have written the header before another chunk reported).
+__global__ void settle_kernel(const uint32_t *status, uint64_t *out_size) {
+    if (*status != RANS_OK) *out_size = 0;
 }
 
 struct FinalizeParams {
@@ -138,11 +212,11 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
                                p.offs);
 }
 
-template <int NT, int KIND>
+template <int NT, int KIND, bool PLACE = false>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     void (*kernel)(EncodeParams);
-    if constexpr (KIND == kAdaptive) kernel = encode_kernel_adaptive<NT>;
-    else kernel = encode_kernel<NT, KIND>;
+    if constexpr (KIND == kAdaptive) kernel = encode_kernel_adaptive<NT, PLACE>;
+    else kernel = encode_kernel<NT, KIND, PLACE>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, kSmemBytes) !=
             cudaSuccess ||
@@ -152,6 +226,61 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     kernel<<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    return check_launch();
+}
+
+// Code and place a whole message of n_chunks > 0 chunks (ep complete but for
+// the placement fields): zero the look-back words and the ticket, launch the
+// placing coder, then settle the size.
+int encode_placed(EncodeParams &ep, const ScratchLayout &sl, uint8_t *scr, uint8_t *d_out,
+                  uint64_t *d_out_size, uint32_t data0, uint32_t version, int kind,
+                  cudaStream_t st) {
+    ep.out = d_out;
+    ep.out_size = d_out_size;
+    ep.lb.look = reinterpret_cast<uint64_t *>(scr + sl.look);
+    ep.lb.glook = reinterpret_cast<uint64_t *>(scr + sl.glook);
+    ep.lb.gacc = reinterpret_cast<uint64_t *>(scr + sl.gacc);
+    ep.lb.n_chunks = ep.n_chunks;
+    // Every wait ends once the chunks started before it are coded: allow a
+    // second plus a microsecond per step of a chunk (several times the
+    // coding time of one chunk on a loaded GPU).
+    ep.lb.wait_ns = 1000000000ull + 1000ull * (ep.CS / ep.N + 1);
+    ep.ticket = reinterpret_cast<uint32_t *>(scr + sl.ticket);
+    ep.data0 = data0;
+    ep.version = version;
+    ep.c_begin = 0;  // the placed coder always covers the whole message
+    if (cudaMemsetAsync(scr + sl.look, 0, sl.total - sl.look, st) != cudaSuccess)
+        return RANS_ERR_CUDA;
+    const bool n32 = ep.N == 32;
+    int rc;
+    switch (kind) {
+        case kWide: rc = n32 ? launch_encode<32, kWide, true>(ep, st) : launch_encode<0, kWide, true>(ep, st); break;
+        case kAdaptive: rc = n32 ? launch_encode<32, kAdaptive, true>(ep, st) : launch_encode<0, kAdaptive, true>(ep, st); break;
+        case kBypass: rc = n32 ? launch_encode<32, kBypass, true>(ep, st) : launch_encode<0, kBypass, true>(ep, st); break;
+        case kBytes: rc = n32 ? launch_encode<32, kBytes, true>(ep, st) : launch_encode<0, kBytes, true>(ep, st); break;
+        default: rc = n32 ? launch_encode<32, kPlain, true>(ep, st) : launch_encode<0, kPlain, true>(ep, st); break;
+    }
+    if (rc != RANS_OK) return rc;
+    settle_kernel<<<1, 1, 0, st>>>(ep.status, d_out_size);
+    return check_launch();
+}
+
+// The header of a message without chunks.
+int encode_empty(uint8_t *d_out, uint64_t *d_out_size, uint32_t *d_status, uint64_t n_sym,
+                 const rans_params *params, uint32_t data0, uint32_t version, uint32_t log2m,
+                 cudaStream_t st) {
+    FinalizeParams fp{};
+    fp.out = d_out;
+    fp.out_size = d_out_size;
+    fp.status = d_status;
+    fp.n_sym = n_sym;
+    fp.N = params->n_lanes;
+    fp.CS = params->chunk_symbols;
+    fp.n_chunks = 0;
+    fp.data0 = data0;
+    fp.version = version;
+    fp.log2m = log2m;
+    finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
     return check_launch();
 }
 
@@ -241,54 +370,19 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.log2m = lm;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
-    if (g.n_chunks > 0) {
-        int rc;
-        if (lm != RANS_LOG2_M)
-            rc = ep.N == 32 ? launch_encode<32, kWide>(ep, st) : launch_encode<0, kWide>(ep, st);
-        else if (adaptive)
-            rc = ep.N == 32 ? launch_encode<32, kAdaptive>(ep, st) : launch_encode<0, kAdaptive>(ep, st);
-        else if (bypass)
-            rc = ep.N == 32 ? launch_encode<32, kBypass>(ep, st) : launch_encode<0, kBypass>(ep, st);
-        else if (bytes)
-            rc = ep.N == 32 ? launch_encode<32, kBytes>(ep, st) : launch_encode<0, kBytes>(ep, st);
-        else
-            rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
-        if (rc != RANS_OK) return rc;
-    }
-    FinalizeParams fp{};
-    fp.out = d_out;
-    fp.out_size = d_out_size;
-    fp.sizes = ep.sizes;
-    fp.status = d_status;
-    fp.n_sym = n_symbols;
-    fp.N = ep.N;
-    fp.CS = ep.CS;
-    fp.n_chunks = ep.n_chunks;
-    fp.data0 = uint32_t(g.data0);
-    fp.version = bypass ? RANS_VERSION_BYPASS : bytes ? RANS_VERSION_BYTES
-                 : adaptive ? RANS_VERSION_ADAPTIVE : RANS_VERSION;
-    fp.log2m = lm;
-    finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
-    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    if (g.n_chunks > 0) {
-        PackParams pp{};
-        pp.out = d_out;
-        pp.words = ep.words;
-        pp.states = ep.states;
-        pp.wstart = ep.wstart;
-        pp.status = d_status;
-        pp.N = ep.N;
-        pp.n_chunks = ep.n_chunks;
-        pp.data0 = fp.data0;
-        pp.slot_bytes = ep.slot_bytes;
-        pp.c_begin = 0;
-        pp.c_end = ep.n_chunks;
-        const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
-        if (bytes) pack_kernel<true><<<grid, kPackThreads, 0, st>>>(pp);
-        else pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
-        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    }
-    return RANS_OK;
+    const uint32_t version = bypass     ? RANS_VERSION_BYPASS
+                             : bytes    ? RANS_VERSION_BYTES
+                             : adaptive ? RANS_VERSION_ADAPTIVE
+                                        : RANS_VERSION;
+    if (g.n_chunks == 0)
+        return encode_empty(d_out, d_out_size, d_status, n_symbols, params, uint32_t(g.data0),
+                            version, lm, st);
+    const int kind = lm != RANS_LOG2_M ? kWide
+                     : adaptive        ? kAdaptive
+                     : bypass          ? kBypass
+                     : bytes           ? kBytes
+                                       : kPlain;
+    return encode_placed(ep, sl, scr, d_out, d_out_size, uint32_t(g.data0), version, kind, st);
 }
 
 extern "C" uint64_t rans_encode_scratch_size_adaptive(uint64_t n_symbols, const rans_params *params) {
@@ -390,8 +484,9 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     uint8_t *scr = nullptr;
     if (static_scratch_address(&scr) != RANS_OK) return RANS_ERR_CUDA;
 
-    // Nothing in the scratch has to start at zero: the coder writes every
-    // word, state, size and offset before the later kernels read them.
+    // Only the look-back words and the ticket start at zero (encode_placed
+    // clears them): the coder writes every word, state, size and offset
+    // before they are read.
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
 
@@ -409,43 +504,13 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     ep.slot_bytes = sl.slot_bytes;
     ep.c_begin = 0;
     ep.c_end = ep.n_chunks;
+    ep.log2m = RANS_LOG2_M;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
-    if (g.n_chunks > 0) {
-        const int rc = ep.N == 32 ? launch_encode<32, kPlain>(ep, st) : launch_encode<0, kPlain>(ep, st);
-        if (rc != RANS_OK) return rc;
-    }
-    FinalizeParams fp{};
-    fp.out = d_out;
-    fp.out_size = d_out_size;
-    fp.sizes = ep.sizes;
-    fp.status = d_status;
-    fp.n_sym = n_symbols;
-    fp.N = ep.N;
-    fp.CS = ep.CS;
-    fp.n_chunks = ep.n_chunks;
-    fp.data0 = uint32_t(g.data0);
-    fp.version = RANS_VERSION;
-    fp.log2m = RANS_LOG2_M;
-    finalize_kernel<<<1, kScanThreads, 0, st>>>(fp);
-    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    if (g.n_chunks > 0) {
-        PackParams pp{};
-        pp.out = d_out;
-        pp.words = ep.words;
-        pp.states = ep.states;
-        pp.wstart = ep.wstart;
-        pp.status = d_status;
-        pp.N = ep.N;
-        pp.n_chunks = ep.n_chunks;
-        pp.data0 = fp.data0;
-        pp.slot_bytes = ep.slot_bytes;
-        pp.c_begin = 0;
-        pp.c_end = ep.n_chunks;
-        const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
-        pack_kernel<false><<<grid, kPackThreads, 0, st>>>(pp);
-        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    }
-    return RANS_OK;
+    if (g.n_chunks == 0)
+        return encode_empty(d_out, d_out_size, d_status, n_symbols, params, uint32_t(g.data0),
+                            RANS_VERSION, RANS_LOG2_M, st);
+    return encode_placed(ep, sl, scr, d_out, d_out_size, uint32_t(g.data0), RANS_VERSION, kPlain,
+                         st);
 }
 
 // ---------------------------------------------------------------------------
