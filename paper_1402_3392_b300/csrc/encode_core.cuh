@@ -699,29 +699,43 @@ __device__ __forceinline__ void finalize_message(uint8_t *out, uint64_t *out_siz
 // destination is only 2-byte aligned, so whole 16-byte destination blocks are
 // assembled from two aligned 16-byte source loads and a funnel shift (the
 // source-to-destination shift is the same for every block of a chunk); the
-// partial blocks at both ends are written in 16-bit units.  Two blocks per
-// thread are in flight.  Source loads go through L2 only (ld.global.cg): the
-// words arrived there by bulk copies in the same launch.
-template <int K>  // K = (source shift in bytes) / 4; rs = 8 * (shift mod 4)
+// partial blocks at both ends are written in 16-bit units.  U blocks per
+// thread are in flight.  L2: source loads go through L2 only (ld.global.cg),
+// for words that arrived there by bulk copies in the same launch.
+template <bool L2>
+__device__ __forceinline__ uint4 ld_src16(const uint8_t *p) {
+    return L2 ? __ldcg(reinterpret_cast<const uint4 *>(p)) : *reinterpret_cast<const uint4 *>(p);
+}
+template <bool L2>
+__device__ __forceinline__ uint16_t ld_src2(const uint8_t *p) {
+    return L2 ? __ldcg(reinterpret_cast<const unsigned short *>(p))
+              : *reinterpret_cast<const uint16_t *>(p);
+}
+template <bool L2>
+__device__ __forceinline__ uint8_t ld_src1(const uint8_t *p) {
+    return L2 ? uint8_t(__ldcg(reinterpret_cast<const unsigned char *>(p))) : *p;
+}
+
+template <int K, int U, bool L2>  // K = (source shift in bytes) / 4; rs = 8 * (shift mod 4)
 __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, uint64_t B0,
                                             uint64_t B1, uint64_t s_minus_d, uint32_t rs,
                                             uint32_t t, uint32_t nt) {
     const bool need_hi = K > 0 || rs != 0;
     const uint64_t stride = 16ull * nt;
-    for (uint64_t B = B0 + 16ull * t; B < B1; B += 2 * stride) {
-        uint4 v[2][2];
+    for (uint64_t B = B0 + 16ull * t; B < B1; B += U * stride) {
+        uint4 v[U][2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint64_t Bu = B + u * stride;
             const uint64_t sa = (Bu + s_minus_d) & ~uint64_t(15);
             v[u][0] = v[u][1] = make_uint4(0u, 0u, 0u, 0u);
             if (Bu < B1) {
-                v[u][0] = __ldcg(reinterpret_cast<const uint4 *>(src + sa));
-                if (need_hi) v[u][1] = __ldcg(reinterpret_cast<const uint4 *>(src + sa + 16));
+                v[u][0] = ld_src16<L2>(src + sa);
+                if (need_hi) v[u][1] = ld_src16<L2>(src + sa + 16);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint64_t Bu = B + u * stride;
             if (Bu >= B1) break;
             const uint32_t w[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w,
@@ -740,8 +754,9 @@ __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, ui
 // wstart) into out at message byte D.  The words buffer must have 16
 // readable bytes past its last slot.
 // BYTES: the chunk's byte count may be odd and its start in the slot too;
-// the chunk is padded with zeros to a multiple of 4 bytes.
-template <bool BYTES = false>
+// the chunk is padded with zeros to a multiple of 4 bytes.  U: 16-byte
+// blocks in flight per thread; L2: loads through L2 only (ld_src16).
+template <bool BYTES, int U, bool L2>
 __device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const uint8_t *words,
                                               const uint32_t *states, const uint32_t *wstart,
                                               uint32_t N, uint32_t slot_bytes, uint32_t c,
@@ -757,32 +772,30 @@ __device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const ui
     const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
     const uint64_t head_end = B0 < d1 ? B0 : d1;
     if (BYTES) {
-        for (uint64_t b = d0 + t; b < head_end; b += nt) out[b] = __ldcg(words + s0 + (b - d0));
+        for (uint64_t b = d0 + t; b < head_end; b += nt) out[b] = ld_src1<L2>(words + s0 + (b - d0));
     } else {
         for (uint64_t b = d0 + 2ull * t; b < head_end; b += 2ull * nt)
-            *reinterpret_cast<uint16_t *>(out + b) =
-                __ldcg(reinterpret_cast<const uint16_t *>(words + s0 + (b - d0)));
+            *reinterpret_cast<uint16_t *>(out + b) = ld_src2<L2>(words + s0 + (b - d0));
     }
     if (B0 < B1) {
         const uint64_t s_minus_d = s0 - d0;  // modulo 2^64
         const uint32_t sh = uint32_t(s_minus_d & 15u);
         const uint32_t rs = 8u * (sh & 3u);
         switch (sh >> 2) {
-            case 0: pack_blocks<0>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
-            case 1: pack_blocks<1>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
-            case 2: pack_blocks<2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
-            default: pack_blocks<3>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            case 0: pack_blocks<0, U, L2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            case 1: pack_blocks<1, U, L2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            case 2: pack_blocks<2, U, L2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
+            default: pack_blocks<3, U, L2>(out, words, B0, B1, s_minus_d, rs, t, nt); break;
         }
     }
     const uint64_t tail_start = B1 > head_end ? B1 : head_end;
     if (BYTES) {
-        for (uint64_t b = tail_start + t; b < d1; b += nt) out[b] = __ldcg(words + s0 + (b - d0));
+        for (uint64_t b = tail_start + t; b < d1; b += nt) out[b] = ld_src1<L2>(words + s0 + (b - d0));
         const uint64_t end = D + ((d1 - D + 3) & ~uint64_t(3));
         for (uint64_t b = d1 + t; b < end; b += nt) out[b] = 0;
     } else {
         for (uint64_t b = tail_start + 2ull * t; b < d1; b += 2ull * nt)
-            *reinterpret_cast<uint16_t *>(out + b) =
-                __ldcg(reinterpret_cast<const uint16_t *>(words + s0 + (b - d0)));
+            *reinterpret_cast<uint16_t *>(out + b) = ld_src2<L2>(words + s0 + (b - d0));
     }
 }
 
@@ -794,8 +807,8 @@ __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const u
                                            uint32_t N, uint32_t slot_bytes, uint32_t c,
                                            const uint32_t *offs_in = nullptr) {
     const uint32_t *offs = offs_in ? offs_in : reinterpret_cast<const uint32_t *>(out + 32);
-    pack_chunk_at<BYTES>(out, uint64_t(data0) + offs[c], words, states, wstart, N, slot_bytes, c,
-                         threadIdx.x, blockDim.x);
+    pack_chunk_at<BYTES, 1, false>(out, uint64_t(data0) + offs[c], words, states, wstart, N,
+                                   slot_bytes, c, threadIdx.x, blockDim.x);
 }
 
 // ---- single-pass placement: decoupled look-back over the chunk sizes -------

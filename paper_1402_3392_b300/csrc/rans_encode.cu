@@ -83,7 +83,9 @@ __device__ __forceinline__ void chunk_coded(const EncodeParams &p, uint32_t c, u
 // chunk copied to its place, and -- for the message's last chunk -- the
 // header, the last offset, the padding and the message size.  Without
 // `block`, false (nothing done) if a chunk before it is not yet published.
-template <bool BYTES>
+// U: 16-byte blocks each lane copies at a time (2 keeps the adaptive coder
+// within its 64 registers).
+template <bool BYTES, int U>
 __device__ __forceinline__ bool place_chunk(const EncodeParams &p, uint32_t c, uint32_t lane,
                                             bool block) {
     const uint32_t size = p.sizes[c];
@@ -95,8 +97,8 @@ __device__ __forceinline__ bool place_chunk(const EncodeParams &p, uint32_t c, u
         return true;
     }
     if (lane == 0) reinterpret_cast<uint32_t *>(p.out + 32)[c] = uint32_t(excl);
-    enc::pack_chunk_at<BYTES>(p.out, uint64_t(p.data0) + excl, p.words, p.states, p.wstart, p.N,
-                              p.slot_bytes, c, lane, 32);
+    enc::pack_chunk_at<BYTES, U, true>(p.out, uint64_t(p.data0) + excl, p.words, p.states, p.wstart,
+                                 p.N, p.slot_bytes, c, lane, 32);
     if (c + 1 == p.n_chunks && lane == 0)
         enc::write_header(p.out, p.out_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
                           uint32_t(excl + size), p.version, p.log2m);
@@ -125,6 +127,7 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     // placed after the warp's next chunk (never waiting on chunks started
     // after its own).
     constexpr uint32_t kNone = 0xFFFFFFFFu;
+    constexpr int kCopyU = ADAPT ? 2 : 4;
     uint32_t pending = kNone;
     for (uint32_t c = PLACE ? next_chunk<true>(p, 0, lane) : p.c_begin + blockIdx.x * kWarps + warp;
          c < p.c_end; c = next_chunk<PLACE>(p, c, lane)) {
@@ -138,11 +141,11 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
             acc, RAW ? p.raw + first : nullptr, ctx);
         if (PLACE) {
             chunk_coded(p, c, lane, acc);
-            if (pending != kNone) place_chunk<BYTES>(p, pending, lane, true);
-            pending = place_chunk<BYTES>(p, c, lane, false) ? kNone : c;
+            if (pending != kNone) place_chunk<BYTES, kCopyU>(p, pending, lane, true);
+            pending = place_chunk<BYTES, kCopyU>(p, c, lane, false) ? kNone : c;
         }
     }
-    if (PLACE && pending != kNone) place_chunk<BYTES>(p, pending, lane, true);
+    if (PLACE && pending != kNone) place_chunk<BYTES, kCopyU>(p, pending, lane, true);
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
     if (lane == 0) bulk_wait<0>();
