@@ -812,6 +812,21 @@ __device__ __forceinline__ void pack_chunk(uint8_t *out, uint32_t data0, const u
 }
 
 // ---- single-pass placement: decoupled look-back over the chunk sizes -------
+// Order completed async-proxy (bulk copy) writes to global memory before the
+// issuing thread's later generic-proxy accesses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Publication between CTAs: release / acquire at GPU scope.
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // look[c] holds a flag in its top two bits and a byte count below them:
 // kLookSize = chunk c's own size, kLookPrefix = the bytes of chunks 0..c
 // (inclusive prefix), kLookFailed = a wait before it gave up; zero: nothing

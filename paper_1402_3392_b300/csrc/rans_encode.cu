@@ -72,7 +72,7 @@ __device__ __forceinline__ void chunk_coded(const EncodeParams &p, uint32_t c, u
                                             uint32_t acc) {
     if (lane == 0) {
         bulk_wait<0>();
-        fence_proxy_async_global();
+        enc::fence_proxy_async_global();
     }
     __syncwarp();
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
