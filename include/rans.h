@@ -567,6 +567,23 @@ int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_symbols,
 int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream);
 
 /*
+ * rans_check_lookback_wait -- diagnostic of the failure path; no step of the
+ * paper's method.  rans_encode (and the other whole-message encoders) find
+ * each chunk's offset by waiting, bounded, for the sizes of the chunks
+ * before it.  This launches one warp that runs that look-back for chunk 1 of
+ * a two-chunk message whose chunk 0 never publishes its size, with a 200 ms
+ * bound: the look-back gives up, marks its chunk failed (so that later
+ * chunks give up at once), and the kernel writes RANS_ERR_TIMEOUT to
+ * *d_status (RANS_OK if the look-back ended any other way).
+ *
+ * d_status : device u32, overwritten.  Returns RANS_OK when the kernel was
+ * enqueued, RANS_ERR_INVALID_ARG for a null d_status, RANS_ERR_CUDA on a
+ * launch error.  The kernel takes about 200 ms of GPU time; calls must not
+ * overlap (they share one small device array).
+ */
+int rans_check_lookback_wait(uint32_t *d_status, rans_stream_t stream);
+
+/*
  * Checked builds (a test build compiled with -DRANS_CHECKED; the library
  * built normally answers RANS_ERR_INVALID_ARG to both calls).  The kernels
  * then test their invariants as they run and count the ones that fail (the

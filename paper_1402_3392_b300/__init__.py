@@ -10,7 +10,7 @@ _BINDING = frozenset({
     "rans_max_encoded_size", "rans_encode_scratch_size", "rans_encode", "rans_decode",
     "rans_encode_static_scratch", "encode", "decode", "rans_decode_batch",
     "rans_decode_batch_scratch_size", "rans_encode_batch", "rans_encode_batch_plan",
-    "rans_check_bounded_wait", "rans_decode_host", "rans_decode_host_work_size", "decode_host",
+    "rans_check_bounded_wait", "rans_check_lookback_wait", "rans_decode_host", "rans_decode_host_work_size", "decode_host",
     "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass", "rans_encode_bypass",
     "rans_decode_bypass", "encode_bypass", "decode_bypass", "rans_max_encoded_size_bytes",
     "rans_encode_bytes", "rans_decode_bytes", "encode_bytes", "decode_bytes",

@@ -28,8 +28,8 @@ __all__ = [
     "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
     "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
-    "Server", "rans_check_bounded_wait", "rans_decode_host", "rans_decode_host_work_size",
-    "decode_host", "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass",
+    "Server", "rans_check_bounded_wait", "rans_check_lookback_wait", "rans_decode_host",
+    "rans_decode_host_work_size", "decode_host", "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass",
     "rans_encode_bypass", "rans_decode_bypass", "encode_bypass", "decode_bypass",
     "rans_max_encoded_size_bytes", "rans_encode_bytes", "rans_decode_bytes", "encode_bytes",
     "decode_bytes",
@@ -101,6 +101,7 @@ def _load() -> C.CDLL:
         "rans_decode": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp]),
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
         "rans_check_bounded_wait": (i32, [vp, vp]),
+        "rans_check_lookback_wait": (i32, [vp, vp]),
         "rans_debug_checks": (i32, [vp]),
         "rans_debug_check_selftest": (i32, [vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
@@ -624,6 +625,13 @@ def rans_check_bounded_wait(d_status, stream=None, check=True) -> int:
     completes gives up after about 200 ms and writes RANS_ERR_TIMEOUT."""
     rc = lib.rans_check_bounded_wait(_ptr(d_status), _stream(stream))
     return _check(rc, "rans_check_bounded_wait") if check else rc
+
+
+def rans_check_lookback_wait(d_status, stream=None, check=True) -> int:
+    """Diagnostic: the encoder's look-back for a chunk whose predecessor never
+    publishes gives up after about 200 ms and writes RANS_ERR_TIMEOUT."""
+    rc = lib.rans_check_lookback_wait(_ptr(d_status), _stream(stream))
+    return _check(rc, "rans_check_lookback_wait") if check else rc
 
 
 def rans_encode_static_scratch(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out,
