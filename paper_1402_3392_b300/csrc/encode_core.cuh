@@ -864,6 +864,12 @@ __device__ __forceinline__ void publish_size(const LookBack &lb, uint32_t c, uin
     }
 }
 
+// One warp: chunk c will never be coded (its stream was rejected); chunks
+// after it give up at once instead of waiting for it.
+__device__ __forceinline__ void publish_failed(const LookBack &lb, uint32_t c, uint32_t lane) {
+    if (lane == 0) st_release_u64(lb.look + c, kLookFailed);
+}
+
 enum LookResult : uint32_t { kLookDone, kLookNotYet, kLookGaveUp };
 
 // One round of a look-back: lane i reads entry q - i (own = the lane has an
@@ -926,6 +932,74 @@ __device__ __forceinline__ LookResult chunk_offset(const LookBack &lb, uint32_t 
         if (i == 31 || c + 1 == lb.n_chunks) st_release_u64(lb.glook + g, kLookPrefix | (sum + size));
     }
     return kLookDone;
+}
+
+// A message whose coder warps place its chunks themselves.
+struct Placement {
+    uint8_t *out;
+    uint64_t *out_size;
+    uint32_t *status;
+    const uint8_t *words;      // the chunk slots
+    const uint32_t *states;    // N final states per chunk
+    const uint32_t *wstart;    // first word byte of each slot
+    const uint32_t *sizes;     // chunk bytes
+    LookBack lb;               // look-back words, n_chunks, wait bound
+    uint64_t n_sym;
+    uint32_t N, CS, data0, slot_bytes, version, log2m;
+};
+
+// Chunk c is coded (its slot, state, start and size written by this warp):
+// wait until the slot's bulk stores have completed, report a symbol without
+// probability (acc), publish the chunk's size.
+__device__ __forceinline__ void chunk_coded(const Placement &m, uint32_t c, uint32_t lane,
+                                            uint32_t acc) {
+    if (lane == 0) {
+        bulk_wait<0>();
+        fence_proxy_async_global();
+    }
+    __syncwarp();
+    if (__any_sync(kFull, acc & kZeroFlag) && lane == 0) report(m.status, RANS_ERR_ZERO_FREQ);
+    publish_size(m.lb, c, m.sizes[c], lane);
+}
+
+// Place coded chunk c: its offset by look-back, the offset table entry, the
+// chunk copied to its place, and -- for the message's last chunk -- the
+// header, the last offset, the padding and the message size.  Without
+// `block`, false (nothing done) if a chunk before it is not yet published.
+// U: 16-byte blocks each lane copies at a time.
+template <bool BYTES, int U>
+__device__ __forceinline__ bool place_chunk(const Placement &m, uint32_t c, uint32_t lane,
+                                            bool block) {
+    const uint32_t size = m.sizes[c];
+    uint64_t excl;
+    const LookResult r = chunk_offset(m.lb, c, size, lane, block, excl);
+    if (r == kLookNotYet) return false;
+    if (r == kLookGaveUp) {
+        if (lane == 0) report(m.status, RANS_ERR_TIMEOUT);
+        return true;
+    }
+    if (lane == 0) reinterpret_cast<uint32_t *>(m.out + 32)[c] = uint32_t(excl);
+    pack_chunk_at<BYTES, U, true>(m.out, uint64_t(m.data0) + excl, m.words, m.states, m.wstart,
+                                  m.N, m.slot_bytes, c, lane, 32);
+    if (c + 1 == m.lb.n_chunks && lane == 0)
+        write_header(m.out, m.out_size, m.n_sym, m.N, m.CS, m.lb.n_chunks, m.data0,
+                     uint32_t(excl + size), m.version, m.log2m);
+    return true;
+}
+
+// The look-back words of a message's scratch (zeroed before its launch).
+__host__ __device__ inline LookBack scratch_lookback(uint8_t *scr, const ScratchLayout &sl,
+                                                     uint32_t n_chunks, uint32_t CS, uint32_t N) {
+    LookBack lb;
+    lb.look = reinterpret_cast<uint64_t *>(scr + sl.look);
+    lb.glook = reinterpret_cast<uint64_t *>(scr + sl.glook);
+    lb.gacc = reinterpret_cast<uint64_t *>(scr + sl.gacc);
+    lb.n_chunks = n_chunks;
+    // Every wait ends once the chunks started before it are coded: allow a
+    // second plus a microsecond per step of a chunk (several times the
+    // coding time of one chunk on a loaded GPU).
+    lb.wait_ns = 1000000000ull + 1000ull * (CS / N + 1);
+    return lb;
 }
 
 }  // namespace enc

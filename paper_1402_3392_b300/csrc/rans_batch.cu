@@ -219,7 +219,7 @@ struct BatchEncodeParams {
     uint8_t *scratch;
     uint64_t scratch_cap;
     uint32_t *items;    // n_streams + 1 work-item offsets
-    uint32_t *chunks;   // n_streams + 1 chunk offsets (for packing)
+    uint32_t *chunks;   // n_streams + 1 chunk offsets (the batch's chunk count at the end)
     uint32_t *counter;
     uint32_t n_streams;
     uint32_t n_tables;
@@ -329,6 +329,87 @@ __device__ __forceinline__ uint32_t find_stream(const uint32_t *prefix, uint32_t
     return lo;
 }
 
+// Stream s's message as its coder warps place it (descriptor d, geometry g).
+__device__ __forceinline__ enc::Placement stream_placement(const BatchEncodeParams &p, uint32_t s,
+                                                           const rans_encode_stream &d,
+                                                           const EncGeom &g) {
+    uint8_t *scr = p.scratch + d.scratch_offset;
+    enc::Placement m;
+    m.out = d.out;
+    m.out_size = p.out_sizes + s;
+    m.status = p.status + s;
+    m.words = scr + g.sl.words;
+    m.states = reinterpret_cast<const uint32_t *>(scr + g.sl.states);
+    m.wstart = reinterpret_cast<const uint32_t *>(scr + g.sl.wstart);
+    m.sizes = reinterpret_cast<const uint32_t *>(scr + g.sl.sizes);
+    m.lb = enc::scratch_lookback(scr, g.sl, uint32_t(g.n_chunks), d.chunk_symbols, d.n_lanes);
+    m.n_sym = d.n_symbols;
+    m.N = d.n_lanes;
+    m.CS = d.chunk_symbols;
+    m.data0 = g.data0;
+    m.slot_bytes = g.sl.slot_bytes;
+    m.version = RANS_VERSION;
+    m.log2m = kLog2M;
+    return m;
+}
+
+// Chunk c of stream s is coded (acc: the table flags it met): publish it and
+// place it if every chunk before it is published (false: not yet).  Out of
+// line, so that the coding loop keeps its registers.
+__device__ __noinline__ bool coded_and_placed(const BatchEncodeParams &p, uint32_t s, uint32_t c,
+                                              uint32_t lane, uint32_t acc) {
+    const rans_encode_stream d = p.streams[s];
+    const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+    const enc::Placement m = stream_placement(p, s, d, g);
+    enc::chunk_coded(m, c, lane, acc);
+    return enc::place_chunk<false, 4>(m, c, lane, false);
+}
+
+// Place coded chunk c of stream s, waiting (bounded) for the chunks before it.
+__device__ __noinline__ void place_pending(const BatchEncodeParams &p, uint32_t s, uint32_t c,
+                                           uint32_t lane) {
+    const rans_encode_stream d = p.streams[s];
+    const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+    enc::place_chunk<false, 4>(stream_placement(p, s, d, g), c, lane, true);
+}
+
+// One CTA per stream (grid-stride): zero the look-back words and ticket of
+// every accepted stream's scratch.
+constexpr int kClearThreads = 256;
+__global__ void __launch_bounds__(kClearThreads)
+    enc_clear_kernel(const __grid_constant__ BatchEncodeParams p) {
+    for (uint32_t s = blockIdx.x; s < p.n_streams; s += gridDim.x) {
+        if (p.status[s] != RANS_OK) continue;
+        const rans_encode_stream d = p.streams[s];
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        uint4 *w = reinterpret_cast<uint4 *>(p.scratch + d.scratch_offset + g.sl.look);
+        const uint64_t n = (g.sl.total - g.sl.look) / 16;
+        for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) w[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// After the placing coder: a rejected stream's size is 0; an accepted stream
+// without chunks gets its header here.
+__global__ void __launch_bounds__(kClearThreads)
+    enc_settle_kernel(const __grid_constant__ BatchEncodeParams p) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < p.n_streams;
+         s += gridDim.x * blockDim.x) {
+        if (p.status[s] != RANS_OK) {
+            p.out_sizes[s] = 0;
+            continue;
+        }
+        const rans_encode_stream d = p.streams[s];
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        if (g.n_chunks == 0)
+            enc::write_header(d.out, p.out_sizes + s, d.n_symbols, d.n_lanes, d.chunk_symbols, 0,
+                              g.data0, 0, RANS_VERSION);
+    }
+}
+
+// Persistent: CTAs take work items (8 chunks of one stream, one per warp) in
+// order from a counter.  Each warp codes its chunk, publishes the chunk's
+// size and places it -- at once if every chunk before it is published, else
+// after the warp's next chunk (waiting only for chunks taken earlier).
 __global__ void __launch_bounds__(enc::kThreads, 4)
     batch_encode_kernel(const __grid_constant__ BatchEncodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -342,6 +423,8 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     const uint32_t total = p.items[p.n_streams];
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    uint32_t pend_s = kNone, pend_c = 0;  // a coded chunk not yet placed
     for (;;) {
         __syncthreads();  // every warp is done with the previous item
         if (threadIdx.x == 0) {
@@ -363,12 +446,19 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             }
             __syncthreads();
         }
-        if (!model_ok) {
-            if (threadIdx.x == 0) report(p.status + s, RANS_ERR_INVALID_ARG);
-            continue;
-        }
         const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
         const uint32_t c = (it - p.items[s]) * enc::kWarps + warp;
+        if (!model_ok) {
+            if (threadIdx.x == 0) report(p.status + s, RANS_ERR_INVALID_ARG);
+            if (c < g.n_chunks) {
+                uint8_t *scr = p.scratch + d.scratch_offset;
+                enc::publish_failed(
+                    enc::scratch_lookback(scr, g.sl, uint32_t(g.n_chunks), d.chunk_symbols, d.n_lanes),
+                    c, lane);
+            }
+            continue;
+        }
+        bool coded = false, placed = false;
         if (c < g.n_chunks) {
             uint8_t *scr = p.scratch + d.scratch_offset;
             const uint64_t first = uint64_t(c) * d.chunk_symbols;
@@ -384,49 +474,20 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             else
                 enc::encode_chunk<0, false>(d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart,
                                      sizes, states, sm.tab_s, ring_s, ge, lane, acc);
-            if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0)
-                report(p.status + s, RANS_ERR_ZERO_FREQ);
+            placed = coded_and_placed(p, s, c, lane, acc);
+            coded = true;
+        }
+        if (pend_s != kNone) {
+            place_pending(p, pend_s, pend_c, lane);
+            pend_s = kNone;
+        }
+        if (coded && !placed) {
+            pend_s = s;
+            pend_c = c;
         }
     }
+    if (pend_s != kNone) place_pending(p, pend_s, pend_c, lane);
     if (lane == 0) bulk_wait<0>();
-}
-
-constexpr int kFinThreads = 256;
-__global__ void __launch_bounds__(kFinThreads)
-    enc_finalize_kernel(const __grid_constant__ BatchEncodeParams p) {
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint64_t carry_s;
-    for (uint32_t s = blockIdx.x; s < p.n_streams; s += gridDim.x) {
-        const uint32_t st = p.status[s];
-        if (st != RANS_OK) {
-            if (threadIdx.x == 0) p.out_sizes[s] = 0;
-            continue;
-        }
-        const rans_encode_stream d = p.streams[s];
-        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
-        const uint8_t *scr = p.scratch + d.scratch_offset;
-        enc::finalize_message(d.out, p.out_sizes + s, reinterpret_cast<const uint32_t *>(scr + g.sl.sizes),
-                              d.n_symbols, d.n_lanes, d.chunk_symbols, uint32_t(g.n_chunks), g.data0,
-                              warp_sums, &carry_s);
-        __syncthreads();
-    }
-}
-
-constexpr int kEncPackThreads = 256;
-__global__ void __launch_bounds__(kEncPackThreads)
-    enc_pack_kernel(const __grid_constant__ BatchEncodeParams p) {
-    const uint32_t total = p.chunks[p.n_streams];
-    for (uint32_t gc = blockIdx.x; gc < total; gc += gridDim.x) {
-        const uint32_t s = find_stream(p.chunks, p.n_streams, gc);
-        if (p.status[s] != RANS_OK) continue;
-        const rans_encode_stream d = p.streams[s];
-        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
-        const uint8_t *scr = p.scratch + d.scratch_offset;
-        enc::pack_chunk(d.out, g.data0, scr + g.sl.words,
-                        reinterpret_cast<const uint32_t *>(scr + g.sl.states),
-                        reinterpret_cast<const uint32_t *>(scr + g.sl.wstart), d.n_lanes,
-                        g.sl.slot_bytes, gc - p.chunks[s]);
-    }
 }
 
 }  // namespace
@@ -526,11 +587,12 @@ extern "C" int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n
     const unsigned sms = unsigned(sm_count());
     enc_setup_kernel<<<1, kSetupThreads, 0, st>>>(p);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    enc_clear_kernel<<<std::min<unsigned>(n_streams, 8 * sms), kClearThreads, 0, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
     batch_encode_kernel<<<unsigned(per_sm) * sms, enc::kThreads, enc::kSmemBytes, st>>>(p);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    enc_finalize_kernel<<<std::min<unsigned>(n_streams, 8 * sms), kFinThreads, 0, st>>>(p);
-    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    enc_pack_kernel<<<16 * sms, kEncPackThreads, 0, st>>>(p);
+    enc_settle_kernel<<<std::min<unsigned>((n_streams + kClearThreads - 1) / kClearThreads, 8 * sms),
+                        kClearThreads, 0, st>>>(p);
     return check_launch();
 }
 

@@ -37,14 +37,10 @@ struct EncodeParams {
     const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
     uint64_t ctx_stride;  // u32 words per chunk in ctx
-    // Whole messages placed by the coder itself: the message and its size
-    // word, the look-back words and the chunk ticket (zeroed before the
-    // launch), the data region's offset, the version, and the wait bound.
-    uint8_t *out;
-    uint64_t *out_size;
-    enc::LookBack lb;
+    // Whole messages placed by the coder itself: the message and where its
+    // pieces are, and the chunk ticket (zeroed before the launch).
+    enc::Placement pl;
     uint32_t *ticket;
-    uint32_t data0, version;
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
 };
@@ -64,45 +60,6 @@ __device__ __forceinline__ uint32_t next_chunk(const EncodeParams &p, uint32_t c
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1u);
     return p.c_begin + __shfl_sync(kFull, t, 0);
-}
-
-// Chunk c is coded: wait until its slot's bulk stores have completed, report
-// a symbol without probability, publish the chunk's size.
-__device__ __forceinline__ void chunk_coded(const EncodeParams &p, uint32_t c, uint32_t lane,
-                                            uint32_t acc) {
-    if (lane == 0) {
-        bulk_wait<0>();
-        enc::fence_proxy_async_global();
-    }
-    __syncwarp();
-    if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
-    enc::publish_size(p.lb, c, p.sizes[c], lane);
-}
-
-// Place coded chunk c: its offset by look-back, the offset table entry, the
-// chunk copied to its place, and -- for the message's last chunk -- the
-// header, the last offset, the padding and the message size.  Without
-// `block`, false (nothing done) if a chunk before it is not yet published.
-// U: 16-byte blocks each lane copies at a time (2 keeps the adaptive coder
-// within its 64 registers).
-template <bool BYTES, int U>
-__device__ __forceinline__ bool place_chunk(const EncodeParams &p, uint32_t c, uint32_t lane,
-                                            bool block) {
-    const uint32_t size = p.sizes[c];
-    uint64_t excl;
-    const enc::LookResult r = enc::chunk_offset(p.lb, c, size, lane, block, excl);
-    if (r == enc::kLookNotYet) return false;
-    if (r == enc::kLookGaveUp) {
-        if (lane == 0) report(p.status, RANS_ERR_TIMEOUT);
-        return true;
-    }
-    if (lane == 0) reinterpret_cast<uint32_t *>(p.out + 32)[c] = uint32_t(excl);
-    enc::pack_chunk_at<BYTES, U, true>(p.out, uint64_t(p.data0) + excl, p.words, p.states, p.wstart,
-                                 p.N, p.slot_bytes, c, lane, 32);
-    if (c + 1 == p.n_chunks && lane == 0)
-        enc::write_header(p.out, p.out_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
-                          uint32_t(excl + size), p.version, p.log2m);
-    return true;
 }
 
 template <int NT, int KIND, bool PLACE = false>
@@ -140,12 +97,12 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
             acc, RAW ? p.raw + first : nullptr, ctx);
         if (PLACE) {
-            chunk_coded(p, c, lane, acc);
-            if (pending != kNone) place_chunk<BYTES, kCopyU>(p, pending, lane, true);
-            pending = place_chunk<BYTES, kCopyU>(p, c, lane, false) ? kNone : c;
+            enc::chunk_coded(p.pl, c, lane, acc);
+            if (pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane, true);
+            pending = enc::place_chunk<BYTES, kCopyU>(p.pl, c, lane, false) ? kNone : c;
         }
     }
-    if (PLACE && pending != kNone) place_chunk<BYTES, kCopyU>(p, pending, lane, true);
+    if (PLACE && pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane, true);
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
     if (lane == 0) bulk_wait<0>();
@@ -238,19 +195,23 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
 int encode_placed(EncodeParams &ep, const ScratchLayout &sl, uint8_t *scr, uint8_t *d_out,
                   uint64_t *d_out_size, uint32_t data0, uint32_t version, int kind,
                   cudaStream_t st) {
-    ep.out = d_out;
-    ep.out_size = d_out_size;
-    ep.lb.look = reinterpret_cast<uint64_t *>(scr + sl.look);
-    ep.lb.glook = reinterpret_cast<uint64_t *>(scr + sl.glook);
-    ep.lb.gacc = reinterpret_cast<uint64_t *>(scr + sl.gacc);
-    ep.lb.n_chunks = ep.n_chunks;
-    // Every wait ends once the chunks started before it are coded: allow a
-    // second plus a microsecond per step of a chunk (several times the
-    // coding time of one chunk on a loaded GPU).
-    ep.lb.wait_ns = 1000000000ull + 1000ull * (ep.CS / ep.N + 1);
+    enc::Placement &m = ep.pl;
+    m.out = d_out;
+    m.out_size = d_out_size;
+    m.status = ep.status;
+    m.words = ep.words;
+    m.states = ep.states;
+    m.wstart = ep.wstart;
+    m.sizes = ep.sizes;
+    m.lb = enc::scratch_lookback(scr, sl, ep.n_chunks, ep.CS, ep.N);
+    m.n_sym = ep.n_sym;
+    m.N = ep.N;
+    m.CS = ep.CS;
+    m.data0 = data0;
+    m.slot_bytes = ep.slot_bytes;
+    m.version = version;
+    m.log2m = ep.log2m;
     ep.ticket = reinterpret_cast<uint32_t *>(scr + sl.ticket);
-    ep.data0 = data0;
-    ep.version = version;
     ep.c_begin = 0;  // the placed coder always covers the whole message
     if (cudaMemsetAsync(scr + sl.look, 0, sl.total - sl.look, st) != cudaSuccess)
         return RANS_ERR_CUDA;
