@@ -750,25 +750,14 @@ __device__ __forceinline__ void pack_blocks(uint8_t *out, const uint8_t *src, ui
     }
 }
 
-// Threads t of nt: chunk c of a message from scratch (words base, states,
-// wstart) into out at message byte D.  The words buffer must have 16
-// readable bytes past its last slot.
-// BYTES: the chunk's byte count may be odd and its start in the slot too;
-// the chunk is padded with zeros to a multiple of 4 bytes.  U: 16-byte
-// blocks in flight per thread; L2: loads through L2 only (ld_src16).
+// Threads t of nt: bytes s0 .. s0+len of words (16-byte aligned base) to
+// out + d0.  d0 and s0 are even and len is even, except with BYTES (any
+// byte).  U: 16-byte blocks in flight per thread; L2: loads through L2 only
+// (ld_src16).  words must have 16 readable bytes past s0 + len.
 template <bool BYTES, int U, bool L2>
-__device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const uint8_t *words,
-                                              const uint32_t *states, const uint32_t *wstart,
-                                              uint32_t N, uint32_t slot_bytes, uint32_t c,
-                                              uint32_t t, uint32_t nt) {
-    uint16_t *dst16 = reinterpret_cast<uint16_t *>(out + D);
-    const uint32_t *st = states + uint64_t(c) * N;
-    for (uint32_t i = t; i < 2 * N; i += nt) dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
-    // words: destination bytes [d0, d1), source bytes from s0 in words
-    const uint32_t ws = wstart[c];
-    const uint64_t d0 = D + 4ull * N;
-    const uint64_t s0 = uint64_t(c) * slot_bytes + ws;
-    const uint64_t d1 = d0 + (slot_bytes - ws);
+__device__ __forceinline__ void copy_bytes(uint8_t *out, uint64_t d0, const uint8_t *words,
+                                           uint64_t s0, uint64_t len, uint32_t t, uint32_t nt) {
+    const uint64_t d1 = d0 + len;
     const uint64_t B0 = round16(d0), B1 = d1 & ~uint64_t(15);
     const uint64_t head_end = B0 < d1 ? B0 : d1;
     if (BYTES) {
@@ -791,11 +780,32 @@ __device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const ui
     const uint64_t tail_start = B1 > head_end ? B1 : head_end;
     if (BYTES) {
         for (uint64_t b = tail_start + t; b < d1; b += nt) out[b] = ld_src1<L2>(words + s0 + (b - d0));
-        const uint64_t end = D + ((d1 - D + 3) & ~uint64_t(3));
-        for (uint64_t b = d1 + t; b < end; b += nt) out[b] = 0;
     } else {
         for (uint64_t b = tail_start + 2ull * t; b < d1; b += 2ull * nt)
             *reinterpret_cast<uint16_t *>(out + b) = ld_src2<L2>(words + s0 + (b - d0));
+    }
+}
+
+// Threads t of nt: chunk c of a message from scratch (words base, states,
+// wstart) into out at message byte D.  The words buffer must have 16
+// readable bytes past its last slot.
+// BYTES: the chunk's byte count may be odd and its start in the slot too;
+// the chunk is padded with zeros to a multiple of 4 bytes.
+template <bool BYTES, int U, bool L2>
+__device__ __forceinline__ void pack_chunk_at(uint8_t *out, uint64_t D, const uint8_t *words,
+                                              const uint32_t *states, const uint32_t *wstart,
+                                              uint32_t N, uint32_t slot_bytes, uint32_t c,
+                                              uint32_t t, uint32_t nt) {
+    uint16_t *dst16 = reinterpret_cast<uint16_t *>(out + D);
+    const uint32_t *st = states + uint64_t(c) * N;
+    for (uint32_t i = t; i < 2 * N; i += nt) dst16[i] = uint16_t(st[i >> 1] >> ((i & 1) * 16));
+    const uint32_t ws = wstart[c];
+    const uint64_t d1 = D + 4ull * N + (slot_bytes - ws);
+    copy_bytes<BYTES, U, L2>(out, D + 4ull * N, words, uint64_t(c) * slot_bytes + ws,
+                             slot_bytes - ws, t, nt);
+    if (BYTES) {
+        const uint64_t end = D + ((d1 - D + 3) & ~uint64_t(3));
+        for (uint64_t b = d1 + t; b < end; b += nt) out[b] = 0;
     }
 }
 

@@ -35,6 +35,13 @@ struct PrefixEncodeParams {
     uint32_t *status;
     uint64_t n_sym;
     uint32_t N, CS, n_chunks, slot_bytes;
+    // The message's placement: where it goes, the look-back words (the
+    // scratch's enc::LookBack) and the chunk ticket, zeroed before the launch.
+    uint8_t *out;
+    uint64_t *out_size;
+    uint32_t data0;
+    enc::LookBack lb;
+    uint32_t *ticket;
     uint32_t code[RANS_MAX_ALPHABET];  // len << 16 | code; len 0: symbol not in the code
 };
 
@@ -131,22 +138,66 @@ __device__ __forceinline__ void prefix_encode_chunk(const uint8_t *sym, uint32_t
     if (lane == 0) *size = 4u * wpos;
 }
 
+// Place coded chunk c: its offset by look-back (enc::chunk_offset), the
+// offset table entry, its words copied to their place, and -- for the last
+// chunk -- the header.  Without `block`, false if a chunk before it is not
+// yet published.
+__device__ __forceinline__ bool prefix_place(const PrefixEncodeParams &p, uint32_t c,
+                                             uint32_t lane, bool block) {
+    const uint32_t size = p.sizes[c];
+    uint64_t excl;
+    const enc::LookResult r = enc::chunk_offset(p.lb, c, size, lane, block, excl);
+    if (r == enc::kLookNotYet) return false;
+    if (r == enc::kLookGaveUp) {
+        if (lane == 0) report(p.status, RANS_ERR_TIMEOUT);
+        return true;
+    }
+    if (lane == 0) reinterpret_cast<uint32_t *>(p.out + 32)[c] = uint32_t(excl);
+    enc::copy_bytes<false, 4, true>(p.out, uint64_t(p.data0) + excl, p.slots,
+                                    uint64_t(c) * p.slot_bytes, size, lane, 32);
+    if (c + 1 == p.n_chunks && lane == 0)
+        enc::write_header(p.out, p.out_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
+                          uint32_t(excl + size), RANS_VERSION_PREFIX);
+    return true;
+}
+
+// Warps take chunks in order from a counter, code each into its slot,
+// publish its size and place it -- at once if every chunk before it is
+// published, else after the warp's next chunk (see enc::chunk_offset).
 template <int NT>
 __global__ void __launch_bounds__(kPfxWarps * 32)
     prefix_encode_kernel(const __grid_constant__ PrefixEncodeParams p) {
     __shared__ uint32_t tab[RANS_MAX_ALPHABET];
     for (uint32_t i = threadIdx.x; i < RANS_MAX_ALPHABET; i += blockDim.x) tab[i] = p.code[i];
     __syncthreads();
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, lt = lanemask_lt();
+    const uint32_t lane = lane_id(), lt = lanemask_lt();
     uint32_t err = 0;
-    for (uint32_t c = blockIdx.x * kPfxWarps + warp; c < p.n_chunks; c += gridDim.x * kPfxWarps) {
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+    uint32_t pending = kNone;
+    auto next = [&]() {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(p.ticket, 1u);
+        return __shfl_sync(kFull, t, 0);
+    };
+    for (uint32_t c = next(); c < p.n_chunks; c = next()) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
         prefix_encode_chunk<NT>(p.sym + first, n_c, p.N,
                                 reinterpret_cast<uint32_t *>(p.slots + uint64_t(c) * p.slot_bytes),
                                 p.slot_bytes / 4, p.sizes + c, tab, lane, lt, err);
+        __syncwarp();  // the chunk's words and size are written
+        // A symbol without a code is reported before the size is published.
+        if (__any_sync(kFull, err) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
+        enc::publish_size(p.lb, c, p.sizes[c], lane);
+        if (pending != kNone) prefix_place(p, pending, lane, true);
+        pending = prefix_place(p, c, lane, false) ? kNone : c;
     }
-    if (__any_sync(kFull, err) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
+    if (pending != kNone) prefix_place(p, pending, lane, true);
+}
+
+// After the placing launch: a rejected message has size 0.
+__global__ void prefix_settle_kernel(const uint32_t *status, uint64_t *out_size) {
+    if (*status != RANS_OK) *out_size = 0;
 }
 
 struct PrefixFinalizeParams {
@@ -171,30 +222,26 @@ __global__ void __launch_bounds__(kFinThreads)
                           warp_sums, &carry_s, RANS_VERSION_PREFIX);
 }
 
-struct PrefixPackParams {
-    uint8_t *out;
-    const uint8_t *slots;
-    const uint32_t *status;
-    uint32_t n_chunks, data0, slot_bytes;
-};
-
-// Chunk c's words (4-byte aligned at both ends) to their place in out.
-constexpr int kPackThreads = 256;
-__global__ void __launch_bounds__(kPackThreads)
-    prefix_pack_kernel(const __grid_constant__ PrefixPackParams p) {
-    if (*p.status != RANS_OK) return;
-    const uint32_t *offs = reinterpret_cast<const uint32_t *>(p.out + 32);
-    for (uint32_t c = blockIdx.x; c < p.n_chunks; c += gridDim.x) {
-        uint32_t *dst = reinterpret_cast<uint32_t *>(p.out + p.data0 + offs[c]);
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(p.slots + uint64_t(c) * p.slot_bytes);
-        const uint32_t n = (offs[c + 1] - offs[c]) / 4;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-    }
-}
-
 // Worst-case words of a chunk of CS symbols: ceil(12 CS / 32) + 2N, plus one.
 uint32_t prefix_slot_bytes(uint32_t CS, uint32_t N) {
     return uint32_t(round16(4ull * ((uint64_t(CS) * kPfxMaxLen + 31) / 32 + 2ull * N + 1)));
+}
+
+// Scratch of a prefix message: the chunk slots, then the chunk sizes, then
+// the look-back words and the ticket (as in enc::ScratchLayout).
+struct PrefixScratch {
+    uint64_t sizes, look, glook, gacc, ticket, total;
+};
+PrefixScratch prefix_scratch(uint64_t n_chunks, uint32_t slot_bytes) {
+    PrefixScratch s{};
+    const uint64_t n_groups = (n_chunks + 31) / 32;
+    s.sizes = n_chunks * slot_bytes;
+    s.look = s.sizes + round16(4 * n_chunks) + 16;  // 16 readable bytes past the last slot
+    s.glook = s.look + round16(8 * n_chunks);
+    s.gacc = s.glook + round16(8 * n_groups);
+    s.ticket = s.gacc + round16(8 * n_groups);
+    s.total = s.ticket + 16;
+    return s;
 }
 
 }  // namespace
@@ -205,8 +252,8 @@ using namespace rans;
 extern "C" uint64_t rans_encode_scratch_size_prefix(uint64_t n_symbols, const rans_params *params) {
     if (!params_ok(params)) return 0;
     const MessageGeometry g = geometry(n_symbols, params);
-    return g.n_chunks * prefix_slot_bytes(params->chunk_symbols, params->n_lanes) +
-           round16(4 * g.n_chunks) + 16;
+    return prefix_scratch(g.n_chunks, prefix_slot_bytes(params->chunk_symbols, params->n_lanes))
+        .total;
 }
 
 extern "C" int rans_encode_prefix(const uint8_t *d_symbols, uint64_t n_symbols,
@@ -231,56 +278,56 @@ extern "C" int rans_encode_prefix(const uint8_t *d_symbols, uint64_t n_symbols,
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     uint8_t *scr = static_cast<uint8_t *>(d_scratch);
+    const PrefixScratch ps = prefix_scratch(g.n_chunks, slot_bytes);
+    if (g.n_chunks == 0) {
+        PrefixFinalizeParams fp{};
+        fp.out = d_out;
+        fp.out_size = d_out_size;
+        fp.status = d_status;
+        fp.n_sym = n_symbols;
+        fp.N = params->n_lanes;
+        fp.CS = params->chunk_symbols;
+        fp.data0 = uint32_t(g.data0);
+        prefix_finalize_kernel<<<1, kFinThreads, 0, st>>>(fp);
+        return check_launch();
+    }
     PrefixEncodeParams ep{};
     ep.sym = d_symbols;
     ep.slots = scr;
-    ep.sizes = reinterpret_cast<uint32_t *>(scr + g.n_chunks * slot_bytes);
+    ep.sizes = reinterpret_cast<uint32_t *>(scr + ps.sizes);
     ep.status = d_status;
     ep.n_sym = n_symbols;
     ep.N = params->n_lanes;
     ep.CS = params->chunk_symbols;
     ep.n_chunks = uint32_t(g.n_chunks);
     ep.slot_bytes = slot_bytes;
+    ep.out = d_out;
+    ep.out_size = d_out_size;
+    ep.data0 = uint32_t(g.data0);
+    ep.lb.look = reinterpret_cast<uint64_t *>(scr + ps.look);
+    ep.lb.glook = reinterpret_cast<uint64_t *>(scr + ps.glook);
+    ep.lb.gacc = reinterpret_cast<uint64_t *>(scr + ps.gacc);
+    ep.lb.n_chunks = ep.n_chunks;
+    // As for rans_encode: a second plus a microsecond per step of a chunk.
+    ep.lb.wait_ns = 1000000000ull + 1000ull * (ep.CS / ep.N + 1);
+    ep.ticket = reinterpret_cast<uint32_t *>(scr + ps.ticket);
     for (uint32_t s = 0; s < n_alpha; ++s)
         ep.code[s] = h_lengths[s] ? (uint32_t(h_lengths[s]) << 16) | codes[s] : 0u;
-    if (g.n_chunks > 0) {
-        auto kernel = ep.N == 32 ? prefix_encode_kernel<32> : prefix_encode_kernel<0>;
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPfxWarps * 32, 0) !=
-                cudaSuccess ||
-            per_sm <= 0)
-            return RANS_ERR_CUDA;
-        const uint64_t want = ceil_div(g.n_chunks, kPfxWarps);
-        const unsigned grid =
-            unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(per_sm) * sm_count())));
-        kernel<<<grid, kPfxWarps * 32, 0, st>>>(ep);
-        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    }
-    PrefixFinalizeParams fp{};
-    fp.out = d_out;
-    fp.out_size = d_out_size;
-    fp.sizes = ep.sizes;
-    fp.status = d_status;
-    fp.n_sym = n_symbols;
-    fp.N = ep.N;
-    fp.CS = ep.CS;
-    fp.n_chunks = ep.n_chunks;
-    fp.data0 = uint32_t(g.data0);
-    prefix_finalize_kernel<<<1, kFinThreads, 0, st>>>(fp);
+    if (cudaMemsetAsync(scr + ps.look, 0, ps.total - ps.look, st) != cudaSuccess)
+        return RANS_ERR_CUDA;
+    auto kernel = ep.N == 32 ? prefix_encode_kernel<32> : prefix_encode_kernel<0>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPfxWarps * 32, 0) !=
+            cudaSuccess ||
+        per_sm <= 0)
+        return RANS_ERR_CUDA;
+    const uint64_t want = ceil_div(g.n_chunks, kPfxWarps);
+    const unsigned grid =
+        unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(per_sm) * sm_count())));
+    kernel<<<grid, kPfxWarps * 32, 0, st>>>(ep);
     if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    if (g.n_chunks > 0) {
-        PrefixPackParams pp{};
-        pp.out = d_out;
-        pp.slots = scr;
-        pp.status = d_status;
-        pp.n_chunks = ep.n_chunks;
-        pp.data0 = fp.data0;
-        pp.slot_bytes = slot_bytes;
-        const unsigned grid = unsigned(std::min<uint64_t>(g.n_chunks, 65535ull * 8));
-        prefix_pack_kernel<<<grid, kPackThreads, 0, st>>>(pp);
-        if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    }
-    return RANS_OK;
+    prefix_settle_kernel<<<1, 1, 0, st>>>(d_status, d_out_size);
+    return check_launch();
 }
 
 #ifdef RANS_CHECKED
