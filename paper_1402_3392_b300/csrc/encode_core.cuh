@@ -880,26 +880,24 @@ __device__ __forceinline__ void publish_failed(const LookBack &lb, uint32_t c, u
     if (lane == 0) st_release_u64(lb.look + c, kLookFailed);
 }
 
-enum LookResult : uint32_t { kLookDone, kLookNotYet, kLookGaveUp };
-
 // One round of a look-back: lane i reads entry q - i (own = the lane has an
-// entry, else it contributes `none`), waits for it if `block`.  Adds the
-// entries up to the nearest prefix to sum; sets `found` if there was one.
-__device__ __forceinline__ LookResult look_round(const uint64_t *q, bool own, uint64_t none,
-                                                 bool block, uint64_t t0, uint64_t wait_ns,
-                                                 uint32_t lane, uint64_t &sum, bool &found) {
+// entry, else it contributes `none`), waiting for it until t0 + wait_ns.
+// Adds the entries up to the nearest prefix to sum and sets `found` if there
+// was one; false if an entry stayed unpublished or says failed.
+__device__ __forceinline__ bool look_round(const uint64_t *q, bool own, uint64_t none, uint64_t t0,
+                                           uint64_t wait_ns, uint32_t lane, uint64_t &sum,
+                                           bool &found) {
     uint64_t v = none;
     if (own) {
         v = ld_acquire_u64(q - lane);
-        for (uint32_t ns = 64; block && (v >> 62) == 0 && globaltimer_ns() - t0 <= wait_ns;) {
+        for (uint32_t ns = 64; (v >> 62) == 0 && globaltimer_ns() - t0 <= wait_ns;) {
             __nanosleep(ns);
             ns = ns < 4096 ? 2 * ns : ns;
             v = ld_acquire_u64(q - lane);
         }
     }
     const uint64_t flag = v & ~kLookValue;
-    if (__any_sync(kFull, flag == kLookFailed || (block && flag == 0))) return kLookGaveUp;
-    if (__any_sync(kFull, flag == 0)) return kLookNotYet;
+    if (__any_sync(kFull, flag == 0 || flag == kLookFailed)) return false;
     const uint32_t pref = __ballot_sync(kFull, flag == kLookPrefix);
     const uint32_t stop = pref ? __ffs(pref) - 1 : 31;  // the nearest prefix
     unsigned long long add = lane <= stop ? (v & kLookValue) : 0ull;
@@ -907,41 +905,41 @@ __device__ __forceinline__ LookResult look_round(const uint64_t *q, bool own, ui
     for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(kFull, add, d);
     sum += add;
     found = pref != 0;
-    return kLookDone;
+    return true;
 }
 
 // One warp: the bytes before chunk c (of `size` bytes, published), from the
-// nearest published prefix; publishes c's prefix (and its group's, if c is
-// the group's last chunk) and returns kLookDone with the bytes in `excl`.
-// An entry not yet published: without `block`, kLookNotYet at once; with
-// `block`, waits for it.  Chunks take their numbers from a counter in the
-// order the warps start them, so every chunk (or group) waited for is being
-// coded by running warps, which publish sizes before they wait for anything:
-// each wait ends.  The waits of a call share the deadline now + wait_ns;
-// kLookGaveUp if it passed or a chunk before gave up (look[c] then says so).
-__device__ __forceinline__ LookResult chunk_offset(const LookBack &lb, uint32_t c, uint32_t size,
-                                                   uint32_t lane, bool block, uint64_t &excl) {
+// nearest published prefix, in `excl`; publishes c's prefix (and its
+// group's, if c is the group's last chunk).  Waits for entries not yet
+// published.  Chunks take their numbers from a counter in the order the
+// warps start them, so every chunk (or group) waited for is being coded by
+// running warps, which publish sizes before they wait for anything: each
+// wait ends.  The waits of a call share the deadline now + wait_ns; false if
+// it passed or a chunk before gave up (look[c] then says failed).
+__device__ __forceinline__ bool chunk_offset(const LookBack &lb, uint32_t c, uint32_t size,
+                                             uint32_t lane, uint64_t &excl) {
     excl = 0;
-    if (c == 0) return kLookDone;
+    if (c == 0) return true;
     const uint64_t t0 = globaltimer_ns();
     const uint32_t g = c / 32, i = c % 32;
     uint64_t sum = 0;
     bool found = false;
     // The chunks before c in its group (lanes at or past i add nothing).
-    LookResult r = look_round(lb.look + (c - 1), lane < i, kLookSize, block, t0, lb.wait_ns, lane,
-                              sum, found);
+    bool ok = look_round(lb.look + (c - 1), lane < i, kLookSize, t0, lb.wait_ns, lane, sum, found);
     // Then whole groups, nearest first (before group 0: the message start).
-    for (uint32_t j = g; r == kLookDone && !found; j -= 32)
-        r = look_round(lb.glook + (int64_t(j) - 1), j >= 1 + lane, kLookPrefix, block, t0,
-                       lb.wait_ns, lane, sum, found);
-    if (r == kLookGaveUp && lane == 0) st_release_u64(lb.look + c, kLookFailed);
-    if (r != kLookDone) return r;
+    for (uint32_t j = g; ok && !found; j -= 32)
+        ok = look_round(lb.glook + (int64_t(j) - 1), j >= 1 + lane, kLookPrefix, t0, lb.wait_ns,
+                        lane, sum, found);
+    if (!ok) {
+        if (lane == 0) st_release_u64(lb.look + c, kLookFailed);
+        return false;
+    }
     excl = sum;
     if (lane == 0) {
         st_release_u64(lb.look + c, kLookPrefix | (sum + size));
         if (i == 31 || c + 1 == lb.n_chunks) st_release_u64(lb.glook + g, kLookPrefix | (sum + size));
     }
-    return kLookDone;
+    return true;
 }
 
 // A message whose coder warps place its chunks themselves.
@@ -974,19 +972,15 @@ __device__ __forceinline__ void chunk_coded(const Placement &m, uint32_t c, uint
 
 // Place coded chunk c: its offset by look-back, the offset table entry, the
 // chunk copied to its place, and -- for the message's last chunk -- the
-// header, the last offset, the padding and the message size.  Without
-// `block`, false (nothing done) if a chunk before it is not yet published.
-// U: 16-byte blocks each lane copies at a time.
+// header, the last offset, the padding and the message size.  U: 16-byte
+// blocks each lane copies at a time.
 template <bool BYTES, int U>
-__device__ __forceinline__ bool place_chunk(const Placement &m, uint32_t c, uint32_t lane,
-                                            bool block) {
+__device__ __forceinline__ void place_chunk(const Placement &m, uint32_t c, uint32_t lane) {
     const uint32_t size = m.sizes[c];
     uint64_t excl;
-    const LookResult r = chunk_offset(m.lb, c, size, lane, block, excl);
-    if (r == kLookNotYet) return false;
-    if (r == kLookGaveUp) {
+    if (!chunk_offset(m.lb, c, size, lane, excl)) {
         if (lane == 0) report(m.status, RANS_ERR_TIMEOUT);
-        return true;
+        return;
     }
     if (lane == 0) reinterpret_cast<uint32_t *>(m.out + 32)[c] = uint32_t(excl);
     pack_chunk_at<BYTES, U, true>(m.out, uint64_t(m.data0) + excl, m.words, m.states, m.wstart,
@@ -994,7 +988,6 @@ __device__ __forceinline__ bool place_chunk(const Placement &m, uint32_t c, uint
     if (c + 1 == m.lb.n_chunks && lane == 0)
         write_header(m.out, m.out_size, m.n_sym, m.N, m.CS, m.lb.n_chunks, m.data0,
                      uint32_t(excl + size), m.version, m.log2m);
-    return true;
 }
 
 // The look-back words of a message's scratch (zeroed before its launch).

@@ -353,16 +353,14 @@ __device__ __forceinline__ enc::Placement stream_placement(const BatchEncodePara
     return m;
 }
 
-// Chunk c of stream s is coded (acc: the table flags it met): publish it and
-// place it if every chunk before it is published (false: not yet).  Out of
-// line, so that the coding loop keeps its registers.
-__device__ __noinline__ bool coded_and_placed(const BatchEncodeParams &p, uint32_t s, uint32_t c,
-                                              uint32_t lane, uint32_t acc) {
+// Chunk c of stream s is coded (acc: the table flags it met): publish its
+// size.  Out of line, as is place_pending, so that the coding loop keeps
+// its registers.
+__device__ __noinline__ void coded(const BatchEncodeParams &p, uint32_t s, uint32_t c,
+                                   uint32_t lane, uint32_t acc) {
     const rans_encode_stream d = p.streams[s];
     const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
-    const enc::Placement m = stream_placement(p, s, d, g);
-    enc::chunk_coded(m, c, lane, acc);
-    return enc::place_chunk<false, 4>(m, c, lane, false);
+    enc::chunk_coded(stream_placement(p, s, d, g), c, lane, acc);
 }
 
 // Place coded chunk c of stream s, waiting (bounded) for the chunks before it.
@@ -370,7 +368,7 @@ __device__ __noinline__ void place_pending(const BatchEncodeParams &p, uint32_t 
                                            uint32_t lane) {
     const rans_encode_stream d = p.streams[s];
     const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
-    enc::place_chunk<false, 4>(stream_placement(p, s, d, g), c, lane, true);
+    enc::place_chunk<false, 4>(stream_placement(p, s, d, g), c, lane);
 }
 
 // One CTA per stream (grid-stride): zero the look-back words and ticket of
@@ -408,8 +406,8 @@ __global__ void __launch_bounds__(kClearThreads)
 
 // Persistent: CTAs take work items (8 chunks of one stream, one per warp) in
 // order from a counter.  Each warp codes its chunk, publishes the chunk's
-// size and places it -- at once if every chunk before it is published, else
-// after the warp's next chunk (waiting only for chunks taken earlier).
+// size, and places it after its next item (the last one at the end),
+// waiting only for chunks taken earlier.
 __global__ void __launch_bounds__(enc::kThreads, 4)
     batch_encode_kernel(const __grid_constant__ BatchEncodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -458,7 +456,7 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             }
             continue;
         }
-        bool coded = false, placed = false;
+        bool did = false;
         if (c < g.n_chunks) {
             uint8_t *scr = p.scratch + d.scratch_offset;
             const uint64_t first = uint64_t(c) * d.chunk_symbols;
@@ -474,14 +472,14 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             else
                 enc::encode_chunk<0, false>(d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart,
                                      sizes, states, sm.tab_s, ring_s, ge, lane, acc);
-            placed = coded_and_placed(p, s, c, lane, acc);
-            coded = true;
+            coded(p, s, c, lane, acc);
+            did = true;
         }
         if (pend_s != kNone) {
             place_pending(p, pend_s, pend_c, lane);
             pend_s = kNone;
         }
-        if (coded && !placed) {
+        if (did) {
             pend_s = s;
             pend_c = c;
         }

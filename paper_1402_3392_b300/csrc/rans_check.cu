@@ -38,11 +38,11 @@ __global__ void __launch_bounds__(32) lookback_wait_kernel(uint32_t *status) {
     __syncwarp();
     const enc::LookBack lb{g_look_words, g_look_words + 2, g_look_words + 4, 2, kWaitNs};
     uint64_t excl = 0;
-    const enc::LookResult r = enc::chunk_offset(lb, 1, 0, lane, true, excl);
+    const bool done = enc::chunk_offset(lb, 1, 0, lane, excl);
     __syncwarp();
     if (lane == 0) {
         const bool failed = (g_look_words[1] & ~enc::kLookValue) == enc::kLookFailed;
-        *status = r == enc::kLookGaveUp && failed ? RANS_ERR_TIMEOUT : RANS_OK;
+        *status = !done && failed ? RANS_ERR_TIMEOUT : RANS_OK;
     }
 }
 

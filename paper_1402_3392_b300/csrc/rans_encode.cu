@@ -80,9 +80,10 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
     const uint32_t ge = lanemask_ge();
     uint32_t acc = 0;
-    // PLACE: a chunk whose offset was not yet known when it was coded is
-    // placed after the warp's next chunk (never waiting on chunks started
-    // after its own).
+    // PLACE: a chunk is placed after the warp's next chunk is coded (its
+    // last chunk at the end), when the chunks before it have long been
+    // published: the look-back rarely waits.  Trying at once, without
+    // waiting, measured slower (1 GiB: 1.515 against 1.430 ms).
     constexpr uint32_t kNone = 0xFFFFFFFFu;
     constexpr int kCopyU = ADAPT ? 2 : 4;
     uint32_t pending = kNone;
@@ -98,30 +99,32 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
             acc, RAW ? p.raw + first : nullptr, ctx);
         if (PLACE) {
             enc::chunk_coded(p.pl, c, lane, acc);
-            if (pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane, true);
-            pending = enc::place_chunk<BYTES, kCopyU>(p.pl, c, lane, false) ? kNone : c;
+            if (pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane);
+            pending = c;
         }
     }
-    if (PLACE && pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane, true);
+    if (PLACE && pending != kNone) enc::place_chunk<BYTES, kCopyU>(p.pl, pending, lane);
     // Symbols with f_s = 0 leave the table's flag bit in acc.
     if (__any_sync(kFull, acc & enc::kZeroFlag) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
     if (lane == 0) bulk_wait<0>();
 }
 
-// The launch bound alone keeps the plain, bypass and byte-wise encoders at
-// 64 registers or fewer (four CTAs per SM); asking for a minimum of one CTA
-// per SM lets the compiler spend more and costs a CTA per SM.  Adaptive
-// chunks need the explicit bound of four CTAs per SM.
+// Four CTAs per SM (64 registers) for every kind but the 13/14-bit models,
+// whose 16-byte table entries need more registers than that (two or three
+// CTAs per SM).  The plain 32-coder kernel stays within 64 registers
+// without asking (asking made the compiler spill one); the others need the
+// bound.  A bound of one CTA per SM, asked for explicitly, let the compiler
+// spend more registers and cost a CTA per SM.
 template <int NT, int KIND, bool PLACE>
-__global__ void __launch_bounds__(enc::kThreads)
+__global__ void __launch_bounds__(enc::kThreads, KIND == kPlain && NT == 32 ? 0 : 4)
     encode_kernel(const __grid_constant__ EncodeParams p) {
     encode_body<NT, KIND, PLACE>(p);
 }
 
 template <int NT, bool PLACE>
-__global__ void __launch_bounds__(enc::kThreads, 4)
-    encode_kernel_adaptive(const __grid_constant__ EncodeParams p) {
-    encode_body<NT, kAdaptive, PLACE>(p);
+__global__ void __launch_bounds__(enc::kThreads)
+    encode_kernel_wide(const __grid_constant__ EncodeParams p) {
+    encode_body<NT, kWide, PLACE>(p);
 }
 
 // After a placing launch: a rejected message has size 0 (the last chunk may
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 template <int NT, int KIND, bool PLACE = false>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     void (*kernel)(EncodeParams);
-    if constexpr (KIND == kAdaptive) kernel = encode_kernel_adaptive<NT, PLACE>;
+    if constexpr (KIND == kWide) kernel = encode_kernel_wide<NT, PLACE>;
     else kernel = encode_kernel<NT, KIND, PLACE>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, kSmemBytes) !=

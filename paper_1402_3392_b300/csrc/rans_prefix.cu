@@ -140,17 +140,14 @@ __device__ __forceinline__ void prefix_encode_chunk(const uint8_t *sym, uint32_t
 
 // Place coded chunk c: its offset by look-back (enc::chunk_offset), the
 // offset table entry, its words copied to their place, and -- for the last
-// chunk -- the header.  Without `block`, false if a chunk before it is not
-// yet published.
-__device__ __forceinline__ bool prefix_place(const PrefixEncodeParams &p, uint32_t c,
-                                             uint32_t lane, bool block) {
+// chunk -- the header.
+__device__ __forceinline__ void prefix_place(const PrefixEncodeParams &p, uint32_t c,
+                                             uint32_t lane) {
     const uint32_t size = p.sizes[c];
     uint64_t excl;
-    const enc::LookResult r = enc::chunk_offset(p.lb, c, size, lane, block, excl);
-    if (r == enc::kLookNotYet) return false;
-    if (r == enc::kLookGaveUp) {
+    if (!enc::chunk_offset(p.lb, c, size, lane, excl)) {
         if (lane == 0) report(p.status, RANS_ERR_TIMEOUT);
-        return true;
+        return;
     }
     if (lane == 0) reinterpret_cast<uint32_t *>(p.out + 32)[c] = uint32_t(excl);
     enc::copy_bytes<false, 4, true>(p.out, uint64_t(p.data0) + excl, p.slots,
@@ -158,12 +155,11 @@ __device__ __forceinline__ bool prefix_place(const PrefixEncodeParams &p, uint32
     if (c + 1 == p.n_chunks && lane == 0)
         enc::write_header(p.out, p.out_size, p.n_sym, p.N, p.CS, p.n_chunks, p.data0,
                           uint32_t(excl + size), RANS_VERSION_PREFIX);
-    return true;
 }
 
 // Warps take chunks in order from a counter, code each into its slot,
-// publish its size and place it -- at once if every chunk before it is
-// published, else after the warp's next chunk (see enc::chunk_offset).
+// publish its size, and place it after the warp's next chunk (the last one
+// at the end; see enc::chunk_offset).
 template <int NT>
 __global__ void __launch_bounds__(kPfxWarps * 32)
     prefix_encode_kernel(const __grid_constant__ PrefixEncodeParams p) {
@@ -189,10 +185,10 @@ __global__ void __launch_bounds__(kPfxWarps * 32)
         // A symbol without a code is reported before the size is published.
         if (__any_sync(kFull, err) && lane == 0) report(p.status, RANS_ERR_ZERO_FREQ);
         enc::publish_size(p.lb, c, p.sizes[c], lane);
-        if (pending != kNone) prefix_place(p, pending, lane, true);
-        pending = prefix_place(p, c, lane, false) ? kNone : c;
+        if (pending != kNone) prefix_place(p, pending, lane);
+        pending = c;
     }
-    if (pending != kNone) prefix_place(p, pending, lane, true);
+    if (pending != kNone) prefix_place(p, pending, lane);
 }
 
 // After the placing launch: a rejected message has size 0.
