@@ -88,6 +88,42 @@ def test_batch_encode_matches_oracle(rlib, orc, cuda):
         assert np.array_equal(eb.message(i).cpu().numpy(), ref), i
 
 
+def test_batch_encode_rejected_model_fails_alone_and_fast(rlib, orc, cuda):
+    """A many-chunk stream whose model is rejected (its frequencies do not
+    sum to M) fails alone with RANS_ERR_INVALID_ARG and size 0, promptly (no
+    chunk of it waits for the others: the coders place every chunk after the
+    chunks before it in its own stream), while the streams around it, many
+    chunks each, are bit-exact with the oracle."""
+    import time
+
+    import torch
+
+    rng = np.random.default_rng(131)
+    zipf = rlib.rans_quantize_table(wl.weights_from_probs(wl.zipf_probs(256, 1.1)))
+    bad = np.zeros(256, dtype=np.uint16)
+    bad[:3] = 1000                                   # sums to 3000
+    tables = [zipf, bad]
+    streams = [dict(sym=rng.choice(256, size=n, p=zipf / zipf.sum()).astype(np.uint8), table=t)
+               for n, t in [(300_000, 0), (250_000, 1), (333_333, 0), (4096 * 40 + 7, 0)]]
+    streams[1]["sym"] = rng.integers(0, 3, size=250_000).astype(np.uint8)
+    arena, offs = upload_symbols(torch, cuda, streams)
+    tabs = B.upload_tables(tables, cuda)
+    for _ in range(2):  # the second call is timed (the first loads the kernels)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eb = B.encode_batch(arena, offs, [s["sym"].size for s in streams], tabs,
+                            [s["table"] for s in streams], 32, 4096)
+        torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 0.5
+    st = eb.status.cpu().numpy()
+    sizes = eb.host_sizes()
+    assert st[1] == rlib.RANS_ERR_INVALID_ARG and sizes[1] == 0
+    for i in (0, 2, 3):
+        assert st[i] == 0
+        ref = orc.encode_message(streams[i]["sym"], zipf, N=32, chunk_symbols=4096)
+        assert np.array_equal(eb.message(i).cpu().numpy(), ref), i
+
+
 def test_batch_round_trip_log_uniform_streams(rlib, orc, cuda):
     """500 streams, sizes log-uniform in [1 KiB, 1 MiB], per-stream
     Dirichlet(0.3) models over 16..256 symbols; all round-trip on the device,
