@@ -648,9 +648,9 @@ __device__ __forceinline__ void decode_step_raw(uint32_t &x, uint32_t &rp, bool 
 }
 
 // One step of a byte-wise chunk (b = 2^8 < M, Section 5): after D a lane may
-// need two digits.  The digits are read breadth-first across the warp: round
-// 1 gives every lane below L one byte (lanes in order), round 2 -- taken
-// only when some lane is still below L -- a second one.  (x << 8) | byte is
+// need two digits.  The digits are read breadth-first across the warp: a
+// first pass gives every lane below L one byte (lanes in order), a second
+// pass -- taken only when some lane is still below L -- a second one.  (x << 8) | byte is
 // a byte permute.
 template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step_bytes(uint32_t &x, uint32_t &rp, bool active,

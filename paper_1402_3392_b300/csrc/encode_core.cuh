@@ -276,10 +276,11 @@ __device__ __forceinline__ void encode_step_wide(uint32_t &x, uint32_t &wp, uint
 // One step of a byte-wise chunk (b = 2^8 < M, Section 5): a lane emits
 // k = [x >= f*2^19] + [x >= f*2^27] bytes (x must end below f*2^19 = the top
 // of I_s) before coding.  The decoder reads a step's bytes breadth-first --
-// round 1: one byte for every lane that needs one, lanes in order; round 2:
-// the second byte of the lanes that need two -- so in the backwards-filled
-// buffer the step's round-2 bytes sit above its round-1 bytes.  A lane's
-// round-1 byte is the one its decoder reads first: the higher of two.
+// first pass: one byte for every lane that needs one, lanes in order; second
+// pass: the second byte of the lanes that need two -- so in the backwards-
+// filled buffer the step's second-pass bytes sit above its first-pass bytes.
+// A lane's first-pass byte is the one its decoder reads first: the higher of
+// two.
 template <bool FULL>
 __device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uint32_t &acc,
                                                   bool active, uint32_t s, uint32_t tab_s,
