@@ -226,10 +226,28 @@ __device__ __forceinline__ void st_ring_u16(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(uint16_t(v)) : "memory");
 }
 
+// a * b + c (mod 2^32) as one multiply-add.
+__device__ __forceinline__ uint32_t imad_u32(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// Shared address of the 16-bit word that the k-th emitting lane from the top
+// stores below write position wp.  RING > 0: wp is the byte position in the
+// chunk's slot, which lives in the warp's ring (aligned to RING) at
+// wp mod RING.  RING = 0: wp is the shared address of the write position
+// itself, for groups whose stores cannot pass below the ring's start (one
+// multiply-add, no wrap).
+template <uint32_t RING>
+__device__ __forceinline__ uint32_t store_at(uint32_t wp, uint32_t k, uint32_t ring_s) {
+    return RING ? ((wp - 2u * k) & (RING - 1)) | ring_s : imad_u32(k, 0u - 2u, wp);
+}
+
 // Encode one step: renormalize (emit the low 16 bits if x >= f_s * 2^20), then
 // x = C(s, x).  wp is the warp-uniform write position (bytes, counting down);
 // ring_s is the warp's 4 KiB-aligned ring.
-template <bool FULL>
+template <bool FULL, uint32_t RING = kRing>
 __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
                                             uint32_t s, uint32_t tab_s, uint32_t ring_s,
                                             uint32_t ge) {
@@ -239,10 +257,11 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
     const bool emit = on && (x > ~(t.y & 0xFFF00000u));
     const uint32_t m = __ballot_sync(kFull, emit);
     if (emit) {
-        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        st_ring_u16(store_at<RING>(wp, __popc(m & ge), ring_s), x);
         x >>= 16;
     }
-    wp -= 2u * __popc(m);
+    if (RING) wp -= 2u * __popc(m);
+    else wp = imad_u32(__popc(m), 0u - 2u, wp);
     if (on) {
         // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
         const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
@@ -252,7 +271,7 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
 }
 
 // One step with a wide model: as encode_step with the 16-byte entry.
-template <bool FULL>
+template <bool FULL, uint32_t RING = kRing>
 __device__ __forceinline__ void encode_step_wide(uint32_t &x, uint32_t &wp, uint32_t &acc,
                                                  bool active, uint32_t s, uint32_t tab_s,
                                                  uint32_t ring_s, uint32_t ge) {
@@ -262,10 +281,11 @@ __device__ __forceinline__ void encode_step_wide(uint32_t &x, uint32_t &wp, uint
     const bool emit = on && x > t.y;
     const uint32_t m = __ballot_sync(kFull, emit);
     if (emit) {
-        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        st_ring_u16(store_at<RING>(wp, __popc(m & ge), ring_s), x);
         x >>= 16;
     }
-    wp -= 2u * __popc(m);
+    if (RING) wp -= 2u * __popc(m);
+    else wp = imad_u32(__popc(m), 0u - 2u, wp);
     if (on) {
         const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
         const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.w >> 24);
@@ -396,13 +416,29 @@ __device__ __forceinline__ void encode_step_adaptive(uint32_t &x, uint32_t &wp, 
 }
 
 // The step of a chunk of the byte-wise, wide or plain kind.
-template <bool FULL, bool BYTES, bool WIDE>
+// RING = 0 (plain and wide chunks only): wp is an absolute shared address
+// (store_at).
+template <bool FULL, bool BYTES, bool WIDE, uint32_t RING = kRing>
 __device__ __forceinline__ void coded_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
                                            uint32_t ge) {
+    static_assert(RING || !BYTES, "byte-wise steps address the ring by offset");
     if (BYTES) encode_step_bytes<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
-    else if (WIDE) encode_step_wide<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
-    else encode_step<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
+    else if (WIDE) encode_step_wide<FULL, RING>(x, wp, acc, active, s, tab_s, ring_s, ge);
+    else encode_step<FULL, RING>(x, wp, acc, active, s, tab_s, ring_s, ge);
+}
+
+// A step stores at most 32 words (64 bytes), so a group of kGroup steps
+// stores within [wp - kGroup * 64, wp).  When the write position's ring
+// offset is at least that, none of the group's stores wraps below the
+// ring's start (3 groups in 4 with a 4 KiB ring).  Used by the batched
+// encoder's groups (measured on B300: 10,000 streams 23.57 -> 23.37 ms); in
+// the single-message encoder, whose groups also load the next group's
+// symbols, the second copy of the unrolled group made it slower (1 GiB:
+// 1408 -> 1474 us), so that one always wraps.
+constexpr uint32_t kGroupBytes = kGroup * 64u;
+__device__ __forceinline__ bool group_is_linear(uint32_t wp) {
+    return (wp & (kRing - 1)) >= kGroupBytes;
 }
 
 // One step of a bypass chunk (Section 3): a lane whose symbol carries a raw
@@ -578,13 +614,24 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                 if (RAW) curw[u] = lane_on ? rawp[uint64_t(t - u) * N] : 0u;
             }
             service();
+            if (!RAW && !BYTES && group_is_linear(wp)) {
+                const uint32_t a0 = ring_s + (wp & (kRing - 1));
+                uint32_t wa = a0;
 #pragma unroll
-            for (uint32_t u = 0; u < kG; ++u) {
-                if (RAW)
-                    encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s, ring_s,
-                                              ge);
-                else
-                    coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+                for (uint32_t u = 0; u < kG; ++u)
+                    coded_step<NT == 32, BYTES, WIDE, (RAW || BYTES ? kRing : 0u)>(
+                        x, wa, acc, lane_on, cur[u], tab_s, ring_s, ge);
+                wp -= a0 - wa;
+            } else {
+#pragma unroll
+                for (uint32_t u = 0; u < kG; ++u) {
+                    if (RAW)
+                        encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s,
+                                                  ring_s, ge);
+                    else
+                        coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s,
+                                                          ring_s, ge);
+                }
             }
         }
     }
