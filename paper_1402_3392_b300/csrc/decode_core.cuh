@@ -26,8 +26,10 @@
 namespace rans {
 namespace dec {
 
-constexpr int kWarps = 8;                 // warps per CTA
+constexpr int kWarps = 8;                 // warps per CTA (the default shape)
 constexpr uint32_t kThreads = kWarps * 32;
+constexpr uint32_t kBuildThreads = 256;   // threads that build a table: one per symbol
+static_assert(kThreads >= kBuildThreads, "a table build needs 256 threads");
 constexpr uint32_t kChains = 2;           // chunks a warp decodes side by side
 constexpr uint32_t kChunksPerCta = kWarps * kChains;
 constexpr uint32_t kWarpRing = 4096;      // ring bytes per warp (4 KiB aligned)
@@ -70,14 +72,38 @@ static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRin
               "ring sizes");
 
 constexpr uint32_t kTableBytes = kM * 4;
-// Shared memory: [slot table 16 KiB][alignment slack 4 KiB][4 KiB ring per
-// warp][kNSeg mbarriers per chunk slot][a few words of CTA state][256 raw-word
-// flags].
-constexpr uint32_t kBarOffset = kTableBytes + kWarpRing + kWarps * kWarpRing;
-constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
-constexpr uint32_t kFlagsOffset = kMiscOffset + 64;   // 256 raw-word flags (bypass)
-constexpr uint32_t kFbOffset = kFlagsOffset + 256;    // 256 words B << 16 | f (wide models)
-constexpr uint32_t kSmemBytes = kFbOffset + 1024;
+// Shared memory of a CTA of W warps: [slot table 16 KiB][alignment slack 4
+// KiB][4 KiB ring per warp][kNSeg mbarriers per chunk slot][a few words of
+// CTA state][256 raw-word flags][256 (B, f) words].
+//
+// Two CTA shapes.  W = 8 with 4 CTAs per SM (32 warps, 64 registers a
+// thread) is the default.  W = 12 with 3 CTAs per SM (36 warps, at most 56
+// registers) lets each 16 KiB slot table serve 12 rings; it is used where a
+// warp decodes one chunk of a plain or byte-wise message.  Measured on B300
+// with the same message decoded by both shapes: 1 GiB plain 889 -> 866 us,
+// byte-wise 788 -> 832 GB/s; chunk pairs, bypass, adaptive and prefix
+// chunks are slower with 12 (batched decode 1325 -> 1254 GB/s).
+template <int W>
+struct Shape {
+    static constexpr int kWarps = W;
+    static constexpr uint32_t kThreads = W * 32;
+    static constexpr int kCtasPerSm = W == 12 ? 3 : 4;
+    static constexpr uint32_t kChunksPerCta = W * kChains;
+    static constexpr uint32_t kBarOffset = kTableBytes + kWarpRing + W * kWarpRing;
+    static constexpr uint32_t kMiscOffset = kBarOffset + kChunksPerCta * kNSeg * 8;
+    static constexpr uint32_t kFlagsOffset = kMiscOffset + 64;  // 256 raw-word flags (bypass)
+    static constexpr uint32_t kFbOffset = kFlagsOffset + 256;   // 256 words B << 16 | f (wide)
+    static constexpr uint32_t kSmemBytes = kFbOffset + 1024;
+    static_assert(W == 8 || W == 12, "the two measured shapes");
+    static_assert(kThreads >= kBuildThreads, "a table build needs 256 threads");
+    static_assert(kCtasPerSm * (kSmemBytes + 1024) <= 233472, "CTAs per SM fit in shared memory");
+};
+constexpr int kWarpsOne = 12;  // the shape for one plain or byte-wise chunk per warp
+constexpr uint32_t kBarOffset = Shape<kWarps>::kBarOffset;
+constexpr uint32_t kMiscOffset = Shape<kWarps>::kMiscOffset;
+constexpr uint32_t kFlagsOffset = Shape<kWarps>::kFlagsOffset;
+constexpr uint32_t kFbOffset = Shape<kWarps>::kFbOffset;
+constexpr uint32_t kSmemBytes = Shape<kWarps>::kSmemBytes;
 constexpr uint32_t kNoConst = 0xFFFFFFFFu;
 // Byte-wise messages (version 3): L = 2^23, b = 2^8, I = [2^23, 2^31).
 constexpr uint32_t kL8 = 1u << 23;
@@ -122,19 +148,21 @@ struct Smem {
     uint32_t fb_s;
 };
 
+template <int W = kWarps>
 __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
+    using S = Shape<W>;
     Smem s;
     s.tab = reinterpret_cast<uint32_t *>(smem);
     s.tab_s = smem_addr(smem);
     const uint32_t raw = smem_addr(smem + kTableBytes);
     s.rings_s = (raw + kWarpRing - 1) & ~(kWarpRing - 1);
     s.rings = smem + kTableBytes + (s.rings_s - raw);
-    s.bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
-    s.misc = reinterpret_cast<uint32_t *>(smem + kMiscOffset);
-    s.flags = smem + kFlagsOffset;
-    s.flags_s = smem_addr(smem + kFlagsOffset);
-    s.fb = reinterpret_cast<uint32_t *>(smem + kFbOffset);
-    s.fb_s = smem_addr(smem + kFbOffset);
+    s.bars = reinterpret_cast<uint64_t *>(smem + S::kBarOffset);
+    s.misc = reinterpret_cast<uint32_t *>(smem + S::kMiscOffset);
+    s.flags = smem + S::kFlagsOffset;
+    s.flags_s = smem_addr(smem + S::kFlagsOffset);
+    s.fb = reinterpret_cast<uint32_t *>(smem + S::kFbOffset);
+    s.fb_s = smem_addr(smem + S::kFbOffset);
     return s;
 }
 
@@ -185,21 +213,23 @@ __device__ __forceinline__ uint32_t ld_ring_u32(uint32_t a) {
 }
 
 // Build the 4096-entry slot table from 256 frequencies (zero for unused
-// symbols) with the whole CTA (kThreads threads).  scratch: >= 5 KiB of
-// shared memory not in use (the rings before any chunk is decoded).
+// symbols) with the whole CTA (the first kBuildThreads threads fill the
+// slots).  scratch: >= 5 KiB of shared memory not in use (the rings before
+// any chunk is decoded).
 // Returns (to every thread) the sum of the frequencies; *const_sym receives
 // the symbol with f = M, or kNoConst.
 //   cum[s] = f_0 + ... + f_{s-1}                       (warp scan)
 //   mark[cum[s]] = s for every s with f_s > 0           (scatter)
 //   sym(slot) = max of mark[0..slot]                    (max-scan: symbols
 //               are laid out in increasing order)
+template <int W = kWarps>
 __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, uint32_t *tab, uint8_t *scratch,
                                      uint32_t *const_sym) {
     uint32_t *cum = reinterpret_cast<uint32_t *>(scratch);        // 257 words
     uint8_t *mark = scratch + 1040;                               // 4096 bytes
     uint32_t *part = reinterpret_cast<uint32_t *>(scratch + 1040 + kM);  // 8 words
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t i = tid; i < kM / 4; i += kThreads) reinterpret_cast<uint32_t *>(mark)[i] = 0;
+    for (uint32_t i = tid; i < kM / 4; i += Shape<W>::kThreads) reinterpret_cast<uint32_t *>(mark)[i] = 0;
     if (tid < 32) {
         uint32_t v[8], run = 0;
 #pragma unroll
@@ -227,41 +257,48 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
         if (b - a == kM) *const_sym = tid;
     }
     __syncthreads();
-    // kThreads threads x 16 slots each
-    constexpr uint32_t kPer = kM / kThreads;
-    static_assert(kPer == 16, "slot table build assumes 256 threads");
+    // the first kBuildThreads threads (8 warps, whole warps) x 16 slots each;
+    // every thread reaches the barriers
+    constexpr uint32_t kPer = kM / kBuildThreads;
+    static_assert(kPer == 16, "16 slots a building thread");
+    const bool builder = Shape<W>::kThreads == kBuildThreads || tid < kBuildThreads;
     const uint32_t base = tid * kPer;
     uint32_t mk[kPer];
+    uint32_t incl = 0;
+    if (builder) {
 #pragma unroll
-    for (uint32_t q = 0; q < kPer / 4; ++q) {
-        const uint32_t w = reinterpret_cast<const uint32_t *>(mark + base)[q];
+        for (uint32_t q = 0; q < kPer / 4; ++q) {
+            const uint32_t w = reinterpret_cast<const uint32_t *>(mark + base)[q];
 #pragma unroll
-        for (uint32_t b = 0; b < 4; ++b) mk[4 * q + b] = (w >> (8 * b)) & 0xFFu;
+            for (uint32_t b = 0; b < 4; ++b) mk[4 * q + b] = (w >> (8 * b)) & 0xFFu;
+        }
+        uint32_t run = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kPer; ++i) {
+            run = max(run, mk[i]);
+            mk[i] = run;
+        }
+        // exclusive max-scan of the per-thread maxima across the builders
+        incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= uint32_t(d)) incl = max(incl, y);
+        }
+        if (lane == 31) part[warp] = incl;
     }
-    uint32_t run = 0;
-#pragma unroll
-    for (uint32_t i = 0; i < kPer; ++i) {
-        run = max(run, mk[i]);
-        mk[i] = run;
-    }
-    // exclusive max-scan of the per-thread maxima across the CTA
-    uint32_t incl = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= uint32_t(d)) incl = max(incl, y);
-    }
-    if (lane == 31) part[warp] = incl;
     __syncthreads();
-    uint32_t carry = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) carry = 0;
-    for (uint32_t w = 0; w < warp; ++w) carry = max(carry, part[w]);
+    if (builder) {
+        uint32_t carry = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0) carry = 0;
+        for (uint32_t w = 0; w < warp; ++w) carry = max(carry, part[w]);
 #pragma unroll
-    for (uint32_t i = 0; i < kPer; ++i) {
-        const uint32_t s = max(carry, mk[i]);
-        const uint32_t slot = base + i;
-        const uint32_t f = cum[s + 1] - cum[s];
-        tab[slot] = (f << 20) | ((slot - cum[s]) << 8) | s;
+        for (uint32_t i = 0; i < kPer; ++i) {
+            const uint32_t s = max(carry, mk[i]);
+            const uint32_t slot = base + i;
+            const uint32_t f = cum[s + 1] - cum[s];
+            tab[slot] = (f << 20) | ((slot - cum[s]) << 8) | s;
+        }
     }
     __syncthreads();
     return total;
@@ -276,6 +313,7 @@ __device__ __noinline__ static uint32_t build_slot_table(const uint16_t *freq, u
 // exclusive max-scan of the threads' maxima.  scratch: >= 1.1 KiB of free
 // shared memory.  Returns the frequencies' sum; *const_sym: the symbol with
 // f = M, or kNoConst.
+template <int W = kWarps>
 __device__ __noinline__ static uint32_t build_wide_table(const uint16_t *freq, uint32_t lm,
                                                          uint8_t *sym, uint32_t *fb,
                                                          uint8_t *scratch, uint32_t *const_sym) {
@@ -283,7 +321,7 @@ __device__ __noinline__ static uint32_t build_wide_table(const uint16_t *freq, u
     uint32_t *part = reinterpret_cast<uint32_t *>(scratch + 1040);  // 8 words
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = 1u << lm;
     uint32_t *sym32 = reinterpret_cast<uint32_t *>(sym);
-    for (uint32_t i = tid; i < M / 4; i += kThreads) sym32[i] = 0;
+    for (uint32_t i = tid; i < M / 4; i += Shape<W>::kThreads) sym32[i] = 0;
     if (tid < 32) {
         uint32_t v[8], run = 0;
 #pragma unroll
@@ -312,32 +350,40 @@ __device__ __noinline__ static uint32_t build_wide_table(const uint16_t *freq, u
         if (f == M) *const_sym = tid;
     }
     __syncthreads();
-    const uint32_t words = M / 4 / kThreads, base = tid * words;   // 8 or 16 words a thread
-    uint32_t run = 0;
-    for (uint32_t q = 0; q < words; ++q) {
-        const uint32_t w = sym32[base + q];
-        run = max(run, max(max(w & 0xFFu, (w >> 8) & 0xFFu), max((w >> 16) & 0xFFu, w >> 24)));
-    }
-    uint32_t incl = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= uint32_t(d)) incl = max(incl, y);
-    }
-    if (lane == 31) part[warp] = incl;
-    __syncthreads();
-    uint32_t carry = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) carry = 0;
-    for (uint32_t w = 0; w < warp; ++w) carry = max(carry, part[w]);
-    for (uint32_t q = 0; q < words; ++q) {
-        const uint32_t w = sym32[base + q];
-        uint32_t out = 0;
-#pragma unroll
-        for (uint32_t b = 0; b < 4; ++b) {
-            carry = max(carry, (w >> (8 * b)) & 0xFFu);
-            out |= carry << (8 * b);
+    // the first kBuildThreads threads (whole warps), 8 or 16 words each;
+    // every thread reaches the barriers
+    const bool builder = Shape<W>::kThreads == kBuildThreads || tid < kBuildThreads;
+    const uint32_t words = M / 4 / kBuildThreads, base = tid * words;
+    uint32_t incl = 0;
+    if (builder) {
+        uint32_t run = 0;
+        for (uint32_t q = 0; q < words; ++q) {
+            const uint32_t w = sym32[base + q];
+            run = max(run, max(max(w & 0xFFu, (w >> 8) & 0xFFu), max((w >> 16) & 0xFFu, w >> 24)));
         }
-        sym32[base + q] = out;
+        incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= uint32_t(d)) incl = max(incl, y);
+        }
+        if (lane == 31) part[warp] = incl;
+    }
+    __syncthreads();
+    if (builder) {
+        uint32_t carry = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0) carry = 0;
+        for (uint32_t w = 0; w < warp; ++w) carry = max(carry, part[w]);
+        for (uint32_t q = 0; q < words; ++q) {
+            const uint32_t w = sym32[base + q];
+            uint32_t out = 0;
+#pragma unroll
+            for (uint32_t b = 0; b < 4; ++b) {
+                carry = max(carry, (w >> (8 * b)) & 0xFFu);
+                out |= carry << (8 * b);
+            }
+            sym32[base + q] = out;
+        }
     }
     __syncthreads();
     return total;
@@ -346,14 +392,15 @@ __device__ __noinline__ static uint32_t build_wide_table(const uint16_t *freq, u
 // The 4096-entry decode table of a canonical prefix code, with the whole CTA:
 // the entries whose top len bits are symbol s's code hold len << 8 | s, the
 // rest kPrefixNoCode.  len[s] = 0: s not in the code.
+template <int W = kWarps>
 __device__ __noinline__ static void build_prefix_table(const uint8_t *len, const uint16_t *code,
                                                        uint32_t *tab) {
     const uint32_t tid = threadIdx.x;
-    for (uint32_t i = tid; i < kM / 4; i += kThreads)
+    for (uint32_t i = tid; i < kM / 4; i += Shape<W>::kThreads)
         reinterpret_cast<uint4 *>(tab)[i] =
             make_uint4(kPrefixNoCode, kPrefixNoCode, kPrefixNoCode, kPrefixNoCode);
     __syncthreads();
-    for (uint32_t s = tid; s < RANS_MAX_ALPHABET; s += kThreads) {
+    for (uint32_t s = tid; s < RANS_MAX_ALPHABET; s += Shape<W>::kThreads) {
         const uint32_t l = len[s];
         if (l == 0 || l > kPrefixMaxLen) continue;
         const uint32_t first = uint32_t(code[s]) << (kPrefixMaxLen - l), n = 1u << (kPrefixMaxLen - l);

@@ -14,8 +14,6 @@
 namespace rans {
 namespace {
 
-using dec::kSmemBytes;
-using dec::kWarps;
 
 struct DecodeParams {
     const uint8_t *msg;
@@ -47,18 +45,17 @@ constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::k
               kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix,
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14;
 
-// NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  Bypass and
-// byte-wise messages are decoded one chunk per warp.
-template <int NT, int KIND>
-__global__ void __launch_bounds__(dec::kThreads)
-    decode_kernel(const __grid_constant__ DecodeParams p) {
+// NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
+// CTA (dec::Shape).  Only plain messages with W = 8 pair chunks in a warp.
+template <int NT, int KIND, int W>
+__device__ __forceinline__ void decode_body(const DecodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPTIVE = KIND == kAdaptive;
     constexpr bool PREFIX = KIND == kPrefix;
     constexpr bool WIDE = KIND == kWide13 || KIND == kWide14;
     extern __shared__ __align__(128) uint8_t smem[];
-    const dec::Smem sm = dec::smem_layout(smem);
+    const dec::Smem sm = dec::smem_layout<W>(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t &hdr_ok = sm.misc[0];
     uint32_t &const_sym = sm.misc[1];
@@ -74,11 +71,11 @@ __global__ void __launch_bounds__(dec::kThreads)
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
     if (ADAPTIVE) __syncthreads();  // no table: the contexts live in registers
-    else if (PREFIX) dec::build_prefix_table(p.plen, p.pcode, sm.tab);
+    else if (PREFIX) dec::build_prefix_table<W>(p.plen, p.pcode, sm.tab);
     else if (WIDE)
-        dec::build_wide_table(p.freq, dec::WideBits<KIND>::kLog2, reinterpret_cast<uint8_t *>(sm.tab),
+        dec::build_wide_table<W>(p.freq, dec::WideBits<KIND>::kLog2, reinterpret_cast<uint8_t *>(sm.tab),
                               sm.fb, sm.rings, &const_sym);  // rings unused yet
-    else dec::build_slot_table(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
+    else dec::build_slot_table<W>(p.freq, sm.tab, sm.rings, &const_sym);  // rings unused yet
     if (!hdr_ok) {
         if (threadIdx.x == 0) report(p.status, RANS_ERR_CORRUPT);
         return;
@@ -91,7 +88,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     const uint32_t per = p.per_warp;
     const uint32_t n_units = (p.c_end - p.c_begin + per - 1) / per;
 
-    for (uint32_t q = blockIdx.x * kWarps + warp; q < n_units; q += gridDim.x * kWarps) {
+    for (uint32_t q = blockIdx.x * W + warp; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q * per;
         const uint32_t count = min(per, p.c_end - c);
         uint32_t st;
@@ -109,16 +106,37 @@ __global__ void __launch_bounds__(dec::kThreads)
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt, nullptr, sm.fb_s);
+        else if (W == dec::kWarps && per > 1)
+            st = dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
+                                              count, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
         else
-            st = per > 1 ? dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs,
-                                                        data_end, c, count, p.n_sym, p.CS, p.N,
-                                                        p.out, cs, lane, lt)
-                         : dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs,
-                                                         data_end, c, 1, p.n_sym, p.CS, p.N,
-                                                         p.out, cs, lane, lt);
+            st = dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1,
+                                               p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
+}
+
+// The two CTA shapes as kernels.  8 warps: bound by the CTA's threads alone,
+// the form these kernels were measured fastest with (a bound of 4 CTAs per SM
+// let bypass and 13/14-bit decoding take more registers, 5-10% slower).
+// 12 warps: 3 CTAs per SM, which caps a thread at 56 registers.
+template <int NT, int KIND>
+__global__ void __launch_bounds__(dec::kThreads)
+    decode_kernel(const __grid_constant__ DecodeParams p) {
+    decode_body<NT, KIND, dec::kWarps>(p);
+}
+template <int NT, int KIND>
+__global__ void __launch_bounds__(dec::Shape<dec::kWarpsOne>::kThreads,
+                                  dec::Shape<dec::kWarpsOne>::kCtasPerSm)
+    decode_kernel12(const __grid_constant__ DecodeParams p) {
+    decode_body<NT, KIND, dec::kWarpsOne>(p);
+}
+
+template <int NT, int KIND, int W>
+constexpr void (*kernel_for())(DecodeParams) {
+    if constexpr (W == dec::kWarps) return decode_kernel<NT, KIND>;
+    else return decode_kernel12<NT, KIND>;
 }
 
 // Chunks per warp for a message of n_chunks chunks when `warps` warps are
@@ -126,8 +144,9 @@ __global__ void __launch_bounds__(dec::kThreads)
 // least one chunk's latency and its last wave leaves warps idle.  One chunk
 // per warp streams through the warp's whole 4 KiB ring in 1 KiB copies; two
 // chunks per warp overlap two chains but have 2 KiB rings (512-byte copies)
-// and half the chains in flight.  Measured on a B300 (64 KiB chunks, N = 32;
-// w = n_chunks / resident warps; times in us):
+// and half the chains in flight.  Measured on a B300 with 8-warp CTAs for
+// both (64 KiB chunks, N = 32; w = n_chunks / resident warps; times in us;
+// one chunk per warp has since moved to 12-warp CTAs, 2.6% faster at 3.5):
 //   w      0.4  1.0  1.3  1.7  2.0  2.3  2.6  3.0  3.5  3.8   4.3   5.2
 //   one    202  292  430  562  561  654  722  833  958  1102  1175  1448
 //   two    271  331  431  561  560  658  758  905  1098 1100  1203  1384
@@ -135,31 +154,66 @@ uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
     return double(n_chunks) >= 5.0 * double(warps) ? dec::kChains : 1u;
 }
 
-template <int NT, int KIND>
-int launch_decode(DecodeParams &p, cudaStream_t stream) {
+// Resident CTAs of the W-warp kernel for <NT, KIND> on the whole GPU (0 on error);
+// sets its shared-memory limit once per device.
+template <int NT, int KIND, int W>
+uint64_t resident_ctas() {
+    using S = dec::Shape<W>;
     // Set once per device; concurrent first calls may both set it (harmless).
     static std::atomic<bool> configured[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !configured[dev].load()) {
-        if (cudaFuncSetAttribute(decode_kernel<NT, KIND>,
+        if (cudaFuncSetAttribute(kernel_for<NT, KIND, W>(),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(kSmemBytes)) != cudaSuccess)
-            return RANS_ERR_CUDA;
+                                 int(S::kSmemBytes)) != cudaSuccess)
+            return 0;
         configured[dev].store(true);
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<NT, KIND>, kWarps * 32,
-                                                      kSmemBytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for<NT, KIND, W>(),
+                                                      S::kThreads, S::kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
-        return RANS_ERR_CUDA;
-    const uint64_t cap = uint64_t(per_sm) * sm_count();
-    const uint64_t n_range = p.c_end - p.c_begin;
-    p.per_warp = KIND != kPlain ? 1u : chunks_per_warp(n_range, cap * kWarps);
-    const uint64_t want = ceil_div(n_range, uint64_t(kWarps) * p.per_warp);
+        return 0;
+    return uint64_t(per_sm) * sm_count();
+}
+
+template <int NT, int KIND, int W>
+int launch_shape(DecodeParams &p, uint64_t cap, uint32_t per_warp, cudaStream_t stream) {
+    using S = dec::Shape<W>;
+    p.per_warp = per_warp;
+    const uint64_t want = ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W) * per_warp);
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    decode_kernel<NT, KIND><<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    kernel_for<NT, KIND, W>()<<<grid, S::kThreads, S::kSmemBytes, stream>>>(p);
     return check_launch();
+}
+
+// Plain messages: chunk pairs in 8-warp CTAs from five waves up
+// (chunks_per_warp); one chunk per warp in 8-warp CTAs below one wave, where
+// more resident warps gain nothing and the 64-register form has the shorter
+// step (one 1 MiB chunk: 2.39 against 2.44 ms); otherwise one chunk per warp
+// in 12-warp CTAs.  Byte-wise messages: one chunk per warp in 12-warp CTAs.
+// The other kinds: one chunk per warp in 8-warp CTAs (dec::Shape).
+template <int NT, int KIND>
+int launch_decode(DecodeParams &p, cudaStream_t stream) {
+    const uint64_t n_range = p.c_end - p.c_begin;
+    if constexpr (KIND == kPlain) {
+        const uint64_t cap8 = resident_ctas<NT, KIND, dec::kWarps>();
+        if (!cap8) return RANS_ERR_CUDA;
+        if (chunks_per_warp(n_range, cap8 * dec::kWarps) > 1)
+            return launch_shape<NT, KIND, dec::kWarps>(p, cap8, dec::kChains, stream);
+        if (n_range < cap8 * dec::kWarps)
+            return launch_shape<NT, KIND, dec::kWarps>(p, cap8, 1, stream);
+    }
+    if constexpr (KIND == kPlain || KIND == kBytes) {
+        const uint64_t cap = resident_ctas<NT, KIND, dec::kWarpsOne>();
+        if (!cap) return RANS_ERR_CUDA;
+        return launch_shape<NT, KIND, dec::kWarpsOne>(p, cap, 1, stream);
+    } else {
+        const uint64_t cap = resident_ctas<NT, KIND, dec::kWarps>();
+        if (!cap) return RANS_ERR_CUDA;
+        return launch_shape<NT, KIND, dec::kWarps>(p, cap, 1, stream);
+    }
 }
 
 }  // namespace
