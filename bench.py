@@ -1018,7 +1018,7 @@ def main(argv=None):
             "decode_ms": dec_mean, "encode_ms": enc_mean,
             "encode_gbs": world * n / (enc_mean * 1e-3) / 1e9,
             "compression_ratio": msg_size / n, "bit_exact_roundtrip": bool(ok),
-            "roofline": {"kernel": "decode_kernel", "bound": "hbm", "achieved": achieved,
+            "roofline": {"kernel": "decode_kernel12", "bound": "hbm", "achieved": achieved,
                          "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": profiled_traffic(),
                          "algorithmic_bytes_per_launch": alg_bytes},
