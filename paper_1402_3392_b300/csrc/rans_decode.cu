@@ -1,7 +1,7 @@
-// rans_decode.cu -- single-message GPU decoder: one warp per chunk or per
-// pair of consecutive chunks (chosen per launch from the chunk count), each
+// rans_decode.cu -- single-message GPU decoder: one warp per chunk, the
 // chunk's N interleaved coders on the warp's lanes (decode_core.cuh), one
-// slot table per CTA built from the message's model.
+// slot table per CTA built from the message's model, in CTAs of 8 or 12
+// warps (chosen per launch from the kind and the chunk count).
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -27,7 +27,6 @@ struct DecodeParams {
     uint32_t data0;
     uint32_t c_begin;   // chunks [c_begin, c_end) are decoded by this launch
     uint32_t c_end;
-    uint32_t per_warp;  // chunks a warp decodes side by side: 1 or dec::kChains
     uint32_t kind;      // kPlain, kBypass (raw words after their symbols) or kBytes
     uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
@@ -46,7 +45,7 @@ constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::k
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
-// CTA (dec::Shape).  Only plain messages with W = 8 pair chunks in a warp.
+// CTA (dec::Shape).  A warp decodes one chunk at a time.
 template <int NT, int KIND, int W>
 __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
@@ -85,12 +84,10 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(p.msg + 32);
     const uint32_t data_end = offs[p.n_chunks];
     const uint32_t lt = lanemask_lt();
-    const uint32_t per = p.per_warp;
-    const uint32_t n_units = (p.c_end - p.c_begin + per - 1) / per;
+    const uint32_t n_units = p.c_end - p.c_begin;
 
     for (uint32_t q = blockIdx.x * W + warp; q < n_units; q += gridDim.x * W) {
-        const uint32_t c = p.c_begin + q * per;
-        const uint32_t count = min(per, p.c_end - c);
+        const uint32_t c = p.c_begin + q;
         uint32_t st;
         if (RAW)
             st = dec::decode_chunks<NT, false, kBypass>(wr, sm.tab_s, p.msg, p.data0, offs,
@@ -106,9 +103,6 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt, nullptr, sm.fb_s);
-        else if (W == dec::kWarps && per > 1)
-            st = dec::decode_chunks<NT, true>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c,
-                                              count, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
         else
             st = dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1,
                                                p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
@@ -139,21 +133,6 @@ constexpr void (*kernel_for())(DecodeParams) {
     else return decode_kernel12<NT, KIND>;
 }
 
-// Chunks per warp for a message of n_chunks chunks when `warps` warps are
-// resident.  A chunk is one chain of dependent steps, so a launch lasts at
-// least one chunk's latency and its last wave leaves warps idle.  One chunk
-// per warp streams through the warp's whole 4 KiB ring in 1 KiB copies; two
-// chunks per warp overlap two chains but have 2 KiB rings (512-byte copies)
-// and half the chains in flight.  Measured on a B300 with 8-warp CTAs for
-// both (64 KiB chunks, N = 32; w = n_chunks / resident warps; times in us;
-// one chunk per warp has since moved to 12-warp CTAs, 2.6% faster at 3.5):
-//   w      0.4  1.0  1.3  1.7  2.0  2.3  2.6  3.0  3.5  3.8   4.3   5.2
-//   one    202  292  430  562  561  654  722  833  958  1102  1175  1448
-//   two    271  331  431  561  560  658  758  905  1098 1100  1203  1384
-uint32_t chunks_per_warp(uint64_t n_chunks, uint64_t warps) {
-    return double(n_chunks) >= 5.0 * double(warps) ? dec::kChains : 1u;
-}
-
 // Resident CTAs of the W-warp kernel for <NT, KIND> on the whole GPU (0 on error);
 // sets its shared-memory limit once per device.
 template <int NT, int KIND, int W>
@@ -179,40 +158,39 @@ uint64_t resident_ctas() {
 }
 
 template <int NT, int KIND, int W>
-int launch_shape(DecodeParams &p, uint64_t cap, uint32_t per_warp, cudaStream_t stream) {
+int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
     using S = dec::Shape<W>;
-    p.per_warp = per_warp;
-    const uint64_t want = ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W) * per_warp);
+    const uint64_t want = ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W));
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     kernel_for<NT, KIND, W>()<<<grid, S::kThreads, S::kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
-// Plain messages: chunk pairs in 8-warp CTAs from five waves up
-// (chunks_per_warp); one chunk per warp in 8-warp CTAs below one wave, where
-// more resident warps gain nothing and the 64-register form has the shorter
-// step (one 1 MiB chunk: 2.39 against 2.44 ms); otherwise one chunk per warp
-// in 12-warp CTAs.  Byte-wise messages: one chunk per warp in 12-warp CTAs.
-// The other kinds: one chunk per warp in 8-warp CTAs (dec::Shape).
+// A warp decodes one chunk.  Plain messages under one wave of chunks: 8-warp
+// CTAs, where more resident warps gain nothing and the 64-register form has
+// the shorter step (one 1 MiB chunk: 2.41 against 2.44 ms).  Plain messages
+// of a wave or more, and byte-wise messages: 12-warp CTAs.  The other kinds:
+// 8-warp CTAs (dec::Shape).  Two chunks side by side in a warp of an 8-warp
+// CTA were faster than one per warp in 8-warp CTAs from five waves up; one
+// per warp in 12-warp CTAs beats both (32256 chunks of 64 Ki symbols, 6.8
+// waves: 1636 against 1814 us), so single messages no longer pair chunks.
 template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
     const uint64_t n_range = p.c_end - p.c_begin;
     if constexpr (KIND == kPlain) {
         const uint64_t cap8 = resident_ctas<NT, KIND, dec::kWarps>();
         if (!cap8) return RANS_ERR_CUDA;
-        if (chunks_per_warp(n_range, cap8 * dec::kWarps) > 1)
-            return launch_shape<NT, KIND, dec::kWarps>(p, cap8, dec::kChains, stream);
         if (n_range < cap8 * dec::kWarps)
-            return launch_shape<NT, KIND, dec::kWarps>(p, cap8, 1, stream);
+            return launch_shape<NT, KIND, dec::kWarps>(p, cap8, stream);
     }
     if constexpr (KIND == kPlain || KIND == kBytes) {
         const uint64_t cap = resident_ctas<NT, KIND, dec::kWarpsOne>();
         if (!cap) return RANS_ERR_CUDA;
-        return launch_shape<NT, KIND, dec::kWarpsOne>(p, cap, 1, stream);
+        return launch_shape<NT, KIND, dec::kWarpsOne>(p, cap, stream);
     } else {
         const uint64_t cap = resident_ctas<NT, KIND, dec::kWarps>();
         if (!cap) return RANS_ERR_CUDA;
-        return launch_shape<NT, KIND, dec::kWarps>(p, cap, 1, stream);
+        return launch_shape<NT, KIND, dec::kWarps>(p, cap, stream);
     }
 }
 
