@@ -464,17 +464,25 @@ int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n_streams,
  */
 #define RANS_REQ_ENCODE 0u
 #define RANS_REQ_DECODE 1u
+/* Or'ed into kind: input and output are device memory (a message input and
+ * an encode output 16-byte aligned).  The coders then read and write them in
+ * place: no copies, and only the batch's scratch and descriptors take arena
+ * memory.  The request is done when its kernels are. */
+#define RANS_REQ_DEVICE_MEMORY 0x100u
 
 typedef struct {
-    uint32_t kind;            /* RANS_REQ_ENCODE or RANS_REQ_DECODE */
+    uint32_t kind;            /* RANS_REQ_ENCODE or RANS_REQ_DECODE, optionally
+                                 | RANS_REQ_DEVICE_MEMORY */
     uint32_t table;           /* model index in the server's d_freqs */
     uint32_t n_lanes;         /* N of the message (made or read) */
     uint32_t chunk_symbols;   /* chunk size of the message */
-    const uint8_t *input;     /* host (page-locked for overlap): symbols (encode)
-                                 or a message (decode) */
+    const uint8_t *input;     /* host (page-locked for overlap), or device with
+                                 RANS_REQ_DEVICE_MEMORY: symbols (encode) or a
+                                 message (decode) */
     uint64_t input_size;      /* bytes: = n_symbols (encode), message size (decode) */
     uint64_t n_symbols;       /* symbols in the request */
-    uint8_t *output;          /* host: receives the message (encode) or symbols (decode) */
+    uint8_t *output;          /* host (device with RANS_REQ_DEVICE_MEMORY): receives
+                                 the message (encode) or symbols (decode) */
     uint64_t output_cap;      /* >= rans_max_encoded_size (encode), >= n_symbols (decode) */
     double arrival_s;         /* arrival, seconds after rans_server_run starts;
                                  non-decreasing along the trace */
@@ -486,7 +494,8 @@ typedef struct {
                                  request can never fit the budget */
     uint32_t batch;           /* index of the batch that served it */
     double admit_s;           /* admission time, seconds after the start */
-    double done_s;            /* completion (output in host memory) */
+    double done_s;            /* completion (output in host memory, or in the
+                                 device output for RANS_REQ_DEVICE_MEMORY) */
 } rans_result;
 
 typedef struct rans_server rans_server;
@@ -496,7 +505,11 @@ typedef struct rans_server rans_server;
  * resident); d_arena: device memory of arena_bytes (16-byte aligned) that
  * bounds everything the server places on the device; max_batch: requests per
  * batch; n_slots: batches in flight at once (1..16).  Creates CUDA streams,
- * events and page-locked staging; allocates no device memory.
+ * events and page-locked staging; allocates no device memory.  The arena is
+ * the server's budget, not the process's whole device footprint: the
+ * library's fixed RANS_STATIC_SCRATCH_BYTES array (see
+ * rans_encode_static_scratch), held by every GPU that loads the library,
+ * comes on top of it.
  */
 int rans_server_create(const uint16_t *d_freqs, uint32_t n_tables, void *d_arena,
                        uint64_t arena_bytes, uint32_t max_batch, uint32_t n_slots,
@@ -527,7 +540,8 @@ void rans_server_destroy(rans_server *server);
  * library.
  *
  * Arguments, output format and status codes are those of rans_encode,
- * without d_scratch/scratch_cap.  The scratch is a file-scope device array of
+ * without d_scratch/scratch_cap; the model may sum to 2^12, 2^13 or 2^14 as
+ * there.  The scratch is a file-scope device array of
  * RANS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  An input whose scratch need,
  * rans_encode_scratch_size(n_symbols, params), exceeds that returns
@@ -536,7 +550,12 @@ void rans_server_destroy(rans_server *server);
  *
  * - The first call on a device, with that device current, looks up the
  *   array's device address (cudaGetSymbolAddress); make that first call
- *   before any stream capture.  No call allocates device memory.
+ *   before any stream capture.  No call allocates device memory.  The
+ *   address is kept until the process exits, so after a reset of the
+ *   device's context (cudaDeviceReset) this entry point must not be called
+ *   again in the same process.
+ * - The array counts against the device's memory on top of any budget the
+ *   caller manages (for example rans_server_create's arena).
  * - Every call on a device shares the one array and leaves its contents
  *   behind; nothing in it needs to start at zero.  Calls whose work overlaps
  *   on the GPU (different streams, or different host threads without
@@ -582,6 +601,29 @@ int rans_check_bounded_wait(uint32_t *d_status, rans_stream_t stream);
  * overlap (they share one small device array).
  */
 int rans_check_lookback_wait(uint32_t *d_status, rans_stream_t stream);
+
+/*
+ * rans_check_division -- diagnostic of the encoders' exact division; no step
+ * of the paper's method, but C(s, x) = floor(x / f_s) * M + B_s + (x mod f_s)
+ * (Section 2) needs floor(x / f_s) exactly, and the encoders compute it
+ * without a divide.  Enqueues one kernel that runs the encoders' own division
+ * code over every frequency f in [1, M - 1] (M = 2^log2m) and every state x
+ * in the range it is applied to, the precursor set I_s = [f L / M, f b L / M)
+ * of Section 2 (L = b = 2^16), and checks each quotient q against the
+ * definition q * f <= x < (q + 1) * f in 64-bit integers.
+ *
+ * method   : 0 = the multiply-high by the table's reciprocal (static models,
+ *            log2m 12, 13 or 14); 1 = the adaptive coder's float estimate and
+ *            one correction (log2m 12; the remainder is checked too).
+ * d_result : device, 8-byte aligned, 4 u64, overwritten: [0] states checked,
+ *            [1] wrong quotients, [2] the smallest f << 32 | x that was wrong
+ *            (~0 if none), [3] 0.
+ * Returns RANS_OK when the kernels were enqueued, RANS_ERR_INVALID_ARG for a
+ * bad method/log2m or pointer, RANS_ERR_CUDA on a launch error.  It takes
+ * seconds of GPU time (about 9e12 states at log2m 12, 3.5e13 at 14).
+ */
+int rans_check_division(uint32_t method, uint32_t log2m, uint64_t *d_result,
+                        rans_stream_t stream);
 
 /*
  * Checked builds (a test build compiled with -DRANS_CHECKED; the library

@@ -117,6 +117,10 @@ constexpr int kKindPlain = 0, kKindRaw = 1, kKindBytes = 2, kKindAdaptive = 3, k
 // Their model takes a slot -> symbol byte table (M bytes, in the table area)
 // and a symbol -> (B_s << 16 | f_s) table of 256 words.
 constexpr int kKindWide13 = 5, kKindWide14 = 6;
+// Plain messages whose model has two symbols, 0 and 1, both with f > 0 (a
+// binary model, rABS in the paper's terms, Section 2): D needs no table.
+// The same bitstream as kKindPlain; only the decoder's step differs.
+constexpr int kKindBinary = 7;
 template <int KIND>
 struct WideBits {
     static constexpr uint32_t kLog2 = KIND == kKindWide13 ? 13u : 14u;
@@ -642,6 +646,32 @@ __device__ __forceinline__ void decode_step_wide(uint32_t &x, uint32_t &rp, bool
     rp = imad(__popc(m), 2u, rp);
 }
 
+// One step with a binary model (f_0 + f_1 = M, both > 0): the symbol is
+// [slot >= f_0], and D is x = f_s * floor(x/M) + slot - B_s with B_0 = 0,
+// B_1 = f_0 -- two multiply-adds, one of them kept, instead of a table load.
+__device__ __forceinline__ uint32_t decode_update_binary(uint32_t x, uint32_t f0, uint32_t f1,
+                                                         uint32_t &one) {
+    const uint32_t slot = x & (kM - 1), q = x >> kLog2M;
+    one = slot >= f0;
+    return one ? imad(f1, q, slot - f0) : imad(f0, q, slot);
+}
+
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step_binary(uint32_t &x, uint32_t &rp, bool active,
+                                                   uint32_t f0, uint32_t f1, uint32_t ring_s,
+                                                   uint8_t *outp, uint32_t lt) {
+    if (FULL || active) {
+        uint32_t one;
+        x = decode_update_binary(x, f0, f1, one);
+        *outp = uint8_t(one);
+    }
+    const bool need = (FULL || active) && x < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
+    if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
+    rp = imad(__popc(m), 2u, rp);
+}
+
 // One step of two chunks a and b, their instructions interleaved.
 template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32_t ra_s, uint8_t *oa,
@@ -654,6 +684,31 @@ __device__ __forceinline__ void decode_step2(uint32_t &xa, uint32_t &rpa, uint32
         xb = decode_update(xb, eb);
         *oa = uint8_t(ea);
         *ob = uint8_t(eb);
+    }
+    const bool na = (FULL || active) && xa < kL;
+    const bool nb = (FULL || active) && xb < kL;
+    const uint32_t ma = __ballot_sync(kFull, na);
+    const uint32_t mb = __ballot_sync(kFull, nb);
+    const uint32_t wa = ld_ring_u16(((rpa + 2u * __popc(ma & lt)) & (RING - 1)) | ra_s);
+    const uint32_t wb = ld_ring_u16(((rpb + 2u * __popc(mb & lt)) & (RING - 1)) | rb_s);
+    if (na) xa = __byte_perm(xa, wa, 0x1054u);
+    if (nb) xb = __byte_perm(xb, wb, 0x1054u);
+    rpa = imad(__popc(ma), 2u, rpa);
+    rpb = imad(__popc(mb), 2u, rpb);
+}
+
+// decode_step2 for a binary model (f0, f1).
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void decode_step2_binary(uint32_t &xa, uint32_t &rpa, uint32_t ra_s,
+                                                    uint8_t *oa, uint32_t &xb, uint32_t &rpb,
+                                                    uint32_t rb_s, uint8_t *ob, bool active,
+                                                    uint32_t f0, uint32_t f1, uint32_t lt) {
+    if (FULL || active) {
+        uint32_t sa, sb;
+        xa = decode_update_binary(xa, f0, f1, sa);
+        xb = decode_update_binary(xb, f0, f1, sb);
+        *oa = uint8_t(sa);
+        *ob = uint8_t(sb);
     }
     const bool na = (FULL || active) && xa < kL;
     const bool nb = (FULL || active) && xb < kL;
@@ -793,6 +848,8 @@ __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s,
     else if (KIND == kKindWide13 || KIND == kKindWide14)  // flags_s: the f/B table
         decode_step_wide<FULL, RING, WideBits<KIND>::kLog2>(c.x, c.rp, active, tab_s, flags_s,
                                                            ring_s, outp, lt);
+    else if (KIND == kKindBinary)  // tab_s, flags_s: f_0, f_1
+        decode_step_binary<FULL, RING>(c.x, c.rp, active, tab_s, flags_s, ring_s, outp, lt);
     else
         decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
 }
@@ -810,7 +867,8 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
         // Measured on B300: 2-3.5 % faster for plain, bypass and byte-wise
         // chunks alone in a warp's ring; no gain for adaptive, prefix and
         // 13/14-bit chunks, and slower for chunk pairs (more code).
-        constexpr bool kLinear = (KIND == kKindPlain || KIND == kKindRaw || KIND == kKindBytes) &&
+        constexpr bool kLinear = (KIND == kKindPlain || KIND == kKindRaw || KIND == kKindBytes ||
+                                  KIND == kKindBinary) &&
                                  G::kRing == kWarpRing;
         if (kLinear && off + G::kGroup * G::kStep <= G::kRing) {
             // A group reads at most kGroup * kStep bytes from rp: here they
@@ -939,7 +997,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     constexpr bool RAW = KIND == kKindRaw;
     constexpr bool BYTES = KIND == kKindBytes;
     constexpr bool PREFIX = KIND == kKindPrefix;
-    static_assert(!(PAIR && KIND != kKindPlain), "only plain messages pair chunks");
+    static_assert(!(PAIR && KIND != kKindPlain && KIND != kKindBinary),
+                  "only plain messages pair chunks");
+    constexpr bool BINARY = KIND == kKindBinary;
     using G = typename std::conditional<
         RAW, GeoRaw,
         typename std::conditional<PREFIX, GeoPrefix,
@@ -989,16 +1049,25 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
             RANS_CHECK(w.timeouts || (ring_window_ok<G>(a, G::kGroup * G::kStep) &&
                                       ring_window_ok<G>(b, G::kGroup * G::kStep)));
 #pragma unroll
-            for (uint32_t u = 0; u < G::kGroup; ++u)
-                decode_step2<kFullWarp, G::kRing>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x,
-                                                  b.rp, w.r[1].ring_s, b.outp + u * N, lane_on,
-                                                  tab_s, lt);
+            for (uint32_t u = 0; u < G::kGroup; ++u) {
+                if (BINARY)
+                    decode_step2_binary<kFullWarp, G::kRing>(
+                        a.x, a.rp, w.r[0].ring_s, a.outp + u * N, b.x, b.rp, w.r[1].ring_s,
+                        b.outp + u * N, lane_on, tab_s, flags_s, lt);
+                else
+                    decode_step2<kFullWarp, G::kRing>(a.x, a.rp, w.r[0].ring_s, a.outp + u * N,
+                                                      b.x, b.rp, w.r[1].ring_s, b.outp + u * N,
+                                                      lane_on, tab_s, lt);
+            }
             a.outp += G::kGroup * N;
             b.outp += G::kGroup * N;
         }
     }
     chain_run<kFullWarp, G, KIND>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
-    if (two) chain_run<kFullWarp, G>(b, w.r[1], w.timeouts, N, lane_on, lane, tab_s, lt);
+    if (two)
+        chain_run<kFullWarp, G, BINARY ? kKindBinary : kKindPlain>(b, w.r[1], w.timeouts, N,
+                                                                    lane_on, lane, tab_s, lt,
+                                                                    flags_s);
     const uint32_t sa = chain_close<G, BYTES, PREFIX>(a, w.r[0], w.timeouts, lane_on, N);
     const uint32_t sb = two ? chain_close<G>(b, w.r[1], w.timeouts, lane_on) : RANS_OK;
     return sa != RANS_OK ? sa : sb;

@@ -103,12 +103,45 @@ __device__ __forceinline__ Smem smem_layout(uint8_t *smem) {
     return s;
 }
 
+// floor(x / f) for every x < 2^32 by a multiply-high (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// with k = ceil(log2 f) and m = ceil(2^(32+k) / f) = 2^32 + m_lo, the
+// quotient is (x + umulhi(x, m_lo)) >> k, the sum taken in 33 bits.  m is
+// 2^(32+k)/f + e with 0 <= e < 1, so the error x*e/2^(32+k) < 2^-k <= 1/f
+// never carries x/f past the next integer.  reciprocal() gives (m_lo, k);
+// div_reciprocal() takes k from the low 5 bits of kbits (the funnel shift's
+// wrap mode), so a table word holding k in bits 12..16 can be passed whole.
+__host__ __device__ inline void reciprocal(uint32_t f, uint32_t &m_lo, uint32_t &k) {
+    k = 0;
+    while ((1u << k) < f) ++k;
+    const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
+    m_lo = uint32_t(m - (1ull << 32));
+}
+__device__ __forceinline__ uint32_t div_reciprocal(uint32_t x, uint32_t m_lo, uint32_t kbits) {
+    const uint64_t sum = uint64_t(x) + __umulhi(x, m_lo);
+    return __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), kbits);
+}
+
+// floor(x / f) and x mod f for 1 <= f < M and x < f * 2^20, as the adaptive
+// coder computes them: a float estimate rounded towards zero at every step
+// (reciprocal, conversion, product), so never above x/f and, since x/f <
+// 2^20 and each rounding loses less than 2^-23 relative, below it by less
+// than 1; then one exact correction by the remainder.
+__device__ __forceinline__ uint32_t div_float(uint32_t x, uint32_t f, uint32_t &r) {
+    const float rf = __frcp_rz(float(f));
+    uint32_t q = __float2uint_rz(__fmul_rz(__uint2float_rz(x), rf));
+    r = x - q * f;
+    if (r >= f) {
+        ++q;
+        r -= f;
+    }
+    return q;
+}
+
 // Encode-table entry for symbol s with frequency f (1 <= f <= M):
 //   .x = m_lo = ceil(2^(32+k) / f) - 2^32,  k = ceil(log2 f)   (0 <= m_lo < 2^32)
 //   .y = (M - f) << 20 | k << 12 | B_s
-// floor(x/f) = (x + umulhi(x, m_lo)) >> k for every x < 2^32: with
-// m = 2^(32+k)/f + e, 0 <= e < 1, the error x*e/2^(32+k) < 2^-k <= 1/f never
-// carries x/f past the next integer.
+// floor(x/f) = div_reciprocal(x, m_lo, k) for every x < 2^32.
 // Emit test: x >= f * 2^20  <=>  x > f * 2^20 - 1 = ~((M - f) << 20)  (u32).
 // Built by the whole CTA; cum: 257 words of free shared memory.  Returns the
 // sum of the frequencies to every thread.
@@ -143,9 +176,8 @@ __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq,
         if (f == 0) {
             t = make_uint2(0u, kZeroFlag);  // never emits, leaves x unchanged
         } else {
-            const uint32_t k = 32u - __clz(f - 1u);
-            const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
-            t.x = uint32_t(m - (1ull << 32));
+            uint32_t k;
+            reciprocal(f, t.x, k);
             t.y = ((kM - (f & (2 * kM - 1))) << 20) | (k << 12) | (cum[s] & (kM - 1));
             if (raw_words && raw_words[s]) t.y |= kRawFlag;  // the shift uses k's 5 bits only
         }
@@ -192,9 +224,8 @@ __device__ __noinline__ static uint32_t build_wide_encode_table(const uint16_t *
         if (f == 0) {
             t = make_uint4(0u, 0xFFFFFFFFu, 0u, kZeroFlag);
         } else {
-            const uint32_t k = 32u - __clz(f - 1u);
-            const uint64_t m = ((1ull << (32 + k)) + f - 1) / f;
-            t.x = uint32_t(m - (1ull << 32));
+            uint32_t k;
+            reciprocal(f, t.x, k);
             t.y = uint32_t((uint64_t(f) << (32 - lm)) - 1);
             t.z = M - f;
             t.w = (cum[s] & 0xFFFFu) | (k << 24);
@@ -264,8 +295,7 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
     else wp = imad_u32(__popc(m), 0u - 2u, wp);
     if (on) {
         // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
-        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
-        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        const uint32_t q = div_reciprocal(x, t.x, t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
     }
 }
@@ -287,8 +317,7 @@ __device__ __forceinline__ void encode_step_wide(uint32_t &x, uint32_t &wp, uint
     if (RING) wp -= 2u * __popc(m);
     else wp = imad_u32(__popc(m), 0u - 2u, wp);
     if (on) {
-        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
-        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.w >> 24);
+        const uint32_t q = div_reciprocal(x, t.x, t.w >> 24);
         x = x + q * t.z + (t.w & 0xFFFFu);
     }
 }
@@ -320,8 +349,7 @@ __device__ __forceinline__ void encode_step_bytes(uint32_t &x, uint32_t &wp, uin
     if (e1) x >>= e2 ? 16 : 8;
     wp -= n1 + n2;
     if (on) {
-        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
-        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        const uint32_t q = div_reciprocal(x, t.x, t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
     }
 }
@@ -404,13 +432,8 @@ __device__ __forceinline__ void encode_step_adaptive(uint32_t &x, uint32_t &wp, 
     }
     wp -= 2u * __popc(m);
     if (on) {
-        const float rf = __frcp_rz(float(f));
-        uint32_t q = __float2uint_rz(__fmul_rz(__uint2float_rz(x), rf));
-        uint32_t r = x - q * f;
-        if (r >= f) {
-            ++q;
-            r -= f;
-        }
+        uint32_t r;
+        const uint32_t q = div_float(x, f, r);
         x = (q << kLog2M) + (one ? p : 0u) + r;
     }
 }
@@ -465,8 +488,7 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
     }
     wp -= 2u * (__popc(m) + __popc(mr));
     if (on) {
-        const uint64_t sum = uint64_t(x) + __umulhi(x, t.x);
-        const uint32_t q = __funnelshift_r(uint32_t(sum), uint32_t(sum >> 32), t.y >> 12);
+        const uint32_t q = div_reciprocal(x, t.x, t.y >> 12);
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
     }
 }

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(dec::kThreads)
     uint32_t &const_sym = sm.misc[3];
     uint32_t &model_ok = sm.misc[4];
     uint32_t &hdr_ok = sm.misc[5];
+    uint32_t &bin_f = sm.misc[6];       // binary model: f_0 | f_1 << 16, else 0
     if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
     dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t lt = lanemask_lt();
@@ -156,12 +157,29 @@ __global__ void __launch_bounds__(dec::kThreads)
         const uint32_t s = stream_s;
         const rans_stream d = p.streams[s];
         if (d.table != loaded) {
-            if (threadIdx.x == 0) const_sym = dec::kNoConst;
-            const uint32_t sum =
-                dec::build_slot_table(p.freqs + uint64_t(d.table) * 256, sm.tab, sm.rings, &const_sym);
-            if (threadIdx.x == 0) {
-                loaded = d.table;
-                model_ok = sum == kM;
+            // A binary model (symbols 0 and 1 only, both with f > 0) needs no
+            // slot table: its D is two multiply-adds (dec::kKindBinary).
+            const uint16_t *fr = p.freqs + uint64_t(d.table) * 256;
+            const uint32_t f0 = fr[0], f1 = fr[1];
+            bool binary = f0 > 0 && f1 > 0 && f0 + f1 == kM;
+            for (uint32_t k = 2 + lane; binary && k < 256; k += 32) binary = fr[k] == 0;
+            binary = __all_sync(kFull, binary);
+            const bool cta_binary = __syncthreads_and(binary);
+            if (cta_binary) {
+                if (threadIdx.x == 0) {
+                    const_sym = dec::kNoConst;
+                    loaded = d.table;
+                    model_ok = 1;
+                    bin_f = f0 | (f1 << 16);
+                }
+            } else {
+                if (threadIdx.x == 0) const_sym = dec::kNoConst;
+                const uint32_t sum = dec::build_slot_table(fr, sm.tab, sm.rings, &const_sym);
+                if (threadIdx.x == 0) {
+                    loaded = d.table;
+                    model_ok = sum == kM;
+                    bin_f = 0;
+                }
             }
             __syncthreads();
         }
@@ -180,14 +198,28 @@ __global__ void __launch_bounds__(dec::kThreads)
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
             const uint32_t count = uint32_t(umin64(dec::kChains, g.n_chunks - c));
-            const uint32_t st =
-                d.n_lanes == 32
-                    ? dec::decode_chunks<32, true>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
-                                             d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane,
-                                             lt)
-                    : dec::decode_chunks<0, true>(wr, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
-                                            d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs,
-                                            lane, lt);
+            const uint32_t bf = bin_f;
+            uint32_t st;
+            if (bf)  // binary model: f_0 and f_1 ride in the table and flag arguments
+                st = d.n_lanes == 32
+                         ? dec::decode_chunks<32, true, dec::kKindBinary>(
+                               wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
+                               d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane, lt, nullptr,
+                               bf >> 16)
+                         : dec::decode_chunks<0, true, dec::kKindBinary>(
+                               wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
+                               d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs, lane, lt,
+                               nullptr, bf >> 16);
+            else
+                st = d.n_lanes == 32
+                         ? dec::decode_chunks<32, true>(wr, sm.tab_s, d.msg, g.data0, offs,
+                                                        data_end, c, count, d.n_symbols,
+                                                        d.chunk_symbols, 32, d.symbols, cs, lane,
+                                                        lt)
+                         : dec::decode_chunks<0, true>(wr, sm.tab_s, d.msg, g.data0, offs,
+                                                       data_end, c, count, d.n_symbols,
+                                                       d.chunk_symbols, d.n_lanes, d.symbols, cs,
+                                                       lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);
         }
     }

@@ -42,7 +42,8 @@ struct DecodeParams {
 // prefix (version 5: canonical prefix codes in their decoder's read order).
 constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::kKindBytes,
               kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix,
-              kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14;
+              kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14,
+              kBinary = dec::kKindBinary;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
 // CTA (dec::Shape).  A warp decodes one chunk at a time.
@@ -53,6 +54,7 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     constexpr bool ADAPTIVE = KIND == kAdaptive;
     constexpr bool PREFIX = KIND == kPrefix;
     constexpr bool WIDE = KIND == kWide13 || KIND == kWide14;
+    constexpr bool BINARY = KIND == kBinary;  // a plain message with a binary model
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout<W>(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -69,7 +71,7 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
-    if (ADAPTIVE) __syncthreads();  // no table: the contexts live in registers
+    if (ADAPTIVE || BINARY) __syncthreads();  // no table: contexts, or f_0 and f_1
     else if (PREFIX) dec::build_prefix_table<W>(p.plen, p.pcode, sm.tab);
     else if (WIDE)
         dec::build_wide_table<W>(p.freq, dec::WideBits<KIND>::kLog2, reinterpret_cast<uint8_t *>(sm.tab),
@@ -103,6 +105,10 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt, nullptr, sm.fb_s);
+        else if (BINARY)  // f_0 and f_1 ride in the table and flag arguments
+            st = dec::decode_chunks<NT, false, KIND>(wr, p.freq[0], p.msg, p.data0, offs,
+                                                     data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
+                                                     cs, lane, lt, nullptr, p.freq[1]);
         else
             st = dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1,
                                                p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
@@ -177,13 +183,13 @@ int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
 template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
     const uint64_t n_range = p.c_end - p.c_begin;
-    if constexpr (KIND == kPlain) {
+    if constexpr (KIND == kPlain || KIND == kBinary) {
         const uint64_t cap8 = resident_ctas<NT, KIND, dec::kWarps>();
         if (!cap8) return RANS_ERR_CUDA;
         if (n_range < cap8 * dec::kWarps)
             return launch_shape<NT, KIND, dec::kWarps>(p, cap8, stream);
     }
-    if constexpr (KIND == kPlain || KIND == kBytes) {
+    if constexpr (KIND == kPlain || KIND == kBytes || KIND == kBinary) {
         const uint64_t cap = resident_ctas<NT, KIND, dec::kWarpsOne>();
         if (!cap) return RANS_ERR_CUDA;
         return launch_shape<NT, KIND, dec::kWarpsOne>(p, cap, stream);
@@ -227,6 +233,11 @@ static int prepare_decode(const uint8_t *msg, uint64_t msg_size, const uint16_t 
     p.log2m = lm;
     p.kind = lm == 13 ? kWide13 : lm == 14 ? kWide14 : kPlain;
     for (uint32_t s = 0; s < n_alpha; ++s) p.freq[s] = h_freq[s];
+    // symbols 0 and 1 only, both possible: the table-free binary decoder
+    bool binary = lm == RANS_LOG2_M && n_alpha >= 2 && p.freq[0] > 0 && p.freq[1] > 0 &&
+                  p.freq[0] + p.freq[1] == RANS_M;
+    for (uint32_t s = 2; binary && s < n_alpha; ++s) binary = p.freq[s] == 0;
+    if (binary) p.kind = kBinary;
     return RANS_OK;
 }
 
@@ -245,6 +256,8 @@ static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaSt
         return p.N == 32 ? launch_decode<32, kWide13>(p, st) : launch_decode<0, kWide13>(p, st);
     if (p.kind == kWide14)
         return p.N == 32 ? launch_decode<32, kWide14>(p, st) : launch_decode<0, kWide14>(p, st);
+    if (p.kind == kBinary)
+        return p.N == 32 ? launch_decode<32, kBinary>(p, st) : launch_decode<0, kBinary>(p, st);
     return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 

@@ -411,7 +411,9 @@ static __device__ __align__(256) uint8_t g_static_scratch[RANS_STATIC_SCRATCH_BY
 // Device address of g_static_scratch per device, looked up on the first call
 // made with that device current.  The host-side name of the array is only a
 // stand-in for the symbol, never a device address, so it is never passed to a
-// kernel.
+// kernel.  The address is kept for the life of the process: a reset of the
+// device's context (cudaDeviceReset) would leave it stale, which rans.h
+// states as a limit of this entry point.
 std::mutex g_static_mu;
 uint8_t *g_static_ptr[64] = {nullptr};
 
@@ -437,7 +439,9 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
                                           const rans_params *params, uint8_t *d_out,
                                           uint64_t out_cap, uint64_t *d_out_size,
                                           uint32_t *d_status, rans_stream_t stream) {
-    if (!params_ok(params) || !table_ok(h_freq, n_alpha, nullptr) || !d_out || !d_out_size ||
+    // The model may sum to 2^12, 2^13 or 2^14, as for rans_encode.
+    uint32_t lm = RANS_LOG2_M;
+    if (!params_ok(params) || !table_log2m(h_freq, n_alpha, &lm) || !d_out || !d_out_size ||
         !d_status || !aligned16(d_out))
         return RANS_ERR_INVALID_ARG;
     if (n_symbols && !d_symbols) return RANS_ERR_INVALID_ARG;
@@ -471,13 +475,13 @@ extern "C" int rans_encode_static_scratch(const uint8_t *d_symbols, uint64_t n_s
     ep.slot_bytes = sl.slot_bytes;
     ep.c_begin = 0;
     ep.c_end = ep.n_chunks;
-    ep.log2m = RANS_LOG2_M;
+    ep.log2m = lm;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
     if (g.n_chunks == 0)
         return encode_empty(d_out, d_out_size, d_status, n_symbols, params, uint32_t(g.data0),
-                            RANS_VERSION, RANS_LOG2_M, st);
-    return encode_placed(ep, sl, scr, d_out, d_out_size, uint32_t(g.data0), RANS_VERSION, kPlain,
-                         st);
+                            RANS_VERSION, lm, st);
+    return encode_placed(ep, sl, scr, d_out, d_out_size, uint32_t(g.data0), RANS_VERSION,
+                         lm != RANS_LOG2_M ? kWide : kPlain, st);
 }
 
 // ---------------------------------------------------------------------------

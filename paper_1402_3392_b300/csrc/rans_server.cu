@@ -16,7 +16,11 @@
 //     slots as memory frees up, so copies and kernels of different batches
 //     overlap on the device;
 //   - a request is done when its output is in host memory; its device memory
-//     is released then.
+//     is released then;
+//   - a request flagged RANS_REQ_DEVICE_MEMORY carries device input and output
+//     buffers: the coders read and write them in place, nothing is copied and
+//     only the batch's scratch and descriptors take arena memory; it is done
+//     when its kernels are.
 // All device work goes through the library's batched entry points; this file
 // is host code only.
 #include <algorithm>
@@ -112,8 +116,11 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+uint32_t request_kind(const rans_request &r) { return r.kind & ~RANS_REQ_DEVICE_MEMORY; }
+bool on_device(const rans_request &r) { return (r.kind & RANS_REQ_DEVICE_MEMORY) != 0; }
+
 uint64_t request_output_bytes(const rans_request &r) {
-    if (r.kind == RANS_REQ_ENCODE) {
+    if (request_kind(r) == RANS_REQ_ENCODE) {
         rans_params p{r.n_lanes, r.chunk_symbols};
         return rans_max_encoded_size(r.n_symbols, &p);
     }
@@ -177,11 +184,16 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
         const rans_request &r = reqs[i];
         rans_params p{r.n_lanes, r.chunk_symbols};
         std::memset(&results[i], 0, sizeof(rans_result));
-        if ((r.kind != RANS_REQ_ENCODE && r.kind != RANS_REQ_DECODE) || !params_ok(&p) ||
+        const uint32_t kind = request_kind(r);
+        if ((kind != RANS_REQ_ENCODE && kind != RANS_REQ_DECODE) || !params_ok(&p) ||
             r.table >= s->n_tables || (r.input_size && !r.input) || !r.output ||
             r.output_cap < request_output_bytes(r) ||
-            (r.kind == RANS_REQ_ENCODE && r.input_size != r.n_symbols) ||
-            (r.kind == RANS_REQ_DECODE && (r.input_size & 15u)) ||
+            (kind == RANS_REQ_ENCODE && r.input_size != r.n_symbols) ||
+            (kind == RANS_REQ_DECODE && (r.input_size & 15u)) ||
+            // device payloads are read and written in place: a message and an
+            // encode output must be 16-byte aligned, as for the coders
+            (on_device(r) && kind == RANS_REQ_DECODE && !aligned16(r.input)) ||
+            (on_device(r) && kind == RANS_REQ_ENCODE && !aligned16(r.output)) ||
             (i && r.arrival_s < reqs[i - 1].arrival_s))
             return RANS_ERR_INVALID_ARG;
     }
@@ -190,6 +202,29 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
     uint32_t next = 0, done = 0, batches = 0;
     int rc = RANS_OK;
 
+    // A request's input and output regions in the arena (none for device
+    // payloads, which the coders read and write in place).
+    auto release_payload = [&](const Req &q) {
+        if (on_device(reqs[q.id])) return;
+        s->arena.release(q.in_off, q.in_len);
+        s->arena.release(q.out_off, q.out_len);
+    };
+    auto place_payload = [&](Req &q) {
+        if (on_device(reqs[q.id])) return true;
+        if (!s->arena.alloc(q.in_len, &q.in_off)) return false;
+        if (!s->arena.alloc(q.out_len, &q.out_off)) {
+            s->arena.release(q.in_off, q.in_len);
+            return false;
+        }
+        return true;
+    };
+    auto input_of = [&](const Req &q) -> const uint8_t * {
+        return on_device(reqs[q.id]) ? reqs[q.id].input : s->d_arena + q.in_off;
+    };
+    auto output_of = [&](const Req &q) -> uint8_t * {
+        return on_device(reqs[q.id]) ? reqs[q.id].output : s->d_arena + q.out_off;
+    };
+
     auto finish = [&](Slot &sl) {
         const double t = seconds_since(t0);
         for (size_t k = 0; k < sl.enc.size(); ++k) {
@@ -197,8 +232,7 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
             results[q.id].status = sl.h_status[k];
             results[q.id].output_size = sl.h_status[k] == RANS_OK ? sl.h_sizes[k] : 0;
             results[q.id].done_s = t;
-            s->arena.release(q.in_off, q.in_len);
-            s->arena.release(q.out_off, q.out_len);
+            release_payload(q);
         }
         for (size_t k = 0; k < sl.dec.size(); ++k) {
             const Req &q = sl.dec[k];
@@ -206,8 +240,7 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
             results[q.id].status = st;
             results[q.id].output_size = st == RANS_OK ? reqs[q.id].n_symbols : 0;
             results[q.id].done_s = t;
-            s->arena.release(q.in_off, q.in_len);
-            s->arena.release(q.out_off, q.out_len);
+            release_payload(q);
         }
         for (auto &a : sl.batch_allocs) s->arena.release(a.first, a.second);
         done += uint32_t(sl.enc.size() + sl.dec.size());
@@ -232,11 +265,15 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 break;
             }
             progressed = true;
-            if (sl.phase == 1 && !sl.enc.empty()) {
+            const bool copy_out = std::any_of(sl.enc.begin(), sl.enc.end(), [&](const Req &q) {
+                return !on_device(reqs[q.id]);
+            });
+            if (sl.phase == 1 && copy_out) {
                 // encoded sizes are known now: copy the messages out
                 for (size_t k = 0; k < sl.enc.size(); ++k) {
                     if (sl.h_status[k] != RANS_OK) continue;
                     const Req &qq = sl.enc[k];
+                    if (on_device(reqs[qq.id])) continue;
                     if (cudaMemcpyAsync(reqs[qq.id].output, s->d_arena + qq.out_off, sl.h_sizes[k],
                                         cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
                         rc = RANS_ERR_CUDA;
@@ -257,7 +294,7 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 const uint32_t id = pending.front();
                 const rans_request &r = reqs[id];
                 Req q{id, 0, r.input_size, 0, request_output_bytes(r)};
-                if (up(q.in_len) + up(q.out_len) > s->arena.bytes()) {
+                if (!on_device(r) && up(q.in_len) + up(q.out_len) > s->arena.bytes()) {
                     results[id].status = RANS_ERR_OOM;  // can never fit
                     results[id].admit_s = results[id].done_s = seconds_since(t0);
                     pending.pop_front();
@@ -265,13 +302,9 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                     progressed = true;
                     continue;
                 }
-                if (!s->arena.alloc(q.in_len, &q.in_off)) break;
-                if (!s->arena.alloc(q.out_len, &q.out_off)) {
-                    s->arena.release(q.in_off, q.in_len);
-                    break;
-                }
+                if (!place_payload(q)) break;
                 pending.pop_front();
-                (r.kind == RANS_REQ_ENCODE ? enc : dec).push_back(q);
+                (request_kind(r) == RANS_REQ_ENCODE ? enc : dec).push_back(q);
             }
             if (enc.empty() && dec.empty()) break;
             // Batch-level regions: encode scratch, decode scratch, descriptors,
@@ -283,9 +316,9 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 for (size_t k = 0; k < enc.size(); ++k) {
                     const rans_request &r = reqs[enc[k].id];
                     rans_encode_stream &d = sl.h_enc[k];
-                    d.symbols = s->d_arena + enc[k].in_off;
+                    d.symbols = input_of(enc[k]);
                     d.n_symbols = r.n_symbols;
-                    d.out = s->d_arena + enc[k].out_off;
+                    d.out = output_of(enc[k]);
                     d.out_cap = enc[k].out_len;
                     d.scratch_offset = 0;
                     d.table = r.table;
@@ -311,8 +344,7 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 while (v.size() > keep) {
                     const Req q = v.back();
                     v.pop_back();
-                    s->arena.release(q.in_off, q.in_len);
-                    s->arena.release(q.out_off, q.out_len);
+                    release_payload(q);
                     pending.push_front(q.id);
                 }
             };
@@ -334,8 +366,7 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 std::vector<Req> &v = enc.empty() ? dec : enc;
                 if (!busy) {  // alone and nothing will free memory: it can never run
                     const Req q = v.front();
-                    s->arena.release(q.in_off, q.in_len);
-                    s->arena.release(q.out_off, q.out_len);
+                    release_payload(q);
                     results[q.id].status = RANS_ERR_OOM;
                     results[q.id].admit_s = results[q.id].done_s = seconds_since(t0);
                     ++done;
@@ -360,9 +391,9 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
             for (size_t k = 0; k < sl.dec.size(); ++k) {
                 const rans_request &r = reqs[sl.dec[k].id];
                 rans_stream &d = sl.h_dec[k];
-                d.msg = s->d_arena + sl.dec[k].in_off;
+                d.msg = input_of(sl.dec[k]);
                 d.msg_size = r.input_size;
-                d.symbols = s->d_arena + sl.dec[k].out_off;
+                d.symbols = output_of(sl.dec[k]);
                 d.n_symbols = r.n_symbols;
                 d.table = r.table;
                 d.n_lanes = r.n_lanes;
@@ -378,11 +409,13 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
             cudaStream_t st = sl.stream;
             bool cu = true;
             for (const Req &q : sl.enc)
-                cu = cu && cudaMemcpyAsync(s->d_arena + q.in_off, reqs[q.id].input, q.in_len,
-                                           cudaMemcpyHostToDevice, st) == cudaSuccess;
+                cu = cu && (on_device(reqs[q.id]) ||
+                            cudaMemcpyAsync(s->d_arena + q.in_off, reqs[q.id].input, q.in_len,
+                                            cudaMemcpyHostToDevice, st) == cudaSuccess);
             for (const Req &q : sl.dec)
-                cu = cu && cudaMemcpyAsync(s->d_arena + q.in_off, reqs[q.id].input, q.in_len,
-                                           cudaMemcpyHostToDevice, st) == cudaSuccess;
+                cu = cu && (on_device(reqs[q.id]) ||
+                            cudaMemcpyAsync(s->d_arena + q.in_off, reqs[q.id].input, q.in_len,
+                                            cudaMemcpyHostToDevice, st) == cudaSuccess);
             if (!sl.enc.empty()) {
                 cu = cu && cudaMemcpyAsync(desc_enc, sl.h_enc, sizeof(rans_encode_stream) * sl.enc.size(),
                                            cudaMemcpyHostToDevice, st) == cudaSuccess;
@@ -405,8 +438,10 @@ extern "C" int rans_server_run(rans_server *srv, const rans_request *reqs, uint3
                 cu = cu && cudaMemcpyAsync(sl.h_status + s->max_batch, d_st_dec, 4 * sl.dec.size(),
                                            cudaMemcpyDeviceToHost, st) == cudaSuccess;
                 for (const Req &q : sl.dec)
-                    cu = cu && cudaMemcpyAsync(reqs[q.id].output, s->d_arena + q.out_off, q.out_len,
-                                               cudaMemcpyDeviceToHost, st) == cudaSuccess;
+                    cu = cu && (on_device(reqs[q.id]) ||
+                                cudaMemcpyAsync(reqs[q.id].output, s->d_arena + q.out_off,
+                                                q.out_len, cudaMemcpyDeviceToHost,
+                                                st) == cudaSuccess);
             }
             cu = cu && cudaEventRecord(sl.ev, st) == cudaSuccess;
             if (!cu) rc = RANS_ERR_CUDA;

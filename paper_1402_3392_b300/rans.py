@@ -27,8 +27,8 @@ __all__ = [
     "rans_encode_scratch_size", "rans_encode", "rans_decode", "rans_encode_static_scratch",
     "RANS_STATIC_SCRATCH_BYTES", "encode", "decode", "STREAM_DTYPE", "ENCODE_STREAM_DTYPE",
     "rans_decode_batch_scratch_size", "rans_decode_batch", "rans_encode_batch_plan",
-    "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE",
-    "Server", "rans_check_bounded_wait", "rans_check_lookback_wait", "rans_decode_host",
+    "rans_encode_batch", "REQUEST_DTYPE", "RESULT_DTYPE", "RANS_REQ_ENCODE", "RANS_REQ_DECODE", "RANS_REQ_DEVICE_MEMORY",
+    "Server", "rans_check_bounded_wait", "rans_check_lookback_wait", "rans_check_division", "rans_decode_host",
     "rans_decode_host_work_size", "decode_host", "rans_max_encoded_size_bypass", "rans_encode_scratch_size_bypass",
     "rans_encode_bypass", "rans_decode_bypass", "encode_bypass", "decode_bypass",
     "rans_max_encoded_size_bytes", "rans_encode_bytes", "rans_decode_bytes", "encode_bytes",
@@ -66,6 +66,7 @@ RESULT_DTYPE = np.dtype([("output_size", "<u8"), ("status", "<u4"), ("batch", "<
                          ("admit_s", "<f8"), ("done_s", "<f8")])
 RANS_REQ_ENCODE = 0
 RANS_REQ_DECODE = 1
+RANS_REQ_DEVICE_MEMORY = 0x100
 assert STREAM_DTYPE.itemsize == 48 and ENCODE_STREAM_DTYPE.itemsize == 56
 assert REQUEST_DTYPE.itemsize == 64 and RESULT_DTYPE.itemsize == 32
 
@@ -102,6 +103,7 @@ def _load() -> C.CDLL:
         "rans_encode_static_scratch": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp]),
         "rans_check_bounded_wait": (i32, [vp, vp]),
         "rans_check_lookback_wait": (i32, [vp, vp]),
+        "rans_check_division": (i32, [u32, u32, vp, vp]),
         "rans_debug_checks": (i32, [vp]),
         "rans_debug_check_selftest": (i32, [vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
@@ -632,6 +634,15 @@ def rans_check_lookback_wait(d_status, stream=None, check=True) -> int:
     publishes gives up after about 200 ms and writes RANS_ERR_TIMEOUT."""
     rc = lib.rans_check_lookback_wait(_ptr(d_status), _stream(stream))
     return _check(rc, "rans_check_lookback_wait") if check else rc
+
+
+def rans_check_division(method: int, log2m: int, d_result, stream=None, check=True) -> int:
+    """Diagnostic: the encoders' division (method 0: reciprocal multiply-high,
+    method 1: the adaptive coder's float estimate) checked on the device for
+    every frequency below M = 2^log2m and every state it divides; d_result is
+    a device tensor of 4 u64 (checked, wrong, first wrong f << 32 | x, 0)."""
+    rc = lib.rans_check_division(int(method), int(log2m), _ptr(d_result), _stream(stream))
+    return _check(rc, "rans_check_division") if check else rc
 
 
 def rans_encode_static_scratch(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out,

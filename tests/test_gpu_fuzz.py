@@ -50,6 +50,13 @@ def message(rlib, orc, kind, rng):
         m = orc.encode_message_adaptive(bits, N=N, chunk_symbols=CS)
         ref = lambda b: orc.decode_message_adaptive(b, N_SYM, N=N, chunk_symbols=CS)  # noqa: E731
         gpu = lambda d: rlib.decode_adaptive(d, N_SYM, N, CS, sync=False)  # noqa: E731
+    elif kind == "binary":             # decoded without a slot table
+        pb = np.array([0.8, 0.2])
+        fb = rlib.rans_quantize_table(wl.weights_from_probs(pb))
+        bits = wl.iid_symbols(rng, pb, N_SYM)
+        m = orc.encode_message(bits, fb, N=N, chunk_symbols=CS)
+        ref = lambda b: orc.decode_message(b, N_SYM, fb, N=N, chunk_symbols=CS)  # noqa: E731
+        gpu = lambda d: rlib.decode(d, N_SYM, fb, N, CS, sync=False)  # noqa: E731
     elif kind == "wide14":
         f14 = rlib.rans_quantize_table(wl.weights_from_probs(p), 14)
         m = orc.encode_message(sym, f14, N=N, chunk_symbols=CS)
@@ -81,7 +88,8 @@ def damage(m, rng, how):
     return b
 
 
-@pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14"])
+@pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14",
+                                  "binary"])
 @pytest.mark.parametrize("how", ["bytes", "offset", "chunk"])
 def test_damaged_messages_agree_with_oracle(rlib, orc, cuda, kind, how):
     rng = np.random.default_rng(zlib.crc32(repr(("fuzz", kind, how)).encode()))
@@ -111,7 +119,8 @@ def _gpu_status(torch, gpu, bad, cuda):
     return out, int(st.item())
 
 
-@pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14"])
+@pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14",
+                                  "binary"])
 def test_truncated_messages_agree_with_oracle(rlib, orc, cuda, kind):
     """Messages cut short: by whole 16-byte blocks (the size no longer matches
     the offset table: both reject); cut with the offset table's last entry

@@ -97,3 +97,53 @@ def test_request_that_never_fits_fails_alone(rlib, orc, cuda):
     for i in range(reqs.size):
         assert np.array_equal(out_bytes(trace, res, i + 1), expect[i]), i
     srv.close()
+
+
+def test_device_resident_requests_equal_oracle(rlib, orc, cuda):
+    """Requests flagged RANS_REQ_DEVICE_MEMORY read their input from and write
+    their output to device buffers in place (no copies; the arena holds only
+    the batches' scratch).  In a trace that mixes them with host-payload
+    requests, every result equals the oracle's."""
+    import torch
+
+    rng = np.random.default_rng(149)
+    count = 60
+    sizes = wl.log_uniform_sizes(rng, count, 4 << 10, 4 << 20)
+    probs = wl.batched_models(rng, count, 64, 256, 0.5)
+    tables = [rlib.rans_quantize_table(wl.weights_from_probs(p)) for p in probs]
+    arrivals = wl.poisson_arrivals(rng, 5000.0, count)
+    kinds = rng.integers(0, 2, size=count)
+    on_dev = rng.integers(0, 2, size=count).astype(bool)
+    reqs = np.zeros(count, dtype=rlib.REQUEST_DTYPE)
+    keep, expect, outs = [], [], []
+    for i in range(count):
+        f = tables[i]
+        sym = rng.choice(len(f), size=int(sizes[i]), p=f / f.sum()).astype(np.uint8)
+        msg = orc.encode_message(sym, f, N=32, chunk_symbols=16384)
+        if kinds[i] == rlib.RANS_REQ_ENCODE:
+            inp, exp, cap = sym, msg, rlib.rans_max_encoded_size(sym.size, 32, 16384)
+        else:
+            inp, exp, cap = msg, sym, sym.size
+        if on_dev[i]:
+            b_in = torch.from_numpy(inp.copy()).to(cuda)
+            b_out = torch.zeros(max(cap, 16), dtype=torch.uint8, device=cuda)
+            kind = int(kinds[i]) | rlib.RANS_REQ_DEVICE_MEMORY
+        else:
+            b_in = torch.from_numpy(inp.copy()).pin_memory()
+            b_out = torch.zeros(max(cap, 1), dtype=torch.uint8).pin_memory()
+            kind = int(kinds[i])
+        keep += [b_in, b_out]
+        outs.append(b_out)
+        expect.append(exp)
+        reqs[i] = (kind, i, 32, 16384, b_in.data_ptr(), inp.size, sym.size, b_out.data_ptr(),
+                   cap, arrivals[i])
+    tdev = B.upload_tables(tables, cuda)
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device=cuda)
+    srv = rlib.Server(tdev, arena, max_batch=16, n_slots=3)
+    res = srv.run(reqs)
+    srv.close()
+    assert (res["status"] == 0).all(), res["status"]
+    for i in range(count):
+        n_out = int(res["output_size"][i])
+        got = outs[i][:n_out].cpu().numpy()
+        assert n_out == expect[i].size and np.array_equal(got, expect[i]), (i, bool(on_dev[i]))

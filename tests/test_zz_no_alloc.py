@@ -3,12 +3,13 @@ device memory (for example a host that reserved the device up front, or a
 real-time pipeline that forbids allocation while it runs).  Its scratch is a
 fixed array inside the library instead of a caller buffer.
 
-The test calls it through the C ABI twice in a row, with different inputs, and
-checks each message byte for byte (the coder's tolerance is zero) against the
-ordinary rans_encode on the same input.  It also checks that an input whose
-scratch need is above the fixed array's size is refused without launching.
-This file is collected last so that a run stopping at the first failure has
-already run every other test."""
+The test calls it through the C ABI several times in a row, with different
+inputs and models (12- and 14-bit), and checks each message byte for byte
+(the coder's tolerance is zero) against the CPU oracle's message and against
+the ordinary rans_encode on the same input.  It also checks that an input
+whose scratch need is above the fixed array's size is refused without
+launching.  This file is collected last so that a run stopping at the first
+failure has already run every other test."""
 import numpy as np
 import pytest
 
@@ -37,18 +38,22 @@ def _encode_both(rlib, torch, dev, sym, freq, N, CS):
     return out_a[:sa], out_b[:sb]
 
 
-def test_static_scratch_encode_matches_rans_encode(rlib, cuda):
+def test_static_scratch_encode_matches_oracle_and_rans_encode(rlib, orc, cuda):
     import torch
 
     rng = np.random.default_rng(71)
     cases = [
-        (wl.zipf_probs(256, 1.1), 3 * 65536 + 4321, 32, 65536),
-        (wl.dirichlet_probs(rng, 97, 0.3), 200_001, 7, 1000),
+        (wl.zipf_probs(256, 1.1), 3 * 65536 + 4321, 32, 65536, 12),
+        (wl.dirichlet_probs(rng, 97, 0.3), 200_001, 7, 1000, 12),
+        (wl.zipf_probs(256, 1.3), 150_003, 32, 4096, 14),
     ]
-    for p, n, N, CS in cases:              # two calls in a row on the shared array
-        freq = rlib.rans_quantize_table(wl.weights_from_probs(p))
-        sym = torch.from_numpy(wl.iid_symbols(rng, p, n)).to(cuda)
+    for p, n, N, CS, lm in cases:          # calls in a row on the shared array
+        freq = rlib.rans_quantize_table(wl.weights_from_probs(p), lm)
+        h_sym = wl.iid_symbols(rng, p, n)
+        sym = torch.from_numpy(h_sym).to(cuda)
         a, b = _encode_both(rlib, torch, cuda, sym, freq, N, CS)
+        ref = orc.encode_message(h_sym, freq, N=N, chunk_symbols=CS)
+        assert np.array_equal(b.cpu().numpy(), ref)
         assert torch.equal(a, b)
         out, _ = rlib.decode(b, n, freq, N, CS)
         assert torch.equal(out, sym)
