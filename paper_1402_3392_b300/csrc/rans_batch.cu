@@ -3,7 +3,7 @@
 //
 // The work list is built on the device: a setup kernel validates every
 // descriptor and writes the exclusive prefix of work items per stream (one
-// item = up to dec::kChunksPerCta chunks of one stream).  The persistent decode
+// item = the chunks one CTA decodes at once, of one stream).  The persistent decode
 // kernel's CTAs take items from an atomic counter; an item's stream is found
 // by binary search in the prefix; its model's slot table is rebuilt in shared
 // memory only when the model changes; each warp decodes one chunk with the
@@ -41,6 +41,7 @@ struct BatchDecodeParams {
     uint32_t *counter;  // next work item
     uint32_t n_streams;
     uint32_t n_tables;
+    uint32_t item_chunks;  // chunks in one work item: the CTA's warps x chunks per warp
 };
 
 struct StreamGeom {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kSetupThreads)
             const StreamGeom g = check_stream(p.streams[i], p.n_tables);
             p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
             if (g.ok) {
-                const uint64_t k = (g.n_chunks + dec::kChunksPerCta - 1) / dec::kChunksPerCta;
+                const uint64_t k = (g.n_chunks + p.item_chunks - 1) / p.item_chunks;
                 items = k > 0 ? uint32_t(k) : 1u;  // an empty stream still has its header checked
             }
         }
@@ -115,10 +116,16 @@ __global__ void __launch_bounds__(kSetupThreads)
     }
 }
 
-__global__ void __launch_bounds__(dec::kThreads)
+// W warps a CTA; PAIR: a warp decodes two chunks side by side (one item =
+// 2W chunks), else one (one item = W chunks).
+// Bounded for the shape's resident CTAs per SM (8 warps: 4, at most 64
+// registers; 12 warps: 3, at most 56).
+template <int W, bool PAIR>
+__global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasPerSm)
     batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
+    constexpr uint32_t kPer = PAIR ? dec::kChains : 1u;
     extern __shared__ __align__(128) uint8_t smem[];
-    const dec::Smem sm = dec::smem_layout(smem);
+    const dec::Smem sm = dec::smem_layout<W>(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t &item_s = sm.misc[0];
     uint32_t &stream_s = sm.misc[1];
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(dec::kThreads)
                 }
             } else {
                 if (threadIdx.x == 0) const_sym = dec::kNoConst;
-                const uint32_t sum = dec::build_slot_table(fr, sm.tab, sm.rings, &const_sym);
+                const uint32_t sum = dec::build_slot_table<W>(fr, sm.tab, sm.rings, &const_sym);
                 if (threadIdx.x == 0) {
                     loaded = d.table;
                     model_ok = sum == kM;
@@ -192,31 +199,31 @@ __global__ void __launch_bounds__(dec::kThreads)
             continue;
         }
         const StreamGeom g = check_stream(d, p.n_tables);
-        const uint32_t c = (it - p.prefix[s]) * dec::kChunksPerCta + dec::kChains * warp;
+        const uint32_t c = (it - p.prefix[s]) * (W * kPer) + kPer * warp;
         if (c < g.n_chunks && !wr.timeouts) {
             const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
-            const uint32_t count = uint32_t(umin64(dec::kChains, g.n_chunks - c));
+            const uint32_t count = uint32_t(umin64(kPer, g.n_chunks - c));
             const uint32_t bf = bin_f;
             uint32_t st;
             if (bf)  // binary model: f_0 and f_1 ride in the table and flag arguments
                 st = d.n_lanes == 32
-                         ? dec::decode_chunks<32, true, dec::kKindBinary>(
+                         ? dec::decode_chunks<32, PAIR, dec::kKindBinary>(
                                wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
                                d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane, lt, nullptr,
                                bf >> 16)
-                         : dec::decode_chunks<0, true, dec::kKindBinary>(
+                         : dec::decode_chunks<0, PAIR, dec::kKindBinary>(
                                wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
                                d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs, lane, lt,
                                nullptr, bf >> 16);
             else
                 st = d.n_lanes == 32
-                         ? dec::decode_chunks<32, true>(wr, sm.tab_s, d.msg, g.data0, offs,
+                         ? dec::decode_chunks<32, PAIR>(wr, sm.tab_s, d.msg, g.data0, offs,
                                                         data_end, c, count, d.n_symbols,
                                                         d.chunk_symbols, 32, d.symbols, cs, lane,
                                                         lt)
-                         : dec::decode_chunks<0, true>(wr, sm.tab_s, d.msg, g.data0, offs,
+                         : dec::decode_chunks<0, PAIR>(wr, sm.tab_s, d.msg, g.data0, offs,
                                                        data_end, c, count, d.n_symbols,
                                                        d.chunk_symbols, d.n_lanes, d.symbols, cs,
                                                        lane, lt);
@@ -525,6 +532,43 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
 
 using namespace rans;
 
+namespace rans {
+namespace {
+
+// The batched decoder's CTA shape: 8 warps, two chunks side by side in each
+// (items of 16 chunks).
+constexpr int kBatchWarps = 8;
+constexpr bool kBatchPair = true;
+
+template <int W, bool PAIR>
+int launch_batch_decode(BatchDecodeParams &p, cudaStream_t st) {
+    using S = dec::Shape<W>;
+    auto kern = batch_decode_kernel<W, PAIR>;
+    p.item_chunks = W * (PAIR ? dec::kChains : 1u);
+    // Set once per device; concurrent first calls may both set it (harmless).
+    static std::atomic<bool> configured[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(S::kSmemBytes)) != cudaSuccess)
+            return RANS_ERR_CUDA;
+        configured[dev].store(true);
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, S::kSmemBytes) !=
+            cudaSuccess ||
+        per_sm <= 0)
+        return RANS_ERR_CUDA;
+    batch_setup_kernel<<<1, kSetupThreads, 0, st>>>(p);
+    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
+    kern<<<unsigned(per_sm * sm_count()), S::kThreads, S::kSmemBytes, st>>>(p);
+    return check_launch();
+}
+
+}  // namespace
+}  // namespace rans
+
 extern "C" uint64_t rans_decode_batch_scratch_size(uint32_t n_streams) {
     return batch_layout(n_streams).total;
 }
@@ -547,27 +591,7 @@ extern "C" int rans_decode_batch(const rans_stream *d_streams, uint32_t n_stream
     p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
     p.n_streams = n_streams;
     p.n_tables = n_tables;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-
-    // Set once per device; concurrent first calls may both set it (harmless).
-    static std::atomic<bool> configured[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev].load()) {
-        if (cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(dec::kSmemBytes)) != cudaSuccess)
-            return RANS_ERR_CUDA;
-        configured[dev].store(true);
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_decode_kernel, dec::kThreads,
-                                                      dec::kSmemBytes) != cudaSuccess ||
-        per_sm <= 0)
-        return RANS_ERR_CUDA;
-    batch_setup_kernel<<<1, kSetupThreads, 0, st>>>(p);
-    if (check_launch() != RANS_OK) return RANS_ERR_CUDA;
-    batch_decode_kernel<<<unsigned(per_sm * sm_count()), dec::kThreads, dec::kSmemBytes, st>>>(p);
-    return check_launch();
+    return launch_batch_decode<kBatchWarps, kBatchPair>(p, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" uint64_t rans_encode_batch_plan(rans_encode_stream *h_streams, uint32_t n_streams) {
