@@ -161,6 +161,29 @@ def load(mutant: int = 0) -> C.CDLL:
         lib.orc_decode_message_adaptive.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
                                                     _u8p, C.c_uint64]
         lib.orc_decode_message_adaptive.restype = C.c_int
+        lib.orc_adaptive_n_trace.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _u32p,
+                                             C.c_uint64, _u64p]
+        lib.orc_adaptive_n_trace.restype = C.c_int
+        lib.orc_encode_adaptive_n.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
+                                              C.c_uint32, C.c_uint32, _u32p, C.c_uint64, _u64p,
+                                              C.c_uint64, _u64p, _u64p]
+        lib.orc_encode_adaptive_n.restype = C.c_int
+        lib.orc_decode_adaptive_n.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
+                                              C.c_uint32, C.c_uint32, _u64p, C.c_uint64, _u64p,
+                                              C.c_uint64, _u32p, _u64p, _u64p]
+        lib.orc_decode_adaptive_n.restype = C.c_int
+        lib.orc_encode_chunk_adaptive_n.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                    _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_chunk_adaptive_n.restype = C.c_int
+        lib.orc_decode_chunk_adaptive_n.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                    _u8p, C.c_uint64]
+        lib.orc_decode_chunk_adaptive_n.restype = C.c_int
+        lib.orc_encode_message_adaptive_n.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                      C.c_uint32, _u8p, C.c_uint64, _u64p]
+        lib.orc_encode_message_adaptive_n.restype = C.c_int
+        lib.orc_decode_message_adaptive_n.argtypes = [_u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                                      C.c_uint32, _u8p, C.c_uint64]
+        lib.orc_decode_message_adaptive_n.restype = C.c_int
         # Section 4: instrumented-decoder mux (mux_oracle.c)
         lib.orc_mux_rans.argtypes = [_u32p, C.c_uint64, C.c_uint32, _u64p, C.c_uint32,
                                      C.c_uint64, C.c_uint64, _u64p, C.c_uint64, _u64p]
@@ -613,6 +636,81 @@ class Oracle:
         rc = self.lib.orc_decode_chunk_adaptive(_p(c, _u8p), c.size, N, _p(out, _u8p), n_sym)
         if rc != OK:
             raise OracleError(rc, "decode_chunk_adaptive")
+        return out[:n_sym].copy()
+
+    # -- adaptive models over n <= 16 symbols, one per coder (Section 5) -------
+    def adaptive_n_trace(self, symbols, n, M=1 << 12, R=5):
+        """The cumulative frequencies of one context: row k = the model symbol
+        k is coded with, row len(symbols) = the model after the last."""
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        out = np.zeros((s.size + 1) * (n + 1), dtype=np.uint64)
+        rc = self.lib.orc_adaptive_n_trace(M, R, n, _p(s, _u32p), s.size, _p(out, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "adaptive_n_trace")
+        return out.reshape(s.size + 1, n + 1).astype(np.int64)
+
+    def encode_adaptive_n(self, symbols, n, N=1, M=1 << 12, L=L_PROD, b=B_PROD, R=5):
+        s = np.ascontiguousarray(symbols, dtype=np.uint32)
+        cap = max(1, 64 * s.size + 64)
+        words = np.zeros(cap, dtype=np.uint64)
+        states = np.zeros(N, dtype=np.uint64)
+        nw = C.c_uint64(0)
+        rc = self.lib.orc_encode_adaptive_n(M, L, b, N, R, n, _p(s, _u32p), s.size,
+                                            _p(words, _u64p), cap, C.byref(nw), _p(states, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "encode_adaptive_n")
+        return dict(words=words[: nw.value].copy(), states=states)
+
+    def decode_adaptive_n(self, words, states, n_sym, n, N=1, M=1 << 12, L=L_PROD, b=B_PROD, R=5):
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        st = np.ascontiguousarray(states, dtype=np.uint64)
+        sym = np.zeros(max(1, n_sym), dtype=np.uint32)
+        st_end = np.zeros(N, dtype=np.uint64)
+        used = C.c_uint64(0)
+        rc = self.lib.orc_decode_adaptive_n(M, L, b, N, R, n, _p(w, _u64p), w.size,
+                                            _p(st, _u64p), n_sym, _p(sym, _u32p), C.byref(used),
+                                            _p(st_end, _u64p))
+        if rc != OK:
+            raise OracleError(rc, "decode_adaptive_n")
+        return dict(symbols=sym[:n_sym].copy(), consumed=used.value, states_end=st_end)
+
+    def encode_message_adaptive_n(self, symbols, n, N=32, chunk_symbols=65536):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        cap = self.max_message_size(s.size, N, chunk_symbols)
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_message_adaptive_n(_p(s, _u8p), s.size, n, N, chunk_symbols,
+                                                    _p(out, _u8p), cap, C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_message_adaptive_n")
+        return out[: size.value].copy()
+
+    def decode_message_adaptive_n(self, msg, n_sym, n, N=32, chunk_symbols=65536):
+        m = np.ascontiguousarray(msg, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_message_adaptive_n(_p(m, _u8p), m.size, n, N, chunk_symbols,
+                                                    _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_message_adaptive_n")
+        return out[:n_sym].copy()
+
+    def encode_chunk_adaptive_n(self, symbols, n, N=32):
+        s = np.ascontiguousarray(symbols, dtype=np.uint8)
+        cap = 4 * N + 2 * s.size
+        out = np.zeros(max(cap, 1), dtype=np.uint8)
+        size = C.c_uint64(0)
+        rc = self.lib.orc_encode_chunk_adaptive_n(_p(s, _u8p), s.size, n, N, _p(out, _u8p), cap,
+                                                  C.byref(size))
+        if rc != OK:
+            raise OracleError(rc, "encode_chunk_adaptive_n")
+        return out[: size.value].copy()
+
+    def decode_chunk_adaptive_n(self, chunk, n_sym, n, N=32):
+        c = np.ascontiguousarray(chunk, dtype=np.uint8)
+        out = np.zeros(max(1, n_sym), dtype=np.uint8)
+        rc = self.lib.orc_decode_chunk_adaptive_n(_p(c, _u8p), c.size, n, N, _p(out, _u8p), n_sym)
+        if rc != OK:
+            raise OracleError(rc, "decode_chunk_adaptive_n")
         return out[:n_sym].copy()
 
     # -- Section 4: interleaving arbitrary coders by an instrumented decoder --

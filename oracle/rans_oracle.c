@@ -631,6 +631,179 @@ done:
     return rc;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Adaptive models over n symbols, one per coder (Section 5: the lanes'    */
+/* models must evolve independently for the coders to vectorize).         */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Alphabet {0..n-1}, 2 <= n <= ORC_ADAPT_NMAX.  Coder j keeps its own
+ * cumulative frequencies C_0 = 0 < C_1 < ... < C_n = M, so f_s = C_{s+1} - C_s
+ * and B_s = C_s (the range form of Section 2), starting from
+ * C_i = floor(i * M / n).  After coding symbol s every interior boundary
+ * 1 <= i <= n-1 moves a 2^-R part of the way to its target, rounded down:
+ *     i <= s:  C_i -= (C_i - i) >> R            (target i)
+ *     i >  s:  C_i += (M - n + i - C_i) >> R    (target M - n + i)
+ * so symbol s's interval [C_s, C_{s+1}) widens and the others narrow.
+ * Every f stays >= 1 and every boundary within [i, M - n + i]:
+ *   - two boundaries below s: with a_i = C_i - i, a_{i+1} >= a_i (since
+ *     f_i >= 1), and a -> a - (a >> R) is non-decreasing, so the new
+ *     a_{i+1} >= a_i again, i.e. the new f_i >= 1;
+ *   - two above s: the same with u_i = M - n + i - C_i (u_{i+1} <= u_i);
+ *   - across s: C_s moves down and C_{s+1} up.
+ * The decoder updates after decoding; the encoder, which runs backwards,
+ * first runs every coder's model forwards to know each symbol's (B_s, f_s).
+ * (The binary contexts above use a different rounding; n = 2 here is its
+ * own model, not the same as them.)
+ */
+#define ORC_ADAPT_NMAX 16u
+
+static void cdf_init(u128 *c, uint32_t n, u128 M)
+{
+    for (uint32_t i = 0; i <= n; ++i) c[i] = (u128)i * M / n;
+}
+
+static void cdf_adapt(u128 *c, uint32_t n, u128 M, uint32_t R, uint32_t s)
+{
+    for (uint32_t i = 1; i < n; ++i) {
+#if ORACLE_MUTANT == 15
+        if (i < s)                                  /* planted mistake: C_s moves up */
+#else
+        if (i <= s)
+#endif
+            c[i] -= (c[i] - i) >> R;
+        else
+            c[i] += (M - n + i - c[i]) >> R;
+    }
+}
+
+/* The model a coder's cumulative frequencies give (model_init's form). */
+static int cdf_model(orc_model *m, const u128 *c, uint32_t n, uint64_t L, uint64_t b)
+{
+    uint64_t f[ORC_ADAPT_NMAX];
+    for (uint32_t s = 0; s < n; ++s) f[s] = (uint64_t)(c[s + 1] - c[s]);
+    return model_init(m, f, n, L, b);
+}
+
+static int adapt_n_args(uint64_t M, uint32_t N, uint32_t R, uint32_t n)
+{
+    return N == 0 || n < 2 || n > ORC_ADAPT_NMAX || M < n || R == 0 || R > 30;
+}
+
+/* The cumulative frequencies of one context over sym[0..n_sym): row k of
+ * cdf_out ((n_sym + 1) x (n + 1) values) is the model symbol k is coded
+ * with; row n_sym the model after the last symbol. */
+int orc_adaptive_n_trace(uint64_t M, uint32_t R, uint32_t n, const uint32_t *sym, uint64_t n_sym,
+                         uint64_t *cdf_out)
+{
+    if (adapt_n_args(M, 1, R, n)) return ORC_ERR_ARG;
+    u128 c[ORC_ADAPT_NMAX + 1];
+    cdf_init(c, n, M);
+    for (uint64_t k = 0; k <= n_sym; ++k) {
+        for (uint32_t i = 0; i <= n; ++i) cdf_out[k * (n + 1) + i] = (uint64_t)c[i];
+        if (k == n_sym) break;
+        if (sym[k] >= n) return ORC_ERR_SYMBOL;
+        cdf_adapt(c, n, M, R, sym[k]);
+    }
+    return ORC_OK;
+}
+
+int orc_encode_adaptive_n(uint64_t M, uint64_t L, uint64_t b, uint32_t N, uint32_t R, uint32_t n,
+                          const uint32_t *sym, uint64_t n_sym, uint64_t *words, uint64_t word_cap,
+                          uint64_t *n_words, uint64_t *states)
+{
+    if (adapt_n_args(M, N, R, n)) return ORC_ERR_ARG;
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    u128 *cdf = (u128 *)malloc(sizeof(u128) * N * (ORC_ADAPT_NMAX + 1));
+    u128 *Bi = (u128 *)malloc(sizeof(u128) * (n_sym ? n_sym : 1));
+    u128 *fi = (u128 *)malloc(sizeof(u128) * (n_sym ? n_sym : 1));
+    int rc = ORC_OK;
+    uint64_t W = 0;
+    if (!mp || !x || !cdf || !Bi || !fi) { rc = ORC_ERR_ARG; goto done; }
+    /* forward: the (B_s, f_s) every symbol is coded with */
+    for (uint32_t j = 0; j < N; ++j) cdf_init(cdf + j * (ORC_ADAPT_NMAX + 1), n, M);
+    for (uint64_t i = 0; i < n_sym; ++i) {
+        uint32_t j = coder_of(i, N), s = sym[i];
+        u128 *c = cdf + j * (ORC_ADAPT_NMAX + 1);
+        if (s >= n) { rc = ORC_ERR_SYMBOL; goto done; }
+#if ORACLE_MUTANT == 14
+        cdf_adapt(c, n, M, R, s);                   /* planted mistake: update before coding */
+        Bi[i] = c[s];
+        fi[i] = c[s + 1] - c[s];
+#else
+        Bi[i] = c[s];
+        fi[i] = c[s + 1] - c[s];
+        cdf_adapt(c, n, M, R, s);
+#endif
+    }
+    /* backwards: Algorithm 1 with symbol i's model.  C(s, x) needs only M,
+     * B_s and f_s, so the three-part model [B_s, f_s, M - B_s - f_s] with the
+     * symbol in the middle gives the same C as the coder's full model. */
+    if ((rc = cdf_model(mp, cdf, n, L, b)) != ORC_OK) goto done;
+    for (uint32_t j = 0; j < N; ++j) x[j] = initial_state(mp);
+    for (uint64_t i = n_sym; i-- > 0;) {
+        uint32_t j = coder_of(i, N);
+        uint64_t part[3] = {(uint64_t)Bi[i], (uint64_t)fi[i], (uint64_t)(M - Bi[i] - fi[i])};
+        if ((rc = model_init(mp, part, 3, L, b)) != ORC_OK) goto done;
+        while (!in_I(mp, C(mp, 1, x[j]))) {
+            if (W >= word_cap) { rc = ORC_ERR_SPACE; goto done; }
+            words[W++] = (uint64_t)(x[j] % mp->b);
+            x[j] = x[j] / mp->b;
+        }
+        x[j] = C(mp, 1, x[j]);
+        if (!in_I(mp, x[j])) { rc = ORC_ERR_INVARIANT; goto done; }
+    }
+    for (uint64_t a = 0, z = W; a + 1 < z; ++a, --z) {
+        uint64_t t = words[a];
+        words[a] = words[z - 1];
+        words[z - 1] = t;
+    }
+    for (uint32_t j = 0; j < N; ++j) states[j] = (uint64_t)x[j];
+    *n_words = W;
+done:
+    free(mp); free(x); free(cdf); free(Bi); free(fi);
+    return rc;
+}
+
+int orc_decode_adaptive_n(uint64_t M, uint64_t L, uint64_t b, uint32_t N, uint32_t R, uint32_t n,
+                          const uint64_t *words, uint64_t n_words, const uint64_t *states_in,
+                          uint64_t n_sym, uint32_t *sym_out, uint64_t *consumed,
+                          uint64_t *states_out)
+{
+    if (adapt_n_args(M, N, R, n)) return ORC_ERR_ARG;
+    orc_model *mp = (orc_model *)malloc(sizeof(orc_model));
+    u128 *x = (u128 *)malloc(sizeof(u128) * N);
+    u128 *cdf = (u128 *)malloc(sizeof(u128) * N * (ORC_ADAPT_NMAX + 1));
+    int rc = ORC_OK;
+    uint64_t rp = 0;
+    if (!mp || !x || !cdf) { rc = ORC_ERR_ARG; goto done; }
+    for (uint32_t j = 0; j < N; ++j) {
+        cdf_init(cdf + j * (ORC_ADAPT_NMAX + 1), n, M);
+        x[j] = states_in[j];
+        if (x[j] < L || x[j] >= (u128)L * b) rc = ORC_ERR_CORRUPT;   /* x must be in I */
+    }
+    for (uint64_t i = 0; !rc && i < n_sym; ++i) {
+        uint32_t j = coder_of(i, N), s;
+        u128 *c = cdf + j * (ORC_ADAPT_NMAX + 1);
+        if ((rc = cdf_model(mp, c, n, L, b)) != ORC_OK) break;
+        x[j] = D(mp, x[j], &s);
+        sym_out[i] = s;
+        while (!in_I(mp, x[j])) {
+            if (rp >= n_words || x[j] >= mp->L * mp->b) { rc = ORC_ERR_CORRUPT; break; }
+            x[j] = mp->b * x[j] + words[rp++];
+        }
+        cdf_adapt(c, n, M, R, s);
+    }
+    if (!rc) {
+        for (uint32_t j = 0; j < N; ++j) states_out[j] = (uint64_t)x[j];
+        *consumed = rp;
+    }
+done:
+    free(mp); free(x); free(cdf);
+    return rc;
+}
+
 /* Single coding-function evaluations, for checking the oracle against the
  * paper's printed example (Section 2.1).  *ok = 0 on bad input. */
 uint64_t orc_C(const uint64_t *f, uint32_t n_alpha, uint32_t s, uint64_t x, int *ok)
@@ -679,6 +852,8 @@ uint64_t orc_D(const uint64_t *f, uint32_t n_alpha, uint64_t x, uint32_t *s_out,
 #define ORC_VERSION_ADAPTIVE 4u /* adaptive binary contexts, one per coder */
 #define ORC_ADAPT_RATE 5u      /* adaptive messages: p moves by (target - p) >> 5 */
 #define ORC_ADAPT_P0 2048u     /* ... from p = M/2 at the start of every chunk */
+#define ORC_VERSION_ADAPTIVE_N 6u /* adaptive models over n <= 16 symbols, one per coder;
+                                     the header's log2_M word holds 12 | n << 16 */
 #define ORC_L8 (1ull << 23)    /* byte-wise: L = 2^23, b = 2^8, I = [2^23, 2^31) */
 #define ORC_B8 (1ull << 8)
 #define ORC_L (1ull << 16)
@@ -1000,8 +1175,72 @@ int orc_decode_chunk_adaptive(const uint8_t *chunk, uint64_t size, uint32_t N, u
     return chunk_decode_adaptive(chunk, size, N, sym_out, n_c);
 }
 
+/* Adaptive n-symbol chunk (version 6): [u32 state[N]][u16 words], M = 2^12,
+ * L = b = 2^16, per-coder models from the uniform start, rate 5. */
+static int chunk_encode_adaptive_n(const uint8_t *sym, uint64_t n_c, uint32_t n, uint32_t N,
+                                   uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (n_c ? n_c : 1) * 2);
+    if (!s32 || !w) { free(s32); free(w); return ORC_ERR_ARG; }
+    for (uint64_t i = 0; i < n_c; ++i) s32[i] = sym[i];
+    uint64_t st[32], W = 0;
+    int rc = orc_encode_adaptive_n(1ull << ORC_LOG2_M, ORC_L, ORC_B, N, ORC_ADAPT_RATE, n, s32,
+                                   n_c, w, 2 * (n_c ? n_c : 1), &W, st);
+    if (rc == ORC_OK) {
+        uint64_t need = 4ull * N + 2ull * W;
+        if (need > cap) rc = ORC_ERR_SPACE;
+        else {
+            for (uint32_t j = 0; j < N; ++j) put_u32(out + 4 * j, (uint32_t)st[j]);
+            for (uint64_t k = 0; k < W; ++k) put_u16(out + 4ull * N + 2 * k, (uint32_t)w[k]);
+            *size = need;
+        }
+    }
+    free(s32);
+    free(w);
+    return rc;
+}
+
+static int chunk_decode_adaptive_n(const uint8_t *chunk, uint64_t size, uint32_t n, uint32_t N,
+                                   uint8_t *sym_out, uint64_t n_c)
+{
+    if (N == 0 || N > 32) return ORC_ERR_ARG;
+    if (size < 4ull * N || ((size - 4ull * N) & 1)) return ORC_ERR_CORRUPT;
+    uint64_t W = (size - 4ull * N) / 2;
+    uint64_t st[32], st_end[32], used = 0;
+    for (uint32_t j = 0; j < N; ++j) st[j] = get_u32(chunk + 4 * j);
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (W ? W : 1));
+    uint32_t *s32 = (uint32_t *)malloc(sizeof(uint32_t) * (n_c ? n_c : 1));
+    if (!w || !s32) { free(w); free(s32); return ORC_ERR_ARG; }
+    for (uint64_t k = 0; k < W; ++k) w[k] = get_u16(chunk + 4ull * N + 2 * k);
+    int rc = orc_decode_adaptive_n(1ull << ORC_LOG2_M, ORC_L, ORC_B, N, ORC_ADAPT_RATE, n, w, W,
+                                   st, n_c, s32, &used, st_end);
+    if (rc == ORC_OK) {
+        for (uint32_t j = 0; j < N; ++j)
+            if (st_end[j] != ORC_L) rc = ORC_ERR_CORRUPT;
+        if (used != W) rc = ORC_ERR_CORRUPT;
+        for (uint64_t i = 0; i < n_c; ++i) sym_out[i] = (uint8_t)s32[i];
+    }
+    free(w);
+    free(s32);
+    return rc;
+}
+
+int orc_encode_chunk_adaptive_n(const uint8_t *sym, uint64_t n_c, uint32_t n, uint32_t N,
+                                uint8_t *out, uint64_t cap, uint64_t *size)
+{
+    return chunk_encode_adaptive_n(sym, n_c, n, N, out, cap, size);
+}
+int orc_decode_chunk_adaptive_n(const uint8_t *chunk, uint64_t size, uint32_t n, uint32_t N,
+                                uint8_t *sym_out, uint64_t n_c)
+{
+    return chunk_decode_adaptive_n(chunk, size, n, N, sym_out, n_c);
+}
+
 /* Message = header + offsets + chunks; version 2 marks a bypass message,
- * version 3 a byte-wise one (bytes != 0). */
+ * version 3 a byte-wise one (bytes == 1), 4 adaptive binary contexts
+ * (bytes == 2), 6 adaptive n-symbol models (bytes == 3, n = n_alpha). */
 static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_sym,
                           const uint16_t *freq, const uint8_t *rawf, uint32_t n_alpha, uint32_t N,
                           uint32_t chunk_symbols, uint8_t *out, uint64_t cap, uint64_t *size,
@@ -1014,14 +1253,18 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
     if (cap < data0) return ORC_ERR_SPACE;
     memset(out, 0, data0);
     put_u32(out + 0, ORC_MAGIC);
-    put_u32(out + 4, bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
-                     : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
+    put_u32(out + 4, bytes == 3 ? ORC_VERSION_ADAPTIVE_N : bytes == 2 ? ORC_VERSION_ADAPTIVE
+                     : bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION);
     put_u32(out + 8, N);
     uint32_t lm = ORC_LOG2_M;
     if (bytes == 0 && !rawf) {
         uint64_t f64[256];
         int rc0 = plain_table(freq, n_alpha, f64, 1, &lm);
         if (rc0) return rc0;
+    }
+    if (bytes == 3) {
+        if (n_alpha < 2 || n_alpha > ORC_ADAPT_NMAX) return ORC_ERR_ARG;
+        lm |= n_alpha << 16;
     }
     put_u32(out + 12, lm);
     put_u32(out + 16, (uint32_t)n_sym);
@@ -1036,8 +1279,10 @@ static int message_encode(const uint8_t *sym, const uint16_t *raw16, uint64_t n_
         put_u32(out + 32 + 4 * c, (uint32_t)pos);
         uint64_t sz = 0;
         if (data0 + pos > cap) return ORC_ERR_SPACE;
-        int rc = bytes == 2 ? chunk_encode_adaptive(sym + first, n_c, N, out + data0 + pos,
-                                                    cap - data0 - pos, &sz)
+        int rc = bytes == 3 ? chunk_encode_adaptive_n(sym + first, n_c, n_alpha, N,
+                                                      out + data0 + pos, cap - data0 - pos, &sz)
+                 : bytes == 2 ? chunk_encode_adaptive(sym + first, n_c, N, out + data0 + pos,
+                                                      cap - data0 - pos, &sz)
                  : bytes ? chunk_encode_bytes(sym + first, n_c, freq, n_alpha, N,
                                               out + data0 + pos, cap - data0 - pos, &sz)
                          : chunk_encode(sym + first, raw16 ? raw16 + first : NULL, n_c, freq,
@@ -1064,13 +1309,17 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
     if (size < 48 || (size & 15)) return ORC_ERR_CORRUPT;
     uint64_t n_chunks = (n_sym + chunk_symbols - 1) / chunk_symbols;
     uint64_t hdr_n = (uint64_t)get_u32(msg + 16) | ((uint64_t)get_u32(msg + 20) << 32);
-    uint32_t version = bytes == 2 ? ORC_VERSION_ADAPTIVE : bytes ? ORC_VERSION_BYTES
-                       : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
+    uint32_t version = bytes == 3 ? ORC_VERSION_ADAPTIVE_N : bytes == 2 ? ORC_VERSION_ADAPTIVE
+                       : bytes ? ORC_VERSION_BYTES : rawf ? ORC_VERSION_BYPASS : ORC_VERSION;
     uint32_t lm = ORC_LOG2_M;
     if (bytes == 0 && !rawf) {
         uint64_t f64[256];
         int rc0 = plain_table(freq, n_alpha, f64, 1, &lm);
         if (rc0) return rc0;
+    }
+    if (bytes == 3) {
+        if (n_alpha < 2 || n_alpha > ORC_ADAPT_NMAX) return ORC_ERR_ARG;
+        lm |= n_alpha << 16;
     }
     if (get_u32(msg) != ORC_MAGIC || get_u32(msg + 4) != version ||
         get_u32(msg + 8) != N || get_u32(msg + 12) != lm || hdr_n != n_sym ||
@@ -1088,8 +1337,10 @@ static int message_decode(const uint8_t *msg, uint64_t size, const uint16_t *fre
         uint64_t first = c * chunk_symbols;
         uint64_t n_c = n_sym - first < chunk_symbols ? n_sym - first : chunk_symbols;
         if (z < a || z > end_all) return ORC_ERR_CORRUPT;
-        int rc = bytes == 2 ? chunk_decode_adaptive(msg + data0 + a, z - a, N, sym_out + first,
-                                                    n_c)
+        int rc = bytes == 3 ? chunk_decode_adaptive_n(msg + data0 + a, z - a, n_alpha, N,
+                                                      sym_out + first, n_c)
+                 : bytes == 2 ? chunk_decode_adaptive(msg + data0 + a, z - a, N, sym_out + first,
+                                                      n_c)
                  : bytes ? chunk_decode_bytes(msg + data0 + a, z - a, freq, n_alpha, N,
                                               sym_out + first, n_c)
                          : chunk_decode(msg + data0 + a, z - a, freq, rawf, n_alpha, N,
@@ -1139,6 +1390,17 @@ int orc_decode_message_adaptive(const uint8_t *msg, uint64_t size, uint32_t N,
                                 uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
 {
     return message_decode(msg, size, NULL, NULL, 0, N, chunk_symbols, sym_out, NULL, n_sym, 2);
+}
+int orc_encode_message_adaptive_n(const uint8_t *sym, uint64_t n_sym, uint32_t n, uint32_t N,
+                                  uint32_t chunk_symbols, uint8_t *out, uint64_t cap,
+                                  uint64_t *size)
+{
+    return message_encode(sym, NULL, n_sym, NULL, NULL, n, N, chunk_symbols, out, cap, size, 3);
+}
+int orc_decode_message_adaptive_n(const uint8_t *msg, uint64_t size, uint32_t n, uint32_t N,
+                                  uint32_t chunk_symbols, uint8_t *sym_out, uint64_t n_sym)
+{
+    return message_decode(msg, size, NULL, NULL, n, N, chunk_symbols, sym_out, NULL, n_sym, 3);
 }
 int orc_encode_message_bytes(const uint8_t *sym, uint64_t n_sym, const uint16_t *freq,
                              uint32_t n_alpha, uint32_t N, uint32_t chunk_symbols, uint8_t *out,

@@ -767,6 +767,150 @@ def pin_adaptive_container(o):
 
 
 # ----------------------------------------------------------------------------
+# Adaptive models over n symbols, one per coder (Section 5)
+# ----------------------------------------------------------------------------
+
+def pin_adaptive_n_worked_example(o):
+    """The model update worked out by hand for two small cases.
+
+    (a) M = 16, n = 3, R = 1, start floor(i*16/3) = [0, 5, 10, 16]; targets
+        i below and at the coded symbol, 13 + i above it:
+        s=2: C1 = 5-((5-1)>>1) = 3, C2 = 10-((10-2)>>1) = 6
+        s=0: C1 = 3+((14-3)>>1) = 8, C2 = 6+((15-6)>>1) = 10
+        s=1: C1 = 8-((8-1)>>1) = 5, C2 = 10+((15-10)>>1) = 12
+        s=1: C1 = 5-2 = 3, C2 = 12+1 = 13
+        s=2: C1 = 3-1 = 2, C2 = 13-5 = 8
+        s=2: C1 = 2-0 = 2, C2 = 8-3 = 5
+        s=0: C1 = 2+6 = 8, C2 = 5+5 = 10
+    (b) M = 4096, n = 4, R = 5, start [0, 1024, 2048, 3072, 4096]:
+        s=0: +(3069>>5)=95, +(2046>>5)=63, +(1023>>5)=31 -> 1119 2111 3103
+        s=3: -(1118>>5)=34, -(2109>>5)=65, -(3100>>5)=96 -> 1085 2046 3007"""
+    rows = [[0, 5, 10, 16], [0, 3, 6, 16], [0, 8, 10, 16], [0, 5, 12, 16], [0, 3, 13, 16],
+            [0, 2, 8, 16], [0, 2, 5, 16], [0, 8, 10, 16]]
+    tr = o.adaptive_n_trace([2, 0, 1, 1, 2, 2, 0], 3, M=16, R=1)
+    assert tr.tolist() == rows
+    tr = o.adaptive_n_trace([0, 3], 4, M=4096, R=5)
+    assert tr.tolist() == [[0, 1024, 2048, 3072, 4096], [0, 1119, 2111, 3103, 4096],
+                           [0, 1085, 2046, 3007, 4096]]
+
+
+def pin_adaptive_n_invariants(o):
+    """Along long random sequences every model is a valid one (C_0 = 0,
+    C_n = M, every f >= 1, boundary i within [i, M - n + i]); coding a
+    symbol never narrows its own interval nor widens another's; and a
+    symbol coded over and over settles: each boundary below it within
+    2^R - 1 of its target, where the update stops moving it."""
+    rng = np.random.default_rng(41)
+    M = 1 << 12
+    for n in (2, 5, 16):
+        seq = rng.integers(0, n, size=3000).astype(np.uint32)
+        seq[1000:1600] = 1
+        tr = o.adaptive_n_trace(seq, n)
+        i = np.arange(n + 1)
+        assert (tr[:, 0] == 0).all() and (tr[:, n] == M).all()
+        f = np.diff(tr, axis=1)
+        assert (f >= 1).all()
+        assert (tr >= i).all() and (tr <= M - n + i).all()
+        for k, s in enumerate(seq):
+            grow = f[k + 1] - f[k]
+            assert grow[s] >= 0 and (np.delete(grow, s) <= 0).all(), (n, k)
+        # a long run of the last symbol: every boundary settles within 2^R - 1
+        # of its lower target i (the shift no longer moves it), after which
+        # the model is fixed
+        run = o.adaptive_n_trace(np.full(5000, n - 1, np.uint32), n)
+        a = run[-1][1:n] - np.arange(1, n)
+        assert (a >= 0).all() and (a >> 5 == 0).all()
+        assert np.array_equal(run[-1], run[-2])
+        assert M - run[-1][n - 1] >= M - (n - 1) - 31
+
+
+def pin_adaptive_n_static_limit(o):
+    """With R = 30 no boundary ever moves (every distance is below 2^30), so
+    each coder keeps the uniform start model and the stream is the static
+    Algorithm-1 coder's with f = diff(floor(i*M/n))."""
+    rng = np.random.default_rng(43)
+    for n, N in ((3, 1), (7, 4), (16, 5)):
+        msg = rng.integers(0, n, size=2000).astype(np.uint32)
+        freq = np.diff([(i * M12) // n for i in range(n + 1)])
+        a = o.encode_adaptive_n(msg, n, N=N, R=30)
+        s = o.encode(freq, msg, N=N)
+        assert np.array_equal(a["words"], s["words"])
+        assert np.array_equal(a["states"], s["states"])
+
+
+def pin_adaptive_n_lanes_independent(o):
+    """Separate models per lane: coder j's final state equals that of one
+    coder run on symbols j, j+N, ... alone, and the stream decodes back."""
+    rng = np.random.default_rng(47)
+    for n, N in ((4, 2), (9, 3), (16, 8)):
+        p = rng.dirichlet(np.full(n, 0.4))
+        msg = rng.choice(n, size=60 * N + 7, p=p).astype(np.uint32)
+        enc = o.encode_adaptive_n(msg, n, N=N)
+        for j in range(N):
+            solo = o.encode_adaptive_n(msg[j::N], n, N=1)
+            assert int(enc["states"][j]) == int(solo["states"][0]), (n, N, j)
+        dec = o.decode_adaptive_n(enc["words"], enc["states"], msg.size, n, N=N)
+        assert np.array_equal(dec["symbols"], msg) and dec["consumed"] == enc["words"].size
+        assert all(int(v) == L16 for v in dec["states_end"])
+
+
+def pin_adaptive_n_brute_force(o):
+    """All messages over 3 symbols up to length 6, N = 1 and 2: distinct
+    messages get distinct encodings, and every one decodes back."""
+    for N in (1, 2):
+        seen = set()
+        for k in range(0, 7):
+            for msg in itertools.product(range(3), repeat=k):
+                enc = o.encode_adaptive_n(list(msg), 3, N=N)
+                key = (k, tuple(enc["words"]), tuple(int(v) for v in enc["states"]))
+                assert key not in seen
+                seen.add(key)
+                dec = o.decode_adaptive_n(enc["words"], enc["states"], k, 3, N=N)
+                assert tuple(dec["symbols"]) == msg
+
+
+def pin_adaptive_n_size(o):
+    """The coded size stays within the derived per-symbol bound (reading 13)
+    around the information content of the models the contexts give; on data
+    the models can learn (a skewed source with a burst of one symbol) it is
+    well below log2 n bits per symbol."""
+    rng = np.random.default_rng(53)
+    n, N = 8, 4
+    p = np.array([0.6, 0.2, 0.1, 0.05, 0.02, 0.01, 0.01, 0.01])
+    msg = rng.choice(n, size=8000, p=p).astype(np.uint32)
+    msg[3000:5000] = 2
+    info = 0.0
+    for j in range(N):
+        sub = msg[j::N]
+        tr = o.adaptive_n_trace(sub, n)
+        f = tr[np.arange(sub.size), sub + 1] - tr[np.arange(sub.size), sub]
+        info += float(np.sum(np.log2(M12 / f)))
+    enc = o.encode_adaptive_n(msg, n, N=N)
+    W = enc["words"].size
+    bits = 16 * W + sum(math.log2(int(x) / L16) for x in enc["states"])
+    lo = info + msg.size * math.log2(15 / 16) - W * math.log2(17 / 16) - 1e-6
+    hi = info + msg.size * math.log2(17 / 16) + 1e-6
+    assert lo <= bits <= hi, (lo, bits, hi)
+    assert bits / msg.size < 0.75 * math.log2(n)
+
+
+def pin_adaptive_n_container(o):
+    rng = np.random.default_rng(59)
+    msg = rng.integers(0, 11, size=5000).astype(np.uint8)
+    m = o.encode_message_adaptive_n(msg, 11, N=7, chunk_symbols=999)
+    h = m[:32].view(np.uint32)
+    assert int(h[1]) == 6 and int(h[3]) == 12 | (11 << 16)
+    assert np.array_equal(o.decode_message_adaptive_n(m, msg.size, 11, N=7, chunk_symbols=999),
+                          msg)
+    data0 = (32 + 4 * 7 + 15) // 16 * 16
+    offs = m[32:32 + 4 * 7].view(np.uint32)
+    enc = o.encode_adaptive_n(msg[:999].astype(np.uint32), 11, N=7)
+    ch = m[data0 + offs[0]:data0 + offs[1]]
+    assert list(ch[:28].view(np.uint32)) == list(enc["states"])
+    assert list(ch[28:].view(np.uint16)) == list(enc["words"])
+
+
+# ----------------------------------------------------------------------------
 # Section 4: interleaving arbitrary coders by running an instrumented decoder
 # ----------------------------------------------------------------------------
 
@@ -1015,5 +1159,7 @@ ALL_PINS = [
     pin_adaptive_brute_force, pin_adaptive_size_and_learning, pin_adaptive_container,
     pin_mux_rans_is_section3_interleaving, pin_prefix_codes_rfc1951, pin_prefix_lengths_optimal,
     pin_prefix_mux_lane_streams, pin_prefix_mux_brute_force, pin_mux_coroutine_and_flush,
-    pin_prefix_container, pin_wide_resolution,
+    pin_prefix_container, pin_wide_resolution, pin_adaptive_n_worked_example,
+    pin_adaptive_n_invariants, pin_adaptive_n_static_limit, pin_adaptive_n_lanes_independent,
+    pin_adaptive_n_brute_force, pin_adaptive_n_size, pin_adaptive_n_container,
 ]

@@ -10,13 +10,15 @@ The mutants are compiled from the same source with -DORACLE_MUTANT=k:
  11 updates an adaptive context before coding the symbol, not after
  12 muxes the coders' buffers by concatenation, not in the decoders' read order
  13 hands out canonical codes of one length in decreasing symbol order
+ 14 updates an adaptive n-symbol model before coding the symbol, not after
+ 15 moves the coded symbol's lower boundary up with the ones above it
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTANTS = range(1, 14)
+MUTANTS = range(1, 16)
 
 
 @pytest.mark.parametrize("k", MUTANTS)
