@@ -53,12 +53,16 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="run the timed region without the clock sampler")
     ap.add_argument("--symbols", type=int, default=0,
                     help="override the workload's symbol count (small profiling cases)")
     ap.add_argument("--legs",
-                    default="batched,binary,single,serving,bypass,bytes,adaptive,prefix,wide",
+                    default="batched,binary,single,serving,bypass,bytes,adaptive,adaptive_n,"
+                            "prefix,wide",
                     help="extra legs after the headline one: comma list of batched, binary, "
-                         "single, serving, bypass, bytes, adaptive, prefix, wide, none")
+                         "single, serving, bypass, bytes, adaptive, adaptive_n, prefix, wide, "
+                         "none")
     ap.add_argument("--serving-requests", type=int, default=5000)
     ap.add_argument("--batched-streams", type=int, default=0,
                     help="override the batched workload's stream count")
@@ -109,10 +113,47 @@ def profiled_traffic():
     return float(m.group(1))
 
 
+class _Nvml:
+    """The few NVML queries the clock sampler needs, called through ctypes on
+    the driver's libnvidia-ml (read only: clocks and clock-event reasons)."""
+
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, uuid: str):
+        import ctypes
+
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+        self.h = ctypes.c_void_p()
+        rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetHandleByUUID({uuid}) returned {rc}")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def max_sm_mhz(self):
+        v = self.C.c_uint()
+        rc = self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.NVML_CLOCK_SM, self.C.byref(v))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetMaxClockInfo returned {rc}")
+        return int(v.value)
+
+    def sample(self):
+        mhz, bits = self.C.c_uint(), self.C.c_ulonglong()
+        rc = self.lib.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, self.C.byref(mhz))
+        rc2 = self.reasons_fn(self.h, self.C.byref(bits))
+        if rc or rc2:
+            raise RuntimeError(f"nvml sample returned {rc}/{rc2}")
+        return int(mhz.value), int(bits.value)
+
+
 class ClockSampler:
     """Samples the SM clock and the clock-event reasons (read only) while the
-    timed region runs: NVML in this process when the Python module can reach
-    the device, else an `nvidia-smi -lms` child.  Either is started and has
+    timed region runs: NVML in this process (the driver's libnvidia-ml through
+    ctypes), else an `nvidia-smi -lms` child.  Either is started and has
     delivered its first sample before the timed region begins (an
     nvidia-smi started inside it was seen to hold up the region's CUDA calls
     for seconds), and only samples taken between mark_start() and
@@ -145,33 +186,12 @@ class ClockSampler:
         self._stop = threading.Event()
         self._first = threading.Event()
         try:
-            import pynvml
-
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = self._nvml_handle(pynvml)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.nv = _Nvml(self.uuid)
+            self.max_mhz = self.nv.max_sm_mhz()
             self.mode = "nvml"
         except Exception as e:  # noqa: BLE001
             self.errors.append(f"nvml: {e!r}"[:160])
             self.mode = "nvidia-smi"
-
-    def _nvml_handle(self, nv):
-        try:
-            return nv.nvmlDeviceGetHandleByUUID(self.uuid)
-        except Exception as e:  # noqa: BLE001
-            self.errors.append(f"nvml uuid {self.uuid}: {e!r}"[:160])
-        for i in range(nv.nvmlDeviceGetCount()):
-            h = nv.nvmlDeviceGetHandleByIndex(i)
-            u = nv.nvmlDeviceGetUUID(h)
-            u = u.decode() if isinstance(u, bytes) else u
-            if u == self.uuid:
-                return h
-            if self.pci is not None:
-                pi = nv.nvmlDeviceGetPciInfo(h)
-                if (pi.domain, pi.bus, pi.device) == self.pci:
-                    return h
-        raise RuntimeError("no NVML device matches the CUDA device")
 
     def _record(self, mhz, reasons):
         self.samples.append((time.perf_counter(), float(mhz), frozenset(reasons)))
@@ -181,13 +201,12 @@ class ClockSampler:
         nv = self.nv
         while not self._stop.is_set():
             try:
-                mhz = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
-                bits = int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+                mhz, bits = nv.sample()
                 self._record(mhz, {n for b, n in self.REASONS.items() if bits & b})
             except Exception as e:  # noqa: BLE001
                 if len(self.errors) < 4:
                     self.errors.append(f"nvml sample: {e!r}"[:160])
-            time.sleep(0.002)
+            time.sleep(0.005)
 
     def _run_smi(self):
         for line in self.proc.stdout:
@@ -700,6 +719,60 @@ def adaptive_leg(rans, dev, args, hbm):
                          "algorithmic_bytes_per_launch": alg}}
 
 
+def adaptive_n_leg(rans, dev, args, hbm):
+    """256 Mi symbols over 16 whose distribution drifts (Dirichlet(0.5) per
+    run of 4096 symbols), coded with one adaptive 16-symbol model per coder
+    (Section 5): encode and decode timed, the round trip checked, the size set
+    beside one static model for the whole message."""
+    import torch
+
+    cfg = wl.WORKLOADS["adaptive_n"]
+    n, k, N, CS = (args.symbols or cfg["n_symbols"]), cfg["n_alpha"], cfg["n_lanes"], \
+        cfg["chunk_symbols"]
+    sym = wl.drifting_symbols_device(n, k, cfg["segment"], wl.seed_for("adaptive_n"), dev,
+                                     cfg["dirichlet"])
+    cap = rans.rans_max_encoded_size(n, N, CS)
+    scap = rans.rans_encode_scratch_size_adaptive_n(n, N, CS)
+    msg = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(scap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    est = torch.zeros(1, dtype=torch.int32, device=dev)
+    enc = lambda: rans.rans_encode_adaptive_n(sym, n, k, N, CS, msg, cap, size, est,  # noqa: E731
+                                              scratch, scap)
+    enc()
+    torch.cuda.synchronize()
+    assert int(est.item()) == 0
+    msg_size = int(size.item())
+    enc_ms = statistics.median(_events(torch, enc, 5))
+    counts = torch.bincount(sym.long(), minlength=k).cpu().numpy().astype(np.float64)
+    freq = rans.rans_quantize_table(wl.weights_from_probs(np.maximum(counts, 1) / counts.sum()))
+    del scratch
+    static_size = int(rans.encode(sym, freq, N, CS)[1].item())   # not timed
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    dst = torch.zeros(1, dtype=torch.int32, device=dev)
+    dec = lambda: rans.rans_decode_adaptive_n(msg, msg_size, k, N, CS, out, n, dst)  # noqa: E731
+    dec()
+    torch.cuda.synchronize()
+    ok = int(dst.item()) == 0 and torch.equal(out, sym)
+    dec_ms = statistics.median(_events(torch, dec, 10))
+    alg = msg_size + n
+    orc = _oracle()
+    cpu = oracle_leg_baseline(lambda ch: orc.decode_chunk_adaptive_n(ch, CS, k, N=N),
+                              host_chunks(msg, n // CS, 4 * host_cores()), CS, unit_bytes=False)
+    return {"cpu_baseline": cpu,
+            "workload": f"{n} symbols over {k}, Dirichlet({cfg['dirichlet']}) per run of "
+                        f"{cfg['segment']}, {n // CS} chunks x {CS}, N = {N}, one adaptive "
+                        f"{k}-symbol model per coder (rate 1/32)",
+            "decode_gsym_s": n / (dec_ms * 1e-3) / 1e9, "decode_ms": dec_ms,
+            "encode_gsym_s": n / (enc_ms * 1e-3) / 1e9, "encode_ms": enc_ms,
+            "bits_per_symbol": 8 * msg_size / n, "static_bits_per_symbol": 8 * static_size / n,
+            "bit_exact_roundtrip": bool(ok),
+            "roofline": {"kernel": "decode_kernel (adaptive-n)", "bound": "hbm",
+                         "achieved": alg / (dec_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (dec_ms * 1e-3) / 1e9 / hbm,
+                         "algorithmic_bytes_per_launch": alg}}
+
+
 def prefix_leg(rans, dev, args, hbm):
     """Section 4: the 1 GiB chunked workload coded by 32 prefix coders per
     chunk (package-merge lengths <= 12 from the Zipf(1.1) weights), their
@@ -1031,7 +1104,9 @@ def main(argv=None):
         raise SystemExit("round trip failed in warm-up")
 
     evs = [mk() for _ in range(args.steps)]
-    sampler = ClockSampler(local).start()
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -1089,6 +1164,9 @@ def main(argv=None):
     if "adaptive" in legs:
         extra["adaptive"] = adaptive_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
+    if "adaptive_n" in legs:
+        extra["adaptive_n"] = adaptive_n_leg(rans, dev, args, peaks()[0])
+        torch.cuda.empty_cache()
     if "prefix" in legs:
         extra["prefix"] = prefix_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
@@ -1125,8 +1203,8 @@ def main(argv=None):
         # the legs of the scope table's next rows first, the headline's
         # companions (batched, binary, serving) last: a reader that keeps only
         # the end of the line still sees them
-        for k in ("bypass", "bytes", "adaptive", "prefix", "wide", "single", "serving", "binary",
-                  "batched"):
+        for k in ("bypass", "bytes", "adaptive", "adaptive_n", "prefix", "wide", "single",
+                  "serving", "binary", "batched"):
             if k in extra:
                 line[k] = extra[k]
         print(json.dumps(line), flush=True)

@@ -86,6 +86,7 @@ typedef struct CUstream_st *rans_stream_t; /* same type as cudaStream_t */
 #define RANS_VERSION_BYTES 3u          /* byte-wise messages (rans_encode_bytes) */
 #define RANS_VERSION_ADAPTIVE 4u       /* adaptive binary messages (rans_encode_adaptive) */
 #define RANS_VERSION_PREFIX 5u         /* prefix-code messages (rans_encode_prefix) */
+#define RANS_VERSION_ADAPTIVE_N 6u     /* adaptive n-symbol messages (rans_encode_adaptive_n) */
 #define RANS_PREFIX_MAX_LEN 12         /* longest prefix code */
 
 typedef struct {
@@ -321,6 +322,39 @@ int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols, const ran
 int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size, const rans_params *params,
                          uint8_t *d_symbols, uint64_t n_symbols, uint32_t *d_status,
                          rans_stream_t stream);
+
+/*
+ * Adaptive messages over n symbols (2 <= n <= RANS_ADAPTIVE_N_MAX) -- Section 5
+ * of the paper: adaptive models vectorize as long as every lane updates only
+ * its own model.  Symbols are bytes 0..n-1.  Coder j keeps its own cumulative
+ * frequencies C_0 = 0 < C_1 < ... < C_n = M (M = 2^12; f_s = C_{s+1} - C_s,
+ * B_s = C_s), starting at C_i = floor(i M / n) in every chunk.  After coding
+ * symbol s it moves every interior boundary a 1/32 part of the way (rounded
+ * down) towards i when i <= s and towards M - n + i when i > s:
+ *     i <= s:  C_i -= (C_i - i) >> 5      i > s:  C_i += (M - n + i - C_i) >> 5
+ * so s's interval widens and every f stays >= 1.  Coder j sees only its own
+ * symbols, so the stream depends on N like the rest of the container.
+ * L = b = 2^16, 16-bit words, version 6 (RANS_VERSION_ADAPTIVE_N); the
+ * header's log2_M field holds 12 | n << 16.  No model table is passed.
+ *
+ * rans_encode_adaptive_n: as rans_encode with the alphabet size n_alpha in
+ *   place of the model; out_cap >= rans_max_encoded_size(...), scratch_cap >=
+ *   rans_encode_scratch_size_adaptive_n(...) (the plain scratch plus 4 bytes
+ *   per symbol: the encoder runs every coder's model forwards and stores each
+ *   symbol's (B_s, f_s), then codes backwards from those).  A symbol >= n
+ *   gives RANS_ERR_ZERO_FREQ; n_alpha outside [2, 16] RANS_ERR_INVALID_ARG.
+ * rans_decode_adaptive_n: as rans_decode with n_alpha in place of the model;
+ *   a header whose n differs from n_alpha is corrupt.
+ */
+#define RANS_ADAPTIVE_N_MAX 16u
+uint64_t rans_encode_scratch_size_adaptive_n(uint64_t n_symbols, const rans_params *params);
+int rans_encode_adaptive_n(const uint8_t *d_symbols, uint64_t n_symbols, uint32_t n_alpha,
+                           const rans_params *params, uint8_t *d_out, uint64_t out_cap,
+                           uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
+                           uint64_t scratch_cap, rans_stream_t stream);
+int rans_decode_adaptive_n(const uint8_t *d_msg, uint64_t msg_size, uint32_t n_alpha,
+                           const rans_params *params, uint8_t *d_symbols, uint64_t n_symbols,
+                           uint32_t *d_status, rans_stream_t stream);
 
 /*
  * Interleaving arbitrary coders -- Section 4 of the paper: any entropy

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "adapt_model.cuh"
 #include "device_util.cuh"
 #include "host_util.h"
 
@@ -121,6 +122,14 @@ constexpr int kKindWide13 = 5, kKindWide14 = 6;
 // binary model, rABS in the paper's terms, Section 2): D needs no table.
 // The same bitstream as kKindPlain; only the decoder's step differs.
 constexpr int kKindBinary = 7;
+// Adaptive models over n symbols, one per coder (version 6, adapt_model.cuh),
+// with register room for 3, 7 or 15 boundaries (n <= 4, 8, 16).
+constexpr int kKindAdaptN4 = 8, kKindAdaptN8 = 9, kKindAdaptN16 = 10;
+template <int KIND>
+struct AdaptN {
+    static constexpr bool kOn = KIND == kKindAdaptN4 || KIND == kKindAdaptN8 || KIND == kKindAdaptN16;
+    static constexpr int kNB = KIND == kKindAdaptN4 ? 3 : KIND == kKindAdaptN8 ? 7 : 15;
+};
 template <int KIND>
 struct WideBits {
     static constexpr uint32_t kLog2 = KIND == kKindWide13 ? 13u : 14u;
@@ -469,6 +478,8 @@ struct Chain {
     uint32_t len;        // byte-wise messages: chunk bytes (states, digits, padding)
     uint32_t bhi, blo;   // prefix messages: this lane's bits, right-aligned in bhi:blo
     uint32_t nb;         // prefix messages: bits held (at most 43 unless a code was missing)
+    uint32_t cm[15];     // adaptive-n messages: this lane's model (adapt_model.cuh)
+    uint32_t nm;         // adaptive-n messages: M - n
 };
 
 __device__ __forceinline__ void chain_empty(Chain &c) {
@@ -805,6 +816,38 @@ __device__ __forceinline__ void decode_step_adaptive(uint32_t &x, uint32_t &p, u
     rp = imad(__popc(m), 2u, rp);
 }
 
+// One step of an adaptive-n chunk: the lane's own model gives s (the
+// boundaries at or below the slot, counted), B_s and f_s by selects; D, then
+// the model update, then the usual renormalization.  A boundary is at or
+// below the slot exactly when it is at or below s, so the same predicates
+// drive the update.
+template <bool FULL, uint32_t RING, int NB>
+__device__ __forceinline__ void decode_step_adaptive_n(Chain &c, bool active, uint32_t ring_s,
+                                                       uint8_t *outp, uint32_t lt) {
+    const bool on = FULL || active;
+    if (on) {
+        const uint32_t slot = c.x & (kM - 1);
+        uint32_t s = 0, B = 0, F = kM;
+        bool le[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            le[i] = c.cm[i] <= slot;
+            s += le[i];
+            B = le[i] ? c.cm[i] : B;
+        }
+#pragma unroll
+        for (int i = NB - 1; i >= 0; --i) F = le[i] ? F : c.cm[i];
+        c.x = imad(F - B, c.x >> kLog2M, slot - B);
+        *outp = uint8_t(s);
+        adapt::update<NB>(c.cm, le, c.nm);
+    }
+    const bool need = on && c.x < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = ld_ring_u16(word_at<RING>(c.rp, __popc(m & lt), ring_s));
+    if (need) c.x = __byte_perm(c.x, w, 0x1054u);  // (x << 16) | w
+    c.rp = imad(__popc(m), 2u, c.rp);
+}
+
 // One step of a prefix-message chunk (Section 4): a lane holding fewer than
 // 12 bits reads its next 32-bit word first (lanes in order, ballot + popc,
 // as for rANS words), then the top 12 of its bits index the code table;
@@ -850,6 +893,8 @@ __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s,
                                                            ring_s, outp, lt);
     else if (KIND == kKindBinary)  // tab_s, flags_s: f_0, f_1
         decode_step_binary<FULL, RING>(c.x, c.rp, active, tab_s, flags_s, ring_s, outp, lt);
+    else if (AdaptN<KIND>::kOn)
+        decode_step_adaptive_n<FULL, RING, AdaptN<KIND>::kNB>(c, active, ring_s, outp, lt);
     else
         decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
 }
@@ -1013,7 +1058,8 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     const uint32_t n_b = two ? uint32_t(umin64(CS, n_sym - first - CS)) : 0u;
     const uint32_t o0 = offs[c], o1 = offs[c + 1], o2 = two ? offs[c + 2] : 0u;
 
-    if (KIND != kKindAdaptive && !PREFIX && const_sym != kNoConst) {
+    constexpr bool ADAPTN = AdaptN<KIND>::kOn;
+    if (KIND != kKindAdaptive && !ADAPTN && !PREFIX && const_sym != kNoConst) {
         if (RAW)
             return const_chunk_raw(msg, data0, o0, o1, data_end, n_a, N, out + first,
                                    raw_out + first, const_sym, const_raw, lane);
@@ -1037,6 +1083,10 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
                              RAW ? raw_out + first : nullptr, lane);
     if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, nullptr, lane);
     else chain_empty(b);
+    if (ADAPTN) {  // flags_s: the alphabet size n
+        adapt::init<AdaptN<KIND>::kNB>(a.cm, flags_s);
+        a.nm = kM - flags_s;
+    }
 
     if (PAIR) {
         // Both chunks step together while each has a full group left.

@@ -27,6 +27,7 @@
 
 #include <cstdint>
 
+#include "adapt_model.cuh"
 #include "device_util.cuh"
 #include "host_util.h"
 
@@ -413,6 +414,60 @@ __device__ __forceinline__ void adaptive_forward(const uint8_t *sym, uint32_t n_
     if (bad > 1u) acc |= kZeroFlag;
 }
 
+// Pass 1 of an adaptive-n chunk (adapt_model.cuh): run every coder's model
+// forwards over its own symbols and store, for each symbol, the word
+// B_s | f_s << 16 it is coded with at words[t * N + lane] (step t).  A symbol
+// >= n sets kZeroFlag.
+template <int NT, int NB>
+__device__ __forceinline__ void adaptive_n_forward(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
+                                                   uint32_t n, uint32_t *words, uint32_t lane,
+                                                   uint32_t &acc) {
+    const uint32_t N = NT ? NT : N_rt;
+    if (lane >= N) return;
+    const uint32_t T_end = n_c / N + (lane < n_c % N ? 1u : 0u), nm = kM - n;
+    uint32_t cm[NB];
+    adapt::init<NB>(cm, n);
+    bool bad = false;
+    for (uint32_t t = 0; t < T_end; ++t) {
+        const uint32_t s = sym[uint64_t(t) * N + lane];
+        bad |= s >= n;
+        uint32_t B = 0, F = kM;
+        bool le[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const uint32_t b = uint32_t(i + 1);
+            B = b == s ? cm[i] : B;
+            F = b == s + 1 ? cm[i] : F;
+            le[i] = b <= s;
+        }
+        words[uint64_t(t) * N + lane] = B | ((F - B) << 16);
+        adapt::update<NB>(cm, le, nm);
+    }
+    if (bad) acc |= kZeroFlag;
+}
+
+// Pass 2 of an adaptive-n chunk, one step: the symbol's stored word gives
+// B = w & 0xFFFF and f = w >> 16; renormalize (emit if x >= f * 2^20), then
+// C with the exact float-estimate division.
+template <bool FULL>
+__device__ __forceinline__ void encode_step_bf(uint32_t &x, uint32_t &wp, bool active, uint32_t w,
+                                               uint32_t ring_s, uint32_t ge) {
+    const bool on = FULL || active;
+    const uint32_t f = w >> 16;
+    const bool emit = on && x >= (f << 20);
+    const uint32_t m = __ballot_sync(kFull, emit);
+    if (emit) {
+        st_ring_u16(((wp - 2u * __popc(m & ge)) & (kRing - 1)) | ring_s, x);
+        x >>= 16;
+    }
+    wp -= 2u * __popc(m);
+    if (on) {
+        uint32_t r;
+        const uint32_t q = div_float(x, f, r);
+        x = (q << kLog2M) + (w & 0xFFFFu) + r;
+    }
+}
+
 // Adaptive chunks, pass 2, one step: symbol s (0 or 1) coded with the stored
 // context p: f = p or M - p, B = 0 or p.  floor(x/f) comes from a float
 // estimate rounded towards zero throughout -- never above x/f, and below it
@@ -504,7 +559,7 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // ADAPT: an adaptive chunk; ctx holds the chunk's words from adaptive_forward.
 // WIDE: a wide model's 16-byte table entries (encode_step_wide).
 template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false,
-          bool WIDE = false>
+          bool WIDE = false, bool ADAPTN = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
@@ -512,12 +567,12 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                                              uint32_t lane, uint32_t &acc,
                                              const uint16_t *raw = nullptr,
                                              const uint32_t *ctx = nullptr) {
-    static_assert(!((RAW || ADAPT) && PREFETCH), "these chunks load each group up front");
+    static_assert(!((RAW || ADAPT || ADAPTN) && PREFETCH), "these chunks load each group up front");
     constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
     const uint16_t *rawp = RAW ? raw + lane : nullptr;
-    const uint32_t *ctxp = ADAPT ? ctx + lane : nullptr;
+    const uint32_t *ctxp = (ADAPT || ADAPTN) ? ctx + lane : nullptr;
     uint32_t x = BYTES ? kL8 : kL;
     uint32_t wp = slot_bytes;               // words occupy [wp, slot_bytes)
     uint32_t flushed = slot_bytes / kSeg;   // segments >= flushed are stored
@@ -553,8 +608,11 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     const bool lane_on = lane < N;
     if (rem) {
         const bool act = lane < rem;
-        const uint32_t s = act ? symp[uint64_t(T_full) * N] : 0u;
-        if (ADAPT) {
+        const uint32_t s = act && !ADAPTN ? symp[uint64_t(T_full) * N] : 0u;
+        if (ADAPTN) {
+            const uint32_t w = act ? ctxp[uint64_t(T_full) * N] : 0u;
+            encode_step_bf<false>(x, wp, act, w, ring_s, ge);
+        } else if (ADAPT) {
             const uint32_t pw = act ? ctxp[uint64_t(T_full - top0) * N] : kAdaptP0;
             encode_step_adaptive<false>(x, wp, act, s, pw, ring_s, ge);
         } else if (RAW) {
@@ -567,8 +625,11 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     int64_t t = int64_t(T_full) - 1;
     for (uint32_t r = T_full % kG; r > 0; --r, --t) {
         service();
-        const uint32_t s = lane_on ? symp[uint64_t(t) * N] : 0u;
-        if (ADAPT) {
+        const uint32_t s = lane_on && !ADAPTN ? symp[uint64_t(t) * N] : 0u;
+        if (ADAPTN) {
+            const uint32_t w = lane_on ? ctxp[uint64_t(t) * N] : 0u;
+            encode_step_bf<NT == 32>(x, wp, lane_on, w, ring_s, ge);
+        } else if (ADAPT) {
             const uint32_t pw = lane_on ? ctxp[uint64_t(t - top0) * N] : kAdaptP0;
             encode_step_adaptive<NT == 32>(x, wp, lane_on, s, pw, ring_s, ge);
         } else if (RAW) {
@@ -578,7 +639,18 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
         }
     }
-    if (ADAPT) {
+    if (ADAPTN) {
+        // Groups of kGroup steps, each step's stored (B, f) word loaded up front.
+        for (; t >= 0; t -= kGroup) {
+            uint32_t cw[kGroup];
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) cw[u] = lane_on ? ctxp[uint64_t(t - u) * N] : 0u;
+            service();
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u)
+                encode_step_bf<NT == 32>(x, wp, lane_on, cw[u], ring_s, ge);
+        }
+    } else if (ADAPT) {
         // Groups of kGroup steps coded from pass 1's words alone (the next
         // group's word loaded ahead): the contexts are re-run forwards from
         // the group's first step into registers, two per word, then the group

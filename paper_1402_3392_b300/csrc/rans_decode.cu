@@ -32,6 +32,7 @@ struct DecodeParams {
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
     uint32_t log2m;                        // plain messages: log2 M (12, 13 or 14)
+    uint32_t n_alpha;                      // adaptive-n messages: the alphabet size n
     uint8_t plen[RANS_MAX_ALPHABET];       // prefix messages: code lengths (0: no code)
     uint16_t pcode[RANS_MAX_ALPHABET];     // prefix messages: canonical codes
 };
@@ -43,7 +44,8 @@ struct DecodeParams {
 constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::kKindBytes,
               kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix,
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14,
-              kBinary = dec::kKindBinary;
+              kBinary = dec::kKindBinary, kAdaptN4 = dec::kKindAdaptN4,
+              kAdaptN8 = dec::kKindAdaptN8, kAdaptN16 = dec::kKindAdaptN16;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
 // CTA (dec::Shape).  A warp decodes one chunk at a time.
@@ -55,6 +57,7 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     constexpr bool PREFIX = KIND == kPrefix;
     constexpr bool WIDE = KIND == kWide13 || KIND == kWide14;
     constexpr bool BINARY = KIND == kBinary;  // a plain message with a binary model
+    constexpr bool ADAPTN = dec::AdaptN<KIND>::kOn;
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout<W>(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -66,12 +69,15 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
                                 RAW ? RANS_VERSION_BYPASS : BYTES ? RANS_VERSION_BYTES
                                 : ADAPTIVE                        ? RANS_VERSION_ADAPTIVE
                                 : PREFIX                          ? RANS_VERSION_PREFIX
+                                : ADAPTN                          ? RANS_VERSION_ADAPTIVE_N
                                                                   : RANS_VERSION,
-                                WIDE ? dec::WideBits<KIND>::kLog2 : uint32_t(kLog2M));
+                                WIDE     ? dec::WideBits<KIND>::kLog2
+                                : ADAPTN ? uint32_t(kLog2M) | (p.n_alpha << 16)
+                                         : uint32_t(kLog2M));
         const_sym = dec::kNoConst;
     }
     if (RAW && threadIdx.x < RANS_MAX_ALPHABET) sm.flags[threadIdx.x] = p.raw_words[threadIdx.x];
-    if (ADAPTIVE || BINARY) __syncthreads();  // no table: contexts, or f_0 and f_1
+    if (ADAPTIVE || BINARY || ADAPTN) __syncthreads();  // no table: contexts, or f_0 and f_1
     else if (PREFIX) dec::build_prefix_table<W>(p.plen, p.pcode, sm.tab);
     else if (WIDE)
         dec::build_wide_table<W>(p.freq, dec::WideBits<KIND>::kLog2, reinterpret_cast<uint8_t *>(sm.tab),
@@ -105,6 +111,10 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt, nullptr, sm.fb_s);
+        else if (ADAPTN)  // n rides in the flag argument
+            st = dec::decode_chunks<NT, false, KIND>(wr, 0, p.msg, p.data0, offs, data_end, c, 1,
+                                                     p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
+                                                     nullptr, p.n_alpha);
         else if (BINARY)  // f_0 and f_1 ride in the table and flag arguments
             st = dec::decode_chunks<NT, false, KIND>(wr, p.freq[0], p.msg, p.data0, offs,
                                                      data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
@@ -258,6 +268,12 @@ static int launch_range(DecodeParams p, uint32_t c_begin, uint32_t c_end, cudaSt
         return p.N == 32 ? launch_decode<32, kWide14>(p, st) : launch_decode<0, kWide14>(p, st);
     if (p.kind == kBinary)
         return p.N == 32 ? launch_decode<32, kBinary>(p, st) : launch_decode<0, kBinary>(p, st);
+    if (p.kind == kAdaptN4)
+        return p.N == 32 ? launch_decode<32, kAdaptN4>(p, st) : launch_decode<0, kAdaptN4>(p, st);
+    if (p.kind == kAdaptN8)
+        return p.N == 32 ? launch_decode<32, kAdaptN8>(p, st) : launch_decode<0, kAdaptN8>(p, st);
+    if (p.kind == kAdaptN16)
+        return p.N == 32 ? launch_decode<32, kAdaptN16>(p, st) : launch_decode<0, kAdaptN16>(p, st);
     return p.N == 32 ? launch_decode<32, kPlain>(p, st) : launch_decode<0, kPlain>(p, st);
 }
 
@@ -328,6 +344,26 @@ extern "C" int rans_decode_adaptive(const uint8_t *d_msg, uint64_t msg_size,
     p.out = d_symbols;
     p.status = d_status;
     p.kind = kAdaptive;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
+    return launch_range(p, 0, p.n_chunks, st);
+}
+
+extern "C" int rans_decode_adaptive_n(const uint8_t *d_msg, uint64_t msg_size, uint32_t n_alpha,
+                                      const rans_params *params, uint8_t *d_symbols,
+                                      uint64_t n_symbols, uint32_t *d_status,
+                                      rans_stream_t stream) {
+    if (n_alpha < 2 || n_alpha > RANS_ADAPTIVE_N_MAX) return RANS_ERR_INVALID_ARG;
+    uint16_t any_model[2] = {RANS_M / 2, RANS_M / 2};  // the models need no table
+    DecodeParams p;
+    const int rc = prepare_decode(d_msg, msg_size, any_model, 2, params, n_symbols, p);
+    if (rc != RANS_OK) return rc;
+    if (!d_status || !aligned16(d_msg) || (n_symbols && !d_symbols)) return RANS_ERR_INVALID_ARG;
+    p.msg = d_msg;
+    p.out = d_symbols;
+    p.status = d_status;
+    p.n_alpha = n_alpha;
+    p.kind = n_alpha <= 4 ? kAdaptN4 : n_alpha <= 8 ? kAdaptN8 : kAdaptN16;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return RANS_ERR_CUDA;
     return launch_range(p, 0, p.n_chunks, st);

@@ -37,6 +37,7 @@ struct EncodeParams {
     const uint16_t *raw;  // bypass messages: raw word of each symbol
     uint32_t *ctx;        // adaptive messages: scratch, pass 1's words per chunk
     uint64_t ctx_stride;  // u32 words per chunk in ctx
+    uint32_t n_alpha;     // adaptive-n messages: the alphabet size n
     // Whole messages placed by the coder itself: the message and where its
     // pieces are, and the chunk ticket (zeroed before the launch).
     enc::Placement pl;
@@ -51,6 +52,14 @@ struct EncodeParams {
 constexpr int kPlain = 0, kBypass = 1, kBytes = 2, kAdaptive = 3;
 // Plain messages with M = 2^13 or 2^14 (16-byte table entries).
 constexpr int kWide = 4;
+// Adaptive models over n symbols (version 6), per coder, with room for 3, 7
+// or 15 boundaries (n <= 4, 8, 16): pass 1 stores each symbol's (B, f).
+constexpr int kAdaptN4 = 5, kAdaptN8 = 6, kAdaptN16 = 7;
+template <int KIND>
+struct AdaptN {
+    static constexpr bool kOn = KIND == kAdaptN4 || KIND == kAdaptN8 || KIND == kAdaptN16;
+    static constexpr int kNB = KIND == kAdaptN4 ? 3 : KIND == kAdaptN8 ? 7 : 15;
+};
 
 // PLACE: the next chunk number from the ticket counter (the order the warps
 // start their chunks), else chunks strided over the grid's warps.
@@ -68,13 +77,14 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     constexpr bool BYTES = KIND == kBytes;
     constexpr bool ADAPT = KIND == kAdaptive;
     constexpr bool WIDE = KIND == kWide;
+    constexpr bool ADAPTN = AdaptN<KIND>::kOn;
     extern __shared__ __align__(128) uint8_t smem[];
     const enc::Smem sm = enc::smem_layout(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     if (WIDE)
         enc::build_wide_encode_table(p.freq, p.log2m, reinterpret_cast<uint4 *>(sm.tab),
                                      reinterpret_cast<uint32_t *>(sm.rings));
-    else if (!ADAPT)  // adaptive contexts need no table
+    else if (!ADAPT && !ADAPTN)  // adaptive models need no table
         enc::build_encode_table(p.freq, sm.tab, reinterpret_cast<uint32_t *>(sm.rings),
                                 RAW ? p.raw_words : nullptr);
     const uint32_t ring_s = sm.rings_s + warp * enc::kRing;
@@ -85,15 +95,18 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     // published: the look-back rarely waits.  Trying at once, without
     // waiting, measured slower (1 GiB: 1.515 against 1.430 ms).
     constexpr uint32_t kNone = 0xFFFFFFFFu;
-    constexpr int kCopyU = ADAPT ? 2 : 4;
+    constexpr int kCopyU = ADAPT || ADAPTN ? 2 : 4;
     uint32_t pending = kNone;
     for (uint32_t c = PLACE ? next_chunk<true>(p, 0, lane) : p.c_begin + blockIdx.x * kWarps + warp;
          c < p.c_end; c = next_chunk<PLACE>(p, c, lane)) {
         const uint64_t first = uint64_t(c) * p.CS;
         const uint32_t n_c = uint32_t(umin64(p.CS, p.n_sym - first));
-        uint32_t *ctx = ADAPT ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
+        uint32_t *ctx = ADAPT || ADAPTN ? p.ctx + uint64_t(c) * p.ctx_stride : nullptr;
         if (ADAPT) enc::adaptive_forward<NT>(p.sym + first, n_c, p.N, ctx, lane, acc);
-        enc::encode_chunk<NT, !RAW && !ADAPT, RAW, BYTES, ADAPT, WIDE>(
+        if (ADAPTN)
+            enc::adaptive_n_forward<NT, AdaptN<KIND>::kNB>(p.sym + first, n_c, p.N, p.n_alpha, ctx,
+                                                          lane, acc);
+        enc::encode_chunk<NT, !RAW && !ADAPT && !ADAPTN, RAW, BYTES, ADAPT, WIDE, ADAPTN>(
             p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
             acc, RAW ? p.raw + first : nullptr, ctx);
@@ -223,6 +236,9 @@ int encode_placed(EncodeParams &ep, const ScratchLayout &sl, uint8_t *scr, uint8
     switch (kind) {
         case kWide: rc = n32 ? launch_encode<32, kWide, true>(ep, st) : launch_encode<0, kWide, true>(ep, st); break;
         case kAdaptive: rc = n32 ? launch_encode<32, kAdaptive, true>(ep, st) : launch_encode<0, kAdaptive, true>(ep, st); break;
+        case kAdaptN4: rc = n32 ? launch_encode<32, kAdaptN4, true>(ep, st) : launch_encode<0, kAdaptN4, true>(ep, st); break;
+        case kAdaptN8: rc = n32 ? launch_encode<32, kAdaptN8, true>(ep, st) : launch_encode<0, kAdaptN8, true>(ep, st); break;
+        case kAdaptN16: rc = n32 ? launch_encode<32, kAdaptN16, true>(ep, st) : launch_encode<0, kAdaptN16, true>(ep, st); break;
         case kBypass: rc = n32 ? launch_encode<32, kBypass, true>(ep, st) : launch_encode<0, kBypass, true>(ep, st); break;
         case kBytes: rc = n32 ? launch_encode<32, kBytes, true>(ep, st) : launch_encode<0, kBytes, true>(ep, st); break;
         default: rc = n32 ? launch_encode<32, kPlain, true>(ep, st) : launch_encode<0, kPlain, true>(ep, st); break;
@@ -276,10 +292,11 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
                           const rans_params *params, uint8_t *d_out, uint64_t out_cap,
                           uint64_t *d_out_size, uint32_t *d_status, void *d_scratch,
                           uint64_t scratch_cap, rans_stream_t stream, bool bytes = false,
-                          bool adaptive = false) {
+                          bool adaptive = false, uint32_t adaptive_n = 0) {
     // Plain messages may use M = 2^13 or 2^14 (the table's sum); the other
-    // kinds keep M = 2^12.
-    const bool plain = raw_words == nullptr && !bytes && !adaptive;
+    // kinds keep M = 2^12.  adaptive_n > 0: adaptive models over that many
+    // symbols (the model argument is not used).
+    const bool plain = raw_words == nullptr && !bytes && !adaptive && !adaptive_n;
     uint32_t lm = RANS_LOG2_M;
     if (!params_ok(params) ||
         !(plain ? table_log2m(h_freq, n_alpha, &lm) : table_ok(h_freq, n_alpha, nullptr)) ||
@@ -302,9 +319,11 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     const uint64_t max_out = bypass  ? rans_max_encoded_size_bypass(n_symbols, params)
                              : bytes ? rans_max_encoded_size_bytes(n_symbols, params)
                                      : rans_max_encoded_size(n_symbols, params);
-    const uint64_t ctx_stride = adaptive_ctx_stride(params->chunk_symbols, params->n_lanes);
+    const uint64_t ctx_stride = adaptive_n ? uint64_t(params->chunk_symbols)
+                                           : adaptive_ctx_stride(params->chunk_symbols,
+                                                                 params->n_lanes);
     const uint64_t need_scratch =
-        adaptive ? sl.ctx + round16(4 * g.n_chunks * ctx_stride) : sl.total;
+        adaptive || adaptive_n ? sl.ctx + round16(4 * g.n_chunks * ctx_stride) : sl.total;
     if (out_cap < max_out || scratch_cap < need_scratch) return RANS_ERR_BUFFER_TOO_SMALL;
 
     EncodeParams ep{};
@@ -335,16 +354,23 @@ static int encode_message(const uint8_t *d_symbols, const uint16_t *d_raw, uint6
     ep.c_begin = 0;
     ep.c_end = ep.n_chunks;
     ep.log2m = lm;
+    ep.n_alpha = adaptive_n;
     for (uint32_t s = 0; s < n_alpha; ++s) ep.freq[s] = h_freq[s];
 
-    const uint32_t version = bypass     ? RANS_VERSION_BYPASS
-                             : bytes    ? RANS_VERSION_BYTES
-                             : adaptive ? RANS_VERSION_ADAPTIVE
-                                        : RANS_VERSION;
+    const uint32_t version = bypass       ? RANS_VERSION_BYPASS
+                             : bytes      ? RANS_VERSION_BYTES
+                             : adaptive   ? RANS_VERSION_ADAPTIVE
+                             : adaptive_n ? RANS_VERSION_ADAPTIVE_N
+                                          : RANS_VERSION;
+    // adaptive-n headers record n beside log2 M
+    const uint32_t hdr_lm = adaptive_n ? lm | (adaptive_n << 16) : lm;
+    ep.log2m = hdr_lm;
     if (g.n_chunks == 0)
         return encode_empty(d_out, d_out_size, d_status, n_symbols, params, uint32_t(g.data0),
-                            version, lm, st);
-    const int kind = lm != RANS_LOG2_M ? kWide
+                            version, hdr_lm, st);
+    const int kind = adaptive_n      ? (adaptive_n <= 4 ? kAdaptN4 : adaptive_n <= 8 ? kAdaptN8
+                                                                                  : kAdaptN16)
+                     : lm != RANS_LOG2_M ? kWide
                      : adaptive        ? kAdaptive
                      : bypass          ? kBypass
                      : bytes           ? kBytes
@@ -368,6 +394,26 @@ extern "C" int rans_encode_adaptive(const uint8_t *d_symbols, uint64_t n_symbols
     return encode_message(d_symbols, nullptr, n_symbols, any_model, nullptr, 2, params, d_out,
                           out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream, false,
                           true);
+}
+
+extern "C" uint64_t rans_encode_scratch_size_adaptive_n(uint64_t n_symbols,
+                                                        const rans_params *params) {
+    if (!params_ok(params)) return 0;
+    const MessageGeometry g = geometry(n_symbols, params);
+    return scratch_layout(g.n_chunks, params->n_lanes, params->chunk_symbols).ctx +
+           round16(4 * g.n_chunks * uint64_t(params->chunk_symbols));
+}
+
+extern "C" int rans_encode_adaptive_n(const uint8_t *d_symbols, uint64_t n_symbols,
+                                      uint32_t n_alpha, const rans_params *params, uint8_t *d_out,
+                                      uint64_t out_cap, uint64_t *d_out_size, uint32_t *d_status,
+                                      void *d_scratch, uint64_t scratch_cap,
+                                      rans_stream_t stream) {
+    if (n_alpha < 2 || n_alpha > RANS_ADAPTIVE_N_MAX) return RANS_ERR_INVALID_ARG;
+    const uint16_t any_model[2] = {RANS_M / 2, RANS_M / 2};  // the models need no table
+    return encode_message(d_symbols, nullptr, n_symbols, any_model, nullptr, 2, params, d_out,
+                          out_cap, d_out_size, d_status, d_scratch, scratch_cap, stream, false,
+                          false, n_alpha);
 }
 
 extern "C" int rans_encode_bytes(const uint8_t *d_symbols, uint64_t n_symbols,

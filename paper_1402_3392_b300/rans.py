@@ -123,6 +123,9 @@ def _load() -> C.CDLL:
         "rans_encode_scratch_size_adaptive": (u64, [u64, pp]),
         "rans_encode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp, vp, u64, vp]),
         "rans_decode_adaptive": (i32, [vp, u64, pp, vp, u64, vp, vp]),
+        "rans_encode_scratch_size_adaptive_n": (u64, [u64, pp]),
+        "rans_encode_adaptive_n": (i32, [vp, u64, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
+        "rans_decode_adaptive_n": (i32, [vp, u64, u32, pp, vp, u64, vp, vp]),
         "rans_decode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, u64, vp]),
         "rans_encode_host_work_size": (u64, [u64, pp]),
         "rans_encode_host": (i32, [vp, u64, vp, u32, pp, vp, u64, vp, vp, vp, u64, vp]),
@@ -433,6 +436,77 @@ def decode_adaptive(msg, n_symbols: int, n_lanes: int = 32, chunk_symbols: int =
         st = int(status.item())
         if st != RANS_OK:
             raise RansError(st, "rans_decode_adaptive (device status)")
+    return out[:n_symbols], status
+
+
+RANS_ADAPTIVE_N_MAX = 16
+
+
+def rans_encode_scratch_size_adaptive_n(n_symbols: int, n_lanes: int, chunk_symbols: int) -> int:
+    return int(lib.rans_encode_scratch_size_adaptive_n(int(n_symbols),
+                                                       C.byref(_params(n_lanes, chunk_symbols))))
+
+
+def rans_encode_adaptive_n(d_symbols, n_symbols, n_alpha, n_lanes, chunk_symbols, d_out, out_cap,
+                           d_out_size, d_status, d_scratch, scratch_cap, stream=None,
+                           check=True) -> int:
+    """Adaptive encode over n_alpha <= 16 symbols: one model per coder (Section 5)."""
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_encode_adaptive_n(_ptr(d_symbols), int(n_symbols), int(n_alpha), C.byref(p),
+                                    _ptr(d_out), int(out_cap), _ptr(d_out_size), _ptr(d_status),
+                                    _ptr(d_scratch), int(scratch_cap), _stream(stream))
+    return _check(rc, "rans_encode_adaptive_n") if check else rc
+
+
+def rans_decode_adaptive_n(d_msg, msg_size, n_alpha, n_lanes, chunk_symbols, d_symbols, n_symbols,
+                           d_status, stream=None, check=True) -> int:
+    p = _params(n_lanes, chunk_symbols)
+    rc = lib.rans_decode_adaptive_n(_ptr(d_msg), int(msg_size), int(n_alpha), C.byref(p),
+                                    _ptr(d_symbols), int(n_symbols), _ptr(d_status),
+                                    _stream(stream))
+    return _check(rc, "rans_decode_adaptive_n") if check else rc
+
+
+def encode_adaptive_n(symbols, n_alpha: int, n_lanes: int = 32, chunk_symbols: int = 65536,
+                      stream=None, sync: bool = True):
+    """Encode a CUDA uint8 tensor of symbols < n_alpha with per-coder adaptive
+    models; (message, size, status)."""
+    import torch
+
+    dev = symbols.device
+    n = symbols.numel()
+    cap = rans_max_encoded_size(n, n_lanes, chunk_symbols)
+    scap = rans_encode_scratch_size_adaptive_n(n, n_lanes, chunk_symbols)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(scap, 16), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_encode_adaptive_n(symbols, n, n_alpha, n_lanes, chunk_symbols, out, cap, size, status,
+                           scratch, scratch.numel(), stream)
+    if not sync:
+        return out, size, status
+    torch.cuda.synchronize(dev)
+    st = int(status.item())
+    if st != RANS_OK:
+        raise RansError(st, "rans_encode_adaptive_n (device status)")
+    return out[: int(size.item())], size, status
+
+
+def decode_adaptive_n(msg, n_symbols: int, n_alpha: int, n_lanes: int = 32,
+                      chunk_symbols: int = 65536, stream=None, sync: bool = True):
+    """Decode an adaptive-n message; (symbols, status)."""
+    import torch
+
+    dev = msg.device
+    out = torch.empty(max(1, n_symbols), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rans_decode_adaptive_n(msg, msg.numel(), n_alpha, n_lanes, chunk_symbols, out, n_symbols,
+                           status, stream)
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st != RANS_OK:
+            raise RansError(st, "rans_decode_adaptive_n (device status)")
     return out[:n_symbols], status
 
 

@@ -26,6 +26,9 @@ Workloads (sizes and distributions):
   adaptive : 256 Mi bits for adaptive per-coder contexts, 4096 chunks of
              64 Ki, 32-way interleaving; P(bit = 0) is piecewise constant over
              segments of 4096 symbols, each segment's p0 ~ U[0.001, 0.999]
+  adaptive_n: 256 Mi symbols over 16 for adaptive per-coder models, 4096
+             chunks of 64 Ki, 32-way interleaving; the distribution is
+             constant over runs of 4096 symbols, Dirichlet(0.5) per run
 """
 from __future__ import annotations
 
@@ -50,6 +53,8 @@ WORKLOADS = {
                    n_lanes=32, chunk_symbols=1 << 16),
     "adaptive": dict(index=6, n_symbols=1 << 28, n_lanes=32, chunk_symbols=1 << 16,
                      segment=4096, p0_lo=0.001, p0_hi=0.999),
+    "adaptive_n": dict(index=7, n_symbols=1 << 28, n_alpha=16, n_lanes=32,
+                       chunk_symbols=1 << 16, segment=4096, dirichlet=0.5),
 }
 
 
@@ -147,6 +152,46 @@ def drifting_bits_device(n: int, segment: int, seed: int, device, lo: float = 0.
         p0 = lo + (hi - lo) * torch.rand(n_seg, generator=g, device=device, dtype=torch.float64)
         u = torch.rand(z - a, generator=g, device=device, dtype=torch.float64)
         out[a:z] = (u >= p0.repeat_interleave(segment)[: z - a]).to(torch.uint8)
+    return out
+
+
+def drifting_symbols(rng: np.random.Generator, n: int, n_alpha: int, segment: int,
+                     alpha: float = 0.5) -> np.ndarray:
+    """n symbols (uint8 < n_alpha) whose distribution is constant over each
+    run of `segment` symbols and drawn Dirichlet(alpha) per run (host)."""
+    n_seg = max(1, -(-n // segment))
+    out = np.empty(n, dtype=np.uint8)
+    for k in range(n_seg):
+        a, z = k * segment, min(n, (k + 1) * segment)
+        p = rng.dirichlet(np.full(n_alpha, alpha))
+        cdf = np.cumsum(p)
+        cdf[-1] = 1.0
+        out[a:z] = np.minimum(np.searchsorted(cdf, rng.random(z - a), side="right"),
+                              n_alpha - 1)
+    return out
+
+
+def drifting_symbols_device(n: int, n_alpha: int, segment: int, seed: int, device,
+                            alpha: float = 0.5, piece: int = 1 << 26):
+    """drifting_symbols generated on a CUDA device (torch), in pieces; piece
+    must be a multiple of segment.  The per-run Dirichlet draws are made as
+    normalised Gamma(alpha) variates."""
+    import torch
+
+    assert piece % segment == 0
+    g = torch.Generator(device=device)
+    g.manual_seed(seed & 0x7FFFFFFFFFFFFFFF)
+    out = torch.empty(n, dtype=torch.uint8, device=device)
+    conc = torch.full((n_alpha,), float(alpha), dtype=torch.float64, device=device)
+    for a in range(0, n, piece):
+        z = min(n, a + piece)
+        n_seg = -(-(z - a) // segment)
+        gam = torch._standard_gamma(conc.expand(n_seg, n_alpha).contiguous(), generator=g)
+        cdf = torch.cumsum(gam / gam.sum(dim=1, keepdim=True), dim=1)
+        cdf[:, -1] = 1.0
+        u = torch.rand(n_seg * segment, generator=g, device=device, dtype=torch.float64)
+        idx = torch.searchsorted(cdf, u.view(n_seg, segment), right=True).view(-1)[: z - a]
+        out[a:z] = idx.clamp_(max=n_alpha - 1).to(torch.uint8)
     return out
 
 

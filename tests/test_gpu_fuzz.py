@@ -57,6 +57,12 @@ def message(rlib, orc, kind, rng):
         m = orc.encode_message(bits, fb, N=N, chunk_symbols=CS)
         ref = lambda b: orc.decode_message(b, N_SYM, fb, N=N, chunk_symbols=CS)  # noqa: E731
         gpu = lambda d: rlib.decode(d, N_SYM, fb, N, CS, sync=False)  # noqa: E731
+    elif kind == "adaptive_n":         # per-coder models over 9 symbols
+        syms = wl.drifting_symbols(rng, N_SYM, 9, 500, 0.5)
+        m = orc.encode_message_adaptive_n(syms, 9, N=N, chunk_symbols=CS)
+        ref = lambda b: orc.decode_message_adaptive_n(b, N_SYM, 9, N=N,  # noqa: E731
+                                                      chunk_symbols=CS)
+        gpu = lambda d: rlib.decode_adaptive_n(d, N_SYM, 9, N, CS, sync=False)  # noqa: E731
     elif kind == "wide14":
         f14 = rlib.rans_quantize_table(wl.weights_from_probs(p), 14)
         m = orc.encode_message(sym, f14, N=N, chunk_symbols=CS)
@@ -89,7 +95,7 @@ def damage(m, rng, how):
 
 
 @pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14",
-                                  "binary"])
+                                  "binary", "adaptive_n"])
 @pytest.mark.parametrize("how", ["bytes", "offset", "chunk"])
 def test_damaged_messages_agree_with_oracle(rlib, orc, cuda, kind, how):
     rng = np.random.default_rng(zlib.crc32(repr(("fuzz", kind, how)).encode()))
@@ -120,7 +126,7 @@ def _gpu_status(torch, gpu, bad, cuda):
 
 
 @pytest.mark.parametrize("kind", ["plain", "bypass", "bytes", "adaptive", "prefix", "wide14",
-                                  "binary"])
+                                  "binary", "adaptive_n"])
 def test_truncated_messages_agree_with_oracle(rlib, orc, cuda, kind):
     """Messages cut short: by whole 16-byte blocks (the size no longer matches
     the offset table: both reject); cut with the offset table's last entry
