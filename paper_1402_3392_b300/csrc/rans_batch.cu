@@ -23,25 +23,35 @@ namespace {
 constexpr int kSetupThreads = 1024;
 
 struct BatchLayout {
-    uint64_t prefix, counter, total;
+    uint64_t prefix, wprefix, counter, total;
 };
 BatchLayout batch_layout(uint32_t n) {
     BatchLayout l{};
+    const uint64_t arr = round16(4ull * (uint64_t(n) + 1));
     l.prefix = 0;
-    l.counter = round16(4ull * (uint64_t(n) + 1));
+    l.wprefix = arr;
+    l.counter = 2 * arr;
     l.total = l.counter + 16;
     return l;
 }
 
+// Two kinds of work item.  A CTA item: up to item_chunks chunks of one
+// stream, decoded by the whole CTA with the stream's slot table in shared
+// memory (the CTA rebuilds it when the model changes).  A warp item: up to
+// two chunks of a stream with a binary model (symbols 0 and 1, both with
+// f > 0), decoded by one warp alone -- D needs no table, so the warps of a
+// CTA take chunks of different streams and wait on nobody.  The persistent
+// kernel's CTAs drain the CTA items first, then their warps the warp items.
 struct BatchDecodeParams {
     const rans_stream *streams;
     const uint16_t *freqs;
     uint32_t *status;
-    uint32_t *prefix;   // n_streams + 1 work-item offsets
-    uint32_t *counter;  // next work item
+    uint32_t *prefix;   // n_streams + 1 CTA-item offsets
+    uint32_t *wprefix;  // n_streams + 1 warp-item offsets
+    uint32_t *counter;  // [0] next CTA item, [1] next warp item
     uint32_t n_streams;
     uint32_t n_tables;
-    uint32_t item_chunks;  // chunks in one work item: the CTA's warps x chunks per warp
+    uint32_t item_chunks;  // chunks in one CTA item: the CTA's warps x chunks per warp
 };
 
 struct StreamGeom {
@@ -66,58 +76,90 @@ __device__ __forceinline__ StreamGeom check_stream(const rans_stream &d, uint32_
     return g;
 }
 
-// One CTA: statuses, work-item prefix, counter.
+// The binary-model test the setup kernel can afford per stream (its first
+// two frequencies); the warp that decodes a chunk checks the whole table.
+__device__ __forceinline__ bool binary_candidate(const uint16_t *fr) {
+    const uint32_t f0 = fr[0], f1 = fr[1];
+    return f0 > 0 && f1 > 0 && f0 + f1 == kM;
+}
+
+// One CTA: statuses, the CTA-item and warp-item prefixes, counters.
 __global__ void __launch_bounds__(kSetupThreads)
     batch_setup_kernel(const __grid_constant__ BatchDecodeParams p) {
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry_s;
+    __shared__ uint32_t sums[2][32];
+    __shared__ uint32_t carry_s[2];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
+    if (tid < 2) carry_s[tid] = 0;
     __syncthreads();
     for (uint32_t base = 0; base < p.n_streams; base += kSetupThreads) {
         const uint32_t i = base + tid;
-        uint32_t items = 0;
+        uint32_t v[2] = {0u, 0u};  // CTA items, warp items
         if (i < p.n_streams) {
-            const StreamGeom g = check_stream(p.streams[i], p.n_tables);
+            const rans_stream d = p.streams[i];
+            const StreamGeom g = check_stream(d, p.n_tables);
             p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
-            if (g.ok) {
+            if (g.ok && g.n_chunks > 0 && binary_candidate(p.freqs + uint64_t(d.table) * 256)) {
+                v[1] = uint32_t((g.n_chunks + dec::kChains - 1) / dec::kChains);
+            } else if (g.ok) {
                 const uint64_t k = (g.n_chunks + p.item_chunks - 1) / p.item_chunks;
-                items = k > 0 ? uint32_t(k) : 1u;  // an empty stream still has its header checked
+                v[0] = k > 0 ? uint32_t(k) : 1u;  // an empty stream still has its header checked
             }
         }
-        uint32_t incl = items;
+        uint32_t incl[2] = {v[0], v[1]};
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, d);
-            if (lane >= uint32_t(d)) incl += y;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t y = __shfl_up_sync(kFull, incl[k], d);
+                if (lane >= uint32_t(d)) incl[k] += y;
+            }
         }
-        if (lane == 31) warp_sums[warp] = incl;
+        if (lane == 31) {
+            sums[0][warp] = incl[0];
+            sums[1][warp] = incl[1];
+        }
         __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = warp_sums[lane];
+        if (warp < 2) {
+            const uint32_t w = sums[warp][lane];
             uint32_t wi = w;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint32_t y = __shfl_up_sync(kFull, wi, d);
                 if (lane >= uint32_t(d)) wi += y;
             }
-            warp_sums[lane] = wi - w;
+            sums[warp][lane] = wi - w;
         }
         __syncthreads();
-        const uint32_t carry = carry_s;
-        if (i < p.n_streams) p.prefix[i] = carry + warp_sums[warp] + incl - items;
+        const uint32_t c0 = carry_s[0], c1 = carry_s[1];
+        if (i < p.n_streams) {
+            p.prefix[i] = c0 + sums[0][warp] + incl[0] - v[0];
+            p.wprefix[i] = c1 + sums[1][warp] + incl[1] - v[1];
+        }
         __syncthreads();
-        if (tid == kSetupThreads - 1) carry_s = carry + warp_sums[warp] + incl;
+        if (tid == kSetupThreads - 1) {
+            carry_s[0] = c0 + sums[0][warp] + incl[0];
+            carry_s[1] = c1 + sums[1][warp] + incl[1];
+        }
         __syncthreads();
     }
     if (tid == 0) {
-        p.prefix[p.n_streams] = carry_s;
-        *p.counter = 0;
+        p.prefix[p.n_streams] = carry_s[0];
+        p.wprefix[p.n_streams] = carry_s[1];
+        p.counter[0] = p.counter[1] = 0;
     }
 }
 
-// W warps a CTA; PAIR: a warp decodes two chunks side by side (one item =
-// 2W chunks), else one (one item = W chunks).
+// The stream of work item v: the largest s with prefix[s] <= v.
+__device__ __forceinline__ uint32_t item_stream(const uint32_t *prefix, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Bounded for the shape's resident CTAs per SM (8 warps: 4, at most 64
 // registers; 12 warps: 3, at most 56).
 template <int W, bool PAIR>
@@ -133,7 +175,6 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
     uint32_t &const_sym = sm.misc[3];
     uint32_t &model_ok = sm.misc[4];
     uint32_t &hdr_ok = sm.misc[5];
-    uint32_t &bin_f = sm.misc[6];       // binary model: f_0 | f_1 << 16, else 0
     if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
     dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t lt = lanemask_lt();
@@ -145,12 +186,7 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
             const uint32_t it = atomicAdd(p.counter, 1u);
             item_s = it;
             if (it < total) {
-                uint32_t lo = 0, hi = p.n_streams;  // largest s with prefix[s] <= it
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (p.prefix[mid] <= it) lo = mid;
-                    else hi = mid;
-                }
+                const uint32_t lo = item_stream(p.prefix, p.n_streams, it);
                 stream_s = lo;
                 const rans_stream d = p.streams[lo];
                 const StreamGeom g = check_stream(d, p.n_tables);
@@ -164,29 +200,12 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
         const uint32_t s = stream_s;
         const rans_stream d = p.streams[s];
         if (d.table != loaded) {
-            // A binary model (symbols 0 and 1 only, both with f > 0) needs no
-            // slot table: its D is two multiply-adds (dec::kKindBinary).
-            const uint16_t *fr = p.freqs + uint64_t(d.table) * 256;
-            const uint32_t f0 = fr[0], f1 = fr[1];
-            bool binary = f0 > 0 && f1 > 0 && f0 + f1 == kM;
-            for (uint32_t k = 2 + lane; binary && k < 256; k += 32) binary = fr[k] == 0;
-            binary = __all_sync(kFull, binary);
-            const bool cta_binary = __syncthreads_and(binary);
-            if (cta_binary) {
-                if (threadIdx.x == 0) {
-                    const_sym = dec::kNoConst;
-                    loaded = d.table;
-                    model_ok = 1;
-                    bin_f = f0 | (f1 << 16);
-                }
-            } else {
-                if (threadIdx.x == 0) const_sym = dec::kNoConst;
-                const uint32_t sum = dec::build_slot_table<W>(fr, sm.tab, sm.rings, &const_sym);
-                if (threadIdx.x == 0) {
-                    loaded = d.table;
-                    model_ok = sum == kM;
-                    bin_f = 0;
-                }
+            if (threadIdx.x == 0) const_sym = dec::kNoConst;
+            const uint32_t sum = dec::build_slot_table<W>(p.freqs + uint64_t(d.table) * 256,
+                                                          sm.tab, sm.rings, &const_sym);
+            if (threadIdx.x == 0) {
+                loaded = d.table;
+                model_ok = sum == kM;
             }
             __syncthreads();
         }
@@ -205,20 +224,8 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
             const uint32_t count = uint32_t(umin64(kPer, g.n_chunks - c));
-            const uint32_t bf = bin_f;
-            uint32_t st;
-            if (bf)  // binary model: f_0 and f_1 ride in the table and flag arguments
-                st = d.n_lanes == 32
-                         ? dec::decode_chunks<32, PAIR, dec::kKindBinary>(
-                               wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
-                               d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane, lt, nullptr,
-                               bf >> 16)
-                         : dec::decode_chunks<0, PAIR, dec::kKindBinary>(
-                               wr, bf & 0xFFFFu, d.msg, g.data0, offs, data_end, c, count,
-                               d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs, lane, lt,
-                               nullptr, bf >> 16);
-            else
-                st = d.n_lanes == 32
+            const uint32_t st =
+                d.n_lanes == 32
                          ? dec::decode_chunks<32, PAIR>(wr, sm.tab_s, d.msg, g.data0, offs,
                                                         data_end, c, count, d.n_symbols,
                                                         d.chunk_symbols, 32, d.symbols, cs, lane,
@@ -229,6 +236,49 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
                                                        lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);
         }
+    }
+
+    // Warp items: chunk pairs of binary-model streams, a warp at a time.
+    const uint32_t wtotal = p.wprefix[p.n_streams];
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(p.counter + 1, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= wtotal || wr.timeouts) break;
+        const uint32_t s = item_stream(p.wprefix, p.n_streams, it);
+        const rans_stream d = p.streams[s];
+        const StreamGeom g = check_stream(d, p.n_tables);
+        // the whole model: two frequencies summing to M leave no room for
+        // others in a valid table
+        const uint16_t *fr = p.freqs + uint64_t(d.table) * 256;
+        uint32_t part = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) part += fr[lane * 8 + k];
+        const bool model_ok = __reduce_add_sync(kFull, part) == kM;
+        uint32_t hdr = 0;
+        if (lane == 0)
+            hdr = dec::header_ok(d.msg, d.msg_size, g.data0, d.n_symbols, d.n_lanes,
+                                 d.chunk_symbols, uint32_t(g.n_chunks));
+        hdr = __shfl_sync(kFull, hdr, 0);
+        if (!model_ok || !hdr) {
+            if (lane == 0) report(p.status + s, model_ok ? RANS_ERR_CORRUPT : RANS_ERR_INVALID_ARG);
+            continue;
+        }
+        const uint32_t f0 = fr[0], f1 = fr[1];
+        const uint32_t c = (it - p.wprefix[s]) * dec::kChains;
+        const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
+        const uint32_t data_end = offs[g.n_chunks];
+        const uint32_t count = uint32_t(umin64(dec::kChains, g.n_chunks - c));
+        // f_0 and f_1 ride in the table and flag arguments
+        const uint32_t st =
+            d.n_lanes == 32
+                ? dec::decode_chunks<32, true, dec::kKindBinary>(
+                      wr, f0, d.msg, g.data0, offs, data_end, c, count, d.n_symbols,
+                      d.chunk_symbols, 32, d.symbols, dec::kNoConst, lane, lt, nullptr, f1)
+                : dec::decode_chunks<0, true, dec::kKindBinary>(
+                      wr, f0, d.msg, g.data0, offs, data_end, c, count, d.n_symbols,
+                      d.chunk_symbols, d.n_lanes, d.symbols, dec::kNoConst, lane, lt, nullptr, f1);
+        if (st != RANS_OK && lane == 0) report(p.status + s, st);
     }
 }
 
@@ -588,6 +638,7 @@ extern "C" int rans_decode_batch(const rans_stream *d_streams, uint32_t n_stream
     p.freqs = d_freqs;
     p.status = d_status;
     p.prefix = reinterpret_cast<uint32_t *>(scr + l.prefix);
+    p.wprefix = reinterpret_cast<uint32_t *>(scr + l.wprefix);
     p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
     p.n_streams = n_streams;
     p.n_tables = n_tables;

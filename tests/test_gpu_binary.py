@@ -135,3 +135,36 @@ def test_damaged_binary_batch_stream_is_reported(rlib, orc, cuda):
     assert list(st) == [0, rlib.RANS_ERR_CORRUPT, 0]
     for i in (0, 2):
         assert np.array_equal(dec.output(i).cpu().numpy(), syms[i])
+
+
+def test_batched_binary_edge_streams(rlib, orc, cuda):
+    """In one batch: an empty binary stream (its header is still checked), a
+    binary-looking table that is not a valid model (f_0 + f_1 = M plus one
+    more symbol: RANS_ERR_INVALID_ARG for that stream alone), one-chunk and
+    odd-chunk binary streams, and a 256-symbol stream."""
+    import torch
+
+    rng = np.random.default_rng(227)
+    good = binary_table(2900)
+    bad = np.zeros(256, dtype=np.uint16)
+    bad[0], bad[1], bad[7] = 2900, 1196, 3
+    zipf = rlib.rans_quantize_table(wl.weights_from_probs(wl.zipf_probs(256, 1.1)))
+    tables = [good, bad, zipf]
+    plan = [(0, 0), (0, 5000), (0, 3 * 4096 + 17), (1, 9000), (2, 30_000), (0, 1)]
+    syms, msgs = [], []
+    for t, n in plan:
+        f = tables[t] if t != 1 else good            # the bad table's message is a good one
+        s = draw(rng, f, n) if t != 2 else rng.choice(256, size=n, p=zipf / zipf.sum()).astype(np.uint8)
+        syms.append(s)
+        msgs.append(orc.encode_message(s, f, N=32, chunk_symbols=4096))
+    offs, total = B.aligned_offsets([m.size for m in msgs])
+    host = np.zeros(total, dtype=np.uint8)
+    for m, o in zip(msgs, offs):
+        host[o:o + m.size] = m
+    dec = B.BatchDecoder(torch.from_numpy(host).to(cuda), offs, [m.size for m in msgs],
+                         [s.size for s in syms], B.upload_tables(tables, cuda),
+                         [t for t, _ in plan], 32, 4096)
+    st = dec().cpu().numpy()
+    assert list(st) == [0, 0, 0, rlib.RANS_ERR_INVALID_ARG, 0, 0]
+    for i in (1, 2, 4, 5):
+        assert np.array_equal(dec.output(i).cpu().numpy(), syms[i]), i
