@@ -530,9 +530,10 @@ def binary_leg(rans, dev, args, hbm):
     sym = wl.streams_on_device(probs, sizes, offs, arena_bytes, wl.seed_for("binary"), dev)
     tdev = B.upload_tables(tables, dev)
     idx = np.arange(count)
-    sample = np.arange(0, count, 16)
-    best, tried = autotune.autotune(sym, offs[sample], sizes[sample], tdev, sample, widths=(32,),
-                                    reps=3)
+    # 256 MiB in all: every stream goes into the tuning runs, so that each
+    # candidate layout is timed with the whole GPU's worth of work (a sample
+    # leaves a one-chunk-per-stream layout under one wave of warps)
+    best, tried = autotune.autotune(sym, offs, sizes, tdev, idx, widths=(32,), reps=3)
     cs = autotune.chunk_sizes(sizes, best["chunk"], best["policy"])
     eb = B.encode_batch(sym, offs, sizes, tdev, idx, 32, cs)
     torch.cuda.synchronize()
@@ -558,7 +559,8 @@ def binary_leg(rans, dev, args, hbm):
             "compression_ratio": msg_total / total, "bit_exact_roundtrip": bool(ok),
             "roofline": {"kernel": "batch_decode_kernel", "bound": "hbm", "achieved": achieved,
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm},
-            "layout": {"n_lanes": 32, "chunk": best["chunk"], "policy": best["policy"]}}
+            "layout": {"n_lanes": 32, "chunk": best["chunk"], "policy": best["policy"],
+                       "chunk_symbols": int(cs[0]), "candidates": len(tried)}}
 
 
 def bypass_leg(rans, dev, args, hbm):

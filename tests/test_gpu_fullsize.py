@@ -114,7 +114,7 @@ def _streams_vs_oracle(orc, eb, sym_arena, sym_offs, sizes, tables, table_of, N,
 
 def test_binary_4096_streams_every_stream_equals_oracle(rlib, orc, cuda):
     """The binary workload as the benchmark runs it: the autotuner's layout
-    on the same sample, batched encode, batched decode."""
+    (tuned on all the streams), batched encode, batched decode."""
     import torch
 
     cfg = wl.WORKLOADS["binary"]
@@ -129,8 +129,7 @@ def test_binary_4096_streams_every_stream_equals_oracle(rlib, orc, cuda):
     sym = wl.streams_on_device(probs, sizes, offs, arena_bytes, wl.seed_for("binary"), cuda)
     tdev = B.upload_tables(tables, cuda)
     idx = np.arange(count)
-    sample = np.arange(0, count, 16)
-    best, _ = autotune.autotune(sym, offs[sample], sizes[sample], tdev, sample, widths=(32,), reps=2)
+    best, _ = autotune.autotune(sym, offs, sizes, tdev, idx, widths=(32,), reps=2)
     cs = autotune.chunk_sizes(sizes, best["chunk"], best["policy"])
     eb = B.encode_batch(sym, offs, sizes, tdev, idx, 32, cs)
     torch.cuda.synchronize()
