@@ -500,6 +500,7 @@ def batched_leg(rans, dev, args, hbm):
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "algorithmic_bytes_per_launch": msg_total + total},
         "layout": {"n_lanes": N, "chunk": best["chunk"], "policy": best["policy"],
+                   "chunk_symbols_min": int(cs.min()), "chunk_symbols_max": int(cs.max()),
                    "autotune_s": tune_s, "candidates": len(tried)},
         "graph": "setup + persistent decode kernel captured in one CUDA graph, replayed",
     }

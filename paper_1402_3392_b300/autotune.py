@@ -4,15 +4,18 @@ on a sample of its streams.
 
 The layout is a property of the bitstream (the encoder fixes N and the chunk
 size), so the choice is made before encoding.  Candidates:
-  N          : 4, 8, 16, 32 (coders per chunk; the decoder maps one coder to
-               one warp lane, so N < 32 leaves lanes idle)
+  N          : 4, 8, 16, 32 (coders per chunk, which is also the lanes a
+               stream takes: the decoder maps one coder to one warp lane, so
+               N < 32 leaves lanes idle; a warp never holds two streams)
   chunk      : 16, 32, 64, 128, 256 KiB
   per-stream : "fixed" (every stream uses the chunk size) or "fill" (a stream
                shorter than 16 chunks is cut into up to 16 smaller chunks, at
-               least 4 KiB each, so its one work item keeps all 16 chunk
-               slots of a CTA -- 8 warps x 2 chunks -- busy)
+               least 4 KiB each -- below the 16 KiB of the candidate list --
+               so its one work item keeps all 16 chunk slots of a CTA -- 8
+               warps x 2 chunks -- busy)
 The score is decoded bytes per second of the batched decoder (median of a few
-runs); ties go to the larger chunk.
+runs); ties go to the larger chunk.  The chosen policy and the chunk sizes it
+gives are reported beside the result.
 """
 from __future__ import annotations
 

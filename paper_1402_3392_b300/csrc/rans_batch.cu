@@ -149,6 +149,38 @@ __global__ void __launch_bounds__(kSetupThreads)
     }
 }
 
+// item_stream with a whole warp: 32 probes per round narrow the range 32-fold,
+// so 10,000 streams take 3 dependent loads instead of 14.  Warp-uniform.
+__device__ __forceinline__ uint32_t item_stream_warp(const uint32_t *prefix, uint32_t n,
+                                                     uint32_t v, uint32_t lane) {
+    uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + lane * step;
+        const bool le = idx < hi && prefix[idx] <= v;   // true for a prefix of the lanes
+        const uint32_t k = __popc(__ballot_sync(kFull, le)) - 1;   // lane 0 always holds
+        lo += k * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// dec::header_ok with the loads spread over a warp's lanes.  Warp-uniform.
+__device__ __forceinline__ bool header_ok_warp(const uint8_t *msg, uint64_t msg_size,
+                                               uint32_t data0, uint64_t n_sym, uint32_t N,
+                                               uint32_t CS, uint32_t n_chunks, uint32_t lane) {
+    const uint32_t *h32 = reinterpret_cast<const uint32_t *>(msg);
+    const uint32_t idx = lane < 8 ? lane : lane == 8 ? 8u : 8u + n_chunks;
+    const uint32_t v = lane < 10 ? h32[idx] : 0u;
+    const uint64_t hn = uint64_t(__shfl_sync(kFull, v, 4)) | (uint64_t(__shfl_sync(kFull, v, 5)) << 32);
+    const uint32_t want = lane == 0 ? RANS_MAGIC : lane == 1 ? RANS_VERSION : lane == 2 ? N
+                          : lane == 3 ? kLog2M : lane == 6 ? CS : lane == 7 ? n_chunks
+                          : lane == 8 ? 0u : v;
+    const uint32_t last = __shfl_sync(kFull, v, 9);
+    const bool ok = (lane >= 10 || lane == 4 || lane == 5 || lane == 9 || v == want);
+    return __all_sync(kFull, ok) && hn == n_sym && round16(last) == msg_size - data0;
+}
+
 // The stream of work item v: the largest s with prefix[s] <= v.
 __device__ __forceinline__ uint32_t item_stream(const uint32_t *prefix, uint32_t n, uint32_t v) {
     uint32_t lo = 0, hi = n;
@@ -245,7 +277,7 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
         if (lane == 0) it = atomicAdd(p.counter + 1, 1u);
         it = __shfl_sync(kFull, it, 0);
         if (it >= wtotal || wr.timeouts) break;
-        const uint32_t s = item_stream(p.wprefix, p.n_streams, it);
+        const uint32_t s = item_stream_warp(p.wprefix, p.n_streams, it, lane);
         const rans_stream d = p.streams[s];
         const StreamGeom g = check_stream(d, p.n_tables);
         // the whole model: two frequencies summing to M leave no room for
@@ -255,11 +287,8 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
 #pragma unroll
         for (uint32_t k = 0; k < 8; ++k) part += fr[lane * 8 + k];
         const bool model_ok = __reduce_add_sync(kFull, part) == kM;
-        uint32_t hdr = 0;
-        if (lane == 0)
-            hdr = dec::header_ok(d.msg, d.msg_size, g.data0, d.n_symbols, d.n_lanes,
-                                 d.chunk_symbols, uint32_t(g.n_chunks));
-        hdr = __shfl_sync(kFull, hdr, 0);
+        const bool hdr = header_ok_warp(d.msg, d.msg_size, g.data0, d.n_symbols, d.n_lanes,
+                                        d.chunk_symbols, uint32_t(g.n_chunks), lane);
         if (!model_ok || !hdr) {
             if (lane == 0) report(p.status + s, model_ok ? RANS_ERR_CORRUPT : RANS_ERR_INVALID_ARG);
             continue;
