@@ -69,6 +69,9 @@ def parse_args(argv=None):
     ap.add_argument("--batched-layout", default="",
                     help="N,chunk_symbols,policy for the batched leg instead of the "
                          "autotuner's choice (e.g. 32,16384,fill)")
+    ap.add_argument("--binary-layout", default="",
+                    help="chunk_symbols,policy for the binary leg instead of the autotuner's "
+                         "choice (e.g. 16384,fixed)")
     return ap.parse_args(argv)
 
 
@@ -534,7 +537,11 @@ def binary_leg(rans, dev, args, hbm):
     # 256 MiB in all: every stream goes into the tuning runs, so that each
     # candidate layout is timed with the whole GPU's worth of work (a sample
     # leaves a one-chunk-per-stream layout under one wave of warps)
-    best, tried = autotune.autotune(sym, offs, sizes, tdev, idx, widths=(32,), reps=3)
+    if args.binary_layout:
+        ch, pol = args.binary_layout.split(",")
+        best, tried = dict(n_lanes=32, chunk=int(ch), policy=pol), []
+    else:
+        best, tried = autotune.autotune(sym, offs, sizes, tdev, idx, widths=(32,), reps=3)
     cs = autotune.chunk_sizes(sizes, best["chunk"], best["policy"])
     eb = B.encode_batch(sym, offs, sizes, tdev, idx, 32, cs)
     torch.cuda.synchronize()

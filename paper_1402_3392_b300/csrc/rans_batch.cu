@@ -193,11 +193,16 @@ __device__ __forceinline__ uint32_t item_stream(const uint32_t *prefix, uint32_t
 }
 
 // Bounded for the shape's resident CTAs per SM (8 warps: 4, at most 64
-// registers; 12 warps: 3, at most 56).
-template <int W, bool PAIR>
+// registers; 12 warps: 3, at most 56).  A CTA item holds ROUNDS groups of
+// chunks per warp (a group: one chunk, or a pair): each warp starts with
+// group `warp`, then takes the item's next group from a shared counter, so
+// a warp that finishes early takes more and the CTA waits for the slowest
+// warp once per item, not once per group.
+template <int W, bool PAIR, uint32_t ROUNDS>
 __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasPerSm)
     batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
     constexpr uint32_t kPer = PAIR ? dec::kChains : 1u;
+    constexpr uint32_t kItem = W * kPer * ROUNDS;  // chunks in a CTA item
     extern __shared__ __align__(128) uint8_t smem[];
     const dec::Smem sm = dec::smem_layout<W>(smem);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -207,6 +212,7 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
     uint32_t &const_sym = sm.misc[3];
     uint32_t &model_ok = sm.misc[4];
     uint32_t &hdr_ok = sm.misc[5];
+    uint32_t &next_group = sm.misc[6];  // the current item's next group to take
     if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
     dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t lt = lanemask_lt();
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
         if (threadIdx.x == 0) {
             const uint32_t it = atomicAdd(p.counter, 1u);
             item_s = it;
+            next_group = W;
             if (it < total) {
                 const uint32_t lo = item_stream(p.prefix, p.n_streams, it);
                 stream_s = lo;
@@ -250,8 +257,11 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
             continue;
         }
         const StreamGeom g = check_stream(d, p.n_tables);
-        const uint32_t c = (it - p.prefix[s]) * (W * kPer) + kPer * warp;
-        if (c < g.n_chunks && !wr.timeouts) {
+        const uint32_t c0 = (it - p.prefix[s]) * kItem;
+        const uint32_t c_end = uint32_t(umin64(g.n_chunks, uint64_t(c0) + kItem));
+        for (uint32_t grp = warp;;) {
+            const uint32_t c = c0 + kPer * grp;
+            if (c >= c_end || wr.timeouts) break;
             const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
@@ -267,6 +277,10 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
                                                        d.chunk_symbols, d.n_lanes, d.symbols, cs,
                                                        lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);
+            if (ROUNDS == 1) break;
+            uint32_t nxt = 0;
+            if (lane == 0) nxt = atomicAdd(&next_group, 1u);
+            grp = __shfl_sync(kFull, nxt, 0);
         }
     }
 
@@ -614,16 +628,17 @@ using namespace rans;
 namespace rans {
 namespace {
 
-// The batched decoder's CTA shape: 8 warps, two chunks side by side in each
-// (items of 16 chunks).
+// The batched decoder's CTA shape: 8 warps, two chunks side by side in each;
+// CTA items of kBatchRounds pairs per warp.
 constexpr int kBatchWarps = 8;
 constexpr bool kBatchPair = true;
+constexpr uint32_t kBatchRounds = 1;
 
-template <int W, bool PAIR>
+template <int W, bool PAIR, uint32_t ROUNDS>
 int launch_batch_decode(BatchDecodeParams &p, cudaStream_t st) {
     using S = dec::Shape<W>;
-    auto kern = batch_decode_kernel<W, PAIR>;
-    p.item_chunks = W * (PAIR ? dec::kChains : 1u);
+    auto kern = batch_decode_kernel<W, PAIR, ROUNDS>;
+    p.item_chunks = W * (PAIR ? dec::kChains : 1u) * ROUNDS;
     // Set once per device; concurrent first calls may both set it (harmless).
     static std::atomic<bool> configured[64];
     int dev = 0;
@@ -671,7 +686,8 @@ extern "C" int rans_decode_batch(const rans_stream *d_streams, uint32_t n_stream
     p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
     p.n_streams = n_streams;
     p.n_tables = n_tables;
-    return launch_batch_decode<kBatchWarps, kBatchPair>(p, reinterpret_cast<cudaStream_t>(stream));
+    return launch_batch_decode<kBatchWarps, kBatchPair, kBatchRounds>(
+        p, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" uint64_t rans_encode_batch_plan(rans_encode_stream *h_streams, uint32_t n_streams) {
