@@ -400,10 +400,23 @@ def workload_config(name, world, n_symbols=None):
 # Batched leg: 10,000 streams of uneven size, one model each
 # ---------------------------------------------------------------------------
 
+# A spin of about 0.1 ms queued before each timed call: the stream is then
+# busy while the host enqueues the call, so the device time between the two
+# events is the call's own, not the host's launch latency as well.
+SPIN_CYCLES = 200_000
+
+
 def _events(torch, fn, reps, stream=None):
+    """Device time (ms) of each of reps calls of fn, between CUDA events
+    recorded on the stream fn launches on (the current stream by default)."""
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if stream is None:
+            torch.cuda._sleep(SPIN_CYCLES)
+        else:
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(SPIN_CYCLES)
         a.record(stream)
         fn()
         b.record(stream)

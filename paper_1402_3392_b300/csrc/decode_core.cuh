@@ -523,8 +523,9 @@ __device__ __forceinline__ void chain_open_prefix(Chain &c, const uint8_t *msg, 
 // Open chunk [o, e) (byte offsets in the data region that starts at msg +
 // data0; data_end = end of all chunks) of n_c symbols with N coders, output
 // at out.  Reads the N initial states; a malformed chunk gets c.st set and no
-// steps.
-template <class G, bool BYTES = false>
+// steps.  UNI: the read position is made visibly warp-uniform (warp_uniform),
+// so that its updates leave the vector pipes.
+template <class G, bool BYTES = false, bool UNI = false>
 __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
                                            uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,
                                            uint8_t *out, uint16_t *raw_out, uint32_t lane) {
@@ -549,7 +550,7 @@ __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_
     c.span = uint32_t(round16(P1) - A);
     c.nseg = (c.span + G::kSeg - 1) / G::kSeg;
     c.endrel = uint32_t(P1 - A);
-    c.rp = uint32_t(P0 - A);
+    c.rp = UNI ? warp_uniform(uint32_t(P0 - A)) : uint32_t(P0 - A);
     c.rp0 = c.rp;
     c.len = e - o;
     c.next_evt = 0;
@@ -1029,9 +1030,10 @@ __device__ __forceinline__ uint32_t const_chunk_raw(const uint8_t *msg, uint32_t
 // interleaved; otherwise one chunk in the warp's 4 KiB ring.  RAW: a bypass
 // message (one chunk per warp); symbol i's raw word, or 0, goes to
 // raw_out[i] and flags_s addresses the 256 raw-word flags.  const_sym !=
-// kNoConst: the model has one symbol with f = M.  Returns the warp-uniform
-// status (RANS_OK, or the first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
-template <int NT, bool PAIR, int KIND = kKindPlain>  // NT = 32: all lanes are coders
+// kNoConst: the model has one symbol with f = M.  UNI: chain_open's UNI (the
+// batched decoder's form).  Returns the warp-uniform status (RANS_OK, or the
+// first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
+template <int NT, bool PAIR, int KIND = kKindPlain, bool UNI = false>  // NT = 32: all lanes are coders
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
@@ -1079,9 +1081,11 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     if (PREFIX)
         chain_open_prefix<G>(a, msg, data0, o0, o1, data_end, n_a, N, out + first, lane);
     else
-        chain_open<G, BYTES>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
-                             RAW ? raw_out + first : nullptr, lane);
-    if (two) chain_open<G>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS, nullptr, lane);
+        chain_open<G, BYTES, UNI>(a, msg, data0, o0, o1, data_end, n_a, N, out + first,
+                                  RAW ? raw_out + first : nullptr, lane);
+    if (two)
+        chain_open<G, false, UNI>(b, msg, data0, o1, o2, data_end, n_b, N, out + first + CS,
+                                  nullptr, lane);
     else chain_empty(b);
     if (ADAPTN) {  // flags_s: the alphabet size n
         adapt::init<AdaptN<KIND>::kNB>(a.cm, flags_s);

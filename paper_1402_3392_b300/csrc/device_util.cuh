@@ -36,6 +36,14 @@ __device__ __forceinline__ uint32_t lane_id() {
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
+// v, a value every lane of the (full) warp holds, returned through a warp
+// reduction, whose result the compiler keeps in a uniform register: work
+// derived from it alone (a read position advanced by a ballot's count) then
+// runs on the uniform datapath instead of the vector pipes.
+__device__ __forceinline__ uint32_t warp_uniform(uint32_t v) {
+    return __reduce_or_sync(kFull, v);
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

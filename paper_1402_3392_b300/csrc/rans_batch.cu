@@ -192,20 +192,21 @@ __device__ __forceinline__ uint32_t item_stream(const uint32_t *prefix, uint32_t
     return lo;
 }
 
-// Bounded for the shape's resident CTAs per SM (8 warps: 4, at most 64
-// registers; 12 warps: 3, at most 56).  A CTA item holds ROUNDS groups of
-// chunks per warp (a group: one chunk, or a pair): each warp starts with
-// group `warp`, then takes the item's next group from a shared counter, so
-// a warp that finishes early takes more and the CTA waits for the slowest
-// warp once per item, not once per group.
+// Phase 1 of the batched decoder: CTA items (chunks of table-model streams).
+// A CTA item holds ROUNDS groups of chunks per warp (a group: one chunk, or a
+// pair): each warp starts with group `warp`, then takes the item's next
+// group from a shared counter, so a warp that finishes early takes more and
+// the CTA waits for the slowest warp once per item, not once per group.
+// Ring addresses and read positions are made visibly warp-uniform here
+// (warp_uniform, chain_open's UNI), so that the read-position updates run on
+// the uniform datapath.  Returns wr with the rings' state (barrier phases,
+// timeouts) after the phase.
 template <int W, bool PAIR, uint32_t ROUNDS>
-__global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasPerSm)
-    batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
+__device__ __forceinline__ dec::WarpRings batch_cta_items(const BatchDecodeParams &p,
+                                                          const dec::Smem &sm, dec::WarpRings wr,
+                                                          uint32_t lane, uint32_t warp) {
     constexpr uint32_t kPer = PAIR ? dec::kChains : 1u;
     constexpr uint32_t kItem = W * kPer * ROUNDS;  // chunks in a CTA item
-    extern __shared__ __align__(128) uint8_t smem[];
-    const dec::Smem sm = dec::smem_layout<W>(smem);
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t &item_s = sm.misc[0];
     uint32_t &stream_s = sm.misc[1];
     uint32_t &loaded = sm.misc[2];      // model whose slot table is in shared memory
@@ -213,11 +214,11 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
     uint32_t &model_ok = sm.misc[4];
     uint32_t &hdr_ok = sm.misc[5];
     uint32_t &next_group = sm.misc[6];  // the current item's next group to take
-    if (threadIdx.x == 0) loaded = 0xFFFFFFFFu;
-    dec::WarpRings wr = dec::rings_init(sm, warp, lane);
     const uint32_t lt = lanemask_lt();
     const uint32_t total = p.prefix[p.n_streams];
-
+    dec::WarpRings wa = wr;
+#pragma unroll
+    for (uint32_t k = 0; k < dec::kChains; ++k) wa.r[k].ring_s = warp_uniform(wr.r[k].ring_s);
     for (;;) {
         __syncthreads();  // every warp is done with the previous item
         if (threadIdx.x == 0) {
@@ -261,21 +262,19 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
         const uint32_t c_end = uint32_t(umin64(g.n_chunks, uint64_t(c0) + kItem));
         for (uint32_t grp = warp;;) {
             const uint32_t c = c0 + kPer * grp;
-            if (c >= c_end || wr.timeouts) break;
+            if (c >= c_end || wa.timeouts) break;
             const uint32_t *offs = reinterpret_cast<const uint32_t *>(d.msg + 32);
             const uint32_t data_end = offs[g.n_chunks];
             const uint32_t cs = const_sym;
             const uint32_t count = uint32_t(umin64(kPer, g.n_chunks - c));
             const uint32_t st =
                 d.n_lanes == 32
-                         ? dec::decode_chunks<32, PAIR>(wr, sm.tab_s, d.msg, g.data0, offs,
-                                                        data_end, c, count, d.n_symbols,
-                                                        d.chunk_symbols, 32, d.symbols, cs, lane,
-                                                        lt)
-                         : dec::decode_chunks<0, PAIR>(wr, sm.tab_s, d.msg, g.data0, offs,
-                                                       data_end, c, count, d.n_symbols,
-                                                       d.chunk_symbols, d.n_lanes, d.symbols, cs,
-                                                       lane, lt);
+                         ? dec::decode_chunks<32, PAIR, dec::kKindPlain, true>(
+                               wa, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                               d.n_symbols, d.chunk_symbols, 32, d.symbols, cs, lane, lt)
+                         : dec::decode_chunks<0, PAIR, dec::kKindPlain, true>(
+                               wa, sm.tab_s, d.msg, g.data0, offs, data_end, c, count,
+                               d.n_symbols, d.chunk_symbols, d.n_lanes, d.symbols, cs, lane, lt);
             if (st != RANS_OK && lane == 0) report(p.status + s, st);
             if (ROUNDS == 1) break;
             uint32_t nxt = 0;
@@ -283,8 +282,17 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
             grp = __shfl_sync(kFull, nxt, 0);
         }
     }
+#pragma unroll
+    for (uint32_t k = 0; k < dec::kChains; ++k) wr.r[k].phase = wa.r[k].phase;
+    wr.timeouts = wa.timeouts;
+    return wr;
+}
 
-    // Warp items: chunk pairs of binary-model streams, a warp at a time.
+// Phase 2: warp items, chunk pairs of binary-model streams, a warp at a time
+// (read positions warp-uniform as above).
+__device__ __forceinline__ void batch_warp_items(const BatchDecodeParams &p, dec::WarpRings wr,
+                                                 uint32_t lane) {
+    const uint32_t lt = lanemask_lt();
     const uint32_t wtotal = p.wprefix[p.n_streams];
     for (;;) {
         uint32_t it = 0;
@@ -315,14 +323,36 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
         // f_0 and f_1 ride in the table and flag arguments
         const uint32_t st =
             d.n_lanes == 32
-                ? dec::decode_chunks<32, true, dec::kKindBinary>(
+                ? dec::decode_chunks<32, true, dec::kKindBinary, true>(
                       wr, f0, d.msg, g.data0, offs, data_end, c, count, d.n_symbols,
                       d.chunk_symbols, 32, d.symbols, dec::kNoConst, lane, lt, nullptr, f1)
-                : dec::decode_chunks<0, true, dec::kKindBinary>(
+                : dec::decode_chunks<0, true, dec::kKindBinary, true>(
                       wr, f0, d.msg, g.data0, offs, data_end, c, count, d.n_symbols,
                       d.chunk_symbols, d.n_lanes, d.symbols, dec::kNoConst, lane, lt, nullptr, f1);
         if (st != RANS_OK && lane == 0) report(p.status + s, st);
     }
+}
+
+// The persistent batched decoder: every CTA takes CTA items until none is
+// left, then its warps take warp items.  Bounded for the shape's resident
+// CTAs per SM (8 warps: 4, at most 64 registers; 12 warps: 3, at most 56).
+// Read positions are warp-uniform in both phases, ring addresses in the
+// first only.  Measured on B300 against the kernel with neither (3000
+// streams of the batched workload: 4.270 -> 4.249 ms; the binary workload:
+// 216.5 -> 208.5 us).  Other arrangements moved the two phases against each
+// other, in one kernel or in two: uniform ring addresses in both phases
+// 4.169 ms / 218.5 us, rebuilt for the second 4.164 ms / 216.3 us, the two
+// phases as two kernels 4.261 ms / 213.8 us.
+template <int W, bool PAIR, uint32_t ROUNDS>
+__global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasPerSm)
+    batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const dec::Smem sm = dec::smem_layout<W>(smem);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sm.misc[2] = 0xFFFFFFFFu;  // no slot table loaded yet
+    dec::WarpRings wr = dec::rings_init(sm, warp, lane);
+    wr = batch_cta_items<W, PAIR, ROUNDS>(p, sm, wr, lane, warp);
+    batch_warp_items(p, wr, lane);
 }
 
 

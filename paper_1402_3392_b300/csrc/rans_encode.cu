@@ -124,10 +124,10 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
 
 // Four CTAs per SM (64 registers) for every kind but the 13/14-bit models,
 // whose 16-byte table entries need more registers than that (two or three
-// CTAs per SM).  The plain 32-coder kernel stays within 64 registers
-// without asking (asking made the compiler spill one); the others need the
-// bound.  A bound of one CTA per SM, asked for explicitly, let the compiler
-// spend more registers and cost a CTA per SM.
+// CTAs per SM), and the plain 32-coder kernel: left unbounded it takes 80
+// registers (three CTAs per SM) for its two register sets of prefetched
+// symbols, and ran faster so than held to 64 with spills (measured on B300,
+// 1 GiB: 1246 against 1257 us).  The others need the bound.
 template <int NT, int KIND, bool PLACE>
 __global__ void __launch_bounds__(enc::kThreads, KIND == kPlain && NT == 32 ? 0 : 4)
     encode_kernel(const __grid_constant__ EncodeParams p) {
