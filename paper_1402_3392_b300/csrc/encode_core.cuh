@@ -157,6 +157,13 @@ __device__ __forceinline__ uint32_t div_float(uint32_t x, uint32_t f, uint32_t &
 // sum of the frequencies to every thread.
 // raw_words (bypass messages, may be null): symbol s carries raw_words[s]
 // (0 or 1) raw words; marked by kRawFlag in .y.
+__device__ __forceinline__ uint2 encode_entry(uint32_t f, uint32_t B) {
+    uint2 t;
+    uint32_t k;
+    reciprocal(f, t.x, k);
+    t.y = ((kM - (f & (2 * kM - 1))) << 20) | (k << 12) | (B & (kM - 1));
+    return t;
+}
 __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq, uint2 *tab,
                                                            uint32_t *cum,
                                                            const uint8_t *raw_words = nullptr) {
@@ -186,9 +193,7 @@ __device__ __noinline__ static uint32_t build_encode_table(const uint16_t *freq,
         if (f == 0) {
             t = make_uint2(0u, kZeroFlag);  // never emits, leaves x unchanged
         } else {
-            uint32_t k;
-            reciprocal(f, t.x, k);
-            t.y = ((kM - (f & (2 * kM - 1))) << 20) | (k << 12) | (cum[s] & (kM - 1));
+            t = encode_entry(f, cum[s]);
             if (raw_words && raw_words[s]) t.y |= kRawFlag;  // the shift uses k's 5 bits only
         }
         tab[s] = t;
@@ -294,16 +299,13 @@ __device__ __forceinline__ uint32_t store_at(uint32_t wp, uint32_t k, uint32_t r
     return RING ? ((wp - 2u * k) & (RING - 1)) | ring_s : imad_u32(k, 0u - 2u, wp);
 }
 
-// Encode one step: renormalize (emit the low 16 bits if x >= f_s * 2^20), then
-// x = C(s, x).  wp is the warp-uniform write position (bytes, counting down);
-// ring_s is the warp's 4 KiB-aligned ring.
-template <bool FULL, uint32_t RING = kRing>
-__device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
-                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
-                                            uint32_t ge) {
-    const uint2 t = ld_enc_table(tab_s + (s << 3));
-    const bool on = FULL || active;
-    if (on) acc |= t.y;
+// Encode one step with the symbol's table entry t (lanes with on set):
+// renormalize (emit the low 16 bits if x >= f_s * 2^20), then x = C(s, x).
+// wp is the warp-uniform write position (bytes, counting down); ring_s is
+// the warp's 4 KiB-aligned ring.
+template <bool FULL, uint32_t RING>
+__device__ __forceinline__ void encode_with(uint32_t &x, uint32_t &wp, bool on, uint2 t,
+                                            uint32_t ring_s, uint32_t ge) {
     const bool emit = on && (x > ~(t.y & 0xFFF00000u));
     const uint32_t m = __ballot_sync(kFull, emit);
     st_ring_u16_if(emit, store_at<RING>(wp, __popc(m & ge), ring_s), x);
@@ -311,10 +313,33 @@ __device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t 
     if (RING) wp -= 2u * __popc(m);
     else wp = imad_u32(__popc(m), 0u - 2u, wp);
     if (on) {
-        // floor(x / f) = (x + umulhi(x, m_lo)) >> k with a 33-bit sum
-        const uint32_t q = div_reciprocal(x, t.x, t.y >> 12);
+        const uint32_t q = div_reciprocal(x, t.x, t.y >> 12);  // floor(x / f_s)
         x = x + q * (t.y >> 20) + (t.y & 0xFFFu);
     }
+}
+// The step with the entry from the shared-memory table (acc collects the
+// entries' flags).
+template <bool FULL, uint32_t RING = kRing>
+__device__ __forceinline__ void encode_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
+                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
+                                            uint32_t ge) {
+    const uint2 t = ld_enc_table(tab_s + (s << 3));
+    const bool on = FULL || active;
+    if (on) acc |= t.y;
+    encode_with<FULL, RING>(x, wp, on, t, ring_s, ge);
+}
+// The step with a binary model (f_0 + f_1 = M, both > 0; rABS, Section 2):
+// the entries of symbols 0 and 1 (encode_entry) are held in registers and
+// selected by the symbol, no table.  acc collects the symbols: above 1, one
+// the model does not have.
+template <bool FULL, uint32_t RING = kRing>
+__device__ __forceinline__ void encode_step_binary(uint32_t &x, uint32_t &wp, uint32_t &acc,
+                                                   bool active, uint32_t s, uint2 e0, uint2 e1,
+                                                   uint32_t ring_s, uint32_t ge) {
+    const bool on = FULL || active;
+    if (on) acc |= s;
+    const uint2 t = s ? e1 : e0;
+    encode_with<FULL, RING>(x, wp, on, t, ring_s, ge);
 }
 
 // One step with a wide model: as encode_step with the 16-byte entry.
@@ -509,15 +534,16 @@ __device__ __forceinline__ void encode_step_adaptive(uint32_t &x, uint32_t &wp, 
     }
 }
 
-// The step of a chunk of the byte-wise, wide or plain kind.
-// RING = 0 (plain and wide chunks only): wp is an absolute shared address
-// (store_at).
-template <bool FULL, bool BYTES, bool WIDE, uint32_t RING = kRing>
+// The step of a chunk of the byte-wise, wide, binary or plain kind.
+// RING = 0 (plain, binary and wide chunks only): wp is an absolute shared
+// address (store_at).  e0, e1: a binary model's entries.
+template <bool FULL, bool BYTES, bool WIDE, uint32_t RING = kRing, bool BINARY = false>
 __device__ __forceinline__ void coded_step(uint32_t &x, uint32_t &wp, uint32_t &acc, bool active,
                                            uint32_t s, uint32_t tab_s, uint32_t ring_s,
-                                           uint32_t ge) {
+                                           uint32_t ge, uint2 e0 = {}, uint2 e1 = {}) {
     static_assert(RING || !BYTES, "byte-wise steps address the ring by offset");
-    if (BYTES) encode_step_bytes<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
+    if (BINARY) encode_step_binary<FULL, RING>(x, wp, acc, active, s, e0, e1, ring_s, ge);
+    else if (BYTES) encode_step_bytes<FULL>(x, wp, acc, active, s, tab_s, ring_s, ge);
     else if (WIDE) encode_step_wide<FULL, RING>(x, wp, acc, active, s, tab_s, ring_s, ge);
     else encode_step<FULL, RING>(x, wp, acc, active, s, tab_s, ring_s, ge);
 }
@@ -574,16 +600,21 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // BYTES: a byte-wise chunk (at most 2 bytes per symbol, size padded to 4).
 // ADAPT: an adaptive chunk; ctx holds the chunk's words from adaptive_forward.
 // WIDE: a wide model's 16-byte table entries (encode_step_wide).
+// BINARY: a binary model whose symbols' entries are e0 and e1 (no table; acc
+// then collects the symbols themselves).
 template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false,
-          bool WIDE = false, bool ADAPTN = false>
+          bool WIDE = false, bool ADAPTN = false, bool BINARY = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
                                              uint32_t tab_s, uint32_t ring_s, uint32_t ge,
                                              uint32_t lane, uint32_t &acc,
                                              const uint16_t *raw = nullptr,
-                                             const uint32_t *ctx = nullptr) {
+                                             const uint32_t *ctx = nullptr, uint2 e0 = {},
+                                             uint2 e1 = {}) {
     static_assert(!((RAW || ADAPT || ADAPTN) && PREFETCH), "these chunks load each group up front");
+    static_assert(!(BINARY && (RAW || BYTES || ADAPT || WIDE || ADAPTN || PREFETCH)),
+                  "binary chunks are plain and load each group up front");
     constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
@@ -635,7 +666,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = act ? rawp[uint64_t(T_full) * N] : 0u;
             encode_step_raw<false>(x, wp, acc, act, s, rw, tab_s, ring_s, ge);
         } else {
-            coded_step<false, BYTES, WIDE>(x, wp, acc, act, s, tab_s, ring_s, ge);
+            coded_step<false, BYTES, WIDE, kRing, BINARY>(x, wp, acc, act, s, tab_s, ring_s, ge, e0,
+                                                             e1);
         }
     }
     int64_t t = int64_t(T_full) - 1;
@@ -652,7 +684,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             const uint32_t rw = lane_on ? rawp[uint64_t(t) * N] : 0u;
             encode_step_raw<NT == 32>(x, wp, acc, lane_on, s, rw, tab_s, ring_s, ge);
         } else {
-            coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, s, tab_s, ring_s, ge);
+            coded_step<NT == 32, BYTES, WIDE, kRing, BINARY>(x, wp, acc, lane_on, s, tab_s, ring_s,
+                                                                  ge, e0, e1);
         }
     }
     if (ADAPTN) {
@@ -694,6 +727,28 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                                                (v & 1u) ? pv[v >> 1] >> 16 : pv[v >> 1] & 0xFFFFu,
                                                ring_s, ge);
             }
+        }
+    } else if (PREFETCH && (BYTES || WIDE)) {
+        // Groups of kGroup steps, symbols of the next group loaded ahead and
+        // copied over at the group's end (the two-set form below took more
+        // registers here: byte-wise chunks spilled at their 64, 13/14-bit
+        // ones went from 94 to 108 and three CTAs per SM to two).
+        uint32_t cur[kGroup], nxt[kGroup];
+        if (t >= 0) {
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
+        }
+        for (; t >= 0; t -= kGroup) {
+            const int64_t tn = t - int64_t(kGroup);
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u)
+                nxt[u] = (tn >= 0 && lane_on) ? symp[uint64_t(tn - u) * N] : 0u;
+            service();
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u)
+                coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge);
+#pragma unroll
+            for (uint32_t u = 0; u < kGroup; ++u) cur[u] = nxt[u];
         }
     } else if (PREFETCH) {
         // Groups of kGroup steps, symbols of the next group loaded ahead
@@ -738,8 +793,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                 uint32_t wa = a0;
 #pragma unroll
                 for (uint32_t u = 0; u < kG; ++u)
-                    coded_step<NT == 32, BYTES, WIDE, (RAW || BYTES ? kRing : 0u)>(
-                        x, wa, acc, lane_on, cur[u], tab_s, ring_s, ge);
+                    coded_step<NT == 32, BYTES, WIDE, (RAW || BYTES ? kRing : 0u), BINARY>(
+                        x, wa, acc, lane_on, cur[u], tab_s, ring_s, ge, e0, e1);
                 wp -= a0 - wa;
             } else {
 #pragma unroll
@@ -748,8 +803,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                         encode_step_raw<NT == 32>(x, wp, acc, lane_on, cur[u], curw[u], tab_s,
                                                   ring_s, ge);
                     else
-                        coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, cur[u], tab_s,
-                                                          ring_s, ge);
+                        coded_step<NT == 32, BYTES, WIDE, kRing, BINARY>(
+                            x, wp, acc, lane_on, cur[u], tab_s, ring_s, ge, e0, e1);
                 }
             }
         }

@@ -361,13 +361,13 @@ __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasP
 // ---------------------------------------------------------------------------
 
 struct EncBatchLayout {
-    uint64_t items, chunks, counter, total;
+    uint64_t items, witems, counter, total;
 };
 __host__ __device__ inline EncBatchLayout enc_batch_layout(uint32_t n) {
     EncBatchLayout l{};
     const uint64_t arr = (4ull * (uint64_t(n) + 1) + 15) & ~uint64_t(15);
     l.items = 0;
-    l.chunks = arr;
+    l.witems = arr;
     l.counter = 2 * arr;
     l.total = l.counter + 16;
     return l;
@@ -380,9 +380,9 @@ struct BatchEncodeParams {
     uint32_t *status;
     uint8_t *scratch;
     uint64_t scratch_cap;
-    uint32_t *items;    // n_streams + 1 work-item offsets
-    uint32_t *chunks;   // n_streams + 1 chunk offsets (the batch's chunk count at the end)
-    uint32_t *counter;
+    uint32_t *items;    // n_streams + 1 CTA-item offsets
+    uint32_t *witems;   // n_streams + 1 warp-item offsets (chunks of binary-model streams)
+    uint32_t *counter;  // [0] next CTA item, [1] next warp item
     uint32_t n_streams;
     uint32_t n_tables;
 };
@@ -417,7 +417,9 @@ __device__ __forceinline__ EncGeom check_enc_stream(const rans_encode_stream &d,
     return g;
 }
 
-// One CTA: statuses, work-item and chunk prefixes, counter.
+// One CTA: statuses, CTA-item and warp-item prefixes, counters.  A stream
+// whose model passes binary_candidate is coded by single warps, one chunk a
+// warp item; any other in CTA items of kWarps chunks.
 __global__ void __launch_bounds__(kSetupThreads)
     enc_setup_kernel(const __grid_constant__ BatchEncodeParams p) {
     __shared__ uint32_t sums[2][32];
@@ -432,10 +434,10 @@ __global__ void __launch_bounds__(kSetupThreads)
             const EncGeom g = check_enc_stream(p.streams[i], p.n_tables, p.scratch_cap);
             p.status[i] = g.ok ? RANS_OK : RANS_ERR_INVALID_ARG;
             p.out_sizes[i] = 0;
-            if (g.ok) {
-                v[0] = uint32_t((g.n_chunks + enc::kWarps - 1) / enc::kWarps);
+            if (g.ok && binary_candidate(p.freqs + uint64_t(p.streams[i].table) * 256))
                 v[1] = uint32_t(g.n_chunks);
-            }
+            else if (g.ok)
+                v[0] = uint32_t((g.n_chunks + enc::kWarps - 1) / enc::kWarps);
         }
         uint32_t incl[2] = {v[0], v[1]};
 #pragma unroll
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(kSetupThreads)
         const uint32_t c0 = carry_s[0], c1 = carry_s[1];
         if (i < p.n_streams) {
             p.items[i] = c0 + sums[0][warp] + incl[0] - v[0];
-            p.chunks[i] = c1 + sums[1][warp] + incl[1] - v[1];
+            p.witems[i] = c1 + sums[1][warp] + incl[1] - v[1];
         }
         __syncthreads();
         if (tid == kSetupThreads - 1) {
@@ -476,8 +478,8 @@ __global__ void __launch_bounds__(kSetupThreads)
     }
     if (tid == 0) {
         p.items[p.n_streams] = carry_s[0];
-        p.chunks[p.n_streams] = carry_s[1];
-        *p.counter = 0;
+        p.witems[p.n_streams] = carry_s[1];
+        p.counter[0] = p.counter[1] = 0;
     }
 }
 
@@ -566,10 +568,15 @@ __global__ void __launch_bounds__(kClearThreads)
     }
 }
 
-// Persistent: CTAs take work items (8 chunks of one stream, one per warp) in
-// order from a counter.  Each warp codes its chunk, publishes the chunk's
-// size, and places it after its next item (the last one at the end),
-// waiting only for chunks taken earlier.
+// Persistent: CTAs take CTA items (8 chunks of one stream, one per warp) in
+// order from a counter; when none is left, warps take warp items (one chunk
+// of a binary-model stream each) in order from a second counter.  Each warp
+// codes its chunk, publishes the chunk's size, and places it after its next
+// item (the last one at the end), waiting only for chunks taken earlier.
+// A binary stream's chunk needs no table: the model's two entries are built
+// in registers per item, and no warp of a CTA waits for another (its chunks
+// of 16 Ki symbols left half the warps of an 8-chunk CTA item idle, the
+// workload's streams having 4).
 __global__ void __launch_bounds__(enc::kThreads, 4)
     batch_encode_kernel(const __grid_constant__ BatchEncodeParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -645,6 +652,53 @@ __global__ void __launch_bounds__(enc::kThreads, 4)
             pend_s = s;
             pend_c = c;
         }
+    }
+
+    const uint32_t wtotal = p.witems[p.n_streams];
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(p.counter + 1, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= wtotal) break;
+        const uint32_t s = item_stream_warp(p.witems, p.n_streams, it, lane);
+        const rans_encode_stream d = p.streams[s];
+        const EncGeom g = check_enc_stream(d, p.n_tables, p.scratch_cap);
+        const uint32_t c = it - p.witems[s];
+        uint8_t *scr = p.scratch + d.scratch_offset;
+        // the whole model: f_0 + f_1 = M (binary_candidate) leaves no room
+        // for another symbol in a valid table
+        const uint16_t *fr = p.freqs + uint64_t(d.table) * 256;
+        uint32_t part = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) part += fr[lane * 8 + k];
+        if (__reduce_add_sync(kFull, part) != kM) {
+            if (lane == 0) report(p.status + s, RANS_ERR_INVALID_ARG);
+            enc::publish_failed(
+                enc::scratch_lookback(scr, g.sl, uint32_t(g.n_chunks), d.chunk_symbols, d.n_lanes),
+                c, lane);
+            continue;
+        }
+        const uint32_t f0 = fr[0];
+        const uint2 e0 = enc::encode_entry(f0, 0u), e1 = enc::encode_entry(fr[1], f0);
+        const uint64_t first = uint64_t(c) * d.chunk_symbols;
+        const uint32_t n_c = uint32_t(umin64(d.chunk_symbols, d.n_symbols - first));
+        uint32_t acc = 0;
+        uint8_t *slot = scr + g.sl.words + uint64_t(c) * g.sl.slot_bytes;
+        uint32_t *wstart = reinterpret_cast<uint32_t *>(scr + g.sl.wstart) + c;
+        uint32_t *sizes = reinterpret_cast<uint32_t *>(scr + g.sl.sizes) + c;
+        uint32_t *states = reinterpret_cast<uint32_t *>(scr + g.sl.states) + uint64_t(c) * d.n_lanes;
+        if (d.n_lanes == 32)
+            enc::encode_chunk<32, false, false, false, false, false, false, true>(
+                d.symbols + first, n_c, 32, slot, g.sl.slot_bytes, wstart, sizes, states, 0u,
+                ring_s, ge, lane, acc, nullptr, nullptr, e0, e1);
+        else
+            enc::encode_chunk<0, false, false, false, false, false, false, true>(
+                d.symbols + first, n_c, d.n_lanes, slot, g.sl.slot_bytes, wstart, sizes, states, 0u,
+                ring_s, ge, lane, acc, nullptr, nullptr, e0, e1);
+        coded(p, s, c, lane, acc > 1u ? enc::kZeroFlag : 0u);  // a symbol outside {0, 1}
+        if (pend_s != kNone) place_pending(p, pend_s, pend_c, lane);
+        pend_s = s;
+        pend_c = c;
     }
     if (pend_s != kNone) place_pending(p, pend_s, pend_c, lane);
     if (lane == 0) bulk_wait<0>();
@@ -754,7 +808,7 @@ extern "C" int rans_encode_batch(const rans_encode_stream *d_streams, uint32_t n
     p.scratch = scr;
     p.scratch_cap = scratch_cap;
     p.items = reinterpret_cast<uint32_t *>(scr + l.items);
-    p.chunks = reinterpret_cast<uint32_t *>(scr + l.chunks);
+    p.witems = reinterpret_cast<uint32_t *>(scr + l.witems);
     p.counter = reinterpret_cast<uint32_t *>(scr + l.counter);
     p.n_streams = n_streams;
     p.n_tables = n_tables;

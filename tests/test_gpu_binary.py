@@ -168,3 +168,48 @@ def test_batched_binary_edge_streams(rlib, orc, cuda):
     assert list(st) == [0, 0, 0, rlib.RANS_ERR_INVALID_ARG, 0, 0]
     for i in (1, 2, 4, 5):
         assert np.array_equal(dec.output(i).cpu().numpy(), syms[i]), i
+
+
+def test_batched_binary_encode_edge_streams(rlib, orc, cuda):
+    """The batched encoder codes binary-model streams as warp items (one
+    chunk a warp, the model's two entries in registers): in one batch with a
+    256-symbol stream, an empty binary stream gets its header-only message,
+    one-chunk and ragged ones the oracle's bytes, a binary-looking table that
+    is not a valid model (f_0 + f_1 = M plus one more symbol) fails alone
+    with RANS_ERR_INVALID_ARG, and a symbol outside {0, 1} in a binary
+    stream with RANS_ERR_ZERO_FREQ (size 0)."""
+    import torch
+
+    rng = np.random.default_rng(229)
+    good = binary_table(2900)
+    bad = np.zeros(256, dtype=np.uint16)
+    bad[0], bad[1], bad[7] = 2900, 1196, 3
+    zipf = rlib.rans_quantize_table(wl.weights_from_probs(wl.zipf_probs(256, 1.1)))
+    tables = [good, bad, zipf]
+    plan = [(0, 0, 32), (0, 5000, 32), (0, 3 * 4096 + 17, 32), (1, 9000, 32), (2, 30_000, 32),
+            (0, 1, 32), (0, 7000, 32), (0, 2 * 4096 + 5, 11)]
+    syms = []
+    for t, n, _ in plan:
+        if t == 2:
+            syms.append(rng.choice(256, size=n, p=zipf / zipf.sum()).astype(np.uint8))
+        else:
+            syms.append(draw(rng, good, n))
+    syms[6][3333] = 2  # not a symbol of the binary model
+    offs, total = B.aligned_offsets([s.size for s in syms])
+    host = np.zeros(max(total, B.ALIGN), dtype=np.uint8)
+    for s, o in zip(syms, offs):
+        host[o:o + s.size] = s
+    eb = B.encode_batch(torch.from_numpy(host).to(cuda), offs, [s.size for s in syms],
+                        B.upload_tables(tables, cuda), [t for t, _, _ in plan],
+                        [n for _, _, n in plan], 4096)
+    torch.cuda.synchronize()
+    st = eb.status.cpu().numpy()
+    want = [0, 0, 0, rlib.RANS_ERR_INVALID_ARG, 0, 0, rlib.RANS_ERR_ZERO_FREQ, 0]
+    assert list(st) == want
+    sizes = eb.host_sizes()
+    for i, (t, _, N) in enumerate(plan):
+        if want[i]:
+            assert sizes[i] == 0, i
+            continue
+        ref = orc.encode_message(syms[i], tables[t], N=N, chunk_symbols=4096)
+        assert np.array_equal(eb.message(i).cpu().numpy(), ref), i
