@@ -523,8 +523,8 @@ __device__ __forceinline__ void chain_open_prefix(Chain &c, const uint8_t *msg, 
 // Open chunk [o, e) (byte offsets in the data region that starts at msg +
 // data0; data_end = end of all chunks) of n_c symbols with N coders, output
 // at out.  Reads the N initial states; a malformed chunk gets c.st set and no
-// steps.  UNI: the read position is made visibly warp-uniform (warp_uniform),
-// so that its updates leave the vector pipes.
+// steps.  UNI: the read position passes through warp_uniform (the batched
+// decoder's form).
 template <class G, bool BYTES = false, bool UNI = false>
 __device__ __forceinline__ void chain_open(Chain &c, const uint8_t *msg, uint32_t data0, uint32_t o,
                                            uint32_t e, uint32_t data_end, uint32_t n_c, uint32_t N,

@@ -197,9 +197,8 @@ __device__ __forceinline__ uint32_t item_stream(const uint32_t *prefix, uint32_t
 // pair): each warp starts with group `warp`, then takes the item's next
 // group from a shared counter, so a warp that finishes early takes more and
 // the CTA waits for the slowest warp once per item, not once per group.
-// Ring addresses and read positions are made visibly warp-uniform here
-// (warp_uniform, chain_open's UNI), so that the read-position updates run on
-// the uniform datapath.  Returns wr with the rings' state (barrier phases,
+// Ring addresses and read positions pass through warp_uniform here
+// (chain_open's UNI).  Returns wr with the rings' state (barrier phases,
 // timeouts) after the phase.
 template <int W, bool PAIR, uint32_t ROUNDS>
 __device__ __forceinline__ dec::WarpRings batch_cta_items(const BatchDecodeParams &p,
@@ -336,13 +335,15 @@ __device__ __forceinline__ void batch_warp_items(const BatchDecodeParams &p, dec
 // The persistent batched decoder: every CTA takes CTA items until none is
 // left, then its warps take warp items.  Bounded for the shape's resident
 // CTAs per SM (8 warps: 4, at most 64 registers; 12 warps: 3, at most 56).
-// Read positions are warp-uniform in both phases, ring addresses in the
-// first only.  Measured on B300 against the kernel with neither (3000
+// Read positions pass through warp_uniform in both phases, ring addresses in
+// the first only.  Measured on B300 against the kernel with neither (3000
 // streams of the batched workload: 4.270 -> 4.249 ms; the binary workload:
-// 216.5 -> 208.5 us).  Other arrangements moved the two phases against each
-// other, in one kernel or in two: uniform ring addresses in both phases
-// 4.169 ms / 218.5 us, rebuilt for the second 4.164 ms / 216.3 us, the two
-// phases as two kernels 4.261 ms / 213.8 us.
+// 216.5 -> 208.5 us, issue 74.5 -> 77.6 % of cycles with the same
+// instructions per opcode in ncu: a scheduling effect, no work moved or
+// removed).  Other arrangements moved the two phases against each other, in
+// one kernel or in two: uniform ring addresses in both phases 4.169 ms /
+// 218.5 us, rebuilt for the second 4.164 ms / 216.3 us, the two phases as
+// two kernels 4.261 ms / 213.8 us.
 template <int W, bool PAIR, uint32_t ROUNDS>
 __global__ void __launch_bounds__(dec::Shape<W>::kThreads, dec::Shape<W>::kCtasPerSm)
     batch_decode_kernel(const __grid_constant__ BatchDecodeParams p) {
