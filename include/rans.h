@@ -646,8 +646,8 @@ int rans_check_lookback_wait(uint32_t *d_status, rans_stream_t stream);
  * of Section 2 (L = b = 2^16), and checks each quotient q against the
  * definition q * f <= x < (q + 1) * f in 64-bit integers.
  *
- * method   : 0 = the multiply-high by the table's reciprocal (static models,
- *            log2m 12, 13 or 14); 1 = the adaptive coder's float estimate and
+ * method   : 0 = the 64-bit multiply-add by the table's reciprocal (static
+ *            models, log2m 12, 13 or 14); 1 = the adaptive coder's float estimate and
  *            one correction (log2m 12; the remainder is checked too).
  * d_result : device, 8-byte aligned, 4 u64, overwritten: [0] states checked,
  *            [1] wrong quotients, [2] the smallest f << 32 | x that was wrong
