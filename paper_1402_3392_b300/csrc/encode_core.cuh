@@ -728,11 +728,12 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
                                                ring_s, ge);
             }
         }
-    } else if (PREFETCH && (BYTES || WIDE)) {
+    } else if (PREFETCH && (BYTES || WIDE || NT != 32)) {
         // Groups of kGroup steps, symbols of the next group loaded ahead and
         // copied over at the group's end (the two-set form below took more
-        // registers here: byte-wise chunks spilled at their 64, 13/14-bit
-        // ones went from 94 to 108 and three CTAs per SM to two).
+        // registers here: byte-wise chunks and plain ones of fewer than 32
+        // coders spilled at their 64, 13/14-bit ones went from 94 to 108 and
+        // three CTAs per SM to two).
         uint32_t cur[kGroup], nxt[kGroup];
         if (t >= 0) {
 #pragma unroll
