@@ -125,6 +125,10 @@ constexpr int kKindBinary = 7;
 // Adaptive models over n symbols, one per coder (version 6, adapt_model.cuh),
 // with register room for 3, 7 or 15 boundaries (n <= 4, 8, 16).
 constexpr int kKindAdaptN4 = 8, kKindAdaptN8 = 9, kKindAdaptN16 = 10;
+// Plain messages decoded with the step's word taken early (decode_step's
+// EARLY form): the plain bitstream, for messages under one wave of chunks,
+// where a warp's chain of dependent steps, not the SM's pipes, sets the pace.
+constexpr int kKindPlainEarly = 11;
 template <int KIND>
 struct AdaptN {
     static constexpr bool kOn = KIND == kKindAdaptN4 || KIND == kKindAdaptN8 || KIND == kKindAdaptN16;
@@ -621,18 +625,27 @@ __device__ __forceinline__ uint32_t word_at(uint32_t rp, uint32_t k, uint32_t ri
 // Decode one step of a chunk: every active lane decodes one symbol and reads
 // at most one word.  FULL: every lane of the warp is a coder with a symbol in
 // this step.  rp: the warp-uniform read position (word_at).
-template <bool FULL, uint32_t RING>
+// EARLY: lane j loads the word at rp + 2j before the table lookup (every
+// word the step can read, within its 64-byte window), and the lane that
+// needs one takes the word of lane popc(m & lt) by a shuffle: the shared
+// load leaves the step's dependent chain, the shuffle takes its place.
+// Measured on B300: one 1 MiB chunk 73.2 -> 70.4 ns a step, but a full GPU
+// 840 -> 880 us on 1 GiB (a second data-pipe wavefront a step), so only the
+// decoder of messages under one wave of chunks uses it.
+template <bool FULL, uint32_t RING, bool EARLY = false>
 __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool active,
                                             uint32_t tab_s, uint32_t ring_s, uint8_t *outp,
                                             uint32_t lt) {
     const uint32_t e = ld_table(imad(x & (kM - 1), 4u, tab_s));
+    const uint32_t wl = EARLY ? ld_ring_u16(word_at<RING>(rp, threadIdx.x & 31u, ring_s)) : 0u;
     if (FULL || active) {
         x = decode_update(x, e);
         *outp = uint8_t(e);
     }
     const bool need = (FULL || active) && x < kL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
+    const uint32_t w = EARLY ? __shfl_sync(kFull, wl, __popc(m & lt))
+                             : ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp = imad(__popc(m), 2u, rp);
 }
@@ -897,7 +910,8 @@ __device__ __forceinline__ void kind_step(Chain &c, bool active, uint32_t tab_s,
     else if (AdaptN<KIND>::kOn)
         decode_step_adaptive_n<FULL, RING, AdaptN<KIND>::kNB>(c, active, ring_s, outp, lt);
     else
-        decode_step<FULL, RING>(c.x, c.rp, active, tab_s, ring_s, outp, lt);
+        decode_step<FULL, RING, KIND == kKindPlainEarly>(c.x, c.rp, active, tab_s, ring_s, outp,
+                                                         lt);
 }
 
 // Decode what is left of one chunk on its own.
@@ -913,7 +927,8 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
         // Measured on B300: 2-3.5 % faster for plain, bypass and byte-wise
         // chunks alone in a warp's ring; no gain for adaptive, prefix and
         // 13/14-bit chunks, and slower for chunk pairs (more code).
-        constexpr bool kLinear = (KIND == kKindPlain || KIND == kKindRaw || KIND == kKindBytes ||
+        constexpr bool kLinear = (KIND == kKindPlain || KIND == kKindPlainEarly ||
+                                  KIND == kKindRaw || KIND == kKindBytes ||
                                   KIND == kKindBinary) &&
                                  G::kRing == kWarpRing;
         if (kLinear && off + G::kGroup * G::kStep <= G::kRing) {

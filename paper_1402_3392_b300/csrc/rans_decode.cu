@@ -45,7 +45,8 @@ constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::k
               kAdaptive = dec::kKindAdaptive, kPrefix = dec::kKindPrefix,
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14,
               kBinary = dec::kKindBinary, kAdaptN4 = dec::kKindAdaptN4,
-              kAdaptN8 = dec::kKindAdaptN8, kAdaptN16 = dec::kKindAdaptN16;
+              kAdaptN8 = dec::kKindAdaptN8, kAdaptN16 = dec::kKindAdaptN16,
+              kPlainEarly = dec::kKindPlainEarly;
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
 // CTA (dec::Shape).  A warp decodes one chunk at a time.
@@ -119,9 +120,9 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
             st = dec::decode_chunks<NT, false, KIND>(wr, p.freq[0], p.msg, p.data0, offs,
                                                      data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
                                                      cs, lane, lt, nullptr, p.freq[1]);
-        else
-            st = dec::decode_chunks<NT, false>(wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1,
-                                               p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
+        else  // plain (KIND kPlain or kPlainEarly)
+            st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
+                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
@@ -184,7 +185,13 @@ int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
 
 // A warp decodes one chunk.  Plain messages under one wave of chunks: 8-warp
 // CTAs, where more resident warps gain nothing and the 64-register form has
-// the shorter step (one 1 MiB chunk: 2.41 against 2.44 ms).  Plain messages
+// the shorter step (one 1 MiB chunk: 2.41 against 2.44 ms); up to half a
+// wave with the early-word step (dec::kKindPlainEarly), whose step is
+// shorter on an SM with few warps and costs a data-pipe wavefront on a full
+// one (measured, µs, committed step against it: 1 chunk 164.7 / 158.8, 1184
+// chunks 171.6 / 167.6, 2368 chunks 192.5 / 189.1, 3552 chunks 220.4 /
+// 221.4, 4700 chunks 267.4 / 270.1; one 1 MiB chunk 73.2 / 70.5 ns a
+// step).  Plain messages
 // of a wave or more, and byte-wise messages: 12-warp CTAs.  The other kinds:
 // 8-warp CTAs (dec::Shape).  Two chunks side by side in a warp of an 8-warp
 // CTA were faster than one per warp in 8-warp CTAs from five waves up; one
@@ -196,6 +203,13 @@ int launch_decode(DecodeParams &p, cudaStream_t stream) {
     if constexpr (KIND == kPlain || KIND == kBinary) {
         const uint64_t cap8 = resident_ctas<NT, KIND, dec::kWarps>();
         if (!cap8) return RANS_ERR_CUDA;
+        if constexpr (KIND == kPlain) {
+            if (2 * n_range <= cap8 * dec::kWarps) {
+                const uint64_t cap_e = resident_ctas<NT, kPlainEarly, dec::kWarps>();
+                if (!cap_e) return RANS_ERR_CUDA;
+                return launch_shape<NT, kPlainEarly, dec::kWarps>(p, cap_e, stream);
+            }
+        }
         if (n_range < cap8 * dec::kWarps)
             return launch_shape<NT, KIND, dec::kWarps>(p, cap8, stream);
     }
