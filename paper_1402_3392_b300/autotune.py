@@ -10,9 +10,10 @@ size), so the choice is made before encoding.  Candidates:
   chunk      : 16, 32, 64, 128, 256 KiB
   per-stream : "fixed" (every stream uses the chunk size) or "fill" (a stream
                shorter than 16 chunks is cut into up to 16 smaller chunks, at
-               least 4 KiB each -- below the 16 KiB of the candidate list --
-               so its one work item keeps all 16 chunk slots of a CTA -- 8
-               warps x 2 chunks -- busy)
+               least 16 KiB each -- the low end of the candidate list, so no
+               chunk but a stream's last is below it -- so that its one work
+               item keeps more of the 16 chunk slots of a CTA -- 8 warps x 2
+               chunks -- busy)
 The score is decoded bytes per second of the batched decoder (median of a few
 runs); ties go to the larger chunk.  The chosen policy and the chunk sizes it
 gives are reported beside the result.
@@ -29,7 +30,7 @@ WIDTHS = (4, 8, 16, 32)
 CHUNKS = (16 << 10, 32 << 10, 64 << 10, 128 << 10, 256 << 10)
 POLICIES = ("fixed", "fill")
 ITEM_CHUNKS = 16       # chunks in one work item of the batched decoder
-MIN_FILL_CHUNK = 4096
+MIN_FILL_CHUNK = CHUNKS[0]
 
 
 def chunk_sizes(n_symbols, chunk, policy):
