@@ -303,10 +303,23 @@ __device__ __forceinline__ uint32_t store_at(uint32_t wp, uint32_t k, uint32_t r
 // renormalize (emit the low 16 bits if x >= f_s * 2^20), then x = C(s, x).
 // wp is the warp-uniform write position (bytes, counting down); ring_s is
 // the warp's 4 KiB-aligned ring.
-template <bool FULL, uint32_t RING>
+// XFIRST: the new state is computed before the ballot and the word's store
+// (the latency form, encode_chunk's LAT).
+template <bool FULL, uint32_t RING, bool XFIRST = false>
 __device__ __forceinline__ void encode_with(uint32_t &x, uint32_t &wp, bool on, uint2 t,
                                             uint32_t ring_s, uint32_t ge) {
     const bool emit = on && (x > ~(t.y & 0xFFF00000u));
+    if constexpr (XFIRST) {
+        const uint32_t xs = emit ? x >> 16 : x;
+        const uint32_t q = div_reciprocal(xs, t.x, t.y >> 12);  // floor(x / f_s)
+        const uint32_t xn = on ? xs + q * (t.y >> 20) + (t.y & 0xFFFu) : x;
+        const uint32_t m = __ballot_sync(kFull, emit);
+        st_ring_u16_if(emit, store_at<RING>(wp, __popc(m & ge), ring_s), x);
+        if (RING) wp -= 2u * __popc(m);
+        else wp = imad_u32(__popc(m), 0u - 2u, wp);
+        x = xn;
+        return;
+    }
     const uint32_t m = __ballot_sync(kFull, emit);
     st_ring_u16_if(emit, store_at<RING>(wp, __popc(m & ge), ring_s), x);
     x = emit ? x >> 16 : x;
@@ -602,8 +615,18 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // WIDE: a wide model's 16-byte table entries (encode_step_wide).
 // BINARY: a binary model whose symbols' entries are e0 and e1 (no table; acc
 // then collects the symbols themselves).
+// LAT (plain chunks of 32 coders with PREFETCH): the form for warps whose
+// chain of dependent steps sets the pace, on an SM with few of them: each
+// step's table entry is loaded during the step before, and the new state is
+// computed ahead of the ballot and the word's store (encode_with's XFIRST).
+// Measured on B300, against the form below: one 1 MiB chunk 1991 -> 1347 us,
+// 592 chunks of 64 Ki symbols 190.6 -> 156.5 us, but one wave (3552 chunks)
+// 319.0 -> 327.2 us and 1 GiB 1236 -> 1283 us (the launcher's choice:
+// rans_encode.cu kLatMaxChunks).  Either form alone gains nothing (1 MiB
+// chunk: 1985 -> 1948 us with the early table loads, 1988 -> 2000 us with
+// the state first).
 template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false,
-          bool WIDE = false, bool ADAPTN = false, bool BINARY = false>
+          bool WIDE = false, bool ADAPTN = false, bool BINARY = false, bool LAT = false>
 __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, uint32_t N_rt,
                                              uint8_t *slot_base, uint32_t slot_bytes,
                                              uint32_t *wstart, uint32_t *size, uint32_t *states,
@@ -615,6 +638,8 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
     static_assert(!((RAW || ADAPT || ADAPTN) && PREFETCH), "these chunks load each group up front");
     static_assert(!(BINARY && (RAW || BYTES || ADAPT || WIDE || ADAPTN || PREFETCH)),
                   "binary chunks are plain and load each group up front");
+    static_assert(!LAT || (PREFETCH && NT == 32 && !RAW && !BYTES && !ADAPT && !WIDE && !ADAPTN),
+                  "the latency form is for plain chunks of 32 coders");
     constexpr uint32_t kG = RAW ? kGroup / 2 : kGroup;
     const uint32_t N = NT ? NT : N_rt;
     const uint8_t *symp = sym + lane;
@@ -765,9 +790,20 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         };
         auto code = [&](const uint32_t(&c)[kGroup]) {
             service();
+            if constexpr (LAT) {
+                uint2 tn = ld_enc_table(tab_s + (c[0] << 3));
 #pragma unroll
-            for (uint32_t u = 0; u < kGroup; ++u)
-                coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, c[u], tab_s, ring_s, ge);
+                for (uint32_t u = 0; u < kGroup; ++u) {
+                    const uint2 t = tn;
+                    if (u + 1 < kGroup) tn = ld_enc_table(tab_s + (c[u + 1] << 3));
+                    acc |= t.y;
+                    encode_with<true, kRing, true>(x, wp, true, t, ring_s, ge);
+                }
+            } else {
+#pragma unroll
+                for (uint32_t u = 0; u < kGroup; ++u)
+                    coded_step<NT == 32, BYTES, WIDE>(x, wp, acc, lane_on, c[u], tab_s, ring_s, ge);
+            }
         };
         load(sa, t);
         while (t >= 0) {

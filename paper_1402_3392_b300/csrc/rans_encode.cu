@@ -71,7 +71,9 @@ __device__ __forceinline__ uint32_t next_chunk(const EncodeParams &p, uint32_t c
     return p.c_begin + __shfl_sync(kFull, t, 0);
 }
 
-template <int NT, int KIND, bool PLACE = false>
+// LAT: encode_chunk's latency form (plain chunks of 32 coders, messages of
+// few chunks).
+template <int NT, int KIND, bool PLACE = false, bool LAT = false>
 __device__ __forceinline__ void encode_body(const EncodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
     constexpr bool BYTES = KIND == kBytes;
@@ -106,7 +108,7 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
         if (ADAPTN)
             enc::adaptive_n_forward<NT, AdaptN<KIND>::kNB>(p.sym + first, n_c, p.N, p.n_alpha, ctx,
                                                           lane, acc);
-        enc::encode_chunk<NT, !RAW && !ADAPT && !ADAPTN, RAW, BYTES, ADAPT, WIDE, ADAPTN>(
+        enc::encode_chunk<NT, !RAW && !ADAPT && !ADAPTN, RAW, BYTES, ADAPT, WIDE, ADAPTN, false, LAT>(
             p.sym + first, n_c, p.N, p.words + uint64_t(c) * p.slot_bytes, p.slot_bytes,
             p.wstart + c, p.sizes + c, p.states + uint64_t(c) * p.N, sm.tab_s, ring_s, ge, lane,
             acc, RAW ? p.raw + first : nullptr, ctx);
@@ -132,10 +134,10 @@ __device__ __forceinline__ void encode_body(const EncodeParams &p) {
 // registers (three CTAs per SM) for its two register sets of prefetched
 // symbols, and ran faster so than held to 64 with spills (measured on B300,
 // 1 GiB: 1246 against 1257 us).  The others need the bound.
-template <int NT, int KIND, bool PLACE>
+template <int NT, int KIND, bool PLACE, bool LAT = false>
 __global__ void __launch_bounds__(enc::kThreads, KIND == kPlain && NT == 32 ? 0 : 4)
     encode_kernel(const __grid_constant__ EncodeParams p) {
-    encode_body<NT, KIND, PLACE>(p);
+    encode_body<NT, KIND, PLACE, LAT>(p);
 }
 
 template <int NT, bool PLACE>
@@ -192,10 +194,22 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
                                p.offs);
 }
 
+// Plain messages of 32 coders and up to this many chunks take the encoder's
+// latency form (encode_chunk's LAT): two thirds of a wave of the placing
+// coder's warps (3 CTAs of 8 warps per SM on 148 SMs), where the SM has too
+// few warps to hide a step's latencies.  Measured on B300 (chunks of 64 Ki
+// symbols, latency form against the other): 1184 chunks 202.0 -> 165.3 us,
+// 1776 chunks 239.2 -> 221.4 us, 2368 chunks 251.9 -> 232.7 us, but 2960
+// chunks 310.2 -> 314.5 us and 3552 chunks 319.0 -> 327.2 us.
+constexpr uint32_t kLatMaxChunks = 2368;
+
 template <int NT, int KIND, bool PLACE = false>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     void (*kernel)(EncodeParams);
     if constexpr (KIND == kWide) kernel = encode_kernel_wide<NT, PLACE>;
+    else if constexpr (KIND == kPlain && NT == 32)
+        kernel = p.c_end - p.c_begin <= kLatMaxChunks ? encode_kernel<NT, KIND, PLACE, true>
+                                                      : encode_kernel<NT, KIND, PLACE, false>;
     else kernel = encode_kernel<NT, KIND, PLACE>;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, kSmemBytes) !=
