@@ -1215,6 +1215,8 @@ def main(argv=None):
                          "frac": achieved / hbm, "traffic": profiled_traffic(),
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": sampler.summary(),
+            "device": {"name": torch.cuda.get_device_name(dev),
+                       "sm_count": torch.cuda.get_device_properties(dev).multi_processor_count},
             # per step: encode_kernel (codes and places the chunks), settle_kernel
             # (the size of a rejected message), decode_kernel
             "gpu_launches": 3 * args.steps,
