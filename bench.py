@@ -1158,6 +1158,8 @@ def main(argv=None):
         e2e_enc = end_to_end_encode(rans, sym, freq, N, CS, dev, max(3, min(args.steps, 10)),
                                     msg[:msg_size])
 
+    ceiling = pipe_ceiling(rans, dev, (n / N) / (dec_mean * 1e-3)) if rank == 0 else None
+
     cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, cpu1 = cpu_baseline(msg[:msg_size].cpu().numpy(), freq, N, CS, n // CS)
@@ -1197,6 +1199,11 @@ def main(argv=None):
         extra["wide"] = wide_leg(rans, dev, args, peaks()[0])
         torch.cuda.empty_cache()
 
+    if ceiling and "batched" in extra:
+        # the batched decoder's chunk-steps (32 symbols each) per second
+        b = extra["batched"]
+        rate = b["decode_gbs"] * 1e9 / 32
+        b["roofline"]["pipe_ceiling_fraction"] = rate / ceiling["warp_steps_per_s"]
     if rank == 0:
         hbm, peak_kind = peaks()
         alg_bytes = msg_size + n
@@ -1213,7 +1220,8 @@ def main(argv=None):
             "roofline": {"kernel": "decode_kernel12", "bound": "hbm", "achieved": achieved,
                          "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": profiled_traffic(),
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "pipe_ceiling": ceiling},
             "clocks": sampler.summary(),
             "device": {"name": torch.cuda.get_device_name(dev),
                        "sm_count": torch.cuda.get_device_properties(dev).multi_processor_count},
@@ -1236,6 +1244,28 @@ def main(argv=None):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def pipe_ceiling(rans, dev, decoder_warp_steps_per_s):
+    """The rate of rans_check_gather_ceiling (the decode step's slot-table
+    gather, ring window read and 32-byte symbol store, without its arithmetic,
+    in the plain decoder's shape) beside the headline decoder's own rate, both
+    in warp-steps per second."""
+    import torch
+
+    warps = rans.rans_check_gather_ceiling_warps()
+    out = torch.empty(warps * 4096, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    steps = 6144  # three 64 Ki-symbol chunks per warp
+    run = lambda: rans.rans_check_gather_ceiling(steps, out, out.numel(), sink)  # noqa: E731
+    run()
+    torch.cuda.synchronize(dev)
+    ms = statistics.median(_events(torch, run, 10))
+    rate = warps * steps / (ms * 1e-3)
+    return {"kernel": "gather_ceiling_kernel", "warps": warps, "steps_per_warp": steps,
+            "ms": ms, "warp_steps_per_s": rate,
+            "decoder_warp_steps_per_s": decoder_warp_steps_per_s,
+            "decoder_fraction": decoder_warp_steps_per_s / rate}
 
 
 def end_to_end(rans, msg_dev, n, freq, N, CS, dev, steps, sym_dev):

@@ -660,6 +660,37 @@ int rans_check_division(uint32_t method, uint32_t log2m, uint64_t *d_result,
                         rans_stream_t stream);
 
 /*
+ * rans_check_gather_ceiling -- diagnostic of what bounds the table decoder; no
+ * step of the paper's method.  The decode step of Section 6 puts three
+ * accesses through the SM's L1/shared-memory pipe: the slot-table lookup (32
+ * random entries of a 4096-entry table in shared memory), the read of the
+ * step's words (a contiguous window of the word ring) and the store of the
+ * step's 32 symbols.  This enqueues one kernel that does only those three
+ * accesses per step, in the plain decoder's shape (CTAs of 12 warps, 3 per SM,
+ * one 16 KiB table per CTA, a 4 KiB ring per warp), each lane's next slot
+ * taken from a multiply-add of the two values it loaded, so that each warp's
+ * steps form a chain as the decoder's do.  Every warp runs `steps` steps; the
+ * kernel's time for rans_check_gather_ceiling_warps() * steps warp-steps is
+ * the pipe's rate for the decode step's access mix, to set beside the
+ * decoder's own steps per second.
+ *
+ * steps  : warp-steps per warp, a positive multiple of 16.
+ * d_out  : device, out_size >= rans_check_gather_ceiling_warps() * 4096 bytes,
+ *          overwritten (4 KiB per warp, written cyclically).
+ * d_sink : device u32, incremented only by a lane whose state reaches 0 (it
+ *          keeps the chain live; almost never).
+ * Returns RANS_OK when the kernel was enqueued, RANS_ERR_INVALID_ARG for a bad
+ * steps or pointer, RANS_ERR_BUFFER_TOO_SMALL for a small d_out, RANS_ERR_CUDA
+ * on a launch error.
+ *
+ * rans_check_gather_ceiling_warps -- the number of warps that kernel runs on
+ * the current device (resident CTAs x 12), 0 on a CUDA error.
+ */
+int rans_check_gather_ceiling(uint32_t steps, uint8_t *d_out, uint64_t out_size,
+                              uint32_t *d_sink, rans_stream_t stream);
+uint64_t rans_check_gather_ceiling_warps(void);
+
+/*
  * Checked builds (a test build compiled with -DRANS_CHECKED; the library
  * built normally answers RANS_ERR_INVALID_ARG to both calls).  The kernels
  * then test their invariants as they run and count the ones that fail (the

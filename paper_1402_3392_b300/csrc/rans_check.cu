@@ -2,6 +2,7 @@
 // device-side wait that runs out ends the kernel with a status, not a hang.
 #include <cuda_runtime.h>
 
+#include "decode_core.cuh"
 #include "device_util.cuh"
 #include "encode_core.cuh"
 #include "host_util.h"
@@ -112,6 +113,59 @@ __global__ void division_check_init(unsigned long long *out) {
     out[2] = ~0ull;
 }
 
+// The table decoder's data-pipe work without its arithmetic: the ceiling of
+// the SM's L1/shared-memory pipe for the decode step's access mix.  Same
+// shape as the plain decoder of large messages (12-warp CTAs, 3 per SM, a
+// 16 KiB table per CTA and a 4 KiB ring per warp).  Per step lane j loads the
+// table entry of a slot taken from its state (32 random words of the
+// 4096-word table, as the decode step's slot lookup), the word at rp + 2j of
+// the warp's ring (a contiguous 64-byte window, as the renormalization
+// read), and stores one byte to 32 consecutive bytes of the warp's 4 KiB of
+// out (as the decoded symbols).  The next state is a multiply-add of both
+// loads, so every warp's steps form a chain as the decoder's do; rp moves 24
+// bytes a step, about a step's words.  36 warps of such chains ask the pipe
+// for several wavefronts a cycle, so the rate this kernel reaches is the
+// pipe's.
+constexpr int kCeilWarps = dec::kWarpsOne;
+constexpr uint32_t kCeilSmem = dec::kTableBytes + dec::kWarpRing + kCeilWarps * dec::kWarpRing;
+constexpr uint32_t kCeilOutPerWarp = 4096;
+
+__device__ __forceinline__ uint32_t ceil_mix(uint32_t v) {  // a fixed scramble of v
+    v ^= v >> 16;
+    v *= 0x7FEB352Du;
+    v ^= v >> 15;
+    v *= 0x846CA68Bu;
+    return v ^ (v >> 16);
+}
+
+__global__ void __launch_bounds__(kCeilWarps * 32, 3)
+    gather_ceiling_kernel(uint32_t steps, uint8_t *out, uint32_t *sink) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+    const uint32_t raw = smem_addr(smem + dec::kTableBytes);
+    const uint32_t rings_s = (raw + dec::kWarpRing - 1) & ~(dec::kWarpRing - 1);
+    uint32_t *rings = reinterpret_cast<uint32_t *>(smem + dec::kTableBytes + (rings_s - raw));
+    for (uint32_t i = threadIdx.x; i < kM; i += blockDim.x) tab[i] = ceil_mix(i);
+    for (uint32_t i = threadIdx.x; i < kCeilWarps * dec::kWarpRing / 4; i += blockDim.x)
+        rings[i] = ceil_mix(i ^ 0x9E3779B9u);
+    __syncthreads();
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t tab_s = smem_addr(tab), ring_s = rings_s + warp * dec::kWarpRing;
+    uint8_t *o = out + (uint64_t(blockIdx.x) * kCeilWarps + warp) * kCeilOutPerWarp + lane;
+    uint32_t x = ceil_mix(blockIdx.x * blockDim.x + threadIdx.x + 1u), rp = 0;
+    for (uint32_t t = 0; t < steps; t += 16) {
+#pragma unroll
+        for (uint32_t u = 0; u < 16; ++u) {
+            const uint32_t e = dec::ld_table(dec::imad(x & (kM - 1), 4u, tab_s));
+            const uint32_t w = dec::ld_ring_u16(dec::word_at<dec::kWarpRing>(rp, lane, ring_s));
+            x = dec::imad(x, 0x9E3779B1u, e ^ w);
+            o[((t + u) * 32u) & (kCeilOutPerWarp - 1)] = uint8_t(e);
+            rp += 24u;
+        }
+    }
+    if (x == 0u) atomicAdd(sink, 1u);  // keeps the chain live
+}
+
 #ifdef RANS_CHECKED
 // Checked builds: one invariant that fails on purpose, so a test can see the
 // counters work.
@@ -168,5 +222,29 @@ extern "C" int rans_check_division(uint32_t method, uint32_t log2m, uint64_t *d_
     const dim3 grid(nf, unsigned((span + kDivSlice - 1) / kDivSlice));
     if (method == 0) division_check_kernel<0><<<grid, kDivThreads, 0, st>>>(log2m, out);
     else division_check_kernel<1><<<grid, kDivThreads, 0, st>>>(log2m, out);
+    return check_launch();
+}
+
+extern "C" uint64_t rans_check_gather_ceiling_warps(void) {
+    static_assert(3 * (kCeilSmem + 1024) <= 233472, "three CTAs per SM");
+    if (cudaFuncSetAttribute(gather_ceiling_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kCeilSmem)) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_ceiling_kernel,
+                                                      kCeilWarps * 32, kCeilSmem) != cudaSuccess ||
+        per_sm <= 0)
+        return 0;
+    return uint64_t(per_sm) * uint64_t(sm_count()) * kCeilWarps;
+}
+
+extern "C" int rans_check_gather_ceiling(uint32_t steps, uint8_t *d_out, uint64_t out_size,
+                                         uint32_t *d_sink, rans_stream_t stream) {
+    const uint64_t warps = rans_check_gather_ceiling_warps();
+    if (!warps) return RANS_ERR_CUDA;
+    if (!d_out || !d_sink || steps == 0 || (steps & 15u)) return RANS_ERR_INVALID_ARG;
+    if (out_size < warps * kCeilOutPerWarp) return RANS_ERR_BUFFER_TOO_SMALL;
+    gather_ceiling_kernel<<<unsigned(warps / kCeilWarps), kCeilWarps * 32, kCeilSmem,
+                            reinterpret_cast<cudaStream_t>(stream)>>>(steps, d_out, d_sink);
     return check_launch();
 }

@@ -104,6 +104,8 @@ def _load() -> C.CDLL:
         "rans_check_bounded_wait": (i32, [vp, vp]),
         "rans_check_lookback_wait": (i32, [vp, vp]),
         "rans_check_division": (i32, [u32, u32, vp, vp]),
+        "rans_check_gather_ceiling": (i32, [u32, vp, u64, vp, vp]),
+        "rans_check_gather_ceiling_warps": (u64, []),
         "rans_debug_checks": (i32, [vp]),
         "rans_debug_check_selftest": (i32, [vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
@@ -717,6 +719,21 @@ def rans_check_division(method: int, log2m: int, d_result, stream=None, check=Tr
     a device tensor of 4 u64 (checked, wrong, first wrong f << 32 | x, 0)."""
     rc = lib.rans_check_division(int(method), int(log2m), _ptr(d_result), _stream(stream))
     return _check(rc, "rans_check_division") if check else rc
+
+
+def rans_check_gather_ceiling_warps() -> int:
+    return int(lib.rans_check_gather_ceiling_warps())
+
+
+def rans_check_gather_ceiling(steps: int, d_out, out_size: int, d_sink, stream=None,
+                              check=True) -> int:
+    """Diagnostic: the table decoder's data-pipe work (slot-table gather, ring
+    window read, 32-byte symbol store per step) without its arithmetic, in the
+    plain decoder's shape; every one of rans_check_gather_ceiling_warps()
+    warps runs `steps` steps (a multiple of 16)."""
+    rc = lib.rans_check_gather_ceiling(int(steps), _ptr(d_out), int(out_size), _ptr(d_sink),
+                                       _stream(stream))
+    return _check(rc, "rans_check_gather_ceiling") if check else rc
 
 
 def rans_encode_static_scratch(d_symbols, n_symbols, freq, n_lanes, chunk_symbols, d_out,
