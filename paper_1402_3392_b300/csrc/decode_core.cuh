@@ -68,6 +68,13 @@ using GeoPair = Geometry<512, kNSeg, 16>;
 using GeoRaw = Geometry<1024, kNSeg, 16, 128>;
 // Prefix messages read up to one 32-bit word per lane and step: as GeoRaw.
 using GeoPrefix = Geometry<1024, kNSeg, 16, 128>;
+// The entry-ahead step (kKindPlainSpec) reads 64 bytes a step but converts
+// the words up to 2 KiB past rp before every group: with 128 counted per
+// step a copy is waited one segment after its issue, which keeps
+// [rp, rp + 2 KiB) in after the events due at rp.
+using GeoSpec = Geometry<1024, kNSeg, 16, 128>;
+static_assert(GeoSpec::kLag == 1 && GeoSpec::kSeg * (GeoSpec::kNSeg - 1 - GeoSpec::kLag) >= 2048,
+              "the entry-ahead step converts 2 KiB of resident words ahead");
 static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing &&
                   GeoRaw::kRing == kWarpRing,
               "ring sizes");
@@ -129,6 +136,15 @@ constexpr int kKindAdaptN4 = 8, kKindAdaptN8 = 9, kKindAdaptN16 = 10;
 // EARLY form): the plain bitstream, for messages under one wave of chunks,
 // where a warp's chain of dependent steps, not the SM's pipes, sets the pace.
 constexpr int kKindPlainEarly = 11;
+// Plain messages decoded with the next step's table entry taken early
+// (decode_step_spec): the plain bitstream, for messages of at most two chunks
+// per SM, where a single warp's chain of dependent steps is all that sets
+// the pace.  Beside its word ring each warp keeps an entry ring: for every
+// word of the stream ahead, the slot-table entry of the state that word
+// would complete (its slot is the word's low 12 bits), kERing bytes (1024
+// entries, so 2 KiB of stream positions) per warp.
+constexpr int kKindPlainSpec = 12;
+constexpr uint32_t kERing = 4096;
 template <int KIND>
 struct AdaptN {
     static constexpr bool kOn = KIND == kKindAdaptN4 || KIND == kKindAdaptN8 || KIND == kKindAdaptN16;
@@ -484,6 +500,7 @@ struct Chain {
     uint32_t nb;         // prefix messages: bits held (at most 43 unless a code was missing)
     uint32_t cm[15];     // adaptive-n messages: this lane's model (adapt_model.cuh)
     uint32_t nm;         // adaptive-n messages: M - n
+    uint32_t cv;         // entry-ahead step: entries hold for stream bytes below cv
 };
 
 __device__ __forceinline__ void chain_empty(Chain &c) {
@@ -497,6 +514,7 @@ __device__ __forceinline__ void chain_empty(Chain &c) {
     c.rp0 = c.len = 0;
     c.p = kAdaptP0;
     c.bhi = c.blo = c.nb = 0;
+    c.cv = 0;
 }
 
 // Open a prefix-message chunk [o, e): no states, its 32-bit words start at
@@ -648,6 +666,88 @@ __device__ __forceinline__ void decode_step(uint32_t &x, uint32_t &rp, bool acti
                              : ld_ring_u16(word_at<RING>(rp, __popc(m & lt), ring_s));
     if (need) x = __byte_perm(x, w, 0x1054u);  // (x << 16) | w
     rp = imad(__popc(m), 2u, rp);
+}
+
+// Entry ring (kKindPlainSpec) loads and stores: the ring is rewritten by the
+// warp as the stream advances, so both stay ordered (volatile).
+__device__ __forceinline__ uint32_t ld_ering(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void st_ering(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// Entry-ring address of stream byte position p (even): entry (p / 2) mod 1024.
+__device__ __forceinline__ uint32_t ering_at(uint32_t p, uint32_t ering_s) {
+    return ((p * 2u) & (kERing - 1)) | ering_s;
+}
+
+// The entry-ahead step (kKindPlainSpec), for warps whose chain of dependent
+// steps sets the pace.  e: the slot-table entry of x's slot, carried from
+// the step before.  A renormalizing lane's next slot is the low 12 bits of
+// the word it reads, so its next entry is known as soon as the word is: lane
+// j loads the word at rp + 2j and that word's entry from the entry ring
+// (spec_convert filled it) before D, and a lane that reads a word takes the
+// word and the entry of lane popc(m & lt) by two shuffles.  A lane that does
+// not renormalize looks its next entry up from x'.  The step's chain is then
+// D, the ballot, its prefix count, a shuffle and a select: no shared-memory
+// load after the word is known.  The order of the shared-memory operations
+// matters: that table lookup issued after the shuffles (as here) measured
+// 65.6 ns a step on one 1 MiB chunk, issued before the ballot 77.4 ns,
+// against 70.5 ns for the early-word step.
+template <bool FULL>
+__device__ __forceinline__ void decode_step_spec(uint32_t &x, uint32_t &e, uint32_t &rp, bool active,
+                                                 uint32_t tab_s, uint32_t ring_s, uint32_t ering_s,
+                                                 uint8_t *outp, uint32_t lt) {
+    const uint32_t pos = imad(threadIdx.x & 31u, 2u, rp);
+    const uint32_t wl = ld_ring_u16(word_at<kWarpRing>(pos, 0u, ring_s));
+    const uint32_t el = ld_ering(ering_at(pos, ering_s));
+    uint32_t xn = x;
+    if (FULL || active) {
+        xn = decode_update(x, e);
+        *outp = uint8_t(e);
+    }
+    const bool need = (FULL || active) && xn < kL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t k = __popc(m & lt);
+    const uint32_t w = __shfl_sync(kFull, wl, k);
+    const uint32_t ew = __shfl_sync(kFull, el, k);
+    const uint32_t en = ld_table(imad(xn & (kM - 1), 4u, tab_s));
+    x = need ? __byte_perm(xn, w, 0x1054u) : xn;  // (x << 16) | w
+    e = need ? ew : en;
+    rp = imad(__popc(m), 2u, rp);
+}
+
+// Fill the entry ring ahead of the entry-ahead step: for every word at
+// stream bytes [c.cv, rp + 2 KiB), in whole 64-byte blocks, the slot-table
+// entry of its low 12 bits, at the word's place in the entry ring.  Called
+// after the ring events due at rp, which keep [rp, rp + 2 KiB) of words in
+// (GeoSpec); entries below rp are spent, so the 1024-entry ring holds what
+// is ahead.  Four blocks at a time (loads first, so their latencies
+// overlap), then __syncwarp: every lane sees the entries the others stored.
+__device__ __forceinline__ void spec_convert(Chain &c, uint32_t ring_s, uint32_t ering_s,
+                                             uint32_t tab_s, uint32_t lane) {
+    const uint32_t lim = c.rp + 2048u;
+    while (c.cv + 64u <= lim) {
+        const uint32_t nb = min(4u, (lim - c.cv) >> 6);
+        const uint32_t p0 = imad(lane, 2u, c.cv);
+        // Selects, not branches, around the loads: the four table lookups
+        // then issue back to back (with a branch around each they waited for
+        // one another: one 1 MiB chunk 2.15 -> 2.39 ms).
+        uint32_t w[4], v[4];
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i)
+            w[i] = i < nb ? ld_ring_u16(word_at<kWarpRing>(p0 + 64u * i, 0u, ring_s)) : 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i)
+            v[i] = i < nb ? ld_table(imad(w[i] & (kM - 1), 4u, tab_s)) : 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i)
+            if (i < nb) st_ering(ering_at(p0 + 64u * i, ering_s), v[i]);
+        c.cv += 64u * nb;
+    }
+    __syncwarp();
 }
 
 // One step at 13 or 14 bits of resolution (LM): the slot's symbol from the
@@ -969,6 +1069,41 @@ __device__ __forceinline__ void chain_run(Chain &c, ChainRing &r, uint32_t &time
     }
 }
 
+// Decode what is left of one chunk with the entry-ahead step (G = GeoSpec,
+// ering_s: the warp's entry ring).
+template <bool FULL, class G>
+__device__ __forceinline__ void chain_run_spec(Chain &c, ChainRing &r, uint32_t &timeouts,
+                                               uint32_t N, bool lane_on, uint32_t lane,
+                                               uint32_t tab_s, uint32_t lt, uint32_t ering_s) {
+    c.cv = c.rp & ~63u;
+    uint32_t e = ld_table(imad(c.x & (kM - 1), 4u, tab_s));
+    for (uint32_t g = c.steps / G::kGroup; g > 0; --g) {
+        chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kGroup * G::kStep));
+        spec_convert(c, r.ring_s, ering_s, tab_s, lane);
+#pragma unroll
+        for (uint32_t u = 0; u < G::kGroup; ++u)
+            decode_step_spec<FULL>(c.x, e, c.rp, lane_on, tab_s, r.ring_s, ering_s,
+                                   c.outp + u * N, lt);
+        c.outp += G::kGroup * N;
+    }
+    for (uint32_t t = c.steps % G::kGroup; t > 0; --t) {
+        chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kGroup * G::kStep));
+        spec_convert(c, r.ring_s, ering_s, tab_s, lane);
+        decode_step_spec<FULL>(c.x, e, c.rp, lane_on, tab_s, r.ring_s, ering_s, c.outp, lt);
+        c.outp += N;
+    }
+    c.steps = 0;
+    if (c.rem) {
+        chain_service<G>(c, r, timeouts, lane);
+        RANS_CHECK(timeouts || ring_window_ok<G>(c, G::kGroup * G::kStep));
+        spec_convert(c, r.ring_s, ering_s, tab_s, lane);
+        decode_step_spec<false>(c.x, e, c.rp, lane < c.rem, tab_s, r.ring_s, ering_s, c.outp, lt);
+        c.rem = 0;
+    }
+}
+
 // Byte-wise chunks end in zero padding up to a multiple of 4 bytes: the chunk
 // must be exactly round4(4N + digits read) long, with zeros after the digits
 // (src + rp .. src + endrel, at most 3 bytes).
@@ -1062,10 +1197,13 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
     static_assert(!(PAIR && KIND != kKindPlain && KIND != kKindBinary),
                   "only plain messages pair chunks");
     constexpr bool BINARY = KIND == kKindBinary;
+    constexpr bool SPEC = KIND == kKindPlainSpec;
+    static_assert(!(PAIR && SPEC), "the entry-ahead step decodes one chunk per warp");
     using G = typename std::conditional<
         RAW, GeoRaw,
+        typename std::conditional<SPEC, GeoSpec,
         typename std::conditional<PREFIX, GeoPrefix,
-                                  typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type>::type;
+                                  typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type>::type>::type;
     constexpr bool kFullWarp = NT == 32;
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;
@@ -1132,7 +1270,10 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
             b.outp += G::kGroup * N;
         }
     }
-    chain_run<kFullWarp, G, KIND>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
+    if constexpr (SPEC)  // flags_s: the warp's entry ring
+        chain_run_spec<kFullWarp, G>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
+    else
+        chain_run<kFullWarp, G, KIND>(a, w.r[0], w.timeouts, N, lane_on, lane, tab_s, lt, flags_s);
     if (two)
         chain_run<kFullWarp, G, BINARY ? kKindBinary : kKindPlain>(b, w.r[1], w.timeouts, N,
                                                                     lane_on, lane, tab_s, lt,

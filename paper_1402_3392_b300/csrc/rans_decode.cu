@@ -46,7 +46,15 @@ constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::k
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14,
               kBinary = dec::kKindBinary, kAdaptN4 = dec::kKindAdaptN4,
               kAdaptN8 = dec::kKindAdaptN8, kAdaptN16 = dec::kKindAdaptN16,
-              kPlainEarly = dec::kKindPlainEarly;
+              kPlainEarly = dec::kKindPlainEarly, kPlainSpec = dec::kKindPlainSpec;
+
+// Dynamic shared memory of the W-warp kernel for KIND: the shape's layout,
+// and for the entry-ahead step one entry ring per warp after it (aligned to
+// its size, with that much slack).
+template <int KIND, int W>
+constexpr uint32_t smem_bytes() {
+    return dec::Shape<W>::kSmemBytes + (KIND == kPlainSpec ? (W + 1) * dec::kERing : 0u);
+}
 
 // NT = 32: every chunk uses all 32 lanes; NT = 0: runtime N.  W: warps per
 // CTA (dec::Shape).  A warp decodes one chunk at a time.
@@ -94,8 +102,17 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t data_end = offs[p.n_chunks];
     const uint32_t lt = lanemask_lt();
     const uint32_t n_units = p.c_end - p.c_begin;
+    // The entry-ahead step: each warp's entry ring after the shape's layout;
+    // chunks dealt warp-major, so that a message of few chunks spreads over
+    // the SMs one warp each rather than filling a few CTAs.
+    constexpr bool SPEC = KIND == kPlainSpec;
+    const uint32_t ering_s =
+        SPEC ? ((smem_addr(smem + dec::Shape<W>::kSmemBytes) + dec::kERing - 1) &
+                ~(dec::kERing - 1)) + warp * dec::kERing
+             : 0u;
+    const uint32_t q0 = SPEC ? warp * gridDim.x + blockIdx.x : blockIdx.x * W + warp;
 
-    for (uint32_t q = blockIdx.x * W + warp; q < n_units; q += gridDim.x * W) {
+    for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
         uint32_t st;
         if (RAW)
@@ -120,9 +137,10 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
             st = dec::decode_chunks<NT, false, KIND>(wr, p.freq[0], p.msg, p.data0, offs,
                                                      data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
                                                      cs, lane, lt, nullptr, p.freq[1]);
-        else  // plain (KIND kPlain or kPlainEarly)
+        else  // plain (KIND kPlain, kPlainEarly or kPlainSpec; the entry ring rides in flags_s)
             st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
-                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt);
+                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
+                                                     nullptr, ering_s);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
@@ -162,13 +180,14 @@ uint64_t resident_ctas() {
     if (dev >= 0 && dev < 64 && !configured[dev].load()) {
         if (cudaFuncSetAttribute(kernel_for<NT, KIND, W>(),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(S::kSmemBytes)) != cudaSuccess)
+                                 int(smem_bytes<KIND, W>())) != cudaSuccess)
             return 0;
         configured[dev].store(true);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for<NT, KIND, W>(),
-                                                      S::kThreads, S::kSmemBytes) != cudaSuccess ||
+                                                      S::kThreads, smem_bytes<KIND, W>()) !=
+            cudaSuccess ||
         per_sm <= 0)
         return 0;
     return uint64_t(per_sm) * sm_count();
@@ -177,15 +196,19 @@ uint64_t resident_ctas() {
 template <int NT, int KIND, int W>
 int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
     using S = dec::Shape<W>;
-    const uint64_t want = ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W));
+    // The entry-ahead step deals chunks warp-major: a CTA per chunk up to the
+    // resident limit.
+    const uint64_t want = KIND == kPlainSpec ? uint64_t(p.c_end - p.c_begin)
+                                             : ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W));
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    kernel_for<NT, KIND, W>()<<<grid, S::kThreads, S::kSmemBytes, stream>>>(p);
+    kernel_for<NT, KIND, W>()<<<grid, S::kThreads, smem_bytes<KIND, W>(), stream>>>(p);
     return check_launch();
 }
 
 // A warp decodes one chunk.  Plain messages under one wave of chunks: 8-warp
 // CTAs, where more resident warps gain nothing and the 64-register form has
-// the shorter step (one 1 MiB chunk: 2.41 against 2.44 ms); up to half a
+// the shorter step (one 1 MiB chunk: 2.41 against 2.44 ms); up to two chunks
+// per SM with the entry-ahead step (kSpecMaxChunks), up to half a
 // wave with the early-word step (dec::kKindPlainEarly), whose step is
 // shorter on an SM with few warps and costs a data-pipe wavefront on a full
 // one (measured, µs, committed step against it: 1 chunk 164.7 / 158.8, 1184
@@ -197,6 +220,13 @@ int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
 // CTA were faster than one per warp in 8-warp CTAs from five waves up; one
 // per warp in 12-warp CTAs beats both (32256 chunks of 64 Ki symbols, 6.8
 // waves: 1636 against 1814 us), so single messages no longer pair chunks.
+// Plain messages of up to this many chunks, two per SM, take the entry-ahead
+// step (dec::kKindPlainSpec), one chunk per CTA.  Measured on B300 (chunks of
+// 64 Ki symbols, against the early-word step): 1 chunk of 1 MiB 2312 -> 2149
+// us, 148 chunks 166.8 -> 150.7 us, 296 chunks 166.3 -> 152.4 us; at 444 to
+// 1184 chunks the two are within 1 %.
+constexpr uint64_t kSpecMaxChunks = 296;
+
 template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
     const uint64_t n_range = p.c_end - p.c_begin;
@@ -204,6 +234,11 @@ int launch_decode(DecodeParams &p, cudaStream_t stream) {
         const uint64_t cap8 = resident_ctas<NT, KIND, dec::kWarps>();
         if (!cap8) return RANS_ERR_CUDA;
         if constexpr (KIND == kPlain) {
+            if (n_range <= kSpecMaxChunks) {
+                const uint64_t cap_s = resident_ctas<NT, kPlainSpec, dec::kWarps>();
+                if (!cap_s) return RANS_ERR_CUDA;
+                return launch_shape<NT, kPlainSpec, dec::kWarps>(p, cap_s, stream);
+            }
             if (2 * n_range <= cap8 * dec::kWarps) {
                 const uint64_t cap_e = resident_ctas<NT, kPlainEarly, dec::kWarps>();
                 if (!cap_e) return RANS_ERR_CUDA;
