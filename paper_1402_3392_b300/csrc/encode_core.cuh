@@ -303,23 +303,10 @@ __device__ __forceinline__ uint32_t store_at(uint32_t wp, uint32_t k, uint32_t r
 // renormalize (emit the low 16 bits if x >= f_s * 2^20), then x = C(s, x).
 // wp is the warp-uniform write position (bytes, counting down); ring_s is
 // the warp's 4 KiB-aligned ring.
-// XFIRST: the new state is computed before the ballot and the word's store
-// (the latency form, encode_chunk's LAT).
-template <bool FULL, uint32_t RING, bool XFIRST = false>
+template <bool FULL, uint32_t RING>
 __device__ __forceinline__ void encode_with(uint32_t &x, uint32_t &wp, bool on, uint2 t,
                                             uint32_t ring_s, uint32_t ge) {
     const bool emit = on && (x > ~(t.y & 0xFFF00000u));
-    if constexpr (XFIRST) {
-        const uint32_t xs = emit ? x >> 16 : x;
-        const uint32_t q = div_reciprocal(xs, t.x, t.y >> 12);  // floor(x / f_s)
-        const uint32_t xn = on ? xs + q * (t.y >> 20) + (t.y & 0xFFFu) : x;
-        const uint32_t m = __ballot_sync(kFull, emit);
-        st_ring_u16_if(emit, store_at<RING>(wp, __popc(m & ge), ring_s), x);
-        if (RING) wp -= 2u * __popc(m);
-        else wp = imad_u32(__popc(m), 0u - 2u, wp);
-        x = xn;
-        return;
-    }
     const uint32_t m = __ballot_sync(kFull, emit);
     st_ring_u16_if(emit, store_at<RING>(wp, __popc(m & ge), ring_s), x);
     x = emit ? x >> 16 : x;
@@ -618,8 +605,9 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // LAT (plain chunks of 32 coders with PREFETCH): the form for warps whose
 // chain of dependent steps sets the pace, on an SM with few of them: each
 // step's table entry is loaded during the step before, and the new state is
-// computed ahead of the ballot and the word's store (encode_with's XFIRST).
-// Measured on B300, against the form below: one 1 MiB chunk 1991 -> 1347 us,
+// computed ahead of the ballot and the word's store, which are deferred to
+// the next step.  Measured on B300, against the form below (before the
+// deferral; with it one 1 MiB chunk takes 1211 us): one 1 MiB chunk 1991 -> 1347 us,
 // 592 chunks of 64 Ki symbols 190.6 -> 156.5 us, but one wave (3552 chunks)
 // 319.0 -> 327.2 us and 1 GiB 1236 -> 1283 us (the launcher's choice:
 // rans_encode.cu kLatMaxChunks).  Either form alone gains nothing (1 MiB
@@ -812,14 +800,34 @@ __device__ __forceinline__ void encode_chunk(const uint8_t *sym, uint32_t n_c, u
         auto code = [&](const uint32_t(&c)[kGroup]) {
             service();
             if constexpr (LAT) {
+                // Each step's ballot and word store are deferred to the next
+                // step and written between its own state-update operations,
+                // so that the two dependent chains overlap in the warp's
+                // in-order issue (the same stores in the same order; one
+                // 1 MiB chunk 1353 -> 1211 us).
                 uint2 tn = ld_enc_table(tab_s + (c[0] << 3));
+                bool pe = false;     // the previous step emits a word
+                uint32_t pw = 0u;    // its state, whose low 16 bits are the word
 #pragma unroll
                 for (uint32_t u = 0; u < kGroup; ++u) {
                     const uint2 t = tn;
                     if (u + 1 < kGroup) tn = ld_enc_table(tab_s + (c[u + 1] << 3));
                     acc |= t.y;
-                    encode_with<true, kRing, true>(x, wp, true, t, ring_s, ge);
+                    const bool emit = x > ~(t.y & 0xFFF00000u);
+                    const uint32_t mp = __ballot_sync(kFull, pe);
+                    const uint32_t xs = emit ? x >> 16 : x;
+                    const uint32_t kp = __popc(mp & ge);
+                    const uint32_t q = div_reciprocal(xs, t.x, t.y >> 12);  // floor(x / f_s)
+                    st_ring_u16_if(pe, store_at<kRing>(wp, kp, ring_s), pw);
+                    const uint32_t xn = xs + q * (t.y >> 20) + (t.y & 0xFFFu);
+                    wp -= 2u * __popc(mp);
+                    pe = emit;
+                    pw = x;
+                    x = xn;
                 }
+                const uint32_t mp = __ballot_sync(kFull, pe);
+                st_ring_u16_if(pe, store_at<kRing>(wp, __popc(mp & ge), ring_s), pw);
+                wp -= 2u * __popc(mp);
             } else {
 #pragma unroll
                 for (uint32_t u = 0; u < kGroup; ++u)
