@@ -953,7 +953,7 @@ __device__ __forceinline__ void decode_step_adaptive_n(Chain &c, bool active, ui
         for (int i = NB - 1; i >= 0; --i) F = le[i] ? F : c.cm[i];
         c.x = imad(F - B, c.x >> kLog2M, slot - B);
         *outp = uint8_t(s);
-        adapt::update<NB>(c.cm, le, c.nm);
+        adapt::update_signed<NB>(c.cm, le, c.nm);
     }
     const bool need = on && c.x < kL;
     const uint32_t m = __ballot_sync(kFull, need);

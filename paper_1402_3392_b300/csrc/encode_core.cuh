@@ -474,12 +474,26 @@ __device__ __forceinline__ void adaptive_n_forward(const uint8_t *sym, uint32_t 
         bad |= s >= n;
         uint32_t B = 0, F = kM;
         bool le[NB];
+        if constexpr (NB < 15) {
+            // B = C_s and F = C_{s+1} from the boundaries' sides (le is true
+            // below s + 1), as the decoder finds them.  Measured on B300 (256
+            // Mi symbols): n = 8 1553 -> 1407 us, n = 4 1122 -> 1091 us, but n
+            // = 16 2412 -> 2499 us, which keeps the two compares.
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const uint32_t b = uint32_t(i + 1);
-            B = b == s ? cm[i] : B;
-            F = b == s + 1 ? cm[i] : F;
-            le[i] = b <= s;
+            for (int i = 0; i < NB; ++i) {
+                le[i] = uint32_t(i + 1) <= s;
+                B = le[i] ? cm[i] : B;
+            }
+#pragma unroll
+            for (int i = NB - 1; i >= 0; --i) F = le[i] ? F : cm[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const uint32_t b = uint32_t(i + 1);
+                B = b == s ? cm[i] : B;
+                F = b == s + 1 ? cm[i] : F;
+                le[i] = b <= s;
+            }
         }
         words[uint64_t(t) * N + lane] = B | ((F - B) << 16);
         adapt::update<NB>(cm, le, nm);
