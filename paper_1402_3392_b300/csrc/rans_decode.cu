@@ -46,7 +46,8 @@ constexpr int kPlain = dec::kKindPlain, kBypass = dec::kKindRaw, kBytes = dec::k
               kWide13 = dec::kKindWide13, kWide14 = dec::kKindWide14,
               kBinary = dec::kKindBinary, kAdaptN4 = dec::kKindAdaptN4,
               kAdaptN8 = dec::kKindAdaptN8, kAdaptN16 = dec::kKindAdaptN16,
-              kPlainEarly = dec::kKindPlainEarly, kPlainSpec = dec::kKindPlainSpec;
+              kPlainEarly = dec::kKindPlainEarly, kPlainSpec = dec::kKindPlainSpec,
+              kBytesLat = dec::kKindBytesLat;
 
 // Dynamic shared memory of the W-warp kernel for KIND: the shape's layout,
 // and for the entry-ahead step one entry ring per warp after it (aligned to
@@ -61,7 +62,7 @@ constexpr uint32_t smem_bytes() {
 template <int NT, int KIND, int W>
 __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     constexpr bool RAW = KIND == kBypass;
-    constexpr bool BYTES = KIND == kBytes;
+    constexpr bool BYTES = KIND == kBytes || KIND == kBytesLat;
     constexpr bool ADAPTIVE = KIND == kAdaptive;
     constexpr bool PREFIX = KIND == kPrefix;
     constexpr bool WIDE = KIND == kWide13 || KIND == kWide14;
@@ -102,15 +103,17 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t data_end = offs[p.n_chunks];
     const uint32_t lt = lanemask_lt();
     const uint32_t n_units = p.c_end - p.c_begin;
-    // The entry-ahead step: each warp's entry ring after the shape's layout;
-    // chunks dealt warp-major, so that a message of few chunks spreads over
-    // the SMs one warp each rather than filling a few CTAs.
+    // The entry-ahead step: each warp's entry ring after the shape's layout.
+    // It and the byte-wise latency form deal chunks warp-major, so that a
+    // message of few chunks spreads over the SMs one warp each rather than
+    // filling a few CTAs.
     constexpr bool SPEC = KIND == kPlainSpec;
+    constexpr bool WARP_MAJOR = SPEC || KIND == kBytesLat;
     const uint32_t ering_s =
         SPEC ? ((smem_addr(smem + dec::Shape<W>::kSmemBytes) + dec::kERing - 1) &
                 ~(dec::kERing - 1)) + warp * dec::kERing
              : 0u;
-    const uint32_t q0 = SPEC ? warp * gridDim.x + blockIdx.x : blockIdx.x * W + warp;
+    const uint32_t q0 = WARP_MAJOR ? warp * gridDim.x + blockIdx.x : blockIdx.x * W + warp;
 
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
@@ -196,9 +199,9 @@ uint64_t resident_ctas() {
 template <int NT, int KIND, int W>
 int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
     using S = dec::Shape<W>;
-    // The entry-ahead step deals chunks warp-major: a CTA per chunk up to the
-    // resident limit.
-    const uint64_t want = KIND == kPlainSpec ? uint64_t(p.c_end - p.c_begin)
+    // The entry-ahead step and the byte-wise latency form deal chunks
+    // warp-major: a CTA per chunk up to the resident limit.
+    const uint64_t want = (KIND == kPlainSpec || KIND == kBytesLat) ? uint64_t(p.c_end - p.c_begin)
                                              : ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W));
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     kernel_for<NT, KIND, W>()<<<grid, S::kThreads, smem_bytes<KIND, W>(), stream>>>(p);
@@ -226,6 +229,12 @@ int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
 // us, 148 chunks 166.8 -> 150.7 us, 296 chunks 166.3 -> 152.4 us; at 444 to
 // 1184 chunks the two are within 1 %.
 constexpr uint64_t kSpecMaxChunks = 296;
+// Byte-wise messages of up to this many chunks (24 per SM) take the latency
+// form (dec::kKindBytesLat), chunks dealt warp-major.  Measured on B300
+// (chunks of 64 Ki symbols, against the block-major two-pass form): 888
+// chunks 276 -> 207 us, 1776 chunks 277 -> 225 us, 2369 chunks 327 -> 285
+// us, 3552 chunks 327 -> 323 us, 4736 chunks 424 -> 453 us.
+constexpr uint64_t kBytesLatMaxChunks = 3552;
 
 template <int NT, int KIND>
 int launch_decode(DecodeParams &p, cudaStream_t stream) {
@@ -247,6 +256,13 @@ int launch_decode(DecodeParams &p, cudaStream_t stream) {
         }
         if (n_range < cap8 * dec::kWarps)
             return launch_shape<NT, KIND, dec::kWarps>(p, cap8, stream);
+    }
+    if constexpr (KIND == kBytes) {
+        if (n_range <= kBytesLatMaxChunks) {
+            const uint64_t cap_l = resident_ctas<NT, kBytesLat, dec::kWarpsOne>();
+            if (!cap_l) return RANS_ERR_CUDA;
+            return launch_shape<NT, kBytesLat, dec::kWarpsOne>(p, cap_l, stream);
+        }
     }
     if constexpr (KIND == kPlain || KIND == kBytes || KIND == kBinary) {
         const uint64_t cap = resident_ctas<NT, KIND, dec::kWarpsOne>();

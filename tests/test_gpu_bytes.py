@@ -135,6 +135,31 @@ def test_bytes_decode_oracle_messages_and_damage(rlib, orc, cuda):
             assert np.array_equal(out.cpu().numpy()[c * 8192:(c + 1) * 8192], want)
 
 
+# Chunk counts on both sides of the decoder's switch on a B300 (148 SMs):
+# messages of up to 3552 chunks take the latency form (both digit passes
+# issued together, chunks dealt warp-major), larger ones the two-pass form.
+@pytest.mark.parametrize("n_chunks,N,kind", [(1, 32, "rare"), (148, 32, "rare"), (3552, 32, "rare"),
+                                             (3553, 32, "rare"), (4736, 32, "rare"),
+                                             (3552, 32, "zipf256"), (3553, 32, "zipf256"),
+                                             (3552, 7, "rare"), (3553, 7, "rare")])
+def test_bytes_every_launch_shape(rlib, orc, cuda, n_chunks, N, kind):
+    """A byte-wise message of n_chunks chunks of 96 symbols (the last one
+    ragged) is the oracle's, and the oracle's message decodes back, whichever
+    form of the step the decoder launches for it."""
+    import torch
+
+    CS = 96
+    rng = np.random.default_rng(n_chunks * 100 + N + len(kind))
+    freq = model(rlib, kind, rng)
+    sym = draw(rng, freq, (n_chunks - 1) * CS + 37, kind)
+    msg, out = gpu_pair(rlib, cuda, sym, freq, N, CS)
+    ref = orc.encode_message_bytes(sym, freq, N=N, chunk_symbols=CS)
+    assert np.array_equal(msg, ref)
+    assert np.array_equal(out, sym)
+    back, _ = rlib.decode_bytes(torch.from_numpy(ref).to(cuda), sym.size, freq, N, CS)
+    assert np.array_equal(back.cpu().numpy(), sym)
+
+
 def test_bytes_many_chunks(rlib, orc, cuda):
     rng = np.random.default_rng(41)
     freq = model(rlib, "dirichlet", rng)
