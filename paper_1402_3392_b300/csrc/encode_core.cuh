@@ -623,8 +623,9 @@ __device__ __forceinline__ void encode_step_raw(uint32_t &x, uint32_t &wp, uint3
 // the next step.  Measured on B300, against the form below (before the
 // deferral; with it one 1 MiB chunk takes 1211 us): one 1 MiB chunk 1991 -> 1347 us,
 // 592 chunks of 64 Ki symbols 190.6 -> 156.5 us, but one wave (3552 chunks)
-// 319.0 -> 327.2 us and 1 GiB 1236 -> 1283 us (the launcher's choice:
-// rans_encode.cu kLatMaxChunks).  Either form alone gains nothing (1 MiB
+// 319.0 -> 327.2 us and 1 GiB 1236 -> 1283 us; with the deferral it is the
+// faster form up to 4736 chunks (the launcher's choice: rans_encode.cu
+// kLatMaxChunks).  Either form alone gains nothing (1 MiB
 // chunk: 1985 -> 1948 us with the early table loads, 1988 -> 2000 us with
 // the state first).
 template <int NT, bool PREFETCH, bool RAW = false, bool BYTES = false, bool ADAPT = false,

@@ -195,13 +195,15 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 }
 
 // Plain messages of 32 coders and up to this many chunks take the encoder's
-// latency form (encode_chunk's LAT): two thirds of a wave of the placing
+// latency form (encode_chunk's LAT): up to a wave and a third of the placing
 // coder's warps (3 CTAs of 8 warps per SM on 148 SMs), where the SM has too
 // few warps to hide a step's latencies.  Measured on B300 (chunks of 64 Ki
 // symbols, latency form against the other): 1184 chunks 202.0 -> 165.3 us,
-// 1776 chunks 239.2 -> 221.4 us, 2368 chunks 251.9 -> 232.7 us, but 2960
-// chunks 310.2 -> 314.5 us and 3552 chunks 319.0 -> 327.2 us.
-constexpr uint32_t kLatMaxChunks = 2368;
+// 2368 chunks 251.9 -> 232.7 us; with each step's ballot and store deferred
+// into the next step, 2960 chunks 312.6 -> 304.8 us, 4144 chunks 419.2 ->
+// 404.0 us, 4736 chunks 430.7 -> 416.2 us, but 5328 chunks 470.7 -> 477.8 us
+// and 7104 chunks 579.2 -> 605.2 us.
+constexpr uint32_t kLatMaxChunks = 4736;
 
 template <int NT, int KIND, bool PLACE = false>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
@@ -211,15 +213,26 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
         kernel = p.c_end - p.c_begin <= kLatMaxChunks ? encode_kernel<NT, KIND, PLACE, true>
                                                       : encode_kernel<NT, KIND, PLACE, false>;
     else kernel = encode_kernel<NT, KIND, PLACE>;
+    // Warps per CTA: kWarps, but for the latency form of a placing launch as
+    // few as spread the message's chunks over all SMs (chunks come from the
+    // ticket counter, so any CTA size covers them all).  Measured on B300
+    // (chunks of 64 Ki symbols, 8-warp CTAs against these): 16 chunks 127.5
+    // -> 102.6 us, 148 chunks 129.0 -> 105.6 us, 592 chunks 149.9 -> 130.4
+    // us; from 1184 chunks (8 warps again) the same.
+    uint64_t warps = kWarps;
+    if constexpr (KIND == kPlain && NT == 32 && PLACE)
+        if (p.c_end - p.c_begin <= kLatMaxChunks)
+            warps = std::min<uint64_t>(
+                kWarps, std::max<uint64_t>(1, ceil_div(p.c_end - p.c_begin, sm_count())));
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, kSmemBytes) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, int(warps * 32),
+                                                      kSmemBytes) != cudaSuccess ||
         per_sm <= 0)
         return RANS_ERR_CUDA;
-    const uint64_t want = ceil_div(p.c_end - p.c_begin, kWarps);
+    const uint64_t want = ceil_div(p.c_end - p.c_begin, warps);
     const uint64_t cap = uint64_t(per_sm) * sm_count();
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    kernel<<<grid, kWarps * 32, kSmemBytes, stream>>>(p);
+    kernel<<<grid, unsigned(warps * 32), kSmemBytes, stream>>>(p);
     return check_launch();
 }
 
