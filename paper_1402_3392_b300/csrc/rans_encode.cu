@@ -4,6 +4,7 @@
 // copies the chunk into the message); pieces of a message (host-memory
 // encoding) use a scan of the chunk sizes and a separate copy.
 #include <algorithm>
+#include <deque>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -205,6 +206,37 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 // and 7104 chunks 579.2 -> 605.2 us.
 constexpr uint32_t kLatMaxChunks = 4736;
 
+// Dynamic shared memory of a CTA of w warps: the table, the rings' alignment
+// slack, w rings and the CTA-state words.  The single-message kernels touch
+// only the table and their warps' rings.
+constexpr uint32_t smem_for_warps(uint64_t w) {
+    return uint32_t(enc::kTabBytes + enc::kRing + w * enc::kRing + 64);
+}
+
+// Resident CTAs per SM of `kernel` with CTAs of w = 1 .. kWarps warps
+// (per_sm[w]; 0 where none fits), computed once per device and kernel.
+const int *occupancy_by_warps(void (*kernel)(EncodeParams)) {
+    struct Entry {
+        int dev;
+        void (*k)(EncodeParams);
+        int per_sm[kWarps + 1];
+    };
+    static std::mutex mu;
+    static std::deque<Entry> cache;  // push_back leaves earlier entries in place
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry &e : cache)
+        if (e.dev == dev && e.k == kernel) return e.per_sm;
+    Entry e{dev, kernel, {0}};
+    for (uint64_t w = 1; w <= uint64_t(kWarps); ++w)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.per_sm[w], kernel, int(w * 32),
+                                                          smem_for_warps(w)) != cudaSuccess)
+            return nullptr;
+    cache.push_back(e);
+    return cache.back().per_sm;
+}
+
 template <int NT, int KIND, bool PLACE = false>
 int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     void (*kernel)(EncodeParams);
@@ -213,26 +245,37 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
         kernel = p.c_end - p.c_begin <= kLatMaxChunks ? encode_kernel<NT, KIND, PLACE, true>
                                                       : encode_kernel<NT, KIND, PLACE, false>;
     else kernel = encode_kernel<NT, KIND, PLACE>;
-    // Warps per CTA: kWarps, but for the latency form of a placing launch as
-    // few as spread the message's chunks over all SMs (chunks come from the
-    // ticket counter, so any CTA size covers them all).  Measured on B300
-    // (chunks of 64 Ki symbols, 8-warp CTAs against these): 16 chunks 127.5
-    // -> 102.6 us, 148 chunks 129.0 -> 105.6 us, 592 chunks 149.9 -> 130.4
-    // us; from 1184 chunks (8 warps again) the same.
+    const int *per_sm = occupancy_by_warps(kernel);
+    if (!per_sm || per_sm[kWarps] <= 0) return RANS_ERR_CUDA;
+    const uint64_t n = p.c_end - p.c_begin, sms = sm_count();
+    // Warps per CTA: kWarps, but a placing launch whose chunks all start at
+    // once (at most one wave) takes the CTA size that gives the busiest SM the
+    // fewest warps, the larger of equal ones: the message is done when that
+    // SM's chunks are, and the others wait for it.  Its chunks come from the
+    // ticket counter, so any CTA size covers them all.  Measured on B300
+    // (chunks of 64 Ki symbols, 8-warp CTAs against the chosen size): plain
+    // 148 chunks 129.0 -> 105.6 us (1 warp), 592 chunks 149.9 -> 130.4 us (4
+    // warps), 2960 chunks 306.3 -> 271.7 us; adaptive-n models over 16
+    // symbols, 4096 chunks, 2407 -> 2263 us; over 8, 1405 -> 1301 us.
     uint64_t warps = kWarps;
-    if constexpr (KIND == kPlain && NT == 32 && PLACE)
-        if (p.c_end - p.c_begin <= kLatMaxChunks)
-            warps = std::min<uint64_t>(
-                kWarps, std::max<uint64_t>(1, ceil_div(p.c_end - p.c_begin, sm_count())));
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, int(warps * 32),
-                                                      kSmemBytes) != cudaSuccess ||
-        per_sm <= 0)
-        return RANS_ERR_CUDA;
-    const uint64_t want = ceil_div(p.c_end - p.c_begin, warps);
-    const uint64_t cap = uint64_t(per_sm) * sm_count();
+    if constexpr (PLACE && KIND != kWide) {
+        if (n <= uint64_t(per_sm[kWarps]) * sms * kWarps) {
+            uint64_t best = ceil_div(ceil_div(n, uint64_t(kWarps)), sms) * kWarps;
+            for (uint64_t w = kWarps - 1; w >= 1; --w) {
+                const uint64_t ctas = ceil_div(n, w);
+                if (per_sm[w] <= 0 || ctas > uint64_t(per_sm[w]) * sms) continue;
+                const uint64_t busiest = ceil_div(ctas, sms) * w;
+                if (busiest < best) {
+                    best = busiest;
+                    warps = w;
+                }
+            }
+        }
+    }
+    const uint64_t want = ceil_div(n, warps);
+    const uint64_t cap = uint64_t(per_sm[warps]) * sms;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
-    kernel<<<grid, unsigned(warps * 32), kSmemBytes, stream>>>(p);
+    kernel<<<grid, unsigned(warps * 32), smem_for_warps(warps), stream>>>(p);
     return check_launch();
 }
 

@@ -138,12 +138,15 @@ def test_more_chunks_than_resident_warps(rlib, orc, cuda, n_chunks, N, CS):
 # a B300 (148 SMs, 4 CTAs of 8 warps each): the entry-ahead step up to two
 # chunks per SM (296), the early-word step up to half a wave of 8-warp CTAs
 # (2368 chunks), the plain step in 8-warp CTAs below a wave (4736), 12-warp
-# CTAs from there.  (The encoder's latency form covers up to 4736 chunks, in
-# CTAs of fewer than 8 warps up to 1036 chunks.)
+# CTAs from there.  (The encoder's latency form covers up to 4736 chunks; a
+# message of at most one wave of the encoder's warps takes the CTA size that
+# loads the busiest SM least: 1 warp for up to 148 chunks, 4 for 592, 7 for
+# 1036, 5 for 2960.)
 @pytest.mark.parametrize("n_chunks,N", [(1, 32), (148, 32), (296, 32), (297, 32), (2367, 32),
                                         (2368, 32), (2369, 32), (4735, 32), (4736, 32),
                                         (4737, 32), (16, 32), (592, 32), (1036, 32),
-                                        (1037, 32), (296, 7), (297, 7), (2368, 7), (2369, 7),
+                                        (1037, 32), (2960, 32), (296, 7), (297, 7), (2368, 7),
+                                        (2369, 7),
                                         (4736, 7)])
 def test_every_launch_shape(rlib, orc, cuda, n_chunks, N):
     """A message of n_chunks chunks of 96 symbols (the last one ragged) is
