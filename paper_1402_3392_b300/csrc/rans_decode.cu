@@ -28,6 +28,7 @@ struct DecodeParams {
     uint32_t c_begin;   // chunks [c_begin, c_end) are decoded by this launch
     uint32_t c_end;
     uint32_t kind;      // kPlain, kBypass (raw words after their symbols) or kBytes
+    uint32_t warp_major;  // 1: chunks dealt warp-major across the grid (set by the launcher)
     uint16_t *raw_out;  // bypass messages: raw word (or 0) per symbol
     uint16_t freq[RANS_MAX_ALPHABET];
     uint8_t raw_words[RANS_MAX_ALPHABET];  // bypass: raw words symbol s carries (0 or 1)
@@ -113,7 +114,8 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
         SPEC ? ((smem_addr(smem + dec::Shape<W>::kSmemBytes) + dec::kERing - 1) &
                 ~(dec::kERing - 1)) + warp * dec::kERing
              : 0u;
-    const uint32_t q0 = WARP_MAJOR ? warp * gridDim.x + blockIdx.x : blockIdx.x * W + warp;
+    const uint32_t q0 = (WARP_MAJOR || p.warp_major) ? warp * gridDim.x + blockIdx.x
+                                                     : blockIdx.x * W + warp;
 
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
@@ -200,9 +202,20 @@ template <int NT, int KIND, int W>
 int launch_shape(DecodeParams &p, uint64_t cap, cudaStream_t stream) {
     using S = dec::Shape<W>;
     // The entry-ahead step and the byte-wise latency form deal chunks
-    // warp-major: a CTA per chunk up to the resident limit.
-    const uint64_t want = (KIND == kPlainSpec || KIND == kBytesLat) ? uint64_t(p.c_end - p.c_begin)
-                                             : ceil_div(uint64_t(p.c_end - p.c_begin), uint64_t(W));
+    // warp-major: a CTA per chunk up to the resident limit.  So does every
+    // launch of at most one wave of chunks: all its CTAs are resident at once,
+    // so each SM gets its share of chunks to within one per CTA, where whole
+    // CTAs of W chunks left some SMs a CTA more than others.  Measured on
+    // B300 (chunks of 64 Ki symbols, block-major against warp-major): plain
+    // 2400 chunks 219.6 -> 205.4 us, 4000 chunks 266.7 -> 244.2 us; byte-wise
+    // 4000 chunks 422.0 -> 391.0 us; adaptive-n over 8 symbols, 4096 chunks,
+    // 910 -> 822 us.  Launches of more than a wave stay block-major (1 GiB:
+    // 839 -> 978 us warp-major).
+    const uint64_t n_range = p.c_end - p.c_begin;
+    p.warp_major = n_range <= cap * W ? 1u : 0u;
+    const uint64_t want = (KIND == kPlainSpec || KIND == kBytesLat || p.warp_major)
+                              ? n_range
+                              : ceil_div(n_range, uint64_t(W));
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));
     kernel_for<NT, KIND, W>()<<<grid, S::kThreads, smem_bytes<KIND, W>(), stream>>>(p);
     return check_launch();
