@@ -64,6 +64,12 @@ struct Geometry {
 // costs the warp an issue, a wait and bookkeeping.  With raw words (bypass
 // messages, one chunk per warp): 1 KiB copies waited 1 KiB after issue.
 using GeoOne = Geometry<1024, kNSeg, 16>;
+// 32-step groups (half the ring-event checks and branches a step) for the
+// 12-warp kernel's plain chunks, where the SM is full.  Measured on B300: 1
+// GiB 851 -> 840 us, 10656 chunks 546 -> 538 us; the byte-wise and binary
+// steps spill with them (byte-wise 1 GiB 1288 -> 1298 us), and 8-warp CTAs
+// under a wave gain nothing (4000 chunks 243 -> 248 us).
+using GeoOneLong = Geometry<1024, kNSeg, 32>;
 using GeoPair = Geometry<512, kNSeg, 16>;
 using GeoRaw = Geometry<1024, kNSeg, 16, 128>;
 // Prefix messages read up to one 32-bit word per lane and step: as GeoRaw.
@@ -75,7 +81,8 @@ using GeoPrefix = Geometry<1024, kNSeg, 16, 128>;
 using GeoSpec = Geometry<1024, kNSeg, 16, 128>;
 static_assert(GeoSpec::kLag == 1 && GeoSpec::kSeg * (GeoSpec::kNSeg - 1 - GeoSpec::kLag) >= 2048,
               "the entry-ahead step converts 2 KiB of resident words ahead");
-static_assert(GeoOne::kRing == kWarpRing && GeoPair::kRing * kChains == kWarpRing &&
+static_assert(GeoOne::kRing == kWarpRing && GeoOneLong::kRing == kWarpRing &&
+                  GeoPair::kRing * kChains == kWarpRing &&
                   GeoRaw::kRing == kWarpRing,
               "ring sizes");
 
@@ -1208,7 +1215,8 @@ __device__ __forceinline__ uint32_t const_chunk_raw(const uint8_t *msg, uint32_t
 // kNoConst: the model has one symbol with f = M.  UNI: chain_open's UNI (the
 // batched decoder's form).  Returns the warp-uniform status (RANS_OK, or the
 // first of RANS_ERR_CORRUPT / RANS_ERR_TIMEOUT found).
-template <int NT, bool PAIR, int KIND = kKindPlain, bool UNI = false>  // NT = 32: all lanes are coders
+template <int NT, bool PAIR, int KIND = kKindPlain, bool UNI = false,
+          bool LONG = false>  // NT = 32: all lanes are coders; LONG: GeoOneLong
 __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, const uint8_t *msg,
                                                   uint32_t data0, const uint32_t *offs,
                                                   uint32_t data_end, uint32_t c, uint32_t count,
@@ -1228,7 +1236,9 @@ __device__ __forceinline__ uint32_t decode_chunks(WarpRings &w, uint32_t tab_s, 
         RAW, GeoRaw,
         typename std::conditional<SPEC, GeoSpec,
         typename std::conditional<PREFIX, GeoPrefix,
-                                  typename std::conditional<PAIR, GeoPair, GeoOne>::type>::type>::type>::type;
+                                  typename std::conditional<
+                                      PAIR, GeoPair,
+                                      typename std::conditional<LONG, GeoOneLong, GeoOne>::type>::type>::type>::type>::type;
     constexpr bool kFullWarp = NT == 32;
     const uint32_t N = NT ? NT : N_rt;
     const bool lane_on = lane < N;

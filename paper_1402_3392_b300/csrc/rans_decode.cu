@@ -117,6 +117,8 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t q0 = (WARP_MAJOR || p.warp_major) ? warp * gridDim.x + blockIdx.x
                                                      : blockIdx.x * W + warp;
 
+    // 32-step groups for plain chunks in the 12-warp shape
+    constexpr bool LONG = W == dec::kWarpsOne && KIND == kPlain;
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
         uint32_t st;
@@ -139,13 +141,13 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
                                                      p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
                                                      nullptr, p.n_alpha);
         else if (BINARY)  // f_0 and f_1 ride in the table and flag arguments
-            st = dec::decode_chunks<NT, false, KIND>(wr, p.freq[0], p.msg, p.data0, offs,
-                                                     data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
-                                                     cs, lane, lt, nullptr, p.freq[1]);
+            st = dec::decode_chunks<NT, false, KIND, false, LONG>(
+                wr, p.freq[0], p.msg, p.data0, offs, data_end, c, 1, p.n_sym, p.CS, p.N, p.out,
+                cs, lane, lt, nullptr, p.freq[1]);
         else  // plain (KIND kPlain, kPlainEarly or kPlainSpec; the entry ring rides in flags_s)
-            st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
-                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
-                                                     nullptr, ering_s);
+            st = dec::decode_chunks<NT, false, KIND, false, LONG>(
+                wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1, p.n_sym, p.CS, p.N, p.out, cs,
+                lane, lt, nullptr, ering_s);
         if (st != RANS_OK && lane == 0) report(p.status, st);
         if (wr.timeouts) break;
     }
