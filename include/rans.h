@@ -691,6 +691,27 @@ int rans_check_gather_ceiling(uint32_t steps, uint8_t *d_out, uint64_t out_size,
 uint64_t rans_check_gather_ceiling_warps(void);
 
 /*
+ * rans_check_cta_warps -- the launch rule the placing encoders apply to a
+ * message whose chunks all start at once, exposed for host-side tests (no
+ * CUDA call, no step of the paper's method).  With one chunk per warp at a
+ * time, the message is done when the SM given the most warps is: of the CTA
+ * sizes w = 1 .. max_warps, the one whose ceil(n_units / w) CTAs, spread
+ * evenly over sms SMs, give the busiest SM the fewest warps, the larger w of
+ * equal ones.
+ *
+ * n_units   : chunks of the launch.
+ * sms       : SMs of the device.
+ * per_sm    : host, max_warps + 1 entries; per_sm[w] = w-warp CTAs an SM
+ *             holds (0: none fits); per_sm[0] unused.  A launch of more than
+ *             per_sm[max_warps] * sms * max_warps units keeps max_warps.
+ * max_warps : 1 .. 32.
+ * Returns the chosen warps per CTA, or 0 for a null per_sm or a max_warps
+ * out of range.
+ */
+uint32_t rans_check_cta_warps(uint64_t n_units, uint32_t sms, const int32_t *per_sm,
+                              uint32_t max_warps);
+
+/*
  * Checked builds (a test build compiled with -DRANS_CHECKED; the library
  * built normally answers RANS_ERR_INVALID_ARG to both calls).  The kernels
  * then test their invariants as they run and count the ones that fail (the

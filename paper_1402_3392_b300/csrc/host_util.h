@@ -74,6 +74,32 @@ int copy_streams(CopyStreams *cs);
 // Stream `waiter` waits for the work enqueued on `signaler` so far.
 bool join(cudaStream_t waiter, cudaStream_t signaler);
 
+// CTA size, 1 .. max_warps warps, for a launch whose n units (chunks, one
+// per warp at a time) all start at once: the one that gives the busiest SM
+// the fewest warps, the larger of equal ones.  per_sm[w] (w = 1 .. max_warps)
+// is the number of w-warp CTAs an SM holds (0: none fits).  A launch of more
+// than one wave of max_warps-warp CTAs (or one that fits no CTA) keeps
+// max_warps.
+inline uint32_t balanced_cta_warps(uint64_t n, uint64_t sms, const int *per_sm,
+                                   uint32_t max_warps) {
+    if (sms == 0 || max_warps == 0 || per_sm[max_warps] <= 0 ||
+        n > uint64_t(per_sm[max_warps]) * sms * max_warps)
+        return max_warps;
+    auto cdiv = [](uint64_t a, uint64_t b) { return (a + b - 1) / b; };
+    uint32_t warps = max_warps;
+    uint64_t best = cdiv(cdiv(n, max_warps), sms) * max_warps;
+    for (uint32_t w = max_warps - 1; w >= 1; --w) {
+        const uint64_t ctas = cdiv(n, w);
+        if (per_sm[w] <= 0 || ctas > uint64_t(per_sm[w]) * sms) continue;
+        const uint64_t busiest = cdiv(ctas, sms) * w;
+        if (busiest < best) {
+            best = busiest;
+            warps = w;
+        }
+    }
+    return warps;
+}
+
 inline int check_launch() {
     return cudaGetLastError() == cudaSuccess ? RANS_OK : RANS_ERR_CUDA;
 }

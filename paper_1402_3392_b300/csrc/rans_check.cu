@@ -225,6 +225,12 @@ extern "C" int rans_check_division(uint32_t method, uint32_t log2m, uint64_t *d_
     return check_launch();
 }
 
+extern "C" uint32_t rans_check_cta_warps(uint64_t n_units, uint32_t sms, const int32_t *per_sm,
+                                         uint32_t max_warps) {
+    if (!per_sm || max_warps == 0 || max_warps > 32) return 0;
+    return rans::balanced_cta_warps(n_units, sms, per_sm, max_warps);
+}
+
 extern "C" uint64_t rans_check_gather_ceiling_warps(void) {
     static_assert(3 * (kCeilSmem + 1024) <= 233472, "three CTAs per SM");
     if (cudaFuncSetAttribute(gather_ceiling_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -258,20 +258,7 @@ int launch_encode(const EncodeParams &p, cudaStream_t stream) {
     // warps), 2960 chunks 306.3 -> 271.7 us; adaptive-n models over 16
     // symbols, 4096 chunks, 2407 -> 2263 us; over 8, 1405 -> 1301 us.
     uint64_t warps = kWarps;
-    if constexpr (PLACE && KIND != kWide) {
-        if (n <= uint64_t(per_sm[kWarps]) * sms * kWarps) {
-            uint64_t best = ceil_div(ceil_div(n, uint64_t(kWarps)), sms) * kWarps;
-            for (uint64_t w = kWarps - 1; w >= 1; --w) {
-                const uint64_t ctas = ceil_div(n, w);
-                if (per_sm[w] <= 0 || ctas > uint64_t(per_sm[w]) * sms) continue;
-                const uint64_t busiest = ceil_div(ctas, sms) * w;
-                if (busiest < best) {
-                    best = busiest;
-                    warps = w;
-                }
-            }
-        }
-    }
+    if constexpr (PLACE && KIND != kWide) warps = balanced_cta_warps(n, sms, per_sm, kWarps);
     const uint64_t want = ceil_div(n, warps);
     const uint64_t cap = uint64_t(per_sm[warps]) * sms;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, cap)));

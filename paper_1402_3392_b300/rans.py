@@ -106,6 +106,7 @@ def _load() -> C.CDLL:
         "rans_check_division": (i32, [u32, u32, vp, vp]),
         "rans_check_gather_ceiling": (i32, [u32, vp, u64, vp, vp]),
         "rans_check_gather_ceiling_warps": (u64, []),
+        "rans_check_cta_warps": (u32, [u64, u32, vp, u32]),
         "rans_debug_checks": (i32, [vp]),
         "rans_debug_check_selftest": (i32, [vp]),
         "rans_decode_host_work_size": (u64, [u64, u64]),
@@ -723,6 +724,16 @@ def rans_check_division(method: int, log2m: int, d_result, stream=None, check=Tr
 
 def rans_check_gather_ceiling_warps() -> int:
     return int(lib.rans_check_gather_ceiling_warps())
+
+
+def rans_check_cta_warps(n_units: int, sms: int, per_sm, max_warps: int) -> int:
+    """The placing encoders' CTA size for n_units chunks that all start at
+    once (host logic only); per_sm[w] = w-warp CTAs an SM holds, w = 0 ..
+    max_warps (entry 0 unused)."""
+    a = np.ascontiguousarray(per_sm, dtype=np.int32)
+    if a.size < max_warps + 1:
+        raise ValueError("per_sm needs max_warps + 1 entries")
+    return int(lib.rans_check_cta_warps(int(n_units), int(sms), a.ctypes.data, int(max_warps)))
 
 
 def rans_check_gather_ceiling(steps: int, d_out, out_size: int, d_sink, stream=None,
