@@ -117,8 +117,11 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t q0 = (WARP_MAJOR || p.warp_major) ? warp * gridDim.x + blockIdx.x
                                                      : blockIdx.x * W + warp;
 
-    // 32-step groups for plain chunks in the 12-warp shape
-    constexpr bool LONG = W == dec::kWarpsOne && KIND == kPlain;
+    // 32-step groups for plain chunks in the 12-warp shape and for 13/14-bit
+    // chunks (measured on B300, 14-bit model: 1 GiB 1104 -> 1084 us, 4000
+    // chunks 295 -> 288 us; adaptive models over 16 symbols were slower with
+    // them, 1991 -> 2322 us)
+    constexpr bool LONG = (W == dec::kWarpsOne && KIND == kPlain) || WIDE;
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
         uint32_t st;
@@ -133,9 +136,9 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
                                                      c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
                                                      lt);
         else if (WIDE)  // the f/B table goes where bypass messages keep their flags
-            st = dec::decode_chunks<NT, false, KIND>(wr, sm.tab_s, p.msg, p.data0, offs, data_end,
-                                                     c, 1, p.n_sym, p.CS, p.N, p.out, cs, lane,
-                                                     lt, nullptr, sm.fb_s);
+            st = dec::decode_chunks<NT, false, KIND, false, LONG>(
+                wr, sm.tab_s, p.msg, p.data0, offs, data_end, c, 1, p.n_sym, p.CS, p.N, p.out, cs,
+                lane, lt, nullptr, sm.fb_s);
         else if (ADAPTN)  // n rides in the flag argument
             st = dec::decode_chunks<NT, false, KIND>(wr, 0, p.msg, p.data0, offs, data_end, c, 1,
                                                      p.n_sym, p.CS, p.N, p.out, cs, lane, lt,
