@@ -119,8 +119,8 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
 
     // 32-step groups for plain chunks in the 12-warp shape and for 13/14-bit
     // chunks (measured on B300, 14-bit model: 1 GiB 1104 -> 1084 us, 4000
-    // chunks 295 -> 288 us; adaptive models over 16 symbols were slower with
-    // them, 1991 -> 2322 us)
+    // chunks 295 -> 288 us; adaptive models were slower with them: over 16
+    // symbols 1991 -> 2322 us, binary contexts 295 -> 309 us)
     constexpr bool LONG = (W == dec::kWarpsOne && KIND == kPlain) || WIDE;
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
