@@ -65,8 +65,8 @@ struct Geometry {
 // messages, one chunk per warp): 1 KiB copies waited 1 KiB after issue.
 using GeoOne = Geometry<1024, kNSeg, 16>;
 // 32-step groups (half the ring-event checks and branches a step) for the
-// 12-warp kernel's plain chunks, where the SM is full, and for 13/14-bit
-// chunks.  Measured on B300: 1
+// 12-warp kernel's plain chunks, where the SM is full, for the early-word
+// step and for 13/14-bit chunks.  Measured on B300: 1
 // GiB 851 -> 840 us, 10656 chunks 546 -> 538 us; the byte-wise and binary
 // steps spill with them (byte-wise 1 GiB 1288 -> 1298 us), and 8-warp CTAs
 // under a wave gain nothing (4000 chunks 243 -> 248 us).

@@ -117,11 +117,15 @@ __device__ __forceinline__ void decode_body(const DecodeParams &p) {
     const uint32_t q0 = (WARP_MAJOR || p.warp_major) ? warp * gridDim.x + blockIdx.x
                                                      : blockIdx.x * W + warp;
 
-    // 32-step groups for plain chunks in the 12-warp shape and for 13/14-bit
-    // chunks (measured on B300, 14-bit model: 1 GiB 1104 -> 1084 us, 4000
-    // chunks 295 -> 288 us; adaptive models were slower with them: over 16
-    // symbols 1991 -> 2322 us, binary contexts 295 -> 309 us)
-    constexpr bool LONG = (W == dec::kWarpsOne && KIND == kPlain) || WIDE;
+    // 32-step groups for plain chunks in the 12-warp shape, the early-word
+    // step and 13/14-bit chunks (measured on B300: early-word 297 chunks 166.0
+    // -> 161.3 us, 2368 chunks 191.7 -> 187.1 us; 14-bit model 1 GiB 1104 ->
+    // 1084 us, 4000 chunks 295 -> 288 us; slower with them: adaptive models
+    // over 16 symbols 1991 -> 2322 us, binary contexts 295 -> 309 us, the
+    // byte-wise latency form 193 -> 195 us at 296 chunks, binary models in
+    // 8-warp CTAs 232 -> 240 us at 4000 chunks)
+    constexpr bool LONG =
+        (W == dec::kWarpsOne && KIND == kPlain) || KIND == kPlainEarly || WIDE;
     for (uint32_t q = q0; q < n_units; q += gridDim.x * W) {
         const uint32_t c = p.c_begin + q;
         uint32_t st;
